@@ -1,0 +1,79 @@
+"""Seeded synthetic inputs for the linear C-SVC dual (arXiv 1910.01312).
+
+This module only draws data; it holds none of the method's arithmetic.  Both
+the FP64 oracle (tests, CPU baseline) and the CUDA path read the arrays it
+returns, so the two sides always see the same bytes.
+
+The paper evaluates on LIBSVM datasets (Sec. 4, Table 1), which are not
+available here; the workloads below stand in for them with the shapes, value
+distributions and label structure of a two-class problem with label noise.
+Every generator is keyed by (workload id, seed) through numpy's PCG64.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+_IDS = {"small": 0, "gauss2000": 1, "gauss1m": 2, "csr": 3, "mnist_like": 4, "warm": 5}
+
+
+def _rng(kind: str, seed: int) -> np.random.Generator:
+    return np.random.default_rng([_IDS[kind], int(seed)])
+
+
+def balanced_labels(rng: np.random.Generator, n: int) -> np.ndarray:
+    """n/2 (+1) and n - n/2 (-1) labels in random order, int8."""
+    y = np.empty(n, np.int8)
+    y[: (n + 1) // 2] = 1
+    y[(n + 1) // 2:] = -1
+    rng.shuffle(y)
+    return y
+
+
+def flip_labels(rng: np.random.Generator, y: np.ndarray, frac: float) -> np.ndarray:
+    """Flip exactly round(frac*n) labels chosen uniformly without replacement."""
+    y = y.copy()
+    k = int(round(frac * y.size))
+    if k:
+        idx = rng.choice(y.size, size=k, replace=False)
+        y[idx] = -y[idx]
+    return y
+
+
+def gaussian_two_class(n: int, q: int, mean_scale: float, var=None, flip: float = 0.0,
+                       seed: int = 0, dtype=np.float64, kind: str = "small"):
+    """Rows x_i = y_i * mean_scale/sqrt(q) * 1 + sqrt(var) * eps_i, eps ~ N(0, I_q),
+    drawn with the true label, then a fraction `flip` of the labels flipped.
+
+    Returns (X [n x q, row-major, dtype], y [n] int8 in {-1,+1})."""
+    rng = _rng(kind, seed)
+    y_true = balanced_labels(rng, n)
+    mu = mean_scale / np.sqrt(q)
+    sd = np.ones(q) if var is None else np.sqrt(np.asarray(var, dtype=np.float64))
+    X = np.empty((n, q), dtype=dtype)
+    step = 1 << 16
+    for s in range(0, n, step):
+        e = rng.standard_normal((min(step, n - s), q))
+        X[s:s + e.shape[0]] = (y_true[s:s + e.shape[0], None] * mu + e * sd).astype(dtype)
+    y = flip_labels(rng, y_true, flip)
+    return X, y
+
+
+def small(n: int, q: int, seed: int = 0, dtype=np.float64, mean_scale: float = 1.0,
+          flip: float = 0.1):
+    """Small random two-class problem for unit tests."""
+    return gaussian_two_class(n, q, mean_scale, None, flip, seed, dtype, "small")
+
+
+def gauss2000(seed: int = 0):
+    """n=2000 x q=50 dense FP64, N(+-0.5/sqrt(q) 1, I), balanced, 5% flipped, C=1."""
+    X, y = gaussian_two_class(2000, 50, 0.5, None, 0.05, seed, np.float64, "gauss2000")
+    return X, y, 1.0
+
+
+def gauss1m(seed: int = 0, n: int = 1_000_000, q: int = 128):
+    """n=1e6 x q=128 dense FP32, means +-0.3/sqrt(q) 1, covariance
+    diag(linspace(0.1, 2, q)), 10% labels flipped, C=0.1.  `n` may be lowered
+    for bounded samples of the same distribution."""
+    X, y = gaussian_two_class(n, q, 0.3, np.linspace(0.1, 2.0, q), 0.10, seed, np.float32,
+                              "gauss1m")
+    return X, y, 0.1
