@@ -1,0 +1,306 @@
+#!/usr/bin/env python
+"""Benchmark of the SSsNAL C-SVC solver on GB300.
+
+Metric: time to R_KKT <= 1e-6 per SVM solve (eq. (4.1)), on the dense
+two-Gaussian workload n = 1,000,000 x q = 128 FP32, C = 0.1 (means
++-0.3/sqrt(q) 1, covariance diag(linspace(0.1, 2, q)), 10% labels flipped),
+plus the achieved HBM bandwidth of the forward product A v against the
+measured copy bandwidth.  One "step" is one whole solve from alpha = 0.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun, one independent replica per rank (weak scaling,
+no collective on the data path; each rank draws its own seed).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "gauss1m: dense two-Gaussian C-SVC, n=1000000 x q=128 FP32, C=0.1, 10% label noise"
+METRIC = "time-to-KKT<=1e-6 per SVM solve"
+N_FULL = 1_000_000
+N_CPU_SAMPLE = 50_000      # oracle sample for the cpu_baseline leg (~10-30 s)
+N_REF_SAMPLE = 20_000      # oracle sample per step of the reference arm
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _traffic(kernel_src: str, key: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current source of the kernel (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(path))[key]
+        sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+        if d.get("src_sha") != sha:
+            return None
+        return float(d["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+def cpu_baseline(n_sample, seed=0):
+    import oracle
+    import datagen
+    X, y, C = datagen.gauss1m(seed, n=n_sample)
+    t0 = time.perf_counter()
+    r = oracle.solve(X, y, C, tol=1e-6)
+    dt = time.perf_counter() - t0
+    return dt, r
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 CPU oracle, as it stands, on the host cores."""
+    if rank != 0:
+        return 0
+    times = []
+    r = None
+    for it in range(args.warmup + args.steps):
+        dt, r = cpu_baseline(N_REF_SAMPLE, seed=it % 3)
+        if it >= args.warmup:
+            times.append(dt)
+    scale = N_FULL / N_REF_SAMPLE
+    ms = 1e3 * statistics.mean(times) * scale
+    sample = (f"oracle (plain C, FP64, 1 thread) on n={N_REF_SAMPLE} rows of the same distribution, "
+              f"one solve to R_KKT<=1e-6 per step; time scaled linearly by n to n={N_FULL}")
+    line = {"impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": ms, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "solve": {"outer": r["outer"], "inner": r["inner_total"], "kkt": r["kkt"]}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=None)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+
+    import datagen
+    import paper_1910_01312_gb300 as P
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    P.load()
+    X, y, C = datagen.gauss1m(seed=rank)
+    n, q = X.shape
+    Xd = torch.from_numpy(X).cuda()
+    yd = torch.from_numpy(y).cuda()
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+
+    def solver(prec):
+        return P.Solver(Xd, yd, C_=C, tol=1e-6, precision=prec, stream=sptr)
+
+    alpha = torch.zeros(n, dtype=torch.float64, device="cuda")
+    w = torch.zeros(q, dtype=torch.float64, device="cuda")
+
+    # ---- chosen form (mixed precision), device-resident inputs ----
+    s = solver(P.PREC_MIXED)
+    for _ in range(args.warmup):
+        r = s.solve(alpha, w)
+    s.set_timing(True)
+    s.stats(reset=True)
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    results = []
+    for _ in range(args.steps):
+        results.append(s.solve(alpha, w))
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    t_ms = ev0.elapsed_time(ev1)
+    st = s.stats(reset=True)
+    s.set_timing(False)
+    t_max = t_ms
+    if dist is not None:
+        tt = torch.tensor([t_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    ms_per_step = t_max / args.steps
+    value = t_max / (args.steps * world)
+    r = results[-1]
+
+    # roofline of the dominant kernel: the forward product z = A v
+    peak, peak_kind = _peaks()
+    alg_bytes = n * q * X.itemsize + n * 1 + n * 8 + q * 8       # X + y read, z written, v read
+    mv_ms = st["matvec_ms"] / max(st["matvec_calls"], 1)
+    achieved = alg_bytes / (mv_ms * 1e-3) / 1e9
+    traffic = _traffic(os.path.join(ROOT, "paper_1910_01312_gb300", "csrc", "k_matvec.cu"), "matvec_gauss1m")
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "kernel": "matvec_kernel (z = A v)",
+                "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": mv_ms,
+                "launches_per_step": st["matvec_calls"] / args.steps, "peak_source": f"{peak_kind} hbm_gbs"}
+    breakdown = {k: st[k] / args.steps for k in ("matvec_ms", "rmatvec_ms", "proj_ms", "newton_ms")}
+    breakdown.update({k: st[k] / args.steps for k in ("matvec_calls", "rmatvec_calls", "proj_calls",
+                                                       "newton_calls", "host_syncs")})
+    gpu_launches = int(st["launches"])
+    s.close()
+
+    # ---- plain FP64 form (the baseline the chosen form must beat) ----
+    plain = None
+    if not args.no_plain:
+        sp = solver(P.PREC_PLAIN_FP64)
+        sp.solve(alpha, w)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rp = sp.solve(alpha, w)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        plain = {"ms_per_solve": e0.elapsed_time(e1), "outer": rp["outer_iters"], "inner": rp["inner_iters_total"],
+                 "kkt": rp["kkt"], "objective": rp["objective"]}
+        sp.close()
+
+    # ---- end to end through the C ABI with host buffers ----
+    e2e_steps = args.e2e_steps or max(1, min(args.steps, 3))
+    Xh = torch.from_numpy(X).pin_memory()
+    yh = torch.from_numpy(y).pin_memory()
+    ah = torch.zeros(n, dtype=torch.float64).pin_memory()
+    wh = torch.zeros(q, dtype=torch.float64).pin_memory()
+    se = P.Solver(Xh, yh, C_=C, tol=1e-6, precision=P.PREC_MIXED, stream=sptr)   # warm-up of the host path
+    se.solve(ah, wh)
+    se.close()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        se = P.Solver(Xh, yh, C_=C, tol=1e-6, precision=P.PREC_MIXED, stream=sptr)
+        se.solve(ah, wh)
+        se.close()
+    torch.cuda.synchronize()
+    e2e_ms = 1e3 * (time.perf_counter() - t0) / e2e_steps
+    if dist is not None:
+        tt = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+    e2e = {"value": e2e_ms / world, "unit": "ms", "h2d_bytes_per_step": int(X.nbytes + y.nbytes),
+           "d2h_bytes_per_step": int(8 * n + 8 * q)}
+
+    # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1) ----
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        dt, rr = cpu_baseline(N_CPU_SAMPLE)
+        cpu = {"value": 1e3 * dt * N_FULL / N_CPU_SAMPLE, "unit": "ms", "cores": 1, "kind": "oracle",
+               "sample": (f"oracle (plain C, FP64, 1 thread) solving n={N_CPU_SAMPLE} rows of the same "
+                          f"distribution to R_KKT<=1e-6 in {dt:.2f} s ({rr['outer']} outer / "
+                          f"{rr['inner_total']} Newton iterations); scaled linearly by n to n={N_FULL}")}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "ms", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "n": n, "q": q, "C": C, "tol": 1e-6, "form": "mixed",
+                           "l2": "inputs larger than L2 (X is 512 MB, L2 129 MB)", "seed": "rank"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
+                "clocks": clk,
+                "solve": {"outer": r["outer_iters"], "inner": r["inner_iters_total"], "kkt": r["kkt"],
+                          "objective": r["objective"], "n_free": r["n_free"], "n_upper": r["n_upper"]},
+                "plain_fp64": plain, "per_step": breakdown}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

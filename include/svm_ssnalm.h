@@ -1,0 +1,212 @@
+/*
+ * svm_ssnalm.h -- C ABI of the GB300 (sm_103a) SSsNAL solver for the
+ * linear-kernel C-SVC dual of arXiv 1910.01312.
+ *
+ * The problem (Sec. 1, eq. (1.2)):
+ *     min_alpha  1/2 alpha' Q alpha - e' alpha
+ *     s.t.       y' alpha = 0,   0 <= alpha_i <= C,
+ * with Q = A A', A = Diag(y) X, X the n x q data matrix (linear kernel).
+ * The paper calls the variable x; this header calls it alpha.
+ *
+ * Method: the augmented Lagrangian method on the restricted dual (Algorithm 1,
+ * multiplier update of eq. (3.5)), whose subproblems are solved by the
+ * semismooth Newton method with Armijo line search (Algorithm 3), using the
+ * projection onto {y'x = 0, 0 <= x <= C} (Sec. 3.2.1), its HS-Jacobian
+ * (Theorem 3.2) and the reduced Newton system of Proposition 3.5.  The stopping
+ * test is the relative KKT residual of eq. (4.1).
+ *
+ * Conventions for every call below:
+ *  - All entry points are extern "C"; no C++ exception crosses them.
+ *  - Pointers marked "device" are CUDA device pointers (for example a torch
+ *    tensor's data_ptr()); "host" pointers are ordinary CPU memory.
+ *  - Work is issued on the stream given in svm_params.stream (NULL = legacy
+ *    default stream).  Calls that return scalars synchronise that stream
+ *    before returning.
+ *  - Errors: every call returns an svm_status; svm_ssnalm_last_error() gives a
+ *    one-line reason for the last failure on a handle.  On error the contents
+ *    of output buffers are unspecified unless stated.
+ *  - Threads: a handle is used by one host thread at a time.
+ */
+#ifndef SVM_SSNALM_H
+#define SVM_SSNALM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct svm_ssnalm svm_ssnalm_t; /* opaque solver handle */
+
+typedef enum {
+    SVM_OK = 0,
+    SVM_ERR_INVALID_ARG = 1,   /* bad size, pointer, C, tol or label        */
+    SVM_ERR_CUDA = 2,          /* a CUDA runtime call failed                */
+    SVM_ERR_OOM = 3,           /* device or host allocation failed          */
+    SVM_ERR_NOT_CONVERGED = 4, /* iteration cap reached; results are filled */
+    SVM_ERR_NUMERIC = 5,       /* non-finite value or failed factorisation  */
+    SVM_ERR_DEGENERATE = 6,    /* labels of one class only: alpha = 0       */
+    SVM_ERR_TIMEOUT = 7,       /* a bounded device-side wait gave up        */
+    SVM_ERR_UNSUPPORTED = 8    /* size or layout outside this build's range */
+} svm_status;
+
+typedef enum { SVM_DENSE_ROWMAJOR = 0, SVM_CSR = 1 } svm_layout;
+typedef enum { SVM_F32 = 0, SVM_F64 = 1 } svm_dtype;
+
+/* Arithmetic of the solve.
+ * PLAIN_FP64: every vector, product and reduction in IEEE FP64 (X is read in
+ *   its storage type and widened exactly).
+ * MIXED: FP32 products; FP64 accuracy recovered where the method needs it by
+ *   FP32 error-free transformations (compensated sums and products); FP64
+ *   kept for the multiplier/sigma updates, the KKT/gap reductions and the
+ *   small Newton factorisation. */
+typedef enum { SVM_PREC_PLAIN_FP64 = 0, SVM_PREC_MIXED = 1 } svm_precision;
+
+/* Where the problem arrays and the result arrays live. */
+typedef enum { SVM_MEM_DEVICE = 0, SVM_MEM_HOST = 1 } svm_memory;
+
+typedef struct {
+    int64_t n;              /* number of samples (rows of X), >= 1             */
+    int64_t q;              /* number of features (columns of X), >= 1         */
+    int32_t layout;         /* svm_layout; this build: SVM_DENSE_ROWMAJOR      */
+    int32_t dtype;          /* svm_dtype of X                                  */
+    int32_t memory;         /* svm_memory of X and y                           */
+    int32_t reserved0;
+    const void *X;          /* dense: n*q elements, row-major, 16-byte aligned */
+    const int64_t *indptr;  /* CSR (reserved)                                  */
+    const int32_t *indices; /* CSR (reserved)                                  */
+    const void *values;     /* CSR (reserved)                                  */
+    int64_t nnz;            /* CSR (reserved)                                  */
+    const int8_t *y;        /* n labels, each +1 or -1                         */
+} svm_problem;
+
+typedef struct {
+    double C;            /* box bound, finite and > 0                         */
+    double tol;          /* R_KKT tolerance of eq. (4.1); default 1e-6         */
+    int32_t max_outer;   /* ALM iterations; default 200 (Sec. 4.1)            */
+    int32_t max_inner;   /* SsN iterations per subproblem; default 50          */
+    int32_t max_ls;      /* Armijo trials per Newton step; default 40          */
+    int32_t precision;   /* svm_precision; default SVM_PREC_MIXED              */
+    double sigma0;       /* initial sigma of Algorithm 1; default 1            */
+    double sigma_growth; /* sigma *= growth when R_KKT fell by < 1/2; 5        */
+    double sigma_max;    /* cap on sigma; default 1e6                          */
+    double mu;           /* Armijo constant of Algorithm 3; default 1e-4       */
+    double delta;        /* step reduction of Algorithm 3; default 0.5         */
+    double tau;          /* inexact-Newton exponent of Algorithm 3; 0.5        */
+    double eta;          /* inexact-Newton cap of Algorithm 3; 0.1             */
+    int32_t newton_mode; /* 0 auto (reserved for other solvers)                */
+    int32_t deterministic; /* 1: fixed-order reductions (always, this build)   */
+    void *stream;        /* cudaStream_t, NULL for the default stream          */
+} svm_params;
+
+typedef struct {
+    double *alpha;  /* n, caller-owned, FP64; device pointer (memory=DEVICE) or
+                       host pointer (memory=HOST).  Receives the solution.    */
+    double *w;      /* q, caller-owned, FP64, same memory kind: w = A' alpha  */
+    double b;       /* bias: the multiplier of y'alpha = 0 at the solution    */
+    double kkt;     /* R_KKT(alpha), eq. (4.1), computed in FP64              */
+    double objective;        /* 1/2 |A'alpha|^2 - e'alpha                     */
+    double primal_objective; /* 1/2 |w|^2 + C sum hinge(1 - y_i(<w,x_i> + b)) */
+    double gap;              /* primal_objective + objective (>= 0)           */
+    double sigma;            /* final sigma                                   */
+    int32_t outer_iters;
+    int32_t inner_iters_total;
+    int32_t status;          /* same as the return value of the solve         */
+    int32_t reserved0;
+    int64_t n_free;          /* 0 < alpha_i < C                               */
+    int64_t n_upper;         /* alpha_i = C                                   */
+    int64_t n_sv;            /* alpha_i > 0                                   */
+} svm_result;
+
+/* Fill *p with the defaults listed above (C = 1). */
+void svm_default_params(svm_params *p);
+
+/* Create a solver for one problem (Sec. 1, eq. (1.2)).
+ * Validates n, q, C, tol, pointers and (device-side) the labels.  With
+ * memory = SVM_MEM_DEVICE the handle BORROWS X and y: they must stay valid
+ * and unchanged until svm_ssnalm_destroy.  With SVM_MEM_HOST it copies them
+ * to the device (the copy is timed as part of create).  The handle owns all
+ * device workspace (O(n) vectors, O(q^2) Newton matrix).
+ * Returns SVM_ERR_INVALID_ARG, SVM_ERR_OOM, SVM_ERR_CUDA, SVM_ERR_UNSUPPORTED.
+ * *out is NULL on failure. */
+svm_status svm_ssnalm_create(svm_ssnalm_t **out, const svm_problem *prob,
+                             const svm_params *params);
+
+/* Solve (Algorithm 1 with Algorithm 3 inside) until R_KKT <= tol or
+ * max_outer.  alpha0 (nullable; same memory kind as the problem) is a warm
+ * start: it is projected onto {y'x = 0, 0 <= x <= C} and the ALM dual starts
+ * at v = A'alpha0; NULL starts from zero (Sec. 4.1).  res->alpha and res->w
+ * must be non-NULL.  Synchronises the stream.  Returns SVM_OK,
+ * SVM_ERR_NOT_CONVERGED (results filled), SVM_ERR_DEGENERATE (one class:
+ * alpha = 0, b = NaN), SVM_ERR_NUMERIC, SVM_ERR_TIMEOUT, SVM_ERR_CUDA. */
+svm_status svm_ssnalm_solve(svm_ssnalm_t *h, const double *alpha0, svm_result *res);
+
+/* Release the handle and its workspace.  NULL-safe. */
+void svm_ssnalm_destroy(svm_ssnalm_t *h);
+
+/* One-line description of the last error on h (or of the last failed
+ * create when h is NULL).  Never NULL. */
+const char *svm_ssnalm_last_error(const svm_ssnalm_t *h);
+
+/* ---------------------------------------------------------------------
+ * Step-level entry points.  Each runs one step of the hot path with the
+ * handle's problem, precision and workspace, so that each step can be checked
+ * on its own.  All vector arguments are device pointers (FP64 unless stated);
+ * they are valid for problems created with either memory kind.
+ * ------------------------------------------------------------------- */
+
+/* z = A v  (z_i = y_i <x_i, v>): v has q entries, z has n. */
+svm_status svm_op_matvec(svm_ssnalm_t *h, const double *v, double *z);
+
+/* out = A' c = sum_i c_i y_i x_i over the rows with c_i != 0 (q entries).
+ * c has n entries; rows with c_i == 0 are skipped. */
+svm_status svm_op_rmatvec(svm_ssnalm_t *h, const double *c, double *out);
+
+/* pi = Pi_{K cap L}(u), K = [0,C]^n, L = {y'x = 0} (Sec. 3.2.1).
+ * lambda (host, out): the multiplier lambda-hat with pi = clip(u - lambda y).
+ * J (device int32, n, nullable): ascending indices with 0 < u_i - lambda y_i < C
+ *   (the free set, complement of the active set of eq. (3.8)); *p_out its size.
+ * S (device int32, n, nullable): ascending indices with pi_i > 0; *s_out.
+ * Returns SVM_ERR_NUMERIC if the root search did not terminate. */
+svm_status svm_op_project(svm_ssnalm_t *h, const double *u, double *pi, double *lambda,
+                          int32_t *J, int64_t *p_out, int32_t *S, int64_t *s_out);
+
+/* Newton direction of Algorithm 3, Step 1, through Proposition 3.5 in the
+ * coordinates v = A'w:  (I_q + sigma A'PA) dv = -g, with P the HS-Jacobian of
+ * Theorem 3.2 on the free set J (device int32, p ascending indices).
+ * g, dv: q entries. */
+svm_status svm_op_newton(svm_ssnalm_t *h, const int32_t *J, int64_t p, double sigma,
+                         const double *g, double *dv);
+
+/* Relative KKT residual of eq. (4.1) at alpha (n, device).  *kkt and *lambda
+ * (multiplier of the projection in the residual) are host outputs. */
+svm_status svm_op_kkt(svm_ssnalm_t *h, const double *alpha, double *kkt, double *lambda);
+
+/* ---------------------------------------------------------------------
+ * Instrumentation (no counterpart in the paper: measurement support).
+ * ------------------------------------------------------------------- */
+typedef struct {
+    int64_t launches;          /* kernels launched by this handle since reset  */
+    int64_t matvec_calls;      /* z = A v products (one kernel each)           */
+    double matvec_ms;          /* their summed CUDA-event time (timing on)     */
+    int64_t rmatvec_calls;     /* A' c products (two kernels each)             */
+    double rmatvec_ms;
+    int64_t proj_calls;        /* projections (one cooperative kernel each)    */
+    double proj_ms;
+    int64_t newton_calls;      /* Newton-system solves                          */
+    double newton_ms;
+    int64_t host_syncs;        /* stream synchronisations for scalar read-back */
+} svm_stats;
+
+/* Enable (1) or disable (0) CUDA-event timing of the step kinds above.  When
+ * enabled, each timed launch is bracketed by two events recorded on the
+ * handle's stream; times are accumulated when the solve (or op) returns. */
+svm_status svm_ssnalm_set_timing(svm_ssnalm_t *h, int enable);
+
+/* Copy the counters into *out (host); reset them when reset != 0. */
+svm_status svm_ssnalm_get_stats(svm_ssnalm_t *h, svm_stats *out, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SVM_SSNALM_H */

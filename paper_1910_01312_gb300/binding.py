@@ -1,0 +1,218 @@
+"""ctypes binding of include/svm_ssnalm.h (argument marshalling only).
+
+Every step of the solver runs in libsvm_ssnalm.so; this module only converts
+torch tensors / numpy arrays to pointers and C structs.  It never falls back to
+a CPU implementation: if the library is missing it raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+from . import build as _build
+
+OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_NOT_CONVERGED, ERR_NUMERIC, ERR_DEGENERATE, \
+    ERR_TIMEOUT, ERR_UNSUPPORTED = range(9)
+DENSE_ROWMAJOR, CSR = 0, 1
+F32, F64 = 0, 1
+PREC_PLAIN_FP64, PREC_MIXED = 0, 1
+MEM_DEVICE, MEM_HOST = 0, 1
+
+
+class Problem(C.Structure):
+    _fields_ = [("n", C.c_int64), ("q", C.c_int64), ("layout", C.c_int32), ("dtype", C.c_int32),
+                ("memory", C.c_int32), ("reserved0", C.c_int32), ("X", C.c_void_p),
+                ("indptr", C.c_void_p), ("indices", C.c_void_p), ("values", C.c_void_p),
+                ("nnz", C.c_int64), ("y", C.c_void_p)]
+
+
+class Params(C.Structure):
+    _fields_ = [("C", C.c_double), ("tol", C.c_double), ("max_outer", C.c_int32),
+                ("max_inner", C.c_int32), ("max_ls", C.c_int32), ("precision", C.c_int32),
+                ("sigma0", C.c_double), ("sigma_growth", C.c_double), ("sigma_max", C.c_double),
+                ("mu", C.c_double), ("delta", C.c_double), ("tau", C.c_double), ("eta", C.c_double),
+                ("newton_mode", C.c_int32), ("deterministic", C.c_int32), ("stream", C.c_void_p)]
+
+
+class Result(C.Structure):
+    _fields_ = [("alpha", C.c_void_p), ("w", C.c_void_p), ("b", C.c_double), ("kkt", C.c_double),
+                ("objective", C.c_double), ("primal_objective", C.c_double), ("gap", C.c_double),
+                ("sigma", C.c_double), ("outer_iters", C.c_int32), ("inner_iters_total", C.c_int32),
+                ("status", C.c_int32), ("reserved0", C.c_int32), ("n_free", C.c_int64),
+                ("n_upper", C.c_int64), ("n_sv", C.c_int64)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("launches", C.c_int64), ("matvec_calls", C.c_int64), ("matvec_ms", C.c_double),
+                ("rmatvec_calls", C.c_int64), ("rmatvec_ms", C.c_double), ("proj_calls", C.c_int64),
+                ("proj_ms", C.c_double), ("newton_calls", C.c_int64), ("newton_ms", C.c_double),
+                ("host_syncs", C.c_int64)]
+
+
+SYMBOLS = ["svm_default_params", "svm_ssnalm_create", "svm_ssnalm_solve", "svm_ssnalm_destroy",
+           "svm_ssnalm_last_error", "svm_op_matvec", "svm_op_rmatvec", "svm_op_project",
+           "svm_op_newton", "svm_op_kkt", "svm_ssnalm_set_timing", "svm_ssnalm_get_stats"]
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libsvm_ssnalm.so (raises if it is missing and not built here)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_build.LIB):
+            if not build_if_missing:
+                raise RuntimeError(f"CUDA library not built: {_build.LIB} (run __graft_entry__.build())")
+            _build.build()
+        L = C.CDLL(_build.LIB)
+        vp, i64 = C.c_void_p, C.c_int64
+        L.svm_default_params.argtypes = [C.POINTER(Params)]
+        L.svm_default_params.restype = None
+        L.svm_ssnalm_create.argtypes = [C.POINTER(vp), C.POINTER(Problem), C.POINTER(Params)]
+        L.svm_ssnalm_create.restype = C.c_int
+        L.svm_ssnalm_solve.argtypes = [vp, vp, C.POINTER(Result)]
+        L.svm_ssnalm_solve.restype = C.c_int
+        L.svm_ssnalm_destroy.argtypes = [vp]
+        L.svm_ssnalm_destroy.restype = None
+        L.svm_ssnalm_last_error.argtypes = [vp]
+        L.svm_ssnalm_last_error.restype = C.c_char_p
+        L.svm_op_matvec.argtypes = [vp, vp, vp]
+        L.svm_op_rmatvec.argtypes = [vp, vp, vp]
+        L.svm_op_project.argtypes = [vp, vp, vp, C.POINTER(C.c_double), vp, C.POINTER(i64), vp,
+                                     C.POINTER(i64)]
+        L.svm_op_newton.argtypes = [vp, vp, i64, C.c_double, vp, vp]
+        L.svm_op_kkt.argtypes = [vp, vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        L.svm_ssnalm_set_timing.argtypes = [vp, C.c_int]
+        L.svm_ssnalm_get_stats.argtypes = [vp, C.POINTER(Stats), C.c_int]
+        for f in ("svm_op_matvec", "svm_op_rmatvec", "svm_op_project", "svm_op_newton", "svm_op_kkt",
+                  "svm_ssnalm_set_timing", "svm_ssnalm_get_stats"):
+            getattr(L, f).restype = C.c_int
+        _lib = L
+        return L
+
+
+class SVMError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"status {status}: {msg}")
+        self.status = status
+
+
+def default_params(**kw) -> Params:
+    P = Params()
+    load().svm_default_params(C.byref(P))
+    for k, v in kw.items():
+        if not hasattr(P, k):
+            raise KeyError(k)
+        setattr(P, k, v)
+    return P
+
+
+def _ptr(t):
+    """Address of a torch tensor or numpy array (contiguous)."""
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        assert t.is_contiguous()
+        return t.data_ptr()
+    assert t.flags["C_CONTIGUOUS"]
+    return t.ctypes.data
+
+
+class Solver:
+    """Owns one svm_ssnalm_t handle.
+
+    X, y: torch CUDA tensors (memory=DEVICE, borrowed: keep them alive) or
+    host arrays -- numpy or torch CPU tensors, pinned or not -- (memory=HOST,
+    copied to the device by create; the solve's outputs are then host arrays
+    too)."""
+
+    def __init__(self, X, y, C_=1.0, stream=None, **params):
+        self._lib = load()
+        self.h = C.c_void_p()
+        is_host = not bool(getattr(X, "is_cuda", False))
+        self.memory = MEM_HOST if is_host else MEM_DEVICE
+        n, q = X.shape
+        dt = str(X.dtype)
+        if dt.endswith("float32"):
+            dtype = F32
+        elif dt.endswith("float64"):
+            dtype = F64
+        else:
+            raise TypeError(f"X dtype {dt} not supported")
+        self.n, self.q = int(n), int(q)
+        self._keep = (X, y)
+        prob = Problem(n=n, q=q, layout=DENSE_ROWMAJOR, dtype=dtype, memory=self.memory, X=_ptr(X),
+                       indptr=None, indices=None, values=None, nnz=0, y=_ptr(y))
+        P = default_params(C=float(C_), **params)
+        if stream is not None:
+            P.stream = stream
+        self.params = P
+        st = self._lib.svm_ssnalm_create(C.byref(self.h), C.byref(prob), C.byref(P))
+        if st != OK:
+            raise SVMError(st, self._lib.svm_ssnalm_last_error(None).decode())
+
+    def close(self):
+        if self.h:
+            self._lib.svm_ssnalm_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def last_error(self) -> str:
+        return self._lib.svm_ssnalm_last_error(self.h).decode()
+
+    def _check(self, st, allow=(OK,)):
+        if st not in allow:
+            raise SVMError(st, self.last_error())
+        return st
+
+    def solve(self, alpha, w, alpha0=None, allow=(OK, ERR_NOT_CONVERGED, ERR_DEGENERATE)):
+        """alpha (n), w (q): FP64 output buffers (device tensors or numpy)."""
+        R = Result(alpha=_ptr(alpha), w=_ptr(w))
+        st = self._lib.svm_ssnalm_solve(self.h, _ptr(alpha0), C.byref(R))
+        self._check(st, allow)
+        out = {k: getattr(R, k) for k, _ in Result._fields_ if k not in ("alpha", "w", "reserved0")}
+        out["status"] = st
+        return out
+
+    def set_timing(self, enable=True):
+        self._check(self._lib.svm_ssnalm_set_timing(self.h, 1 if enable else 0))
+
+    def stats(self, reset=False):
+        S = Stats()
+        self._check(self._lib.svm_ssnalm_get_stats(self.h, C.byref(S), 1 if reset else 0))
+        return {k: getattr(S, k) for k, _ in S._fields_}
+
+    # ---- step-level entry points (device FP64 buffers) ----
+    def matvec(self, v, z):
+        self._check(self._lib.svm_op_matvec(self.h, _ptr(v), _ptr(z)))
+
+    def rmatvec(self, c, out):
+        self._check(self._lib.svm_op_rmatvec(self.h, _ptr(c), _ptr(out)))
+
+    def project(self, u, pi, J=None, S=None):
+        lam = C.c_double(0.0)
+        p, s = C.c_int64(0), C.c_int64(0)
+        self._check(self._lib.svm_op_project(self.h, _ptr(u), _ptr(pi), C.byref(lam), _ptr(J),
+                                             C.byref(p), _ptr(S), C.byref(s)))
+        return lam.value, p.value, s.value
+
+    def newton(self, J, p, sigma, g, dv):
+        self._check(self._lib.svm_op_newton(self.h, _ptr(J), int(p), float(sigma), _ptr(g), _ptr(dv)))
+
+    def kkt(self, alpha):
+        r, lam = C.c_double(0.0), C.c_double(0.0)
+        self._check(self._lib.svm_op_kkt(self.h, _ptr(alpha), C.byref(r), C.byref(lam)))
+        return r.value, lam.value

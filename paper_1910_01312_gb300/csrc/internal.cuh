@@ -1,0 +1,105 @@
+// internal.cuh -- solver workspace and kernel launchers shared by the
+// translation units of libsvm_ssnalm.so.  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace svm {
+
+// Results of one projection launch, written by the device (FP64).
+struct ProjOut {
+    double lam;        // lambda-hat
+    double sum[4];     // mode-dependent reductions (see ProjMode)
+    long long p;       // |J|
+    long long s;       // |S|
+    int passes;        // root-search passes
+    int status;        // 0 ok, DEV_ROOT if the search hit its cap
+};
+
+// What a projection launch reduces besides lambda-hat, J and S.
+enum ProjMode : int {
+    PM_OP = 0,     // nothing (step-level entry point)
+    PM_MAIN = 1,   // sum0 = |pi - alpha|^2, sum1 = sum pi(2u - pi); writes u, pi
+    PM_TRIAL = 2,  // sum0 = sum [pi(2u - pi) - pib(2ub - pib)]  (psi difference)
+    PM_KKT = 3     // sum0 = |alpha - pi|^2, sum1 = |alpha|^2, sum2 = sum alpha,
+                   // sum3 = sum max(0, 1 - (Qalpha_i + y_i lambda))
+};
+
+// u_i = c0 * a_i + c1 * b_i + c2 (b may be null).
+struct ProjIn {
+    const double *a, *b;
+    double c0, c1, c2;
+    int mode;
+    const double *lam0;      // device: warm start for lambda (nullable)
+    double *u_out, *pi_out;  // nullable
+    int32_t *J, *S;          // nullable
+    const double *pi_base;   // PM_TRIAL: pi at the base point (its u is `a`)
+    const double *alpha;     // PM_MAIN: alpha^k
+};
+
+struct Work {
+    // problem
+    int64_t n = 0, q = 0;
+    int xf32 = 1;            // X is FP32 (else FP64)
+    const void *X = nullptr;
+    const int8_t *y = nullptr;
+    double C = 1.0;
+    int precision = 1;
+    cudaStream_t st = nullptr;
+    int dev = 0, nsm = 0;
+    // n-vectors (FP64) and index lists
+    double *alpha = nullptr, *z = nullptr, *dz = nullptr, *u = nullptr, *pi = nullptr,
+           *qa = nullptr, *tmpn = nullptr;
+    int32_t *J = nullptr, *S = nullptr;
+    // q-vectors
+    double *v = nullptr, *dv = nullptr, *g = nullptr, *atp = nullptr, *h = nullptr,
+           *w = nullptr, *tmpq = nullptr;
+    double *M = nullptr;      // q*q Newton matrix / Cholesky factor
+    double *part = nullptr;   // partial sums (size part_len doubles)
+    size_t part_len = 0;
+    int *cnt = nullptr;       // compaction counts
+    size_t cnt_len = 0;
+    unsigned *bar = nullptr;  // grid-barrier counter
+    int *err = nullptr;       // device error flag
+    ProjOut *pout = nullptr;  // 4 slots indexed by ProjMode
+    double *red = nullptr;    // 16 small reductions
+    // owned copies (memory = HOST)
+    void *X_own = nullptr;
+    int8_t *y_own = nullptr;
+    // host pinned mirror for scalar read-back
+    ProjOut *h_pout = nullptr;
+    double *h_red = nullptr;
+    int *h_err = nullptr;
+    // cooperative-launch geometry of the projection kernel
+    int proj_grid = 0, proj_ept = 0;
+    // rmatvec geometry
+    int rm_grid = 0;
+    // kernels launched through this workspace (all kinds)
+    long long nlaunch = 0;
+};
+
+// ---- launchers (return cudaError_t of the launch) ----
+cudaError_t proj_setup(Work &W);
+cudaError_t launch_project(Work &W, const ProjIn &in, ProjOut *out);
+
+cudaError_t launch_matvec(Work &W, const double *v, double *z);
+// out = sum_i c_i y_i x_i over the index list idx (cnt entries, read from
+// *cnt_dev on the device) or over all rows when idx == nullptr.
+// Also red[slot] = sum_j (sum_i |c_i x_ij|)^2 when scale_slot >= 0.
+cudaError_t launch_rmatvec(Work &W, const double *c, const int32_t *idx, const long long *cnt_dev,
+                           double *out, int scale_slot);
+// q-vector helpers
+cudaError_t launch_grad(Work &W);            // g = v - atp; red[0] = |g|^2
+cudaError_t launch_dots(Work &W);            // red[2] = g'dv, red[3] = v'dv, red[4] = dv'dv
+cudaError_t launch_vaxpy(Work &W, double t); // v += t dv
+cudaError_t launch_zaxpy(Work &W, double t); // z += t dz
+cudaError_t launch_negcopy(Work &W, const double *g, double *dv); // dv = -g
+
+// Newton direction (I + sigma A'PA) dv = -g on the free set J (p from *p_dev
+// when p_host < 0).
+cudaError_t launch_newton(Work &W, const int32_t *J, long long p_host, const long long *p_dev,
+                          double sigma, const double *g, double *dv);
+
+}  // namespace svm

@@ -1,0 +1,609 @@
+// svm_ssnalm.cu -- C ABI (include/svm_ssnalm.h) and the host-side control of
+// the SSsNAL method: Algorithm 1 (augmented Lagrangian on the restricted dual,
+// multiplier update of eq. (3.5)) around Algorithm 3 (semismooth Newton with
+// Armijo line search), stopped by the relative KKT residual of eq. (4.1).
+//
+// Variables (paper -> here): x -> alpha (SVM dual, n); w in Ran(Q) -> v = A'w
+// (q), so Q w = A v =: z (n), <w, Qw> = |v|^2 and grad psi = A g with
+// g = v - A'Pi(u) (q).  Every vector step runs in the kernels of k_*.cu; the
+// host only sequences launches and reads back the scalars that decide the
+// next launch (|g|, free-set size, Armijo test, R_KKT).
+//
+// Readings where the paper leaves a choice open (identical in the FP64 CPU
+// oracle used by the tests):
+//  - sigma_0 = 1; sigma *= 5 (cap 1e6) when R_KKT fell by less than 1/2.
+//  - Inner stop (A')/(B') measured in q-space: |g| <= min(eps_k, eps_k |pi -
+//    alpha^k|)/sqrt(sigma_k), eps_k = 0.1 * 0.5^k, floored at 1e-15 times the
+//    absolute-sum scale of A'pi (the roundoff level of g); at most 50
+//    Newton steps; a failed line search ends the subproblem.
+//  - Armijo: mu = 1e-4, delta = 0.5, at most 40 trials; psi differences are
+//    summed term by term.
+//  - z = A v is recomputed at the start of every subproblem.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/svm_ssnalm.h"
+#include "internal.cuh"
+
+using namespace svm;
+
+struct svm_ssnalm {
+    Work W;
+    svm_params P;
+    svm_problem prob;
+    std::string err;
+    double lam_main = 0.0;
+    long long npos = 0;   // number of +1 labels (checked at create)
+    // instrumentation
+    bool timing = false;
+    std::vector<cudaEvent_t> evpool;
+    size_t evused = 0;
+    struct Rec { int kind, e0, e1; };
+    std::vector<Rec> recs;
+    long long kcalls[4] = {0, 0, 0, 0};
+    double kms[4] = {0, 0, 0, 0};
+    long long syncs = 0;
+    long long launch_base = 0;
+};
+
+enum { TK_MATVEC = 0, TK_RMATVEC = 1, TK_PROJ = 2, TK_NEWTON = 3 };
+
+static int ev_take(svm_ssnalm *h)
+{
+    if (h->evused == h->evpool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return -1;
+        h->evpool.push_back(e);
+    }
+    return (int)h->evused++;
+}
+
+// Run f() (which launches on the handle's stream); count it under `kind` and,
+// when timing is on, bracket it with two events.
+template <class F>
+static cudaError_t timed(svm_ssnalm *h, int kind, F f)
+{
+    h->kcalls[kind]++;
+    int e0 = h->timing ? ev_take(h) : -1;
+    if (e0 >= 0) cudaEventRecord(h->evpool[e0], h->W.st);
+    cudaError_t e = f();
+    if (e0 >= 0) {
+        int e1 = ev_take(h);
+        if (e1 >= 0) {
+            cudaEventRecord(h->evpool[e1], h->W.st);
+            h->recs.push_back({kind, e0, e1});
+        }
+    }
+    return e;
+}
+
+// Fold recorded event pairs into the totals (the stream must be idle).
+static void flush_timing(svm_ssnalm *h)
+{
+    for (const auto &r : h->recs) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, h->evpool[r.e0], h->evpool[r.e1]) == cudaSuccess) h->kms[r.kind] += ms;
+    }
+    h->recs.clear();
+    h->evused = 0;
+}
+
+static thread_local std::string g_create_err;
+
+#define CK(call)                                                                                           \
+    do {                                                                                                   \
+        cudaError_t e_ = (call);                                                                           \
+        if (e_ != cudaSuccess) {                                                                           \
+            h->err = std::string(#call) + ": " + cudaGetErrorString(e_);                                   \
+            return SVM_ERR_CUDA;                                                                           \
+        }                                                                                                  \
+    } while (0)
+
+extern "C" void svm_default_params(svm_params *p)
+{
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->C = 1.0;
+    p->tol = 1e-6;
+    p->max_outer = 200;
+    p->max_inner = 50;
+    p->max_ls = 40;
+    p->precision = SVM_PREC_MIXED;
+    p->sigma0 = 1.0;
+    p->sigma_growth = 5.0;
+    p->sigma_max = 1e6;
+    p->mu = 1e-4;
+    p->delta = 0.5;
+    p->tau = 0.5;
+    p->eta = 0.1;
+    p->newton_mode = 0;
+    p->deterministic = 1;
+    p->stream = nullptr;
+}
+
+extern "C" const char *svm_ssnalm_last_error(const svm_ssnalm_t *h)
+{
+    if (!h) return g_create_err.c_str();
+    return h->err.c_str();
+}
+
+static void free_work(Work &W)
+{
+    void *ptrs[] = {W.alpha, W.z, W.dz, W.u, W.pi, W.qa, W.tmpn, W.J, W.S, W.v, W.dv, W.g, W.atp,
+                    W.h, W.w, W.tmpq, W.M, W.part, W.cnt, W.bar, W.err, W.pout, W.red, W.X_own, W.y_own};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (W.h_pout) cudaFreeHost(W.h_pout);
+    if (W.h_red) cudaFreeHost(W.h_red);
+    if (W.h_err) cudaFreeHost(W.h_err);
+    W = Work();
+}
+
+extern "C" void svm_ssnalm_destroy(svm_ssnalm_t *h)
+{
+    if (!h) return;
+    if (h->W.st) cudaStreamSynchronize(h->W.st);
+    for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
+    free_work(h->W);
+    delete h;
+}
+
+__global__ void check_labels_kernel(const int8_t *y, long long n, int *out)
+{
+    // out[0]: count of invalid labels, out[1]: count of +1
+    int bad = 0, pos = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        int8_t v = y[i];
+        bad += (v != 1 && v != -1);
+        pos += (v == 1);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        bad += __shfl_xor_sync(0xffffffffu, bad, o);
+        pos += __shfl_xor_sync(0xffffffffu, pos, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (bad) atomicAdd(out, bad);
+        if (pos) atomicAdd(out + 1, pos);
+    }
+}
+
+__global__ void check_finite_kernel(const void *X, int f32, long long m, int *out)
+{
+    int bad = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x) {
+        double v = f32 ? (double)((const float *)X)[i] : ((const double *)X)[i];
+        bad += !isfinite(v);
+    }
+    for (int o = 16; o > 0; o >>= 1) bad += __shfl_xor_sync(0xffffffffu, bad, o);
+    if ((threadIdx.x & 31) == 0 && bad) atomicAdd(out, bad);
+}
+
+template <typename T>
+static cudaError_t dalloc(T **p, size_t count)
+{
+    return cudaMalloc((void **)p, (count ? count : 1) * sizeof(T));
+}
+
+extern "C" svm_status svm_ssnalm_create(svm_ssnalm_t **out, const svm_problem *prob, const svm_params *params)
+{
+    if (out) *out = nullptr;
+    if (!out || !prob || !params) { g_create_err = "null argument"; return SVM_ERR_INVALID_ARG; }
+    if (prob->n < 1 || prob->q < 1) { g_create_err = "n and q must be >= 1"; return SVM_ERR_INVALID_ARG; }
+    if (!(params->C > 0.0) || !isfinite(params->C)) { g_create_err = "C must be finite and > 0"; return SVM_ERR_INVALID_ARG; }
+    if (!(params->tol > 0.0)) { g_create_err = "tol must be > 0"; return SVM_ERR_INVALID_ARG; }
+    if (!prob->X || !prob->y) { g_create_err = "X and y must be non-null"; return SVM_ERR_INVALID_ARG; }
+    if (prob->layout != SVM_DENSE_ROWMAJOR) { g_create_err = "only dense row-major X in this build"; return SVM_ERR_UNSUPPORTED; }
+    if (prob->dtype != SVM_F32 && prob->dtype != SVM_F64) { g_create_err = "dtype must be F32 or F64"; return SVM_ERR_INVALID_ARG; }
+    if (prob->memory != SVM_MEM_DEVICE && prob->memory != SVM_MEM_HOST) { g_create_err = "bad memory kind"; return SVM_ERR_INVALID_ARG; }
+    if (prob->q > 1024) { g_create_err = "dense q > 1024 not supported in this build"; return SVM_ERR_UNSUPPORTED; }
+    if (params->max_outer < 1 || params->max_inner < 1 || params->max_ls < 1) { g_create_err = "iteration caps must be >= 1"; return SVM_ERR_INVALID_ARG; }
+    if (params->precision != SVM_PREC_PLAIN_FP64 && params->precision != SVM_PREC_MIXED) { g_create_err = "bad precision"; return SVM_ERR_INVALID_ARG; }
+
+    svm_ssnalm *h = new (std::nothrow) svm_ssnalm();
+    if (!h) { g_create_err = "out of host memory"; return SVM_ERR_OOM; }
+    h->P = *params;
+    h->prob = *prob;
+    Work &W = h->W;
+    W.n = prob->n;
+    W.q = prob->q;
+    W.xf32 = prob->dtype == SVM_F32;
+    W.C = params->C;
+    W.precision = params->precision;
+    W.st = (cudaStream_t)params->stream;
+    auto fail = [&](svm_status st, const std::string &m) {
+        g_create_err = m;
+        free_work(h->W);
+        delete h;
+        return st;
+    };
+    cudaError_t e = cudaGetDevice(&W.dev);
+    if (e != cudaSuccess) return fail(SVM_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    cudaDeviceGetAttribute(&W.nsm, cudaDevAttrMultiProcessorCount, W.dev);
+    const size_t n = (size_t)W.n, q = (size_t)W.q;
+    const size_t xbytes = n * q * (W.xf32 ? 4 : 8);
+    if (prob->memory == SVM_MEM_HOST) {
+        if (cudaMalloc(&W.X_own, xbytes) != cudaSuccess || dalloc(&W.y_own, n) != cudaSuccess)
+            return fail(SVM_ERR_OOM, "device allocation of X/y copy failed");
+        if (cudaMemcpyAsync(W.X_own, prob->X, xbytes, cudaMemcpyHostToDevice, W.st) != cudaSuccess ||
+            cudaMemcpyAsync(W.y_own, prob->y, n, cudaMemcpyHostToDevice, W.st) != cudaSuccess)
+            return fail(SVM_ERR_CUDA, "host-to-device copy of X/y failed");
+        W.X = W.X_own;
+        W.y = W.y_own;
+    } else {
+        W.X = prob->X;
+        W.y = prob->y;
+    }
+    if ((uintptr_t)W.X % 16 != 0) return fail(SVM_ERR_INVALID_ARG, "X must be 16-byte aligned");
+    // workspace
+    W.rm_grid = W.nsm * 4;
+    const int ntile = (int)((q + 31) / 32);
+    // Gram split-K partials: at most 32 MiB (at least one q x q partial)
+    size_t part_gram = (size_t)(4 * W.nsm) * (q * q + q);
+    const size_t gram_cap = ((size_t)32 << 20) / sizeof(double);
+    if (part_gram > gram_cap) part_gram = gram_cap > (q * q + q) ? gram_cap : (q * q + q);
+    size_t part_rm = (size_t)2 * W.rm_grid * q;
+    size_t part_proj = (size_t)3 * 8 * 4 * W.nsm * 4;   // generous: 3 slots x grid x stride
+    W.part_len = part_gram > part_rm ? part_gram : part_rm;
+    if (W.part_len < part_proj) W.part_len = part_proj;
+    (void)ntile;
+    if (dalloc(&W.alpha, n) || dalloc(&W.z, n) || dalloc(&W.dz, n) || dalloc(&W.u, n) || dalloc(&W.pi, n) ||
+        dalloc(&W.qa, n) || dalloc(&W.tmpn, n) || dalloc(&W.J, n) || dalloc(&W.S, n) || dalloc(&W.v, q) ||
+        dalloc(&W.dv, q) || dalloc(&W.g, q) || dalloc(&W.atp, q) || dalloc(&W.h, q) || dalloc(&W.w, q) ||
+        dalloc(&W.tmpq, q) || dalloc(&W.M, q * q) || dalloc(&W.part, W.part_len) || dalloc(&W.bar, 4) ||
+        dalloc(&W.err, 4) || dalloc(&W.pout, 4) || dalloc(&W.red, 16))
+        return fail(SVM_ERR_OOM, "device workspace allocation failed");
+    if (cudaMallocHost(&W.h_pout, 4 * sizeof(ProjOut)) != cudaSuccess ||
+        cudaMallocHost(&W.h_red, 16 * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&W.h_err, 4 * sizeof(int)) != cudaSuccess)
+        return fail(SVM_ERR_OOM, "pinned host allocation failed");
+    e = proj_setup(W);
+    if (e != cudaSuccess) return fail(SVM_ERR_UNSUPPORTED, "n too large for the projection kernel");
+    W.cnt_len = (size_t)W.proj_ept * W.proj_grid * 2;
+    if (dalloc(&W.cnt, W.cnt_len)) return fail(SVM_ERR_OOM, "device workspace allocation failed");
+    cudaMemsetAsync(W.bar, 0, 4 * sizeof(unsigned), W.st);
+    cudaMemsetAsync(W.err, 0, 4 * sizeof(int), W.st);
+    cudaMemsetAsync(W.pout, 0, 4 * sizeof(ProjOut), W.st);
+    // validate labels and data on the device
+    int *chk = nullptr;
+    if (dalloc(&chk, 4)) return fail(SVM_ERR_OOM, "device allocation failed");
+    cudaMemsetAsync(chk, 0, 4 * sizeof(int), W.st);
+    check_labels_kernel<<<W.nsm * 2, 256, 0, W.st>>>(W.y, W.n, chk);
+    check_finite_kernel<<<W.nsm * 4, 256, 0, W.st>>>(W.X, W.xf32, (long long)(n * q), chk + 2);
+    int hchk[4] = {0, 0, 0, 0};
+    cudaMemcpyAsync(hchk, chk, sizeof(hchk), cudaMemcpyDeviceToHost, W.st);
+    e = cudaStreamSynchronize(W.st);
+    cudaFree(chk);
+    if (e != cudaSuccess) return fail(SVM_ERR_CUDA, std::string("create: ") + cudaGetErrorString(e));
+    if (hchk[0]) return fail(SVM_ERR_INVALID_ARG, "labels must be +1 or -1");
+    if (hchk[2]) return fail(SVM_ERR_INVALID_ARG, "X has non-finite entries");
+    h->lam_main = 0.0;
+    h->npos = hchk[1];
+    *out = h;
+    return SVM_OK;
+}
+
+// ------------------------------------------------------------ helpers
+
+static svm_status sync_read(svm_ssnalm *h)
+{
+    Work &W = h->W;
+    CK(cudaMemcpyAsync(W.h_pout, W.pout, 4 * sizeof(ProjOut), cudaMemcpyDeviceToHost, W.st));
+    CK(cudaMemcpyAsync(W.h_red, W.red, 16 * sizeof(double), cudaMemcpyDeviceToHost, W.st));
+    CK(cudaMemcpyAsync(W.h_err, W.err, sizeof(int), cudaMemcpyDeviceToHost, W.st));
+    CK(cudaStreamSynchronize(W.st));
+    h->syncs++;
+    if (h->timing) flush_timing(h);
+    int e = W.h_err[0];
+    if (e) {
+        cudaMemsetAsync(W.err, 0, sizeof(int), W.st);
+        cudaMemsetAsync(W.bar, 0, sizeof(unsigned), W.st);
+        if (e == DEV_TIMEOUT) { h->err = "device-side wait timed out"; return SVM_ERR_TIMEOUT; }
+        if (e == DEV_ROOT) { h->err = "projection root search hit its pass cap"; return SVM_ERR_NUMERIC; }
+        if (e == DEV_CHOL) { h->err = "Newton matrix not positive definite"; return SVM_ERR_NUMERIC; }
+        h->err = "device numeric error";
+        return SVM_ERR_NUMERIC;
+    }
+    return SVM_OK;
+}
+
+// R_KKT(alpha) (eq. (4.1)); leaves A'alpha in W.w, Q alpha in W.qa, and the
+// projection results in pout[PM_KKT].  idx/cnt: support of alpha (nullable).
+static svm_status kkt_launch(svm_ssnalm *h, const double *alpha, const int32_t *idx, const long long *cnt)
+{
+    Work &W = h->W;
+    CK(timed(h, TK_RMATVEC, [&] { return launch_rmatvec(W, alpha, idx, cnt, W.w, -1); }));
+    CK(timed(h, TK_MATVEC, [&] { return launch_matvec(W, W.w, W.qa); }));
+    ProjIn in{};
+    in.a = alpha; in.b = W.qa; in.c0 = 1.0; in.c1 = -1.0; in.c2 = 1.0;
+    in.mode = PM_KKT;
+    in.lam0 = &W.pout[PM_KKT].lam;
+    CK(timed(h, TK_PROJ, [&] { return launch_project(W, in, &W.pout[PM_KKT]); }));
+    return SVM_OK;
+}
+
+static double kkt_value(const ProjOut &o)
+{
+    return sqrt(o.sum[0]) / (1.0 + sqrt(o.sum[1]));
+}
+
+__global__ void copy_kernel(long long n, const double *a, double *b)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        b[i] = a[i];
+}
+
+// red[0] += #{0 < a < C}, red[1] += #{a >= C}, red[2] += #{a > 0}
+__global__ void count_kernel(long long n, const double *a, double C, double *red)
+{
+    unsigned long long f = 0, u = 0, s = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double v = a[i];
+        f += (v > 0.0 && v < C);
+        u += (v >= C);
+        s += (v > 0.0);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        f += __shfl_xor_sync(0xffffffffu, f, o);
+        u += __shfl_xor_sync(0xffffffffu, u, o);
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(red + 0, (double)f);
+        atomicAdd(red + 1, (double)u);
+        atomicAdd(red + 2, (double)s);
+    }
+}
+
+// ------------------------------------------------------------ solve
+
+extern "C" svm_status svm_ssnalm_solve(svm_ssnalm_t *h, const double *alpha0, svm_result *res)
+{
+    if (!h) return SVM_ERR_INVALID_ARG;
+    if (!res || !res->alpha || !res->w) { h->err = "result buffers must be non-null"; return SVM_ERR_INVALID_ARG; }
+    Work &W = h->W;
+    const svm_params &P = h->P;
+    const bool host_mem = h->prob.memory == SVM_MEM_HOST;
+    const long long n = W.n;
+    const int q = (int)W.q;
+    svm_status st;
+    h->err.clear();
+
+    // degenerate labels: one class only
+    if (h->npos == 0 || h->npos == n) {
+        CK(cudaMemsetAsync(W.alpha, 0, n * sizeof(double), W.st));
+        CK(cudaMemsetAsync(W.w, 0, q * sizeof(double), W.st));
+        cudaMemcpyKind k = host_mem ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+        CK(cudaMemcpyAsync(res->alpha, W.alpha, n * sizeof(double), k, W.st));
+        CK(cudaMemcpyAsync(res->w, W.w, q * sizeof(double), k, W.st));
+        CK(cudaStreamSynchronize(W.st));
+        res->b = NAN; res->kkt = NAN; res->objective = 0.0; res->primal_objective = NAN; res->gap = NAN;
+        res->sigma = P.sigma0; res->outer_iters = 0; res->inner_iters_total = 0;
+        res->n_free = res->n_upper = res->n_sv = 0;
+        res->status = SVM_ERR_DEGENERATE;
+        h->err = "labels of one class only";
+        return SVM_ERR_DEGENERATE;
+    }
+
+    // start point: alpha^0 = Pi(alpha0) (or 0), v = A'alpha^0 (w^0 = 0 when cold, Sec. 4.1)
+    bool have_support = false;
+    if (alpha0) {
+        cudaMemcpyKind k = host_mem ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+        CK(cudaMemcpyAsync(W.tmpn, alpha0, n * sizeof(double), k, W.st));
+        ProjIn in{};
+        in.a = W.tmpn; in.b = nullptr; in.c0 = 1.0; in.c2 = 0.0; in.mode = PM_OP;
+        in.pi_out = W.alpha; in.S = W.S;
+        CK(timed(h, TK_PROJ, [&] { return launch_project(W, in, &W.pout[PM_OP]); }));
+        CK(timed(h, TK_RMATVEC, [&] { return launch_rmatvec(W, W.alpha, W.S, &W.pout[PM_OP].s, W.v, -1); }));
+        have_support = true;
+    } else {
+        CK(cudaMemsetAsync(W.alpha, 0, n * sizeof(double), W.st));
+        CK(cudaMemsetAsync(W.v, 0, q * sizeof(double), W.st));
+    }
+    // lambda warm starts of the main, trial and KKT projections restart at 0
+    CK(cudaMemsetAsync(W.pout + PM_MAIN, 0, 3 * sizeof(ProjOut), W.st));
+    double sigma = P.sigma0;
+    // R_KKT at the start
+    if ((st = kkt_launch(h, W.alpha, have_support ? W.S : nullptr, have_support ? &W.pout[PM_OP].s : nullptr)) != SVM_OK)
+        return st;
+    if ((st = sync_read(h)) != SVM_OK) return st;
+    double R = kkt_value(W.h_pout[PM_KKT]), Rprev = R;
+    svm_status status = SVM_ERR_NOT_CONVERGED;
+    int k = 0, inner_total = 0;
+    if (R <= P.tol) status = SVM_OK;
+    for (k = 0; k < P.max_outer && status != SVM_OK; ++k) {
+        const double epsk = 0.1 * pow(0.5, (double)k);
+        CK(timed(h, TK_MATVEC, [&] { return launch_matvec(W, W.v, W.z); }));   // z = A v = Q w
+        int j = 0;
+        bool ls_fail = false;
+        for (j = 0;; ++j) {
+            // u = alpha^k - sigma (z - e); pi = Pi(u); J, S
+            ProjIn in{};
+            in.a = W.alpha; in.b = W.z; in.c0 = 1.0; in.c1 = -sigma; in.c2 = sigma;
+            in.mode = PM_MAIN; in.lam0 = &W.pout[PM_MAIN].lam;
+            in.u_out = W.u; in.pi_out = W.pi; in.J = W.J; in.S = W.S; in.alpha = W.alpha;
+            CK(timed(h, TK_PROJ, [&] { return launch_project(W, in, &W.pout[PM_MAIN]); }));
+            // g = v - A'pi (eq. (3.10) in q coordinates) and its roundoff scale
+            CK(timed(h, TK_RMATVEC, [&] { return launch_rmatvec(W, W.pi, W.S, &W.pout[PM_MAIN].s, W.atp, 1); }));
+            CK(launch_grad(W));
+            if ((st = sync_read(h)) != SVM_OK) return st;
+            const ProjOut &m = W.h_pout[PM_MAIN];
+            double gn = sqrt(W.h_red[0]);
+            double dx = sqrt(m.sum[0]);
+            double tol_in = fmin(epsk, epsk * dx) / sqrt(sigma);
+            double floor_g = 1e-15 * sqrt(W.h_red[1]);
+            if (!isfinite(gn)) { h->err = "non-finite gradient"; return SVM_ERR_NUMERIC; }
+            if (gn <= fmax(tol_in, floor_g) || j >= P.max_inner || ls_fail) break;
+            // Newton direction on the free set J
+            CK(timed(h, TK_NEWTON, [&] { return launch_newton(W, W.J, m.p, &W.pout[PM_MAIN].p, sigma, W.g, W.dv); }));
+            CK(timed(h, TK_MATVEC, [&] { return launch_matvec(W, W.dv, W.dz); }));   // A dv = Q d
+            CK(launch_dots(W));
+            if ((st = sync_read(h)) != SVM_OK) return st;
+            const double slope = W.h_red[2], vdv = W.h_red[3], dvdv = W.h_red[4];
+            double t = 1.0;
+            bool accepted = false;
+            for (int mtr = 0; mtr < P.max_ls; ++mtr) {
+                ProjIn tr{};
+                tr.a = W.u; tr.b = W.dz; tr.c0 = 1.0; tr.c1 = -t * sigma; tr.c2 = 0.0;
+                tr.mode = PM_TRIAL; tr.lam0 = &W.pout[PM_MAIN].lam; tr.pi_base = W.pi;
+                CK(timed(h, TK_PROJ, [&] { return launch_project(W, tr, &W.pout[PM_TRIAL]); }));
+                if ((st = sync_read(h)) != SVM_OK) return st;
+                double dpsi = t * vdv + 0.5 * t * t * dvdv + W.h_pout[PM_TRIAL].sum[0] / (2.0 * sigma);
+                if (dpsi <= P.mu * t * slope) { accepted = true; break; }
+                t *= P.delta;
+            }
+            if (!accepted) { ls_fail = true; continue; }
+            CK(launch_vaxpy(W, t));
+            CK(launch_zaxpy(W, t));
+        }
+        inner_total += j;
+        // alpha^{k+1} = Pi(u(w^{k+1}))  (eq. (3.5))
+        {
+            int blocks = (int)((n + 1023) / 1024);
+            if (blocks > W.nsm * 4) blocks = W.nsm * 4;
+            copy_kernel<<<blocks, 1024, 0, W.st>>>(n, W.pi, W.alpha);
+            ++W.nlaunch;
+            CK(cudaGetLastError());
+        }
+        if ((st = kkt_launch(h, W.alpha, W.S, &W.pout[PM_MAIN].s)) != SVM_OK) return st;
+        if ((st = sync_read(h)) != SVM_OK) return st;
+        R = kkt_value(W.h_pout[PM_KKT]);
+        if (!isfinite(R)) { status = SVM_ERR_NUMERIC; h->err = "non-finite KKT residual"; break; }
+        if (R <= P.tol) { status = SVM_OK; ++k; break; }
+        if (R > 0.5 * Rprev) sigma = fmin(P.sigma_max, P.sigma_growth * sigma);
+        Rprev = R;
+    }
+    // results: alpha, w = A'alpha (from the last KKT evaluation), b = lambda of
+    // the KKT projection, objective, primal objective, gap, counts
+    const ProjOut &kk = W.h_pout[PM_KKT];
+    {
+        cudaMemcpyKind kd = host_mem ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+        CK(cudaMemcpyAsync(res->alpha, W.alpha, n * sizeof(double), kd, W.st));
+        CK(cudaMemcpyAsync(res->w, W.w, q * sizeof(double), kd, W.st));
+        double *hw = (double *)malloc(q * sizeof(double));
+        if (!hw) { h->err = "host allocation failed"; return SVM_ERR_OOM; }
+        cudaError_t e1 = cudaMemcpyAsync(hw, W.w, q * sizeof(double), cudaMemcpyDeviceToHost, W.st);
+        cudaError_t e2 = cudaStreamSynchronize(W.st);
+        if (e1 != cudaSuccess || e2 != cudaSuccess) { free(hw); h->err = "result copy failed"; return SVM_ERR_CUDA; }
+        double wsq = 0.0;
+        for (int jj = 0; jj < q; ++jj) wsq += hw[jj] * hw[jj];
+        free(hw);
+        res->kkt = kkt_value(kk);
+        res->b = kk.lam;
+        res->objective = 0.5 * wsq - kk.sum[2];
+        res->primal_objective = 0.5 * wsq + W.C * kk.sum[3];
+        res->gap = res->primal_objective + res->objective;
+        res->sigma = sigma;
+        res->outer_iters = k;
+        res->inner_iters_total = inner_total;
+        res->status = status;
+    }
+    // counts of free / upper / support entries
+    {
+        CK(cudaMemsetAsync(W.red + 8, 0, 3 * sizeof(double), W.st));
+        count_kernel<<<W.nsm * 2, 256, 0, W.st>>>(n, W.alpha, W.C, W.red + 8);
+        ++W.nlaunch;
+        CK(cudaGetLastError());
+        if ((st = sync_read(h)) != SVM_OK) return st;
+        res->n_free = (int64_t)W.h_red[8];
+        res->n_upper = (int64_t)W.h_red[9];
+        res->n_sv = (int64_t)W.h_red[10];
+    }
+    if (status != SVM_OK && h->err.empty()) h->err = "iteration cap reached";
+    return status;
+}
+
+// ------------------------------------------------------------ step-level ops
+
+extern "C" svm_status svm_op_matvec(svm_ssnalm_t *h, const double *v, double *z)
+{
+    if (!h || !v || !z) return SVM_ERR_INVALID_ARG;
+    CK(timed(h, TK_MATVEC, [&] { return launch_matvec(h->W, v, z); }));
+    CK(cudaStreamSynchronize(h->W.st));
+    return SVM_OK;
+}
+
+extern "C" svm_status svm_op_rmatvec(svm_ssnalm_t *h, const double *c, double *out)
+{
+    if (!h || !c || !out) return SVM_ERR_INVALID_ARG;
+    CK(timed(h, TK_RMATVEC, [&] { return launch_rmatvec(h->W, c, nullptr, nullptr, out, -1); }));
+    CK(cudaStreamSynchronize(h->W.st));
+    return SVM_OK;
+}
+
+extern "C" svm_status svm_op_project(svm_ssnalm_t *h, const double *u, double *pi, double *lambda, int32_t *J,
+                                     int64_t *p_out, int32_t *S, int64_t *s_out)
+{
+    if (!h || !u || !pi) return SVM_ERR_INVALID_ARG;
+    Work &W = h->W;
+    ProjIn in{};
+    in.a = u; in.b = nullptr; in.c0 = 1.0; in.c2 = 0.0; in.mode = PM_OP;
+    in.lam0 = nullptr; in.pi_out = pi; in.J = J; in.S = S;
+    CK(timed(h, TK_PROJ, [&] { return launch_project(W, in, &W.pout[PM_OP]); }));
+    svm_status st = sync_read(h);
+    if (st != SVM_OK) return st;
+    if (lambda) *lambda = W.h_pout[PM_OP].lam;
+    if (p_out) *p_out = W.h_pout[PM_OP].p;
+    if (s_out) *s_out = W.h_pout[PM_OP].s;
+    return SVM_OK;
+}
+
+extern "C" svm_status svm_op_newton(svm_ssnalm_t *h, const int32_t *J, int64_t p, double sigma, const double *g,
+                                    double *dv)
+{
+    if (!h || !g || !dv || p < 0 || (p > 0 && !J) || !(sigma > 0.0)) return SVM_ERR_INVALID_ARG;
+    Work &W = h->W;
+    CK(timed(h, TK_NEWTON, [&] { return launch_newton(W, J, p, nullptr, sigma, g, dv); }));
+    return sync_read(h);
+}
+
+extern "C" svm_status svm_op_kkt(svm_ssnalm_t *h, const double *alpha, double *kkt, double *lambda)
+{
+    if (!h || !alpha) return SVM_ERR_INVALID_ARG;
+    svm_status st = kkt_launch(h, alpha, nullptr, nullptr);
+    if (st != SVM_OK) return st;
+    if ((st = sync_read(h)) != SVM_OK) return st;
+    if (kkt) *kkt = kkt_value(h->W.h_pout[PM_KKT]);
+    if (lambda) *lambda = h->W.h_pout[PM_KKT].lam;
+    return SVM_OK;
+}
+
+// ------------------------------------------------------------ instrumentation
+
+extern "C" svm_status svm_ssnalm_set_timing(svm_ssnalm_t *h, int enable)
+{
+    if (!h) return SVM_ERR_INVALID_ARG;
+    CK(cudaStreamSynchronize(h->W.st));
+    flush_timing(h);
+    h->timing = enable != 0;
+    return SVM_OK;
+}
+
+extern "C" svm_status svm_ssnalm_get_stats(svm_ssnalm_t *h, svm_stats *out, int reset)
+{
+    if (!h || !out) return SVM_ERR_INVALID_ARG;
+    CK(cudaStreamSynchronize(h->W.st));
+    flush_timing(h);
+    out->launches = h->W.nlaunch - h->launch_base;
+    out->matvec_calls = h->kcalls[TK_MATVEC];
+    out->matvec_ms = h->kms[TK_MATVEC];
+    out->rmatvec_calls = h->kcalls[TK_RMATVEC];
+    out->rmatvec_ms = h->kms[TK_RMATVEC];
+    out->proj_calls = h->kcalls[TK_PROJ];
+    out->proj_ms = h->kms[TK_PROJ];
+    out->newton_calls = h->kcalls[TK_NEWTON];
+    out->newton_ms = h->kms[TK_NEWTON];
+    out->host_syncs = h->syncs;
+    if (reset) {
+        h->launch_base = h->W.nlaunch;
+        for (int k = 0; k < 4; ++k) { h->kcalls[k] = 0; h->kms[k] = 0.0; }
+        h->syncs = 0;
+    }
+    return SVM_OK;
+}

@@ -1,0 +1,293 @@
+"""GPU parity: every step of the hot path and the whole solve, through the C
+ABI, against the FP64 CPU oracle on the same seeded inputs.
+
+Tolerances.  PLAIN_FP64 steps are FP64 with a different summation order than
+the oracle, so elementwise results agree to a few ulps of the summed
+magnitudes (rtol 1e-12 against the absolute-sum scale).  Index sets (J, S) are
+compared exactly except for components whose clipped value lies within
+roundoff of a bound, where either side is correct.  Whole solves are compared
+on what is unique (objective, w, b when free SVs exist) at the north-star
+tolerance: relative objective <= 1e-6 and R_KKT <= 1e-6.
+"""
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1910_01312_gb300 as P  # noqa: E402
+
+PRECS = [P.PREC_PLAIN_FP64, P.PREC_MIXED]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    P.load()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def make(X, y, C=1.0, **kw):
+    Xd, yd = dev(X), dev(y.astype(np.int8))
+    s = P.Solver(Xd, yd, C_=C, **kw)
+    return s, Xd, yd
+
+
+# ------------------------------------------------------------------ matvecs
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("dtype,n,q", [(np.float32, 5003, 128), (np.float64, 2000, 50),
+                                       (np.float32, 777, 33), (np.float64, 1031, 7),
+                                       (np.float32, 4099, 784)])
+def test_matvec_rmatvec(prec, dtype, n, q):
+    X, y = datagen.small(n, q, seed=n + q, dtype=dtype)
+    s, Xd, yd = make(X, y, precision=prec)
+    rng = np.random.default_rng(1)
+    v = rng.normal(size=q)
+    c = np.where(rng.random(n) < 0.3, 0.0, rng.uniform(0, 1, n))
+    z = torch.empty(n, dtype=torch.float64, device="cuda")
+    o = torch.empty(q, dtype=torch.float64, device="cuda")
+    s.matvec(dev(v), z)
+    s.rmatvec(dev(c), o)
+    zr = oracle.matvec(X, y, v)
+    orr, sc = oracle.rmatvec(X, y, c, with_scale=True)
+    scale_z = np.abs(X.astype(np.float64)) @ np.abs(v)
+    np.testing.assert_array_less(np.abs(host(z) - zr), 1e-12 * scale_z + 1e-300)
+    np.testing.assert_array_less(np.abs(host(o) - orr), 1e-12 * sc + 1e-300)
+
+
+# ---------------------------------------------------------------- projection
+
+def _check_projection(u, y, C, pi, lam, J, S, p, s_):
+    pi_r, lam_r = oracle.project(u, y, C)
+    scale = C + np.max(np.abs(u))
+    np.testing.assert_allclose(pi, pi_r, rtol=0, atol=1e-12 * scale)
+    t = u - lam * y.astype(np.float64)
+    np.testing.assert_array_equal(pi, np.clip(t, 0.0, C))    # pi = clip(u - lambda y) exactly
+    assert abs(np.sum(y * pi)) <= 1e-11 * (1 + np.sum(pi))
+    Jr = oracle.free_set(u, y, C, lam_r)
+    ambiguous = np.minimum(np.abs(t), np.abs(t - C)) <= 1e-11 * scale
+    Jset, Jrset = set(J[:p].tolist()), set(Jr.tolist())
+    diff = Jset ^ Jrset
+    assert all(ambiguous[i] for i in diff), sorted(diff)[:10]
+    assert list(J[:p]) == sorted(J[:p])                     # ascending, stable
+    Sr = np.nonzero(pi > 0)[0]
+    np.testing.assert_array_equal(S[:s_], Sr)
+
+
+def test_projection_worked_example():
+    g = {}
+    import os
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", "projection_worked_n4.txt")):
+        if line.strip() and not line.startswith("#"):
+            k, *v = line.split()
+            g[k] = np.array([float(x) for x in v])
+    y = g["y"].astype(np.int8)
+    X = np.ones((4, 2))
+    s, _, _ = make(X, y, C=g["C"][0])
+    pi = torch.empty(4, dtype=torch.float64, device="cuda")
+    J = torch.empty(4, dtype=torch.int32, device="cuda")
+    S = torch.empty(4, dtype=torch.int32, device="cuda")
+    lam, p, sc = s.project(dev(g["u"]), pi, J, S)
+    assert lam == pytest.approx(0.05, abs=1e-15)
+    np.testing.assert_allclose(host(pi), g["pi"], atol=1e-15)
+    assert host(J)[:p].tolist() == [0, 1]
+    assert host(S)[:sc].tolist() == [0, 1, 3]
+
+
+@pytest.mark.parametrize("n,C,seed", [(5, 1.0, 0), (2000, 1.0, 1), (2000, 0.1, 2), (70001, 0.5, 3),
+                                      (300000, 2.0, 4), (1_000_000, 0.1, 5)])
+def test_projection(n, C, seed):
+    rng = np.random.default_rng(seed)
+    y = np.where(rng.random(n) < 0.45, 1, -1).astype(np.int8)
+    y[0], y[1] = 1, -1
+    u = rng.normal(0.3 * C, 2.0 * C, size=n)
+    # exact ties at the bounds for a few components
+    if n >= 6:
+        u[2:6] = [0.0, C, -0.0, C]
+    X = np.ones((n, 1))
+    s, _, _ = make(X, y, C=C)
+    pi = torch.empty(n, dtype=torch.float64, device="cuda")
+    J = torch.empty(n, dtype=torch.int32, device="cuda")
+    S = torch.empty(n, dtype=torch.int32, device="cuda")
+    lam, p, sc = s.project(dev(u), pi, J, S)
+    _check_projection(u, y, C, host(pi), lam, host(J), host(S), p, sc)
+
+
+def test_projection_flat_segment():
+    """All components saturate at the root (empty free set): pi is unique,
+    lambda may be any point of the flat piece."""
+    y = np.array([1, 1, -1, -1], np.int8)
+    u = np.array([5.0, -3.0, 4.0, -2.0])
+    X = np.ones((4, 1))
+    s, _, _ = make(X, y, C=1.0)
+    pi = torch.empty(4, dtype=torch.float64, device="cuda")
+    lam, p, _ = s.project(dev(u), pi)
+    pi_r, _ = oracle.project(u, y, 1.0)
+    np.testing.assert_array_equal(host(pi), pi_r)
+    assert p == 0
+
+
+# ------------------------------------------------------------------ Newton
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("dtype,n,q,frac", [(np.float64, 400, 50, 0.3), (np.float32, 3000, 128, 0.2),
+                                            (np.float32, 5000, 33, 0.01), (np.float64, 300, 150, 0.9)])
+def test_newton_direction(prec, dtype, n, q, frac):
+    X, y = datagen.small(n, q, seed=q, dtype=dtype)
+    rng = np.random.default_rng(q)
+    J = np.sort(rng.choice(n, size=max(1, int(frac * n)), replace=False)).astype(np.int64)
+    g = rng.normal(size=q)
+    sigma = 3.7
+    dv_r = oracle.newton_direction(X, y, J, sigma, g, form=1)
+    s, _, _ = make(X, y, precision=prec)
+    dv = torch.empty(q, dtype=torch.float64, device="cuda")
+    s.newton(dev(J.astype(np.int32)), J.size, sigma, dev(g), dv)
+    # the Newton matrix M has eigenvalues in [1, 1 + sigma |X_J|^2]; compare the
+    # residual of the oracle's system, relative to |g|
+    A = X.astype(np.float64) * y[:, None]
+    AJ = A[J]
+    h = AJ.T @ y[J].astype(np.float64)
+    M = np.eye(q) + sigma * (AJ.T @ AJ - np.outer(h, h) / J.size)
+    r = M @ host(dv) + g
+    tol = 1e-10 if prec == P.PREC_PLAIN_FP64 else 1e-6
+    assert np.linalg.norm(r) <= tol * np.linalg.norm(g) * np.linalg.cond(M) ** 0.5
+    np.testing.assert_allclose(host(dv), dv_r, rtol=0, atol=tol * np.linalg.cond(M) * np.linalg.norm(dv_r))
+
+
+def test_newton_empty_free_set():
+    X, y = datagen.small(50, 8, seed=0)
+    s, _, _ = make(X, y)
+    g = np.arange(8.0)
+    dv = torch.empty(8, dtype=torch.float64, device="cuda")
+    s.newton(None, 0, 2.0, dev(g), dv)
+    np.testing.assert_array_equal(host(dv), -g)
+
+
+# --------------------------------------------------------------------- KKT
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_kkt_residual(prec):
+    X, y = datagen.small(3000, 20, seed=3)
+    C = 0.7
+    rng = np.random.default_rng(0)
+    a, _ = oracle.project(rng.uniform(0, C, 3000), y, C)
+    s, _, _ = make(X, y, C=C, precision=prec)
+    r, lam = s.kkt(dev(a))
+    r_ref, lam_ref, _ = oracle.kkt(X, y, C, a, with_extras=True)
+    assert r == pytest.approx(r_ref, rel=1e-9)
+
+
+# ------------------------------------------------------------ whole solves
+
+def _solve_gpu(X, y, C, tol=1e-6, host_mem=False, alpha0=None, **kw):
+    n, q = X.shape
+    if host_mem:
+        s = P.Solver(np.ascontiguousarray(X), np.ascontiguousarray(y, dtype=np.int8), C_=C, tol=tol, **kw)
+        alpha, w = np.zeros(n), np.zeros(q)
+        r = s.solve(alpha, w, alpha0=alpha0)
+        return r, alpha, w
+    s, Xd, yd = make(X, y, C=C, tol=tol, **kw)
+    alpha = torch.zeros(n, dtype=torch.float64, device="cuda")
+    w = torch.zeros(q, dtype=torch.float64, device="cuda")
+    r = s.solve(alpha, w, alpha0=None if alpha0 is None else dev(alpha0))
+    return r, host(alpha), host(w)
+
+
+def _compare_solution(X, y, C, r, alpha, w, ref):
+    assert r["status"] == P.OK, r
+    assert r["kkt"] <= 1e-6
+    # the GPU's alpha judged by the oracle's own KKT residual
+    r_or = oracle.kkt(X, y, C, alpha)
+    assert r_or <= 2e-6, r_or
+    assert alpha.min() >= 0.0 and alpha.max() <= C
+    assert abs(np.sum(y * alpha)) <= 1e-9 * max(1.0, np.sum(alpha))
+    assert r["objective"] == pytest.approx(ref["objective"], rel=1e-6)
+    assert np.linalg.norm(w - ref["w"]) <= 1e-4 * max(1.0, np.linalg.norm(ref["w"]))
+    if ref["n_free"] > 0 and r["n_free"] > 0:
+        assert r["b"] == pytest.approx(ref["b"], abs=1e-4)
+    assert r["gap"] >= -1e-8 * (1 + abs(r["primal_objective"]))
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_solve_gauss2000(prec):
+    X, y, C = datagen.gauss2000(0)
+    ref = oracle.solve(X, y, C, tol=1e-10)
+    r, alpha, w = _solve_gpu(X, y, C, precision=prec)
+    _compare_solution(X, y, C, r, alpha, w, ref)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("n,q,seed,C,dtype", [(100, 5, 0, 1.0, np.float64), (1000, 30, 1, 0.05, np.float32),
+                                              (5000, 128, 2, 0.1, np.float32), (257, 300, 3, 10.0, np.float64)])
+def test_solve_small(prec, n, q, seed, C, dtype):
+    X, y = datagen.small(n, q, seed=seed, dtype=dtype)
+    ref = oracle.solve(X, y, C, tol=1e-10)
+    r, alpha, w = _solve_gpu(X, y, C, precision=prec)
+    _compare_solution(X, y, C, r, alpha, w, ref)
+
+
+def test_solve_host_memory_and_warm_start():
+    X, y, C = datagen.gauss2000(1)
+    ref = oracle.solve(X, y, C, tol=1e-10)
+    r, alpha, w = _solve_gpu(X, y, C, host_mem=True)
+    _compare_solution(X, y, C, r, alpha, w, ref)
+    # warm start from the solution: converges at once
+    r2, alpha2, w2 = _solve_gpu(X, y, C, host_mem=True, alpha0=alpha)
+    _compare_solution(X, y, C, r2, alpha2, w2, ref)
+    assert r2["outer_iters"] <= 2
+
+
+def test_degenerate_and_invalid():
+    X = np.ones((6, 3))
+    y = np.ones(6, np.int8)
+    r, alpha, w = _solve_gpu(X, y, 1.0)
+    assert r["status"] == P.ERR_DEGENERATE and np.all(alpha == 0)
+    with pytest.raises(P.SVMError) as e:
+        make(X, np.array([1, -1, 2, 1, -1, 1], np.int8))
+    assert e.value.status == P.ERR_INVALID_ARG
+    Xn = np.ones((6, 3))
+    Xn[2, 1] = np.nan
+    with pytest.raises(P.SVMError) as e:
+        make(Xn, np.array([1, -1, 1, 1, -1, 1], np.int8))
+    assert e.value.status == P.ERR_INVALID_ARG
+
+
+def test_single_sample_per_class():
+    x1, x2 = np.array([1.0, 2.0, -0.5]), np.array([-0.3, 0.4, 0.9])
+    X = np.stack([x1, x2])
+    y = np.array([1, -1], np.int8)
+    D = x1 - x2
+    r, alpha, w = _solve_gpu(X, y, 10.0, tol=1e-10)
+    t = 2.0 / (D @ D)
+    np.testing.assert_allclose(alpha, [t, t], rtol=1e-8)
+    assert r["b"] == pytest.approx((x2 @ x2 - x1 @ x1) / (D @ D), abs=1e-8)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_solve_gauss1m_full_size(prec):
+    """The benchmark workload at full size (n = 1e6, q = 128, FP32, C = 0.1):
+    the oracle cannot solve it in seconds, so the GPU solution is judged by
+    the oracle's own R_KKT, feasibility and the primal-dual gap."""
+    X, y, C = datagen.gauss1m(0)
+    r, alpha, w = _solve_gpu(X, y, C, precision=prec)
+    assert r["status"] == P.OK and r["kkt"] <= 1e-6
+    r_or, lam_or, w_or = oracle.kkt(X, y, C, alpha, with_extras=True)
+    assert r_or <= 2e-6
+    assert alpha.min() >= 0 and alpha.max() <= C
+    assert abs(np.sum(y * alpha)) <= 1e-9 * np.sum(alpha)
+    np.testing.assert_allclose(w, w_or, rtol=0, atol=1e-8 * max(1, np.abs(w_or).max()))
+    obj_or = 0.5 * w_or @ w_or - alpha.sum()
+    assert r["objective"] == pytest.approx(obj_or, rel=1e-10)
+    assert r["gap"] <= 1e-4 * abs(r["primal_objective"])
