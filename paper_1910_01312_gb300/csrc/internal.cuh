@@ -18,25 +18,34 @@ struct ProjOut {
     int status;        // 0 ok, DEV_ROOT if the search hit its cap
 };
 
-// What a projection launch reduces besides lambda-hat, J and S.
-enum ProjMode : int {
-    PM_OP = 0,     // nothing (step-level entry point)
-    PM_MAIN = 1,   // sum0 = |pi - alpha|^2, sum1 = sum pi(2u - pi); writes u, pi
-    PM_TRIAL = 2,  // sum0 = sum [pi(2u - pi) - pib(2ub - pib)]  (psi difference)
-    PM_KKT = 3     // sum0 = |alpha - pi|^2, sum1 = |alpha|^2, sum2 = sum alpha,
-                   // sum3 = sum max(0, 1 - (Qalpha_i + y_i lambda))
+// What a projection launch reduces besides lambda-hat, J and S (bit flags).
+enum ProjSums : int {
+    SF_DPA = 1,    // sum[0] = |pi - alpha|^2                      (needs alpha)
+    SF_PSID = 2,   // sum[1] = sum [pi(2u - pi) - pib(2ub - pib)]  (psi difference;
+                   //          base u is `a`, base pi is pi_base)
+    SF_KKT = 4     // sum[0] = |alpha - pi|^2, sum[1] = |alpha|^2, sum[2] = sum alpha,
+                   // sum[3] = sum max(0, 1 - (Qalpha_i + y_i lambda)); alpha = a, Qalpha = b
 };
 
-// u_i = c0 * a_i + c1 * b_i + c2 (b may be null).
+// Projection input u_i = a_i + c1 * b_i + c2 (b may be null) and outputs.
 struct ProjIn {
-    const double *a, *b;
-    double c0, c1, c2;
-    int mode;
-    const double *lam0;      // device: warm start for lambda (nullable)
-    double *u_out, *pi_out;  // nullable
-    int32_t *J, *S;          // nullable
-    const double *pi_base;   // PM_TRIAL: pi at the base point (its u is `a`)
-    const double *alpha;     // PM_MAIN: alpha^k
+    const double *a = nullptr, *b = nullptr;
+    double c1 = 0.0, c2 = 0.0;
+    int sums = 0;
+    const double *lam0 = nullptr;   // device: warm start for lambda (nullable)
+    double *u_out = nullptr, *pi_out = nullptr;
+    float2 *wpi_out = nullptr;      // y_i pi_i as an FP32 (hi, lo) pair
+    int32_t *J = nullptr, *S = nullptr;
+    const double *pi_base = nullptr;
+    const double *alpha = nullptr;
+};
+
+// One projection's output buffers (the solver keeps two and swaps them when a
+// line-search trial is accepted).
+struct ProjBuf {
+    double *u = nullptr, *pi = nullptr;
+    float2 *wpi = nullptr;
+    int32_t *J = nullptr, *S = nullptr;
 };
 
 struct Work {
@@ -50,11 +59,10 @@ struct Work {
     cudaStream_t st = nullptr;
     int dev = 0, nsm = 0;
     // n-vectors (FP64) and index lists
-    double *alpha = nullptr, *z = nullptr, *dz = nullptr, *u = nullptr, *pi = nullptr,
-           *qa = nullptr, *tmpn = nullptr;
-    int32_t *J = nullptr, *S = nullptr;
+    double *alpha = nullptr, *z = nullptr, *dz = nullptr, *qa = nullptr, *tmpn = nullptr;
+    ProjBuf pb[2];            // current / trial projection buffers
     // q-vectors
-    double *v = nullptr, *dv = nullptr, *g = nullptr, *atp = nullptr, *h = nullptr,
+    double *v = nullptr, *dv = nullptr, *g = nullptr, *atp = nullptr, *atp2 = nullptr, *h = nullptr,
            *w = nullptr, *tmpq = nullptr;
     double *M = nullptr;      // q*q Newton matrix / Cholesky factor
     double *part = nullptr;   // partial sums (size part_len doubles)
@@ -84,12 +92,17 @@ struct Work {
 cudaError_t proj_setup(Work &W);
 cudaError_t launch_project(Work &W, const ProjIn &in, ProjOut *out);
 
-cudaError_t launch_matvec(Work &W, const double *v, double *z);
+// z0 = A v0 (and z1 = A v1 when v1 != nullptr, in the same pass over X)
+cudaError_t launch_matvec(Work &W, const double *v0, double *z0, const double *v1 = nullptr,
+                          double *z1 = nullptr);
 // out = sum_i c_i y_i x_i over the index list idx (cnt entries, read from
-// *cnt_dev on the device) or over all rows when idx == nullptr.
+// *cnt_dev on the device) or over all rows when idx == nullptr.  The mixed
+// form reads the weights as y_i c_i FP32 pairs from wc (when non-null).
 // Also red[slot] = sum_j (sum_i |c_i x_ij|)^2 when scale_slot >= 0.
-cudaError_t launch_rmatvec(Work &W, const double *c, const int32_t *idx, const long long *cnt_dev,
-                           double *out, int scale_slot);
+cudaError_t launch_rmatvec(Work &W, const double *c, const float2 *wc, const int32_t *idx,
+                           const long long *cnt_dev, double *out, int scale_slot);
+// wc_i = y_i c_i as an FP32 (hi, lo) pair (input of the mixed A' c)
+cudaError_t split_weights(Work &W, const double *c, float2 *wc);
 // q-vector helpers
 cudaError_t launch_grad(Work &W);            // g = v - atp; red[0] = |g|^2
 cudaError_t launch_dots(Work &W);            // red[2] = g'dv, red[3] = v'dv, red[4] = dv'dv

@@ -2,10 +2,19 @@
 // (z = A v is Q w in the paper's variables, eq. (3.3); A' pi gives the
 // gradient of eq. (3.10)), plus the small q-vector updates of Algorithm 3.
 //
-// PLAIN_FP64 arithmetic: X elements are widened exactly to FP64 and every
-// product and sum is FP64.  Rows are read with 16-byte vector loads by a
-// group of G lanes per row (G chosen so each lane issues <= 4 loads per row),
-// so every load instruction of a warp touches whole 32-byte sectors.
+// Both products stream X once from HBM with 16-byte vector loads (every warp
+// load instruction touches whole 32-byte sectors) and are bandwidth-shaped:
+// X (512 MB at n = 1e6, q = 128 FP32) never fits in L2.
+//
+// PLAIN_FP64: X elements are widened exactly to FP64 and every product and
+// sum is FP64.  On this part the FP64 pipe is ~1/64 of the FP32 rate, so this
+// form is ALU-bound, not HBM-bound.
+// MIXED: products and sums on the FP32 pipes with error-free transformations
+// (Dot2 of Ogita, Rump and Oishi, SIAM J. Sci. Comput. 26(6), 2005): the FP64
+// operand is split into FP32 hi + lo, x*hi is formed exactly with TwoProd,
+// accumulated with TwoSum, and the rounding terms plus x*lo are carried in a
+// compensation word.  The result is as accurate as FP64 accumulation (error
+// ~2^-48 of the sum of |terms|), at HBM speed.
 #include <math.h>
 
 #include "internal.cuh"
@@ -27,14 +36,40 @@ __device__ __forceinline__ void vload(const double2 *p, double *o)
     o[0] = t.x; o[1] = t.y;
 }
 
-// z_i = y_i <x_i, v>; GL lanes per row; vectorised when VEC.
-template <typename TX, int GL, bool VEC>
-__global__ void __launch_bounds__(256) matvec_kernel(const TX *__restrict__ X, const int8_t *__restrict__ y,
-                                                     long long n, int q, const double *__restrict__ v,
-                                                     double *__restrict__ z)
+// One Dot2 step: (s, c) += x * (w.x + w.y), x exact FP32.
+__device__ __forceinline__ void dot2_step(float x, float2 w, float &s, float &c)
 {
-    extern __shared__ double sv[];
-    for (int j = threadIdx.x; j < q; j += blockDim.x) sv[j] = v[j];
+    float p, e, sn, t;
+    two_prod(x, w.x, p, e);
+    two_sum(s, p, sn, t);
+    s = sn;
+    c = fmaf(x, w.y, c + (t + e));
+}
+
+// (s, c) += (s2, c2) for double-float pairs.
+__device__ __forceinline__ void df_acc(float &s, float &c, float s2, float c2)
+{
+    float sn, e;
+    two_sum(s, s2, sn, e);
+    e += c + c2;
+    s = sn + e;
+    c = e - (s - sn);
+}
+
+// ---------------------------------------------------------------- A v, FP64
+
+// z_i = y_i <x_i, v> (and the same for a second vector); GL lanes per row.
+template <typename TX, int GL, bool VEC, int NV>
+__global__ void __launch_bounds__(256) matvec_kernel(const TX *__restrict__ X, const int8_t *__restrict__ y,
+                                                     long long n, int q, const double *__restrict__ v0,
+                                                     const double *__restrict__ v1, double *__restrict__ z0,
+                                                     double *__restrict__ z1)
+{
+    extern __shared__ double sv[];   // [NV][q]
+    for (int j = threadIdx.x; j < q; j += blockDim.x) {
+        sv[j] = v0[j];
+        if (NV == 2) sv[q + j] = v1[j];
+    }
     __syncthreads();
     constexpr int RPW = 32 / GL;   // rows per warp step
     const int lane = threadIdx.x & 31;
@@ -42,8 +77,10 @@ __global__ void __launch_bounds__(256) matvec_kernel(const TX *__restrict__ X, c
     const long long warps_total = (long long)gridDim.x * (blockDim.x >> 5);
     const long long wid = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     for (long long r0 = wid * RPW; r0 < n; r0 += warps_total * RPW) {
-        long long i = r0 + grp;
-        double acc = 0.0;
+        const long long i = r0 + grp;
+        double acc[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) acc[k] = 0.0;
         if (i < n) {
             const TX *row = X + i * (long long)q;
             if (VEC) {
@@ -55,46 +92,172 @@ __global__ void __launch_bounds__(256) matvec_kernel(const TX *__restrict__ X, c
                     double e[W];
                     vload(rv + c, e);
 #pragma unroll
-                    for (int k = 0; k < W; ++k) acc = fma(e[k], sv[c * W + k], acc);
+                    for (int k = 0; k < W; ++k) {
+                        acc[0] = fma(e[k], sv[c * W + k], acc[0]);
+                        if (NV == 2) acc[NV - 1] = fma(e[k], sv[q + c * W + k], acc[NV - 1]);
+                    }
                 }
             } else {
-                for (int c = sub; c < q; c += GL) acc = fma((double)row[c], sv[c], acc);
+                for (int c = sub; c < q; c += GL) {
+                    const double e = (double)row[c];
+                    acc[0] = fma(e, sv[c], acc[0]);
+                    if (NV == 2) acc[NV - 1] = fma(e, sv[q + c], acc[NV - 1]);
+                }
             }
         }
 #pragma unroll
-        for (int o = GL / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (i < n && sub == 0) z[i] = (y[i] > 0) ? acc : -acc;
+        for (int o = GL / 2; o > 0; o >>= 1)
+#pragma unroll
+            for (int k = 0; k < NV; ++k) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+        if (i < n && sub == 0) {
+            const bool pos = y[i] > 0;
+            z0[i] = pos ? acc[0] : -acc[0];
+            if (NV == 2) z1[i] = pos ? acc[NV - 1] : -acc[NV - 1];
+        }
     }
 }
 
-template <typename TX, bool VEC>
-static cudaError_t matvec_dispatch(Work &W, const double *v, double *z)
+// ---------------------------------------------------------- A v, mixed (Dot2)
+
+// FP32 X, q % 4 == 0.  A warp covers 32 consecutive rows in GL sub-steps of
+// 32/GL rows (GL lanes per row), then transposes so that lane L holds row
+// base + L: the FP64 epilogue and the z store are then one coalesced
+// warp-wide instruction per 32 rows.
+template <int GL, int NV>
+__global__ void __launch_bounds__(256) matvec_mx_kernel(const float *__restrict__ X, const int8_t *__restrict__ y,
+                                                        long long n, int q, const double *__restrict__ v0,
+                                                        const double *__restrict__ v1, double *__restrict__ z0,
+                                                        double *__restrict__ z1)
+{
+    extern __shared__ float2 svf[];   // [NV][q] FP32 (hi, lo) split of v
+    for (int j = threadIdx.x; j < q; j += blockDim.x) {
+        double d = v0[j];
+        float h = (float)d;
+        svf[j] = make_float2(h, (float)(d - (double)h));
+        if (NV == 2) {
+            d = v1[j];
+            h = (float)d;
+            svf[q + j] = make_float2(h, (float)(d - (double)h));
+        }
+    }
+    __syncthreads();
+    constexpr int RPW = 32 / GL;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane % GL, grp = lane / GL;
+    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+    const long long wid = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int nv4 = q >> 2;
+    for (long long base = wid * 32; base < n; base += nwarps * 32) {
+        float rs[NV], rc[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) { rs[k] = 0.f; rc[k] = 0.f; }
+#pragma unroll 1
+        for (int kk = 0; kk < GL; ++kk) {
+            const long long i = base + kk * RPW + grp;
+            float s[NV], c[NV];
+#pragma unroll
+            for (int k = 0; k < NV; ++k) { s[k] = 0.f; c[k] = 0.f; }
+            if (i < n) {
+                const float4 *rv = reinterpret_cast<const float4 *>(X + i * (long long)q);
+#pragma unroll 8
+                for (int ch = sub; ch < nv4; ch += GL) {
+                    const float4 x4 = __ldcs(rv + ch);
+                    const float xs[4] = {x4.x, x4.y, x4.z, x4.w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+#pragma unroll
+                        for (int k = 0; k < NV; ++k) dot2_step(xs[e], svf[k * q + ch * 4 + e], s[k], c[k]);
+                }
+            }
+#pragma unroll
+            for (int o = GL / 2; o > 0; o >>= 1)
+#pragma unroll
+                for (int k = 0; k < NV; ++k) {
+                    const float s2 = __shfl_xor_sync(0xffffffffu, s[k], o);
+                    const float c2 = __shfl_xor_sync(0xffffffffu, c[k], o);
+                    df_acc(s[k], c[k], s2, c2);
+                }
+            const int src = (lane % RPW) * GL;
+#pragma unroll
+            for (int k = 0; k < NV; ++k) {
+                const float ts = __shfl_sync(0xffffffffu, s[k], src);
+                const float tc = __shfl_sync(0xffffffffu, c[k], src);
+                if (lane / RPW == kk) { rs[k] = ts; rc[k] = tc; }
+            }
+        }
+        const long long i = base + lane;
+        if (i < n) {
+            const bool pos = y[i] > 0;
+            const double d0 = (double)rs[0] + (double)rc[0];
+            z0[i] = pos ? d0 : -d0;
+            if (NV == 2) {
+                const double d1 = (double)rs[NV - 1] + (double)rc[NV - 1];
+                z1[i] = pos ? d1 : -d1;
+            }
+        }
+    }
+}
+
+template <typename TX, bool VEC, int NV>
+static cudaError_t matvec_dispatch(Work &W, const double *v0, double *z0, const double *v1, double *z1)
 {
     constexpr int Wd = VEC ? Vec<TX>::W : 1;
-    int chunks = (int)((W.q + Wd - 1) / Wd);
+    const int chunks = (int)((W.q + Wd - 1) / Wd);
     int gl = 1;
     while (gl < 32 && (chunks + gl - 1) / gl > 4) gl <<= 1;
-    int blocks = W.nsm * 8;
-    size_t smem = (size_t)W.q * sizeof(double);
+    const int blocks = W.nsm * 8;
+    const size_t smem = (size_t)NV * W.q * sizeof(double);
     const TX *X = (const TX *)W.X;
 #define MV_CASE(G)                                                                                         \
     case G:                                                                                                \
-        matvec_kernel<TX, G, VEC><<<blocks, 256, smem, W.st>>>(X, W.y, W.n, (int)W.q, v, z);             \
-        ++W.nlaunch;                                                                                       \
+        matvec_kernel<TX, G, VEC, NV><<<blocks, 256, smem, W.st>>>(X, W.y, W.n, (int)W.q, v0, v1, z0, z1); \
         break;
     switch (gl) {
         MV_CASE(1) MV_CASE(2) MV_CASE(4) MV_CASE(8) MV_CASE(16) MV_CASE(32)
     }
 #undef MV_CASE
+    ++W.nlaunch;
     return cudaGetLastError();
 }
 
-cudaError_t launch_matvec(Work &W, const double *v, double *z)
+template <int NV>
+static cudaError_t matvec_mx_dispatch(Work &W, const double *v0, double *z0, const double *v1, double *z1)
 {
-    size_t es = W.xf32 ? 4 : 8;
-    bool vec = ((W.q * es) % 16 == 0) && ((uintptr_t)W.X % 16 == 0);
-    if (W.xf32) return vec ? matvec_dispatch<float, true>(W, v, z) : matvec_dispatch<float, false>(W, v, z);
-    return vec ? matvec_dispatch<double, true>(W, v, z) : matvec_dispatch<double, false>(W, v, z);
+    const int nv4 = (int)(W.q / 4);
+    int gl = 1;
+    while (gl < 32 && (nv4 + gl - 1) / gl > 8) gl <<= 1;
+    const int blocks = W.nsm * 8;
+    const size_t smem = (size_t)NV * W.q * sizeof(float2);
+    const float *X = (const float *)W.X;
+#define MX_CASE(G)                                                                                        \
+    case G:                                                                                               \
+        matvec_mx_kernel<G, NV><<<blocks, 256, smem, W.st>>>(X, W.y, W.n, (int)W.q, v0, v1, z0, z1);     \
+        break;
+    switch (gl) {
+        MX_CASE(1) MX_CASE(2) MX_CASE(4) MX_CASE(8) MX_CASE(16) MX_CASE(32)
+    }
+#undef MX_CASE
+    ++W.nlaunch;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_matvec(Work &W, const double *v0, double *z0, const double *v1, double *z1)
+{
+    const size_t es = W.xf32 ? 4 : 8;
+    const bool vec = ((W.q * es) % 16 == 0) && ((uintptr_t)W.X % 16 == 0);
+    const bool two = v1 != nullptr;
+    if (W.xf32 && vec && W.precision == 1)
+        return two ? matvec_mx_dispatch<2>(W, v0, z0, v1, z1) : matvec_mx_dispatch<1>(W, v0, z0, v1, z1);
+    if (W.xf32) {
+        if (vec) return two ? matvec_dispatch<float, true, 2>(W, v0, z0, v1, z1)
+                            : matvec_dispatch<float, true, 1>(W, v0, z0, v1, z1);
+        return two ? matvec_dispatch<float, false, 2>(W, v0, z0, v1, z1)
+                   : matvec_dispatch<float, false, 1>(W, v0, z0, v1, z1);
+    }
+    if (vec) return two ? matvec_dispatch<double, true, 2>(W, v0, z0, v1, z1)
+                        : matvec_dispatch<double, true, 1>(W, v0, z0, v1, z1);
+    return two ? matvec_dispatch<double, false, 2>(W, v0, z0, v1, z1)
+               : matvec_dispatch<double, false, 1>(W, v0, z0, v1, z1);
 }
 
 // ----------------------------------------------------------------- A' c
@@ -120,16 +283,16 @@ __global__ void __launch_bounds__(256) rmatvec_part_kernel(const TX *__restrict_
 #pragma unroll
     for (int k = 0; k < NCH; ++k) { acc[k] = 0.0; aac[k] = 0.f; }
     for (long long r = r_beg + warp; r < r_end; r += nw) {
-        long long i = idx ? (long long)idx[r] : r;
-        double ci = c[i];
+        const long long i = idx ? (long long)idx[r] : r;
+        const double ci = c[i];
         if (ci == 0.0) continue;
-        double cy = (y[i] > 0) ? ci : -ci;
+        const double cy = (y[i] > 0) ? ci : -ci;
         const TX *row = X + i * (long long)q;
 #pragma unroll
         for (int k = 0; k < NCH; ++k) {
-            int j = lane + 32 * k;
+            const int j = lane + 32 * k;
             if (j < q) {
-                double xv = (double)__ldcs(row + j);
+                const double xv = (double)__ldcs(row + j);
                 acc[k] = fma(cy, xv, acc[k]);
                 aac[k] += (float)fabs(cy * xv);
             }
@@ -142,7 +305,7 @@ __global__ void __launch_bounds__(256) rmatvec_part_kernel(const TX *__restrict_
         if (warp == w) {
 #pragma unroll
             for (int k = 0; k < NCH; ++k) {
-                int j = lane + 32 * k;
+                const int j = lane + 32 * k;
                 if (j < q) { sred[j] += acc[k]; sred[q + j] += (double)aac[k]; }
             }
         }
@@ -151,6 +314,99 @@ __global__ void __launch_bounds__(256) rmatvec_part_kernel(const TX *__restrict_
     for (int j = threadIdx.x; j < q; j += blockDim.x) {
         part[(size_t)blockIdx.x * q + j] = sred[j];
         apart[(size_t)blockIdx.x * q + j] = sred[q + j];
+    }
+}
+
+// Mixed form.  Weights arrive as y_i c_i in FP32 (hi, lo) pairs; VW = 4:
+// lane l owns the float4 column chunks l + 32k (q % 4 == 0), VW = 1: the
+// scalar columns l + 32k.  Four rows are in flight per warp.
+template <int VW, int NCH>
+__global__ void __launch_bounds__(256) rmatvec_mx_part_kernel(const float *__restrict__ X, long long n, int q,
+                                                              const float2 *__restrict__ wc,
+                                                              const int32_t *__restrict__ idx,
+                                                              const long long *__restrict__ cnt_dev,
+                                                              double *__restrict__ part, double *__restrict__ apart)
+{
+    const long long cnt = idx ? *cnt_dev : n;
+    const int G = gridDim.x;
+    const long long per = (cnt + G - 1) / G;
+    const long long r_beg = (long long)blockIdx.x * per;
+    const long long r_end = r_beg + per < cnt ? r_beg + per : cnt;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int nch = q / VW;
+    float s[NCH][VW], c[NCH][VW], ab[NCH][VW];
+#pragma unroll
+    for (int k = 0; k < NCH; ++k)
+#pragma unroll
+        for (int e = 0; e < VW; ++e) { s[k][e] = 0.f; c[k][e] = 0.f; ab[k][e] = 0.f; }
+    constexpr int R = NCH >= 4 ? 1 : (NCH == 2 ? 2 : 4);   // rows in flight per warp
+    for (long long r0 = r_beg + warp; r0 < r_end; r0 += (long long)nw * R) {
+        float2 w[R];
+        long long ii[R];
+#pragma unroll
+        for (int u = 0; u < R; ++u) {
+            const long long r = r0 + (long long)u * nw;
+            ii[u] = -1;
+            w[u] = make_float2(0.f, 0.f);
+            if (r < r_end) {
+                ii[u] = idx ? (long long)idx[r] : r;
+                w[u] = wc[ii[u]];
+            }
+        }
+        float xv[R][NCH][VW];
+#pragma unroll
+        for (int u = 0; u < R; ++u)
+#pragma unroll
+            for (int k = 0; k < NCH; ++k) {
+                const int ch = lane + 32 * k;
+                if (ii[u] >= 0 && ch < nch) {
+                    if (VW == 4) {
+                        const float4 x4 = __ldcs(reinterpret_cast<const float4 *>(X + ii[u] * (long long)q) + ch);
+                        xv[u][k][0] = x4.x; xv[u][k][VW > 1 ? 1 : 0] = x4.y;
+                        xv[u][k][VW > 2 ? 2 : 0] = x4.z; xv[u][k][VW > 3 ? 3 : 0] = x4.w;
+                    } else {
+                        xv[u][k][0] = __ldcs(X + ii[u] * (long long)q + ch);
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < VW; ++e) xv[u][k][e] = 0.f;
+                }
+            }
+#pragma unroll
+        for (int u = 0; u < R; ++u)
+#pragma unroll
+            for (int k = 0; k < NCH; ++k)
+#pragma unroll
+                for (int e = 0; e < VW; ++e) {
+                    dot2_step(xv[u][k][e], w[u], s[k][e], c[k][e]);
+                    ab[k][e] += fabsf(xv[u][k][e] * w[u].x);
+                }
+    }
+    extern __shared__ float sredf[];   // [3][q]: s, c, |.|
+    for (int j = threadIdx.x; j < 3 * q; j += blockDim.x) sredf[j] = 0.f;
+    __syncthreads();
+    for (int wv = 0; wv < nw; ++wv) {
+        if (warp == wv) {
+#pragma unroll
+            for (int k = 0; k < NCH; ++k) {
+                const int ch = lane + 32 * k;
+                if (ch < nch)
+#pragma unroll
+                    for (int e = 0; e < VW; ++e) {
+                        const int j = ch * VW + e;
+                        float ss = sredf[j], cc = sredf[q + j];
+                        df_acc(ss, cc, s[k][e], c[k][e]);
+                        sredf[j] = ss;
+                        sredf[q + j] = cc;
+                        sredf[2 * q + j] += ab[k][e];
+                    }
+            }
+        }
+        __syncthreads();
+    }
+    for (int j = threadIdx.x; j < q; j += blockDim.x) {
+        part[(size_t)blockIdx.x * q + j] = (double)sredf[j] + (double)sredf[q + j];
+        apart[(size_t)blockIdx.x * q + j] = (double)sredf[2 * q + j];
     }
 }
 
@@ -178,15 +434,15 @@ __global__ void rmatvec_final_kernel(int G, int q, const double *__restrict__ pa
 }
 
 template <typename TX>
-static cudaError_t rmatvec_t(Work &W, const double *c, const int32_t *idx, const long long *cnt_dev,
-                             double *out, int scale_slot)
+static cudaError_t rmatvec_t(Work &W, const double *c, const int32_t *idx, const long long *cnt_dev, double *out,
+                             int scale_slot)
 {
-    int q = (int)W.q;
-    int nch = (q + 31) / 32;
-    int G = W.rm_grid;
+    const int q = (int)W.q;
+    const int nch = (q + 31) / 32;
+    const int G = W.rm_grid;
     double *part = W.part;
     double *apart = W.part + (size_t)G * q;
-    size_t smem = (size_t)2 * q * sizeof(double);
+    const size_t smem = (size_t)2 * q * sizeof(double);
     const TX *X = (const TX *)W.X;
 #define RM_CASE(K)                                                                                         \
     if (nch <= K) {                                                                                        \
@@ -199,9 +455,59 @@ static cudaError_t rmatvec_t(Work &W, const double *c, const int32_t *idx, const
     return cudaGetLastError();
 }
 
-cudaError_t launch_rmatvec(Work &W, const double *c, const int32_t *idx, const long long *cnt_dev,
+static cudaError_t rmatvec_mx(Work &W, const float2 *wc, const int32_t *idx, const long long *cnt_dev, double *out,
+                              int scale_slot)
+{
+    const int q = (int)W.q;
+    const int G = W.rm_grid;
+    double *part = W.part;
+    double *apart = W.part + (size_t)G * q;
+    const size_t smem = (size_t)3 * q * sizeof(float);
+    const float *X = (const float *)W.X;
+    const bool vec = (q % 4 == 0) && ((uintptr_t)W.X % 16 == 0);
+    const int nch = vec ? (q / 4 + 31) / 32 : (q + 31) / 32;
+    if (vec) {
+#define RX_CASE(K)                                                                                         \
+    if (nch <= K) {                                                                                        \
+        rmatvec_mx_part_kernel<4, K><<<G, 256, smem, W.st>>>(X, W.n, q, wc, idx, cnt_dev, part, apart);    \
+    } else
+        RX_CASE(1) RX_CASE(2) RX_CASE(4) RX_CASE(8) { return cudaErrorInvalidValue; }
+#undef RX_CASE
+    } else {
+#define RS_CASE(K)                                                                                         \
+    if (nch <= K) {                                                                                        \
+        rmatvec_mx_part_kernel<1, K><<<G, 256, smem, W.st>>>(X, W.n, q, wc, idx, cnt_dev, part, apart);    \
+    } else
+        RS_CASE(1) RS_CASE(2) RS_CASE(4) RS_CASE(8) RS_CASE(16) RS_CASE(32) { return cudaErrorInvalidValue; }
+#undef RS_CASE
+    }
+    rmatvec_final_kernel<<<1, 1024, 0, W.st>>>(G, q, part, apart, out, W.red, scale_slot);
+    W.nlaunch += 2;
+    return cudaGetLastError();
+}
+
+__global__ void split_weights_kernel(long long n, const double *c, const int8_t *y, float2 *wc)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double v = (y[i] > 0) ? c[i] : -c[i];
+        const float hi = (float)v;
+        wc[i] = make_float2(hi, (float)(v - (double)hi));
+    }
+}
+
+cudaError_t split_weights(Work &W, const double *c, float2 *wc)
+{
+    int blocks = (int)((W.n + 255) / 256);
+    if (blocks > W.nsm * 8) blocks = W.nsm * 8;
+    split_weights_kernel<<<blocks, 256, 0, W.st>>>(W.n, c, W.y, wc);
+    ++W.nlaunch;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rmatvec(Work &W, const double *c, const float2 *wc, const int32_t *idx, const long long *cnt_dev,
                            double *out, int scale_slot)
 {
+    if (W.precision == 1 && W.xf32 && wc) return rmatvec_mx(W, wc, idx, cnt_dev, out, scale_slot);
     return W.xf32 ? rmatvec_t<float>(W, c, idx, cnt_dev, out, scale_slot)
                   : rmatvec_t<double>(W, c, idx, cnt_dev, out, scale_slot);
 }
@@ -224,11 +530,11 @@ __global__ void grad_kernel(int q, const double *v, const double *atp, double *g
     __shared__ double sh[32];
     double s = 0.0;
     for (int j = threadIdx.x; j < q; j += blockDim.x) {
-        double gj = v[j] - atp[j];
+        const double gj = v[j] - atp[j];
         g[j] = gj;
         s = fma(gj, gj, s);
     }
-    double t = block_sum_1024(s, sh);
+    const double t = block_sum_1024(s, sh);
     if (threadIdx.x == 0) red[0] = t;
 }
 

@@ -10,29 +10,41 @@
 // y_i, 0, C) (= -grad phi of Sec. 3.2.1).  One pass reduces f, the one-sided
 // slopes (free counts on each side) and the nearest breakpoint on each side;
 // a Newton step that stays inside the current linear piece lands exactly on
-// the root, otherwise the bracket shrinks (secant, then bisection, as
-// safeguards).  The result is the same lambda-hat as Algorithm 2 up to
-// rounding (and any point of the flat piece when the root set is an interval;
-// pi is the same either way).  Ties follow the paper's clip: t >= C -> C,
+// the root.  Until the root is bracketed the steps grow geometrically; once
+// it is, Newton steps inside the bracket alternate with secant steps and a
+// forced bisection every third pass, so the bracket shrinks geometrically.
+// The result is the same lambda-hat as Algorithm 2 up to rounding (and any
+// point of the flat piece when the root set is an interval; pi is the same
+// either way).  Ties follow the paper's clip: t >= C -> C,
 // t <= 0 -> 0, so J uses strict inequalities.
+//
+// Precision.  The plain form (MX = false) evaluates every component in FP64.
+// The mixed form (MX = true) keeps r_i = fl32(s_i - lambda_0) next to s_i and
+// classifies a component in FP32 whenever its clipped value is certainly 0 or
+// certainly C (|error| bound (|r| + |delta| + C) 2^-20); only the components
+// near a bound -- the free ones and the ambiguous ones -- are evaluated in
+// FP64.  Saturated components enter f through exact integer counts, and their
+// breakpoint distances enter the segment test as conservative (never too far)
+// bounds, so the exact-root test and every output are those of the FP64 form.
 #include <math.h>
 
 #include "internal.cuh"
 
 namespace svm {
 
-constexpr int kMaxPass = 96;
+constexpr int kMaxPass = 256;
 constexpr int kPartStride = 8;   // doubles per block partial
 
 struct ProjArgs {
     const double *a, *b;
-    double c0, c1, c2;
+    double c1, c2;
     const int8_t *y;
     long long n;
     double C;
-    int mode;
+    int sums;
     const double *lam0;
     double *u_out, *pi_out;
+    float2 *wpi_out;
     int32_t *J, *S;
     const double *pi_base;
     const double *alpha;
@@ -43,146 +55,213 @@ struct ProjArgs {
     ProjOut *out;
 };
 
+struct PassAcc {
+    double fex;   // exact part of f over the components evaluated in FP64
+    double nup;   // (#upper with y=+1) - (#upper with y=-1): contributes C * nup
+    double pp;    // free count just right of lambda
+    double pm;    // free count just left of lambda
+    double dhi;   // smallest positive breakpoint offset (+inf: none)
+    double dlo;   // largest negative breakpoint offset (-inf: none)
+};
+
+__device__ __forceinline__ void acc_init(PassAcc &A)
+{
+    A.fex = 0.0; A.nup = 0.0; A.pp = 0.0; A.pm = 0.0; A.dhi = INFINITY; A.dlo = -INFINITY;
+}
+
+__device__ __forceinline__ void offset_in(PassAcc &A, double o)
+{
+    if (o > 0.0) A.dhi = fmin(A.dhi, o);
+    else if (o < 0.0) A.dlo = fmax(A.dlo, o);
+}
+
+// Exact FP64 evaluation of one component at lambda.
+__device__ __forceinline__ void eval_exact(double s, bool pos, double lam, double C, PassAcc &A)
+{
+    const double t = pos ? (s - lam) : (lam - s);
+    if (t >= C) A.nup += pos ? 1.0 : -1.0;
+    else if (t > 0.0) A.fex += pos ? t : -t;
+    const bool open = (t > 0.0) && (t < C);
+    const bool at0 = (t == 0.0), atC = (t == C);
+    A.pp += (open || (pos ? atC : at0)) ? 1.0 : 0.0;
+    A.pm += (open || (pos ? at0 : atC)) ? 1.0 : 0.0;
+    // breakpoints at offsets (in lambda): y=+1: t, t - C;  y=-1: -t, C - t
+    offset_in(A, pos ? t : -t);
+    offset_in(A, pos ? t - C : C - t);
+}
+
+// One component at lambda: in FP32 when it is certainly saturated (mixed
+// form), else exactly.
+template <bool MX>
+__device__ __forceinline__ void eval_comp(double s, float r, bool pos, double lam, float dl, double C,
+                                          float Cf, PassAcc &A)
+{
+    if (MX) {
+        const float tf = pos ? (r - dl) : (dl - r);
+        const float er = (fabsf(r) + fabsf(dl) + Cf) * 9.5367431640625e-07f;   // 2^-20
+        if (tf > Cf + er) {
+            A.nup += pos ? 1.0 : -1.0;
+            // offsets t - C (y=+1, above) or C - t (y=-1, below), made nearer by er
+            if (pos) A.dhi = fmin(A.dhi, (double)(tf - Cf - er));
+            else A.dlo = fmax(A.dlo, (double)(Cf - tf + er));
+            return;
+        }
+        if (tf < -er) {
+            // offsets t (y=+1, below) or -t (y=-1, above)
+            if (pos) A.dlo = fmax(A.dlo, (double)(tf + er));
+            else A.dhi = fmin(A.dhi, (double)(-tf - er));
+            return;
+        }
+    }
+    eval_exact(s, pos, lam, C, A);
+}
+
 // Fixed-order reduction of the G block partials of one slot; every block
-// calls it on the same data and gets bit-identical results.
+// calls it on the same data and gets bit-identical results (warp 0 only).
 __device__ __forceinline__ void reduce_partials(const double *slot, int G, double *tot)
 {
-    // warp 0 only; tot[0]=sum f, [1]=max blo, [2]=min bhi, [3]=sum pp, [4]=sum pm
     const int lane = threadIdx.x & 31;
-    double F = 0.0, blo = -INFINITY, bhi = INFINITY, pp = 0.0, pm = 0.0;
+    double F = 0.0, nu = 0.0, pp = 0.0, pm = 0.0, dh = INFINITY, dlo = -INFINITY;
     for (int bb = lane; bb < G; bb += 32) {
         const double *p = slot + (size_t)bb * kPartStride;
         F += __ldcg(p + 0);
-        blo = fmax(blo, __ldcg(p + 1));
-        bhi = fmin(bhi, __ldcg(p + 2));
-        pp += __ldcg(p + 3);
-        pm += __ldcg(p + 4);
+        nu += __ldcg(p + 1);
+        pp += __ldcg(p + 2);
+        pm += __ldcg(p + 3);
+        dh = fmin(dh, __ldcg(p + 4));
+        dlo = fmax(dlo, __ldcg(p + 5));
     }
-    F = warp_sum(F);
-    blo = warp_max(blo);
-    bhi = warp_min(bhi);
-    pp = warp_sum(pp);
-    pm = warp_sum(pm);
-    tot[0] = F; tot[1] = blo; tot[2] = bhi; tot[3] = pp; tot[4] = pm;
+    tot[0] = warp_sum(F); tot[1] = warp_sum(nu); tot[2] = warp_sum(pp); tot[3] = warp_sum(pm);
+    tot[4] = warp_min(dh); tot[5] = warp_max(dlo);
 }
 
-template <int EPT>
+__device__ __forceinline__ double flip_sign(double x, bool neg)
+{
+    return neg ? __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ULL) : x;
+}
+
+template <int EPT, bool MX>
 __global__ void __launch_bounds__(kTPB) proj_kernel(ProjArgs A)
 {
     const int G = gridDim.x, blk = blockIdx.x, tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const long long NT = (long long)G * kTPB;
     const double C = A.C;
+    const float Cf = (float)C;
+
+    double lam0 = A.lam0 ? __ldcg(A.lam0) : 0.0;
+    if (!isfinite(lam0)) lam0 = 0.0;
 
     double s[EPT];
-    float ys[EPT];
+    float r[EPT];
+    unsigned posm = 0u, valm = 0u;
 #pragma unroll
     for (int k = 0; k < EPT; ++k) {
-        long long i = k * NT + (long long)blk * kTPB + tid;
+        const long long i = k * NT + (long long)blk * kTPB + tid;
+        s[k] = 0.0;
+        r[k] = 0.f;
         if (i < A.n) {
-            double u = A.c0 * A.a[i] + A.c2;
+            double u = A.a[i] + A.c2;
             if (A.b) u = fma(A.c1, A.b[i], u);
-            float yy = (float)A.y[i];
-            s[k] = (yy > 0.f) ? u : -u;
-            ys[k] = yy;
-        } else {
-            s[k] = 0.0;
-            ys[k] = 0.f;
+            const bool pos = A.y[i] > 0;
+            s[k] = flip_sign(u, !pos);
+            if (MX) r[k] = (float)(s[k] - lam0);
+            posm |= (pos ? 1u : 0u) << k;
+            valm |= 1u << k;
         }
     }
 
-    __shared__ double sh_d[kWarps][3];
-    __shared__ double sh_c[kWarps][2];
-    __shared__ double sh_tot[5];
+    __shared__ double sh_d[kWarps][6];
     __shared__ double sh_lam;
     __shared__ int sh_done;
 
-    double lam = A.lam0 ? __ldcg(A.lam0) : 0.0;
-    if (!isfinite(lam)) lam = 0.0;
-    // bracket: f(L) > 0 > f(U)
-    double L = -INFINITY, U = INFINITY, FL = 0.0, FU = 0.0;
+    double lam = lam0;
+    double L = -INFINITY, U = INFINITY, FL = 0.0, FU = 0.0;   // bracket: f(L) > 0 > f(U)
+    double last_step = 0.0;
+    int last_dir = 0, nbr = 0;
     double lam_hat = lam;
     int pass = 0;
     bool alive = true;
 
     for (;;) {
-        double F = 0.0, blo = -INFINITY, bhi = INFINITY, pp = 0.0, pm = 0.0;
+        PassAcc acc;
+        acc_init(acc);
+        const float dl = MX ? (float)(lam - lam0) : 0.f;
 #pragma unroll
-        for (int k = 0; k < EPT; ++k) {
-            if (ys[k] != 0.f) {
-                const bool pos = ys[k] > 0.f;
-                double t = pos ? (s[k] - lam) : (lam - s[k]);
-                double pk = fmin(fmax(t, 0.0), C);
-                F += pos ? pk : -pk;
-                bool open = (t > 0.0) && (t < C);
-                bool at0 = (t == 0.0), atC = (t == C);
-                // one-sided free counts: right (lambda + eps) and left (lambda - eps)
-                pp += (open || (pos ? atC : at0)) ? 1.0 : 0.0;
-                pm += (open || (pos ? at0 : atC)) ? 1.0 : 0.0;
-                double b1 = pos ? s[k] - C : s[k];
-                double b2 = pos ? s[k] : s[k] + C;
-                if (b1 > lam) bhi = fmin(bhi, b1); else if (b1 < lam) blo = fmax(blo, b1);
-                if (b2 > lam) bhi = fmin(bhi, b2); else if (b2 < lam) blo = fmax(blo, b2);
-            }
-        }
-        F = warp_sum(F);
-        blo = warp_max(blo);
-        bhi = warp_min(bhi);
-        pp = warp_sum(pp);
-        pm = warp_sum(pm);
+        for (int k = 0; k < EPT; ++k)
+            if ((valm >> k) & 1u) eval_comp<MX>(s[k], r[k], (posm >> k) & 1u, lam, dl, C, Cf, acc);
+        acc.fex = warp_sum(acc.fex);
+        acc.nup = warp_sum(acc.nup);
+        acc.pp = warp_sum(acc.pp);
+        acc.pm = warp_sum(acc.pm);
+        acc.dhi = warp_min(acc.dhi);
+        acc.dlo = warp_max(acc.dlo);
         if (lane == 0) {
-            sh_d[warp][0] = F; sh_d[warp][1] = blo; sh_d[warp][2] = bhi;
-            sh_c[warp][0] = pp; sh_c[warp][1] = pm;
+            sh_d[warp][0] = acc.fex; sh_d[warp][1] = acc.nup; sh_d[warp][2] = acc.pp;
+            sh_d[warp][3] = acc.pm; sh_d[warp][4] = acc.dhi; sh_d[warp][5] = acc.dlo;
         }
         __syncthreads();
         if (tid == 0) {
-            double bF = 0.0, bl = -INFINITY, bh = INFINITY, bp = 0.0, bm = 0.0;
+            double b0 = 0, b1 = 0, b2 = 0, b3 = 0, b4 = INFINITY, b5 = -INFINITY;
             for (int w = 0; w < kWarps; ++w) {
-                bF += sh_d[w][0]; bl = fmax(bl, sh_d[w][1]); bh = fmin(bh, sh_d[w][2]);
-                bp += sh_c[w][0]; bm += sh_c[w][1];
+                b0 += sh_d[w][0]; b1 += sh_d[w][1]; b2 += sh_d[w][2]; b3 += sh_d[w][3];
+                b4 = fmin(b4, sh_d[w][4]); b5 = fmax(b5, sh_d[w][5]);
             }
             double *p = A.part + ((size_t)(pass & 1) * G + blk) * kPartStride;
-            p[0] = bF; p[1] = bl; p[2] = bh; p[3] = bp; p[4] = bm;
+            p[0] = b0; p[1] = b1; p[2] = b2; p[3] = b3; p[4] = b4; p[5] = b5;
         }
         if (!grid_barrier(A.bar, A.err)) { alive = false; break; }
         if (warp == 0) {
-            double tot[5];
+            double tot[6];
             reduce_partials(A.part + (size_t)(pass & 1) * G * kPartStride, G, tot);
             if (lane == 0) {
-                for (int f = 0; f < 5; ++f) sh_tot[f] = tot[f];
                 // ---- decision (identical in every block) ----
-                double Ft = tot[0], bl = tot[1], bh = tot[2], pr = tot[3], pl = tot[4];
+                const double Ft = tot[0] + C * tot[1];
+                const double pr = tot[2], pl = tot[3];
+                const double bh = lam + tot[4], bl = lam + tot[5];
                 int done = 0;
                 double next = lam;
+                int dir = 0;
                 if (Ft == 0.0) {
                     done = 1; lam_hat = lam;
                 } else if (Ft > 0.0) {
-                    L = lam; FL = Ft;
+                    L = lam; FL = Ft; dir = 1;
                     if (pr > 0.0) {
-                        double lN = lam + Ft / pr;
+                        const double lN = lam + Ft / pr;
                         if (lN <= bh) { done = 1; lam_hat = lN; }
                         else next = lN;
                     } else {
-                        next = bh;
+                        next = lam + 2.0 * (bh - lam);   // flat piece: go past its end
                     }
                 } else {
-                    U = lam; FU = Ft;
+                    U = lam; FU = Ft; dir = -1;
                     if (pl > 0.0) {
-                        double lN = lam + Ft / pl;
+                        const double lN = lam + Ft / pl;
                         if (lN >= bl) { done = 1; lam_hat = lN; }
                         else next = lN;
                     } else {
-                        next = bl;
+                        next = lam + 2.0 * (bl - lam);
                     }
                 }
                 if (!done) {
-                    if (!(next > L && next < U)) {
-                        if (isfinite(L) && isfinite(U)) {
+                    if (!isfinite(L) || !isfinite(U)) {
+                        // not bracketed yet: steps in one direction at least double
+                        double step = next - lam;
+                        if (dir == last_dir && fabs(step) < 2.0 * last_step) step = dir * 2.0 * last_step;
+                        next = lam + step;
+                        last_step = fabs(step);
+                        last_dir = dir;
+                    } else {
+                        // bracketed: Newton point if inside, else secant; every third
+                        // bracketed pass bisects, so the bracket at least halves
+                        ++nbr;
+                        if (nbr % 3 == 0) next = 0.5 * (L + U);
+                        else if (!(next > L && next < U)) {
                             next = L - FL * (U - L) / (FU - FL);
                             if (!(next > L && next < U)) next = 0.5 * (L + U);
                         }
                     }
-                    if (!(next > L && next < U) || !isfinite(next)) {
+                    if (!isfinite(next) || ((isfinite(L) && isfinite(U)) && !(next > L && next < U))) {
                         // no representable point strictly inside the bracket
                         done = 1;
                         lam_hat = (isfinite(L) && (!isfinite(U) || fabs(FL) <= fabs(FU))) ? L : U;
@@ -205,53 +284,82 @@ __global__ void __launch_bounds__(kTPB) proj_kernel(ProjArgs A)
 
     // ---------------- final phase: pi, sums, compaction ----------------
     const double lh = lam_hat;
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    unsigned isJ = 0u, isS = 0u;   // bit k: element k is in J / S
+    const float dlh = MX ? (float)(lh - lam0) : 0.f;
+    const float2 Csplit = make_float2(Cf, (float)(C - (double)Cf));
+    double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0, accu = 0.0;
+    unsigned isJ = 0u, isS = 0u;   // bit k: component k is in J / S
 #pragma unroll
     for (int k = 0; k < EPT; ++k) {
-        if (ys[k] == 0.f) continue;
-        long long i = k * NT + (long long)blk * kTPB + tid;
-        const bool pos = ys[k] > 0.f;
-        double t = pos ? (s[k] - lh) : (lh - s[k]);
-        double pk = fmin(fmax(t, 0.0), C);
-        double u = pos ? s[k] : -s[k];
-        if (t > 0.0 && t < C) isJ |= 1u << k;
+        if (!((valm >> k) & 1u)) continue;
+        const long long i = k * NT + (long long)blk * kTPB + tid;
+        const bool pos = (posm >> k) & 1u;
+        int cls = 1;   // 0 lower, 1 evaluate in FP64, 2 upper
+        if (MX) {
+            const float tf = pos ? (r[k] - dlh) : (dlh - r[k]);
+            const float er = (fabsf(r[k]) + fabsf(dlh) + Cf) * 9.5367431640625e-07f;
+            cls = (tf > Cf + er) ? 2 : ((tf < -er) ? 0 : 1);
+        }
+        double pk;
+        if (cls == 2) {
+            pk = C;
+        } else if (cls == 0) {
+            pk = 0.0;
+        } else {
+            const double t = pos ? (s[k] - lh) : (lh - s[k]);
+            pk = fmin(fmax(t, 0.0), C);
+            if (t > 0.0 && t < C) isJ |= 1u << k;
+        }
         if (pk > 0.0) isS |= 1u << k;
+        const double u = flip_sign(s[k], !pos);
         if (A.pi_out) A.pi_out[i] = pk;
-        if (A.mode == PM_MAIN) {
-            if (A.u_out) A.u_out[i] = u;
-            double al = A.alpha[i];
-            double d = pk - al;
-            acc[0] = fma(d, d, acc[0]);
-            acc[1] += pk * (2.0 * u - pk);
-        } else if (A.mode == PM_TRIAL) {
-            double ub = A.a[i], pb = A.pi_base[i];
-            acc[0] += pk * (2.0 * u - pk) - pb * (2.0 * ub - pb);
-        } else if (A.mode == PM_KKT) {
-            double al = A.a[i];
-            double d = al - pk;
-            acc[0] = fma(d, d, acc[0]);
-            acc[1] = fma(al, al, acc[1]);
-            acc[2] += al;
-            double qa = A.b[i];
-            double marg = qa + (pos ? lh : -lh);
-            acc[3] += fmax(0.0, 1.0 - marg);
+        if (A.u_out) A.u_out[i] = u;
+        if (A.wpi_out) {
+            float2 wv;
+            if (pk == C) wv = Csplit;
+            else if (pk == 0.0) wv = make_float2(0.f, 0.f);
+            else { wv.x = (float)pk; wv.y = (float)(pk - (double)wv.x); }
+            if (!pos) { wv.x = -wv.x; wv.y = -wv.y; }
+            A.wpi_out[i] = wv;
+        }
+        if (A.sums & SF_DPA) {
+            // |pi - alpha|^2: only components that moved need FP64
+            const double al = A.alpha[i];
+            if (__double_as_longlong(al) != __double_as_longlong(pk)) {
+                const double d = pk - al;
+                acc0 = fma(d, d, acc0);
+            }
+        }
+        if (A.sums & SF_PSID) {
+            // psi difference term by term: pi(2u - pi) - pib(2ub - pib)
+            const double pb = A.pi_base[i];
+            if (pk == C && pb == C) {
+                accu += u - A.a[i];                    // 2C(u - ub), factor applied below
+            } else if (pk != 0.0 || pb != 0.0) {
+                const double ub = A.a[i];
+                acc1 += pk * (2.0 * u - pk) - pb * (2.0 * ub - pb);
+            }
+        }
+        if (A.sums & SF_KKT) {
+            const double al = A.a[i];
+            const double d = al - pk;
+            acc0 = fma(d, d, acc0);
+            acc1 = fma(al, al, acc1);
+            acc2 += al;
+            const double marg = A.b[i] + (pos ? lh : -lh);
+            acc3 += fmax(0.0, 1.0 - marg);
         }
     }
+    if (A.sums & SF_PSID) acc1 = fma(2.0 * C, accu, acc1);
     // per-(k, warp) compaction counts
-    __shared__ int sh_wc[EPT > 0 ? EPT : 1][kWarps][2];
+    __shared__ int sh_wc[EPT][kWarps][2];
 #pragma unroll
     for (int k = 0; k < EPT; ++k) {
         unsigned bj = __ballot_sync(0xffffffffu, (isJ >> k) & 1u);
         unsigned bs = __ballot_sync(0xffffffffu, (isS >> k) & 1u);
         if (lane == 0) { sh_wc[k][warp][0] = __popc(bj); sh_wc[k][warp][1] = __popc(bs); }
     }
-#pragma unroll
-    for (int f = 0; f < 4; ++f) acc[f] = warp_sum(acc[f]);
-    if (lane == 0) {
-        sh_d[warp][0] = acc[0]; sh_d[warp][1] = acc[1]; sh_d[warp][2] = acc[2];
-        sh_c[warp][0] = acc[3];
-    }
+    acc0 = warp_sum(acc0); acc1 = warp_sum(acc1); acc2 = warp_sum(acc2); acc3 = warp_sum(acc3);
+    if (lane == 0) { sh_d[warp][0] = acc0; sh_d[warp][1] = acc1; sh_d[warp][2] = acc2; sh_d[warp][3] = acc3; }
     __syncthreads();
     if (tid < EPT) {
         int cj = 0, cs = 0;
@@ -261,20 +369,20 @@ __global__ void __launch_bounds__(kTPB) proj_kernel(ProjArgs A)
     }
     if (tid == 0) {
         double b0 = 0, b1 = 0, b2 = 0, b3 = 0;
-        for (int w = 0; w < kWarps; ++w) { b0 += sh_d[w][0]; b1 += sh_d[w][1]; b2 += sh_d[w][2]; b3 += sh_c[w][0]; }
+        for (int w = 0; w < kWarps; ++w) { b0 += sh_d[w][0]; b1 += sh_d[w][1]; b2 += sh_d[w][2]; b3 += sh_d[w][3]; }
         double *p = A.part + ((size_t)2 * G + blk) * kPartStride;
         p[0] = b0; p[1] = b1; p[2] = b2; p[3] = b3;
     }
     if (!alive || !grid_barrier(A.bar, A.err)) return;
 
     // offsets: off(k) = sum_{k'<k} total(k') + sum_{b'<blk} cnt(k, b')
-    __shared__ long long sh_off[EPT > 0 ? EPT : 1][2];
-    __shared__ long long sh_tot2[EPT > 0 ? EPT : 1][2];
+    __shared__ long long sh_off[EPT][2];
+    __shared__ long long sh_tot2[EPT][2];
     for (int k = warp; k < EPT; k += kWarps) {
         long long tj = 0, ts = 0, pj = 0, ps = 0;
         for (int bb = lane; bb < G; bb += 32) {
-            int cj = __ldcg(A.cnt + ((size_t)k * G + bb) * 2 + 0);
-            int cs = __ldcg(A.cnt + ((size_t)k * G + bb) * 2 + 1);
+            const int cj = __ldcg(A.cnt + ((size_t)k * G + bb) * 2 + 0);
+            const int cs = __ldcg(A.cnt + ((size_t)k * G + bb) * 2 + 1);
             tj += cj; ts += cs;
             if (bb < blk) { pj += cj; ps += cs; }
         }
@@ -286,12 +394,11 @@ __global__ void __launch_bounds__(kTPB) proj_kernel(ProjArgs A)
     if (tid == 0) {
         long long rj = 0, rs = 0;
         for (int k = 0; k < EPT; ++k) {
-            long long oj = rj + sh_off[k][0], os = rs + sh_off[k][1];
+            const long long oj = rj + sh_off[k][0], os = rs + sh_off[k][1];
             rj += sh_tot2[k][0]; rs += sh_tot2[k][1];
             sh_off[k][0] = oj; sh_off[k][1] = os;
         }
         if (blk == 0) {
-            // block 0 publishes the results
             double r0 = 0, r1 = 0, r2 = 0, r3 = 0;
             for (int bb = 0; bb < G; ++bb) {
                 const double *p = A.part + ((size_t)2 * G + bb) * kPartStride;
@@ -310,9 +417,9 @@ __global__ void __launch_bounds__(kTPB) proj_kernel(ProjArgs A)
         const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
         for (int k = 0; k < EPT; ++k) {
-            long long i = k * NT + (long long)blk * kTPB + tid;
-            unsigned bj = __ballot_sync(0xffffffffu, (isJ >> k) & 1u);
-            unsigned bs = __ballot_sync(0xffffffffu, (isS >> k) & 1u);
+            const long long i = k * NT + (long long)blk * kTPB + tid;
+            const unsigned bj = __ballot_sync(0xffffffffu, (isJ >> k) & 1u);
+            const unsigned bs = __ballot_sync(0xffffffffu, (isS >> k) & 1u);
             int wj = 0, ws = 0;
             for (int w = 0; w < warp; ++w) { wj += sh_wc[k][w][0]; ws += sh_wc[k][w][1]; }
             if (A.J && ((isJ >> k) & 1u)) A.J[sh_off[k][0] + wj + __popc(bj & lt)] = (int32_t)i;
@@ -321,35 +428,36 @@ __global__ void __launch_bounds__(kTPB) proj_kernel(ProjArgs A)
     }
 }
 
-template <int EPT>
-static void *kfun() { return (void *)proj_kernel<EPT>; }
-
 static const int kEpts[] = {1, 2, 4, 8, 16, 32};
 
+template <bool MX>
 static void *kernel_for(int ept)
 {
     switch (ept) {
-    case 1: return kfun<1>();
-    case 2: return kfun<2>();
-    case 4: return kfun<4>();
-    case 8: return kfun<8>();
-    case 16: return kfun<16>();
-    default: return kfun<32>();
+    case 1: return (void *)proj_kernel<1, MX>;
+    case 2: return (void *)proj_kernel<2, MX>;
+    case 4: return (void *)proj_kernel<4, MX>;
+    case 8: return (void *)proj_kernel<8, MX>;
+    case 16: return (void *)proj_kernel<16, MX>;
+    default: return (void *)proj_kernel<32, MX>;
     }
 }
 
 cudaError_t proj_setup(Work &W)
 {
-    // Largest co-resident grid for each instantiation; pick the smallest EPT
-    // whose grid covers n.
-    long long n = W.n;
+    // Largest co-resident grid for each instantiation (both precisions); pick
+    // the smallest EPT whose grid covers n.
+    const long long n = W.n;
     for (int ept : kEpts) {
-        int occ = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel_for(ept), kTPB, 0);
+        int occ0 = 0, occ1 = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ0, kernel_for<false>(ept), kTPB, 0);
         if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, kernel_for<true>(ept), kTPB, 0);
+        if (e != cudaSuccess) return e;
+        const int occ = occ0 < occ1 ? occ0 : occ1;
         if (occ < 1) continue;
-        long long gmax = (long long)occ * W.nsm;
-        long long need = (n + (long long)kTPB * ept - 1) / ((long long)kTPB * ept);
+        const long long gmax = (long long)occ * W.nsm;
+        const long long need = (n + (long long)kTPB * ept - 1) / ((long long)kTPB * ept);
         if (need <= gmax) {
             W.proj_grid = (int)(need < 1 ? 1 : need);
             W.proj_ept = ept;
@@ -362,15 +470,15 @@ cudaError_t proj_setup(Work &W)
 cudaError_t launch_project(Work &W, const ProjIn &in, ProjOut *out)
 {
     ProjArgs A;
-    A.a = in.a; A.b = in.b; A.c0 = in.c0; A.c1 = in.c1; A.c2 = in.c2;
-    A.y = W.y; A.n = W.n; A.C = W.C; A.mode = in.mode; A.lam0 = in.lam0;
-    A.u_out = in.u_out; A.pi_out = in.pi_out; A.J = in.J; A.S = in.S;
+    A.a = in.a; A.b = in.b; A.c1 = in.c1; A.c2 = in.c2;
+    A.y = W.y; A.n = W.n; A.C = W.C; A.sums = in.sums; A.lam0 = in.lam0;
+    A.u_out = in.u_out; A.pi_out = in.pi_out; A.wpi_out = in.wpi_out; A.J = in.J; A.S = in.S;
     A.pi_base = in.pi_base; A.alpha = in.alpha;
     A.part = W.part; A.cnt = W.cnt; A.bar = W.bar; A.err = W.err; A.out = out;
     void *args[] = {&A};
     ++W.nlaunch;
-    return cudaLaunchCooperativeKernel(kernel_for(W.proj_ept), dim3(W.proj_grid), dim3(kTPB), args, 0,
-                                       W.st);
+    void *fn = W.precision == 1 ? kernel_for<true>(W.proj_ept) : kernel_for<false>(W.proj_ept);
+    return cudaLaunchCooperativeKernel(fn, dim3(W.proj_grid), dim3(kTPB), args, 0, W.st);
 }
 
 }  // namespace svm

@@ -27,6 +27,7 @@
 
 #include <new>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/svm_ssnalm.h"
@@ -136,10 +137,15 @@ extern "C" const char *svm_ssnalm_last_error(const svm_ssnalm_t *h)
 
 static void free_work(Work &W)
 {
-    void *ptrs[] = {W.alpha, W.z, W.dz, W.u, W.pi, W.qa, W.tmpn, W.J, W.S, W.v, W.dv, W.g, W.atp,
-                    W.h, W.w, W.tmpq, W.M, W.part, W.cnt, W.bar, W.err, W.pout, W.red, W.X_own, W.y_own};
+    void *ptrs[] = {W.alpha, W.z, W.dz, W.qa, W.tmpn, W.v, W.dv, W.g, W.atp, W.atp2, W.h, W.w, W.tmpq, W.M,
+                    W.part, W.cnt, W.bar, W.err, W.pout, W.red, W.X_own, W.y_own};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    for (int b = 0; b < 2; ++b) {
+        void *pp[] = {W.pb[b].u, W.pb[b].pi, W.pb[b].wpi, W.pb[b].J, W.pb[b].S};
+        for (void *p : pp)
+            if (p) cudaFree(p);
+    }
     if (W.h_pout) cudaFreeHost(W.h_pout);
     if (W.h_red) cudaFreeHost(W.h_red);
     if (W.h_err) cudaFreeHost(W.h_err);
@@ -196,6 +202,7 @@ extern "C" svm_status svm_ssnalm_create(svm_ssnalm_t **out, const svm_problem *p
     if (out) *out = nullptr;
     if (!out || !prob || !params) { g_create_err = "null argument"; return SVM_ERR_INVALID_ARG; }
     if (prob->n < 1 || prob->q < 1) { g_create_err = "n and q must be >= 1"; return SVM_ERR_INVALID_ARG; }
+    if (prob->n > 0x7fffffffLL) { g_create_err = "n must fit in int32"; return SVM_ERR_UNSUPPORTED; }
     if (!(params->C > 0.0) || !isfinite(params->C)) { g_create_err = "C must be finite and > 0"; return SVM_ERR_INVALID_ARG; }
     if (!(params->tol > 0.0)) { g_create_err = "tol must be > 0"; return SVM_ERR_INVALID_ARG; }
     if (!prob->X || !prob->y) { g_create_err = "X and y must be non-null"; return SVM_ERR_INVALID_ARG; }
@@ -243,22 +250,23 @@ extern "C" svm_status svm_ssnalm_create(svm_ssnalm_t **out, const svm_problem *p
     if ((uintptr_t)W.X % 16 != 0) return fail(SVM_ERR_INVALID_ARG, "X must be 16-byte aligned");
     // workspace
     W.rm_grid = W.nsm * 4;
-    const int ntile = (int)((q + 31) / 32);
     // Gram split-K partials: at most 32 MiB (at least one q x q partial)
     size_t part_gram = (size_t)(4 * W.nsm) * (q * q + q);
     const size_t gram_cap = ((size_t)32 << 20) / sizeof(double);
     if (part_gram > gram_cap) part_gram = gram_cap > (q * q + q) ? gram_cap : (q * q + q);
-    size_t part_rm = (size_t)2 * W.rm_grid * q;
-    size_t part_proj = (size_t)3 * 8 * 4 * W.nsm * 4;   // generous: 3 slots x grid x stride
+    const size_t part_rm = (size_t)2 * W.rm_grid * q;
+    const size_t part_proj = (size_t)3 * 8 * 4 * W.nsm * 4;
     W.part_len = part_gram > part_rm ? part_gram : part_rm;
     if (W.part_len < part_proj) W.part_len = part_proj;
-    (void)ntile;
-    if (dalloc(&W.alpha, n) || dalloc(&W.z, n) || dalloc(&W.dz, n) || dalloc(&W.u, n) || dalloc(&W.pi, n) ||
-        dalloc(&W.qa, n) || dalloc(&W.tmpn, n) || dalloc(&W.J, n) || dalloc(&W.S, n) || dalloc(&W.v, q) ||
-        dalloc(&W.dv, q) || dalloc(&W.g, q) || dalloc(&W.atp, q) || dalloc(&W.h, q) || dalloc(&W.w, q) ||
-        dalloc(&W.tmpq, q) || dalloc(&W.M, q * q) || dalloc(&W.part, W.part_len) || dalloc(&W.bar, 4) ||
-        dalloc(&W.err, 4) || dalloc(&W.pout, 4) || dalloc(&W.red, 16))
-        return fail(SVM_ERR_OOM, "device workspace allocation failed");
+    bool bad = dalloc(&W.alpha, n) || dalloc(&W.z, n) || dalloc(&W.dz, n) || dalloc(&W.qa, n) ||
+               dalloc(&W.tmpn, n) || dalloc(&W.v, q) || dalloc(&W.dv, q) || dalloc(&W.g, q) ||
+               dalloc(&W.atp, q) || dalloc(&W.atp2, q) || dalloc(&W.h, q) || dalloc(&W.w, q) || dalloc(&W.tmpq, q) ||
+               dalloc(&W.M, q * q) || dalloc(&W.part, W.part_len) || dalloc(&W.bar, 4) || dalloc(&W.err, 4) ||
+               dalloc(&W.pout, 4) || dalloc(&W.red, 16);
+    for (int b = 0; b < 2 && !bad; ++b)
+        bad = dalloc(&W.pb[b].u, n) || dalloc(&W.pb[b].pi, n) || dalloc(&W.pb[b].wpi, n) ||
+              dalloc(&W.pb[b].J, n) || dalloc(&W.pb[b].S, n);
+    if (bad) return fail(SVM_ERR_OOM, "device workspace allocation failed");
     if (cudaMallocHost(&W.h_pout, 4 * sizeof(ProjOut)) != cudaSuccess ||
         cudaMallocHost(&W.h_red, 16 * sizeof(double)) != cudaSuccess ||
         cudaMallocHost(&W.h_err, 4 * sizeof(int)) != cudaSuccess)
@@ -283,7 +291,6 @@ extern "C" svm_status svm_ssnalm_create(svm_ssnalm_t **out, const svm_problem *p
     if (e != cudaSuccess) return fail(SVM_ERR_CUDA, std::string("create: ") + cudaGetErrorString(e));
     if (hchk[0]) return fail(SVM_ERR_INVALID_ARG, "labels must be +1 or -1");
     if (hchk[2]) return fail(SVM_ERR_INVALID_ARG, "X has non-finite entries");
-    h->lam_main = 0.0;
     h->npos = hchk[1];
     *out = h;
     return SVM_OK;
@@ -300,7 +307,7 @@ static svm_status sync_read(svm_ssnalm *h)
     CK(cudaStreamSynchronize(W.st));
     h->syncs++;
     if (h->timing) flush_timing(h);
-    int e = W.h_err[0];
+    const int e = W.h_err[0];
     if (e) {
         cudaMemsetAsync(W.err, 0, sizeof(int), W.st);
         cudaMemsetAsync(W.bar, 0, sizeof(unsigned), W.st);
@@ -313,18 +320,18 @@ static svm_status sync_read(svm_ssnalm *h)
     return SVM_OK;
 }
 
-// R_KKT(alpha) (eq. (4.1)); leaves A'alpha in W.w, Q alpha in W.qa, and the
-// projection results in pout[PM_KKT].  idx/cnt: support of alpha (nullable).
-static svm_status kkt_launch(svm_ssnalm *h, const double *alpha, const int32_t *idx, const long long *cnt)
+// ProjOut slots: 0 step-level op, 1 + b for projection buffer b, 3 KKT.
+enum { SLOT_OP = 0, SLOT_KKT = 3 };
+
+// The KKT projection of eq. (4.1) at alpha given Q alpha in W.qa.
+static svm_status kkt_project(svm_ssnalm *h, const double *alpha)
 {
     Work &W = h->W;
-    CK(timed(h, TK_RMATVEC, [&] { return launch_rmatvec(W, alpha, idx, cnt, W.w, -1); }));
-    CK(timed(h, TK_MATVEC, [&] { return launch_matvec(W, W.w, W.qa); }));
-    ProjIn in{};
-    in.a = alpha; in.b = W.qa; in.c0 = 1.0; in.c1 = -1.0; in.c2 = 1.0;
-    in.mode = PM_KKT;
-    in.lam0 = &W.pout[PM_KKT].lam;
-    CK(timed(h, TK_PROJ, [&] { return launch_project(W, in, &W.pout[PM_KKT]); }));
+    ProjIn in;
+    in.a = alpha; in.b = W.qa; in.c1 = -1.0; in.c2 = 1.0;
+    in.sums = SF_KKT;
+    in.lam0 = &W.pout[SLOT_KKT].lam;
+    CK(timed(h, TK_PROJ, [&] { return launch_project(W, in, &W.pout[SLOT_KKT]); }));
     return SVM_OK;
 }
 
@@ -344,7 +351,7 @@ __global__ void count_kernel(long long n, const double *a, double C, double *red
 {
     unsigned long long f = 0, u = 0, s = 0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        double v = a[i];
+        const double v = a[i];
         f += (v > 0.0 && v < C);
         u += (v >= C);
         s += (v > 0.0);
@@ -361,6 +368,32 @@ __global__ void count_kernel(long long n, const double *a, double C, double *red
     }
 }
 
+// g = (v + t dv) - atp, red[0] = |g|^2 (the gradient at the trial point)
+__global__ void grad_at_kernel(int q, const double *v, const double *dv, double t, const double *atp, double *g,
+                               double *red)
+{
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (int j = threadIdx.x; j < q; j += blockDim.x) {
+        const double gj = fma(t, dv[j], v[j]) - atp[j];
+        g[j] = gj;
+        s = fma(gj, gj, s);
+    }
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r += sh[w];
+        red[0] = r;
+    }
+}
+
+__global__ void copyq_kernel(int q, const double *a, double *b)
+{
+    for (int j = threadIdx.x; j < q; j += blockDim.x) b[j] = a[j];
+}
+
 // ------------------------------------------------------------ solve
 
 extern "C" svm_status svm_ssnalm_solve(svm_ssnalm_t *h, const double *alpha0, svm_result *res)
@@ -372,6 +405,7 @@ extern "C" svm_status svm_ssnalm_solve(svm_ssnalm_t *h, const double *alpha0, sv
     const bool host_mem = h->prob.memory == SVM_MEM_HOST;
     const long long n = W.n;
     const int q = (int)W.q;
+    const int nblk_n = (int)((n + 1023) / 1024 < W.nsm * 4 ? (n + 1023) / 1024 : W.nsm * 4);
     svm_status st;
     h->err.clear();
 
@@ -391,106 +425,148 @@ extern "C" svm_status svm_ssnalm_solve(svm_ssnalm_t *h, const double *alpha0, sv
         return SVM_ERR_DEGENERATE;
     }
 
-    // start point: alpha^0 = Pi(alpha0) (or 0), v = A'alpha^0 (w^0 = 0 when cold, Sec. 4.1)
-    bool have_support = false;
+    // lambda warm starts restart at 0
+    CK(cudaMemsetAsync(W.pout, 0, 4 * sizeof(ProjOut), W.st));
+    int cur = 0;   // projection buffer holding pi(u(v)) at the current point
+
+    // start point: alpha^0 = Pi(alpha0) (or 0); the ALM dual starts at v = A'alpha^0
+    // (w^0 = 0 when cold, Sec. 4.1)
     if (alpha0) {
         cudaMemcpyKind k = host_mem ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
         CK(cudaMemcpyAsync(W.tmpn, alpha0, n * sizeof(double), k, W.st));
-        ProjIn in{};
-        in.a = W.tmpn; in.b = nullptr; in.c0 = 1.0; in.c2 = 0.0; in.mode = PM_OP;
-        in.pi_out = W.alpha; in.S = W.S;
-        CK(timed(h, TK_PROJ, [&] { return launch_project(W, in, &W.pout[PM_OP]); }));
-        CK(timed(h, TK_RMATVEC, [&] { return launch_rmatvec(W, W.alpha, W.S, &W.pout[PM_OP].s, W.v, -1); }));
-        have_support = true;
+        ProjIn in;
+        in.a = W.tmpn; in.pi_out = W.alpha; in.S = W.pb[0].S; in.wpi_out = W.pb[0].wpi;
+        CK(timed(h, TK_PROJ, [&] { return launch_project(W, in, &W.pout[SLOT_OP]); }));
+        CK(timed(h, TK_RMATVEC, [&] {
+            return launch_rmatvec(W, W.alpha, W.pb[0].wpi, W.pb[0].S, &W.pout[SLOT_OP].s, W.v, -1);
+        }));
+        copyq_kernel<<<1, 1024, 0, W.st>>>(q, W.v, W.w);
+        ++W.nlaunch;
+        CK(cudaGetLastError());
+        // Q alpha = A w and z = A v (equal here) in one pass
+        CK(timed(h, TK_MATVEC, [&] { return launch_matvec(W, W.w, W.qa, W.v, W.z); }));
+        CK(cudaMemsetAsync(W.pout, 0, sizeof(ProjOut), W.st));
     } else {
         CK(cudaMemsetAsync(W.alpha, 0, n * sizeof(double), W.st));
         CK(cudaMemsetAsync(W.v, 0, q * sizeof(double), W.st));
+        CK(cudaMemsetAsync(W.w, 0, q * sizeof(double), W.st));
+        CK(cudaMemsetAsync(W.qa, 0, n * sizeof(double), W.st));
+        CK(cudaMemsetAsync(W.z, 0, n * sizeof(double), W.st));
     }
-    // lambda warm starts of the main, trial and KKT projections restart at 0
-    CK(cudaMemsetAsync(W.pout + PM_MAIN, 0, 3 * sizeof(ProjOut), W.st));
     double sigma = P.sigma0;
-    // R_KKT at the start
-    if ((st = kkt_launch(h, W.alpha, have_support ? W.S : nullptr, have_support ? &W.pout[PM_OP].s : nullptr)) != SVM_OK)
-        return st;
+    if ((st = kkt_project(h, W.alpha)) != SVM_OK) return st;
     if ((st = sync_read(h)) != SVM_OK) return st;
-    double R = kkt_value(W.h_pout[PM_KKT]), Rprev = R;
+    double R = kkt_value(W.h_pout[SLOT_KKT]), Rprev = R;
     svm_status status = SVM_ERR_NOT_CONVERGED;
     int k = 0, inner_total = 0;
     if (R <= P.tol) status = SVM_OK;
     for (k = 0; k < P.max_outer && status != SVM_OK; ++k) {
         const double epsk = 0.1 * pow(0.5, (double)k);
-        CK(timed(h, TK_MATVEC, [&] { return launch_matvec(W, W.v, W.z); }));   // z = A v = Q w
-        int j = 0;
-        bool ls_fail = false;
-        for (j = 0;; ++j) {
-            // u = alpha^k - sigma (z - e); pi = Pi(u); J, S
-            ProjIn in{};
-            in.a = W.alpha; in.b = W.z; in.c0 = 1.0; in.c1 = -sigma; in.c2 = sigma;
-            in.mode = PM_MAIN; in.lam0 = &W.pout[PM_MAIN].lam;
-            in.u_out = W.u; in.pi_out = W.pi; in.J = W.J; in.S = W.S; in.alpha = W.alpha;
-            CK(timed(h, TK_PROJ, [&] { return launch_project(W, in, &W.pout[PM_MAIN]); }));
+        // z = A v holds here (from the start or from the fused product below).
+        // u = alpha^k - sigma (z - e); pi = Pi(u); J, S   (eq. (3.3))
+        {
+            ProjBuf &B = W.pb[cur];
+            ProjIn in;
+            in.a = W.alpha; in.b = W.z; in.c1 = -sigma; in.c2 = sigma;
+            in.sums = SF_DPA; in.alpha = W.alpha;
+            in.lam0 = &W.pout[1 + cur].lam;
+            in.u_out = B.u; in.pi_out = B.pi; in.wpi_out = B.wpi; in.J = B.J; in.S = B.S;
+            CK(timed(h, TK_PROJ, [&] { return launch_project(W, in, &W.pout[1 + cur]); }));
             // g = v - A'pi (eq. (3.10) in q coordinates) and its roundoff scale
-            CK(timed(h, TK_RMATVEC, [&] { return launch_rmatvec(W, W.pi, W.S, &W.pout[PM_MAIN].s, W.atp, 1); }));
+            CK(timed(h, TK_RMATVEC, [&] {
+                return launch_rmatvec(W, B.pi, B.wpi, B.S, &W.pout[1 + cur].s, W.atp, 1);
+            }));
             CK(launch_grad(W));
             if ((st = sync_read(h)) != SVM_OK) return st;
-            const ProjOut &m = W.h_pout[PM_MAIN];
-            double gn = sqrt(W.h_red[0]);
-            double dx = sqrt(m.sum[0]);
-            double tol_in = fmin(epsk, epsk * dx) / sqrt(sigma);
-            double floor_g = 1e-15 * sqrt(W.h_red[1]);
+        }
+        int j = 0;
+        for (j = 0;; ++j) {
+            const ProjOut &m = W.h_pout[1 + cur];
+            const double gn = sqrt(W.h_red[0]);
+            const double dx = sqrt(m.sum[0]);
+            const double tol_in = fmin(epsk, epsk * dx) / sqrt(sigma);
+            const double floor_g = 1e-15 * sqrt(W.h_red[1]);
             if (!isfinite(gn)) { h->err = "non-finite gradient"; return SVM_ERR_NUMERIC; }
-            if (gn <= fmax(tol_in, floor_g) || j >= P.max_inner || ls_fail) break;
-            // Newton direction on the free set J
-            CK(timed(h, TK_NEWTON, [&] { return launch_newton(W, W.J, m.p, &W.pout[PM_MAIN].p, sigma, W.g, W.dv); }));
+            if (gn <= fmax(tol_in, floor_g) || j >= P.max_inner) break;
+            // Algorithm 3, Step 1: Newton direction on the free set J
+            const long long p = m.p;
+            CK(timed(h, TK_NEWTON, [&] { return launch_newton(W, W.pb[cur].J, p, &W.pout[1 + cur].p, sigma, W.g, W.dv); }));
             CK(timed(h, TK_MATVEC, [&] { return launch_matvec(W, W.dv, W.dz); }));   // A dv = Q d
             CK(launch_dots(W));
-            if ((st = sync_read(h)) != SVM_OK) return st;
-            const double slope = W.h_red[2], vdv = W.h_red[3], dvdv = W.h_red[4];
+            // Step 2: Armijo line search.  Each trial projects u - t sigma A dv into the
+            // other buffer and, speculatively, forms the gradient there, so an accepted
+            // trial is the next iterate's projection and gradient at no extra pass.
             double t = 1.0;
             bool accepted = false;
+            const int nxt = 1 - cur;
             for (int mtr = 0; mtr < P.max_ls; ++mtr) {
-                ProjIn tr{};
-                tr.a = W.u; tr.b = W.dz; tr.c0 = 1.0; tr.c1 = -t * sigma; tr.c2 = 0.0;
-                tr.mode = PM_TRIAL; tr.lam0 = &W.pout[PM_MAIN].lam; tr.pi_base = W.pi;
-                CK(timed(h, TK_PROJ, [&] { return launch_project(W, tr, &W.pout[PM_TRIAL]); }));
+                ProjBuf &B = W.pb[nxt];
+                ProjIn tr;
+                tr.a = W.pb[cur].u; tr.b = W.dz; tr.c1 = -t * sigma; tr.c2 = 0.0;
+                tr.sums = SF_PSID | SF_DPA; tr.alpha = W.alpha; tr.pi_base = W.pb[cur].pi;
+                tr.lam0 = &W.pout[1 + cur].lam;
+                tr.u_out = B.u; tr.pi_out = B.pi; tr.wpi_out = B.wpi; tr.J = B.J; tr.S = B.S;
+                CK(timed(h, TK_PROJ, [&] { return launch_project(W, tr, &W.pout[1 + nxt]); }));
+                CK(timed(h, TK_RMATVEC, [&] {
+                    return launch_rmatvec(W, B.pi, B.wpi, B.S, &W.pout[1 + nxt].s, W.atp2, 1);
+                }));
+                grad_at_kernel<<<1, 1024, 0, W.st>>>(q, W.v, W.dv, t, W.atp2, W.tmpq, W.red);
+                ++W.nlaunch;
+                CK(cudaGetLastError());
                 if ((st = sync_read(h)) != SVM_OK) return st;
-                double dpsi = t * vdv + 0.5 * t * t * dvdv + W.h_pout[PM_TRIAL].sum[0] / (2.0 * sigma);
+                const double slope = W.h_red[2], vdv = W.h_red[3], dvdv = W.h_red[4];
+                const double dpsi = t * vdv + 0.5 * t * t * dvdv + W.h_pout[1 + nxt].sum[1] / (2.0 * sigma);
                 if (dpsi <= P.mu * t * slope) { accepted = true; break; }
                 t *= P.delta;
             }
-            if (!accepted) { ls_fail = true; continue; }
+            if (!accepted) break;   // line search failed: the subproblem ends at the current point
+            // Step 3
             CK(launch_vaxpy(W, t));
             CK(launch_zaxpy(W, t));
-        }
-        inner_total += j;
-        // alpha^{k+1} = Pi(u(w^{k+1}))  (eq. (3.5))
-        {
-            int blocks = (int)((n + 1023) / 1024);
-            if (blocks > W.nsm * 4) blocks = W.nsm * 4;
-            copy_kernel<<<blocks, 1024, 0, W.st>>>(n, W.pi, W.alpha);
+            copyq_kernel<<<1, 1024, 0, W.st>>>(q, W.tmpq, W.g);
             ++W.nlaunch;
             CK(cudaGetLastError());
+            std::swap(W.atp, W.atp2);   // A'pi of the accepted trial
+            cur = nxt;
         }
-        if ((st = kkt_launch(h, W.alpha, W.S, &W.pout[PM_MAIN].s)) != SVM_OK) return st;
+        inner_total += j;
+        // alpha^{k+1} = Pi(u(w^{k+1}))  (eq. (3.5)); A'alpha^{k+1} is the last A'pi
+        copy_kernel<<<nblk_n, 1024, 0, W.st>>>(n, W.pb[cur].pi, W.alpha);
+        copyq_kernel<<<1, 1024, 0, W.st>>>(q, W.atp, W.w);
+        W.nlaunch += 2;
+        CK(cudaGetLastError());
+        // Q alpha = A w for the KKT test and z = A v for the next subproblem, one pass
+        CK(timed(h, TK_MATVEC, [&] { return launch_matvec(W, W.w, W.qa, W.v, W.z); }));
+        if ((st = kkt_project(h, W.alpha)) != SVM_OK) return st;
         if ((st = sync_read(h)) != SVM_OK) return st;
-        R = kkt_value(W.h_pout[PM_KKT]);
+        R = kkt_value(W.h_pout[SLOT_KKT]);
         if (!isfinite(R)) { status = SVM_ERR_NUMERIC; h->err = "non-finite KKT residual"; break; }
         if (R <= P.tol) { status = SVM_OK; ++k; break; }
         if (R > 0.5 * Rprev) sigma = fmin(P.sigma_max, P.sigma_growth * sigma);
         Rprev = R;
     }
-    // results: alpha, w = A'alpha (from the last KKT evaluation), b = lambda of
-    // the KKT projection, objective, primal objective, gap, counts
-    const ProjOut &kk = W.h_pout[PM_KKT];
+    // results: alpha, w = A'alpha, b = lambda of the KKT projection, objective,
+    // primal objective, gap, counts
+    const ProjOut &kk = W.h_pout[SLOT_KKT];
     {
         cudaMemcpyKind kd = host_mem ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
         CK(cudaMemcpyAsync(res->alpha, W.alpha, n * sizeof(double), kd, W.st));
         CK(cudaMemcpyAsync(res->w, W.w, q * sizeof(double), kd, W.st));
+        CK(cudaMemsetAsync(W.red + 8, 0, 3 * sizeof(double), W.st));
+        count_kernel<<<W.nsm * 2, 256, 0, W.st>>>(n, W.alpha, W.C, W.red + 8);
+        ++W.nlaunch;
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(W.tmpq, W.w, q * sizeof(double), cudaMemcpyDeviceToDevice, W.st));
         double *hw = (double *)malloc(q * sizeof(double));
         if (!hw) { h->err = "host allocation failed"; return SVM_ERR_OOM; }
         cudaError_t e1 = cudaMemcpyAsync(hw, W.w, q * sizeof(double), cudaMemcpyDeviceToHost, W.st);
-        cudaError_t e2 = cudaStreamSynchronize(W.st);
-        if (e1 != cudaSuccess || e2 != cudaSuccess) { free(hw); h->err = "result copy failed"; return SVM_ERR_CUDA; }
+        cudaError_t e2 = cudaMemcpyAsync(W.h_red, W.red, 16 * sizeof(double), cudaMemcpyDeviceToHost, W.st);
+        cudaError_t e3 = cudaStreamSynchronize(W.st);
+        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+            free(hw);
+            h->err = "result copy failed";
+            return SVM_ERR_CUDA;
+        }
         double wsq = 0.0;
         for (int jj = 0; jj < q; ++jj) wsq += hw[jj] * hw[jj];
         free(hw);
@@ -503,18 +579,11 @@ extern "C" svm_status svm_ssnalm_solve(svm_ssnalm_t *h, const double *alpha0, sv
         res->outer_iters = k;
         res->inner_iters_total = inner_total;
         res->status = status;
-    }
-    // counts of free / upper / support entries
-    {
-        CK(cudaMemsetAsync(W.red + 8, 0, 3 * sizeof(double), W.st));
-        count_kernel<<<W.nsm * 2, 256, 0, W.st>>>(n, W.alpha, W.C, W.red + 8);
-        ++W.nlaunch;
-        CK(cudaGetLastError());
-        if ((st = sync_read(h)) != SVM_OK) return st;
         res->n_free = (int64_t)W.h_red[8];
         res->n_upper = (int64_t)W.h_red[9];
         res->n_sv = (int64_t)W.h_red[10];
     }
+    if (h->timing) flush_timing(h);
     if (status != SVM_OK && h->err.empty()) h->err = "iteration cap reached";
     return status;
 }
@@ -532,8 +601,15 @@ extern "C" svm_status svm_op_matvec(svm_ssnalm_t *h, const double *v, double *z)
 extern "C" svm_status svm_op_rmatvec(svm_ssnalm_t *h, const double *c, double *out)
 {
     if (!h || !c || !out) return SVM_ERR_INVALID_ARG;
-    CK(timed(h, TK_RMATVEC, [&] { return launch_rmatvec(h->W, c, nullptr, nullptr, out, -1); }));
-    CK(cudaStreamSynchronize(h->W.st));
+    Work &W = h->W;
+    // the mixed form reads y_i c_i as FP32 (hi, lo) pairs: split them here
+    const float2 *wc = nullptr;
+    if (W.precision == SVM_PREC_MIXED && W.xf32) {
+        split_weights(W, c, W.pb[0].wpi);
+        wc = W.pb[0].wpi;
+    }
+    CK(timed(h, TK_RMATVEC, [&] { return launch_rmatvec(W, c, wc, nullptr, nullptr, out, -1); }));
+    CK(cudaStreamSynchronize(W.st));
     return SVM_OK;
 }
 
@@ -542,15 +618,14 @@ extern "C" svm_status svm_op_project(svm_ssnalm_t *h, const double *u, double *p
 {
     if (!h || !u || !pi) return SVM_ERR_INVALID_ARG;
     Work &W = h->W;
-    ProjIn in{};
-    in.a = u; in.b = nullptr; in.c0 = 1.0; in.c2 = 0.0; in.mode = PM_OP;
-    in.lam0 = nullptr; in.pi_out = pi; in.J = J; in.S = S;
-    CK(timed(h, TK_PROJ, [&] { return launch_project(W, in, &W.pout[PM_OP]); }));
+    ProjIn in;
+    in.a = u; in.pi_out = pi; in.J = J; in.S = S;
+    CK(timed(h, TK_PROJ, [&] { return launch_project(W, in, &W.pout[SLOT_OP]); }));
     svm_status st = sync_read(h);
     if (st != SVM_OK) return st;
-    if (lambda) *lambda = W.h_pout[PM_OP].lam;
-    if (p_out) *p_out = W.h_pout[PM_OP].p;
-    if (s_out) *s_out = W.h_pout[PM_OP].s;
+    if (lambda) *lambda = W.h_pout[SLOT_OP].lam;
+    if (p_out) *p_out = W.h_pout[SLOT_OP].p;
+    if (s_out) *s_out = W.h_pout[SLOT_OP].s;
     return SVM_OK;
 }
 
@@ -566,15 +641,21 @@ extern "C" svm_status svm_op_newton(svm_ssnalm_t *h, const int32_t *J, int64_t p
 extern "C" svm_status svm_op_kkt(svm_ssnalm_t *h, const double *alpha, double *kkt, double *lambda)
 {
     if (!h || !alpha) return SVM_ERR_INVALID_ARG;
-    svm_status st = kkt_launch(h, alpha, nullptr, nullptr);
+    Work &W = h->W;
+    const float2 *wc = nullptr;
+    if (W.precision == SVM_PREC_MIXED && W.xf32) {
+        split_weights(W, alpha, W.pb[0].wpi);
+        wc = W.pb[0].wpi;
+    }
+    CK(timed(h, TK_RMATVEC, [&] { return launch_rmatvec(W, alpha, wc, nullptr, nullptr, W.w, -1); }));
+    CK(timed(h, TK_MATVEC, [&] { return launch_matvec(W, W.w, W.qa); }));
+    svm_status st = kkt_project(h, alpha);
     if (st != SVM_OK) return st;
     if ((st = sync_read(h)) != SVM_OK) return st;
-    if (kkt) *kkt = kkt_value(h->W.h_pout[PM_KKT]);
-    if (lambda) *lambda = h->W.h_pout[PM_KKT].lam;
+    if (kkt) *kkt = kkt_value(W.h_pout[SLOT_KKT]);
+    if (lambda) *lambda = W.h_pout[SLOT_KKT].lam;
     return SVM_OK;
 }
-
-// ------------------------------------------------------------ instrumentation
 
 extern "C" svm_status svm_ssnalm_set_timing(svm_ssnalm_t *h, int enable)
 {
