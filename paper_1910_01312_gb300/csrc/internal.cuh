@@ -65,11 +65,16 @@ struct Work {
     double *v = nullptr, *dv = nullptr, *g = nullptr, *atp = nullptr, *atp2 = nullptr, *h = nullptr,
            *w = nullptr, *tmpq = nullptr;
     double *M = nullptr;      // q*q Newton matrix / Cholesky factor
+    float *Lf = nullptr;      // q*(q+1) FP32 factor when it does not fit in shared memory
+    float2 *Mf = nullptr;     // q*q FP32 (hi, lo) split of M (double-float CG operator)
+    double eta = 0.1, tau = 0.5;   // inexact-Newton constants of Algorithm 3
+    int cg_maxit = 50;
     double *part = nullptr;   // partial sums (size part_len doubles)
     size_t part_len = 0;
     int *cnt = nullptr;       // compaction counts
     size_t cnt_len = 0;
     unsigned *bar = nullptr;  // grid-barrier counter
+    unsigned *rm_counter = nullptr;   // last-block counter of the mixed A'c
     int *err = nullptr;       // device error flag
     ProjOut *pout = nullptr;  // 4 slots indexed by ProjMode
     double *red = nullptr;    // 16 small reductions

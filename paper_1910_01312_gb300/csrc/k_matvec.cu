@@ -317,15 +317,61 @@ __global__ void __launch_bounds__(256) rmatvec_part_kernel(const TX *__restrict_
     }
 }
 
+// Fixed-order final reduction of G block partials, run by one block whose
+// size is a multiple of 128: columns in rounds of 128, blockDim/128 interleaved
+// sub-sums per column, combined in order.  out_j = sum_b part[b][j];
+// red[slot] = sum_j (sum_b apart[b][j])^2 when slot >= 0.
+__device__ void final_reduce(int G, int q, const double *__restrict__ part, const double *__restrict__ apart,
+                             double *__restrict__ out, double *__restrict__ red, int slot, double *sm)
+{
+    const int subs = blockDim.x >> 7;
+    const int tx = threadIdx.x & 127, sub = threadIdx.x >> 7;
+    double *sp = sm, *sa = sm + subs * 128, *sq = sa + subs * 128;
+    double scale = 0.0;
+    for (int c0 = 0; c0 < q; c0 += 128) {
+        const int col = c0 + tx;
+        double s = 0.0, a = 0.0;
+        if (col < q) {
+#pragma unroll 4
+            for (int b = sub; b < G; b += subs) {
+                s += __ldcg(part + (size_t)b * q + col);
+                a += __ldcg(apart + (size_t)b * q + col);
+            }
+        }
+        sp[sub * 128 + tx] = s;
+        sa[sub * 128 + tx] = a;
+        __syncthreads();
+        if (sub == 0 && col < q) {
+            double ts = 0.0, ta = 0.0;
+            for (int k = 0; k < subs; ++k) { ts += sp[k * 128 + tx]; ta += sa[k * 128 + tx]; }
+            out[col] = ts;
+            scale = fma(ta, ta, scale);
+        }
+        __syncthreads();
+    }
+    if (sub == 0) sq[tx] = scale;
+    __syncthreads();
+    if (threadIdx.x == 0 && slot >= 0) {
+        double t = 0.0;
+        for (int k = 0; k < 128; ++k) t += sq[k];
+        red[slot] = t;
+    }
+}
+
 // Mixed form.  Weights arrive as y_i c_i in FP32 (hi, lo) pairs; VW = 4:
 // lane l owns the float4 column chunks l + 32k (q % 4 == 0), VW = 1: the
-// scalar columns l + 32k.  Four rows are in flight per warp.
+// scalar columns l + 32k.  Rows are in flight R at a time per warp.  The
+// block's warps are combined by a tree over shared memory, and the block
+// that finishes last (threadfence + counter) performs the fixed-order final
+// reduction over all block partials, so one launch yields out = A'c.
 template <int VW, int NCH>
-__global__ void __launch_bounds__(256) rmatvec_mx_part_kernel(const float *__restrict__ X, long long n, int q,
-                                                              const float2 *__restrict__ wc,
-                                                              const int32_t *__restrict__ idx,
-                                                              const long long *__restrict__ cnt_dev,
-                                                              double *__restrict__ part, double *__restrict__ apart)
+__global__ void __launch_bounds__(NCH * VW >= 8 ? 256 : 1024) rmatvec_mx_part_kernel(const float *__restrict__ X, long long n, int q,
+                                                               const float2 *__restrict__ wc,
+                                                               const int32_t *__restrict__ idx,
+                                                               const long long *__restrict__ cnt_dev,
+                                                               double *__restrict__ part, double *__restrict__ apart,
+                                                               unsigned *__restrict__ counter, double *__restrict__ out,
+                                                               double *__restrict__ red, int slot)
 {
     const long long cnt = idx ? *cnt_dev : n;
     const int G = gridDim.x;
@@ -339,96 +385,139 @@ __global__ void __launch_bounds__(256) rmatvec_mx_part_kernel(const float *__res
     for (int k = 0; k < NCH; ++k)
 #pragma unroll
         for (int e = 0; e < VW; ++e) { s[k][e] = 0.f; c[k][e] = 0.f; ab[k][e] = 0.f; }
-    constexpr int R = NCH >= 4 ? 1 : (NCH == 2 ? 2 : 4);   // rows in flight per warp
-    for (long long r0 = r_beg + warp; r0 < r_end; r0 += (long long)nw * R) {
-        float2 w[R];
-        long long ii[R];
-#pragma unroll
-        for (int u = 0; u < R; ++u) {
-            const long long r = r0 + (long long)u * nw;
-            ii[u] = -1;
-            w[u] = make_float2(0.f, 0.f);
-            if (r < r_end) {
-                ii[u] = idx ? (long long)idx[r] : r;
-                w[u] = wc[ii[u]];
-            }
+    // A warp takes 32-row chunks of the block's range; its lanes load the 32 row
+    // indices and weights at once, then rows are streamed R at a time with all
+    // R row loads in flight before any arithmetic.
+    constexpr int R = NCH >= 4 ? 2 : (NCH == 2 ? 4 : 8);
+    for (long long c0 = r_beg + (long long)warp * 32; c0 < r_end; c0 += (long long)nw * 32) {
+        const long long rl = c0 + lane;
+        int myi = -1;
+        float2 myw = make_float2(0.f, 0.f);
+        if (rl < r_end) {
+            myi = idx ? idx[rl] : (int)rl;
+            myw = wc[myi];
         }
-        float xv[R][NCH][VW];
+        const int here = (int)((r_end - c0) < 32 ? (r_end - c0) : 32);
+        for (int u0 = 0; u0 < here; u0 += R) {
+            int ii[R];
+            float2 w[R];
 #pragma unroll
-        for (int u = 0; u < R; ++u)
-#pragma unroll
-            for (int k = 0; k < NCH; ++k) {
-                const int ch = lane + 32 * k;
-                if (ii[u] >= 0 && ch < nch) {
-                    if (VW == 4) {
-                        const float4 x4 = __ldcs(reinterpret_cast<const float4 *>(X + ii[u] * (long long)q) + ch);
-                        xv[u][k][0] = x4.x; xv[u][k][VW > 1 ? 1 : 0] = x4.y;
-                        xv[u][k][VW > 2 ? 2 : 0] = x4.z; xv[u][k][VW > 3 ? 3 : 0] = x4.w;
-                    } else {
-                        xv[u][k][0] = __ldcs(X + ii[u] * (long long)q + ch);
-                    }
-                } else {
-#pragma unroll
-                    for (int e = 0; e < VW; ++e) xv[u][k][e] = 0.f;
-                }
+            for (int u = 0; u < R; ++u) {
+                const int src = (u0 + u) & 31;
+                ii[u] = __shfl_sync(0xffffffffu, myi, src);
+                w[u].x = __shfl_sync(0xffffffffu, myw.x, src);
+                w[u].y = __shfl_sync(0xffffffffu, myw.y, src);
+                if (u0 + u >= here) ii[u] = -1;
             }
+            float xv[R][NCH][VW];
 #pragma unroll
-        for (int u = 0; u < R; ++u)
+            for (int u = 0; u < R; ++u)
 #pragma unroll
-            for (int k = 0; k < NCH; ++k)
+                for (int k = 0; k < NCH; ++k) {
+                    const int ch = lane + 32 * k;
+                    if (ii[u] >= 0 && ch < nch) {
+                        if (VW == 4) {
+                            const float4 x4 =
+                                __ldcs(reinterpret_cast<const float4 *>(X + (long long)ii[u] * q) + ch);
+                            xv[u][k][0] = x4.x; xv[u][k][VW > 1 ? 1 : 0] = x4.y;
+                            xv[u][k][VW > 2 ? 2 : 0] = x4.z; xv[u][k][VW > 3 ? 3 : 0] = x4.w;
+                        } else {
+                            xv[u][k][0] = __ldcs(X + (long long)ii[u] * q + ch);
+                        }
+                    } else {
 #pragma unroll
-                for (int e = 0; e < VW; ++e) {
-                    dot2_step(xv[u][k][e], w[u], s[k][e], c[k][e]);
-                    ab[k][e] += fabsf(xv[u][k][e] * w[u].x);
+                        for (int e = 0; e < VW; ++e) xv[u][k][e] = 0.f;
+                    }
                 }
-    }
-    extern __shared__ float sredf[];   // [3][q]: s, c, |.|
-    for (int j = threadIdx.x; j < 3 * q; j += blockDim.x) sredf[j] = 0.f;
-    __syncthreads();
-    for (int wv = 0; wv < nw; ++wv) {
-        if (warp == wv) {
 #pragma unroll
-            for (int k = 0; k < NCH; ++k) {
-                const int ch = lane + 32 * k;
-                if (ch < nch)
+            for (int u = 0; u < R; ++u)
+#pragma unroll
+                for (int k = 0; k < NCH; ++k)
 #pragma unroll
                     for (int e = 0; e < VW; ++e) {
-                        const int j = ch * VW + e;
-                        float ss = sredf[j], cc = sredf[q + j];
-                        df_acc(ss, cc, s[k][e], c[k][e]);
-                        sredf[j] = ss;
-                        sredf[q + j] = cc;
-                        sredf[2 * q + j] += ab[k][e];
+                        dot2_step(xv[u][k][e], w[u], s[k][e], c[k][e]);
+                        ab[k][e] += fabsf(xv[u][k][e] * w[u].x);
                     }
-            }
         }
-        __syncthreads();
     }
+    // per-warp results to shared memory: [warp][3][q]
+    extern __shared__ float sredf[];
+#pragma unroll
+    for (int k = 0; k < NCH; ++k) {
+        const int ch = lane + 32 * k;
+        if (ch < nch)
+#pragma unroll
+            for (int e = 0; e < VW; ++e) {
+                const int j = ch * VW + e;
+                float *b = sredf + (size_t)warp * 3 * q;
+                b[j] = s[k][e];
+                b[q + j] = c[k][e];
+                b[2 * q + j] = ab[k][e];
+            }
+    }
+    __syncthreads();
     for (int j = threadIdx.x; j < q; j += blockDim.x) {
-        part[(size_t)blockIdx.x * q + j] = (double)sredf[j] + (double)sredf[q + j];
-        apart[(size_t)blockIdx.x * q + j] = (double)sredf[2 * q + j];
+        float ss = 0.f, cc = 0.f, aa = 0.f;
+        for (int wv = 0; wv < nw; ++wv) {
+            const float *b = sredf + (size_t)wv * 3 * q;
+            df_acc(ss, cc, b[j], b[q + j]);
+            aa += b[2 * q + j];
+        }
+        part[(size_t)blockIdx.x * q + j] = (double)ss + (double)cc;
+        apart[(size_t)blockIdx.x * q + j] = (double)aa;
+    }
+    __threadfence();
+    __syncthreads();
+    __shared__ int is_last;
+    if (threadIdx.x == 0) is_last = (atomicAdd(counter, 1u) == (unsigned)(G - 1));
+    __syncthreads();
+    if (is_last) {
+        __threadfence();
+        double *sm = reinterpret_cast<double *>(sredf);
+        final_reduce(G, q, part, apart, out, red, slot, sm);
+        if (threadIdx.x == 0) *counter = 0u;
     }
 }
 
-// out_j = sum_b part[b][j] (fixed order); red[slot] = sum_j (sum_b apart[b][j])^2
-__global__ void rmatvec_final_kernel(int G, int q, const double *__restrict__ part,
-                                     const double *__restrict__ apart, double *__restrict__ out,
-                                     double *__restrict__ red, int slot)
+// out_j = sum_b part[b][j] in a fixed order (8 interleaved sub-sums per
+// column, then the 8 combined in order); red[slot] = sum_j (sum_b apart[b][j])^2.
+// One block of 1024 threads: 128 columns x 8 sub-sums per round.
+__global__ void __launch_bounds__(1024) rmatvec_final_kernel(int G, int q, const double *__restrict__ part,
+                                                             const double *__restrict__ apart,
+                                                             double *__restrict__ out, double *__restrict__ red,
+                                                             int slot)
 {
-    __shared__ double sh[32];
-    double local = 0.0;
-    for (int j = threadIdx.x; j < q; j += blockDim.x) {
+    __shared__ double sp[8][128], sa[8][128];
+    __shared__ double sq[128];
+    const int tx = threadIdx.x & 127, sub = threadIdx.x >> 7;
+    double scale = 0.0;
+    for (int c0 = 0; c0 < q; c0 += 128) {
+        const int col = c0 + tx;
         double s = 0.0, a = 0.0;
-        for (int b = 0; b < G; ++b) { s += part[(size_t)b * q + j]; a += apart[(size_t)b * q + j]; }
-        out[j] = s;
-        local += a * a;
+        if (col < q) {
+#pragma unroll 4
+            for (int b = sub; b < G; b += 8) {
+                s += __ldcg(part + (size_t)b * q + col);
+                a += __ldcg(apart + (size_t)b * q + col);
+            }
+        }
+        sp[sub][tx] = s;
+        sa[sub][tx] = a;
+        __syncthreads();
+        if (sub == 0 && col < q) {
+            double ts = 0.0, ta = 0.0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) { ts += sp[k][tx]; ta += sa[k][tx]; }
+            out[col] = ts;
+            scale = fma(ta, ta, scale);
+        }
+        __syncthreads();
     }
-    local = warp_sum(local);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = local;
+    if (sub == 0) sq[tx] = scale;
     __syncthreads();
     if (threadIdx.x == 0 && slot >= 0) {
         double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+        for (int k = 0; k < 128; ++k) t += sq[k];
         red[slot] = t;
     }
 }
@@ -455,34 +544,54 @@ static cudaError_t rmatvec_t(Work &W, const double *c, const int32_t *idx, const
     return cudaGetLastError();
 }
 
+static int g_rmx_attr = 0;
+
 static cudaError_t rmatvec_mx(Work &W, const float2 *wc, const int32_t *idx, const long long *cnt_dev, double *out,
                               int scale_slot)
 {
     const int q = (int)W.q;
-    const int G = W.rm_grid;
-    double *part = W.part;
-    double *apart = W.part + (size_t)G * q;
-    const size_t smem = (size_t)3 * q * sizeof(float);
-    const float *X = (const float *)W.X;
     const bool vec = (q % 4 == 0) && ((uintptr_t)W.X % 16 == 0);
     const int nch = vec ? (q / 4 + 31) / 32 : (q + 31) / 32;
-    if (vec) {
-#define RX_CASE(K)                                                                                         \
-    if (nch <= K) {                                                                                        \
-        rmatvec_mx_part_kernel<4, K><<<G, 256, smem, W.st>>>(X, W.n, q, wc, idx, cnt_dev, part, apart);    \
-    } else
-        RX_CASE(1) RX_CASE(2) RX_CASE(4) RX_CASE(8) { return cudaErrorInvalidValue; }
-#undef RX_CASE
-    } else {
-#define RS_CASE(K)                                                                                         \
-    if (nch <= K) {                                                                                        \
-        rmatvec_mx_part_kernel<1, K><<<G, 256, smem, W.st>>>(X, W.n, q, wc, idx, cnt_dev, part, apart);    \
-    } else
-        RS_CASE(1) RS_CASE(2) RS_CASE(4) RS_CASE(8) RS_CASE(16) RS_CASE(32) { return cudaErrorInvalidValue; }
-#undef RS_CASE
+    int nch_t = 1;
+    while (nch_t < nch) nch_t <<= 1;
+    const int threads = nch_t * (vec ? 4 : 1) >= 8 ? 256 : 1024;   // must match the kernel's launch bounds
+    const int G = threads == 1024 ? W.nsm : W.nsm * 4;
+    double *part = W.part;
+    double *apart = W.part + (size_t)G * q;
+    size_t smem = (size_t)(threads / 32) * 3 * q * sizeof(float);
+    const size_t smem_final = (size_t)(2 * (threads / 128) * 128 + 128) * sizeof(double);
+    if (smem < smem_final) smem = smem_final;
+    if (!g_rmx_attr) {
+        const void *fns[] = {(const void *)rmatvec_mx_part_kernel<4, 1>, (const void *)rmatvec_mx_part_kernel<4, 2>,
+                             (const void *)rmatvec_mx_part_kernel<4, 4>, (const void *)rmatvec_mx_part_kernel<4, 8>,
+                             (const void *)rmatvec_mx_part_kernel<1, 1>, (const void *)rmatvec_mx_part_kernel<1, 2>,
+                             (const void *)rmatvec_mx_part_kernel<1, 4>, (const void *)rmatvec_mx_part_kernel<1, 8>,
+                             (const void *)rmatvec_mx_part_kernel<1, 16>, (const void *)rmatvec_mx_part_kernel<1, 32>};
+        for (const void *f : fns) {
+            const cudaError_t ea = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+            if (ea != cudaSuccess) return ea;
+        }
+        g_rmx_attr = 1;
     }
-    rmatvec_final_kernel<<<1, 1024, 0, W.st>>>(G, q, part, apart, out, W.red, scale_slot);
-    W.nlaunch += 2;
+    const float *X = (const float *)W.X;
+#define RX_ARGS X, W.n, q, wc, idx, cnt_dev, part, apart, W.rm_counter, out, W.red, scale_slot
+    if (vec) {
+        if (nch <= 1) rmatvec_mx_part_kernel<4, 1><<<G, threads, smem, W.st>>>(RX_ARGS);
+        else if (nch <= 2) rmatvec_mx_part_kernel<4, 2><<<G, threads, smem, W.st>>>(RX_ARGS);
+        else if (nch <= 4) rmatvec_mx_part_kernel<4, 4><<<G, threads, smem, W.st>>>(RX_ARGS);
+        else if (nch <= 8) rmatvec_mx_part_kernel<4, 8><<<G, threads, smem, W.st>>>(RX_ARGS);
+        else return cudaErrorInvalidValue;
+    } else {
+        if (nch <= 1) rmatvec_mx_part_kernel<1, 1><<<G, threads, smem, W.st>>>(RX_ARGS);
+        else if (nch <= 2) rmatvec_mx_part_kernel<1, 2><<<G, threads, smem, W.st>>>(RX_ARGS);
+        else if (nch <= 4) rmatvec_mx_part_kernel<1, 4><<<G, threads, smem, W.st>>>(RX_ARGS);
+        else if (nch <= 8) rmatvec_mx_part_kernel<1, 8><<<G, threads, smem, W.st>>>(RX_ARGS);
+        else if (nch <= 16) rmatvec_mx_part_kernel<1, 16><<<G, threads, smem, W.st>>>(RX_ARGS);
+        else if (nch <= 32) rmatvec_mx_part_kernel<1, 32><<<G, threads, smem, W.st>>>(RX_ARGS);
+        else return cudaErrorInvalidValue;
+    }
+#undef RX_ARGS
+    ++W.nlaunch;
     return cudaGetLastError();
 }
 

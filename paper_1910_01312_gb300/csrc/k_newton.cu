@@ -74,9 +74,11 @@ __global__ void __launch_bounds__(256) gram_kernel(const TX *__restrict__ X, int
     if (ti == tj && ty == 0 && cb + tx < q) hpart[(size_t)ks * q + cb + tx] = hacc;
 }
 
-// M = I + sigma (G - h h'/p), both triangles, from the KS partials.
+// M = I + sigma (G - h h'/p), both triangles, from the KS partials (and,
+// when Mf != nullptr, its FP32 (hi, lo) split for the double-float operator).
 __global__ void build_m_kernel(int q, int KS, const double *__restrict__ part, const double *__restrict__ hpart,
-                               double p, double sigma, double *__restrict__ M, double *__restrict__ h)
+                               double p, double sigma, double *__restrict__ M, double *__restrict__ h,
+                               float2 *__restrict__ Mf)
 {
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)q * q;
          e += (long long)gridDim.x * blockDim.x) {
@@ -94,6 +96,12 @@ __global__ void build_m_kernel(int q, int KS, const double *__restrict__ part, c
         if (a == b) { m += 1.0; h[a] = ha; }
         M[(size_t)a * q + b] = m;
         M[(size_t)b * q + a] = m;
+        if (Mf) {
+            const float hi = (float)m;
+            const float2 v = make_float2(hi, (float)(m - (double)hi));
+            Mf[(size_t)a * q + b] = v;
+            Mf[(size_t)b * q + a] = v;
+        }
     }
 }
 
@@ -151,7 +159,301 @@ __global__ void __launch_bounds__(1024) chol_solve_kernel(int q, double *__restr
     if (tid == 0 && bad) set_err(err, DEV_CHOL);
 }
 
+// ------------------------------------------------------------ mixed form
+
+// Gram of FP32 rows with exact products (TwoProd) and double-float sums
+// (TwoSum) on the FP32 pipes; same tiling and outputs as gram_kernel.
+__global__ void __launch_bounds__(256) gram_df_kernel(const float *__restrict__ X, int q, const int32_t *__restrict__ J,
+                                                      long long p, int KS, double *__restrict__ part,
+                                                      double *__restrict__ hpart)
+{
+    int t = blockIdx.x;
+    int ti = 0;
+    while (t > ti) { t -= ti + 1; ++ti; }
+    const int tj = t;
+    const int ks = blockIdx.y;
+    const long long per = (p + KS - 1) / KS;
+    const long long r0 = (long long)ks * per;
+    const long long r1 = r0 + per < p ? r0 + per : p;
+    __shared__ float sA[kGR][kGT + 1], sB[kGR][kGT + 1];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+    float hs[4] = {0.f, 0.f, 0.f, 0.f}, hc[4] = {0.f, 0.f, 0.f, 0.f};
+    float as[4] = {0.f, 0.f, 0.f, 0.f}, ac[4] = {0.f, 0.f, 0.f, 0.f};
+    const int ca = ti * kGT, cb = tj * kGT;
+    (void)hs; (void)hc;
+    float hsum = 0.f, hcmp = 0.f;
+    for (long long rb = r0; rb < r1; rb += kGR) {
+        for (int e = threadIdx.x; e < kGR * kGT; e += blockDim.x) {
+            const int rr = e / kGT, cc = e % kGT;
+            const long long r = rb + rr;
+            float va = 0.f, vb = 0.f;
+            if (r < r1) {
+                const float *row = X + (long long)J[r] * q;
+                if (ca + cc < q) va = row[ca + cc];
+                if (cb + cc < q) vb = row[cb + cc];
+            }
+            sA[rr][cc] = va;
+            sB[rr][cc] = vb;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int rr = 0; rr < kGR; ++rr) {
+            const float b = sB[rr][tx];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                float pr, e, sn, tt;
+                two_prod(sA[rr][ty + 8 * k], b, pr, e);
+                two_sum(as[k], pr, sn, tt);
+                as[k] = sn;
+                ac[k] += tt + e;
+            }
+            if (ti == tj && ty == 0) {
+                float sn, tt;
+                two_sum(hsum, b, sn, tt);
+                hsum = sn;
+                hcmp += tt;
+            }
+        }
+        __syncthreads();
+    }
+    double *P = part + (size_t)ks * q * q;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int a = ca + ty + 8 * k, b = cb + tx;
+        if (a < q && b < q) P[(size_t)a * q + b] = (double)as[k] + (double)ac[k];
+    }
+    if (ti == tj && ty == 0 && cb + tx < q) hpart[(size_t)ks * q + cb + tx] = (double)hsum + (double)hcmp;
+}
+
+__device__ __forceinline__ double block_dot(const double *a, const double *b, int q, double *red)
+{
+    double s = 0.0;
+    for (int j = threadIdx.x; j < q; j += blockDim.x) s = fma(a[j], b[j], s);
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    __syncthreads();
+    return t;
+}
+
+// z = (L L')^{-1} r with the FP32 factor L (row stride ld), by warp 0:
+// lane l owns rows l, l+32, ...  (q <= 32 * kMaxRows)
+template <int kMaxRows>
+__device__ void chol_apply_warp(const float *L, const float *rdiag, int ld, int q, const double *r, double *z)
+{
+    const int lane = threadIdx.x & 31;
+    float b[kMaxRows];
+    const int nr = (q + 31) / 32;
+#pragma unroll
+    for (int m = 0; m < kMaxRows; ++m) b[m] = (m < nr && lane + 32 * m < q) ? (float)r[lane + 32 * m] : 0.f;
+    // forward: L y = b
+    for (int k = 0; k < q; ++k) {
+        const int own = k & 31, km = k >> 5;
+        float yk = 0.f;
+#pragma unroll
+        for (int m = 0; m < kMaxRows; ++m)
+            if (m == km) yk = b[m];
+        yk = __shfl_sync(0xffffffffu, yk, own) * rdiag[k];
+#pragma unroll
+        for (int m = 0; m < kMaxRows; ++m) {
+            const int i = lane + 32 * m;
+            if (m < nr && i > k && i < q) b[m] -= L[(size_t)i * ld + k] * yk;
+            if (m == km && lane == own) b[m] = yk;
+        }
+    }
+    // backward: L' x = y
+    for (int k = q - 1; k >= 0; --k) {
+        const int own = k & 31, km = k >> 5;
+        float xk = 0.f;
+#pragma unroll
+        for (int m = 0; m < kMaxRows; ++m)
+            if (m == km) xk = b[m];
+        xk = __shfl_sync(0xffffffffu, xk, own) * rdiag[k];
+#pragma unroll
+        for (int m = 0; m < kMaxRows; ++m) {
+            const int i = lane + 32 * m;
+            if (m < nr && i < k) b[m] -= L[(size_t)k * ld + i] * xk;
+            if (m == km && lane == own) b[m] = xk;
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < kMaxRows; ++m)
+        if (m < nr && lane + 32 * m < q) z[lane + 32 * m] = (double)b[m];
+}
+
+// One block: FP32 Cholesky of fl32(M) (diagonal shift on breakdown) as the
+// preconditioner of a conjugate-gradient solve of M dv = -g -- the CG of
+// Algorithm 3, Step 1 -- stopped at |M dv + g| <= max(min(eta, |g|^{1+tau}),
+// 1e-14 |g|) or after maxit steps.  The operator is applied in double-float
+// from the (hi, lo) FP32 split of M (relative accuracy ~2^-44, like FP64)
+// so that the one SM doing the solve never waits on the FP64 pipe.
+// Factorisation: right-looking, 32-wide panels: warp 0 factors the diagonal
+// block, one thread per row solves the panel, all threads update the
+// trailing matrix; three block barriers per panel.
+// SMEM: the factor lives in shared memory, else in Lg (row stride q + 1).
+// info[0] = CG steps, info[1] = final residual norm, info[2] = shift used.
+template <bool SMEM, int NR>
+__global__ void __launch_bounds__(1024) newton_pcg_kernel(int q, const double *__restrict__ M,
+                                                          const float2 *__restrict__ Mf, float *__restrict__ Lg,
+                                                          const double *__restrict__ g, double *__restrict__ dv,
+                                                          double eta, double tau, int maxit, double *__restrict__ info,
+                                                          int *err)
+{
+    extern __shared__ double dsm2[];
+    double *x = dsm2, *r = x + q, *z = r + q, *pp = z + q, *Ap = pp + q, *rold = Ap + q;
+    float2 *pf = reinterpret_cast<float2 *>(rold + q);   // df copy of pp
+    const int ld = q + 1;
+    float *L = SMEM ? reinterpret_cast<float *>(pf + q) : Lg;
+    __shared__ double red[32];
+    __shared__ int bad;
+    __shared__ float rdiag[1024];   // 1 / L_jj of the final factor (q <= 1024)
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    // largest diagonal entry (block reduction), scale of the breakdown shift
+    double md = 0.0;
+    for (int j = tid; j < q; j += nt) md = fmax(md, (double)Mf[(size_t)j * q + j].x);
+    md = warp_max(md);
+    if (lane == 0) red[warp] = md;
+    __syncthreads();
+    double maxdiag = 0.0;
+    for (int w = 0; w < nw; ++w) maxdiag = fmax(maxdiag, red[w]);
+    __syncthreads();
+    float shift = 0.f;
+    for (int attempt = 0; attempt < 6; ++attempt) {
+        for (int i = warp; i < q; i += nw)
+            for (int j = lane; j <= i; j += 32) L[(size_t)i * ld + j] = Mf[(size_t)i * q + j].x + (i == j ? shift : 0.f);
+        if (tid == 0) bad = 0;
+        __syncthreads();
+        for (int kb = 0; kb < q; kb += 32) {
+            const int nb = (q - kb) < 32 ? (q - kb) : 32;
+            // (1) diagonal block, warp 0, lane i owns row kb + i
+            if (warp == 0) {
+                for (int j = 0; j < nb; ++j) {
+                    const float d = L[(size_t)(kb + j) * ld + kb + j];
+                    const bool okp = (d > 0.f) && isfinite(d);
+                    const float rs = okp ? rsqrtf(d) : 1.f;
+                    if (!okp && lane == 0) bad = 1;
+                    __syncwarp();
+                    if (lane > j && lane < nb) L[(size_t)(kb + lane) * ld + kb + j] *= rs;
+                    if (lane == j) { L[(size_t)(kb + j) * ld + kb + j] = okp ? d * rs : 1.f; rdiag[kb + j] = rs; }
+                    __syncwarp();
+                    if (lane > j && lane < nb) {
+                        const float lij = L[(size_t)(kb + lane) * ld + kb + j];
+                        for (int k = j + 1; k <= lane; ++k)
+                            L[(size_t)(kb + lane) * ld + kb + k] -= lij * L[(size_t)(kb + k) * ld + kb + j];
+                    }
+                    __syncwarp();
+                }
+            }
+            __syncthreads();
+            if (bad) break;
+            // (2) panel rows below the block: x L_b' = a, one thread per row
+            for (int i = kb + nb + tid; i < q; i += nt) {
+                float *row = L + (size_t)i * ld + kb;
+                for (int j = 0; j < nb; ++j) {
+                    float v = row[j];
+                    const float *lj = L + (size_t)(kb + j) * ld + kb;
+                    for (int m = 0; m < j; ++m) v -= row[m] * lj[m];
+                    row[j] = v * rdiag[kb + j];
+                }
+            }
+            __syncthreads();
+            // (3) trailing update, rows i = base + wy + 32a, columns k = base + wx + 32b, k <= i
+            const int base = kb + nb;
+            for (int i = base + warp; i < q; i += nw) {
+                const float *li = L + (size_t)i * ld + kb;
+                for (int k = base + lane; k <= i; k += 32) {
+                    const float *lk = L + (size_t)k * ld + kb;
+                    float acc = 0.f;
+#pragma unroll 8
+                    for (int m = 0; m < nb; ++m) acc = fmaf(li[m], lk[m], acc);
+                    L[(size_t)i * ld + k] -= acc;
+                }
+            }
+            __syncthreads();
+        }
+        __syncthreads();
+        if (!bad) break;
+        shift = (shift == 0.f) ? (float)(1e-7 * maxdiag) : shift * 100.f;
+        __syncthreads();
+    }
+    if (bad) {
+        if (tid == 0) set_err(err, DEV_CHOL);
+        return;
+    }
+    // CG on M dv = -g
+    for (int j = tid; j < q; j += nt) { x[j] = 0.0; r[j] = -g[j]; }
+    __syncthreads();
+    const double gn = sqrt(block_dot(r, r, q, red));
+    const double tol = fmax(fmin(eta, pow(gn, 1.0 + tau)), 1e-14 * gn);
+    if (tid < 32) chol_apply_warp<NR>(L, rdiag, ld, q, r, z);
+    __syncthreads();
+    for (int j = tid; j < q; j += nt) pp[j] = z[j];
+    __syncthreads();
+    double rz = block_dot(r, z, q, red);
+    double rn = gn;
+    int it = 0;
+    for (it = 0; it < maxit && rn > tol; ++it) {
+        for (int j = tid; j < q; j += nt) {
+            const float hi = (float)pp[j];
+            pf[j] = make_float2(hi, (float)(pp[j] - (double)hi));
+        }
+        __syncthreads();
+        // Ap = M p in double-float, warp per row
+        for (int i = warp; i < q; i += nw) {
+            float sh = 0.f, sc = 0.f;
+            const float2 *mrow = Mf + (size_t)i * q;
+            for (int j = lane; j < q; j += 32) {
+                const float2 a = mrow[j], b = pf[j];
+                float p0, e0, sn, t0;
+                two_prod(a.x, b.x, p0, e0);
+                e0 = fmaf(a.x, b.y, fmaf(a.y, b.x, e0));
+                two_sum(sh, p0, sn, t0);
+                sh = sn;
+                sc += t0 + e0;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float s2 = __shfl_xor_sync(0xffffffffu, sh, o), c2 = __shfl_xor_sync(0xffffffffu, sc, o);
+                float sn, e;
+                two_sum(sh, s2, sn, e);
+                e += sc + c2;
+                sh = sn + e;
+                sc = e - (sh - sn);
+            }
+            if (lane == 0) Ap[i] = (double)sh + (double)sc;
+        }
+        __syncthreads();
+        const double pAp = block_dot(pp, Ap, q, red);
+        if (!(pAp > 0.0)) break;
+        const double al = rz / pAp;
+        for (int j = tid; j < q; j += nt) {
+            x[j] = fma(al, pp[j], x[j]);
+            rold[j] = r[j];
+            r[j] = fma(-al, Ap[j], r[j]);
+        }
+        __syncthreads();
+        rn = sqrt(block_dot(r, r, q, red));
+        if (rn <= tol) { ++it; break; }
+        if (tid < 32) chol_apply_warp<NR>(L, rdiag, ld, q, r, z);
+        __syncthreads();
+        // flexible (Polak-Ribiere) beta: robust to the FP32 preconditioner
+        const double rz_new = block_dot(r, z, q, red);
+        const double rz_old = block_dot(rold, z, q, red);
+        const double beta = fmax(0.0, (rz_new - rz_old) / rz);
+        rz = rz_new;
+        for (int j = tid; j < q; j += nt) pp[j] = fma(beta, pp[j], z[j]);
+        __syncthreads();
+    }
+    for (int j = tid; j < q; j += nt) dv[j] = x[j];
+    if (tid == 0 && info) { info[0] = it; info[1] = rn; info[2] = shift; }
+    (void)M;
+}
+
 static int g_chol_smem_set = 0;
+static int g_pcg_smem_set = 0;
 
 cudaError_t launch_newton(Work &W, const int32_t *J, long long p_host, const long long *p_dev, double sigma,
                           const double *g, double *dv)
@@ -169,16 +471,53 @@ cudaError_t launch_newton(Work &W, const int32_t *J, long long p_host, const lon
     double *part = W.part;
     double *hpart = W.part + (size_t)ks * q * q;
     dim3 grid(ntiles, (unsigned)ks);
-    if (W.xf32)
+    const bool mixed = W.precision == 1 && W.xf32;
+    if (mixed)
+        gram_df_kernel<<<grid, 256, 0, W.st>>>((const float *)W.X, q, J, p_host, (int)ks, part, hpart);
+    else if (W.xf32)
         gram_kernel<float><<<grid, 256, 0, W.st>>>((const float *)W.X, q, J, p_host, (int)ks, part, hpart);
     else
         gram_kernel<double><<<grid, 256, 0, W.st>>>((const double *)W.X, q, J, p_host, (int)ks, part, hpart);
-    build_m_kernel<<<W.nsm * 2, 256, 0, W.st>>>(q, (int)ks, part, hpart, (double)p_host, sigma, W.M, W.h);
-    W.nlaunch += 3;   // gram, build_m, chol_solve
+    const bool cg = W.precision == 1;
+    build_m_kernel<<<W.nsm * 2, 256, 0, W.st>>>(q, (int)ks, part, hpart, (double)p_host, sigma, W.M, W.h,
+                                                cg ? W.Mf : nullptr);
+    W.nlaunch += 3;   // gram, build_m, and the solve below
+    if (cg) {
+        // FP32-Cholesky-preconditioned CG on the FP64 matrix (Algorithm 3's inexact solve)
+        const size_t vec = (size_t)6 * q * sizeof(double) + (size_t)q * sizeof(float2);
+        double *info = W.red + 12;
+        const size_t smem_fac = vec + (size_t)q * (q + 1) * sizeof(float);
+        if (smem_fac <= (size_t)200 * 1024) {
+            const size_t smem = smem_fac;
+            if (!g_pcg_smem_set) {
+                cudaError_t ea = cudaSuccess;
+                ea = cudaFuncSetAttribute(newton_pcg_kernel<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+                if (ea == cudaSuccess) ea = cudaFuncSetAttribute(newton_pcg_kernel<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+                if (ea == cudaSuccess) ea = cudaFuncSetAttribute(newton_pcg_kernel<true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+                if (ea == cudaSuccess) ea = cudaFuncSetAttribute(newton_pcg_kernel<true, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+                if (ea != cudaSuccess) return ea;
+                g_pcg_smem_set = 1;
+            }
+            const int nr = (q + 31) / 32;
+#define PCG_CASE(R)                                                                                        \
+    if (nr <= R) {                                                                                         \
+        newton_pcg_kernel<true, R><<<1, 1024, smem, W.st>>>(q, W.M, W.Mf, nullptr, g, dv, W.eta, W.tau, W.cg_maxit,  \
+                                                            info, W.err);                                  \
+    } else
+            PCG_CASE(1) PCG_CASE(2) PCG_CASE(4) PCG_CASE(8) {}
+#undef PCG_CASE
+        } else {
+            newton_pcg_kernel<false, 32><<<1, 1024, vec, W.st>>>(q, W.M, W.Mf, W.Lf, g, dv, W.eta, W.tau, W.cg_maxit,
+                                                                 info, W.err);
+        }
+        return cudaGetLastError();
+    }
     size_t smem = ((size_t)q * q + q) * sizeof(double);
     if (q <= 144) {
         if (!g_chol_smem_set) {
-            cudaFuncSetAttribute(chol_solve_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            const cudaError_t ea =
+                cudaFuncSetAttribute(chol_solve_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            if (ea != cudaSuccess) return ea;
             g_chol_smem_set = 1;
         }
         chol_solve_kernel<true><<<1, 1024, smem, W.st>>>(q, W.M, g, dv, W.err);

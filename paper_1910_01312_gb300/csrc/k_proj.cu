@@ -56,42 +56,43 @@ struct ProjArgs {
 };
 
 struct PassAcc {
-    double fex;   // exact part of f over the components evaluated in FP64
-    double nup;   // (#upper with y=+1) - (#upper with y=-1): contributes C * nup
-    double pp;    // free count just right of lambda
-    double pm;    // free count just left of lambda
-    double dhi;   // smallest positive breakpoint offset (+inf: none)
-    double dlo;   // largest negative breakpoint offset (-inf: none)
+    double fex;         // exact part of f over the components evaluated in FP64
+    int nup;            // (#upper with y=+1) - (#upper with y=-1): contributes C * nup
+    int pp;             // free count just right of lambda
+    int pm;             // free count just left of lambda
+    float fdhi, fdlo;   // conservative breakpoint offsets of FP32-classified components
+    double ddhi, ddlo;  // breakpoint offsets of FP64-evaluated components
 };
 
 __device__ __forceinline__ void acc_init(PassAcc &A)
 {
-    A.fex = 0.0; A.nup = 0.0; A.pp = 0.0; A.pm = 0.0; A.dhi = INFINITY; A.dlo = -INFINITY;
+    A.fex = 0.0; A.nup = 0; A.pp = 0; A.pm = 0;
+    A.fdhi = INFINITY; A.fdlo = -INFINITY; A.ddhi = INFINITY; A.ddlo = -INFINITY;
 }
 
 __device__ __forceinline__ void offset_in(PassAcc &A, double o)
 {
-    if (o > 0.0) A.dhi = fmin(A.dhi, o);
-    else if (o < 0.0) A.dlo = fmax(A.dlo, o);
+    if (o > 0.0) A.ddhi = fmin(A.ddhi, o);
+    else if (o < 0.0) A.ddlo = fmax(A.ddlo, o);
 }
 
 // Exact FP64 evaluation of one component at lambda.
 __device__ __forceinline__ void eval_exact(double s, bool pos, double lam, double C, PassAcc &A)
 {
     const double t = pos ? (s - lam) : (lam - s);
-    if (t >= C) A.nup += pos ? 1.0 : -1.0;
+    if (t >= C) A.nup += pos ? 1 : -1;
     else if (t > 0.0) A.fex += pos ? t : -t;
     const bool open = (t > 0.0) && (t < C);
     const bool at0 = (t == 0.0), atC = (t == C);
-    A.pp += (open || (pos ? atC : at0)) ? 1.0 : 0.0;
-    A.pm += (open || (pos ? at0 : atC)) ? 1.0 : 0.0;
+    A.pp += (open || (pos ? atC : at0)) ? 1 : 0;
+    A.pm += (open || (pos ? at0 : atC)) ? 1 : 0;
     // breakpoints at offsets (in lambda): y=+1: t, t - C;  y=-1: -t, C - t
     offset_in(A, pos ? t : -t);
     offset_in(A, pos ? t - C : C - t);
 }
 
 // One component at lambda: in FP32 when it is certainly saturated (mixed
-// form), else exactly.
+// form), else exactly.  The FP32 path touches no FP64 instruction.
 template <bool MX>
 __device__ __forceinline__ void eval_comp(double s, float r, bool pos, double lam, float dl, double C,
                                           float Cf, PassAcc &A)
@@ -100,16 +101,16 @@ __device__ __forceinline__ void eval_comp(double s, float r, bool pos, double la
         const float tf = pos ? (r - dl) : (dl - r);
         const float er = (fabsf(r) + fabsf(dl) + Cf) * 9.5367431640625e-07f;   // 2^-20
         if (tf > Cf + er) {
-            A.nup += pos ? 1.0 : -1.0;
+            A.nup += pos ? 1 : -1;
             // offsets t - C (y=+1, above) or C - t (y=-1, below), made nearer by er
-            if (pos) A.dhi = fmin(A.dhi, (double)(tf - Cf - er));
-            else A.dlo = fmax(A.dlo, (double)(Cf - tf + er));
+            if (pos) A.fdhi = fminf(A.fdhi, tf - Cf - er);
+            else A.fdlo = fmaxf(A.fdlo, Cf - tf + er);
             return;
         }
         if (tf < -er) {
             // offsets t (y=+1, below) or -t (y=-1, above)
-            if (pos) A.dlo = fmax(A.dlo, (double)(tf + er));
-            else A.dhi = fmin(A.dhi, (double)(-tf - er));
+            if (pos) A.fdlo = fmaxf(A.fdlo, tf + er);
+            else A.fdhi = fminf(A.fdhi, -tf - er);
             return;
         }
     }
@@ -122,14 +123,15 @@ __device__ __forceinline__ void reduce_partials(const double *slot, int G, doubl
 {
     const int lane = threadIdx.x & 31;
     double F = 0.0, nu = 0.0, pp = 0.0, pm = 0.0, dh = INFINITY, dlo = -INFINITY;
+    // all loads of a lane are independent: issue them together
+#pragma unroll 8
     for (int bb = lane; bb < G; bb += 32) {
         const double *p = slot + (size_t)bb * kPartStride;
-        F += __ldcg(p + 0);
-        nu += __ldcg(p + 1);
-        pp += __ldcg(p + 2);
-        pm += __ldcg(p + 3);
-        dh = fmin(dh, __ldcg(p + 4));
-        dlo = fmax(dlo, __ldcg(p + 5));
+        const double2 a = __ldcg(reinterpret_cast<const double2 *>(p));
+        const double2 b = __ldcg(reinterpret_cast<const double2 *>(p + 2));
+        const double2 c = __ldcg(reinterpret_cast<const double2 *>(p + 4));
+        F += a.x; nu += a.y; pp += b.x; pm += b.y;
+        dh = fmin(dh, c.x); dlo = fmax(dlo, c.y);
     }
     tot[0] = warp_sum(F); tot[1] = warp_sum(nu); tot[2] = warp_sum(pp); tot[3] = warp_sum(pm);
     tot[4] = warp_min(dh); tot[5] = warp_max(dlo);
@@ -141,7 +143,7 @@ __device__ __forceinline__ double flip_sign(double x, bool neg)
 }
 
 template <int EPT, bool MX>
-__global__ void __launch_bounds__(kTPB) proj_kernel(ProjArgs A)
+__global__ void __launch_bounds__(kTPB, EPT >= 16 ? 1 : 2) proj_kernel(ProjArgs A)
 {
     const int G = gridDim.x, blk = blockIdx.x, tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
@@ -175,10 +177,14 @@ __global__ void __launch_bounds__(kTPB) proj_kernel(ProjArgs A)
     __shared__ double sh_lam;
     __shared__ int sh_done;
 
+    // root-search state, kept in shared memory (only warp 0 lane 0 updates it)
+    __shared__ double st_L, st_U, st_FL, st_FU, st_last_step;
+    __shared__ int st_last_dir, st_nbr;
+    if (tid == 0) {
+        st_L = -INFINITY; st_U = INFINITY; st_FL = 0.0; st_FU = 0.0;   // bracket: f(L) > 0 > f(U)
+        st_last_step = 0.0; st_last_dir = 0; st_nbr = 0;
+    }
     double lam = lam0;
-    double L = -INFINITY, U = INFINITY, FL = 0.0, FU = 0.0;   // bracket: f(L) > 0 > f(U)
-    double last_step = 0.0;
-    int last_dir = 0, nbr = 0;
     double lam_hat = lam;
     int pass = 0;
     bool alive = true;
@@ -190,25 +196,28 @@ __global__ void __launch_bounds__(kTPB) proj_kernel(ProjArgs A)
 #pragma unroll
         for (int k = 0; k < EPT; ++k)
             if ((valm >> k) & 1u) eval_comp<MX>(s[k], r[k], (posm >> k) & 1u, lam, dl, C, Cf, acc);
-        acc.fex = warp_sum(acc.fex);
-        acc.nup = warp_sum(acc.nup);
-        acc.pp = warp_sum(acc.pp);
-        acc.pm = warp_sum(acc.pm);
-        acc.dhi = warp_min(acc.dhi);
-        acc.dlo = warp_max(acc.dlo);
-        if (lane == 0) {
-            sh_d[warp][0] = acc.fex; sh_d[warp][1] = acc.nup; sh_d[warp][2] = acc.pp;
-            sh_d[warp][3] = acc.pm; sh_d[warp][4] = acc.dhi; sh_d[warp][5] = acc.dlo;
+        {
+            const double fex = warp_sum(acc.fex);
+            const int nup = __reduce_add_sync(0xffffffffu, acc.nup);
+            const int pp = __reduce_add_sync(0xffffffffu, acc.pp);
+            const int pm = __reduce_add_sync(0xffffffffu, acc.pm);
+            const double dh = warp_min(fmin(acc.ddhi, (double)acc.fdhi));
+            const double dlw = warp_max(fmax(acc.ddlo, (double)acc.fdlo));
+            if (lane == 0) {
+                sh_d[warp][0] = fex; sh_d[warp][1] = (double)nup; sh_d[warp][2] = (double)pp;
+                sh_d[warp][3] = (double)pm; sh_d[warp][4] = dh; sh_d[warp][5] = dlw;
+            }
         }
         __syncthreads();
-        if (tid == 0) {
-            double b0 = 0, b1 = 0, b2 = 0, b3 = 0, b4 = INFINITY, b5 = -INFINITY;
-            for (int w = 0; w < kWarps; ++w) {
-                b0 += sh_d[w][0]; b1 += sh_d[w][1]; b2 += sh_d[w][2]; b3 += sh_d[w][3];
-                b4 = fmin(b4, sh_d[w][4]); b5 = fmax(b5, sh_d[w][5]);
+        if (warp == 0) {
+            const bool v = lane < kWarps;
+            const double b0 = warp_sum(v ? sh_d[lane][0] : 0.0), b1 = warp_sum(v ? sh_d[lane][1] : 0.0);
+            const double b2 = warp_sum(v ? sh_d[lane][2] : 0.0), b3 = warp_sum(v ? sh_d[lane][3] : 0.0);
+            const double b4 = warp_min(v ? sh_d[lane][4] : INFINITY), b5 = warp_max(v ? sh_d[lane][5] : -INFINITY);
+            if (lane == 0) {
+                double *p = A.part + ((size_t)(pass & 1) * G + blk) * kPartStride;
+                p[0] = b0; p[1] = b1; p[2] = b2; p[3] = b3; p[4] = b4; p[5] = b5;
             }
-            double *p = A.part + ((size_t)(pass & 1) * G + blk) * kPartStride;
-            p[0] = b0; p[1] = b1; p[2] = b2; p[3] = b3; p[4] = b4; p[5] = b5;
         }
         if (!grid_barrier(A.bar, A.err)) { alive = false; break; }
         if (warp == 0) {
@@ -216,6 +225,8 @@ __global__ void __launch_bounds__(kTPB) proj_kernel(ProjArgs A)
             reduce_partials(A.part + (size_t)(pass & 1) * G * kPartStride, G, tot);
             if (lane == 0) {
                 // ---- decision (identical in every block) ----
+                double &L = st_L, &U = st_U, &FL = st_FL, &FU = st_FU, &last_step = st_last_step;
+                int &last_dir = st_last_dir, &nbr = st_nbr;
                 const double Ft = tot[0] + C * tot[1];
                 const double pr = tot[2], pl = tot[3];
                 const double bh = lam + tot[4], bl = lam + tot[5];
@@ -286,6 +297,7 @@ __global__ void __launch_bounds__(kTPB) proj_kernel(ProjArgs A)
     const double lh = lam_hat;
     const float dlh = MX ? (float)(lh - lam0) : 0.f;
     const float2 Csplit = make_float2(Cf, (float)(C - (double)Cf));
+    const long long Cbits = __double_as_longlong(C);
     double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0, accu = 0.0;
     unsigned isJ = 0u, isS = 0u;   // bit k: component k is in J / S
 #pragma unroll
@@ -300,23 +312,25 @@ __global__ void __launch_bounds__(kTPB) proj_kernel(ProjArgs A)
             cls = (tf > Cf + er) ? 2 : ((tf < -er) ? 0 : 1);
         }
         double pk;
+        int pc;   // class of pk: 0 (= 0), 1 (free), 2 (= C)
         if (cls == 2) {
-            pk = C;
+            pk = C; pc = 2;
         } else if (cls == 0) {
-            pk = 0.0;
+            pk = 0.0; pc = 0;
         } else {
             const double t = pos ? (s[k] - lh) : (lh - s[k]);
-            pk = fmin(fmax(t, 0.0), C);
-            if (t > 0.0 && t < C) isJ |= 1u << k;
+            if (t >= C) { pk = C; pc = 2; }
+            else if (t <= 0.0) { pk = 0.0; pc = 0; }
+            else { pk = t; pc = 1; isJ |= 1u << k; }
         }
-        if (pk > 0.0) isS |= 1u << k;
+        if (pc) isS |= 1u << k;
         const double u = flip_sign(s[k], !pos);
         if (A.pi_out) A.pi_out[i] = pk;
         if (A.u_out) A.u_out[i] = u;
         if (A.wpi_out) {
             float2 wv;
-            if (pk == C) wv = Csplit;
-            else if (pk == 0.0) wv = make_float2(0.f, 0.f);
+            if (pc == 2) wv = Csplit;
+            else if (pc == 0) wv = make_float2(0.f, 0.f);
             else { wv.x = (float)pk; wv.y = (float)(pk - (double)wv.x); }
             if (!pos) { wv.x = -wv.x; wv.y = -wv.y; }
             A.wpi_out[i] = wv;
@@ -332,9 +346,11 @@ __global__ void __launch_bounds__(kTPB) proj_kernel(ProjArgs A)
         if (A.sums & SF_PSID) {
             // psi difference term by term: pi(2u - pi) - pib(2ub - pib)
             const double pb = A.pi_base[i];
-            if (pk == C && pb == C) {
+            const long long pbb = __double_as_longlong(pb);
+            const int pbc = (pbb == Cbits) ? 2 : ((pbb << 1) == 0 ? 0 : 1);
+            if (pc == 2 && pbc == 2) {
                 accu += u - A.a[i];                    // 2C(u - ub), factor applied below
-            } else if (pk != 0.0 || pb != 0.0) {
+            } else if (pc != 0 || pbc != 0) {
                 const double ub = A.a[i];
                 acc1 += pk * (2.0 * u - pk) - pb * (2.0 * ub - pb);
             }
@@ -367,11 +383,14 @@ __global__ void __launch_bounds__(kTPB) proj_kernel(ProjArgs A)
         A.cnt[((size_t)tid * G + blk) * 2 + 0] = cj;
         A.cnt[((size_t)tid * G + blk) * 2 + 1] = cs;
     }
-    if (tid == 0) {
-        double b0 = 0, b1 = 0, b2 = 0, b3 = 0;
-        for (int w = 0; w < kWarps; ++w) { b0 += sh_d[w][0]; b1 += sh_d[w][1]; b2 += sh_d[w][2]; b3 += sh_d[w][3]; }
-        double *p = A.part + ((size_t)2 * G + blk) * kPartStride;
-        p[0] = b0; p[1] = b1; p[2] = b2; p[3] = b3;
+    if (warp == 0) {
+        const bool v = lane < kWarps;
+        const double b0 = warp_sum(v ? sh_d[lane][0] : 0.0), b1 = warp_sum(v ? sh_d[lane][1] : 0.0);
+        const double b2 = warp_sum(v ? sh_d[lane][2] : 0.0), b3 = warp_sum(v ? sh_d[lane][3] : 0.0);
+        if (lane == 0) {
+            double *p = A.part + ((size_t)2 * G + blk) * kPartStride;
+            p[0] = b0; p[1] = b1; p[2] = b2; p[3] = b3;
+        }
     }
     if (!alive || !grid_barrier(A.bar, A.err)) return;
 
@@ -380,9 +399,10 @@ __global__ void __launch_bounds__(kTPB) proj_kernel(ProjArgs A)
     __shared__ long long sh_tot2[EPT][2];
     for (int k = warp; k < EPT; k += kWarps) {
         long long tj = 0, ts = 0, pj = 0, ps = 0;
+#pragma unroll 8
         for (int bb = lane; bb < G; bb += 32) {
-            const int cj = __ldcg(A.cnt + ((size_t)k * G + bb) * 2 + 0);
-            const int cs = __ldcg(A.cnt + ((size_t)k * G + bb) * 2 + 1);
+            const int2 cc = __ldcg(reinterpret_cast<const int2 *>(A.cnt + ((size_t)k * G + bb) * 2));
+            const int cj = cc.x, cs = cc.y;
             tj += cj; ts += cs;
             if (bb < blk) { pj += cj; ps += cs; }
         }
@@ -391,25 +411,34 @@ __global__ void __launch_bounds__(kTPB) proj_kernel(ProjArgs A)
         if (lane == 0) { sh_tot2[k][0] = tj; sh_tot2[k][1] = ts; sh_off[k][0] = pj; sh_off[k][1] = ps; }
     }
     __syncthreads();
+    if (blk == 0 && warp == 0) {
+        // block 0 publishes the totals (fixed-order lanes, then shuffles)
+        double r0 = 0, r1 = 0, r2 = 0, r3 = 0;
+#pragma unroll 8
+        for (int bb = lane; bb < G; bb += 32) {
+            const double *p = A.part + ((size_t)2 * G + bb) * kPartStride;
+            const double2 a = __ldcg(reinterpret_cast<const double2 *>(p));
+            const double2 b = __ldcg(reinterpret_cast<const double2 *>(p + 2));
+            r0 += a.x; r1 += a.y; r2 += b.x; r3 += b.y;
+        }
+        r0 = warp_sum(r0); r1 = warp_sum(r1); r2 = warp_sum(r2); r3 = warp_sum(r3);
+        if (lane == 0) {
+            long long tj = 0, ts = 0;
+            for (int k = 0; k < EPT; ++k) { tj += sh_tot2[k][0]; ts += sh_tot2[k][1]; }
+            A.out->lam = lam_hat;
+            A.out->sum[0] = r0; A.out->sum[1] = r1; A.out->sum[2] = r2; A.out->sum[3] = r3;
+            A.out->p = tj;
+            A.out->s = ts;
+            A.out->passes = pass;
+            A.out->status = 0;
+        }
+    }
     if (tid == 0) {
         long long rj = 0, rs = 0;
         for (int k = 0; k < EPT; ++k) {
             const long long oj = rj + sh_off[k][0], os = rs + sh_off[k][1];
             rj += sh_tot2[k][0]; rs += sh_tot2[k][1];
             sh_off[k][0] = oj; sh_off[k][1] = os;
-        }
-        if (blk == 0) {
-            double r0 = 0, r1 = 0, r2 = 0, r3 = 0;
-            for (int bb = 0; bb < G; ++bb) {
-                const double *p = A.part + ((size_t)2 * G + bb) * kPartStride;
-                r0 += __ldcg(p + 0); r1 += __ldcg(p + 1); r2 += __ldcg(p + 2); r3 += __ldcg(p + 3);
-            }
-            A.out->lam = lam_hat;
-            A.out->sum[0] = r0; A.out->sum[1] = r1; A.out->sum[2] = r2; A.out->sum[3] = r3;
-            A.out->p = rj;
-            A.out->s = rs;
-            A.out->passes = pass;
-            A.out->status = 0;
         }
     }
     __syncthreads();

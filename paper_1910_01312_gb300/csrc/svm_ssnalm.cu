@@ -52,6 +52,7 @@ struct svm_ssnalm {
     double kms[4] = {0, 0, 0, 0};
     long long syncs = 0;
     long long launch_base = 0;
+    bool trace = false;   // SVM_SSNALM_TRACE=1: one stderr line per Newton step
 };
 
 enum { TK_MATVEC = 0, TK_RMATVEC = 1, TK_PROJ = 2, TK_NEWTON = 3 };
@@ -137,8 +138,8 @@ extern "C" const char *svm_ssnalm_last_error(const svm_ssnalm_t *h)
 
 static void free_work(Work &W)
 {
-    void *ptrs[] = {W.alpha, W.z, W.dz, W.qa, W.tmpn, W.v, W.dv, W.g, W.atp, W.atp2, W.h, W.w, W.tmpq, W.M,
-                    W.part, W.cnt, W.bar, W.err, W.pout, W.red, W.X_own, W.y_own};
+    void *ptrs[] = {W.alpha, W.z, W.dz, W.qa, W.tmpn, W.v, W.dv, W.g, W.atp, W.atp2, W.h, W.w, W.tmpq, W.M, W.Lf, W.Mf,
+                    W.part, W.cnt, W.bar, W.rm_counter, W.err, W.pout, W.red, W.X_own, W.y_own};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (int b = 0; b < 2; ++b) {
@@ -223,6 +224,8 @@ extern "C" svm_status svm_ssnalm_create(svm_ssnalm_t **out, const svm_problem *p
     W.xf32 = prob->dtype == SVM_F32;
     W.C = params->C;
     W.precision = params->precision;
+    W.eta = params->eta > 0.0 ? params->eta : 0.1;
+    W.tau = params->tau > 0.0 ? params->tau : 0.5;
     W.st = (cudaStream_t)params->stream;
     auto fail = [&](svm_status st, const std::string &m) {
         g_create_err = m;
@@ -261,7 +264,7 @@ extern "C" svm_status svm_ssnalm_create(svm_ssnalm_t **out, const svm_problem *p
     bool bad = dalloc(&W.alpha, n) || dalloc(&W.z, n) || dalloc(&W.dz, n) || dalloc(&W.qa, n) ||
                dalloc(&W.tmpn, n) || dalloc(&W.v, q) || dalloc(&W.dv, q) || dalloc(&W.g, q) ||
                dalloc(&W.atp, q) || dalloc(&W.atp2, q) || dalloc(&W.h, q) || dalloc(&W.w, q) || dalloc(&W.tmpq, q) ||
-               dalloc(&W.M, q * q) || dalloc(&W.part, W.part_len) || dalloc(&W.bar, 4) || dalloc(&W.err, 4) ||
+               dalloc(&W.M, q * q) || dalloc(&W.Lf, q * (q + 1)) || dalloc(&W.Mf, q * q) || dalloc(&W.part, W.part_len) || dalloc(&W.bar, 4) || dalloc(&W.rm_counter, 4) || dalloc(&W.err, 4) ||
                dalloc(&W.pout, 4) || dalloc(&W.red, 16);
     for (int b = 0; b < 2 && !bad; ++b)
         bad = dalloc(&W.pb[b].u, n) || dalloc(&W.pb[b].pi, n) || dalloc(&W.pb[b].wpi, n) ||
@@ -276,6 +279,7 @@ extern "C" svm_status svm_ssnalm_create(svm_ssnalm_t **out, const svm_problem *p
     W.cnt_len = (size_t)W.proj_ept * W.proj_grid * 2;
     if (dalloc(&W.cnt, W.cnt_len)) return fail(SVM_ERR_OOM, "device workspace allocation failed");
     cudaMemsetAsync(W.bar, 0, 4 * sizeof(unsigned), W.st);
+    cudaMemsetAsync(W.rm_counter, 0, 4 * sizeof(unsigned), W.st);
     cudaMemsetAsync(W.err, 0, 4 * sizeof(int), W.st);
     cudaMemsetAsync(W.pout, 0, 4 * sizeof(ProjOut), W.st);
     // validate labels and data on the device
@@ -292,6 +296,10 @@ extern "C" svm_status svm_ssnalm_create(svm_ssnalm_t **out, const svm_problem *p
     if (hchk[0]) return fail(SVM_ERR_INVALID_ARG, "labels must be +1 or -1");
     if (hchk[2]) return fail(SVM_ERR_INVALID_ARG, "X has non-finite entries");
     h->npos = hchk[1];
+    {
+        const char *tr = getenv("SVM_SSNALM_TRACE");
+        h->trace = tr && tr[0] == '1';
+    }
     *out = h;
     return SVM_OK;
 }
@@ -487,6 +495,9 @@ extern "C" svm_status svm_ssnalm_solve(svm_ssnalm_t *h, const double *alpha0, sv
             const double tol_in = fmin(epsk, epsk * dx) / sqrt(sigma);
             const double floor_g = 1e-15 * sqrt(W.h_red[1]);
             if (!isfinite(gn)) { h->err = "non-finite gradient"; return SVM_ERR_NUMERIC; }
+            if (h->trace)
+                fprintf(stderr, "[svm] k=%d j=%d sigma=%.3g p=%lld s=%lld |g|=%.3e tol=%.3e passes=%d lam=%.6g\n", k, j,
+                        sigma, (long long)m.p, (long long)m.s, gn, fmax(tol_in, floor_g), m.passes, m.lam);
             if (gn <= fmax(tol_in, floor_g) || j >= P.max_inner) break;
             // Algorithm 3, Step 1: Newton direction on the free set J
             const long long p = m.p;
@@ -516,6 +527,9 @@ extern "C" svm_status svm_ssnalm_solve(svm_ssnalm_t *h, const double *alpha0, sv
                 if ((st = sync_read(h)) != SVM_OK) return st;
                 const double slope = W.h_red[2], vdv = W.h_red[3], dvdv = W.h_red[4];
                 const double dpsi = t * vdv + 0.5 * t * t * dvdv + W.h_pout[1 + nxt].sum[1] / (2.0 * sigma);
+                if (h->trace)
+                    fprintf(stderr, "[svm]   trial t=%.3g dpsi=%.3e slope=%.3e passes=%d cg=%g cg_res=%.2e\n", t, dpsi,
+                            slope, W.h_pout[1 + nxt].passes, W.h_red[12], W.h_red[13]);
                 if (dpsi <= P.mu * t * slope) { accepted = true; break; }
                 t *= P.delta;
             }
@@ -540,6 +554,9 @@ extern "C" svm_status svm_ssnalm_solve(svm_ssnalm_t *h, const double *alpha0, sv
         if ((st = kkt_project(h, W.alpha)) != SVM_OK) return st;
         if ((st = sync_read(h)) != SVM_OK) return st;
         R = kkt_value(W.h_pout[SLOT_KKT]);
+        if (h->trace)
+            fprintf(stderr, "[svm] outer k=%d inner=%d R_KKT=%.3e sigma=%.3g kkt_passes=%d\n", k, j, R, sigma,
+                    W.h_pout[SLOT_KKT].passes);
         if (!isfinite(R)) { status = SVM_ERR_NUMERIC; h->err = "non-finite KKT residual"; break; }
         if (R <= P.tol) { status = SVM_OK; ++k; break; }
         if (R > 0.5 * Rprev) sigma = fmin(P.sigma_max, P.sigma_growth * sigma);
