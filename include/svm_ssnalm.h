@@ -206,6 +206,39 @@ svm_status svm_ssnalm_set_timing(svm_ssnalm_t *h, int enable);
 /* Copy the counters into *out (host); reset them when reset != 0. */
 svm_status svm_ssnalm_get_stats(svm_ssnalm_t *h, svm_stats *out, int reset);
 
+/* ---------------------------------------------------------------------
+ * Allocation-free transposed product.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate memory.
+ * ------------------------------------------------------------------- */
+
+/* out = A'c = sum_i c_i y_i x_i (q entries) for dense row-major FP32 X
+ * (n x q), labels y (n, +1/-1) and weights c (n, FP64), computed like the
+ * mixed-form product of svm_op_rmatvec, WITHOUT allocating anything.
+ *
+ * For callers that cannot allocate: code inside a framework that owns all
+ * device memory through its own pool, latency-critical loops that cannot
+ * afford the synchronisation or the failure of an allocation, callers with a
+ * fixed memory budget.  They cannot create a handle (a handle owns its
+ * workspace), so this call needs only the caller's device buffers X, y, c,
+ * out and a stream (NULL = default stream).
+ *
+ * Scratch: one fixed array in device global memory (1.25 MiB + 256 bytes:
+ * block partials for up to 160 blocks x 1024 columns and a counter), present
+ * on every GPU that loads the library until the process exits.  Limits:
+ * 1 <= q <= 1024 and 1 <= n < 2^31; larger sizes return SVM_ERR_UNSUPPORTED,
+ * null pointers or n, q < 1 return SVM_ERR_INVALID_ARG.  It calls no
+ * allocation routine: it only looks up the array's device address, clears
+ * the counter (cudaMemsetAsync) and launches one kernel.
+ *
+ * The first call on a device (with that device current) performs that
+ * device's one-time set-up (address look-up, kernel attribute); make that
+ * first call before any stream capture.  The call is stream-ordered and
+ * returns without synchronising.  All calls on a device share the one
+ * scratch array: calls whose kernels could overlap on the GPU (different
+ * streams or host threads) race and give wrong results -- serialise them. */
+svm_status svm_rmatvec_noalloc(const float *X, const int8_t *y, int64_t n, int64_t q,
+                               const double *c, double *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

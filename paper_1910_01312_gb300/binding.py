@@ -52,7 +52,8 @@ class Stats(C.Structure):
 
 SYMBOLS = ["svm_default_params", "svm_ssnalm_create", "svm_ssnalm_solve", "svm_ssnalm_destroy",
            "svm_ssnalm_last_error", "svm_op_matvec", "svm_op_rmatvec", "svm_op_project",
-           "svm_op_newton", "svm_op_kkt", "svm_ssnalm_set_timing", "svm_ssnalm_get_stats"]
+           "svm_op_newton", "svm_op_kkt", "svm_ssnalm_set_timing", "svm_ssnalm_get_stats",
+           "svm_rmatvec_noalloc"]
 
 _lock = threading.Lock()
 _lib = None
@@ -92,8 +93,9 @@ def load(build_if_missing: bool = False):
         L.svm_op_kkt.argtypes = [vp, vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.svm_ssnalm_set_timing.argtypes = [vp, C.c_int]
         L.svm_ssnalm_get_stats.argtypes = [vp, C.POINTER(Stats), C.c_int]
+        L.svm_rmatvec_noalloc.argtypes = [vp, vp, i64, i64, vp, vp, vp]
         for f in ("svm_op_matvec", "svm_op_rmatvec", "svm_op_project", "svm_op_newton", "svm_op_kkt",
-                  "svm_ssnalm_set_timing", "svm_ssnalm_get_stats"):
+                  "svm_ssnalm_set_timing", "svm_ssnalm_get_stats", "svm_rmatvec_noalloc"):
             getattr(L, f).restype = C.c_int
         _lib = L
         return L
@@ -113,6 +115,13 @@ def default_params(**kw) -> Params:
             raise KeyError(k)
         setattr(P, k, v)
     return P
+
+
+def rmatvec_noalloc(X, y, c, out, stream=None) -> int:
+    """out = A'c through the allocation-free entry point (device FP32 X, int8
+    y, FP64 c and out); returns the svm_status code."""
+    n, q = X.shape
+    return load().svm_rmatvec_noalloc(_ptr(X), _ptr(y), int(n), int(q), _ptr(c), _ptr(out), stream)
 
 
 def _ptr(t):
