@@ -38,7 +38,7 @@ __device__ __forceinline__ int ld_relaxed_i32(const int *p)
 // Sense reversal on the top bit of one counter: block 0 adds 2^31 - (G-1),
 // the others add 1, so after every barrier the low 31 bits are unchanged and
 // the counter needs no reset between launches.  The wait is bounded: after
-// ~0.5 s it records DEV_TIMEOUT and returns false instead of spinning on.
+// 2^24 polls (seconds) it records DEV_TIMEOUT and returns false instead of spinning on.
 // Every block executes the same sequence of barriers.
 __device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err)
 {
@@ -49,14 +49,15 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err)
         unsigned add = (blockIdx.x == 0) ? (0x80000000u - (gridDim.x - 1u)) : 1u;
         __threadfence();
         unsigned old = atomicAdd(bar, add);
+        // poll without sleeping: a sleep here is far coarser than the wait itself;
+        // each acquire load is an L2 round trip, so the poll rate is self-limited
         unsigned spins = 0;
         while (((old ^ ld_acquire_u32(bar)) & 0x80000000u) == 0u) {
-            if (ld_relaxed_i32(err) == DEV_TIMEOUT || ++spins > (1u << 22)) {
+            if (((++spins) & 255u) == 0u && (ld_relaxed_i32(err) == DEV_TIMEOUT || spins > (1u << 24))) {
                 set_err(err, DEV_TIMEOUT);
                 ok = 0;
                 break;
             }
-            __nanosleep(128);
         }
         __threadfence();
         ok_sh = ok;
@@ -141,4 +142,57 @@ __device__ __forceinline__ df df_add(df a, df b)
     return r;
 }
 
+}  // namespace svm
+
+namespace svm {
+// ---------------------------------------------------------------------------
+// Bulk asynchronous copies (cp.async.bulk, the 1-D TMA path) and mbarriers.
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// global -> shared bulk copy completing on bar; dst, src 16-byte aligned, bytes % 16 == 0
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait on a phase of bar: false (and DEV_TIMEOUT recorded) after ~1 s.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity, int *err)
+{
+    for (unsigned it = 0; it < (1u << 22); ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 1023u) == 1023u) {
+            if (ld_relaxed_i32(err) == DEV_TIMEOUT) break;
+            __nanosleep(64);
+        }
+    }
+    set_err(err, DEV_TIMEOUT);
+    return false;
+}
 }  // namespace svm

@@ -28,22 +28,26 @@ enum ProjSums : int {
 };
 
 // Projection input u_i = a_i + c1 * b_i + c2 (b may be null) and outputs.
+// mixed: a, b, u_out are double-float (float2) n-vectors; else FP64.
 struct ProjIn {
-    const double *a = nullptr, *b = nullptr;
+    bool mixed = false;
+    const void *a = nullptr, *b = nullptr;
     double c1 = 0.0, c2 = 0.0;
     int sums = 0;
     const double *lam0 = nullptr;   // device: warm start for lambda (nullable)
-    double *u_out = nullptr, *pi_out = nullptr;
+    void *u_out = nullptr;
+    double *pi_out = nullptr;
     float2 *wpi_out = nullptr;      // y_i pi_i as an FP32 (hi, lo) pair
     int32_t *J = nullptr, *S = nullptr;
     const double *pi_base = nullptr;
-    const double *alpha = nullptr;
+    const double *alpha = nullptr;  // FP64 alpha for SF_DPA and SF_KKT
 };
 
 // One projection's output buffers (the solver keeps two and swaps them when a
 // line-search trial is accepted).
 struct ProjBuf {
-    double *u = nullptr, *pi = nullptr;
+    double *u = nullptr, *pi = nullptr;   // FP64 u (plain form) and pi
+    float2 *uf = nullptr;                 // double-float u (mixed form)
     float2 *wpi = nullptr;
     int32_t *J = nullptr, *S = nullptr;
 };
@@ -60,6 +64,10 @@ struct Work {
     int dev = 0, nsm = 0;
     // n-vectors (FP64) and index lists
     double *alpha = nullptr, *z = nullptr, *dz = nullptr, *qa = nullptr, *tmpn = nullptr;
+    // the mixed form carries z = A v, dz = A dv, Q alpha and alpha as
+    // double-float pairs instead (df = true; z, dz and pb[].u are then unused)
+    bool df = false;
+    float2 *zf = nullptr, *dzf = nullptr, *qaf = nullptr, *alphaf = nullptr;
     ProjBuf pb[2];            // current / trial projection buffers
     // q-vectors
     double *v = nullptr, *dv = nullptr, *g = nullptr, *atp = nullptr, *atp2 = nullptr, *h = nullptr,
@@ -100,6 +108,11 @@ cudaError_t launch_project(Work &W, const ProjIn &in, ProjOut *out);
 // z0 = A v0 (and z1 = A v1 when v1 != nullptr, in the same pass over X)
 cudaError_t launch_matvec(Work &W, const double *v0, double *z0, const double *v1 = nullptr,
                           double *z1 = nullptr);
+// the same with double-float outputs (mixed form, FP32 X with q % 4 == 0)
+cudaError_t launch_matvec_df(Work &W, const double *v0, float2 *z0, const double *v1 = nullptr,
+                             float2 *z1 = nullptr);
+// alphaf_i = y_i wpi_i (double-float alpha from the signed split weights)
+cudaError_t launch_unsign_df(Work &W, const float2 *wpi, float2 *alphaf);
 // out = sum_i c_i y_i x_i over the index list idx (cnt entries, read from
 // *cnt_dev on the device) or over all rows when idx == nullptr.  The mixed
 // form reads the weights as y_i c_i FP32 pairs from wc (when non-null).
@@ -112,7 +125,6 @@ cudaError_t split_weights(Work &W, const double *c, float2 *wc);
 cudaError_t launch_grad(Work &W);            // g = v - atp; red[0] = |g|^2
 cudaError_t launch_dots(Work &W);            // red[2] = g'dv, red[3] = v'dv, red[4] = dv'dv
 cudaError_t launch_vaxpy(Work &W, double t); // v += t dv
-cudaError_t launch_zaxpy(Work &W, double t); // z += t dz
 cudaError_t launch_negcopy(Work &W, const double *g, double *dv); // dv = -g
 
 // Newton direction (I + sigma A'PA) dv = -g on the free set J (p from *p_dev

@@ -123,11 +123,13 @@ __global__ void __launch_bounds__(256) matvec_kernel(const TX *__restrict__ X, c
 // 32/GL rows (GL lanes per row), then transposes so that lane L holds row
 // base + L: the FP64 epilogue and the z store are then one coalesced
 // warp-wide instruction per 32 rows.
-template <int GL, int NV>
+// OUTDF: write y_i * (s + c) as a normalised double-float pair (float2)
+// instead of FP64 (no FP64 instruction at all in that case).
+template <int GL, int NV, bool OUTDF>
 __global__ void __launch_bounds__(256) matvec_mx_kernel(const float *__restrict__ X, const int8_t *__restrict__ y,
                                                         long long n, int q, const double *__restrict__ v0,
-                                                        const double *__restrict__ v1, double *__restrict__ z0,
-                                                        double *__restrict__ z1)
+                                                        const double *__restrict__ v1, void *__restrict__ z0v,
+                                                        void *__restrict__ z1v)
 {
     extern __shared__ float2 svf[];   // [NV][q] FP32 (hi, lo) split of v
     for (int j = threadIdx.x; j < q; j += blockDim.x) {
@@ -188,11 +190,21 @@ __global__ void __launch_bounds__(256) matvec_mx_kernel(const float *__restrict_
         const long long i = base + lane;
         if (i < n) {
             const bool pos = y[i] > 0;
-            const double d0 = (double)rs[0] + (double)rc[0];
-            z0[i] = pos ? d0 : -d0;
-            if (NV == 2) {
-                const double d1 = (double)rs[NV - 1] + (double)rc[NV - 1];
-                z1[i] = pos ? d1 : -d1;
+            if (OUTDF) {
+#pragma unroll
+                for (int k = 0; k < NV; ++k) {
+                    const float hi = rs[k] + rc[k];
+                    float2 v = make_float2(hi, rc[k] - (hi - rs[k]));
+                    if (!pos) { v.x = -v.x; v.y = -v.y; }
+                    reinterpret_cast<float2 *>(k == 0 ? z0v : z1v)[i] = v;
+                }
+            } else {
+                const double d0 = (double)rs[0] + (double)rc[0];
+                reinterpret_cast<double *>(z0v)[i] = pos ? d0 : -d0;
+                if (NV == 2) {
+                    const double d1 = (double)rs[NV - 1] + (double)rc[NV - 1];
+                    reinterpret_cast<double *>(z1v)[i] = pos ? d1 : -d1;
+                }
             }
         }
     }
@@ -220,8 +232,8 @@ static cudaError_t matvec_dispatch(Work &W, const double *v0, double *z0, const 
     return cudaGetLastError();
 }
 
-template <int NV>
-static cudaError_t matvec_mx_dispatch(Work &W, const double *v0, double *z0, const double *v1, double *z1)
+template <int NV, bool OUTDF>
+static cudaError_t matvec_mx_dispatch(Work &W, const double *v0, void *z0, const double *v1, void *z1)
 {
     const int nv4 = (int)(W.q / 4);
     int gl = 1;
@@ -231,7 +243,7 @@ static cudaError_t matvec_mx_dispatch(Work &W, const double *v0, double *z0, con
     const float *X = (const float *)W.X;
 #define MX_CASE(G)                                                                                        \
     case G:                                                                                               \
-        matvec_mx_kernel<G, NV><<<blocks, 256, smem, W.st>>>(X, W.y, W.n, (int)W.q, v0, v1, z0, z1);     \
+        matvec_mx_kernel<G, NV, OUTDF><<<blocks, 256, smem, W.st>>>(X, W.y, W.n, (int)W.q, v0, v1, z0, z1); \
         break;
     switch (gl) {
         MX_CASE(1) MX_CASE(2) MX_CASE(4) MX_CASE(8) MX_CASE(16) MX_CASE(32)
@@ -241,13 +253,19 @@ static cudaError_t matvec_mx_dispatch(Work &W, const double *v0, double *z0, con
     return cudaGetLastError();
 }
 
+cudaError_t launch_matvec_df(Work &W, const double *v0, float2 *z0, const double *v1, float2 *z1)
+{
+    if (!(W.xf32 && W.q % 4 == 0 && (uintptr_t)W.X % 16 == 0)) return cudaErrorInvalidValue;
+    return v1 ? matvec_mx_dispatch<2, true>(W, v0, z0, v1, z1) : matvec_mx_dispatch<1, true>(W, v0, z0, v1, z1);
+}
+
 cudaError_t launch_matvec(Work &W, const double *v0, double *z0, const double *v1, double *z1)
 {
     const size_t es = W.xf32 ? 4 : 8;
     const bool vec = ((W.q * es) % 16 == 0) && ((uintptr_t)W.X % 16 == 0);
     const bool two = v1 != nullptr;
     if (W.xf32 && vec && W.precision == 1)
-        return two ? matvec_mx_dispatch<2>(W, v0, z0, v1, z1) : matvec_mx_dispatch<1>(W, v0, z0, v1, z1);
+        return two ? matvec_mx_dispatch<2, false>(W, v0, z0, v1, z1) : matvec_mx_dispatch<1, false>(W, v0, z0, v1, z1);
     if (W.xf32) {
         if (vec) return two ? matvec_dispatch<float, true, 2>(W, v0, z0, v1, z1)
                             : matvec_dispatch<float, true, 1>(W, v0, z0, v1, z1);
@@ -695,14 +713,26 @@ cudaError_t launch_vaxpy(Work &W, double t)
     ++W.nlaunch;
     return cudaGetLastError();
 }
-cudaError_t launch_zaxpy(Work &W, double t)
+
+// alphaf_i = y_i wpi_i: removing the label's sign from a split weight is exact
+__global__ void unsign_df_kernel(long long n, const int8_t *__restrict__ y, const float2 *__restrict__ wpi,
+                                 float2 *__restrict__ af)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float2 w = wpi[i];
+        af[i] = (y[i] > 0) ? w : make_float2(-w.x, -w.y);
+    }
+}
+
+cudaError_t launch_unsign_df(Work &W, const float2 *wpi, float2 *alphaf)
 {
     int blocks = (int)((W.n + 1023) / 1024);
     if (blocks > W.nsm * 4) blocks = W.nsm * 4;
-    axpy_kernel<<<blocks, 1024, 0, W.st>>>(W.n, t, W.dz, W.z);
+    unsign_df_kernel<<<blocks, 1024, 0, W.st>>>(W.n, W.y, wpi, alphaf);
     ++W.nlaunch;
     return cudaGetLastError();
 }
+
 cudaError_t launch_negcopy(Work &W, const double *g, double *dv)
 {
     negcopy_kernel<<<1, 1024, 0, W.st>>>((int)W.q, g, dv);

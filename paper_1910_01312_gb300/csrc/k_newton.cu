@@ -452,6 +452,332 @@ __global__ void __launch_bounds__(1024) newton_pcg_kernel(int q, const double *_
     (void)M;
 }
 
+// ---- one-block dense SPD solver for q <= 200 (factor in shared memory) ----
+// L (FP32, row stride ld = q + 1, lower triangle) and rdiag = 1 / diag(L).
+
+// Blocked right-looking Cholesky of the matrix already in L; returns false
+// (block-uniformly) when a pivot is not positive.
+__device__ bool chol_blocked(float *L, float *rdiag, int q, int ld, int *bad_sh)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    for (int kb = 0; kb < q; kb += 32) {
+        const int nb = (q - kb) < 32 ? (q - kb) : 32;
+        // (1) diagonal block by warp 0, row kb + lane in registers
+        if (warp == 0) {
+            float a[32];
+#pragma unroll
+            for (int k = 0; k < 32; ++k) a[k] = (lane < nb && k <= lane) ? L[(size_t)(kb + lane) * ld + kb + k] : 0.f;
+            bool ok = true;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                if (j < nb) {
+                    const float d = __shfl_sync(0xffffffffu, a[j], j);
+                    const bool okj = (d > 0.f) && isfinite(d);
+                    ok = ok && okj;
+                    const float rs = okj ? rsqrtf(d) : 1.f;
+                    if (lane == j) a[j] = okj ? d * rs : 1.f;
+                    else if (lane > j) a[j] *= rs;
+#pragma unroll
+                    for (int k = j + 1; k < 32; ++k) {
+                        const float lkj = __shfl_sync(0xffffffffu, a[j], k);
+                        if (lane >= k) a[k] -= a[j] * lkj;
+                    }
+                }
+            }
+            if (lane < nb) {
+#pragma unroll
+                for (int k = 0; k < 32; ++k)
+                    if (k <= lane) L[(size_t)(kb + lane) * ld + kb + k] = a[k];
+                float dl = 1.f;
+#pragma unroll
+                for (int k = 0; k < 32; ++k)
+                    if (k == lane) dl = a[k];
+                rdiag[kb + lane] = 1.f / dl;
+            }
+            if (!ok && lane == 0) *bad_sh = 1;
+        }
+        __syncthreads();
+        if (*bad_sh) return false;
+        // (2) panel rows below the block: x L_bb' = a, a warp per row, lane j holds x_j
+        for (int i = kb + nb + warp; i < q; i += nw) {
+            float v = (lane < nb) ? L[(size_t)i * ld + kb + lane] : 0.f;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                if (j < nb) {
+                    const float xj = __shfl_sync(0xffffffffu, v, j) * rdiag[kb + j];
+                    if (lane == j) v = xj;
+                    else if (lane > j && lane < nb) v -= xj * L[(size_t)(kb + lane) * ld + kb + j];
+                }
+            }
+            if (lane < nb) L[(size_t)i * ld + kb + lane] = v;
+        }
+        __syncthreads();
+        // (3) trailing update with 4x4 register tiles: L_ik -= sum_m L_i,kb+m L_k,kb+m
+        const int base = kb + nb, m = q - base;
+        if (m > 0) {
+            const int nbt = (m + 3) / 4;
+            const int ntile = nbt * (nbt + 1) / 2;
+            for (int t = tid; t < ntile; t += blockDim.x) {
+                int ti = 0, tt = t;
+                while (tt > ti) { tt -= ti + 1; ++ti; }
+                const int i0 = base + 4 * ti, k0 = base + 4 * tt;
+                float acc[4][4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+                for (int mm = 0; mm < nb; ++mm) {
+                    float li[4], lk[4];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        li[a] = (i0 + a < q) ? L[(size_t)(i0 + a) * ld + kb + mm] : 0.f;
+                        lk[a] = (k0 + a < q) ? L[(size_t)(k0 + a) * ld + kb + mm] : 0.f;
+                    }
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(li[a], lk[b], acc[a][b]);
+                }
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        const int i = i0 + a, k = k0 + b;
+                        if (i < q && k <= i) L[(size_t)i * ld + k] -= acc[a][b];
+                    }
+            }
+        }
+        __syncthreads();
+    }
+    return true;
+}
+
+// b <- (L L')^{-1} b (FP32, in shared memory), blocked: warp 0 solves each
+// 32-wide diagonal block with shuffles, all warps update the rest.
+__device__ void chol_solve_blocked(const float *L, const float *rdiag, int q, int ld, float *b)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    // forward: L y = b
+    for (int kb = 0; kb < q; kb += 32) {
+        const int nb = (q - kb) < 32 ? (q - kb) : 32;
+        if (warp == 0) {
+            float v = (lane < nb) ? b[kb + lane] : 0.f;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                if (j < nb) {
+                    const float yj = __shfl_sync(0xffffffffu, v, j) * rdiag[kb + j];
+                    if (lane == j) v = yj;
+                    else if (lane > j && lane < nb) v -= yj * L[(size_t)(kb + lane) * ld + kb + j];
+                }
+            }
+            if (lane < nb) b[kb + lane] = v;
+        }
+        __syncthreads();
+        for (int i = kb + nb + warp; i < q; i += nw) {
+            float s = (lane < nb) ? L[(size_t)i * ld + kb + lane] * b[kb + lane] : 0.f;
+            s = warp_sumf(s);
+            if (lane == 0) b[i] -= s;
+        }
+        __syncthreads();
+    }
+    // backward: L' x = y
+    const int last = ((q - 1) / 32) * 32;
+    for (int kb = last; kb >= 0; kb -= 32) {
+        const int nb = (q - kb) < 32 ? (q - kb) : 32;
+        if (warp == 0) {
+            float v = (lane < nb) ? b[kb + lane] : 0.f;
+#pragma unroll
+            for (int j = 31; j >= 0; --j) {
+                if (j < nb) {
+                    const float xj = __shfl_sync(0xffffffffu, v, j) * rdiag[kb + j];
+                    if (lane == j) v = xj;
+                    else if (lane < j) v -= xj * L[(size_t)(kb + j) * ld + kb + lane];
+                }
+            }
+            if (lane < nb) b[kb + lane] = v;
+        }
+        __syncthreads();
+        for (int i = warp; i < kb; i += nw) {
+            float s = (lane < nb) ? L[(size_t)(kb + lane) * ld + i] * b[kb + lane] : 0.f;
+            s = warp_sumf(s);
+            if (lane == 0) b[i] -= s;
+        }
+        __syncthreads();
+    }
+}
+
+// One block: FP32 Cholesky of fl32(M) (diagonal shift on breakdown) as the
+// preconditioner of CG on M dv = -g (operator in double-float from the
+// (hi, lo) split of M), stopped at |M dv + g| <= max(min(eta, |g|^{1+tau}),
+// 1e-14 |g|) -- the CG of Algorithm 3, Step 1.  Every phase is parallel or a
+// 32-step shuffle chain: no thread walks a q-long chain.
+__global__ void __launch_bounds__(1024) newton_cg_smem_kernel(int q, const float2 *__restrict__ Mf,
+                                                              const double *__restrict__ g, double *__restrict__ dv,
+                                                              double eta, double tau, int maxit,
+                                                              double *__restrict__ info, int *err)
+{
+    // Scalar FP64 work (norms, step sizes, the stopping test) is done by
+    // thread 0 and broadcast through shared memory: replicated across 32 warps
+    // it would occupy the SM's FP64 pipe for tens of microseconds.
+    extern __shared__ double dsm3[];
+    double *x = dsm3, *r = x + q, *pp = r + q, *Ap = pp + q, *rold = Ap + q, *z = rold + q;
+    float2 *pf = reinterpret_cast<float2 *>(z + q);
+    float *bz = reinterpret_cast<float *>(pf + q);
+    float *rdiag = bz + q;
+    const int ld = q + 1;
+    float *L = rdiag + q + ((4 - (q & 3)) & 3);
+    __shared__ double red[3][32];
+    __shared__ double sc_tol, sc_al, sc_beta, sc_rn;
+    __shared__ int sc_go;
+    __shared__ float sc_shift;
+    __shared__ int bad;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    // block partial sums of up to three dot products over q: warp totals to red[*][warp]
+    auto dots = [&](const double *a0, const double *b0, const double *a1, const double *b1, const double *a2,
+                    const double *b2, int nd) {
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+        for (int j = tid; j < q; j += nt) {
+            s0 = fma(a0[j], b0[j], s0);
+            if (nd > 1) s1 = fma(a1[j], b1[j], s1);
+            if (nd > 2) s2 = fma(a2[j], b2[j], s2);
+        }
+        if (warp < (q + 31) / 32) {   // only warps holding entries reduce (q <= 200: at most 7 warps)
+            s0 = warp_sum(s0);
+            if (nd > 1) s1 = warp_sum(s1);
+            if (nd > 2) s2 = warp_sum(s2);
+        }
+        if (lane == 0) { red[0][warp] = s0; red[1][warp] = s1; red[2][warp] = s2; }
+        __syncthreads();
+    };
+    const int nwq = (q + 31) / 32;   // warps that hold vector entries (q <= nt)
+    if (warp == 0) {
+        float md = 0.f;
+        for (int j = lane; j < q; j += 32) md = fmaxf(md, Mf[(size_t)j * q + j].x);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) md = fmaxf(md, __shfl_xor_sync(0xffffffffu, md, o));
+        if (lane == 0) {
+            sc_shift = 0.f;
+            sc_tol = (double)md;   // reused below as the shift scale
+        }
+    }
+    __syncthreads();
+    const float maxdiag = (float)sc_tol;
+    bool okf = false;
+    for (int attempt = 0; attempt < 6 && !okf; ++attempt) {
+        const float shift = sc_shift;
+        for (int i = warp; i < q; i += nw)
+            for (int j = lane; j <= i; j += 32) L[(size_t)i * ld + j] = Mf[(size_t)i * q + j].x + (i == j ? shift : 0.f);
+        if (tid == 0) bad = 0;
+        __syncthreads();
+        okf = chol_blocked(L, rdiag, q, ld, &bad);
+        __syncthreads();
+        if (!okf && tid == 0) sc_shift = (shift == 0.f) ? 1e-7f * maxdiag : shift * 100.f;
+        __syncthreads();
+    }
+    if (!okf) {
+        if (tid == 0) set_err(err, DEV_CHOL);
+        return;
+    }
+    for (int j = tid; j < q; j += nt) { x[j] = 0.0; r[j] = -g[j]; bz[j] = (float)(-g[j]); }
+    __syncthreads();
+    chol_solve_blocked(L, rdiag, q, ld, bz);   // z = P r
+    for (int j = tid; j < q; j += nt) { z[j] = (double)bz[j]; pp[j] = z[j]; }
+    __syncthreads();
+    dots(r, r, r, z, r, r, 2);
+    double rz = 0.0;
+    if (tid == 0) {
+        double rr = 0.0, t = 0.0;
+        for (int w = 0; w < nwq; ++w) { rr += red[0][w]; t += red[1][w]; }
+        const double gn = sqrt(rr);
+        sc_tol = fmax(fmin(eta, pow(gn, 1.0 + tau)), 1e-14 * gn);
+        sc_rn = gn;
+        sc_al = t;   // rz
+        sc_go = gn > sc_tol;
+    }
+    __syncthreads();
+    rz = sc_al;
+    int it = 0;
+    while (sc_go && it < maxit) {
+        for (int j = tid; j < q; j += nt) {
+            const float hi = (float)pp[j];
+            pf[j] = make_float2(hi, (float)(pp[j] - (double)hi));
+        }
+        __syncthreads();
+        for (int i = warp; i < q; i += nw) {
+            float sh = 0.f, sc = 0.f;
+            const float2 *mrow = Mf + (size_t)i * q;
+            for (int j = lane; j < q; j += 32) {
+                const float2 a = mrow[j], bb = pf[j];
+                float p0, e0, sn, t0;
+                two_prod(a.x, bb.x, p0, e0);
+                e0 = fmaf(a.x, bb.y, fmaf(a.y, bb.x, e0));
+                two_sum(sh, p0, sn, t0);
+                sh = sn;
+                sc += t0 + e0;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float s2 = __shfl_xor_sync(0xffffffffu, sh, o), c2 = __shfl_xor_sync(0xffffffffu, sc, o);
+                float sn, e;
+                two_sum(sh, s2, sn, e);
+                e += sc + c2;
+                sh = sn + e;
+                sc = e - (sh - sn);
+            }
+            if (lane == 0) Ap[i] = (double)sh + (double)sc;
+        }
+        __syncthreads();
+        dots(pp, Ap, pp, pp, pp, pp, 1);
+        if (tid == 0) {
+            double pAp = 0.0;
+            for (int w = 0; w < nwq; ++w) pAp += red[0][w];
+            sc_go = pAp > 0.0;
+            sc_al = sc_go ? rz / pAp : 0.0;
+        }
+        __syncthreads();
+        if (!sc_go) break;
+        const double al = sc_al;
+        for (int j = tid; j < q; j += nt) {
+            x[j] = fma(al, pp[j], x[j]);
+            rold[j] = r[j];
+            r[j] = fma(-al, Ap[j], r[j]);
+            bz[j] = (float)r[j];
+        }
+        __syncthreads();
+        ++it;
+        dots(r, r, r, r, r, r, 1);
+        if (tid == 0) {
+            double rr = 0.0;
+            for (int w = 0; w < nwq; ++w) rr += red[0][w];
+            sc_rn = sqrt(rr);
+            sc_go = sc_rn > sc_tol;
+        }
+        __syncthreads();
+        if (!sc_go) break;
+        chol_solve_blocked(L, rdiag, q, ld, bz);
+        for (int j = tid; j < q; j += nt) z[j] = (double)bz[j];
+        __syncthreads();
+        // flexible (Polak-Ribiere) beta: robust to the FP32 preconditioner
+        dots(r, z, rold, z, r, r, 2);
+        if (tid == 0) {
+            double rzn = 0.0, rzo = 0.0;
+            for (int w = 0; w < nwq; ++w) { rzn += red[0][w]; rzo += red[1][w]; }
+            sc_beta = fmax(0.0, (rzn - rzo) / rz);
+            sc_al = rzn;
+        }
+        __syncthreads();
+        const double beta = sc_beta;
+        rz = sc_al;
+        for (int j = tid; j < q; j += nt) pp[j] = fma(beta, pp[j], z[j]);
+        __syncthreads();
+    }
+    for (int j = tid; j < q; j += nt) dv[j] = x[j];
+    if (tid == 0 && info) { info[0] = it; info[1] = sc_rn; info[2] = sc_shift; }
+}
+
+static int g_cgs_attr = 0;
+
 static int g_chol_smem_set = 0;
 static int g_pcg_smem_set = 0;
 
@@ -463,7 +789,7 @@ cudaError_t launch_newton(Work &W, const int32_t *J, long long p_host, const lon
     if (p_host <= 0) return launch_negcopy(W, g, dv);
     const int nt = (q + kGT - 1) / kGT;
     const int ntiles = nt * (nt + 1) / 2;
-    long long ks = (p_host + 255) / 256;
+    long long ks = (p_host + 31) / 32;   // split-K: ~32 gathered rows per block
     int KSmax = (int)(W.part_len / ((size_t)q * q + q));
     if (KSmax > 4 * W.nsm) KSmax = 4 * W.nsm;
     if (ks > KSmax) ks = KSmax;
@@ -484,29 +810,19 @@ cudaError_t launch_newton(Work &W, const int32_t *J, long long p_host, const lon
     W.nlaunch += 3;   // gram, build_m, and the solve below
     if (cg) {
         // FP32-Cholesky-preconditioned CG on the FP64 matrix (Algorithm 3's inexact solve)
-        const size_t vec = (size_t)6 * q * sizeof(double) + (size_t)q * sizeof(float2);
         double *info = W.red + 12;
-        const size_t smem_fac = vec + (size_t)q * (q + 1) * sizeof(float);
-        if (smem_fac <= (size_t)200 * 1024) {
-            const size_t smem = smem_fac;
-            if (!g_pcg_smem_set) {
-                cudaError_t ea = cudaSuccess;
-                ea = cudaFuncSetAttribute(newton_pcg_kernel<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-                if (ea == cudaSuccess) ea = cudaFuncSetAttribute(newton_pcg_kernel<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-                if (ea == cudaSuccess) ea = cudaFuncSetAttribute(newton_pcg_kernel<true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-                if (ea == cudaSuccess) ea = cudaFuncSetAttribute(newton_pcg_kernel<true, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        const size_t smem_new = (size_t)6 * q * sizeof(double) + (size_t)q * sizeof(float2) + (size_t)2 * q * sizeof(float) +
+                                16 + (size_t)q * (q + 1) * sizeof(float);
+        if (smem_new <= (size_t)200 * 1024) {
+            if (!g_cgs_attr) {
+                const cudaError_t ea = cudaFuncSetAttribute(newton_cg_smem_kernel,
+                                                            cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
                 if (ea != cudaSuccess) return ea;
-                g_pcg_smem_set = 1;
+                g_cgs_attr = 1;
             }
-            const int nr = (q + 31) / 32;
-#define PCG_CASE(R)                                                                                        \
-    if (nr <= R) {                                                                                         \
-        newton_pcg_kernel<true, R><<<1, 1024, smem, W.st>>>(q, W.M, W.Mf, nullptr, g, dv, W.eta, W.tau, W.cg_maxit,  \
-                                                            info, W.err);                                  \
-    } else
-            PCG_CASE(1) PCG_CASE(2) PCG_CASE(4) PCG_CASE(8) {}
-#undef PCG_CASE
+            newton_cg_smem_kernel<<<1, 1024, smem_new, W.st>>>(q, W.Mf, g, dv, W.eta, W.tau, W.cg_maxit, info, W.err);
         } else {
+            const size_t vec = (size_t)6 * q * sizeof(double) + (size_t)q * sizeof(float2);
             newton_pcg_kernel<false, 32><<<1, 1024, vec, W.st>>>(q, W.M, W.Mf, W.Lf, g, dv, W.eta, W.tau, W.cg_maxit,
                                                                  info, W.err);
         }

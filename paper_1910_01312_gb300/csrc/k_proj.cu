@@ -15,17 +15,22 @@
 // forced bisection every third pass, so the bracket shrinks geometrically.
 // The result is the same lambda-hat as Algorithm 2 up to rounding (and any
 // point of the flat piece when the root set is an interval; pi is the same
-// either way).  Ties follow the paper's clip: t >= C -> C,
-// t <= 0 -> 0, so J uses strict inequalities.
+// either way).  Ties follow the paper's clip: t >= C -> C, t <= 0 -> 0, so J
+// uses strict inequalities.
 //
-// Precision.  The plain form (MX = false) evaluates every component in FP64.
-// The mixed form (MX = true) keeps r_i = fl32(s_i - lambda_0) next to s_i and
-// classifies a component in FP32 whenever its clipped value is certainly 0 or
-// certainly C (|error| bound (|r| + |delta| + C) 2^-20); only the components
-// near a bound -- the free ones and the ambiguous ones -- are evaluated in
-// FP64.  Saturated components enter f through exact integer counts, and their
-// breakpoint distances enter the segment test as conservative (never too far)
-// bounds, so the exact-root test and every output are those of the FP64 form.
+// Precision.  The plain form (MX = false) reads FP64 vectors and evaluates
+// every component in FP64.  The mixed form (MX = true) reads its vectors as
+// double-float pairs (FP32 hi + lo, relative accuracy ~2^-48), forms u and
+// s_i = y_i u_i with FP32 error-free arithmetic, keeps r_i = fl32(s_i -
+// lambda_0), and classifies a component in FP32 whenever its clipped value is
+// certainly 0 or certainly C (|error| bound (|r| + |delta| + C) 2^-20).  Only
+// the components near a bound -- the free ones and the ambiguous ones -- are
+// evaluated in FP64, out of line.  Saturated components enter f through exact
+// integer counts and their breakpoint distances enter the segment test as
+// conservative (never too far) bounds, so the exact-root test and every output
+// are those of the FP64 form.  On this part one FP64 warp instruction holds
+// the SM's FP64 pipe ~16 cycles, so an FP64 operation per component costs
+// more than the whole FP32 pass.
 #include <math.h>
 
 #include "internal.cuh"
@@ -36,20 +41,21 @@ constexpr int kMaxPass = 256;
 constexpr int kPartStride = 8;   // doubles per block partial
 
 struct ProjArgs {
-    const double *a, *b;
+    const void *a, *b;       // FP64 (plain) or double-float float2 (mixed) n-vectors
     double c1, c2;
     const int8_t *y;
     long long n;
     double C;
     int sums;
     const double *lam0;
-    double *u_out, *pi_out;
+    void *u_out;             // FP64 (plain) or float2 (mixed)
+    double *pi_out;
     float2 *wpi_out;
     int32_t *J, *S;
     const double *pi_base;
-    const double *alpha;
-    double *part;      // [3][G][kPartStride]
-    int *cnt;          // [EPT][G][2]
+    const double *alpha;     // FP64 alpha (SF_DPA, SF_KKT)
+    double *part;            // [3][G][kPartStride]
+    int *cnt;                // [EPT][G][2]
     unsigned *bar;
     int *err;
     ProjOut *out;
@@ -60,61 +66,93 @@ struct PassAcc {
     int nup;            // (#upper with y=+1) - (#upper with y=-1): contributes C * nup
     int pp;             // free count just right of lambda
     int pm;             // free count just left of lambda
+    int ex;             // some component was evaluated in FP64
     float fdhi, fdlo;   // conservative breakpoint offsets of FP32-classified components
     double ddhi, ddlo;  // breakpoint offsets of FP64-evaluated components
 };
 
 __device__ __forceinline__ void acc_init(PassAcc &A)
 {
-    A.fex = 0.0; A.nup = 0; A.pp = 0; A.pm = 0;
+    A.fex = 0.0; A.nup = 0; A.pp = 0; A.pm = 0; A.ex = 0;
     A.fdhi = INFINITY; A.fdlo = -INFINITY; A.ddhi = INFINITY; A.ddlo = -INFINITY;
 }
 
-__device__ __forceinline__ void offset_in(PassAcc &A, double o)
-{
-    if (o > 0.0) A.ddhi = fmin(A.ddhi, o);
-    else if (o < 0.0) A.ddlo = fmax(A.ddlo, o);
-}
+// Exact FP64 evaluation of one component at lambda.  Out of line so that only
+// warps with such a component spend FP64 instructions on it.
+struct ExactOut {
+    double fex, dhi, dlo;
+    int nup, pp, pm;
+};
 
-// Exact FP64 evaluation of one component at lambda.
-__device__ __forceinline__ void eval_exact(double s, bool pos, double lam, double C, PassAcc &A)
+__device__ __noinline__ ExactOut eval_exact_ool(double s, bool pos, double lam, double C)
 {
+    ExactOut o;
     const double t = pos ? (s - lam) : (lam - s);
-    if (t >= C) A.nup += pos ? 1 : -1;
-    else if (t > 0.0) A.fex += pos ? t : -t;
+    o.nup = 0;
+    o.fex = 0.0;
+    if (t >= C) o.nup = pos ? 1 : -1;
+    else if (t > 0.0) o.fex = pos ? t : -t;
     const bool open = (t > 0.0) && (t < C);
     const bool at0 = (t == 0.0), atC = (t == C);
-    A.pp += (open || (pos ? atC : at0)) ? 1 : 0;
-    A.pm += (open || (pos ? at0 : atC)) ? 1 : 0;
+    o.pp = (open || (pos ? atC : at0)) ? 1 : 0;
+    o.pm = (open || (pos ? at0 : atC)) ? 1 : 0;
     // breakpoints at offsets (in lambda): y=+1: t, t - C;  y=-1: -t, C - t
-    offset_in(A, pos ? t : -t);
-    offset_in(A, pos ? t - C : C - t);
+    const double o1 = pos ? t : -t, o2 = pos ? t - C : C - t;
+    o.dhi = INFINITY;
+    o.dlo = -INFINITY;
+    if (o1 > 0.0) o.dhi = o1; else if (o1 < 0.0) o.dlo = o1;
+    if (o2 > 0.0) o.dhi = fmin(o.dhi, o2); else if (o2 < 0.0) o.dlo = fmax(o.dlo, o2);
+    return o;
 }
 
-// One component at lambda: in FP32 when it is certainly saturated (mixed
-// form), else exactly.  The FP32 path touches no FP64 instruction.
-template <bool MX>
-__device__ __forceinline__ void eval_comp(double s, float r, bool pos, double lam, float dl, double C,
-                                          float Cf, PassAcc &A)
+__device__ __forceinline__ void eval_exact(double s, bool pos, double lam, double C, PassAcc &A)
 {
-    if (MX) {
-        const float tf = pos ? (r - dl) : (dl - r);
-        const float er = (fabsf(r) + fabsf(dl) + Cf) * 9.5367431640625e-07f;   // 2^-20
-        if (tf > Cf + er) {
-            A.nup += pos ? 1 : -1;
-            // offsets t - C (y=+1, above) or C - t (y=-1, below), made nearer by er
-            if (pos) A.fdhi = fminf(A.fdhi, tf - Cf - er);
-            else A.fdlo = fmaxf(A.fdlo, Cf - tf + er);
-            return;
-        }
-        if (tf < -er) {
-            // offsets t (y=+1, below) or -t (y=-1, above)
-            if (pos) A.fdlo = fmaxf(A.fdlo, tf + er);
-            else A.fdhi = fminf(A.fdhi, -tf - er);
-            return;
-        }
+    const ExactOut o = eval_exact_ool(s, pos, lam, C);
+    A.nup += o.nup;
+    A.fex += o.fex;
+    A.pp += o.pp;
+    A.pm += o.pm;
+    A.ex = 1;
+    A.ddhi = fmin(A.ddhi, o.dhi);
+    A.ddlo = fmax(A.ddlo, o.dlo);
+}
+
+// double from a double-float pair (FP64; used only on the exact paths)
+__device__ __noinline__ double df2d(float2 v)
+{
+    return (double)v.x + (double)v.y;
+}
+
+// One component at lambda (mixed form): FP32 when certainly saturated.
+__device__ __forceinline__ void eval_comp_mx(float2 sdf, float r, bool pos, double lam, float dl, double C, float Cf,
+                                             PassAcc &A)
+{
+    const float tf = pos ? (r - dl) : (dl - r);
+    const float er = (fabsf(r) + fabsf(dl) + Cf) * 9.5367431640625e-07f;   // 2^-20
+    if (tf > Cf + er) {
+        A.nup += pos ? 1 : -1;
+        // offsets t - C (y=+1, above) or C - t (y=-1, below), made nearer by er
+        if (pos) A.fdhi = fminf(A.fdhi, tf - Cf - er);
+        else A.fdlo = fmaxf(A.fdlo, Cf - tf + er);
+        return;
     }
-    eval_exact(s, pos, lam, C, A);
+    if (tf < -er) {
+        // offsets t (y=+1, below) or -t (y=-1, above)
+        if (pos) A.fdlo = fmaxf(A.fdlo, tf + er);
+        else A.fdhi = fminf(A.fdhi, -tf - er);
+        return;
+    }
+    eval_exact(df2d(sdf), pos, lam, C, A);
+}
+
+// pi component in FP64 and its class (0: = 0, 1: free, 2: = C), out of line
+__device__ __noinline__ double clip_exact_ool(double s, bool pos, double lam, double C, int &pc)
+{
+    const double t = pos ? (s - lam) : (lam - s);
+    if (t >= C) { pc = 2; return C; }
+    if (t <= 0.0) { pc = 0; return 0.0; }
+    pc = 1;
+    return t;
 }
 
 // Fixed-order reduction of the G block partials of one slot; every block
@@ -123,7 +161,6 @@ __device__ __forceinline__ void reduce_partials(const double *slot, int G, doubl
 {
     const int lane = threadIdx.x & 31;
     double F = 0.0, nu = 0.0, pp = 0.0, pm = 0.0, dh = INFINITY, dlo = -INFINITY;
-    // all loads of a lane are independent: issue them together
 #pragma unroll 8
     for (int bb = lane; bb < G; bb += 32) {
         const double *p = slot + (size_t)bb * kPartStride;
@@ -142,6 +179,29 @@ __device__ __forceinline__ double flip_sign(double x, bool neg)
     return neg ? __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ULL) : x;
 }
 
+// double-float helpers (FP32 error-free transformations)
+__device__ __forceinline__ float2 dfx_add(float2 a, float2 b)
+{
+    float s, e;
+    two_sum(a.x, b.x, s, e);
+    e += a.y + b.y;
+    const float hi = s + e;
+    return make_float2(hi, e - (hi - s));
+}
+__device__ __forceinline__ float2 dfx_mul(float2 a, float2 b)
+{
+    float p, e;
+    two_prod(a.x, b.x, p, e);
+    e = fmaf(a.x, b.y, fmaf(a.y, b.x, e));
+    const float hi = p + e;
+    return make_float2(hi, e - (hi - p));
+}
+__device__ __forceinline__ float2 dfx_split(double v)
+{
+    const float hi = (float)v;
+    return make_float2(hi, (float)(v - (double)hi));
+}
+
 template <int EPT, bool MX>
 __global__ void __launch_bounds__(kTPB, EPT >= 16 ? 1 : 2) proj_kernel(ProjArgs A)
 {
@@ -151,30 +211,54 @@ __global__ void __launch_bounds__(kTPB, EPT >= 16 ? 1 : 2) proj_kernel(ProjArgs 
     const double C = A.C;
     const float Cf = (float)C;
 
-    double lam0 = A.lam0 ? __ldcg(A.lam0) : 0.0;
-    if (!isfinite(lam0)) lam0 = 0.0;
+    // Warm start lambda_0 and the FP32 splits of the scalars: computed by one
+    // thread per block and broadcast (scalar FP64 in every thread is costly).
+    __shared__ double sh_lam0;
+    __shared__ float2 sh_c1, sh_c2, sh_l0;
+    if (tid == 0) {
+        double l0 = A.lam0 ? __ldcg(A.lam0) : 0.0;
+        if (!isfinite(l0)) l0 = 0.0;
+        sh_lam0 = l0;
+        if (MX) { sh_c1 = dfx_split(A.c1); sh_c2 = dfx_split(A.c2); sh_l0 = dfx_split(l0); }
+    }
+    __syncthreads();
+    const double lam0 = sh_lam0;
 
-    double s[EPT];
+    double sd[MX ? 1 : EPT];      // plain: s_i in FP64
+    float2 sf[MX ? EPT : 1];      // mixed: s_i as a double-float pair
     float r[EPT];
     unsigned posm = 0u, valm = 0u;
+    {
+        const float2 c1f = sh_c1, c2f = sh_c2, l0f = sh_l0;
 #pragma unroll
-    for (int k = 0; k < EPT; ++k) {
-        const long long i = k * NT + (long long)blk * kTPB + tid;
-        s[k] = 0.0;
-        r[k] = 0.f;
-        if (i < A.n) {
-            double u = A.a[i] + A.c2;
-            if (A.b) u = fma(A.c1, A.b[i], u);
-            const bool pos = A.y[i] > 0;
-            s[k] = flip_sign(u, !pos);
-            if (MX) r[k] = (float)(s[k] - lam0);
-            posm |= (pos ? 1u : 0u) << k;
-            valm |= 1u << k;
+        for (int k = 0; k < EPT; ++k) {
+            const long long i = k * NT + (long long)blk * kTPB + tid;
+            r[k] = 0.f;
+            if (MX) sf[k] = make_float2(0.f, 0.f);
+            else sd[MX ? 0 : k] = 0.0;
+            if (i < A.n) {
+                const bool pos = A.y[i] > 0;
+                if (MX) {
+                    float2 u = reinterpret_cast<const float2 *>(A.a)[i];
+                    if (A.b) u = dfx_add(u, dfx_mul(c1f, reinterpret_cast<const float2 *>(A.b)[i]));
+                    u = dfx_add(u, c2f);
+                    if (!pos) { u.x = -u.x; u.y = -u.y; }
+                    sf[MX ? k : 0] = u;
+                    r[k] = (u.x - l0f.x) + (u.y - l0f.y);
+                } else {
+                    double u = reinterpret_cast<const double *>(A.a)[i] + A.c2;
+                    if (A.b) u = fma(A.c1, reinterpret_cast<const double *>(A.b)[i], u);
+                    sd[MX ? 0 : k] = flip_sign(u, !pos);
+                }
+                posm |= (pos ? 1u : 0u) << k;
+                valm |= 1u << k;
+            }
         }
     }
 
     __shared__ double sh_d[kWarps][6];
     __shared__ double sh_lam;
+    __shared__ float sh_dl;
     __shared__ int sh_done;
 
     // root-search state, kept in shared memory (only warp 0 lane 0 updates it)
@@ -183,7 +267,9 @@ __global__ void __launch_bounds__(kTPB, EPT >= 16 ? 1 : 2) proj_kernel(ProjArgs 
     if (tid == 0) {
         st_L = -INFINITY; st_U = INFINITY; st_FL = 0.0; st_FU = 0.0;   // bracket: f(L) > 0 > f(U)
         st_last_step = 0.0; st_last_dir = 0; st_nbr = 0;
+        sh_dl = 0.f;
     }
+    __syncthreads();
     double lam = lam0;
     double lam_hat = lam;
     int pass = 0;
@@ -192,17 +278,35 @@ __global__ void __launch_bounds__(kTPB, EPT >= 16 ? 1 : 2) proj_kernel(ProjArgs 
     for (;;) {
         PassAcc acc;
         acc_init(acc);
-        const float dl = MX ? (float)(lam - lam0) : 0.f;
+        const float dl = sh_dl;   // fl32(lam - lam0)
 #pragma unroll
-        for (int k = 0; k < EPT; ++k)
-            if ((valm >> k) & 1u) eval_comp<MX>(s[k], r[k], (posm >> k) & 1u, lam, dl, C, Cf, acc);
+        for (int k = 0; k < EPT; ++k) {
+            if ((valm >> k) & 1u) {
+                if (MX) eval_comp_mx(sf[MX ? k : 0], r[k], (posm >> k) & 1u, lam, dl, C, Cf, acc);
+                else eval_exact(sd[MX ? 0 : k], (posm >> k) & 1u, lam, C, acc);
+            }
+        }
         {
-            const double fex = warp_sum(acc.fex);
             const int nup = __reduce_add_sync(0xffffffffu, acc.nup);
             const int pp = __reduce_add_sync(0xffffffffu, acc.pp);
             const int pm = __reduce_add_sync(0xffffffffu, acc.pm);
-            const double dh = warp_min(fmin(acc.ddhi, (double)acc.fdhi));
-            const double dlw = warp_max(fmax(acc.ddlo, (double)acc.fdlo));
+            // FP64 reductions only in warps where some lane evaluated a component
+            // exactly (in the mixed form most warps have none)
+            double fex = 0.0, dh, dlw;
+            if (__any_sync(0xffffffffu, acc.ex)) {
+                fex = warp_sum(acc.fex);
+                dh = warp_min(fmin(acc.ddhi, (double)acc.fdhi));
+                dlw = warp_max(fmax(acc.ddlo, (double)acc.fdlo));
+            } else {
+                float fh = acc.fdhi, fl = acc.fdlo;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    fh = fminf(fh, __shfl_xor_sync(0xffffffffu, fh, o));
+                    fl = fmaxf(fl, __shfl_xor_sync(0xffffffffu, fl, o));
+                }
+                dh = (double)fh;
+                dlw = (double)fl;
+            }
             if (lane == 0) {
                 sh_d[warp][0] = fex; sh_d[warp][1] = (double)nup; sh_d[warp][2] = (double)pp;
                 sh_d[warp][3] = (double)pm; sh_d[warp][4] = dh; sh_d[warp][5] = dlw;
@@ -285,6 +389,7 @@ __global__ void __launch_bounds__(kTPB, EPT >= 16 ? 1 : 2) proj_kernel(ProjArgs 
                 }
                 sh_done = done;
                 sh_lam = done ? lam_hat : next;
+                sh_dl = (float)((done ? lam_hat : next) - lam0);
             }
         }
         __syncthreads();
@@ -295,11 +400,18 @@ __global__ void __launch_bounds__(kTPB, EPT >= 16 ? 1 : 2) proj_kernel(ProjArgs 
 
     // ---------------- final phase: pi, sums, compaction ----------------
     const double lh = lam_hat;
-    const float dlh = MX ? (float)(lh - lam0) : 0.f;
+    const float dlh = sh_dl;   // fl32(lam_hat - lam0)
     const float2 Csplit = make_float2(Cf, (float)(C - (double)Cf));
     const long long Cbits = __double_as_longlong(C);
-    double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0, accu = 0.0;
-    unsigned isJ = 0u, isS = 0u;   // bit k: component k is in J / S
+    __shared__ float2 sh_lh;
+    if (MX && tid == 0) sh_lh = dfx_split(lh);
+    __syncthreads();
+    const float2 lhf = sh_lh;
+    double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
+    float2 du = make_float2(0.f, 0.f);    // double-float sum of (u - ub) over components at C in both
+    float2 hg = make_float2(0.f, 0.f);    // double-float hinge sum (mixed KKT)
+    int nupc = 0;                         // alpha components at C (mixed KKT)
+    unsigned isJ = 0u, isS = 0u;          // bit k: component k is in J / S
 #pragma unroll
     for (int k = 0; k < EPT; ++k) {
         if (!((valm >> k) & 1u)) continue;
@@ -318,22 +430,21 @@ __global__ void __launch_bounds__(kTPB, EPT >= 16 ? 1 : 2) proj_kernel(ProjArgs 
         } else if (cls == 0) {
             pk = 0.0; pc = 0;
         } else {
-            const double t = pos ? (s[k] - lh) : (lh - s[k]);
-            if (t >= C) { pk = C; pc = 2; }
-            else if (t <= 0.0) { pk = 0.0; pc = 0; }
-            else { pk = t; pc = 1; isJ |= 1u << k; }
+            pk = clip_exact_ool(MX ? df2d(sf[MX ? k : 0]) : sd[MX ? 0 : k], pos, lh, C, pc);
+            if (pc == 1) isJ |= 1u << k;
         }
         if (pc) isS |= 1u << k;
-        const double u = flip_sign(s[k], !pos);
         if (A.pi_out) A.pi_out[i] = pk;
-        if (A.u_out) A.u_out[i] = u;
-        if (A.wpi_out) {
-            float2 wv;
-            if (pc == 2) wv = Csplit;
-            else if (pc == 0) wv = make_float2(0.f, 0.f);
-            else { wv.x = (float)pk; wv.y = (float)(pk - (double)wv.x); }
-            if (!pos) { wv.x = -wv.x; wv.y = -wv.y; }
-            A.wpi_out[i] = wv;
+        float2 pkf = make_float2(0.f, 0.f);
+        if (A.wpi_out) pkf = (pc == 2) ? Csplit : ((pc == 0) ? pkf : dfx_split(pk));
+        if (A.wpi_out) A.wpi_out[i] = pos ? pkf : make_float2(-pkf.x, -pkf.y);
+        float2 uf = make_float2(0.f, 0.f);
+        if (MX) {
+            uf = sf[MX ? k : 0];
+            if (!pos) { uf.x = -uf.x; uf.y = -uf.y; }
+            if (A.u_out) reinterpret_cast<float2 *>(A.u_out)[i] = uf;
+        } else if (A.u_out) {
+            reinterpret_cast<double *>(A.u_out)[i] = flip_sign(sd[MX ? 0 : k], !pos);
         }
         if (A.sums & SF_DPA) {
             // |pi - alpha|^2: only components that moved need FP64
@@ -349,32 +460,61 @@ __global__ void __launch_bounds__(kTPB, EPT >= 16 ? 1 : 2) proj_kernel(ProjArgs 
             const long long pbb = __double_as_longlong(pb);
             const int pbc = (pbb == Cbits) ? 2 : ((pbb << 1) == 0 ? 0 : 1);
             if (pc == 2 && pbc == 2) {
-                accu += u - A.a[i];                    // 2C(u - ub), factor applied below
+                // 2C(u - ub), factor applied below
+                if (MX) {
+                    const float2 ub = reinterpret_cast<const float2 *>(A.a)[i];
+                    du = dfx_add(du, make_float2(uf.x - ub.x, uf.y - ub.y));
+                } else {
+                    acc2 += flip_sign(sd[MX ? 0 : k], !pos) - reinterpret_cast<const double *>(A.a)[i];
+                }
             } else if (pc != 0 || pbc != 0) {
-                const double ub = A.a[i];
+                const double u = MX ? df2d(uf) : flip_sign(sd[MX ? 0 : k], !pos);
+                const double ub = MX ? df2d(reinterpret_cast<const float2 *>(A.a)[i])
+                                     : reinterpret_cast<const double *>(A.a)[i];
                 acc1 += pk * (2.0 * u - pk) - pb * (2.0 * ub - pb);
             }
         }
         if (A.sums & SF_KKT) {
-            const double al = A.a[i];
-            const double d = al - pk;
-            acc0 = fma(d, d, acc0);
-            acc1 = fma(al, al, acc1);
-            acc2 += al;
-            const double marg = A.b[i] + (pos ? lh : -lh);
-            acc3 += fmax(0.0, 1.0 - marg);
+            const double al = A.alpha[i];
+            const long long ab = __double_as_longlong(al);
+            if (ab != __double_as_longlong(pk)) {
+                const double d = al - pk;
+                acc0 = fma(d, d, acc0);
+            }
+            if (ab == Cbits) ++nupc;
+            else if ((ab << 1) != 0) { acc1 = fma(al, al, acc1); acc2 += al; }
+            // hinge max(0, 1 - (Qalpha_i + y_i lambda))
+            if (MX) {
+                const float2 qa = reinterpret_cast<const float2 *>(A.b)[i];
+                const float2 m = dfx_add(qa, pos ? lhf : make_float2(-lhf.x, -lhf.y));
+                const float2 h = dfx_add(make_float2(1.f, 0.f), make_float2(-m.x, -m.y));
+                if (h.x > 0.f) hg = dfx_add(hg, h);
+            } else {
+                const double marg = reinterpret_cast<const double *>(A.b)[i] + (pos ? lh : -lh);
+                acc3 += fmax(0.0, 1.0 - marg);
+            }
         }
     }
-    if (A.sums & SF_PSID) acc1 = fma(2.0 * C, accu, acc1);
+    if (A.sums & SF_PSID) acc1 = fma(2.0 * C, acc2 + ((double)du.x + (double)du.y), acc1);
+    if (A.sums & SF_KKT) {
+        acc1 = fma((double)nupc * C, C, acc1);
+        acc2 = fma((double)nupc, C, acc2);
+        if (MX) acc3 = (double)hg.x + (double)hg.y;
+    } else {
+        acc2 = 0.0;
+    }
     // per-(k, warp) compaction counts
     __shared__ int sh_wc[EPT][kWarps][2];
 #pragma unroll
     for (int k = 0; k < EPT; ++k) {
-        unsigned bj = __ballot_sync(0xffffffffu, (isJ >> k) & 1u);
-        unsigned bs = __ballot_sync(0xffffffffu, (isS >> k) & 1u);
+        const unsigned bj = __ballot_sync(0xffffffffu, (isJ >> k) & 1u);
+        const unsigned bs = __ballot_sync(0xffffffffu, (isS >> k) & 1u);
         if (lane == 0) { sh_wc[k][warp][0] = __popc(bj); sh_wc[k][warp][1] = __popc(bs); }
     }
-    acc0 = warp_sum(acc0); acc1 = warp_sum(acc1); acc2 = warp_sum(acc2); acc3 = warp_sum(acc3);
+    // reduce only the sums this launch asks for (FP64 shuffles are costly here)
+    if (A.sums & (SF_DPA | SF_KKT)) acc0 = warp_sum(acc0);
+    if (A.sums & (SF_PSID | SF_KKT)) acc1 = warp_sum(acc1);
+    if (A.sums & SF_KKT) { acc2 = warp_sum(acc2); acc3 = warp_sum(acc3); }
     if (lane == 0) { sh_d[warp][0] = acc0; sh_d[warp][1] = acc1; sh_d[warp][2] = acc2; sh_d[warp][3] = acc3; }
     __syncthreads();
     if (tid < EPT) {
@@ -441,6 +581,16 @@ __global__ void __launch_bounds__(kTPB, EPT >= 16 ? 1 : 2) proj_kernel(ProjArgs 
             sh_off[k][0] = oj; sh_off[k][1] = os;
         }
     }
+    // exclusive prefix of the per-warp counts, one thread per (k, list)
+    for (int t = tid; t < 2 * EPT; t += kTPB) {
+        const int k = t >> 1, l = t & 1;
+        int run = 0;
+        for (int w = 0; w < kWarps; ++w) {
+            const int c = sh_wc[k][w][l];
+            sh_wc[k][w][l] = run;
+            run += c;
+        }
+    }
     __syncthreads();
     if (A.J || A.S) {
         const unsigned lt = (1u << lane) - 1u;
@@ -449,13 +599,12 @@ __global__ void __launch_bounds__(kTPB, EPT >= 16 ? 1 : 2) proj_kernel(ProjArgs 
             const long long i = k * NT + (long long)blk * kTPB + tid;
             const unsigned bj = __ballot_sync(0xffffffffu, (isJ >> k) & 1u);
             const unsigned bs = __ballot_sync(0xffffffffu, (isS >> k) & 1u);
-            int wj = 0, ws = 0;
-            for (int w = 0; w < warp; ++w) { wj += sh_wc[k][w][0]; ws += sh_wc[k][w][1]; }
-            if (A.J && ((isJ >> k) & 1u)) A.J[sh_off[k][0] + wj + __popc(bj & lt)] = (int32_t)i;
-            if (A.S && ((isS >> k) & 1u)) A.S[sh_off[k][1] + ws + __popc(bs & lt)] = (int32_t)i;
+            if (A.J && ((isJ >> k) & 1u)) A.J[sh_off[k][0] + sh_wc[k][warp][0] + __popc(bj & lt)] = (int32_t)i;
+            if (A.S && ((isS >> k) & 1u)) A.S[sh_off[k][1] + sh_wc[k][warp][1] + __popc(bs & lt)] = (int32_t)i;
         }
     }
 }
+
 
 static const int kEpts[] = {1, 2, 4, 8, 16, 32};
 
@@ -501,12 +650,13 @@ cudaError_t launch_project(Work &W, const ProjIn &in, ProjOut *out)
     ProjArgs A;
     A.a = in.a; A.b = in.b; A.c1 = in.c1; A.c2 = in.c2;
     A.y = W.y; A.n = W.n; A.C = W.C; A.sums = in.sums; A.lam0 = in.lam0;
-    A.u_out = in.u_out; A.pi_out = in.pi_out; A.wpi_out = in.wpi_out; A.J = in.J; A.S = in.S;
+    A.u_out = in.u_out; A.pi_out = in.pi_out; A.wpi_out = in.wpi_out;
+    A.J = in.J; A.S = in.S;
     A.pi_base = in.pi_base; A.alpha = in.alpha;
     A.part = W.part; A.cnt = W.cnt; A.bar = W.bar; A.err = W.err; A.out = out;
     void *args[] = {&A};
     ++W.nlaunch;
-    void *fn = W.precision == 1 ? kernel_for<true>(W.proj_ept) : kernel_for<false>(W.proj_ept);
+    void *fn = in.mixed ? kernel_for<true>(W.proj_ept) : kernel_for<false>(W.proj_ept);
     return cudaLaunchCooperativeKernel(fn, dim3(W.proj_grid), dim3(kTPB), args, 0, W.st);
 }
 

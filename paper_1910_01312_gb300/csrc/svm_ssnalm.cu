@@ -138,12 +138,13 @@ extern "C" const char *svm_ssnalm_last_error(const svm_ssnalm_t *h)
 
 static void free_work(Work &W)
 {
-    void *ptrs[] = {W.alpha, W.z, W.dz, W.qa, W.tmpn, W.v, W.dv, W.g, W.atp, W.atp2, W.h, W.w, W.tmpq, W.M, W.Lf, W.Mf,
-                    W.part, W.cnt, W.bar, W.rm_counter, W.err, W.pout, W.red, W.X_own, W.y_own};
+    void *ptrs[] = {W.alpha, W.z, W.dz, W.qa, W.tmpn, W.zf, W.dzf, W.qaf, W.alphaf, W.v, W.dv, W.g, W.atp, W.atp2,
+                    W.h, W.w, W.tmpq, W.M, W.Lf, W.Mf, W.part, W.cnt, W.bar, W.rm_counter, W.err, W.pout, W.red,
+                    W.X_own, W.y_own};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (int b = 0; b < 2; ++b) {
-        void *pp[] = {W.pb[b].u, W.pb[b].pi, W.pb[b].wpi, W.pb[b].J, W.pb[b].S};
+        void *pp[] = {W.pb[b].u, W.pb[b].uf, W.pb[b].pi, W.pb[b].wpi, W.pb[b].J, W.pb[b].S};
         for (void *p : pp)
             if (p) cudaFree(p);
     }
@@ -251,6 +252,8 @@ extern "C" svm_status svm_ssnalm_create(svm_ssnalm_t **out, const svm_problem *p
         W.y = prob->y;
     }
     if ((uintptr_t)W.X % 16 != 0) return fail(SVM_ERR_INVALID_ARG, "X must be 16-byte aligned");
+    // double-float n-vectors wherever the mixed-form matvec applies (FP32 X, q % 4 == 0)
+    W.df = W.precision == SVM_PREC_MIXED && W.xf32 && q % 4 == 0;
     // workspace
     W.rm_grid = W.nsm * 4;
     // Gram split-K partials: at most 32 MiB (at least one q x q partial)
@@ -261,13 +264,16 @@ extern "C" svm_status svm_ssnalm_create(svm_ssnalm_t **out, const svm_problem *p
     const size_t part_proj = (size_t)3 * 8 * 4 * W.nsm * 4;
     W.part_len = part_gram > part_rm ? part_gram : part_rm;
     if (W.part_len < part_proj) W.part_len = part_proj;
-    bool bad = dalloc(&W.alpha, n) || dalloc(&W.z, n) || dalloc(&W.dz, n) || dalloc(&W.qa, n) ||
-               dalloc(&W.tmpn, n) || dalloc(&W.v, q) || dalloc(&W.dv, q) || dalloc(&W.g, q) ||
+    bool bad = dalloc(&W.alpha, n) || dalloc(&W.qa, n) || dalloc(&W.tmpn, n) ||
+               (W.df ? (dalloc(&W.zf, n) || dalloc(&W.dzf, n) || dalloc(&W.qaf, n) || dalloc(&W.alphaf, n))
+                     : (dalloc(&W.z, n) || dalloc(&W.dz, n))) ||
+               dalloc(&W.v, q) || dalloc(&W.dv, q) || dalloc(&W.g, q) ||
                dalloc(&W.atp, q) || dalloc(&W.atp2, q) || dalloc(&W.h, q) || dalloc(&W.w, q) || dalloc(&W.tmpq, q) ||
                dalloc(&W.M, q * q) || dalloc(&W.Lf, q * (q + 1)) || dalloc(&W.Mf, q * q) || dalloc(&W.part, W.part_len) || dalloc(&W.bar, 4) || dalloc(&W.rm_counter, 4) || dalloc(&W.err, 4) ||
                dalloc(&W.pout, 4) || dalloc(&W.red, 16);
     for (int b = 0; b < 2 && !bad; ++b)
-        bad = dalloc(&W.pb[b].u, n) || dalloc(&W.pb[b].pi, n) || dalloc(&W.pb[b].wpi, n) ||
+        bad = (W.df ? dalloc(&W.pb[b].uf, n) : dalloc(&W.pb[b].u, n)) || dalloc(&W.pb[b].pi, n) ||
+              dalloc(&W.pb[b].wpi, n) ||
               dalloc(&W.pb[b].J, n) || dalloc(&W.pb[b].S, n);
     if (bad) return fail(SVM_ERR_OOM, "device workspace allocation failed");
     if (cudaMallocHost(&W.h_pout, 4 * sizeof(ProjOut)) != cudaSuccess ||
@@ -331,13 +337,17 @@ static svm_status sync_read(svm_ssnalm *h)
 // ProjOut slots: 0 step-level op, 1 + b for projection buffer b, 3 KKT.
 enum { SLOT_OP = 0, SLOT_KKT = 3 };
 
-// The KKT projection of eq. (4.1) at alpha given Q alpha in W.qa.
-static svm_status kkt_project(svm_ssnalm *h, const double *alpha)
+// The KKT projection of eq. (4.1) at alpha given Q alpha: from W.alphaf and
+// W.qaf (double-float) when df, else from alpha and W.qa (FP64).
+static svm_status kkt_project(svm_ssnalm *h, const double *alpha, bool df)
 {
     Work &W = h->W;
     ProjIn in;
-    in.a = alpha; in.b = W.qa; in.c1 = -1.0; in.c2 = 1.0;
-    in.sums = SF_KKT;
+    in.mixed = df;
+    in.a = df ? (const void *)W.alphaf : (const void *)alpha;
+    in.b = df ? (const void *)W.qaf : (const void *)W.qa;
+    in.c1 = -1.0; in.c2 = 1.0;
+    in.sums = SF_KKT; in.alpha = alpha;
     in.lam0 = &W.pout[SLOT_KKT].lam;
     CK(timed(h, TK_PROJ, [&] { return launch_project(W, in, &W.pout[SLOT_KKT]); }));
     return SVM_OK;
@@ -346,12 +356,6 @@ static svm_status kkt_project(svm_ssnalm *h, const double *alpha)
 static double kkt_value(const ProjOut &o)
 {
     return sqrt(o.sum[0]) / (1.0 + sqrt(o.sum[1]));
-}
-
-__global__ void copy_kernel(long long n, const double *a, double *b)
-{
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        b[i] = a[i];
 }
 
 // red[0] += #{0 < a < C}, red[1] += #{a >= C}, red[2] += #{a > 0}
@@ -413,7 +417,7 @@ extern "C" svm_status svm_ssnalm_solve(svm_ssnalm_t *h, const double *alpha0, sv
     const bool host_mem = h->prob.memory == SVM_MEM_HOST;
     const long long n = W.n;
     const int q = (int)W.q;
-    const int nblk_n = (int)((n + 1023) / 1024 < W.nsm * 4 ? (n + 1023) / 1024 : W.nsm * 4);
+    const bool df = W.df;
     svm_status st;
     h->err.clear();
 
@@ -452,17 +456,28 @@ extern "C" svm_status svm_ssnalm_solve(svm_ssnalm_t *h, const double *alpha0, sv
         ++W.nlaunch;
         CK(cudaGetLastError());
         // Q alpha = A w and z = A v (equal here) in one pass
-        CK(timed(h, TK_MATVEC, [&] { return launch_matvec(W, W.w, W.qa, W.v, W.z); }));
+        if (df) {
+            CK(launch_unsign_df(W, W.pb[0].wpi, W.alphaf));
+            CK(timed(h, TK_MATVEC, [&] { return launch_matvec_df(W, W.w, W.qaf, W.v, W.zf); }));
+        } else {
+            CK(timed(h, TK_MATVEC, [&] { return launch_matvec(W, W.w, W.qa, W.v, W.z); }));
+        }
         CK(cudaMemsetAsync(W.pout, 0, sizeof(ProjOut), W.st));
     } else {
         CK(cudaMemsetAsync(W.alpha, 0, n * sizeof(double), W.st));
         CK(cudaMemsetAsync(W.v, 0, q * sizeof(double), W.st));
         CK(cudaMemsetAsync(W.w, 0, q * sizeof(double), W.st));
-        CK(cudaMemsetAsync(W.qa, 0, n * sizeof(double), W.st));
-        CK(cudaMemsetAsync(W.z, 0, n * sizeof(double), W.st));
+        if (df) {
+            CK(cudaMemsetAsync(W.alphaf, 0, n * sizeof(float2), W.st));
+            CK(cudaMemsetAsync(W.qaf, 0, n * sizeof(float2), W.st));
+            CK(cudaMemsetAsync(W.zf, 0, n * sizeof(float2), W.st));
+        } else {
+            CK(cudaMemsetAsync(W.qa, 0, n * sizeof(double), W.st));
+            CK(cudaMemsetAsync(W.z, 0, n * sizeof(double), W.st));
+        }
     }
     double sigma = P.sigma0;
-    if ((st = kkt_project(h, W.alpha)) != SVM_OK) return st;
+    if ((st = kkt_project(h, W.alpha, df)) != SVM_OK) return st;
     if ((st = sync_read(h)) != SVM_OK) return st;
     double R = kkt_value(W.h_pout[SLOT_KKT]), Rprev = R;
     svm_status status = SVM_ERR_NOT_CONVERGED;
@@ -475,10 +490,13 @@ extern "C" svm_status svm_ssnalm_solve(svm_ssnalm_t *h, const double *alpha0, sv
         {
             ProjBuf &B = W.pb[cur];
             ProjIn in;
-            in.a = W.alpha; in.b = W.z; in.c1 = -sigma; in.c2 = sigma;
+            in.mixed = df;
+            in.a = df ? (const void *)W.alphaf : (const void *)W.alpha;
+            in.b = df ? (const void *)W.zf : (const void *)W.z;
+            in.c1 = -sigma; in.c2 = sigma;
             in.sums = SF_DPA; in.alpha = W.alpha;
             in.lam0 = &W.pout[1 + cur].lam;
-            in.u_out = B.u; in.pi_out = B.pi; in.wpi_out = B.wpi; in.J = B.J; in.S = B.S;
+            in.u_out = df ? (void *)B.uf : (void *)B.u; in.pi_out = B.pi; in.wpi_out = B.wpi; in.J = B.J; in.S = B.S;
             CK(timed(h, TK_PROJ, [&] { return launch_project(W, in, &W.pout[1 + cur]); }));
             // g = v - A'pi (eq. (3.10) in q coordinates) and its roundoff scale
             CK(timed(h, TK_RMATVEC, [&] {
@@ -502,7 +520,8 @@ extern "C" svm_status svm_ssnalm_solve(svm_ssnalm_t *h, const double *alpha0, sv
             // Algorithm 3, Step 1: Newton direction on the free set J
             const long long p = m.p;
             CK(timed(h, TK_NEWTON, [&] { return launch_newton(W, W.pb[cur].J, p, &W.pout[1 + cur].p, sigma, W.g, W.dv); }));
-            CK(timed(h, TK_MATVEC, [&] { return launch_matvec(W, W.dv, W.dz); }));   // A dv = Q d
+            // A dv = Q d
+            CK(timed(h, TK_MATVEC, [&] { return df ? launch_matvec_df(W, W.dv, W.dzf) : launch_matvec(W, W.dv, W.dz); }));
             CK(launch_dots(W));
             // Step 2: Armijo line search.  Each trial projects u - t sigma A dv into the
             // other buffer and, speculatively, forms the gradient there, so an accepted
@@ -513,10 +532,13 @@ extern "C" svm_status svm_ssnalm_solve(svm_ssnalm_t *h, const double *alpha0, sv
             for (int mtr = 0; mtr < P.max_ls; ++mtr) {
                 ProjBuf &B = W.pb[nxt];
                 ProjIn tr;
-                tr.a = W.pb[cur].u; tr.b = W.dz; tr.c1 = -t * sigma; tr.c2 = 0.0;
+                tr.mixed = df;
+                tr.a = df ? (const void *)W.pb[cur].uf : (const void *)W.pb[cur].u;
+                tr.b = df ? (const void *)W.dzf : (const void *)W.dz;
+                tr.c1 = -t * sigma; tr.c2 = 0.0;
                 tr.sums = SF_PSID | SF_DPA; tr.alpha = W.alpha; tr.pi_base = W.pb[cur].pi;
                 tr.lam0 = &W.pout[1 + cur].lam;
-                tr.u_out = B.u; tr.pi_out = B.pi; tr.wpi_out = B.wpi; tr.J = B.J; tr.S = B.S;
+                tr.u_out = df ? (void *)B.uf : (void *)B.u; tr.pi_out = B.pi; tr.wpi_out = B.wpi; tr.J = B.J; tr.S = B.S;
                 CK(timed(h, TK_PROJ, [&] { return launch_project(W, tr, &W.pout[1 + nxt]); }));
                 CK(timed(h, TK_RMATVEC, [&] {
                     return launch_rmatvec(W, B.pi, B.wpi, B.S, &W.pout[1 + nxt].s, W.atp2, 1);
@@ -534,9 +556,9 @@ extern "C" svm_status svm_ssnalm_solve(svm_ssnalm_t *h, const double *alpha0, sv
                 t *= P.delta;
             }
             if (!accepted) break;   // line search failed: the subproblem ends at the current point
-            // Step 3
+            // Step 3 (z = A v is not read again before it is recomputed after the
+            // inner loop: the trials project from the accepted point's u)
             CK(launch_vaxpy(W, t));
-            CK(launch_zaxpy(W, t));
             copyq_kernel<<<1, 1024, 0, W.st>>>(q, W.tmpq, W.g);
             ++W.nlaunch;
             CK(cudaGetLastError());
@@ -544,14 +566,18 @@ extern "C" svm_status svm_ssnalm_solve(svm_ssnalm_t *h, const double *alpha0, sv
             cur = nxt;
         }
         inner_total += j;
-        // alpha^{k+1} = Pi(u(w^{k+1}))  (eq. (3.5)); A'alpha^{k+1} is the last A'pi
-        copy_kernel<<<nblk_n, 1024, 0, W.st>>>(n, W.pb[cur].pi, W.alpha);
+        // alpha^{k+1} = Pi(u(w^{k+1}))  (eq. (3.5)): the buffer holding pi becomes
+        // alpha (the old alpha buffer takes its place); A'alpha^{k+1} is the last A'pi
+        std::swap(W.alpha, W.pb[cur].pi);
+        if (df) CK(launch_unsign_df(W, W.pb[cur].wpi, W.alphaf));
         copyq_kernel<<<1, 1024, 0, W.st>>>(q, W.atp, W.w);
-        W.nlaunch += 2;
+        ++W.nlaunch;
         CK(cudaGetLastError());
         // Q alpha = A w for the KKT test and z = A v for the next subproblem, one pass
-        CK(timed(h, TK_MATVEC, [&] { return launch_matvec(W, W.w, W.qa, W.v, W.z); }));
-        if ((st = kkt_project(h, W.alpha)) != SVM_OK) return st;
+        CK(timed(h, TK_MATVEC, [&] {
+            return df ? launch_matvec_df(W, W.w, W.qaf, W.v, W.zf) : launch_matvec(W, W.w, W.qa, W.v, W.z);
+        }));
+        if ((st = kkt_project(h, W.alpha, df)) != SVM_OK) return st;
         if ((st = sync_read(h)) != SVM_OK) return st;
         R = kkt_value(W.h_pout[SLOT_KKT]);
         if (h->trace)
@@ -666,7 +692,7 @@ extern "C" svm_status svm_op_kkt(svm_ssnalm_t *h, const double *alpha, double *k
     }
     CK(timed(h, TK_RMATVEC, [&] { return launch_rmatvec(W, alpha, wc, nullptr, nullptr, W.w, -1); }));
     CK(timed(h, TK_MATVEC, [&] { return launch_matvec(W, W.w, W.qa); }));
-    svm_status st = kkt_project(h, alpha);
+    svm_status st = kkt_project(h, alpha, false);
     if (st != SVM_OK) return st;
     if ((st = sync_read(h)) != SVM_OK) return st;
     if (kkt) *kkt = kkt_value(W.h_pout[SLOT_KKT]);

@@ -49,7 +49,10 @@ def make(X, y, C=1.0, **kw):
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("dtype,n,q", [(np.float32, 5003, 128), (np.float64, 2000, 50),
                                        (np.float32, 777, 33), (np.float64, 1031, 7),
-                                       (np.float32, 4099, 784)])
+                                       (np.float32, 4099, 784), (np.float32, 1, 128),
+                                       (np.float32, 31, 4), (np.float32, 261, 12),
+                                       (np.float32, 8197, 64), (np.float32, 3333, 256),
+                                       (np.float32, 40000, 200)])
 def test_matvec_rmatvec(prec, dtype, n, q):
     X, y = datagen.small(n, q, seed=n + q, dtype=dtype)
     s, Xd, yd = make(X, y, precision=prec)
