@@ -142,6 +142,78 @@ __device__ __forceinline__ df df_add(df a, df b)
     return r;
 }
 
+// ---------------------------------------------------------------------------
+// Double-float values as float2 (x = hi, y = lo, normalised: |lo| <= ulp(hi)/2,
+// so the sign and the order are decided by hi first).  Addition is the
+// accurate form with two TwoSums (Hida, Li, Bailey, "Algorithms for
+// quad-double precision floating point arithmetic", ARITH-15, 2001), which
+// stays accurate under cancellation; products use TwoProd via FMA.
+__device__ __forceinline__ float2 dfx_fast(float s, float e)   // requires |s| >= |e| or s == 0
+{
+    const float hi = s + e;
+    return make_float2(hi, e - (hi - s));
+}
+__device__ __forceinline__ float2 dfx_add(float2 a, float2 b)
+{
+    float s, e, t, f;
+    two_sum(a.x, b.x, s, e);
+    two_sum(a.y, b.y, t, f);
+    e += t;
+    float2 r = dfx_fast(s, e);
+    r.y += f;
+    return dfx_fast(r.x, r.y);
+}
+__device__ __forceinline__ float2 dfx_neg(float2 a)
+{
+    return make_float2(-a.x, -a.y);
+}
+__device__ __forceinline__ float2 dfx_sub(float2 a, float2 b)
+{
+    return dfx_add(a, dfx_neg(b));
+}
+__device__ __forceinline__ float2 dfx_addf(float2 a, float b)
+{
+    float s, e;
+    two_sum(a.x, b, s, e);
+    e += a.y;
+    return dfx_fast(s, e);
+}
+__device__ __forceinline__ float2 dfx_mul(float2 a, float2 b)
+{
+    float p, e;
+    two_prod(a.x, b.x, p, e);
+    e = fmaf(a.x, b.y, fmaf(a.y, b.x, e));
+    return dfx_fast(p, e);
+}
+// an integer (|v| < 2^47) as an exact double-float
+__device__ __forceinline__ float2 dfx_from_ll(long long v)
+{
+    const float hi = (float)v;
+    return make_float2(hi, (float)(v - (long long)hi));
+}
+// a / b for b > 0: one correction step on the FP32 quotient (Dekker,
+// "A floating-point technique for extending the available precision",
+// Numer. Math. 18, 1971): q1 = a/b, r = a - q1 b exactly enough, q2 = r/b.
+__device__ __forceinline__ float2 dfx_div(float2 a, float2 b)
+{
+    const float q1 = a.x / b.x;
+    const float2 r = dfx_sub(a, dfx_mul(make_float2(q1, 0.f), b));
+    const float q2 = r.x / b.x;
+    return dfx_fast(q1, q2);
+}
+__device__ __forceinline__ bool dfx_gt(float2 a, float2 b)
+{
+    return a.x > b.x || (a.x == b.x && a.y > b.y);
+}
+__device__ __forceinline__ bool dfx_same(float2 a, float2 b)   // bitwise equality
+{
+    return __float_as_uint(a.x) == __float_as_uint(b.x) && __float_as_uint(a.y) == __float_as_uint(b.y);
+}
+__device__ __forceinline__ float2 shfl_xor_f2(float2 v, int o)
+{
+    return make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
+}
+
 }  // namespace svm
 
 namespace svm {

@@ -8,14 +8,20 @@
 
 namespace svm {
 
-// Results of one projection launch, written by the device (FP64).
+// Results of one projection launch, written by the device.  The FP64 kernel
+// writes lam and sum; the double-float kernel writes lamf and sumf and sets
+// is_df, and the host fills lam and sum from them after reading the record.
 struct ProjOut {
     double lam;        // lambda-hat
-    double sum[4];     // mode-dependent reductions (see ProjMode)
+    double sum[4];     // mode-dependent reductions (see ProjSums)
     long long p;       // |J|
-    long long s;       // |S|
+    long long s;       // |S| (FP64 kernel) or the length of the delta list (double-float kernel)
     int passes;        // root-search passes
     int status;        // 0 ok, DEV_ROOT if the search hit its cap
+    float2 lamf;       // lambda-hat as a double-float pair
+    float2 sumf[4];
+    int is_df;
+    int pad_;
 };
 
 // What a projection launch reduces besides lambda-hat, J and S (bit flags).
@@ -27,20 +33,39 @@ enum ProjSums : int {
                    // sum[3] = sum max(0, 1 - (Qalpha_i + y_i lambda)); alpha = a, Qalpha = b
 };
 
-// Projection input u_i = a_i + c1 * b_i + c2 (b may be null) and outputs.
-// mixed: a, b, u_out are double-float (float2) n-vectors; else FP64.
+// FP64 projection: input u_i = a_i + c1 * b_i + c2 (b may be null), outputs.
 struct ProjIn {
-    bool mixed = false;
-    const void *a = nullptr, *b = nullptr;
+    const double *a = nullptr, *b = nullptr;
     double c1 = 0.0, c2 = 0.0;
     int sums = 0;
     const double *lam0 = nullptr;   // device: warm start for lambda (nullable)
-    void *u_out = nullptr;
+    double *u_out = nullptr;
     double *pi_out = nullptr;
     float2 *wpi_out = nullptr;      // y_i pi_i as an FP32 (hi, lo) pair
     int32_t *J = nullptr, *S = nullptr;
     const double *pi_base = nullptr;
-    const double *alpha = nullptr;  // FP64 alpha for SF_DPA and SF_KKT
+    const double *alpha = nullptr;  // alpha for SF_DPA and SF_KKT
+};
+
+// Double-float projection (mixed form): every n-vector is a float2 (hi, lo)
+// pair.  u_i = a'_i + c1 b_i + c2 with a'_i = a_i, or y_i a_i when a_signed
+// (a holds y o alpha).  Besides J it lists the delta set D = {i : y_i pi_i !=
+// base_w_i} (base_w null = 0) with the weights dw_i = y_i pi_i - base_w_i and
+// dwa_i = |pi_i| - |pi_base,i|, so that A'pi = A'pi_base + sum_D dw_i x_i.
+struct ProjDF {
+    const float2 *a = nullptr;
+    bool a_signed = false;
+    const float2 *b = nullptr;
+    double c1 = 0.0, c2 = 0.0;
+    int sums = 0;
+    const float2 *lam0 = nullptr;     // device: warm start (nullable)
+    float2 *u_out = nullptr;
+    float2 *wpi_out = nullptr;        // y o pi
+    const float2 *alpha_w = nullptr;  // y o alpha (SF_DPA)
+    const float2 *base_w = nullptr;   // y o pi_base (SF_PSID; base of D)
+    float2 *dw_out = nullptr;
+    float *dwa_out = nullptr;
+    int32_t *J = nullptr, *D = nullptr;
 };
 
 // One projection's output buffers (the solver keeps two and swaps them when a
@@ -64,10 +89,15 @@ struct Work {
     int dev = 0, nsm = 0;
     // n-vectors (FP64) and index lists
     double *alpha = nullptr, *z = nullptr, *dz = nullptr, *qa = nullptr, *tmpn = nullptr;
-    // the mixed form carries z = A v, dz = A dv, Q alpha and alpha as
-    // double-float pairs instead (df = true; z, dz and pb[].u are then unused)
+    // the mixed form carries z = A v, dz = A dv, Q alpha and y o alpha as
+    // double-float pairs instead (df = true; z, dz and pb[].u are then unused),
+    // and forms A'pi incrementally over delta lists (weights dw, dwa)
     bool df = false;
-    float2 *zf = nullptr, *dzf = nullptr, *qaf = nullptr, *alphaf = nullptr;
+    float2 *zf = nullptr, *dzf = nullptr, *qaf = nullptr, *alphaw = nullptr;
+    float2 *dw = nullptr;
+    float *dwa = nullptr;
+    // sum_i |pi_i| |x_i| (the roundoff scale of A'pi) for atp and atp2
+    float *atpa = nullptr, *atpa2 = nullptr;
     ProjBuf pb[2];            // current / trial projection buffers
     // q-vectors
     double *v = nullptr, *dv = nullptr, *g = nullptr, *atp = nullptr, *atp2 = nullptr, *h = nullptr,
@@ -104,6 +134,8 @@ struct Work {
 // ---- launchers (return cudaError_t of the launch) ----
 cudaError_t proj_setup(Work &W);
 cudaError_t launch_project(Work &W, const ProjIn &in, ProjOut *out);
+cudaError_t launch_project_df(Work &W, const ProjDF &in, ProjOut *out);
+void *projdf_kernel_for(int ept);   // for the occupancy query of proj_setup
 
 // z0 = A v0 (and z1 = A v1 when v1 != nullptr, in the same pass over X)
 cudaError_t launch_matvec(Work &W, const double *v0, double *z0, const double *v1 = nullptr,
@@ -111,16 +143,23 @@ cudaError_t launch_matvec(Work &W, const double *v0, double *z0, const double *v
 // the same with double-float outputs (mixed form, FP32 X with q % 4 == 0)
 cudaError_t launch_matvec_df(Work &W, const double *v0, float2 *z0, const double *v1 = nullptr,
                              float2 *z1 = nullptr);
-// alphaf_i = y_i wpi_i (double-float alpha from the signed split weights)
-cudaError_t launch_unsign_df(Work &W, const float2 *wpi, float2 *alphaf);
 // out = sum_i c_i y_i x_i over the index list idx (cnt entries, read from
 // *cnt_dev on the device) or over all rows when idx == nullptr.  The mixed
 // form reads the weights as y_i c_i FP32 pairs from wc (when non-null).
 // Also red[slot] = sum_j (sum_i |c_i x_ij|)^2 when scale_slot >= 0.
 cudaError_t launch_rmatvec(Work &W, const double *c, const float2 *wc, const int32_t *idx,
                            const long long *cnt_dev, double *out, int scale_slot);
+// out = base + sum_{i in idx} wc_i x_i (double-float weights, Dot2 sums, the
+// count read from *cnt_dev), aout = abase + sum_i wa_i |x_i| (FP32) and
+// red[slot] = |aout|^2; base and abase may be null (zero).
+cudaError_t launch_rmatvec_df(Work &W, const float2 *wc, const float *wa, const int32_t *idx, const long long *cnt_dev,
+                              const double *base, const float *abase, double *out, float *aout, int slot);
 // wc_i = y_i c_i as an FP32 (hi, lo) pair (input of the mixed A' c)
 cudaError_t split_weights(Work &W, const double *c, float2 *wc);
+// a_i = (y_i when signed, else 1) * c_i as a double-float pair
+cudaError_t split_vector(Work &W, const double *c, bool signed_by_y, float2 *a);
+// c_i = (y_i when signed, else 1) * (a_i.hi + a_i.lo) in FP64; the split of C maps to C
+cudaError_t join_vector(Work &W, const float2 *a, bool signed_by_y, double *c);
 // q-vector helpers
 cudaError_t launch_grad(Work &W);            // g = v - atp; red[0] = |g|^2
 cudaError_t launch_dots(Work &W);            // red[2] = g'dv, red[3] = v'dv, red[4] = dv'dv

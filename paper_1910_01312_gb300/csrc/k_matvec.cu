@@ -335,61 +335,69 @@ __global__ void __launch_bounds__(256) rmatvec_part_kernel(const TX *__restrict_
     }
 }
 
-// Fixed-order final reduction of G block partials, run by one block whose
-// size is a multiple of 128: columns in rounds of 128, blockDim/128 interleaved
-// sub-sums per column, combined in order.  out_j = sum_b part[b][j];
-// red[slot] = sum_j (sum_b apart[b][j])^2 when slot >= 0.
-__device__ void final_reduce(int G, int q, const double *__restrict__ part, const double *__restrict__ apart,
-                             double *__restrict__ out, double *__restrict__ red, int slot, double *sm)
-{
-    const int subs = blockDim.x >> 7;
-    const int tx = threadIdx.x & 127, sub = threadIdx.x >> 7;
-    double *sp = sm, *sa = sm + subs * 128, *sq = sa + subs * 128;
-    double scale = 0.0;
-    for (int c0 = 0; c0 < q; c0 += 128) {
-        const int col = c0 + tx;
-        double s = 0.0, a = 0.0;
-        if (col < q) {
-#pragma unroll 4
-            for (int b = sub; b < G; b += subs) {
-                s += __ldcg(part + (size_t)b * q + col);
-                a += __ldcg(apart + (size_t)b * q + col);
-            }
-        }
-        sp[sub * 128 + tx] = s;
-        sa[sub * 128 + tx] = a;
-        __syncthreads();
-        if (sub == 0 && col < q) {
-            double ts = 0.0, ta = 0.0;
-            for (int k = 0; k < subs; ++k) { ts += sp[k * 128 + tx]; ta += sa[k * 128 + tx]; }
-            out[col] = ts;
-            scale = fma(ta, ta, scale);
-        }
-        __syncthreads();
-    }
-    if (sub == 0) sq[tx] = scale;
-    __syncthreads();
-    if (threadIdx.x == 0 && slot >= 0) {
-        double t = 0.0;
-        for (int k = 0; k < 128; ++k) t += sq[k];
-        red[slot] = t;
-    }
-}
-
 // Mixed form.  Weights arrive as y_i c_i in FP32 (hi, lo) pairs; VW = 4:
 // lane l owns the float4 column chunks l + 32k (q % 4 == 0), VW = 1: the
 // scalar columns l + 32k.  Rows are in flight R at a time per warp.  The
 // block's warps are combined by a tree over shared memory, and the block
 // that finishes last (threadfence + counter) performs the fixed-order final
 // reduction over all block partials, so one launch yields out = A'c.
+// Last-block reduction of the double-float partials [G][3][q] (hi, lo, abs):
+// per column, subs interleaved sub-sums over the blocks, combined in order.
+__device__ void final_reduce_df(int G, int q, const float *__restrict__ part, const double *__restrict__ base,
+                                const float *__restrict__ abase, double *__restrict__ out, float *__restrict__ aout,
+                                double *__restrict__ red, int slot, float *sm)
+{
+    const int subs = blockDim.x >> 7;
+    const int tx = threadIdx.x & 127, sub = threadIdx.x >> 7;
+    float2 *sp = reinterpret_cast<float2 *>(sm);   // [subs][128]
+    float *sa = sm + 2 * subs * 128;               // [subs][128]
+    float scale = 0.f;
+    for (int c0 = 0; c0 < q; c0 += 128) {
+        const int col = c0 + tx;
+        float2 S = make_float2(0.f, 0.f);
+        float A = 0.f;
+        if (col < q) {
+            for (int b = sub; b < G; b += subs) {
+                const float *p = part + (size_t)b * 3 * q;
+                S = dfx_add(S, make_float2(__ldcg(p + col), __ldcg(p + q + col)));
+                A += __ldcg(p + 2 * q + col);
+            }
+        }
+        sp[sub * 128 + tx] = S;
+        sa[sub * 128 + tx] = A;
+        __syncthreads();
+        if (sub == 0 && col < q) {
+            float2 T = make_float2(0.f, 0.f);
+            float TA = 0.f;
+            for (int k = 0; k < subs; ++k) { T = dfx_add(T, sp[k * 128 + tx]); TA += sa[k * 128 + tx]; }
+            const double v = (double)T.x + (double)T.y;
+            out[col] = base ? base[col] + v : v;
+            const float a = abase ? abase[col] + TA : TA;
+            if (aout) aout[col] = a;
+            scale = fmaf(a, a, scale);
+        }
+        __syncthreads();
+    }
+    if (slot >= 0) {
+        if (sub == 0) {
+            const float v = warp_sumf(scale);
+            if ((tx & 31) == 0) sa[tx >> 5] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) red[slot] = (double)((sa[0] + sa[1]) + (sa[2] + sa[3]));
+    }
+}
+
+// out = base + sum_i wc_i x_i, aout = abase + sum_i wa_i |x_i| (wa null: |wc_i.hi|),
+// red[slot] = |aout|^2, over idx (count *cnt_dev) or all rows.  Per-block
+// partials are double-float; the last block to finish adds them in block order
+// in double-float arithmetic (no FP64 beyond one conversion per column).
 template <int VW, int NCH>
-__global__ void __launch_bounds__(NCH * VW >= 8 ? 256 : 1024) rmatvec_mx_part_kernel(const float *__restrict__ X, long long n, int q,
-                                                               const float2 *__restrict__ wc,
-                                                               const int32_t *__restrict__ idx,
-                                                               const long long *__restrict__ cnt_dev,
-                                                               double *__restrict__ part, double *__restrict__ apart,
-                                                               unsigned *__restrict__ counter, double *__restrict__ out,
-                                                               double *__restrict__ red, int slot)
+__global__ void __launch_bounds__(NCH * VW >= 8 ? 256 : 1024) rmatvec_mx_part_kernel(
+    const float *__restrict__ X, long long n, int q, const float2 *__restrict__ wc, const float *__restrict__ wa,
+    const int32_t *__restrict__ idx, const long long *__restrict__ cnt_dev, float *__restrict__ part,
+    unsigned *__restrict__ counter, const double *__restrict__ base, const float *__restrict__ abase,
+    double *__restrict__ out, float *__restrict__ aout, double *__restrict__ red, int slot)
 {
     const long long cnt = idx ? *cnt_dev : n;
     const int G = gridDim.x;
@@ -411,20 +419,24 @@ __global__ void __launch_bounds__(NCH * VW >= 8 ? 256 : 1024) rmatvec_mx_part_ke
         const long long rl = c0 + lane;
         int myi = -1;
         float2 myw = make_float2(0.f, 0.f);
+        float mya = 0.f;
         if (rl < r_end) {
             myi = idx ? idx[rl] : (int)rl;
             myw = wc[myi];
+            mya = wa ? wa[myi] : fabsf(myw.x);
         }
         const int here = (int)((r_end - c0) < 32 ? (r_end - c0) : 32);
         for (int u0 = 0; u0 < here; u0 += R) {
             int ii[R];
             float2 w[R];
+            float wab[R];
 #pragma unroll
             for (int u = 0; u < R; ++u) {
                 const int src = (u0 + u) & 31;
                 ii[u] = __shfl_sync(0xffffffffu, myi, src);
                 w[u].x = __shfl_sync(0xffffffffu, myw.x, src);
                 w[u].y = __shfl_sync(0xffffffffu, myw.y, src);
+                wab[u] = __shfl_sync(0xffffffffu, mya, src);
                 if (u0 + u >= here) ii[u] = -1;
             }
             float xv[R][NCH][VW];
@@ -454,7 +466,7 @@ __global__ void __launch_bounds__(NCH * VW >= 8 ? 256 : 1024) rmatvec_mx_part_ke
 #pragma unroll
                     for (int e = 0; e < VW; ++e) {
                         dot2_step(xv[u][k][e], w[u], s[k][e], c[k][e]);
-                        ab[k][e] += fabsf(xv[u][k][e] * w[u].x);
+                        ab[k][e] = fmaf(fabsf(xv[u][k][e]), wab[u], ab[k][e]);
                     }
         }
     }
@@ -481,8 +493,12 @@ __global__ void __launch_bounds__(NCH * VW >= 8 ? 256 : 1024) rmatvec_mx_part_ke
             df_acc(ss, cc, b[j], b[q + j]);
             aa += b[2 * q + j];
         }
-        part[(size_t)blockIdx.x * q + j] = (double)ss + (double)cc;
-        apart[(size_t)blockIdx.x * q + j] = (double)aa;
+        float hi, lo;
+        two_sum(ss, cc, hi, lo);
+        float *pb = part + (size_t)blockIdx.x * 3 * q;
+        pb[j] = hi;
+        pb[q + j] = lo;
+        pb[2 * q + j] = aa;
     }
     __threadfence();
     __syncthreads();
@@ -491,8 +507,7 @@ __global__ void __launch_bounds__(NCH * VW >= 8 ? 256 : 1024) rmatvec_mx_part_ke
     __syncthreads();
     if (is_last) {
         __threadfence();
-        double *sm = reinterpret_cast<double *>(sredf);
-        final_reduce(G, q, part, apart, out, red, slot, sm);
+        final_reduce_df(G, q, part, base, abase, out, aout, red, slot, sredf);
         if (threadIdx.x == 0) *counter = 0u;
     }
 }
@@ -564,8 +579,9 @@ static cudaError_t rmatvec_t(Work &W, const double *c, const int32_t *idx, const
 
 static int g_rmx_attr = 0;
 
-static cudaError_t rmatvec_mx(Work &W, const float2 *wc, const int32_t *idx, const long long *cnt_dev, double *out,
-                              int scale_slot)
+static cudaError_t rmatvec_mx(Work &W, const float2 *wc, const float *wa, const int32_t *idx,
+                              const long long *cnt_dev, const double *base, const float *abase, double *out,
+                              float *aout, int scale_slot)
 {
     const int q = (int)W.q;
     const bool vec = (q % 4 == 0) && ((uintptr_t)W.X % 16 == 0);
@@ -574,10 +590,9 @@ static cudaError_t rmatvec_mx(Work &W, const float2 *wc, const int32_t *idx, con
     while (nch_t < nch) nch_t <<= 1;
     const int threads = nch_t * (vec ? 4 : 1) >= 8 ? 256 : 1024;   // must match the kernel's launch bounds
     const int G = threads == 1024 ? W.nsm : W.nsm * 4;
-    double *part = W.part;
-    double *apart = W.part + (size_t)G * q;
+    float *part = reinterpret_cast<float *>(W.part);
     size_t smem = (size_t)(threads / 32) * 3 * q * sizeof(float);
-    const size_t smem_final = (size_t)(2 * (threads / 128) * 128 + 128) * sizeof(double);
+    const size_t smem_final = (size_t)3 * (threads / 128) * 128 * sizeof(float);
     if (smem < smem_final) smem = smem_final;
     if (!g_rmx_attr) {
         const void *fns[] = {(const void *)rmatvec_mx_part_kernel<4, 1>, (const void *)rmatvec_mx_part_kernel<4, 2>,
@@ -592,7 +607,7 @@ static cudaError_t rmatvec_mx(Work &W, const float2 *wc, const int32_t *idx, con
         g_rmx_attr = 1;
     }
     const float *X = (const float *)W.X;
-#define RX_ARGS X, W.n, q, wc, idx, cnt_dev, part, apart, W.rm_counter, out, W.red, scale_slot
+#define RX_ARGS X, W.n, q, wc, wa, idx, cnt_dev, part, W.rm_counter, base, abase, out, aout, W.red, scale_slot
     if (vec) {
         if (nch <= 1) rmatvec_mx_part_kernel<4, 1><<<G, threads, smem, W.st>>>(RX_ARGS);
         else if (nch <= 2) rmatvec_mx_part_kernel<4, 2><<<G, threads, smem, W.st>>>(RX_ARGS);
@@ -631,10 +646,60 @@ cudaError_t split_weights(Work &W, const double *c, float2 *wc)
     return cudaGetLastError();
 }
 
+cudaError_t launch_rmatvec_df(Work &W, const float2 *wc, const float *wa, const int32_t *idx, const long long *cnt_dev,
+                              const double *base, const float *abase, double *out, float *aout, int slot)
+{
+    if (!W.xf32) return cudaErrorInvalidValue;
+    return rmatvec_mx(W, wc, wa, idx, cnt_dev, base, abase, out, aout, slot);
+}
+
+__global__ void split_vector_kernel(long long n, const double *c, const int8_t *y, int sgn, float2 *a)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double v = (sgn && y[i] < 0) ? -c[i] : c[i];
+        const float hi = (float)v;
+        a[i] = make_float2(hi, (float)(v - (double)hi));
+    }
+}
+
+// entries equal to the split of C (the projection's value at the upper bound)
+// become C exactly
+__global__ void join_vector_kernel(long long n, const float2 *a, const int8_t *y, int sgn, float2 Cd, double C,
+                                   double *c)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        float2 v = a[i];
+        const bool neg = sgn && y[i] < 0;
+        if (neg) v = make_float2(-v.x, -v.y);
+        c[i] = (v.x == Cd.x && v.y == Cd.y) ? C : (double)v.x + (double)v.y;
+    }
+}
+
+cudaError_t split_vector(Work &W, const double *c, bool signed_by_y, float2 *a)
+{
+    int blocks = (int)((W.n + 255) / 256);
+    if (blocks > W.nsm * 8) blocks = W.nsm * 8;
+    split_vector_kernel<<<blocks, 256, 0, W.st>>>(W.n, c, W.y, signed_by_y ? 1 : 0, a);
+    ++W.nlaunch;
+    return cudaGetLastError();
+}
+
+cudaError_t join_vector(Work &W, const float2 *a, bool signed_by_y, double *c)
+{
+    int blocks = (int)((W.n + 255) / 256);
+    if (blocks > W.nsm * 8) blocks = W.nsm * 8;
+    const float Ch = (float)W.C;
+    const float2 Cd = make_float2(Ch, (float)(W.C - (double)Ch));
+    join_vector_kernel<<<blocks, 256, 0, W.st>>>(W.n, a, W.y, signed_by_y ? 1 : 0, Cd, W.C, c);
+    ++W.nlaunch;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_rmatvec(Work &W, const double *c, const float2 *wc, const int32_t *idx, const long long *cnt_dev,
                            double *out, int scale_slot)
 {
-    if (W.precision == 1 && W.xf32 && wc) return rmatvec_mx(W, wc, idx, cnt_dev, out, scale_slot);
+    if (W.precision == 1 && W.xf32 && wc)
+        return rmatvec_mx(W, wc, nullptr, idx, cnt_dev, nullptr, nullptr, out, nullptr, scale_slot);
     return W.xf32 ? rmatvec_t<float>(W, c, idx, cnt_dev, out, scale_slot)
                   : rmatvec_t<double>(W, c, idx, cnt_dev, out, scale_slot);
 }
@@ -710,25 +775,6 @@ cudaError_t launch_dots(Work &W)
 cudaError_t launch_vaxpy(Work &W, double t)
 {
     axpy_kernel<<<1, 1024, 0, W.st>>>(W.q, t, W.dv, W.v);
-    ++W.nlaunch;
-    return cudaGetLastError();
-}
-
-// alphaf_i = y_i wpi_i: removing the label's sign from a split weight is exact
-__global__ void unsign_df_kernel(long long n, const int8_t *__restrict__ y, const float2 *__restrict__ wpi,
-                                 float2 *__restrict__ af)
-{
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const float2 w = wpi[i];
-        af[i] = (y[i] > 0) ? w : make_float2(-w.x, -w.y);
-    }
-}
-
-cudaError_t launch_unsign_df(Work &W, const float2 *wpi, float2 *alphaf)
-{
-    int blocks = (int)((W.n + 1023) / 1024);
-    if (blocks > W.nsm * 4) blocks = W.nsm * 4;
-    unsign_df_kernel<<<blocks, 1024, 0, W.st>>>(W.n, W.y, wpi, alphaf);
     ++W.nlaunch;
     return cudaGetLastError();
 }

@@ -18,19 +18,9 @@
 // either way).  Ties follow the paper's clip: t >= C -> C, t <= 0 -> 0, so J
 // uses strict inequalities.
 //
-// Precision.  The plain form (MX = false) reads FP64 vectors and evaluates
-// every component in FP64.  The mixed form (MX = true) reads its vectors as
-// double-float pairs (FP32 hi + lo, relative accuracy ~2^-48), forms u and
-// s_i = y_i u_i with FP32 error-free arithmetic, keeps r_i = fl32(s_i -
-// lambda_0), and classifies a component in FP32 whenever its clipped value is
-// certainly 0 or certainly C (|error| bound (|r| + |delta| + C) 2^-20).  Only
-// the components near a bound -- the free ones and the ambiguous ones -- are
-// evaluated in FP64, out of line.  Saturated components enter f through exact
-// integer counts and their breakpoint distances enter the segment test as
-// conservative (never too far) bounds, so the exact-root test and every output
-// are those of the FP64 form.  On this part one FP64 warp instruction holds
-// the SM's FP64 pipe ~16 cycles, so an FP64 operation per component costs
-// more than the whole FP32 pass.
+// Precision.  This kernel is the plain form: it reads FP64 vectors and
+// evaluates every component in FP64.  The mixed form runs the same iteration
+// in double-float arithmetic (k_projdf.cu).
 #include <math.h>
 
 #include "internal.cuh"
@@ -41,14 +31,14 @@ constexpr int kMaxPass = 256;
 constexpr int kPartStride = 8;   // doubles per block partial
 
 struct ProjArgs {
-    const void *a, *b;       // FP64 (plain) or double-float float2 (mixed) n-vectors
+    const double *a, *b;
     double c1, c2;
     const int8_t *y;
     long long n;
     double C;
     int sums;
     const double *lam0;
-    void *u_out;             // FP64 (plain) or float2 (mixed)
+    double *u_out;
     double *pi_out;
     float2 *wpi_out;
     int32_t *J, *S;
@@ -117,34 +107,6 @@ __device__ __forceinline__ void eval_exact(double s, bool pos, double lam, doubl
     A.ddlo = fmax(A.ddlo, o.dlo);
 }
 
-// double from a double-float pair (FP64; used only on the exact paths)
-__device__ __noinline__ double df2d(float2 v)
-{
-    return (double)v.x + (double)v.y;
-}
-
-// One component at lambda (mixed form): FP32 when certainly saturated.
-__device__ __forceinline__ void eval_comp_mx(float2 sdf, float r, bool pos, double lam, float dl, double C, float Cf,
-                                             PassAcc &A)
-{
-    const float tf = pos ? (r - dl) : (dl - r);
-    const float er = (fabsf(r) + fabsf(dl) + Cf) * 9.5367431640625e-07f;   // 2^-20
-    if (tf > Cf + er) {
-        A.nup += pos ? 1 : -1;
-        // offsets t - C (y=+1, above) or C - t (y=-1, below), made nearer by er
-        if (pos) A.fdhi = fminf(A.fdhi, tf - Cf - er);
-        else A.fdlo = fmaxf(A.fdlo, Cf - tf + er);
-        return;
-    }
-    if (tf < -er) {
-        // offsets t (y=+1, below) or -t (y=-1, above)
-        if (pos) A.fdlo = fmaxf(A.fdlo, tf + er);
-        else A.fdhi = fminf(A.fdhi, -tf - er);
-        return;
-    }
-    eval_exact(df2d(sdf), pos, lam, C, A);
-}
-
 // pi component in FP64 and its class (0: = 0, 1: free, 2: = C), out of line
 __device__ __noinline__ double clip_exact_ool(double s, bool pos, double lam, double C, int &pc)
 {
@@ -179,86 +141,49 @@ __device__ __forceinline__ double flip_sign(double x, bool neg)
     return neg ? __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ULL) : x;
 }
 
-// double-float helpers (FP32 error-free transformations)
-__device__ __forceinline__ float2 dfx_add(float2 a, float2 b)
-{
-    float s, e;
-    two_sum(a.x, b.x, s, e);
-    e += a.y + b.y;
-    const float hi = s + e;
-    return make_float2(hi, e - (hi - s));
-}
-__device__ __forceinline__ float2 dfx_mul(float2 a, float2 b)
-{
-    float p, e;
-    two_prod(a.x, b.x, p, e);
-    e = fmaf(a.x, b.y, fmaf(a.y, b.x, e));
-    const float hi = p + e;
-    return make_float2(hi, e - (hi - p));
-}
+// FP32 (hi, lo) split of a double
 __device__ __forceinline__ float2 dfx_split(double v)
 {
     const float hi = (float)v;
     return make_float2(hi, (float)(v - (double)hi));
 }
 
-template <int EPT, bool MX>
+template <int EPT>
 __global__ void __launch_bounds__(kTPB, EPT >= 16 ? 1 : 2) proj_kernel(ProjArgs A)
 {
     const int G = gridDim.x, blk = blockIdx.x, tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const long long NT = (long long)G * kTPB;
     const double C = A.C;
-    const float Cf = (float)C;
 
-    // Warm start lambda_0 and the FP32 splits of the scalars: computed by one
-    // thread per block and broadcast (scalar FP64 in every thread is costly).
+    // warm start lambda_0: read by one thread per block and broadcast
     __shared__ double sh_lam0;
-    __shared__ float2 sh_c1, sh_c2, sh_l0;
     if (tid == 0) {
         double l0 = A.lam0 ? __ldcg(A.lam0) : 0.0;
         if (!isfinite(l0)) l0 = 0.0;
         sh_lam0 = l0;
-        if (MX) { sh_c1 = dfx_split(A.c1); sh_c2 = dfx_split(A.c2); sh_l0 = dfx_split(l0); }
     }
     __syncthreads();
     const double lam0 = sh_lam0;
 
-    double sd[MX ? 1 : EPT];      // plain: s_i in FP64
-    float2 sf[MX ? EPT : 1];      // mixed: s_i as a double-float pair
-    float r[EPT];
+    double sd[EPT];   // s_i = y_i u_i
     unsigned posm = 0u, valm = 0u;
-    {
-        const float2 c1f = sh_c1, c2f = sh_c2, l0f = sh_l0;
 #pragma unroll
-        for (int k = 0; k < EPT; ++k) {
-            const long long i = k * NT + (long long)blk * kTPB + tid;
-            r[k] = 0.f;
-            if (MX) sf[k] = make_float2(0.f, 0.f);
-            else sd[MX ? 0 : k] = 0.0;
-            if (i < A.n) {
-                const bool pos = A.y[i] > 0;
-                if (MX) {
-                    float2 u = reinterpret_cast<const float2 *>(A.a)[i];
-                    if (A.b) u = dfx_add(u, dfx_mul(c1f, reinterpret_cast<const float2 *>(A.b)[i]));
-                    u = dfx_add(u, c2f);
-                    if (!pos) { u.x = -u.x; u.y = -u.y; }
-                    sf[MX ? k : 0] = u;
-                    r[k] = (u.x - l0f.x) + (u.y - l0f.y);
-                } else {
-                    double u = reinterpret_cast<const double *>(A.a)[i] + A.c2;
-                    if (A.b) u = fma(A.c1, reinterpret_cast<const double *>(A.b)[i], u);
-                    sd[MX ? 0 : k] = flip_sign(u, !pos);
-                }
-                posm |= (pos ? 1u : 0u) << k;
-                valm |= 1u << k;
-            }
+    for (int k = 0; k < EPT; ++k) {
+        const long long i = k * NT + (long long)blk * kTPB + tid;
+        sd[k] = 0.0;
+        if (i < A.n) {
+            const bool pos = A.y[i] > 0;
+            double u = A.a[i] + A.c2;
+            if (A.b) u = fma(A.c1, A.b[i], u);
+            sd[k] = flip_sign(u, !pos);
+            posm |= (pos ? 1u : 0u) << k;
+            valm |= 1u << k;
         }
     }
 
     __shared__ double sh_d[kWarps][6];
     __shared__ double sh_lam;
-    __shared__ float sh_dl;
     __shared__ int sh_done;
 
     // root-search state, kept in shared memory (only warp 0 lane 0 updates it)
@@ -267,7 +192,6 @@ __global__ void __launch_bounds__(kTPB, EPT >= 16 ? 1 : 2) proj_kernel(ProjArgs 
     if (tid == 0) {
         st_L = -INFINITY; st_U = INFINITY; st_FL = 0.0; st_FU = 0.0;   // bracket: f(L) > 0 > f(U)
         st_last_step = 0.0; st_last_dir = 0; st_nbr = 0;
-        sh_dl = 0.f;
     }
     __syncthreads();
     double lam = lam0;
@@ -278,14 +202,9 @@ __global__ void __launch_bounds__(kTPB, EPT >= 16 ? 1 : 2) proj_kernel(ProjArgs 
     for (;;) {
         PassAcc acc;
         acc_init(acc);
-        const float dl = sh_dl;   // fl32(lam - lam0)
 #pragma unroll
-        for (int k = 0; k < EPT; ++k) {
-            if ((valm >> k) & 1u) {
-                if (MX) eval_comp_mx(sf[MX ? k : 0], r[k], (posm >> k) & 1u, lam, dl, C, Cf, acc);
-                else eval_exact(sd[MX ? 0 : k], (posm >> k) & 1u, lam, C, acc);
-            }
-        }
+        for (int k = 0; k < EPT; ++k)
+            if ((valm >> k) & 1u) eval_exact(sd[k], (posm >> k) & 1u, lam, C, acc);
         {
             const int nup = __reduce_add_sync(0xffffffffu, acc.nup);
             const int pp = __reduce_add_sync(0xffffffffu, acc.pp);
@@ -389,7 +308,6 @@ __global__ void __launch_bounds__(kTPB, EPT >= 16 ? 1 : 2) proj_kernel(ProjArgs 
                 }
                 sh_done = done;
                 sh_lam = done ? lam_hat : next;
-                sh_dl = (float)((done ? lam_hat : next) - lam0);
             }
         }
         __syncthreads();
@@ -400,52 +318,28 @@ __global__ void __launch_bounds__(kTPB, EPT >= 16 ? 1 : 2) proj_kernel(ProjArgs 
 
     // ---------------- final phase: pi, sums, compaction ----------------
     const double lh = lam_hat;
-    const float dlh = sh_dl;   // fl32(lam_hat - lam0)
+    const float Cf = (float)C;
     const float2 Csplit = make_float2(Cf, (float)(C - (double)Cf));
     const long long Cbits = __double_as_longlong(C);
-    __shared__ float2 sh_lh;
-    if (MX && tid == 0) sh_lh = dfx_split(lh);
-    __syncthreads();
-    const float2 lhf = sh_lh;
     double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
-    float2 du = make_float2(0.f, 0.f);    // double-float sum of (u - ub) over components at C in both
-    float2 hg = make_float2(0.f, 0.f);    // double-float hinge sum (mixed KKT)
-    int nupc = 0;                         // alpha components at C (mixed KKT)
     unsigned isJ = 0u, isS = 0u;          // bit k: component k is in J / S
 #pragma unroll
     for (int k = 0; k < EPT; ++k) {
         if (!((valm >> k) & 1u)) continue;
         const long long i = k * NT + (long long)blk * kTPB + tid;
         const bool pos = (posm >> k) & 1u;
-        int cls = 1;   // 0 lower, 1 evaluate in FP64, 2 upper
-        if (MX) {
-            const float tf = pos ? (r[k] - dlh) : (dlh - r[k]);
-            const float er = (fabsf(r[k]) + fabsf(dlh) + Cf) * 9.5367431640625e-07f;
-            cls = (tf > Cf + er) ? 2 : ((tf < -er) ? 0 : 1);
-        }
-        double pk;
         int pc;   // class of pk: 0 (= 0), 1 (free), 2 (= C)
-        if (cls == 2) {
-            pk = C; pc = 2;
-        } else if (cls == 0) {
-            pk = 0.0; pc = 0;
-        } else {
-            pk = clip_exact_ool(MX ? df2d(sf[MX ? k : 0]) : sd[MX ? 0 : k], pos, lh, C, pc);
-            if (pc == 1) isJ |= 1u << k;
-        }
+        const double pk = clip_exact_ool(sd[k], pos, lh, C, pc);
+        if (pc == 1) isJ |= 1u << k;
         if (pc) isS |= 1u << k;
         if (A.pi_out) A.pi_out[i] = pk;
-        float2 pkf = make_float2(0.f, 0.f);
-        if (A.wpi_out) pkf = (pc == 2) ? Csplit : ((pc == 0) ? pkf : dfx_split(pk));
-        if (A.wpi_out) A.wpi_out[i] = pos ? pkf : make_float2(-pkf.x, -pkf.y);
-        float2 uf = make_float2(0.f, 0.f);
-        if (MX) {
-            uf = sf[MX ? k : 0];
-            if (!pos) { uf.x = -uf.x; uf.y = -uf.y; }
-            if (A.u_out) reinterpret_cast<float2 *>(A.u_out)[i] = uf;
-        } else if (A.u_out) {
-            reinterpret_cast<double *>(A.u_out)[i] = flip_sign(sd[MX ? 0 : k], !pos);
+        if (A.wpi_out) {
+            // y_i pi_i as an FP32 (hi, lo) pair, the weight of the mixed-form A'pi
+            const float2 pkf = (pc == 2) ? Csplit : ((pc == 0) ? make_float2(0.f, 0.f) : dfx_split(pk));
+            A.wpi_out[i] = pos ? pkf : make_float2(-pkf.x, -pkf.y);
         }
+        const double u = flip_sign(sd[k], !pos);
+        if (A.u_out) A.u_out[i] = u;
         if (A.sums & SF_DPA) {
             // |pi - alpha|^2: only components that moved need FP64
             const double al = A.alpha[i];
@@ -459,20 +353,9 @@ __global__ void __launch_bounds__(kTPB, EPT >= 16 ? 1 : 2) proj_kernel(ProjArgs 
             const double pb = A.pi_base[i];
             const long long pbb = __double_as_longlong(pb);
             const int pbc = (pbb == Cbits) ? 2 : ((pbb << 1) == 0 ? 0 : 1);
-            if (pc == 2 && pbc == 2) {
-                // 2C(u - ub), factor applied below
-                if (MX) {
-                    const float2 ub = reinterpret_cast<const float2 *>(A.a)[i];
-                    du = dfx_add(du, make_float2(uf.x - ub.x, uf.y - ub.y));
-                } else {
-                    acc2 += flip_sign(sd[MX ? 0 : k], !pos) - reinterpret_cast<const double *>(A.a)[i];
-                }
-            } else if (pc != 0 || pbc != 0) {
-                const double u = MX ? df2d(uf) : flip_sign(sd[MX ? 0 : k], !pos);
-                const double ub = MX ? df2d(reinterpret_cast<const float2 *>(A.a)[i])
-                                     : reinterpret_cast<const double *>(A.a)[i];
-                acc1 += pk * (2.0 * u - pk) - pb * (2.0 * ub - pb);
-            }
+            const double ub = A.a[i];
+            if (pc == 2 && pbc == 2) acc2 += u - ub;   // 2C(u - ub), factor applied below
+            else if (pc != 0 || pbc != 0) acc1 += pk * (2.0 * u - pk) - pb * (2.0 * ub - pb);
         }
         if (A.sums & SF_KKT) {
             const double al = A.alpha[i];
@@ -481,28 +364,14 @@ __global__ void __launch_bounds__(kTPB, EPT >= 16 ? 1 : 2) proj_kernel(ProjArgs 
                 const double d = al - pk;
                 acc0 = fma(d, d, acc0);
             }
-            if (ab == Cbits) ++nupc;
-            else if ((ab << 1) != 0) { acc1 = fma(al, al, acc1); acc2 += al; }
+            if ((ab << 1) != 0) { acc1 = fma(al, al, acc1); acc2 += al; }
             // hinge max(0, 1 - (Qalpha_i + y_i lambda))
-            if (MX) {
-                const float2 qa = reinterpret_cast<const float2 *>(A.b)[i];
-                const float2 m = dfx_add(qa, pos ? lhf : make_float2(-lhf.x, -lhf.y));
-                const float2 h = dfx_add(make_float2(1.f, 0.f), make_float2(-m.x, -m.y));
-                if (h.x > 0.f) hg = dfx_add(hg, h);
-            } else {
-                const double marg = reinterpret_cast<const double *>(A.b)[i] + (pos ? lh : -lh);
-                acc3 += fmax(0.0, 1.0 - marg);
-            }
+            const double marg = A.b[i] + (pos ? lh : -lh);
+            acc3 += fmax(0.0, 1.0 - marg);
         }
     }
-    if (A.sums & SF_PSID) acc1 = fma(2.0 * C, acc2 + ((double)du.x + (double)du.y), acc1);
-    if (A.sums & SF_KKT) {
-        acc1 = fma((double)nupc * C, C, acc1);
-        acc2 = fma((double)nupc, C, acc2);
-        if (MX) acc3 = (double)hg.x + (double)hg.y;
-    } else {
-        acc2 = 0.0;
-    }
+    if (A.sums & SF_PSID) acc1 = fma(2.0 * C, acc2, acc1);
+    if (!(A.sums & SF_KKT)) acc2 = 0.0;
     // per-(k, warp) compaction counts
     __shared__ int sh_wc[EPT][kWarps][2];
 #pragma unroll
@@ -571,6 +440,7 @@ __global__ void __launch_bounds__(kTPB, EPT >= 16 ? 1 : 2) proj_kernel(ProjArgs 
             A.out->s = ts;
             A.out->passes = pass;
             A.out->status = 0;
+            A.out->is_df = 0;
         }
     }
     if (tid == 0) {
@@ -608,29 +478,28 @@ __global__ void __launch_bounds__(kTPB, EPT >= 16 ? 1 : 2) proj_kernel(ProjArgs 
 
 static const int kEpts[] = {1, 2, 4, 8, 16, 32};
 
-template <bool MX>
 static void *kernel_for(int ept)
 {
     switch (ept) {
-    case 1: return (void *)proj_kernel<1, MX>;
-    case 2: return (void *)proj_kernel<2, MX>;
-    case 4: return (void *)proj_kernel<4, MX>;
-    case 8: return (void *)proj_kernel<8, MX>;
-    case 16: return (void *)proj_kernel<16, MX>;
-    default: return (void *)proj_kernel<32, MX>;
+    case 1: return (void *)proj_kernel<1>;
+    case 2: return (void *)proj_kernel<2>;
+    case 4: return (void *)proj_kernel<4>;
+    case 8: return (void *)proj_kernel<8>;
+    case 16: return (void *)proj_kernel<16>;
+    default: return (void *)proj_kernel<32>;
     }
 }
 
 cudaError_t proj_setup(Work &W)
 {
-    // Largest co-resident grid for each instantiation (both precisions); pick
-    // the smallest EPT whose grid covers n.
+    // Largest co-resident grid for each instantiation (FP64 and double-float
+    // kernels share the geometry); pick the smallest EPT whose grid covers n.
     const long long n = W.n;
     for (int ept : kEpts) {
         int occ0 = 0, occ1 = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ0, kernel_for<false>(ept), kTPB, 0);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ0, kernel_for(ept), kTPB, 0);
         if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, kernel_for<true>(ept), kTPB, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, projdf_kernel_for(ept), kTPB, 0);
         if (e != cudaSuccess) return e;
         const int occ = occ0 < occ1 ? occ0 : occ1;
         if (occ < 1) continue;
@@ -656,8 +525,7 @@ cudaError_t launch_project(Work &W, const ProjIn &in, ProjOut *out)
     A.part = W.part; A.cnt = W.cnt; A.bar = W.bar; A.err = W.err; A.out = out;
     void *args[] = {&A};
     ++W.nlaunch;
-    void *fn = in.mixed ? kernel_for<true>(W.proj_ept) : kernel_for<false>(W.proj_ept);
-    return cudaLaunchCooperativeKernel(fn, dim3(W.proj_grid), dim3(kTPB), args, 0, W.st);
+    return cudaLaunchCooperativeKernel(kernel_for(W.proj_ept), dim3(W.proj_grid), dim3(kTPB), args, 0, W.st);
 }
 
 }  // namespace svm

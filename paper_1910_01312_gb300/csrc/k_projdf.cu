@@ -1,0 +1,625 @@
+// k_projdf.cu -- the projection of Sec. 3.2.1 onto {x : y'x = 0, 0 <= x <= C}
+// in double-float arithmetic (the mixed form of the solver).
+//
+// Same iteration as the FP64 kernel of k_proj.cu: each block keeps its slice
+// of the data in registers and all blocks run, in lock-step, a safeguarded
+// Newton iteration on the monotone piecewise-linear function
+//   f(lambda) = sum_i y_i clip(u_i - lambda y_i, 0, C),
+// whose root lambda-hat gives pi = clip(u - lambda-hat y, 0, C).
+//
+// Why a second kernel: on this part an FP64 instruction has ~64 cycles of
+// latency and a warp can issue one every ~64 cycles (FP64 divide ~640), so
+// even a handful of FP64 operations per pass -- scalar reductions, the
+// decision of the root search, int-to-double conversions -- cost more than
+// the whole FP32 work of the pass.  Here nothing on the device is FP64:
+//  * every n-vector is a double-float pair (hi + lo, ~2^-48 relative);
+//  * lambda = lambda_0 + delta with lambda_0 the warm start and delta a
+//    double-float; each component keeps d_i = s_i - lambda_0 (s_i = y_i u_i)
+//    in registers, so t_i = y_i (d_i - delta);
+//  * f(delta) = C nu + sum_{free} d_i - n_free delta, where nu counts the
+//    components at C (signed by y) and the free sum is a double-float; a
+//    component is classified in FP32 with an error margin (|d| + |delta| + C)
+//    2^-20 when it is certainly below 0, above C or strictly inside, and with
+//    an exact double-float comparison otherwise;
+//  * block partials are floats and integers, every block reduces all partials
+//    in one fixed order (bit-identical decisions everywhere), and thread 0
+//    of each block takes the decision in double-float arithmetic.
+// The Newton step F/p is the exact root whenever it stays inside the current
+// linear piece, whose ends are known as conservative FP32 offsets.
+//
+// Outputs: u (double-float), y o pi, the free set J, and the delta set D of
+// the components whose y_i pi_i differs from a base point, with the weights
+// that update A'pi from the base point's product (the mixed form never
+// recomputes A'pi over all rows).  Sums for the line search (SF_PSID: the
+// psi difference term by term), the inner stopping test (SF_DPA) and the KKT
+// residual (SF_KKT) come back as double-float pairs.
+#include <math.h>
+
+#include "internal.cuh"
+
+namespace svm {
+
+namespace {
+
+constexpr int kMaxPassDF = 256;
+constexpr float kMargin = 9.5367431640625e-07f;   // 2^-20
+constexpr int kStrideF = 16;                      // floats per block partial
+
+struct PDArgs {
+    const float2 *a;
+    int a_signed;
+    const float2 *b;
+    float2 c1, c2;
+    const int8_t *y;
+    long long n;
+    float2 Cd;               // C as a double-float pair
+    int sums;
+    const float2 *lam0;
+    float2 *u_out;
+    float2 *wpi_out;
+    const float2 *alpha_w;
+    const float2 *base_w;
+    float2 *dw_out;
+    float *dwa_out;
+    int32_t *J, *D;
+    float *part;             // [3][G][kStrideF]
+    int *cnt;                // [EPT][G][2]
+    unsigned *bar;
+    int *err;
+    ProjOut *out;
+};
+
+__device__ __forceinline__ float2 u_at(const PDArgs &A, long long i, bool pos)
+{
+    float2 u = A.a[i];
+    if (A.a_signed && !pos) u = dfx_neg(u);
+    if (A.b) u = dfx_add(u, dfx_mul(A.c1, A.b[i]));
+    return dfx_add(u, A.c2);
+}
+
+// conservative FP32 bounds of a double-float offset: never farther than o
+__device__ __forceinline__ float toward_zero(float2 o)
+{
+    return o.x > 0.f ? __fmul_rd(o.x, 0.99999988f) : __fmul_ru(o.x, 0.99999988f);
+}
+
+struct Acc {
+    float2 D;        // sum of d_i over free components
+    int nu, nf;      // signed count at C; free count
+    int ppx, pmx;    // components exactly at a breakpoint that count for the right / left slope
+    float bhi, blo;  // nearest breakpoint offsets above / below (conservative)
+};
+
+__device__ __forceinline__ void acc_zero(Acc &a)
+{
+    a.D = make_float2(0.f, 0.f);
+    a.nu = a.nf = a.ppx = a.pmx = 0;
+    a.bhi = INFINITY;
+    a.blo = -INFINITY;
+}
+
+// One component at delta.  t = y (d - delta); breakpoints (in delta) at
+// offsets e = d - delta (t = 0) and e - y C (t = C).
+__device__ __forceinline__ void eval_df(float2 d, bool pos, float2 dl, float2 Cd, Acc &a)
+{
+    const float r = d.x;
+    const float tf = pos ? (r - dl.x) : (dl.x - r);
+    const float er = (fabsf(r) + fabsf(dl.x) + Cd.x) * kMargin;
+    if (tf > Cd.x + er) {                       // certainly above C
+        a.nu += pos ? 1 : -1;
+        if (pos) a.bhi = fminf(a.bhi, tf - Cd.x - er);
+        else a.blo = fmaxf(a.blo, Cd.x - tf + er);
+        return;
+    }
+    if (tf < -er) {                             // certainly below 0
+        if (pos) a.blo = fmaxf(a.blo, tf + er);
+        else a.bhi = fminf(a.bhi, -tf - er);
+        return;
+    }
+    if (tf > er && tf < Cd.x - er) {            // certainly free
+        a.D = dfx_add(a.D, d);
+        ++a.nf;
+        if (pos) { a.bhi = fminf(a.bhi, tf - er); a.blo = fmaxf(a.blo, tf - Cd.x + er); }
+        else { a.blo = fmaxf(a.blo, -tf + er); a.bhi = fminf(a.bhi, Cd.x - tf - er); }
+        return;
+    }
+    // near a breakpoint: exact double-float comparison
+    const float2 e = dfx_sub(d, dl);
+    const float2 t = pos ? e : dfx_neg(e);
+    const float2 tc = dfx_sub(t, Cd);
+    if (tc.x > 0.f) {
+        a.nu += pos ? 1 : -1;
+    } else if (tc.x == 0.f) {                   // at C
+        a.nu += pos ? 1 : -1;
+        if (pos) ++a.ppx; else ++a.pmx;
+    } else if (t.x > 0.f) {
+        a.D = dfx_add(a.D, d);
+        ++a.nf;
+    } else if (t.x == 0.f) {                    // at 0
+        if (pos) ++a.pmx; else ++a.ppx;
+    }
+    const float2 o2 = pos ? tc : dfx_neg(tc);   // e - y C
+    if (e.x > 0.f) a.bhi = fminf(a.bhi, toward_zero(e));
+    else if (e.x < 0.f) a.blo = fmaxf(a.blo, toward_zero(e));
+    if (o2.x > 0.f) a.bhi = fminf(a.bhi, toward_zero(o2));
+    else if (o2.x < 0.f) a.blo = fmaxf(a.blo, toward_zero(o2));
+}
+
+__device__ __forceinline__ void acc_warp_reduce(Acc &a)
+{
+    a.nu = __reduce_add_sync(0xffffffffu, a.nu);
+    a.nf = __reduce_add_sync(0xffffffffu, a.nf);
+    a.ppx = __reduce_add_sync(0xffffffffu, a.ppx);
+    a.pmx = __reduce_add_sync(0xffffffffu, a.pmx);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a.bhi = fminf(a.bhi, __shfl_xor_sync(0xffffffffu, a.bhi, o));
+        a.blo = fmaxf(a.blo, __shfl_xor_sync(0xffffffffu, a.blo, o));
+        a.D = dfx_add(a.D, shfl_xor_f2(a.D, o));
+    }
+}
+
+struct SearchState {
+    float2 Ld, Ud;
+    float FL, FU, last_step;
+    int hL, hU, last_dir, nbr;
+};
+
+__device__ __forceinline__ float2 dfx_half(float2 a)
+{
+    return make_float2(0.5f * a.x, 0.5f * a.y);
+}
+
+// the final sums of one thread / warp / block: four double-float values and a count
+struct Sums {
+    float2 s[4];
+    int nupa;
+};
+
+__device__ __forceinline__ void sums_warp_reduce(Sums &v)
+{
+    v.nupa = __reduce_add_sync(0xffffffffu, v.nupa);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v.s[k] = dfx_add(v.s[k], shfl_xor_f2(v.s[k], o));
+}
+
+template <int EPT>
+__global__ void __launch_bounds__(kTPB, EPT >= 16 ? 1 : 2) projdf_kernel(PDArgs A)
+{
+    const int G = gridDim.x, blk = blockIdx.x, tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const long long NT = (long long)G * kTPB;
+    const float2 Cd = A.Cd;
+
+    __shared__ float2 sh_l0;
+    if (tid == 0) {
+        float2 l0 = A.lam0 ? __ldcg(A.lam0) : make_float2(0.f, 0.f);
+        if (!isfinite(l0.x) || !isfinite(l0.y)) l0 = make_float2(0.f, 0.f);
+        sh_l0 = l0;
+    }
+    __syncthreads();
+    const float2 l0 = sh_l0;
+
+    // d_i = y_i u_i - lambda_0, register resident; u is written here
+    float2 d[EPT];
+    unsigned posm = 0u, valm = 0u;
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+        const long long i = k * NT + (long long)blk * kTPB + tid;
+        d[k] = make_float2(0.f, 0.f);
+        if (i < A.n) {
+            const bool pos = A.y[i] > 0;
+            const float2 u = u_at(A, i, pos);
+            if (A.u_out) A.u_out[i] = u;
+            d[k] = dfx_sub(pos ? u : dfx_neg(u), l0);
+            posm |= (pos ? 1u : 0u) << k;
+            valm |= 1u << k;
+        }
+    }
+
+    __shared__ float4 sh_wf[kWarps];
+    __shared__ int4 sh_wi[kWarps];
+    __shared__ float2 sh_dl;
+    __shared__ int sh_done;
+    if (tid == 0) sh_dl = make_float2(0.f, 0.f);
+    __syncthreads();
+
+    // root-search state, used by thread 0 only (bracket in delta: f(L) > 0 > f(U))
+    __shared__ SearchState ss;
+    if (tid == 0) {
+        ss.Ld = ss.Ud = make_float2(0.f, 0.f);
+        ss.FL = ss.FU = ss.last_step = 0.f;
+        ss.hL = ss.hU = 0;
+        ss.last_dir = ss.nbr = 0;
+    }
+    int pass = 0;
+    bool alive = true;
+
+    for (;;) {
+        const float2 dl = sh_dl;
+        Acc a;
+        acc_zero(a);
+#pragma unroll
+        for (int k = 0; k < EPT; ++k)
+            if ((valm >> k) & 1u) eval_df(d[k], (posm >> k) & 1u, dl, Cd, a);
+        acc_warp_reduce(a);
+        if (lane == 0) {
+            sh_wf[warp] = make_float4(a.D.x, a.D.y, a.bhi, a.blo);
+            sh_wi[warp] = make_int4(a.nu, a.nf, a.ppx, a.pmx);
+        }
+        __syncthreads();
+        if (warp == 0) {
+            Acc b;
+            acc_zero(b);
+            if (lane < kWarps) {
+                const float4 f = sh_wf[lane];
+                const int4 c = sh_wi[lane];
+                b.D = make_float2(f.x, f.y); b.bhi = f.z; b.blo = f.w;
+                b.nu = c.x; b.nf = c.y; b.ppx = c.z; b.pmx = c.w;
+            }
+            acc_warp_reduce(b);
+            if (lane == 0) {
+                float *p = A.part + ((size_t)(pass & 1) * G + blk) * kStrideF;
+                __stcg(reinterpret_cast<float4 *>(p), make_float4(b.D.x, b.D.y, b.bhi, b.blo));
+                __stcg(reinterpret_cast<int4 *>(p + 4), make_int4(b.nu, b.nf, b.ppx, b.pmx));
+            }
+        }
+        if (!grid_barrier(A.bar, A.err)) { alive = false; break; }
+        if (warp == 0) {
+            // every block reduces all partials in the same order
+            Acc t;
+            acc_zero(t);
+            const float *slot = A.part + (size_t)(pass & 1) * G * kStrideF;
+            for (int bb = lane; bb < G; bb += 32) {
+                const float4 f = __ldcg(reinterpret_cast<const float4 *>(slot + (size_t)bb * kStrideF));
+                const int4 c = __ldcg(reinterpret_cast<const int4 *>(slot + (size_t)bb * kStrideF + 4));
+                t.D = dfx_add(t.D, make_float2(f.x, f.y));
+                t.bhi = fminf(t.bhi, f.z);
+                t.blo = fmaxf(t.blo, f.w);
+                t.nu += c.x; t.nf += c.y; t.ppx += c.z; t.pmx += c.w;
+            }
+            acc_warp_reduce(t);
+            if (lane == 0) {
+                // ---- decision (identical in every block) ----
+                float2 Ld = ss.Ld, Ud = ss.Ud;
+                float FL = ss.FL, FU = ss.FU, last_step = ss.last_step;
+                bool hL = ss.hL != 0, hU = ss.hU != 0;
+                int last_dir = ss.last_dir, nbr = ss.nbr;
+                const float2 F = dfx_add(dfx_add(dfx_mul(Cd, dfx_from_ll(t.nu)), t.D),
+                                         dfx_neg(dfx_mul(dl, dfx_from_ll(t.nf))));
+                const long long pr = (long long)t.nf + t.ppx, pl = (long long)t.nf + t.pmx;
+                int done = 0, dir = 0;
+                float2 next = dl, dhat = dl;
+                if (F.x == 0.f) {
+                    done = 1;
+                } else if (F.x > 0.f) {
+                    Ld = dl; FL = F.x; hL = true; dir = 1;
+                    if (pr > 0) {
+                        const float2 st = dfx_div(F, dfx_from_ll(pr));
+                        next = dfx_add(dl, st);
+                        if (st.x <= t.bhi) { done = 1; dhat = next; }
+                    } else {
+                        next = dfx_addf(dl, 2.f * t.bhi);   // flat piece: go past its end
+                    }
+                } else {
+                    Ud = dl; FU = F.x; hU = true; dir = -1;
+                    if (pl > 0) {
+                        const float2 st = dfx_div(F, dfx_from_ll(pl));
+                        next = dfx_add(dl, st);
+                        if (st.x >= t.blo) { done = 1; dhat = next; }
+                    } else {
+                        next = dfx_addf(dl, 2.f * t.blo);
+                    }
+                }
+                if (!done) {
+                    if (!(hL && hU)) {
+                        // not bracketed yet: steps in one direction at least double
+                        float stf = dfx_sub(next, dl).x;
+                        if (dir == last_dir && fabsf(stf) < 2.f * last_step) {
+                            stf = dir * 2.f * last_step;
+                            next = dfx_addf(dl, stf);
+                        }
+                        if (!(fabsf(stf) > 0.f)) {
+                            stf = dir * fmaxf(fabsf(dl.x) * 1.1920929e-07f, 1e-30f);
+                            next = dfx_addf(dl, stf);
+                        }
+                        last_step = fabsf(stf);
+                        last_dir = dir;
+                    } else {
+                        // bracketed: Newton point if inside, else secant; every third
+                        // bracketed pass bisects, so the bracket at least halves
+                        ++nbr;
+                        const bool inside = dfx_gt(next, Ld) && dfx_gt(Ud, next);
+                        if (nbr % 3 == 0) {
+                            next = dfx_half(dfx_add(Ld, Ud));
+                        } else if (!inside) {
+                            next = dfx_addf(Ld, dfx_sub(Ud, Ld).x * (FL / (FL - FU)));
+                            if (!(dfx_gt(next, Ld) && dfx_gt(Ud, next))) next = dfx_half(dfx_add(Ld, Ud));
+                        }
+                    }
+                    if (!isfinite(next.x) || (hL && hU && !(dfx_gt(next, Ld) && dfx_gt(Ud, next)))) {
+                        // no representable point strictly inside the bracket
+                        done = 1;
+                        dhat = (hL && (!hU || fabsf(FL) <= fabsf(FU))) ? Ld : Ud;
+                    } else if (pass + 1 >= kMaxPassDF) {
+                        done = 1;
+                        dhat = next;
+                        if (blk == 0) set_err(A.err, DEV_ROOT);
+                    }
+                }
+                sh_done = done;
+                sh_dl = done ? dhat : next;
+                ss.Ld = Ld; ss.Ud = Ud; ss.FL = FL; ss.FU = FU; ss.last_step = last_step;
+                ss.hL = hL; ss.hU = hU; ss.last_dir = last_dir; ss.nbr = nbr;
+            }
+        }
+        __syncthreads();
+        ++pass;
+        if (sh_done) break;
+    }
+
+    // ---------------- final phase: pi, sums, lists ----------------
+    const float2 dh = sh_dl;                    // delta-hat
+    const float2 lh = dfx_add(l0, dh);          // lambda-hat
+    Sums sm;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) sm.s[k] = make_float2(0.f, 0.f);
+    sm.nupa = 0;
+    float2 sq0 = make_float2(0.f, 0.f), sq1 = make_float2(0.f, 0.f);   // sums of squares
+    unsigned isJ = 0u, isD = 0u;
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+        if (!((valm >> k) & 1u)) continue;
+        const long long i = k * NT + (long long)blk * kTPB + tid;
+        const bool pos = (posm >> k) & 1u;
+        // pi_i and its class: 0 (= 0), 1 (free), 2 (= C); ties as the paper's clip
+        int pc;
+        float2 pk;
+        {
+            const float r = d[k].x;
+            const float tf = pos ? (r - dh.x) : (dh.x - r);
+            const float er = (fabsf(r) + fabsf(dh.x) + Cd.x) * kMargin;
+            if (tf > Cd.x + er) { pc = 2; pk = Cd; }
+            else if (tf < -er) { pc = 0; pk = make_float2(0.f, 0.f); }
+            else {
+                const float2 e = dfx_sub(d[k], dh);
+                const float2 t = pos ? e : dfx_neg(e);
+                if (!(t.x > 0.f)) { pc = 0; pk = make_float2(0.f, 0.f); }
+                else if (!dfx_gt(Cd, t)) { pc = 2; pk = Cd; }
+                else { pc = 1; pk = t; }
+            }
+        }
+        const float2 wp = (pc == 0) ? make_float2(0.f, 0.f) : (pos ? pk : dfx_neg(pk));
+        if (A.wpi_out) A.wpi_out[i] = wp;
+        if (pc == 1) isJ |= 1u << k;
+        float2 bw = make_float2(0.f, 0.f);
+        if (A.base_w) bw = A.base_w[i];
+        if (A.D && !dfx_same(wp, bw)) {
+            isD |= 1u << k;
+            A.dw_out[i] = dfx_sub(wp, bw);
+            A.dwa_out[i] = (pk.x + pk.y) - fabsf(bw.x + bw.y);
+        }
+        if (A.sums & SF_DPA) {
+            const float2 aw = A.alpha_w[i];
+            if (!dfx_same(aw, wp)) {
+                const float2 dx = dfx_sub(wp, aw);
+                sq0 = dfx_add(sq0, dfx_mul(dx, dx));
+            }
+        }
+        if (A.sums & SF_PSID) {
+            // psi difference term by term: pi(2u - pi) - pib(2ub - pib); pib from the
+            // base point (y o pi_base), ub = a (the base point's u)
+            const float2 pb = pos ? bw : dfx_neg(bw);
+            const int pbc = (bw.x == 0.f) ? 0 : (dfx_same(pb, Cd) ? 2 : 1);
+            if (pc == 2 && pbc == 2) {
+                sm.s[2] = dfx_add(sm.s[2], A.b[i]);   // 2C (u - ub) = 2C c1 b_i, factor applied below
+            } else if (pc != 0 || pbc != 0) {
+                const float2 u = u_at(A, i, pos);
+                const float2 ub = A.a[i];
+                const float2 t1 = dfx_mul(pk, dfx_sub(dfx_add(u, u), pk));
+                const float2 t2 = dfx_mul(pb, dfx_sub(dfx_add(ub, ub), pb));
+                sm.s[1] = dfx_add(sm.s[1], dfx_sub(t1, t2));
+            }
+        }
+        if (A.sums & SF_KKT) {
+            // alpha = a (y o alpha); |alpha - pi|^2, |alpha|^2, sum alpha, hinge
+            const float2 aw = A.a[i];
+            if (!dfx_same(aw, wp)) {
+                const float2 dx = dfx_sub(wp, aw);
+                sq0 = dfx_add(sq0, dfx_mul(dx, dx));
+            }
+            const float2 al = pos ? aw : dfx_neg(aw);
+            if (dfx_same(al, Cd)) {
+                ++sm.nupa;
+            } else if (al.x != 0.f) {
+                sq1 = dfx_add(sq1, dfx_mul(al, al));
+                sm.s[2] = dfx_add(sm.s[2], al);
+            }
+            const float2 m = dfx_add(A.b[i], pos ? lh : dfx_neg(lh));
+            const float2 h = dfx_sub(make_float2(1.f, 0.f), m);
+            if (h.x > 0.f) sm.s[3] = dfx_add(sm.s[3], h);
+        }
+    }
+    sm.s[0] = sq0;
+    if (A.sums & SF_KKT) sm.s[1] = sq1;
+
+    // per-(k, warp) list counts
+    __shared__ int sh_wc[EPT][kWarps][2];
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+        const unsigned bj = __ballot_sync(0xffffffffu, (isJ >> k) & 1u);
+        const unsigned bd = __ballot_sync(0xffffffffu, (isD >> k) & 1u);
+        if (lane == 0) { sh_wc[k][warp][0] = __popc(bj); sh_wc[k][warp][1] = __popc(bd); }
+    }
+    __shared__ float4 sh_s[kWarps][2];
+    __shared__ int sh_n[kWarps];
+    if (A.sums) {
+        sums_warp_reduce(sm);
+        if (lane == 0) {
+            sh_s[warp][0] = make_float4(sm.s[0].x, sm.s[0].y, sm.s[1].x, sm.s[1].y);
+            sh_s[warp][1] = make_float4(sm.s[2].x, sm.s[2].y, sm.s[3].x, sm.s[3].y);
+            sh_n[warp] = sm.nupa;
+        }
+    }
+    __syncthreads();
+    if (tid < EPT) {
+        int cj = 0, cd = 0;
+        for (int w = 0; w < kWarps; ++w) { cj += sh_wc[tid][w][0]; cd += sh_wc[tid][w][1]; }
+        A.cnt[((size_t)tid * G + blk) * 2 + 0] = cj;
+        A.cnt[((size_t)tid * G + blk) * 2 + 1] = cd;
+    }
+    if (A.sums && warp == 0) {
+        Sums b;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) b.s[k] = make_float2(0.f, 0.f);
+        b.nupa = 0;
+        if (lane < kWarps) {
+            const float4 f0 = sh_s[lane][0], f1 = sh_s[lane][1];
+            b.s[0] = make_float2(f0.x, f0.y); b.s[1] = make_float2(f0.z, f0.w);
+            b.s[2] = make_float2(f1.x, f1.y); b.s[3] = make_float2(f1.z, f1.w);
+            b.nupa = sh_n[lane];
+        }
+        sums_warp_reduce(b);
+        if (lane == 0) {
+            float *p = A.part + ((size_t)2 * G + blk) * kStrideF;
+            __stcg(reinterpret_cast<float4 *>(p), make_float4(b.s[0].x, b.s[0].y, b.s[1].x, b.s[1].y));
+            __stcg(reinterpret_cast<float4 *>(p + 4), make_float4(b.s[2].x, b.s[2].y, b.s[3].x, b.s[3].y));
+            __stcg(reinterpret_cast<int *>(p + 8), b.nupa);
+        }
+    }
+    if (!alive || !grid_barrier(A.bar, A.err)) return;
+
+    // offsets: off(k) = sum_{k'<k} total(k') + sum_{b'<blk} cnt(k, b')
+    __shared__ long long sh_off[EPT][2];
+    __shared__ long long sh_tot2[EPT][2];
+    for (int k = warp; k < EPT; k += kWarps) {
+        long long tj = 0, td = 0, pj = 0, pd = 0;
+#pragma unroll 8
+        for (int bb = lane; bb < G; bb += 32) {
+            const int2 cc = __ldcg(reinterpret_cast<const int2 *>(A.cnt + ((size_t)k * G + bb) * 2));
+            tj += cc.x; td += cc.y;
+            if (bb < blk) { pj += cc.x; pd += cc.y; }
+        }
+        tj = warp_sum_ll(tj); td = warp_sum_ll(td);
+        pj = warp_sum_ll(pj); pd = warp_sum_ll(pd);
+        if (lane == 0) { sh_tot2[k][0] = tj; sh_tot2[k][1] = td; sh_off[k][0] = pj; sh_off[k][1] = pd; }
+    }
+    __syncthreads();
+    if (blk == 0 && warp == 0) {
+        // block 0 publishes lambda-hat and the sums (fixed-order reduction)
+        Sums t;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) t.s[k] = make_float2(0.f, 0.f);
+        t.nupa = 0;
+        if (A.sums) {
+            for (int bb = lane; bb < G; bb += 32) {
+                const float *p = A.part + ((size_t)2 * G + bb) * kStrideF;
+                const float4 f0 = __ldcg(reinterpret_cast<const float4 *>(p));
+                const float4 f1 = __ldcg(reinterpret_cast<const float4 *>(p + 4));
+                t.s[0] = dfx_add(t.s[0], make_float2(f0.x, f0.y));
+                t.s[1] = dfx_add(t.s[1], make_float2(f0.z, f0.w));
+                t.s[2] = dfx_add(t.s[2], make_float2(f1.x, f1.y));
+                t.s[3] = dfx_add(t.s[3], make_float2(f1.z, f1.w));
+                t.nupa += __ldcg(reinterpret_cast<const int *>(p + 8));
+            }
+            sums_warp_reduce(t);
+        }
+        if (lane == 0) {
+            long long tj = 0, td = 0;
+            for (int k = 0; k < EPT; ++k) { tj += sh_tot2[k][0]; td += sh_tot2[k][1]; }
+            float2 s1 = t.s[1], s2 = t.s[2];
+            if (A.sums & SF_PSID) {
+                // + 2C c1 sum_{both at C} b_i
+                s1 = dfx_add(s1, dfx_mul(dfx_mul(make_float2(2.f * Cd.x, 2.f * Cd.y), A.c1), s2));
+                s2 = make_float2(0.f, 0.f);
+            }
+            if (A.sums & SF_KKT) {
+                const float2 nc = dfx_mul(Cd, dfx_from_ll(t.nupa));
+                s1 = dfx_add(s1, dfx_mul(nc, Cd));
+                s2 = dfx_add(s2, nc);
+            }
+            A.out->lamf = lh;
+            A.out->sumf[0] = t.s[0];
+            A.out->sumf[1] = s1;
+            A.out->sumf[2] = s2;
+            A.out->sumf[3] = t.s[3];
+            A.out->p = tj;
+            A.out->s = td;
+            A.out->passes = pass;
+            A.out->status = 0;
+            A.out->is_df = 1;
+        }
+    }
+    if (tid == 0) {
+        long long rj = 0, rd = 0;
+        for (int k = 0; k < EPT; ++k) {
+            const long long oj = rj + sh_off[k][0], od = rd + sh_off[k][1];
+            rj += sh_tot2[k][0]; rd += sh_tot2[k][1];
+            sh_off[k][0] = oj; sh_off[k][1] = od;
+        }
+    }
+    // exclusive prefix of the per-warp counts, one thread per (k, list)
+    for (int t = tid; t < 2 * EPT; t += kTPB) {
+        const int k = t >> 1, l = t & 1;
+        int run = 0;
+        for (int w = 0; w < kWarps; ++w) {
+            const int c = sh_wc[k][w][l];
+            sh_wc[k][w][l] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    if (A.J || A.D) {
+        const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+        for (int k = 0; k < EPT; ++k) {
+            const long long i = k * NT + (long long)blk * kTPB + tid;
+            const unsigned bj = __ballot_sync(0xffffffffu, (isJ >> k) & 1u);
+            const unsigned bd = __ballot_sync(0xffffffffu, (isD >> k) & 1u);
+            if (A.J && ((isJ >> k) & 1u)) A.J[sh_off[k][0] + sh_wc[k][warp][0] + __popc(bj & lt)] = (int32_t)i;
+            if (A.D && ((isD >> k) & 1u)) A.D[sh_off[k][1] + sh_wc[k][warp][1] + __popc(bd & lt)] = (int32_t)i;
+        }
+    }
+}
+
+float2 split_host(double v)
+{
+    const float hi = (float)v;
+    return make_float2(hi, (float)(v - (double)hi));
+}
+
+}  // namespace
+
+void *projdf_kernel_for(int ept)
+{
+    switch (ept) {
+    case 1: return (void *)projdf_kernel<1>;
+    case 2: return (void *)projdf_kernel<2>;
+    case 4: return (void *)projdf_kernel<4>;
+    case 8: return (void *)projdf_kernel<8>;
+    case 16: return (void *)projdf_kernel<16>;
+    default: return (void *)projdf_kernel<32>;
+    }
+}
+
+cudaError_t launch_project_df(Work &W, const ProjDF &in, ProjOut *out)
+{
+    if ((in.sums & SF_DPA) && !in.alpha_w) return cudaErrorInvalidValue;
+    if ((in.sums & SF_PSID) && (!in.base_w || !in.b || in.a_signed)) return cudaErrorInvalidValue;
+    if ((in.sums & SF_KKT) && (!in.b || !in.a_signed)) return cudaErrorInvalidValue;
+    if (in.D && (!in.dw_out || !in.dwa_out)) return cudaErrorInvalidValue;
+    PDArgs A;
+    A.a = in.a; A.a_signed = in.a_signed ? 1 : 0; A.b = in.b;
+    A.c1 = split_host(in.c1); A.c2 = split_host(in.c2);
+    A.y = W.y; A.n = W.n; A.Cd = split_host(W.C); A.sums = in.sums; A.lam0 = in.lam0;
+    A.u_out = in.u_out; A.wpi_out = in.wpi_out; A.alpha_w = in.alpha_w; A.base_w = in.base_w;
+    A.dw_out = in.dw_out; A.dwa_out = in.dwa_out; A.J = in.J; A.D = in.D;
+    A.part = reinterpret_cast<float *>(W.part); A.cnt = W.cnt; A.bar = W.bar; A.err = W.err; A.out = out;
+    void *args[] = {&A};
+    ++W.nlaunch;
+    return cudaLaunchCooperativeKernel(projdf_kernel_for(W.proj_ept), dim3(W.proj_grid), dim3(kTPB), args, 0, W.st);
+}
+
+}  // namespace svm

@@ -138,9 +138,9 @@ extern "C" const char *svm_ssnalm_last_error(const svm_ssnalm_t *h)
 
 static void free_work(Work &W)
 {
-    void *ptrs[] = {W.alpha, W.z, W.dz, W.qa, W.tmpn, W.zf, W.dzf, W.qaf, W.alphaf, W.v, W.dv, W.g, W.atp, W.atp2,
-                    W.h, W.w, W.tmpq, W.M, W.Lf, W.Mf, W.part, W.cnt, W.bar, W.rm_counter, W.err, W.pout, W.red,
-                    W.X_own, W.y_own};
+    void *ptrs[] = {W.alpha, W.z, W.dz, W.qa, W.tmpn, W.zf, W.dzf, W.qaf, W.alphaw, W.dw, W.dwa, W.atpa,
+                    W.atpa2, W.v, W.dv, W.g, W.atp, W.atp2, W.h, W.w, W.tmpq, W.M, W.Lf, W.Mf, W.part, W.cnt,
+                    W.bar, W.rm_counter, W.err, W.pout, W.red, W.X_own, W.y_own};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (int b = 0; b < 2; ++b) {
@@ -265,8 +265,10 @@ extern "C" svm_status svm_ssnalm_create(svm_ssnalm_t **out, const svm_problem *p
     W.part_len = part_gram > part_rm ? part_gram : part_rm;
     if (W.part_len < part_proj) W.part_len = part_proj;
     bool bad = dalloc(&W.alpha, n) || dalloc(&W.qa, n) || dalloc(&W.tmpn, n) ||
-               (W.df ? (dalloc(&W.zf, n) || dalloc(&W.dzf, n) || dalloc(&W.qaf, n) || dalloc(&W.alphaf, n))
+               (W.df ? (dalloc(&W.zf, n) || dalloc(&W.dzf, n) || dalloc(&W.qaf, n) || dalloc(&W.alphaw, n) ||
+                        dalloc(&W.dw, n) || dalloc(&W.dwa, n))
                      : (dalloc(&W.z, n) || dalloc(&W.dz, n))) ||
+               dalloc(&W.atpa, q) || dalloc(&W.atpa2, q) ||
                dalloc(&W.v, q) || dalloc(&W.dv, q) || dalloc(&W.g, q) ||
                dalloc(&W.atp, q) || dalloc(&W.atp2, q) || dalloc(&W.h, q) || dalloc(&W.w, q) || dalloc(&W.tmpq, q) ||
                dalloc(&W.M, q * q) || dalloc(&W.Lf, q * (q + 1)) || dalloc(&W.Mf, q * q) || dalloc(&W.part, W.part_len) || dalloc(&W.bar, 4) || dalloc(&W.rm_counter, 4) || dalloc(&W.err, 4) ||
@@ -321,6 +323,12 @@ static svm_status sync_read(svm_ssnalm *h)
     CK(cudaStreamSynchronize(W.st));
     h->syncs++;
     if (h->timing) flush_timing(h);
+    for (int k = 0; k < 4; ++k) {
+        ProjOut &o = W.h_pout[k];
+        if (!o.is_df) continue;
+        o.lam = (double)o.lamf.x + (double)o.lamf.y;
+        for (int j = 0; j < 4; ++j) o.sum[j] = (double)o.sumf[j].x + (double)o.sumf[j].y;
+    }
     const int e = W.h_err[0];
     if (e) {
         cudaMemsetAsync(W.err, 0, sizeof(int), W.st);
@@ -337,19 +345,27 @@ static svm_status sync_read(svm_ssnalm *h)
 // ProjOut slots: 0 step-level op, 1 + b for projection buffer b, 3 KKT.
 enum { SLOT_OP = 0, SLOT_KKT = 3 };
 
-// The KKT projection of eq. (4.1) at alpha given Q alpha: from W.alphaf and
-// W.qaf (double-float) when df, else from alpha and W.qa (FP64).
-static svm_status kkt_project(svm_ssnalm *h, const double *alpha, bool df)
+// The KKT projection of eq. (4.1) at alpha given Q alpha in W.qa (FP64).
+static svm_status kkt_project(svm_ssnalm *h, const double *alpha)
 {
     Work &W = h->W;
     ProjIn in;
-    in.mixed = df;
-    in.a = df ? (const void *)W.alphaf : (const void *)alpha;
-    in.b = df ? (const void *)W.qaf : (const void *)W.qa;
-    in.c1 = -1.0; in.c2 = 1.0;
+    in.a = alpha; in.b = W.qa; in.c1 = -1.0; in.c2 = 1.0;
     in.sums = SF_KKT; in.alpha = alpha;
     in.lam0 = &W.pout[SLOT_KKT].lam;
     CK(timed(h, TK_PROJ, [&] { return launch_project(W, in, &W.pout[SLOT_KKT]); }));
+    return SVM_OK;
+}
+
+// The same in double-float form: alpha given as y o alpha, Q alpha in W.qaf.
+static svm_status kkt_project_df(svm_ssnalm *h, const float2 *alpha_w)
+{
+    Work &W = h->W;
+    ProjDF in;
+    in.a = alpha_w; in.a_signed = true; in.b = W.qaf; in.c1 = -1.0; in.c2 = 1.0;
+    in.sums = SF_KKT;
+    in.lam0 = &W.pout[SLOT_KKT].lamf;
+    CK(timed(h, TK_PROJ, [&] { return launch_project_df(W, in, &W.pout[SLOT_KKT]); }));
     return SVM_OK;
 }
 
@@ -446,38 +462,47 @@ extern "C" svm_status svm_ssnalm_solve(svm_ssnalm_t *h, const double *alpha0, sv
     if (alpha0) {
         cudaMemcpyKind k = host_mem ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
         CK(cudaMemcpyAsync(W.tmpn, alpha0, n * sizeof(double), k, W.st));
-        ProjIn in;
-        in.a = W.tmpn; in.pi_out = W.alpha; in.S = W.pb[0].S; in.wpi_out = W.pb[0].wpi;
-        CK(timed(h, TK_PROJ, [&] { return launch_project(W, in, &W.pout[SLOT_OP]); }));
-        CK(timed(h, TK_RMATVEC, [&] {
-            return launch_rmatvec(W, W.alpha, W.pb[0].wpi, W.pb[0].S, &W.pout[SLOT_OP].s, W.v, -1);
-        }));
+        if (df) {
+            // y o Pi(alpha0) and A'Pi(alpha0) (the delta list against 0 is the support)
+            CK(split_vector(W, W.tmpn, false, W.pb[1].uf));
+            ProjDF in;
+            in.a = W.pb[1].uf;
+            in.wpi_out = W.alphaw; in.dw_out = W.dw; in.dwa_out = W.dwa; in.D = W.pb[0].S;
+            CK(timed(h, TK_PROJ, [&] { return launch_project_df(W, in, &W.pout[SLOT_OP]); }));
+            CK(timed(h, TK_RMATVEC, [&] {
+                return launch_rmatvec_df(W, W.dw, W.dwa, W.pb[0].S, &W.pout[SLOT_OP].s, nullptr, nullptr, W.v, nullptr, -1);
+            }));
+        } else {
+            ProjIn in;
+            in.a = W.tmpn; in.pi_out = W.alpha; in.S = W.pb[0].S; in.wpi_out = W.pb[0].wpi;
+            CK(timed(h, TK_PROJ, [&] { return launch_project(W, in, &W.pout[SLOT_OP]); }));
+            CK(timed(h, TK_RMATVEC, [&] {
+                return launch_rmatvec(W, W.alpha, W.pb[0].wpi, W.pb[0].S, &W.pout[SLOT_OP].s, W.v, -1);
+            }));
+        }
         copyq_kernel<<<1, 1024, 0, W.st>>>(q, W.v, W.w);
         ++W.nlaunch;
         CK(cudaGetLastError());
         // Q alpha = A w and z = A v (equal here) in one pass
-        if (df) {
-            CK(launch_unsign_df(W, W.pb[0].wpi, W.alphaf));
-            CK(timed(h, TK_MATVEC, [&] { return launch_matvec_df(W, W.w, W.qaf, W.v, W.zf); }));
-        } else {
-            CK(timed(h, TK_MATVEC, [&] { return launch_matvec(W, W.w, W.qa, W.v, W.z); }));
-        }
+        CK(timed(h, TK_MATVEC, [&] {
+            return df ? launch_matvec_df(W, W.w, W.qaf, W.v, W.zf) : launch_matvec(W, W.w, W.qa, W.v, W.z);
+        }));
         CK(cudaMemsetAsync(W.pout, 0, sizeof(ProjOut), W.st));
     } else {
-        CK(cudaMemsetAsync(W.alpha, 0, n * sizeof(double), W.st));
         CK(cudaMemsetAsync(W.v, 0, q * sizeof(double), W.st));
         CK(cudaMemsetAsync(W.w, 0, q * sizeof(double), W.st));
         if (df) {
-            CK(cudaMemsetAsync(W.alphaf, 0, n * sizeof(float2), W.st));
+            CK(cudaMemsetAsync(W.alphaw, 0, n * sizeof(float2), W.st));
             CK(cudaMemsetAsync(W.qaf, 0, n * sizeof(float2), W.st));
             CK(cudaMemsetAsync(W.zf, 0, n * sizeof(float2), W.st));
         } else {
+            CK(cudaMemsetAsync(W.alpha, 0, n * sizeof(double), W.st));
             CK(cudaMemsetAsync(W.qa, 0, n * sizeof(double), W.st));
             CK(cudaMemsetAsync(W.z, 0, n * sizeof(double), W.st));
         }
     }
     double sigma = P.sigma0;
-    if ((st = kkt_project(h, W.alpha, df)) != SVM_OK) return st;
+    if ((st = df ? kkt_project_df(h, W.alphaw) : kkt_project(h, W.alpha)) != SVM_OK) return st;
     if ((st = sync_read(h)) != SVM_OK) return st;
     double R = kkt_value(W.h_pout[SLOT_KKT]), Rprev = R;
     svm_status status = SVM_ERR_NOT_CONVERGED;
@@ -486,22 +511,34 @@ extern "C" svm_status svm_ssnalm_solve(svm_ssnalm_t *h, const double *alpha0, sv
     for (k = 0; k < P.max_outer && status != SVM_OK; ++k) {
         const double epsk = 0.1 * pow(0.5, (double)k);
         // z = A v holds here (from the start or from the fused product below).
-        // u = alpha^k - sigma (z - e); pi = Pi(u); J, S   (eq. (3.3))
+        // u = alpha^k - sigma (z - e); pi = Pi(u); J   (eq. (3.3))
         {
             ProjBuf &B = W.pb[cur];
-            ProjIn in;
-            in.mixed = df;
-            in.a = df ? (const void *)W.alphaf : (const void *)W.alpha;
-            in.b = df ? (const void *)W.zf : (const void *)W.z;
-            in.c1 = -sigma; in.c2 = sigma;
-            in.sums = SF_DPA; in.alpha = W.alpha;
-            in.lam0 = &W.pout[1 + cur].lam;
-            in.u_out = df ? (void *)B.uf : (void *)B.u; in.pi_out = B.pi; in.wpi_out = B.wpi; in.J = B.J; in.S = B.S;
-            CK(timed(h, TK_PROJ, [&] { return launch_project(W, in, &W.pout[1 + cur]); }));
-            // g = v - A'pi (eq. (3.10) in q coordinates) and its roundoff scale
-            CK(timed(h, TK_RMATVEC, [&] {
-                return launch_rmatvec(W, B.pi, B.wpi, B.S, &W.pout[1 + cur].s, W.atp, 1);
-            }));
+            if (df) {
+                // A'pi from scratch once per subproblem (the delta list against 0 is
+                // the support): the incremental products of the line search then
+                // carry roundoff from this subproblem only
+                ProjDF in;
+                in.a = W.alphaw; in.a_signed = true; in.b = W.zf; in.c1 = -sigma; in.c2 = sigma;
+                in.sums = SF_DPA; in.alpha_w = W.alphaw;
+                in.lam0 = &W.pout[1 + cur].lamf;
+                in.u_out = B.uf; in.wpi_out = B.wpi; in.dw_out = W.dw; in.dwa_out = W.dwa; in.J = B.J; in.D = B.S;
+                CK(timed(h, TK_PROJ, [&] { return launch_project_df(W, in, &W.pout[1 + cur]); }));
+                CK(timed(h, TK_RMATVEC, [&] {
+                    return launch_rmatvec_df(W, W.dw, W.dwa, B.S, &W.pout[1 + cur].s, nullptr, nullptr, W.atp, W.atpa, 1);
+                }));
+            } else {
+                ProjIn in;
+                in.a = W.alpha; in.b = W.z; in.c1 = -sigma; in.c2 = sigma;
+                in.sums = SF_DPA; in.alpha = W.alpha;
+                in.lam0 = &W.pout[1 + cur].lam;
+                in.u_out = B.u; in.pi_out = B.pi; in.wpi_out = B.wpi; in.J = B.J; in.S = B.S;
+                CK(timed(h, TK_PROJ, [&] { return launch_project(W, in, &W.pout[1 + cur]); }));
+                // g = v - A'pi (eq. (3.10) in q coordinates) and its roundoff scale
+                CK(timed(h, TK_RMATVEC, [&] {
+                    return launch_rmatvec(W, B.pi, B.wpi, B.S, &W.pout[1 + cur].s, W.atp, 1);
+                }));
+            }
             CK(launch_grad(W));
             if ((st = sync_read(h)) != SVM_OK) return st;
         }
@@ -511,7 +548,7 @@ extern "C" svm_status svm_ssnalm_solve(svm_ssnalm_t *h, const double *alpha0, sv
             const double gn = sqrt(W.h_red[0]);
             const double dx = sqrt(m.sum[0]);
             const double tol_in = fmin(epsk, epsk * dx) / sqrt(sigma);
-            const double floor_g = 1e-15 * sqrt(W.h_red[1]);
+            const double floor_g = (df ? 32e-15 : 1e-15) * sqrt(W.h_red[1]);
             if (!isfinite(gn)) { h->err = "non-finite gradient"; return SVM_ERR_NUMERIC; }
             if (h->trace)
                 fprintf(stderr, "[svm] k=%d j=%d sigma=%.3g p=%lld s=%lld |g|=%.3e tol=%.3e passes=%d lam=%.6g\n", k, j,
@@ -531,18 +568,28 @@ extern "C" svm_status svm_ssnalm_solve(svm_ssnalm_t *h, const double *alpha0, sv
             const int nxt = 1 - cur;
             for (int mtr = 0; mtr < P.max_ls; ++mtr) {
                 ProjBuf &B = W.pb[nxt];
-                ProjIn tr;
-                tr.mixed = df;
-                tr.a = df ? (const void *)W.pb[cur].uf : (const void *)W.pb[cur].u;
-                tr.b = df ? (const void *)W.dzf : (const void *)W.dz;
-                tr.c1 = -t * sigma; tr.c2 = 0.0;
-                tr.sums = SF_PSID | SF_DPA; tr.alpha = W.alpha; tr.pi_base = W.pb[cur].pi;
-                tr.lam0 = &W.pout[1 + cur].lam;
-                tr.u_out = df ? (void *)B.uf : (void *)B.u; tr.pi_out = B.pi; tr.wpi_out = B.wpi; tr.J = B.J; tr.S = B.S;
-                CK(timed(h, TK_PROJ, [&] { return launch_project(W, tr, &W.pout[1 + nxt]); }));
-                CK(timed(h, TK_RMATVEC, [&] {
-                    return launch_rmatvec(W, B.pi, B.wpi, B.S, &W.pout[1 + nxt].s, W.atp2, 1);
-                }));
+                if (df) {
+                    ProjDF tr;
+                    tr.a = W.pb[cur].uf; tr.b = W.dzf; tr.c1 = -t * sigma; tr.c2 = 0.0;
+                    tr.sums = SF_PSID | SF_DPA; tr.alpha_w = W.alphaw; tr.base_w = W.pb[cur].wpi;
+                    tr.lam0 = &W.pout[1 + cur].lamf;
+                    tr.u_out = B.uf; tr.wpi_out = B.wpi; tr.dw_out = W.dw; tr.dwa_out = W.dwa; tr.J = B.J; tr.D = B.S;
+                    CK(timed(h, TK_PROJ, [&] { return launch_project_df(W, tr, &W.pout[1 + nxt]); }));
+                    CK(timed(h, TK_RMATVEC, [&] {
+                        return launch_rmatvec_df(W, W.dw, W.dwa, B.S, &W.pout[1 + nxt].s, W.atp, W.atpa, W.atp2,
+                                                 W.atpa2, 1);
+                    }));
+                } else {
+                    ProjIn tr;
+                    tr.a = W.pb[cur].u; tr.b = W.dz; tr.c1 = -t * sigma; tr.c2 = 0.0;
+                    tr.sums = SF_PSID | SF_DPA; tr.alpha = W.alpha; tr.pi_base = W.pb[cur].pi;
+                    tr.lam0 = &W.pout[1 + cur].lam;
+                    tr.u_out = B.u; tr.pi_out = B.pi; tr.wpi_out = B.wpi; tr.J = B.J; tr.S = B.S;
+                    CK(timed(h, TK_PROJ, [&] { return launch_project(W, tr, &W.pout[1 + nxt]); }));
+                    CK(timed(h, TK_RMATVEC, [&] {
+                        return launch_rmatvec(W, B.pi, B.wpi, B.S, &W.pout[1 + nxt].s, W.atp2, 1);
+                    }));
+                }
                 grad_at_kernel<<<1, 1024, 0, W.st>>>(q, W.v, W.dv, t, W.atp2, W.tmpq, W.red);
                 ++W.nlaunch;
                 CK(cudaGetLastError());
@@ -563,13 +610,14 @@ extern "C" svm_status svm_ssnalm_solve(svm_ssnalm_t *h, const double *alpha0, sv
             ++W.nlaunch;
             CK(cudaGetLastError());
             std::swap(W.atp, W.atp2);   // A'pi of the accepted trial
+            std::swap(W.atpa, W.atpa2);
             cur = nxt;
         }
         inner_total += j;
         // alpha^{k+1} = Pi(u(w^{k+1}))  (eq. (3.5)): the buffer holding pi becomes
         // alpha (the old alpha buffer takes its place); A'alpha^{k+1} is the last A'pi
-        std::swap(W.alpha, W.pb[cur].pi);
-        if (df) CK(launch_unsign_df(W, W.pb[cur].wpi, W.alphaf));
+        if (df) std::swap(W.alphaw, W.pb[cur].wpi);
+        else std::swap(W.alpha, W.pb[cur].pi);
         copyq_kernel<<<1, 1024, 0, W.st>>>(q, W.atp, W.w);
         ++W.nlaunch;
         CK(cudaGetLastError());
@@ -577,7 +625,7 @@ extern "C" svm_status svm_ssnalm_solve(svm_ssnalm_t *h, const double *alpha0, sv
         CK(timed(h, TK_MATVEC, [&] {
             return df ? launch_matvec_df(W, W.w, W.qaf, W.v, W.zf) : launch_matvec(W, W.w, W.qa, W.v, W.z);
         }));
-        if ((st = kkt_project(h, W.alpha, df)) != SVM_OK) return st;
+        if ((st = df ? kkt_project_df(h, W.alphaw) : kkt_project(h, W.alpha)) != SVM_OK) return st;
         if ((st = sync_read(h)) != SVM_OK) return st;
         R = kkt_value(W.h_pout[SLOT_KKT]);
         if (h->trace)
@@ -592,6 +640,7 @@ extern "C" svm_status svm_ssnalm_solve(svm_ssnalm_t *h, const double *alpha0, sv
     // primal objective, gap, counts
     const ProjOut &kk = W.h_pout[SLOT_KKT];
     {
+        if (df) CK(join_vector(W, W.alphaw, true, W.alpha));
         cudaMemcpyKind kd = host_mem ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
         CK(cudaMemcpyAsync(res->alpha, W.alpha, n * sizeof(double), kd, W.st));
         CK(cudaMemcpyAsync(res->w, W.w, q * sizeof(double), kd, W.st));
@@ -599,7 +648,6 @@ extern "C" svm_status svm_ssnalm_solve(svm_ssnalm_t *h, const double *alpha0, sv
         count_kernel<<<W.nsm * 2, 256, 0, W.st>>>(n, W.alpha, W.C, W.red + 8);
         ++W.nlaunch;
         CK(cudaGetLastError());
-        CK(cudaMemcpyAsync(W.tmpq, W.w, q * sizeof(double), cudaMemcpyDeviceToDevice, W.st));
         double *hw = (double *)malloc(q * sizeof(double));
         if (!hw) { h->err = "host allocation failed"; return SVM_ERR_OOM; }
         cudaError_t e1 = cudaMemcpyAsync(hw, W.w, q * sizeof(double), cudaMemcpyDeviceToHost, W.st);
@@ -661,9 +709,19 @@ extern "C" svm_status svm_op_project(svm_ssnalm_t *h, const double *u, double *p
 {
     if (!h || !u || !pi) return SVM_ERR_INVALID_ARG;
     Work &W = h->W;
-    ProjIn in;
-    in.a = u; in.pi_out = pi; in.J = J; in.S = S;
-    CK(timed(h, TK_PROJ, [&] { return launch_project(W, in, &W.pout[SLOT_OP]); }));
+    if (W.df) {
+        // the double-float kernel of the mixed form: u split on the device, pi joined back
+        CK(split_vector(W, u, false, W.pb[1].uf));
+        ProjDF in;
+        in.a = W.pb[1].uf; in.wpi_out = W.pb[1].wpi; in.J = J;
+        if (S) { in.D = S; in.dw_out = W.dw; in.dwa_out = W.dwa; }   // the delta list against 0 is the support
+        CK(timed(h, TK_PROJ, [&] { return launch_project_df(W, in, &W.pout[SLOT_OP]); }));
+        CK(join_vector(W, W.pb[1].wpi, true, pi));
+    } else {
+        ProjIn in;
+        in.a = u; in.pi_out = pi; in.J = J; in.S = S;
+        CK(timed(h, TK_PROJ, [&] { return launch_project(W, in, &W.pout[SLOT_OP]); }));
+    }
     svm_status st = sync_read(h);
     if (st != SVM_OK) return st;
     if (lambda) *lambda = W.h_pout[SLOT_OP].lam;
@@ -691,8 +749,15 @@ extern "C" svm_status svm_op_kkt(svm_ssnalm_t *h, const double *alpha, double *k
         wc = W.pb[0].wpi;
     }
     CK(timed(h, TK_RMATVEC, [&] { return launch_rmatvec(W, alpha, wc, nullptr, nullptr, W.w, -1); }));
-    CK(timed(h, TK_MATVEC, [&] { return launch_matvec(W, W.w, W.qa); }));
-    svm_status st = kkt_project(h, alpha, false);
+    svm_status st;
+    if (W.df) {
+        // y o alpha split (pb[0].wpi) is the double-float alpha of the mixed form
+        CK(timed(h, TK_MATVEC, [&] { return launch_matvec_df(W, W.w, W.qaf); }));
+        st = kkt_project_df(h, W.pb[0].wpi);
+    } else {
+        CK(timed(h, TK_MATVEC, [&] { return launch_matvec(W, W.w, W.qa); }));
+        st = kkt_project(h, alpha);
+    }
     if (st != SVM_OK) return st;
     if ((st = sync_read(h)) != SVM_OK) return st;
     if (kkt) *kkt = kkt_value(W.h_pout[SLOT_KKT]);

@@ -3,7 +3,10 @@ ABI, against the FP64 CPU oracle on the same seeded inputs.
 
 Tolerances.  PLAIN_FP64 steps are FP64 with a different summation order than
 the oracle, so elementwise results agree to a few ulps of the summed
-magnitudes (rtol 1e-12 against the absolute-sum scale).  Index sets (J, S) are
+magnitudes (rtol 1e-12 against the absolute-sum scale).  The mixed form's
+projection runs in double-float arithmetic (~2^-48 relative per operation),
+so its pi agrees with clip(u - lambda y, 0, C) recomputed in FP64 to 1e-13 of
+the data's scale instead of bit for bit.  Index sets (J, S) are
 compared exactly except for components whose clipped value lies within
 roundoff of a bound, where either side is correct.  Whole solves are compared
 on what is unique (objective, w, b when free SVs exist) at the north-star
@@ -44,6 +47,17 @@ def make(X, y, C=1.0, **kw):
     return s, Xd, yd
 
 
+# The projection has two kernels: FP64 (PLAIN_FP64 handles) and double-float
+# (MIXED handles with FP32 X and q % 4 == 0).  X only fixes n for it.
+PROJ_KERNELS = ["fp64", "df"]
+
+
+def make_proj(n, y, C, kernel):
+    if kernel == "fp64":
+        return make(np.ones((n, 1)), y, C=C, precision=P.PREC_PLAIN_FP64)
+    return make(np.ones((n, 4), np.float32), y, C=C, precision=P.PREC_MIXED)
+
+
 # ------------------------------------------------------------------ matvecs
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -72,12 +86,16 @@ def test_matvec_rmatvec(prec, dtype, n, q):
 
 # ---------------------------------------------------------------- projection
 
-def _check_projection(u, y, C, pi, lam, J, S, p, s_):
+def _check_projection(u, y, C, pi, lam, J, S, p, s_, kernel="fp64"):
     pi_r, lam_r = oracle.project(u, y, C)
     scale = C + np.max(np.abs(u))
     np.testing.assert_allclose(pi, pi_r, rtol=0, atol=1e-12 * scale)
     t = u - lam * y.astype(np.float64)
-    np.testing.assert_array_equal(pi, np.clip(t, 0.0, C))    # pi = clip(u - lambda y) exactly
+    if kernel == "fp64":
+        np.testing.assert_array_equal(pi, np.clip(t, 0.0, C))    # pi = clip(u - lambda y) exactly
+    else:
+        np.testing.assert_allclose(pi, np.clip(t, 0.0, C), rtol=0, atol=1e-13 * scale)
+        assert np.all((pi == 0) | (pi == C) | ((pi > 0) & (pi < C)))
     assert abs(np.sum(y * pi)) <= 1e-11 * (1 + np.sum(pi))
     Jr = oracle.free_set(u, y, C, lam_r)
     ambiguous = np.minimum(np.abs(t), np.abs(t - C)) <= 1e-11 * scale
@@ -89,7 +107,8 @@ def _check_projection(u, y, C, pi, lam, J, S, p, s_):
     np.testing.assert_array_equal(S[:s_], Sr)
 
 
-def test_projection_worked_example():
+@pytest.mark.parametrize("kernel", PROJ_KERNELS)
+def test_projection_worked_example(kernel):
     g = {}
     import os
     for line in open(os.path.join(os.path.dirname(__file__), "golden", "projection_worked_n4.txt")):
@@ -97,8 +116,7 @@ def test_projection_worked_example():
             k, *v = line.split()
             g[k] = np.array([float(x) for x in v])
     y = g["y"].astype(np.int8)
-    X = np.ones((4, 2))
-    s, _, _ = make(X, y, C=g["C"][0])
+    s, _, _ = make_proj(4, y, g["C"][0], kernel)
     pi = torch.empty(4, dtype=torch.float64, device="cuda")
     J = torch.empty(4, dtype=torch.int32, device="cuda")
     S = torch.empty(4, dtype=torch.int32, device="cuda")
@@ -111,7 +129,8 @@ def test_projection_worked_example():
 
 @pytest.mark.parametrize("n,C,seed", [(5, 1.0, 0), (2000, 1.0, 1), (2000, 0.1, 2), (70001, 0.5, 3),
                                       (300000, 2.0, 4), (1_000_000, 0.1, 5)])
-def test_projection(n, C, seed):
+@pytest.mark.parametrize("kernel", PROJ_KERNELS)
+def test_projection(n, C, seed, kernel):
     rng = np.random.default_rng(seed)
     y = np.where(rng.random(n) < 0.45, 1, -1).astype(np.int8)
     y[0], y[1] = 1, -1
@@ -119,22 +138,21 @@ def test_projection(n, C, seed):
     # exact ties at the bounds for a few components
     if n >= 6:
         u[2:6] = [0.0, C, -0.0, C]
-    X = np.ones((n, 1))
-    s, _, _ = make(X, y, C=C)
+    s, _, _ = make_proj(n, y, C, kernel)
     pi = torch.empty(n, dtype=torch.float64, device="cuda")
     J = torch.empty(n, dtype=torch.int32, device="cuda")
     S = torch.empty(n, dtype=torch.int32, device="cuda")
     lam, p, sc = s.project(dev(u), pi, J, S)
-    _check_projection(u, y, C, host(pi), lam, host(J), host(S), p, sc)
+    _check_projection(u, y, C, host(pi), lam, host(J), host(S), p, sc, kernel)
 
 
-def test_projection_flat_segment():
+@pytest.mark.parametrize("kernel", PROJ_KERNELS)
+def test_projection_flat_segment(kernel):
     """All components saturate at the root (empty free set): pi is unique,
     lambda may be any point of the flat piece."""
     y = np.array([1, 1, -1, -1], np.int8)
     u = np.array([5.0, -3.0, 4.0, -2.0])
-    X = np.ones((4, 1))
-    s, _, _ = make(X, y, C=1.0)
+    s, _, _ = make_proj(4, y, 1.0, kernel)
     pi = torch.empty(4, dtype=torch.float64, device="cuda")
     lam, p, _ = s.project(dev(u), pi)
     pi_r, _ = oracle.project(u, y, 1.0)
@@ -191,8 +209,9 @@ def test_newton_empty_free_set():
 # --------------------------------------------------------------------- KKT
 
 @pytest.mark.parametrize("prec", PRECS)
-def test_kkt_residual(prec):
-    X, y = datagen.small(3000, 20, seed=3)
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])   # FP32 + MIXED: the double-float kernel
+def test_kkt_residual(prec, dtype):
+    X, y = datagen.small(3000, 20, seed=3, dtype=dtype)
     C = 0.7
     rng = np.random.default_rng(0)
     a, _ = oracle.project(rng.uniform(0, C, 3000), y, C)
@@ -258,6 +277,21 @@ def test_solve_host_memory_and_warm_start():
     _compare_solution(X, y, C, r, alpha, w, ref)
     # warm start from the solution: converges at once
     r2, alpha2, w2 = _solve_gpu(X, y, C, host_mem=True, alpha0=alpha)
+    _compare_solution(X, y, C, r2, alpha2, w2, ref)
+    assert r2["outer_iters"] <= 2
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_solve_warm_start_fp32(prec):
+    """Warm start through the double-float path (FP32 X, q % 4 == 0): from a
+    feasible point, then from the solution itself."""
+    X, y = datagen.small(4000, 64, seed=11, dtype=np.float32)
+    C = 0.5
+    ref = oracle.solve(X, y, C, tol=1e-10)
+    a0, _ = oracle.project(np.random.default_rng(2).uniform(0, C, 4000), y, C)
+    r, alpha, w = _solve_gpu(X, y, C, precision=prec, alpha0=a0)
+    _compare_solution(X, y, C, r, alpha, w, ref)
+    r2, alpha2, w2 = _solve_gpu(X, y, C, precision=prec, alpha0=alpha)
     _compare_solution(X, y, C, r2, alpha2, w2, ref)
     assert r2["outer_iters"] <= 2
 
