@@ -177,10 +177,8 @@ __global__ void __launch_bounds__(256) gram_df_kernel(const float *__restrict__ 
     const long long r1 = r0 + per < p ? r0 + per : p;
     __shared__ float sA[kGR][kGT + 1], sB[kGR][kGT + 1];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
-    float hs[4] = {0.f, 0.f, 0.f, 0.f}, hc[4] = {0.f, 0.f, 0.f, 0.f};
     float as[4] = {0.f, 0.f, 0.f, 0.f}, ac[4] = {0.f, 0.f, 0.f, 0.f};
     const int ca = ti * kGT, cb = tj * kGT;
-    (void)hs; (void)hc;
     float hsum = 0.f, hcmp = 0.f;
     for (long long rb = r0; rb < r1; rb += kGR) {
         for (int e = threadIdx.x; e < kGR * kGT; e += blockDim.x) {
@@ -458,333 +456,363 @@ __global__ void __launch_bounds__(1024) newton_pcg_kernel(int q, const double *_
 
 // ---- one-block dense SPD solver for q <= 200 (factor in shared memory) ----
 // L (FP32, row stride ld = q + 1, lower triangle) and rdiag = 1 / diag(L).
+// ---------------------------------------------------------------------------
+// Newton solve for q <= 128 in one block of 512 threads: FP32 Cholesky of
+// fl32(M) as the preconditioner of CG on M dv = -g with the operator applied
+// in double-float from the (hi, lo) split of M -- the CG of Algorithm 3,
+// Step 1.  No FP64 arithmetic except the final conversion of dv: on this part
+// an FP64 operation costs ~64 cycles of latency, so a q = 128 solve with FP64
+// vectors and scalars spends most of its time waiting on it.
+//
+// q is padded to qp = 32 ceil(q/32) with identity rows.  Shared memory holds
+// the double-float M (qp x qp, the CG operator; one bulk asynchronous copy
+// when q = qp) and the factor as a packed lower triangle.  The factor is
+// right-looking by 8-column panels: the critical path of a Cholesky is one
+// pivot after another, and an 8-wide diagonal block keeps each pivot step
+// short (7 shuffles) and its unrolled code small -- wider blocks factored by
+// one warp cost several times more per column.  Warp 0 factors the diagonal
+// block and forms its inverse Dinv_b, the rows below become A_rb Dinv_b'
+// (8-lane shuffle groups), and the trailing triangle is updated a warp per
+// row.  The preconditioner is applied as blocked triangular solves through
+// the Dinv_b.  CG stops at |M dv + g| <= max(min(eta, |g|^{1+tau}, 1e-10
+// |g|), 1e-14 |g|) (the tolerance itself in FP32) or after maxit steps; beta
+// is the flexible (Polak-Ribiere) form, robust to the FP32 preconditioner.
+constexpr int kCgThreads = 512;
+constexpr int kCgMaxQ = 128;
+constexpr int kPb = 8;   // panel width
 
-// Blocked right-looking Cholesky of the matrix already in L; returns false
-// (block-uniformly) when a pivot is not positive.
-__device__ bool chol_blocked(float *L, float *rdiag, int q, int ld, int *bad_sh)
+__device__ __forceinline__ int lpos(int i, int j)   // packed lower triangle, row-major
 {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    for (int kb = 0; kb < q; kb += 32) {
-        const int nb = (q - kb) < 32 ? (q - kb) : 32;
-        // (1) diagonal block by warp 0, row kb + lane in registers
-        if (warp == 0) {
-            float a[32];
-#pragma unroll
-            for (int k = 0; k < 32; ++k) a[k] = (lane < nb && k <= lane) ? L[(size_t)(kb + lane) * ld + kb + k] : 0.f;
-            bool ok = true;
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                if (j < nb) {
-                    const float d = __shfl_sync(0xffffffffu, a[j], j);
-                    const bool okj = (d > 0.f) && isfinite(d);
-                    ok = ok && okj;
-                    const float rs = okj ? rsqrtf(d) : 1.f;
-                    if (lane == j) a[j] = okj ? d * rs : 1.f;
-                    else if (lane > j) a[j] *= rs;
-#pragma unroll
-                    for (int k = j + 1; k < 32; ++k) {
-                        const float lkj = __shfl_sync(0xffffffffu, a[j], k);
-                        if (lane >= k) a[k] -= a[j] * lkj;
-                    }
-                }
-            }
-            if (lane < nb) {
-#pragma unroll
-                for (int k = 0; k < 32; ++k)
-                    if (k <= lane) L[(size_t)(kb + lane) * ld + kb + k] = a[k];
-                float dl = 1.f;
-#pragma unroll
-                for (int k = 0; k < 32; ++k)
-                    if (k == lane) dl = a[k];
-                rdiag[kb + lane] = 1.f / dl;
-            }
-            if (!ok && lane == 0) *bad_sh = 1;
-        }
-        __syncthreads();
-        if (*bad_sh) return false;
-        // (2) panel rows below the block: x L_bb' = a, a warp per row, lane j holds x_j
-        for (int i = kb + nb + warp; i < q; i += nw) {
-            float v = (lane < nb) ? L[(size_t)i * ld + kb + lane] : 0.f;
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                if (j < nb) {
-                    const float xj = __shfl_sync(0xffffffffu, v, j) * rdiag[kb + j];
-                    if (lane == j) v = xj;
-                    else if (lane > j && lane < nb) v -= xj * L[(size_t)(kb + lane) * ld + kb + j];
-                }
-            }
-            if (lane < nb) L[(size_t)i * ld + kb + lane] = v;
-        }
-        __syncthreads();
-        // (3) trailing update with 4x4 register tiles: L_ik -= sum_m L_i,kb+m L_k,kb+m
-        const int base = kb + nb, m = q - base;
-        if (m > 0) {
-            const int nbt = (m + 3) / 4;
-            const int ntile = nbt * (nbt + 1) / 2;
-            for (int t = tid; t < ntile; t += blockDim.x) {
-                int ti = 0, tt = t;
-                while (tt > ti) { tt -= ti + 1; ++ti; }
-                const int i0 = base + 4 * ti, k0 = base + 4 * tt;
-                float acc[4][4];
-#pragma unroll
-                for (int a = 0; a < 4; ++a)
-#pragma unroll
-                    for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-                for (int mm = 0; mm < nb; ++mm) {
-                    float li[4], lk[4];
-#pragma unroll
-                    for (int a = 0; a < 4; ++a) {
-                        li[a] = (i0 + a < q) ? L[(size_t)(i0 + a) * ld + kb + mm] : 0.f;
-                        lk[a] = (k0 + a < q) ? L[(size_t)(k0 + a) * ld + kb + mm] : 0.f;
-                    }
-#pragma unroll
-                    for (int a = 0; a < 4; ++a)
-#pragma unroll
-                        for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(li[a], lk[b], acc[a][b]);
-                }
-#pragma unroll
-                for (int a = 0; a < 4; ++a)
-#pragma unroll
-                    for (int b = 0; b < 4; ++b) {
-                        const int i = i0 + a, k = k0 + b;
-                        if (i < q && k <= i) L[(size_t)i * ld + k] -= acc[a][b];
-                    }
-            }
-        }
-        __syncthreads();
-    }
-    return true;
+    return ((i * (i + 1)) >> 1) + j;
 }
 
-// b <- (L L')^{-1} b (FP32, in shared memory), blocked: warp 0 solves each
-// 32-wide diagonal block with shuffles, all warps update the rest.
-__device__ void chol_solve_blocked(const float *L, const float *rdiag, int q, int ld, float *b)
+struct CgSmem {
+    float2 *M;    // qp x qp double-float M (zero padded)
+    float *L;     // packed lower triangle of the factor
+    float *D;     // (qp / kPb) blocks kPb x kPb: Dinv_b, row-major
+    float *t;     // qp: preconditioner work vector
+    float2 *X, *R, *P, *AP, *Z, *RO;
+};
+
+// warp 0, lanes 0..7: factor the diagonal block at kb and store its inverse;
+// false if a pivot is not positive
+__device__ __forceinline__ bool cg_diag8(float *L, int kb, float *Db)
 {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    // forward: L y = b
-    for (int kb = 0; kb < q; kb += 32) {
-        const int nb = (q - kb) < 32 ? (q - kb) : 32;
-        if (warp == 0) {
-            float v = (lane < nb) ? b[kb + lane] : 0.f;
+    const int lane = threadIdx.x & 31;
+    const bool on = lane < kPb;
+    float a[kPb];
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                if (j < nb) {
-                    const float yj = __shfl_sync(0xffffffffu, v, j) * rdiag[kb + j];
-                    if (lane == j) v = yj;
-                    else if (lane > j && lane < nb) v -= yj * L[(size_t)(kb + lane) * ld + kb + j];
-                }
+    for (int k = 0; k < kPb; ++k) a[k] = (on && k <= lane) ? L[lpos(kb + lane, kb + k)] : 0.f;
+    bool ok = true;
+    float rsd = 1.f;   // this lane's 1 / L_ii
+#pragma unroll
+    for (int j = 0; j < kPb; ++j) {
+        const float d = __shfl_sync(0xffffffffu, a[j], j);
+        const bool okj = (d > 0.f) && isfinite(d);
+        ok = ok && okj;
+        const float rs = okj ? rsqrtf(d) : 1.f;
+        if (lane == j) { a[j] = okj ? d * rs : 1.f; rsd = rs; }
+        else if (lane > j) a[j] *= rs;
+#pragma unroll
+        for (int k = 1; k < kPb; ++k) {
+            if (k > j) {
+                const float lkj = __shfl_sync(0xffffffffu, a[j], k);
+                if (lane >= k) a[k] = fmaf(-a[j], lkj, a[k]);
             }
-            if (lane < nb) b[kb + lane] = v;
         }
-        __syncthreads();
-        for (int i = kb + nb + warp; i < q; i += nw) {
-            float s = (lane < nb) ? L[(size_t)i * ld + kb + lane] * b[kb + lane] : 0.f;
-            s = warp_sumf(s);
-            if (lane == 0) b[i] -= s;
-        }
-        __syncthreads();
     }
-    // backward: L' x = y
-    const int last = ((q - 1) / 32) * 32;
-    for (int kb = last; kb >= 0; kb -= 32) {
-        const int nb = (q - kb) < 32 ? (q - kb) : 32;
-        if (warp == 0) {
-            float v = (lane < nb) ? b[kb + lane] : 0.f;
+    // lane c: column c of the inverse, x_i = (delta_ic - sum_{m<i} L_im x_m) / L_ii
+    float x[kPb];
 #pragma unroll
-            for (int j = 31; j >= 0; --j) {
-                if (j < nb) {
-                    const float xj = __shfl_sync(0xffffffffu, v, j) * rdiag[kb + j];
-                    if (lane == j) v = xj;
-                    else if (lane < j) v -= xj * L[(size_t)(kb + j) * ld + kb + lane];
-                }
+    for (int i = 0; i < kPb; ++i) {
+        float s = (i == lane) ? 1.f : 0.f;
+#pragma unroll
+        for (int m = 0; m < kPb; ++m)
+            if (m < i) s = fmaf(-__shfl_sync(0xffffffffu, a[m], i), x[m], s);
+        const float ri = __shfl_sync(0xffffffffu, rsd, i);   // every lane takes part in the shuffle
+        x[i] = (i >= lane) ? s * ri : 0.f;
+    }
+    if (on) {
+#pragma unroll
+        for (int k = 0; k < kPb; ++k) {
+            if (k <= lane) L[lpos(kb + lane, kb + k)] = a[k];
+            Db[k * kPb + lane] = x[k];
+        }
+    }
+    return ok;
+}
+
+// t <- (L L')^{-1} t (blocked triangular solves through the Dinv_b)
+__device__ __forceinline__ void cg_precond(const CgSmem &S, int qp)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nb = qp / kPb;
+    for (int b = 0; b < nb; ++b) {   // forward: L y = t
+        const int kb = b * kPb;
+        if (warp == 0) {
+            const float tv = lane < kPb ? S.t[kb + lane] : 0.f;
+            const float *Db = S.D + b * kPb * kPb;
+            float acc = 0.f;
+#pragma unroll
+            for (int k = 0; k < kPb; ++k)
+                acc = fmaf(lane < kPb ? Db[lane * kPb + k] : 0.f, __shfl_sync(0xffffffffu, tv, k), acc);
+            if (lane < kPb) S.t[kb + lane] = acc;
+        }
+        __syncthreads();
+        if (b + 1 < nb) {
+            const int r = kb + kPb + tid;
+            if (r < qp) {
+                float s = S.t[r];
+#pragma unroll
+                for (int k = 0; k < kPb; ++k) s = fmaf(-S.L[lpos(r, kb + k)], S.t[kb + k], s);
+                S.t[r] = s;
             }
-            if (lane < nb) b[kb + lane] = v;
+            __syncthreads();
+        }
+    }
+    for (int b = nb - 1; b >= 0; --b) {   // backward: L' x = y
+        const int kb = b * kPb;
+        if (warp == 0) {
+            const float tv = lane < kPb ? S.t[kb + lane] : 0.f;
+            const float *Db = S.D + b * kPb * kPb;
+            float acc = 0.f;
+#pragma unroll
+            for (int k = 0; k < kPb; ++k)
+                acc = fmaf(lane < kPb ? Db[k * kPb + lane] : 0.f, __shfl_sync(0xffffffffu, tv, k), acc);
+            if (lane < kPb) S.t[kb + lane] = acc;
         }
         __syncthreads();
-        for (int i = warp; i < kb; i += nw) {
-            float s = (lane < nb) ? L[(size_t)(kb + lane) * ld + i] * b[kb + lane] : 0.f;
-            s = warp_sumf(s);
-            if (lane == 0) b[i] -= s;
+        if (b > 0) {
+            if (tid < kb) {
+                float s = S.t[tid];
+#pragma unroll
+                for (int k = 0; k < kPb; ++k) s = fmaf(-S.L[lpos(kb + k, tid)], S.t[kb + k], s);
+                S.t[tid] = s;
+            }
+            __syncthreads();
         }
-        __syncthreads();
     }
 }
 
-// One block: FP32 Cholesky of fl32(M) (diagonal shift on breakdown) as the
-// preconditioner of CG on M dv = -g (operator in double-float from the
-// (hi, lo) split of M), stopped at |M dv + g| <= max(min(eta, |g|^{1+tau},
-// 1e-10 |g|), 1e-14 |g|) -- the CG of Algorithm 3, Step 1, capped as in
-// newton_pcg_kernel.  Every phase is parallel or a
-// 32-step shuffle chain: no thread walks a q-long chain.
-__global__ void __launch_bounds__(1024) newton_cg_smem_kernel(int q, const float2 *__restrict__ Mf,
-                                                              const double *__restrict__ g, double *__restrict__ dv,
-                                                              double eta, double tau, int maxit,
-                                                              double *__restrict__ info, int *err)
+// sum_j a_j b_j over j < qp in double-float; every thread returns the same value
+__device__ __forceinline__ float2 cg_dot(const float2 *a, const float2 *b, int qp, float2 *red)
 {
-    // Scalar FP64 work (norms, step sizes, the stopping test) is done by
-    // thread 0 and broadcast through shared memory: replicated across 32 warps
-    // it would occupy the SM's FP64 pipe for tens of microseconds.
-    extern __shared__ double dsm3[];
-    double *x = dsm3, *r = x + q, *pp = r + q, *Ap = pp + q, *rold = Ap + q, *z = rold + q;
-    float2 *pf = reinterpret_cast<float2 *>(z + q);
-    float *bz = reinterpret_cast<float *>(pf + q);
-    float *rdiag = bz + q;
-    const int ld = q + 1;
-    float *L = rdiag + q + ((4 - (q & 3)) & 3);
-    __shared__ double red[3][32];
-    __shared__ double sc_tol, sc_al, sc_beta, sc_rn;
-    __shared__ int sc_go;
-    __shared__ float sc_shift;
-    __shared__ int bad;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-    // block partial sums of up to three dot products over q: warp totals to red[*][warp]
-    auto dots = [&](const double *a0, const double *b0, const double *a1, const double *b1, const double *a2,
-                    const double *b2, int nd) {
-        double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-        for (int j = tid; j < q; j += nt) {
-            s0 = fma(a0[j], b0[j], s0);
-            if (nd > 1) s1 = fma(a1[j], b1[j], s1);
-            if (nd > 2) s2 = fma(a2[j], b2[j], s2);
-        }
-        if (warp < (q + 31) / 32) {   // only warps holding entries reduce (q <= 200: at most 7 warps)
-            s0 = warp_sum(s0);
-            if (nd > 1) s1 = warp_sum(s1);
-            if (nd > 2) s2 = warp_sum(s2);
-        }
-        if (lane == 0) { red[0][warp] = s0; red[1][warp] = s1; red[2][warp] = s2; }
-        __syncthreads();
-    };
-    const int nwq = (q + 31) / 32;   // warps that hold vector entries (q <= nt)
-    if (warp == 0) {
-        float md = 0.f;
-        for (int j = lane; j < q; j += 32) md = fmaxf(md, Mf[(size_t)j * q + j].x);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float2 s = make_float2(0.f, 0.f);
+    if (tid < qp) s = dfx_mul(a[tid], b[tid]);
+    if (warp < (qp >> 5)) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) md = fmaxf(md, __shfl_xor_sync(0xffffffffu, md, o));
-        if (lane == 0) {
-            sc_shift = 0.f;
-            sc_tol = (double)md;   // reused below as the shift scale
-        }
+        for (int o = 16; o > 0; o >>= 1) s = dfx_add(s, shfl_xor_f2(s, o));
+        if (lane == 0) red[warp] = s;
     }
     __syncthreads();
-    const float maxdiag = (float)sc_tol;
+    float2 t = red[0];
+    for (int w = 1; w < (qp >> 5); ++w) t = dfx_add(t, red[w]);
+    __syncthreads();   // red is reused by the next call
+    return t;
+}
+
+__global__ void __launch_bounds__(kCgThreads) newton_cg_fast_kernel(int q, const float2 *__restrict__ Mf,
+                                                                    const double *__restrict__ g,
+                                                                    double *__restrict__ dv, float eta, float tau,
+                                                                    int maxit, double *__restrict__ info, int *err)
+{
+    extern __shared__ float4 cg_sm4[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int qp = (q + 31) & ~31, nb = qp / kPb;
+    CgSmem S;
+    S.M = reinterpret_cast<float2 *>(cg_sm4);
+    S.L = reinterpret_cast<float *>(S.M + qp * qp);
+    S.D = S.L + ((qp * (qp + 1)) >> 1);
+    S.t = S.D + nb * kPb * kPb;
+    S.X = reinterpret_cast<float2 *>(S.t + qp);
+    S.R = S.X + qp; S.P = S.R + qp; S.AP = S.P + qp; S.Z = S.AP + qp; S.RO = S.Z + qp;
+    __shared__ float2 red[8];
+    __shared__ float sc_shift, sc_maxdiag;
+    __shared__ int bad, copy_ok;
+    __shared__ __align__(8) unsigned long long mbar;
+    // M into shared memory: one bulk copy when its rows need no padding
+    if (q == qp) {
+        if (tid == 0) {
+            mbar_init(&mbar, 1);
+            mbar_fence_init();
+            mbar_arrive_expect_tx(&mbar, (unsigned)(qp * qp * sizeof(float2)));
+            bulk_g2s(S.M, Mf, (unsigned)(qp * qp * sizeof(float2)), &mbar);
+            bool okc = mbar_wait_bounded(&mbar, 0, err);
+            if (!okc) okc = mbar_wait_bounded(&mbar, 0, err);   // wait again for the copy in flight
+            copy_ok = okc;
+        }
+    } else {
+        for (int i = warp; i < qp; i += nw)
+            for (int j = lane; j < qp; j += 32)
+                S.M[i * qp + j] = (i < q && j < q) ? Mf[(size_t)i * q + j] : make_float2(0.f, 0.f);
+        if (tid == 0) copy_ok = 1;
+    }
+    if (tid == 0) sc_shift = 0.f;
+    __syncthreads();
+    if (!copy_ok) return;
+    if (warp == 0) {
+        float md = 0.f;
+        for (int j = lane; j < q; j += 32) md = fmaxf(md, S.M[j * qp + j].x);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) md = fmaxf(md, __shfl_xor_sync(0xffffffffu, md, o));
+        if (lane == 0) sc_maxdiag = md;
+    }
+    __syncthreads();
     bool okf = false;
     for (int attempt = 0; attempt < 6 && !okf; ++attempt) {
         const float shift = sc_shift;
-        for (int i = warp; i < q; i += nw)
-            for (int j = lane; j <= i; j += 32) L[(size_t)i * ld + j] = Mf[(size_t)i * q + j].x + (i == j ? shift : 0.f);
+        for (int i = warp; i < qp; i += nw)
+            for (int j = lane; j <= i; j += 32)
+                S.L[lpos(i, j)] = (i < q) ? S.M[i * qp + j].x + (i == j ? shift : 0.f) : (i == j ? 1.f : 0.f);
         if (tid == 0) bad = 0;
         __syncthreads();
-        okf = chol_blocked(L, rdiag, q, ld, &bad);
+        for (int b = 0; b < nb; ++b) {
+            const int kb = b * kPb;
+            if (warp == 0) {
+                const bool ok = cg_diag8(S.L, kb, S.D + b * kPb * kPb);
+                if (!ok && lane == 0) bad = 1;
+            }
+            __syncthreads();
+            if (bad || b + 1 == nb) break;
+            {   // rows below: L_rc = sum_k A_rk Dinv_b[c][k]; 4 rows per warp, 8 lanes a row
+                const int grp = lane >> 3, c = lane & 7;
+                const float *Db = S.D + b * kPb * kPb;
+                float dr[kPb];
+#pragma unroll
+                for (int k = 0; k < kPb; ++k) dr[k] = Db[c * kPb + k];
+                for (int r0 = kb + kPb + warp * 4; r0 < qp; r0 += nw * 4) {
+                    const int r = r0 + grp;
+                    const float av = (r < qp) ? S.L[lpos(r, kb + c)] : 0.f;
+                    float acc = 0.f;
+#pragma unroll
+                    for (int k = 0; k < kPb; ++k) acc = fmaf(__shfl_sync(0xffffffffu, av, grp * 8 + k), dr[k], acc);
+                    if (r < qp) S.L[lpos(r, kb + c)] = acc;
+                }
+            }
+            __syncthreads();
+            // trailing triangle, a warp per row: A_rc -= sum_k L_rk L_ck, kb + 8 <= c <= r
+            for (int r = kb + kPb + warp; r < qp; r += nw) {
+                float lr[kPb];
+#pragma unroll
+                for (int k = 0; k < kPb; ++k) lr[k] = S.L[lpos(r, kb + k)];
+                for (int c = kb + kPb + lane; c <= r; c += 32) {
+                    const int pc = lpos(c, kb);
+                    float acc = 0.f;
+#pragma unroll
+                    for (int k = 0; k < kPb; ++k) acc = fmaf(lr[k], S.L[pc + k], acc);
+                    S.L[lpos(r, c)] -= acc;
+                }
+            }
+            __syncthreads();
+        }
+        okf = !bad;
         __syncthreads();
-        if (!okf && tid == 0) sc_shift = (shift == 0.f) ? 1e-7f * maxdiag : shift * 100.f;
+        if (!okf && tid == 0) sc_shift = (shift == 0.f) ? 1e-7f * sc_maxdiag : shift * 100.f;
         __syncthreads();
     }
     if (!okf) {
         if (tid == 0) set_err(err, DEV_CHOL);
         return;
     }
-    for (int j = tid; j < q; j += nt) { x[j] = 0.0; r[j] = -g[j]; bz[j] = (float)(-g[j]); }
-    __syncthreads();
-    chol_solve_blocked(L, rdiag, q, ld, bz);   // z = P r
-    for (int j = tid; j < q; j += nt) { z[j] = (double)bz[j]; pp[j] = z[j]; }
-    __syncthreads();
-    dots(r, r, r, z, r, r, 2);
-    double rz = 0.0;
-    if (tid == 0) {
-        double rr = 0.0, t = 0.0;
-        for (int w = 0; w < nwq; ++w) { rr += red[0][w]; t += red[1][w]; }
-        const double gn = sqrt(rr);
-        sc_tol = fmax(fmin(fmin(eta, pow(gn, 1.0 + tau)), 1e-10 * gn), 1e-14 * gn);
-        sc_rn = gn;
-        sc_al = t;   // rz
-        sc_go = gn > sc_tol;
+    // CG on M dv = -g in double-float
+    if (tid < qp) {
+        float2 r0 = make_float2(0.f, 0.f);
+        if (tid < q) {
+            const double v = -g[tid];
+            const float hi = (float)v;
+            r0 = make_float2(hi, (float)(v - (double)hi));
+        }
+        S.X[tid] = make_float2(0.f, 0.f);
+        S.R[tid] = r0;
+        S.t[tid] = r0.x + r0.y;
     }
     __syncthreads();
-    rz = sc_al;
+    float2 rr = cg_dot(S.R, S.R, qp, red);
+    const float gn = sqrtf(fmaxf(rr.x, 0.f));
+    const float tol = fmaxf(fminf(fminf(eta, powf(gn, 1.f + tau)), 1e-10f * gn), 1e-14f * gn);
+    const float tol2 = tol * tol;
+    cg_precond(S, qp);
+    if (tid < qp) { S.Z[tid] = make_float2(S.t[tid], 0.f); S.P[tid] = S.Z[tid]; }
+    __syncthreads();
+    float2 rz = cg_dot(S.R, S.Z, qp, red);
     int it = 0;
-    while (sc_go && it < maxit) {
-        for (int j = tid; j < q; j += nt) {
-            const float hi = (float)pp[j];
-            pf[j] = make_float2(hi, (float)(pp[j] - (double)hi));
-        }
-        __syncthreads();
-        for (int i = warp; i < q; i += nw) {
-            float sh = 0.f, sc = 0.f;
-            const float2 *mrow = Mf + (size_t)i * q;
-            for (int j = lane; j < q; j += 32) {
-                const float2 a = mrow[j], bb = pf[j];
-                float p0, e0, sn, t0;
-                two_prod(a.x, bb.x, p0, e0);
-                e0 = fmaf(a.x, bb.y, fmaf(a.y, bb.x, e0));
-                two_sum(sh, p0, sn, t0);
-                sh = sn;
-                sc += t0 + e0;
+    bool go = rr.x > tol2;
+    while (go && it < maxit) {
+        // AP = M P: a warp per row, Dot2-style (s, c) sums of double-float products
+        float2 pl[kCgMaxQ / 32];
+#pragma unroll
+        for (int c = 0; c < kCgMaxQ / 32; ++c) pl[c] = (lane + 32 * c < qp) ? S.P[lane + 32 * c] : make_float2(0.f, 0.f);
+        for (int i = warp; i < qp; i += nw) {
+            float s = 0.f, c = 0.f;
+#pragma unroll
+            for (int cc = 0; cc < kCgMaxQ / 32; ++cc) {
+                const int j = lane + 32 * cc;
+                if (j < qp) {
+                    const float2 a = S.M[i * qp + j], b2 = pl[cc];
+                    float p0, e0, sn, t0;
+                    two_prod(a.x, b2.x, p0, e0);
+                    e0 = fmaf(a.x, b2.y, fmaf(a.y, b2.x, e0));
+                    two_sum(s, p0, sn, t0);
+                    s = sn;
+                    c += t0 + e0;
+                }
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-                const float s2 = __shfl_xor_sync(0xffffffffu, sh, o), c2 = __shfl_xor_sync(0xffffffffu, sc, o);
+                const float s2 = __shfl_xor_sync(0xffffffffu, s, o), c2 = __shfl_xor_sync(0xffffffffu, c, o);
                 float sn, e;
-                two_sum(sh, s2, sn, e);
-                e += sc + c2;
-                sh = sn + e;
-                sc = e - (sh - sn);
+                two_sum(s, s2, sn, e);
+                s = sn;
+                c += e + c2;
             }
-            if (lane == 0) Ap[i] = (double)sh + (double)sc;
+            if (lane == 0) { float hi, lo; two_sum(s, c, hi, lo); S.AP[i] = make_float2(hi, lo); }
         }
         __syncthreads();
-        dots(pp, Ap, pp, pp, pp, pp, 1);
-        if (tid == 0) {
-            double pAp = 0.0;
-            for (int w = 0; w < nwq; ++w) pAp += red[0][w];
-            sc_go = pAp > 0.0;
-            sc_al = sc_go ? rz / pAp : 0.0;
-        }
-        __syncthreads();
-        if (!sc_go) break;
-        const double al = sc_al;
-        for (int j = tid; j < q; j += nt) {
-            x[j] = fma(al, pp[j], x[j]);
-            rold[j] = r[j];
-            r[j] = fma(-al, Ap[j], r[j]);
-            bz[j] = (float)r[j];
+        const float2 pap = cg_dot(S.P, S.AP, qp, red);
+        if (!(pap.x > 0.f)) break;
+        const float2 al = dfx_div(rz, pap);
+        if (tid < qp) {
+            S.X[tid] = dfx_add(S.X[tid], dfx_mul(al, S.P[tid]));
+            S.RO[tid] = S.R[tid];
+            const float2 rn = dfx_sub(S.R[tid], dfx_mul(al, S.AP[tid]));
+            S.R[tid] = rn;
+            S.t[tid] = rn.x + rn.y;
         }
         __syncthreads();
         ++it;
-        dots(r, r, r, r, r, r, 1);
-        if (tid == 0) {
-            double rr = 0.0;
-            for (int w = 0; w < nwq; ++w) rr += red[0][w];
-            sc_rn = sqrt(rr);
-            sc_go = sc_rn > sc_tol;
-        }
+        rr = cg_dot(S.R, S.R, qp, red);
+        go = rr.x > tol2;
+        if (!go) break;
+        cg_precond(S, qp);
+        if (tid < qp) S.Z[tid] = make_float2(S.t[tid], 0.f);
         __syncthreads();
-        if (!sc_go) break;
-        chol_solve_blocked(L, rdiag, q, ld, bz);
-        for (int j = tid; j < q; j += nt) z[j] = (double)bz[j];
-        __syncthreads();
-        // flexible (Polak-Ribiere) beta: robust to the FP32 preconditioner
-        dots(r, z, rold, z, r, r, 2);
-        if (tid == 0) {
-            double rzn = 0.0, rzo = 0.0;
-            for (int w = 0; w < nwq; ++w) { rzn += red[0][w]; rzo += red[1][w]; }
-            sc_beta = fmax(0.0, (rzn - rzo) / rz);
-            sc_al = rzn;
-        }
-        __syncthreads();
-        const double beta = sc_beta;
-        rz = sc_al;
-        for (int j = tid; j < q; j += nt) pp[j] = fma(beta, pp[j], z[j]);
+        const float2 rzn = cg_dot(S.R, S.Z, qp, red);
+        const float2 rzo = cg_dot(S.RO, S.Z, qp, red);
+        float2 beta = dfx_div(dfx_sub(rzn, rzo), rz);
+        if (!(beta.x > 0.f)) beta = make_float2(0.f, 0.f);
+        rz = rzn;
+        if (tid < qp) S.P[tid] = dfx_add(S.Z[tid], dfx_mul(beta, S.P[tid]));
         __syncthreads();
     }
-    for (int j = tid; j < q; j += nt) dv[j] = x[j];
-    if (tid == 0 && info) { info[0] = it; info[1] = sc_rn; info[2] = sc_shift; }
+    if (tid < q) dv[tid] = (double)S.X[tid].x + (double)S.X[tid].y;
+    if (tid == 0 && info) {
+        info[0] = it;
+        info[1] = sqrt((double)fmaxf(rr.x, 0.f));
+        info[2] = sc_shift;
+    }
+}
+
+static size_t cg_fast_smem(int q)
+{
+    const size_t qp = (size_t)((q + 31) & ~31);
+    return qp * qp * sizeof(float2) + ((qp * (qp + 1)) / 2 + (qp / kPb) * kPb * kPb + qp) * sizeof(float) +
+           6 * qp * sizeof(float2);
 }
 
 static int g_cgs_attr = 0;
 
 static int g_chol_smem_set = 0;
-static int g_pcg_smem_set = 0;
 
 cudaError_t launch_newton(Work &W, const int32_t *J, long long p_host, const long long *p_dev, double sigma,
                           const double *g, double *dv)
@@ -816,16 +844,17 @@ cudaError_t launch_newton(Work &W, const int32_t *J, long long p_host, const lon
     if (cg) {
         // FP32-Cholesky-preconditioned CG on the FP64 matrix (Algorithm 3's inexact solve)
         double *info = W.red + 12;
-        const size_t smem_new = (size_t)6 * q * sizeof(double) + (size_t)q * sizeof(float2) + (size_t)2 * q * sizeof(float) +
-                                16 + (size_t)q * (q + 1) * sizeof(float);
-        if (smem_new <= (size_t)200 * 1024) {
+        if (q <= kCgMaxQ) {
+            const size_t smem_new = cg_fast_smem(q);
             if (!g_cgs_attr) {
-                const cudaError_t ea = cudaFuncSetAttribute(newton_cg_smem_kernel,
-                                                            cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+                const cudaError_t ea = cudaFuncSetAttribute(newton_cg_fast_kernel,
+                                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                            (int)cg_fast_smem(kCgMaxQ));
                 if (ea != cudaSuccess) return ea;
                 g_cgs_attr = 1;
             }
-            newton_cg_smem_kernel<<<1, 1024, smem_new, W.st>>>(q, W.Mf, g, dv, W.eta, W.tau, W.cg_maxit, info, W.err);
+            newton_cg_fast_kernel<<<1, kCgThreads, smem_new, W.st>>>(q, W.Mf, g, dv, (float)W.eta, (float)W.tau,
+                                                                    W.cg_maxit, info, W.err);
         } else {
             const size_t vec = (size_t)6 * q * sizeof(double) + (size_t)q * sizeof(float2);
             newton_pcg_kernel<false, 32><<<1, 1024, vec, W.st>>>(q, W.M, W.Mf, W.Lf, g, dv, W.eta, W.tau, W.cg_maxit,
