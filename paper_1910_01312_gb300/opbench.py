@@ -1,0 +1,85 @@
+"""Per-operation timing of the solver on synthetic data.
+
+    python -m paper_1910_01312_gb300.opbench --op solve --n 400000
+    python -m paper_1910_01312_gb300.opbench --op matvec --n 1000000 --reps 20
+
+Ops: ``solve`` (one cold solve after one warm-up, both forms of the stated
+precision), ``matvec`` (z = A v), ``rmatvec`` (A'c over all rows), ``project``
+(the projection at a random u), ``newton`` (the reduced Newton system on a
+random free set of size --p).  The data are the two-Gaussian workload of
+``datagen.gauss1m`` at the requested n and q.  Prints one JSON line with the
+mean time per call from CUDA events on the solver's stream.  Used for the
+profiles: a small case of the same kernels the solve runs.
+"""
+import argparse
+import json
+
+import numpy as np
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--op", default="solve", choices=["solve", "matvec", "rmatvec", "project", "newton"])
+    ap.add_argument("--n", type=int, default=400_000)
+    ap.add_argument("--q", type=int, default=128)
+    ap.add_argument("--p", type=int, default=150)
+    ap.add_argument("--sigma", type=float, default=625.0)
+    ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "plain"])
+    args = ap.parse_args(argv)
+
+    import torch
+
+    import datagen
+    from . import binding as B
+
+    B.load()
+    X, y, C = datagen.gauss1m(0, n=args.n, q=args.q)
+    n, q = X.shape
+    Xd, yd = torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda()
+    stream = torch.cuda.current_stream()
+    prec = B.PREC_MIXED if args.precision == "mixed" else B.PREC_PLAIN_FP64
+    s = B.Solver(Xd, yd, C_=C, tol=1e-6, precision=prec, stream=stream.cuda_stream)
+    rng = np.random.default_rng(0)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+    if args.op == "solve":
+        alpha = torch.zeros(n, dtype=torch.float64, device="cuda")
+        w = torch.zeros(q, dtype=torch.float64, device="cuda")
+        call = lambda: s.solve(alpha, w)
+    elif args.op == "matvec":
+        v, z = dev(rng.normal(size=q)), torch.empty(n, dtype=torch.float64, device="cuda")
+        call = lambda: s.matvec(v, z)
+    elif args.op == "rmatvec":
+        c = dev(np.where(rng.random(n) < 0.8, C, 0.0))
+        o = torch.empty(q, dtype=torch.float64, device="cuda")
+        call = lambda: s.rmatvec(c, o)
+    elif args.op == "project":
+        u = dev(rng.normal(0.05, 0.2, n))
+        pi = torch.empty(n, dtype=torch.float64, device="cuda")
+        J, S = (torch.empty(n, dtype=torch.int32, device="cuda") for _ in range(2))
+        call = lambda: s.project(u, pi, J, S)
+    else:
+        J = dev(np.sort(rng.choice(n, args.p, replace=False)).astype(np.int32))
+        g, dv = dev(rng.normal(size=q) * 1e-2), torch.empty(q, dtype=torch.float64, device="cuda")
+        call = lambda: s.newton(J, args.p, args.sigma, g, dv)
+
+    call()                                  # warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.reps):
+        out = call()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    line = {"op": args.op, "n": n, "q": q, "precision": args.precision, "reps": args.reps,
+            "ms_per_call": e0.elapsed_time(e1) / args.reps}
+    if args.op == "solve":
+        line.update({"outer": out["outer_iters"], "inner": out["inner_iters_total"], "kkt": out["kkt"]})
+    print(json.dumps(line), flush=True)
+    s.close()
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())
