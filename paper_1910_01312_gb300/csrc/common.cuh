@@ -214,6 +214,43 @@ __device__ __forceinline__ float2 shfl_xor_f2(float2 v, int o)
     return make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
 }
 
+// ---------------------------------------------------------------------------
+// Shared by the product kernels.
+template <typename TX> struct Vec;
+template <> struct Vec<float> { using T = float4; static constexpr int W = 4; };
+template <> struct Vec<double> { using T = double2; static constexpr int W = 2; };
+
+__device__ __forceinline__ void vload(const float4 *p, double *o)
+{
+    float4 t = __ldcs(p);
+    o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+}
+__device__ __forceinline__ void vload(const double2 *p, double *o)
+{
+    double2 t = __ldcs(p);
+    o[0] = t.x; o[1] = t.y;
+}
+
+// One Dot2 step: (s, c) += x * (w.x + w.y), x exact FP32.
+__device__ __forceinline__ void dot2_step(float x, float2 w, float &s, float &c)
+{
+    float p, e, sn, t;
+    two_prod(x, w.x, p, e);
+    two_sum(s, p, sn, t);
+    s = sn;
+    c = fmaf(x, w.y, c + (t + e));
+}
+
+// (s, c) += (s2, c2) for double-float pairs.
+__device__ __forceinline__ void df_acc(float &s, float &c, float s2, float c2)
+{
+    float sn, e;
+    two_sum(s, s2, sn, e);
+    e += c + c2;
+    s = sn + e;
+    c = e - (s - sn);
+}
+
 }  // namespace svm
 
 namespace svm {

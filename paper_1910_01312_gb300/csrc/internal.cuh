@@ -101,7 +101,7 @@ struct Work {
     ProjBuf pb[2];            // current / trial projection buffers
     // q-vectors
     double *v = nullptr, *dv = nullptr, *g = nullptr, *atp = nullptr, *atp2 = nullptr, *h = nullptr,
-           *w = nullptr, *tmpq = nullptr;
+           *w = nullptr, *tmpq = nullptr, *vt = nullptr;   // vt: v + t dv at a trial point
     double *M = nullptr;      // q*q Newton matrix / Cholesky factor
     float *Lf = nullptr;      // q*(q+1) FP32 factor when it does not fit in shared memory
     float2 *Mf = nullptr;     // q*q FP32 (hi, lo) split of M (double-float CG operator)
@@ -152,8 +152,16 @@ cudaError_t launch_rmatvec(Work &W, const double *c, const float2 *wc, const int
 // out = base + sum_{i in idx} wc_i x_i (double-float weights, Dot2 sums, the
 // count read from *cnt_dev), aout = abase + sum_i wa_i |x_i| (FP32) and
 // red[slot] = |aout|^2; base and abase may be null (zero).
+// Optional epilogue of launch_rmatvec_df: vt = v + t dv (dv nullable), g = vt - out,
+// red[0] = |g|^2 (the gradient of eq. (3.10) at the point whose A'pi was formed).
+struct GradOut {
+    const double *v = nullptr, *dv = nullptr;
+    double t = 0.0;
+    double *g = nullptr, *vt = nullptr;
+};
 cudaError_t launch_rmatvec_df(Work &W, const float2 *wc, const float *wa, const int32_t *idx, const long long *cnt_dev,
-                              const double *base, const float *abase, double *out, float *aout, int slot);
+                              const double *base, const float *abase, double *out, float *aout, int slot,
+                              const GradOut &go = GradOut());
 // wc_i = y_i c_i as an FP32 (hi, lo) pair (input of the mixed A' c)
 cudaError_t split_weights(Work &W, const double *c, float2 *wc);
 // a_i = (y_i when signed, else 1) * c_i as a double-float pair
@@ -167,8 +175,8 @@ cudaError_t launch_vaxpy(Work &W, double t); // v += t dv
 cudaError_t launch_negcopy(Work &W, const double *g, double *dv); // dv = -g
 
 // Newton direction (I + sigma A'PA) dv = -g on the free set J (p from *p_dev
-// when p_host < 0).
+// when p_host < 0); with dots, also red[2] = g'dv, red[3] = v'dv, red[4] = dv'dv.
 cudaError_t launch_newton(Work &W, const int32_t *J, long long p_host, const long long *p_dev,
-                          double sigma, const double *g, double *dv);
+                          double sigma, const double *g, double *dv, bool dots = false);
 
 }  // namespace svm

@@ -164,8 +164,8 @@ __global__ void __launch_bounds__(1024) chol_solve_kernel(int q, double *__restr
 // Gram of FP32 rows with exact products (TwoProd) and double-float sums
 // (TwoSum) on the FP32 pipes; same tiling and outputs as gram_kernel.
 __global__ void __launch_bounds__(256) gram_df_kernel(const float *__restrict__ X, int q, const int32_t *__restrict__ J,
-                                                      long long p, int KS, double *__restrict__ part,
-                                                      double *__restrict__ hpart)
+                                                      long long p, int KS, float2 *__restrict__ part,
+                                                      float2 *__restrict__ hpart)
 {
     int t = blockIdx.x;
     int ti = 0;
@@ -214,13 +214,45 @@ __global__ void __launch_bounds__(256) gram_df_kernel(const float *__restrict__ 
         }
         __syncthreads();
     }
-    double *P = part + (size_t)ks * q * q;
+    // double-float partials (normalised hi/lo), no FP64
+    float2 *P = part + (size_t)ks * q * q;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const int a = ca + ty + 8 * k, b = cb + tx;
-        if (a < q && b < q) P[(size_t)a * q + b] = (double)as[k] + (double)ac[k];
+        if (a < q && b < q) {
+            float hi, lo;
+            two_sum(as[k], ac[k], hi, lo);
+            P[(size_t)a * q + b] = make_float2(hi, lo);
+        }
     }
-    if (ti == tj && ty == 0 && cb + tx < q) hpart[(size_t)ks * q + cb + tx] = (double)hsum + (double)hcmp;
+    if (ti == tj && ty == 0 && cb + tx < q) {
+        float hi, lo;
+        two_sum(hsum, hcmp, hi, lo);
+        hpart[(size_t)ks * q + cb + tx] = make_float2(hi, lo);
+    }
+}
+
+// M = I + sigma (G - h h' / p) from the double-float split-K partials of
+// gram_df_kernel, summed in block order in double-float; written as the
+// (hi, lo) pair Mf of the CG operator (and the factor's input).
+__global__ void build_m_df_kernel(int q, int KS, const float2 *__restrict__ part, const float2 *__restrict__ hpart,
+                                  float2 pinv, float2 sig, float2 *__restrict__ Mf)
+{
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)q * q;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int a = (int)(e / q), b = (int)(e % q);
+        if (b > a || a / kGT < b / kGT) continue;
+        float2 gsum = make_float2(0.f, 0.f), ha = gsum, hb = gsum;
+        for (int ks = 0; ks < KS; ++ks) {
+            gsum = dfx_add(gsum, part[(size_t)ks * q * q + (size_t)a * q + b]);
+            ha = dfx_add(ha, hpart[(size_t)ks * q + a]);
+            hb = dfx_add(hb, hpart[(size_t)ks * q + b]);
+        }
+        float2 m = dfx_mul(sig, dfx_sub(gsum, dfx_mul(dfx_mul(ha, hb), pinv)));
+        if (a == b) m = dfx_addf(m, 1.f);
+        Mf[(size_t)a * q + b] = m;
+        Mf[(size_t)b * q + a] = m;
+    }
 }
 
 __device__ __forceinline__ double block_dot(const double *a, const double *b, int q, double *red)
@@ -615,7 +647,9 @@ __device__ __forceinline__ float2 cg_dot(const float2 *a, const float2 *b, int q
 __global__ void __launch_bounds__(kCgThreads) newton_cg_fast_kernel(int q, const float2 *__restrict__ Mf,
                                                                     const double *__restrict__ g,
                                                                     double *__restrict__ dv, float eta, float tau,
-                                                                    int maxit, double *__restrict__ info, int *err)
+                                                                    int maxit, double *__restrict__ info, int *err,
+                                                                    const double *__restrict__ vdot,
+                                                                    double *__restrict__ rdots)
 {
     extern __shared__ float4 cg_sm4[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
@@ -801,6 +835,30 @@ __global__ void __launch_bounds__(kCgThreads) newton_cg_fast_kernel(int q, const
         info[1] = sqrt((double)fmaxf(rr.x, 0.f));
         info[2] = sc_shift;
     }
+    if (vdot) {
+        // Algorithm 3, Step 2 quantities: rdots[2] = g'dv, rdots[3] = v'dv, rdots[4] = dv'dv
+        __syncthreads();
+        if (tid < qp) {
+            float2 gv = make_float2(0.f, 0.f), vv = gv;
+            if (tid < q) {
+                const double a = g[tid], b = vdot[tid];
+                const float ah = (float)a, bh = (float)b;
+                gv = make_float2(ah, (float)(a - (double)ah));
+                vv = make_float2(bh, (float)(b - (double)bh));
+            }
+            S.R[tid] = gv;
+            S.P[tid] = vv;
+        }
+        __syncthreads();
+        const float2 d0 = cg_dot(S.R, S.X, qp, red);
+        const float2 d1 = cg_dot(S.P, S.X, qp, red);
+        const float2 d2 = cg_dot(S.X, S.X, qp, red);
+        if (tid == 0) {
+            rdots[2] = (double)d0.x + (double)d0.y;
+            rdots[3] = (double)d1.x + (double)d1.y;
+            rdots[4] = (double)d2.x + (double)d2.y;
+        }
+    }
 }
 
 static size_t cg_fast_smem(int q)
@@ -815,31 +873,46 @@ static int g_cgs_attr = 0;
 static int g_chol_smem_set = 0;
 
 cudaError_t launch_newton(Work &W, const int32_t *J, long long p_host, const long long *p_dev, double sigma,
-                          const double *g, double *dv)
+                          const double *g, double *dv, bool dots)
 {
     (void)p_dev;
     const int q = (int)W.q;
-    if (p_host <= 0) return launch_negcopy(W, g, dv);
+    if (p_host <= 0) {
+        const cudaError_t e = launch_negcopy(W, g, dv);
+        return (e == cudaSuccess && dots) ? launch_dots(W) : e;
+    }
     const int nt = (q + kGT - 1) / kGT;
     const int ntiles = nt * (nt + 1) / 2;
     long long ks = (p_host + 31) / 32;   // split-K: ~32 gathered rows per block
     int KSmax = (int)(W.part_len / ((size_t)q * q + q));
     if (KSmax > 4 * W.nsm) KSmax = 4 * W.nsm;
     if (ks > KSmax) ks = KSmax;
+    const bool mixed = W.precision == 1 && W.xf32;
+    // double-float partials are summed in one chain per element: one split per SM
+    if (mixed && ks > W.nsm) ks = W.nsm;
     if (ks < 1) ks = 1;
     double *part = W.part;
     double *hpart = W.part + (size_t)ks * q * q;
     dim3 grid(ntiles, (unsigned)ks);
-    const bool mixed = W.precision == 1 && W.xf32;
     if (mixed)
-        gram_df_kernel<<<grid, 256, 0, W.st>>>((const float *)W.X, q, J, p_host, (int)ks, part, hpart);
+        gram_df_kernel<<<grid, 256, 0, W.st>>>((const float *)W.X, q, J, p_host, (int)ks,
+                                               reinterpret_cast<float2 *>(part), reinterpret_cast<float2 *>(hpart));
     else if (W.xf32)
         gram_kernel<float><<<grid, 256, 0, W.st>>>((const float *)W.X, q, J, p_host, (int)ks, part, hpart);
     else
         gram_kernel<double><<<grid, 256, 0, W.st>>>((const double *)W.X, q, J, p_host, (int)ks, part, hpart);
     const bool cg = W.precision == 1;
-    build_m_kernel<<<W.nsm * 2, 256, 0, W.st>>>(q, (int)ks, part, hpart, (double)p_host, sigma, W.M, W.h,
-                                                cg ? W.Mf : nullptr);
+    if (mixed) {
+        const double pi = 1.0 / (double)p_host;
+        const float pih = (float)pi, sh = (float)sigma;
+        build_m_df_kernel<<<W.nsm * 2, 256, 0, W.st>>>(q, (int)ks, reinterpret_cast<const float2 *>(part),
+                                                       reinterpret_cast<const float2 *>(hpart),
+                                                       make_float2(pih, (float)(pi - (double)pih)),
+                                                       make_float2(sh, (float)(sigma - (double)sh)), W.Mf);
+    } else {
+        build_m_kernel<<<W.nsm * 2, 256, 0, W.st>>>(q, (int)ks, part, hpart, (double)p_host, sigma, W.M, W.h,
+                                                    cg ? W.Mf : nullptr);
+    }
     W.nlaunch += 3;   // gram, build_m, and the solve below
     if (cg) {
         // FP32-Cholesky-preconditioned CG on the FP64 matrix (Algorithm 3's inexact solve)
@@ -854,13 +927,16 @@ cudaError_t launch_newton(Work &W, const int32_t *J, long long p_host, const lon
                 g_cgs_attr = 1;
             }
             newton_cg_fast_kernel<<<1, kCgThreads, smem_new, W.st>>>(q, W.Mf, g, dv, (float)W.eta, (float)W.tau,
-                                                                    W.cg_maxit, info, W.err);
+                                                                    W.cg_maxit, info, W.err, dots ? W.v : nullptr,
+                                                                    W.red);
+            return cudaGetLastError();
         } else {
             const size_t vec = (size_t)6 * q * sizeof(double) + (size_t)q * sizeof(float2);
             newton_pcg_kernel<false, 32><<<1, 1024, vec, W.st>>>(q, W.M, W.Mf, W.Lf, g, dv, W.eta, W.tau, W.cg_maxit,
                                                                  info, W.err);
         }
-        return cudaGetLastError();
+        const cudaError_t e = cudaGetLastError();
+        return (e == cudaSuccess && dots) ? launch_dots(W) : e;
     }
     size_t smem = ((size_t)q * q + q) * sizeof(double);
     if (q <= 144) {
@@ -874,7 +950,8 @@ cudaError_t launch_newton(Work &W, const int32_t *J, long long p_host, const lon
     } else {
         chol_solve_kernel<false><<<1, 1024, 0, W.st>>>(q, W.M, g, dv, W.err);
     }
-    return cudaGetLastError();
+    const cudaError_t e = cudaGetLastError();
+    return (e == cudaSuccess && dots) ? launch_dots(W) : e;
 }
 
 }  // namespace svm

@@ -139,7 +139,7 @@ extern "C" const char *svm_ssnalm_last_error(const svm_ssnalm_t *h)
 static void free_work(Work &W)
 {
     void *ptrs[] = {W.alpha, W.z, W.dz, W.qa, W.tmpn, W.zf, W.dzf, W.qaf, W.alphaw, W.dw, W.dwa, W.atpa,
-                    W.atpa2, W.v, W.dv, W.g, W.atp, W.atp2, W.h, W.w, W.tmpq, W.M, W.Lf, W.Mf, W.part, W.cnt,
+                    W.atpa2, W.v, W.vt, W.dv, W.g, W.atp, W.atp2, W.h, W.w, W.tmpq, W.M, W.Lf, W.Mf, W.part, W.cnt,
                     W.bar, W.rm_counter, W.err, W.pout, W.red, W.X_own, W.y_own};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -268,7 +268,7 @@ extern "C" svm_status svm_ssnalm_create(svm_ssnalm_t **out, const svm_problem *p
                (W.df ? (dalloc(&W.zf, n) || dalloc(&W.dzf, n) || dalloc(&W.qaf, n) || dalloc(&W.alphaw, n) ||
                         dalloc(&W.dw, n) || dalloc(&W.dwa, n))
                      : (dalloc(&W.z, n) || dalloc(&W.dz, n))) ||
-               dalloc(&W.atpa, q) || dalloc(&W.atpa2, q) ||
+               dalloc(&W.atpa, q) || dalloc(&W.atpa2, q) || dalloc(&W.vt, q) ||
                dalloc(&W.v, q) || dalloc(&W.dv, q) || dalloc(&W.g, q) ||
                dalloc(&W.atp, q) || dalloc(&W.atp2, q) || dalloc(&W.h, q) || dalloc(&W.w, q) || dalloc(&W.tmpq, q) ||
                dalloc(&W.M, q * q) || dalloc(&W.Lf, q * (q + 1)) || dalloc(&W.Mf, q * q) || dalloc(&W.part, W.part_len) || dalloc(&W.bar, 4) || dalloc(&W.rm_counter, 4) || dalloc(&W.err, 4) ||
@@ -524,8 +524,12 @@ extern "C" svm_status svm_ssnalm_solve(svm_ssnalm_t *h, const double *alpha0, sv
                 in.lam0 = &W.pout[1 + cur].lamf;
                 in.u_out = B.uf; in.wpi_out = B.wpi; in.dw_out = W.dw; in.dwa_out = W.dwa; in.J = B.J; in.D = B.S;
                 CK(timed(h, TK_PROJ, [&] { return launch_project_df(W, in, &W.pout[1 + cur]); }));
+                // ... and g = v - A'pi with |g|^2 in the same launch's epilogue
+                GradOut go;
+                go.v = W.v; go.g = W.g;
                 CK(timed(h, TK_RMATVEC, [&] {
-                    return launch_rmatvec_df(W, W.dw, W.dwa, B.S, &W.pout[1 + cur].s, nullptr, nullptr, W.atp, W.atpa, 1);
+                    return launch_rmatvec_df(W, W.dw, W.dwa, B.S, &W.pout[1 + cur].s, nullptr, nullptr, W.atp, W.atpa, 1,
+                                             go);
                 }));
             } else {
                 ProjIn in;
@@ -538,8 +542,8 @@ extern "C" svm_status svm_ssnalm_solve(svm_ssnalm_t *h, const double *alpha0, sv
                 CK(timed(h, TK_RMATVEC, [&] {
                     return launch_rmatvec(W, B.pi, B.wpi, B.S, &W.pout[1 + cur].s, W.atp, 1);
                 }));
+                CK(launch_grad(W));
             }
-            CK(launch_grad(W));
             if ((st = sync_read(h)) != SVM_OK) return st;
         }
         int j = 0;
@@ -556,10 +560,12 @@ extern "C" svm_status svm_ssnalm_solve(svm_ssnalm_t *h, const double *alpha0, sv
             if (gn <= fmax(tol_in, floor_g) || j >= P.max_inner) break;
             // Algorithm 3, Step 1: Newton direction on the free set J
             const long long p = m.p;
-            CK(timed(h, TK_NEWTON, [&] { return launch_newton(W, W.pb[cur].J, p, &W.pout[1 + cur].p, sigma, W.g, W.dv); }));
+            // (with the Armijo quantities g'dv, v'dv, dv'dv)
+            CK(timed(h, TK_NEWTON, [&] {
+                return launch_newton(W, W.pb[cur].J, p, &W.pout[1 + cur].p, sigma, W.g, W.dv, true);
+            }));
             // A dv = Q d
             CK(timed(h, TK_MATVEC, [&] { return df ? launch_matvec_df(W, W.dv, W.dzf) : launch_matvec(W, W.dv, W.dz); }));
-            CK(launch_dots(W));
             // Step 2: Armijo line search.  Each trial projects u - t sigma A dv into the
             // other buffer and, speculatively, forms the gradient there, so an accepted
             // trial is the next iterate's projection and gradient at no extra pass.
@@ -575,9 +581,13 @@ extern "C" svm_status svm_ssnalm_solve(svm_ssnalm_t *h, const double *alpha0, sv
                     tr.lam0 = &W.pout[1 + cur].lamf;
                     tr.u_out = B.uf; tr.wpi_out = B.wpi; tr.dw_out = W.dw; tr.dwa_out = W.dwa; tr.J = B.J; tr.D = B.S;
                     CK(timed(h, TK_PROJ, [&] { return launch_project_df(W, tr, &W.pout[1 + nxt]); }));
+                    // A'pi at the trial point and, in the epilogue, vt = v + t dv and
+                    // g = vt - A'pi with |g|^2 (speculative: kept if the trial is accepted)
+                    GradOut go;
+                    go.v = W.v; go.dv = W.dv; go.t = t; go.g = W.tmpq; go.vt = W.vt;
                     CK(timed(h, TK_RMATVEC, [&] {
                         return launch_rmatvec_df(W, W.dw, W.dwa, B.S, &W.pout[1 + nxt].s, W.atp, W.atpa, W.atp2,
-                                                 W.atpa2, 1);
+                                                 W.atpa2, 1, go);
                     }));
                 } else {
                     ProjIn tr;
@@ -589,10 +599,10 @@ extern "C" svm_status svm_ssnalm_solve(svm_ssnalm_t *h, const double *alpha0, sv
                     CK(timed(h, TK_RMATVEC, [&] {
                         return launch_rmatvec(W, B.pi, B.wpi, B.S, &W.pout[1 + nxt].s, W.atp2, 1);
                     }));
+                    grad_at_kernel<<<1, 1024, 0, W.st>>>(q, W.v, W.dv, t, W.atp2, W.tmpq, W.red);
+                    ++W.nlaunch;
+                    CK(cudaGetLastError());
                 }
-                grad_at_kernel<<<1, 1024, 0, W.st>>>(q, W.v, W.dv, t, W.atp2, W.tmpq, W.red);
-                ++W.nlaunch;
-                CK(cudaGetLastError());
                 if ((st = sync_read(h)) != SVM_OK) return st;
                 const double slope = W.h_red[2], vdv = W.h_red[3], dvdv = W.h_red[4];
                 const double dpsi = t * vdv + 0.5 * t * t * dvdv + W.h_pout[1 + nxt].sum[1] / (2.0 * sigma);
@@ -605,10 +615,12 @@ extern "C" svm_status svm_ssnalm_solve(svm_ssnalm_t *h, const double *alpha0, sv
             if (!accepted) break;   // line search failed: the subproblem ends at the current point
             // Step 3 (z = A v is not read again before it is recomputed after the
             // inner loop: the trials project from the accepted point's u)
-            CK(launch_vaxpy(W, t));
-            copyq_kernel<<<1, 1024, 0, W.st>>>(q, W.tmpq, W.g);
-            ++W.nlaunch;
-            CK(cudaGetLastError());
+            if (df) {
+                std::swap(W.v, W.vt);   // v + t dv, formed by the trial's epilogue
+            } else {
+                CK(launch_vaxpy(W, t));
+            }
+            std::swap(W.g, W.tmpq);     // the gradient at the accepted trial
             std::swap(W.atp, W.atp2);   // A'pi of the accepted trial
             std::swap(W.atpa, W.atpa2);
             cur = nxt;
@@ -618,9 +630,7 @@ extern "C" svm_status svm_ssnalm_solve(svm_ssnalm_t *h, const double *alpha0, sv
         // alpha (the old alpha buffer takes its place); A'alpha^{k+1} is the last A'pi
         if (df) std::swap(W.alphaw, W.pb[cur].wpi);
         else std::swap(W.alpha, W.pb[cur].pi);
-        copyq_kernel<<<1, 1024, 0, W.st>>>(q, W.atp, W.w);
-        ++W.nlaunch;
-        CK(cudaGetLastError());
+        std::swap(W.w, W.atp);   // the next subproblem forms A'pi afresh into the other buffer
         // Q alpha = A w for the KKT test and z = A v for the next subproblem, one pass
         CK(timed(h, TK_MATVEC, [&] {
             return df ? launch_matvec_df(W, W.w, W.qaf, W.v, W.zf) : launch_matvec(W, W.w, W.qa, W.v, W.z);
