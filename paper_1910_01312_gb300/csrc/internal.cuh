@@ -102,6 +102,10 @@ struct Work {
     // q-vectors
     double *v = nullptr, *dv = nullptr, *g = nullptr, *atp = nullptr, *atp2 = nullptr, *h = nullptr,
            *w = nullptr, *tmpq = nullptr, *vt = nullptr;   // vt: v + t dv at a trial point
+    // matrix-free Newton state for large free sets (mixed form, q <= 128)
+    struct MfState *mf_st = nullptr;
+    float *mf_pinv = nullptr;
+    unsigned *mf_counter = nullptr;
     double *M = nullptr;      // q*q Newton matrix / Cholesky factor
     float *Lf = nullptr;      // q*(q+1) FP32 factor when it does not fit in shared memory
     float2 *Mf = nullptr;     // q*q FP32 (hi, lo) split of M (double-float CG operator)
@@ -178,5 +182,7 @@ cudaError_t launch_negcopy(Work &W, const double *g, double *dv); // dv = -g
 // when p_host < 0); with dots, also red[2] = g'dv, red[3] = v'dv, red[4] = dv'dv.
 cudaError_t launch_newton(Work &W, const int32_t *J, long long p_host, const long long *p_dev,
                           double sigma, const double *g, double *dv, bool dots = false);
+// workspace of the large-free-set Newton solve (mixed form, FP32 X, q <= 128)
+cudaError_t newton_mf_alloc(Work &W);
 
 }  // namespace svm

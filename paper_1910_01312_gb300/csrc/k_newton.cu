@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(1024) chol_solve_kernel(int q, double *__restr
 // (TwoSum) on the FP32 pipes; same tiling and outputs as gram_kernel.
 __global__ void __launch_bounds__(256) gram_df_kernel(const float *__restrict__ X, int q, const int32_t *__restrict__ J,
                                                       long long p, int KS, float2 *__restrict__ part,
-                                                      float2 *__restrict__ hpart)
+                                                      float2 *__restrict__ hpart, long long stride)
 {
     int t = blockIdx.x;
     int ti = 0;
@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(256) gram_df_kernel(const float *__restrict__ 
             const long long r = rb + rr;
             float va = 0.f, vb = 0.f;
             if (r < r1) {
-                const float *row = X + (long long)J[r] * q;
+                const float *row = X + (long long)J[r * stride] * q;   // row r of the (subsampled) list
                 if (ca + cc < q) va = row[ca + cc];
                 if (cb + cc < q) vb = row[cb + cc];
             }
@@ -644,25 +644,16 @@ __device__ __forceinline__ float2 cg_dot(const float2 *a, const float2 *b, int q
     return t;
 }
 
-__global__ void __launch_bounds__(kCgThreads) newton_cg_fast_kernel(int q, const float2 *__restrict__ Mf,
-                                                                    const double *__restrict__ g,
-                                                                    double *__restrict__ dv, float eta, float tau,
-                                                                    int maxit, double *__restrict__ info, int *err,
-                                                                    const double *__restrict__ vdot,
-                                                                    double *__restrict__ rdots)
+// M (q x q double-float pairs) into S.M, zero padded to qp (one bulk copy when
+// q = qp), and the FP32 Cholesky factor of fl32(M) + shift into S.L / S.D (a
+// diagonal shift is added and the factor retried when a pivot is not
+// positive).  Block-uniform result; false (err set) when the copy or the
+// factor failed.  *sc_shift (shared) receives the shift used.
+__device__ bool cg_load_factor(CgSmem &S, int q, const float2 *__restrict__ Mf, int *err, float *sc_shift)
 {
-    extern __shared__ float4 cg_sm4[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     const int qp = (q + 31) & ~31, nb = qp / kPb;
-    CgSmem S;
-    S.M = reinterpret_cast<float2 *>(cg_sm4);
-    S.L = reinterpret_cast<float *>(S.M + qp * qp);
-    S.D = S.L + ((qp * (qp + 1)) >> 1);
-    S.t = S.D + nb * kPb * kPb;
-    S.X = reinterpret_cast<float2 *>(S.t + qp);
-    S.R = S.X + qp; S.P = S.R + qp; S.AP = S.P + qp; S.Z = S.AP + qp; S.RO = S.Z + qp;
-    __shared__ float2 red[8];
-    __shared__ float sc_shift, sc_maxdiag;
+    __shared__ float sc_maxdiag;
     __shared__ int bad, copy_ok;
     __shared__ __align__(8) unsigned long long mbar;
     // M into shared memory: one bulk copy when its rows need no padding
@@ -682,9 +673,9 @@ __global__ void __launch_bounds__(kCgThreads) newton_cg_fast_kernel(int q, const
                 S.M[i * qp + j] = (i < q && j < q) ? Mf[(size_t)i * q + j] : make_float2(0.f, 0.f);
         if (tid == 0) copy_ok = 1;
     }
-    if (tid == 0) sc_shift = 0.f;
+    if (tid == 0) *sc_shift = 0.f;
     __syncthreads();
-    if (!copy_ok) return;
+    if (!copy_ok) return false;
     if (warp == 0) {
         float md = 0.f;
         for (int j = lane; j < q; j += 32) md = fmaxf(md, S.M[j * qp + j].x);
@@ -695,7 +686,7 @@ __global__ void __launch_bounds__(kCgThreads) newton_cg_fast_kernel(int q, const
     __syncthreads();
     bool okf = false;
     for (int attempt = 0; attempt < 6 && !okf; ++attempt) {
-        const float shift = sc_shift;
+        const float shift = *sc_shift;
         for (int i = warp; i < qp; i += nw)
             for (int j = lane; j <= i; j += 32)
                 S.L[lpos(i, j)] = (i < q) ? S.M[i * qp + j].x + (i == j ? shift : 0.f) : (i == j ? 1.f : 0.f);
@@ -742,13 +733,36 @@ __global__ void __launch_bounds__(kCgThreads) newton_cg_fast_kernel(int q, const
         }
         okf = !bad;
         __syncthreads();
-        if (!okf && tid == 0) sc_shift = (shift == 0.f) ? 1e-7f * sc_maxdiag : shift * 100.f;
+        if (!okf && tid == 0) *sc_shift = (shift == 0.f) ? 1e-7f * sc_maxdiag : shift * 100.f;
         __syncthreads();
     }
     if (!okf) {
         if (tid == 0) set_err(err, DEV_CHOL);
-        return;
+        return false;
     }
+    return true;
+}
+
+__global__ void __launch_bounds__(kCgThreads) newton_cg_fast_kernel(int q, const float2 *__restrict__ Mf,
+                                                                    const double *__restrict__ g,
+                                                                    double *__restrict__ dv, float eta, float tau,
+                                                                    int maxit, double *__restrict__ info, int *err,
+                                                                    const double *__restrict__ vdot,
+                                                                    double *__restrict__ rdots)
+{
+    extern __shared__ float4 cg_sm4[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int qp = (q + 31) & ~31, nb = qp / kPb;
+    CgSmem S;
+    S.M = reinterpret_cast<float2 *>(cg_sm4);
+    S.L = reinterpret_cast<float *>(S.M + qp * qp);
+    S.D = S.L + ((qp * (qp + 1)) >> 1);
+    S.t = S.D + nb * kPb * kPb;
+    S.X = reinterpret_cast<float2 *>(S.t + qp);
+    S.R = S.X + qp; S.P = S.R + qp; S.AP = S.P + qp; S.Z = S.AP + qp; S.RO = S.Z + qp;
+    __shared__ float2 red[8];
+    __shared__ float sc_shift;
+    if (!cg_load_factor(S, q, Mf, err, &sc_shift)) return;
     // CG on M dv = -g in double-float
     if (tid < qp) {
         float2 r0 = make_float2(0.f, 0.f);
@@ -861,6 +875,416 @@ __global__ void __launch_bounds__(kCgThreads) newton_cg_fast_kernel(int q, const
     }
 }
 
+// ---------------------------------------------------------------------------
+// Newton step for a large free set (p > kMfMinP, FP32 X, q <= 128).  The exact
+// double-float Gram costs p q^2 / 2 double-float terms on the FP32 pipes
+// (2.4 ms at p = 5e5); instead CG runs on the exact operator
+//     M d = d + sigma (X_J'(X_J d) - h (h'd) / p),   h = X_J'1,
+// applied matrix-free in double-float: one pass over the rows of J per CG
+// step, each row read once (its dot with d, then its share of X_J't).  The
+// preconditioner is the explicit inverse of the FP32 Cholesky factor of the
+// same matrix built from a stride subsample of s rows of J, the Gram scaled by
+// p / s (a ~1/sqrt(s) relative approximation, so CG gains ~2 digits a step).
+// The last block of each pass does the CG update; passes are launched back to
+// back and return at once when the state says the solve is done, so the host
+// never waits.  Same stopping rule as newton_cg_fast_kernel.
+// Measured on gauss1m (q = 128): with the stride-subsample preconditioner
+// CG gains only ~0.6 digits a pass (the rank-one centring h h'/p cancels in the
+// class-mean direction and the sample estimates it poorly), so the pass count
+// hits kMfMaxPass; the exact double-float Gram is faster below ~2e5 rows
+// (p = 1.6e4: 207 us exact vs 710 us here; p = 5e5: 2437 us vs 1785 us).
+constexpr long long kMfMinP = 200000;
+constexpr int kMfSample = 2048;
+constexpr int kMfMaxPass = 12;
+constexpr int kMfThreads = 512;
+
+struct MfState {   // CG state carried between passes (global memory)
+    float2 X[kCgMaxQ], R[kCgMaxQ], RO[kCgMaxQ], D[kCgMaxQ], H[kCgMaxQ];
+    float2 rz;
+    float tol2;
+    float shift;
+    int it;
+    int done;
+};
+
+// Armijo quantities and the output of a finished solve (threads < q write dv)
+__device__ __forceinline__ void mf_finish(const float2 *X, int q, int qp, double *dv, const double *g,
+                                          const double *vdot, double *rdots, float2 *tmpa, float2 *tmpb, float2 *red)
+{
+    const int tid = threadIdx.x;
+    if (tid < q) dv[tid] = (double)X[tid].x + (double)X[tid].y;
+    if (!vdot) return;
+    if (tid < qp) {
+        float2 gv = make_float2(0.f, 0.f), vv = gv;
+        if (tid < q) {
+            const double a = g[tid], b = vdot[tid];
+            const float ah = (float)a, bh = (float)b;
+            gv = make_float2(ah, (float)(a - (double)ah));
+            vv = make_float2(bh, (float)(b - (double)bh));
+        }
+        tmpa[tid] = gv;
+        tmpb[tid] = vv;
+    }
+    __syncthreads();
+    const float2 d0 = cg_dot(tmpa, X, qp, red);
+    const float2 d1 = cg_dot(tmpb, X, qp, red);
+    const float2 d2 = cg_dot(X, X, qp, red);
+    if (tid == 0) {
+        rdots[2] = (double)d0.x + (double)d0.y;
+        rdots[3] = (double)d1.x + (double)d1.y;
+        rdots[4] = (double)d2.x + (double)d2.y;
+    }
+}
+
+// One block: factor the subsample matrix (in Mf), form Pinv = (L L')^{-1}
+// explicitly, and start CG on M dv = -g: X = 0, R = -g, D = Pinv R.
+__global__ void __launch_bounds__(kCgThreads) newton_mf_setup_kernel(int q, const float2 *__restrict__ Mf,
+                                                                     const double *__restrict__ g,
+                                                                     double *__restrict__ dv, float eta, float tau,
+                                                                     MfState *__restrict__ st,
+                                                                     float *__restrict__ Pinv, int *err,
+                                                                     const double *__restrict__ vdot,
+                                                                     double *__restrict__ rdots)
+{
+    extern __shared__ float4 cg_sm4[];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int qp = (q + 31) & ~31, nb = qp / kPb;
+    CgSmem S;
+    S.M = reinterpret_cast<float2 *>(cg_sm4);
+    S.L = reinterpret_cast<float *>(S.M + qp * qp);
+    S.D = S.L + ((qp * (qp + 1)) >> 1);
+    S.t = S.D + nb * kPb * kPb;
+    S.X = reinterpret_cast<float2 *>(S.t + qp);
+    S.R = S.X + qp; S.P = S.R + qp; S.AP = S.P + qp; S.Z = S.AP + qp; S.RO = S.Z + qp;
+    __shared__ float2 red[8];
+    __shared__ float sc_shift;
+    if (!cg_load_factor(S, q, Mf, err, &sc_shift)) {
+        if (tid == 0) st->done = 1;
+        return;
+    }
+    // Y = L^{-1} in the (now free) M area, row-major, ld = qp + 1: blocked
+    // forward substitution on I, Y_b = Dinv_b T_b, then T_r -= L_rb Y_b below
+    float *Y = reinterpret_cast<float *>(S.M);
+    const int ld = qp + 1;
+    for (int e = tid; e < qp * qp; e += nt) {
+        const int i = e / qp, j = e - i * qp;
+        Y[i * ld + j] = (i == j) ? 1.f : 0.f;
+    }
+    __syncthreads();
+    for (int b = 0; b < nb; ++b) {
+        const int kb = b * kPb;
+        if (tid <= kb + kPb - 1) {   // column tid of the block rows
+            const float *Db = S.D + b * kPb * kPb;
+            float yv[kPb], out[kPb];
+#pragma unroll
+            for (int k = 0; k < kPb; ++k) yv[k] = Y[(kb + k) * ld + tid];
+#pragma unroll
+            for (int i = 0; i < kPb; ++i) {
+                float a = 0.f;
+#pragma unroll
+                for (int k = 0; k < kPb; ++k) a = fmaf(Db[i * kPb + k], yv[k], a);
+                out[i] = a;
+            }
+#pragma unroll
+            for (int i = 0; i < kPb; ++i) Y[(kb + i) * ld + tid] = out[i];
+        }
+        __syncthreads();
+        const int rows = qp - kb - kPb, cols = kb + kPb;
+        for (int e = tid; e < rows * cols; e += nt) {
+            const int r = kb + kPb + e / cols, c = e % cols;
+            float a = 0.f;
+#pragma unroll
+            for (int k = 0; k < kPb; ++k) a = fmaf(S.L[lpos(r, kb + k)], Y[(kb + k) * ld + c], a);
+            Y[r * ld + c] -= a;
+        }
+        __syncthreads();
+    }
+    // Pinv = Y'Y (symmetric; Y lower triangular)
+    for (int e = tid; e < qp * qp; e += nt) {
+        const int i = e / qp, j = e - i * qp;
+        if (j < i) continue;
+        float a = 0.f;
+        for (int k = j; k < qp; ++k) a = fmaf(Y[k * ld + i], Y[k * ld + j], a);
+        Pinv[i * qp + j] = a;
+        Pinv[j * qp + i] = a;
+    }
+    __syncthreads();
+    // CG start
+    if (tid < qp) {
+        float2 r0 = make_float2(0.f, 0.f);
+        if (tid < q) {
+            const double v = -g[tid];
+            const float hi = (float)v;
+            r0 = make_float2(hi, (float)(v - (double)hi));
+        }
+        S.R[tid] = r0;
+        S.X[tid] = make_float2(0.f, 0.f);
+        S.t[tid] = r0.x + r0.y;
+    }
+    __syncthreads();
+    // z = Pinv t = Y'(Y t), from Y in shared memory (Y lower triangular)
+    float *yt = reinterpret_cast<float *>(S.AP);
+    if (tid < qp) {
+        float a = 0.f;
+        for (int k = 0; k <= tid; ++k) a = fmaf(Y[tid * ld + k], S.t[k], a);
+        yt[tid] = a;
+    }
+    __syncthreads();
+    if (tid < qp) {
+        float z = 0.f;
+        for (int k = tid; k < qp; ++k) z = fmaf(Y[k * ld + tid], yt[k], z);
+        S.Z[tid] = make_float2(z, 0.f);
+    }
+    __syncthreads();
+    const float2 rr = cg_dot(S.R, S.R, qp, red);
+    const float2 rz = cg_dot(S.R, S.Z, qp, red);
+    const float gn = sqrtf(fmaxf(rr.x, 0.f));
+    const float tol = fmaxf(fminf(fminf(eta, powf(gn, 1.f + tau)), 1e-10f * gn), 1e-14f * gn);
+    const bool done = !(rr.x > tol * tol);
+    if (tid < qp) {
+        st->X[tid] = S.X[tid];
+        st->R[tid] = S.R[tid];
+        st->D[tid] = S.Z[tid];
+    }
+    if (tid == 0) {
+        st->rz = rz;
+        st->tol2 = tol * tol;
+        st->shift = sc_shift;
+        st->it = 0;
+        st->done = done ? 1 : 0;
+    }
+    if (done) mf_finish(S.X, q, qp, dv, g, vdot, rdots, S.AP, S.P, red);
+}
+
+// One CG step: y = X_J'(X_J D) over this block's rows of J (and, on the first
+// pass, h = X_J'1), double-float block partials, and in the last block to
+// finish the CG update.  VW = 4 columns per lane (q % 4 == 0, q <= 128).
+template <bool FIRST>
+__global__ void __launch_bounds__(kMfThreads) newton_mf_pass_kernel(
+    const float *__restrict__ X, const int32_t *__restrict__ J, long long p, int q, float2 sig, float2 rp,
+    MfState *__restrict__ st, const float *__restrict__ Pinv, float2 *__restrict__ part, unsigned *__restrict__ counter,
+    int last, int maxit, double *__restrict__ dv, const double *__restrict__ g, const double *__restrict__ vdot,
+    double *__restrict__ rdots, double *__restrict__ info)
+{
+    __shared__ int sh_flag;
+    if (threadIdx.x == 0) sh_flag = __ldcg(&st->done);
+    __syncthreads();
+    if (sh_flag) return;
+    const int G = gridDim.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int qp = (q + 31) & ~31;
+    const bool has = 4 * lane < q;
+    float2 dl[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) dl[k] = has ? __ldcg(&st->D[4 * lane + k]) : make_float2(0.f, 0.f);
+    float as[4] = {0.f, 0.f, 0.f, 0.f}, ac[4] = {0.f, 0.f, 0.f, 0.f};
+    float hs[4] = {0.f, 0.f, 0.f, 0.f}, hc[4] = {0.f, 0.f, 0.f, 0.f};
+    const long long per = (p + G - 1) / G;
+    const long long r_beg = (long long)blockIdx.x * per;
+    const long long r_end = r_beg + per < p ? r_beg + per : p;
+    constexpr int R = 4;
+    for (long long c0 = r_beg + (long long)warp * 32; c0 < r_end; c0 += (long long)nw * 32) {
+        const long long rl = c0 + lane;
+        const int myi = (rl < r_end) ? J[rl] : -1;
+        const int here = (int)((r_end - c0) < 32 ? (r_end - c0) : 32);
+        for (int u0 = 0; u0 < here; u0 += R) {
+            float4 xv[R];
+#pragma unroll
+            for (int u = 0; u < R; ++u) {
+                const int ii = __shfl_sync(0xffffffffu, myi, (u0 + u) & 31);
+                xv[u] = (u0 + u < here && has) ? __ldcs(reinterpret_cast<const float4 *>(X + (long long)ii * q) + lane)
+                                               : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < R; ++u) {
+                // t = x . d (Dot2, then an all-lane butterfly on (s, c))
+                float s = 0.f, c = 0.f;
+                dot2_step(xv[u].x, dl[0], s, c);
+                dot2_step(xv[u].y, dl[1], s, c);
+                dot2_step(xv[u].z, dl[2], s, c);
+                dot2_step(xv[u].w, dl[3], s, c);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float s2 = __shfl_xor_sync(0xffffffffu, s, o), c2 = __shfl_xor_sync(0xffffffffu, c, o);
+                    float sn, e;
+                    two_sum(s, s2, sn, e);
+                    s = sn;
+                    c += c2 + e;
+                }
+                float th, tl;
+                two_sum(s, c, th, tl);
+                const float2 t = make_float2(th, tl);
+                dot2_step(xv[u].x, t, as[0], ac[0]);
+                dot2_step(xv[u].y, t, as[1], ac[1]);
+                dot2_step(xv[u].z, t, as[2], ac[2]);
+                dot2_step(xv[u].w, t, as[3], ac[3]);
+                if (FIRST) {
+                    const float xs[4] = {xv[u].x, xv[u].y, xv[u].z, xv[u].w};
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        float sn, e;
+                        two_sum(hs[k], xs[k], sn, e);
+                        hs[k] = sn;
+                        hc[k] += e;
+                    }
+                }
+            }
+        }
+    }
+    // warps in order -> block partial (double-float) -> part[list][blk][j].
+    // One shared pool: the per-warp sums first, the last block's vectors after.
+    __shared__ float2 pool[2 * (kMfThreads / 32) * kCgMaxQ];
+    float2 *wy = pool, *wh = pool + (kMfThreads / 32) * kCgMaxQ;
+    if (has) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            wy[warp * kCgMaxQ + 4 * lane + k] = make_float2(as[k], ac[k]);
+            if (FIRST) wh[warp * kCgMaxQ + 4 * lane + k] = make_float2(hs[k], hc[k]);
+        }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < q; j += blockDim.x) {
+        float s = 0.f, c = 0.f, s2 = 0.f, c2 = 0.f;
+        for (int w = 0; w < nw; ++w) {
+            df_acc(s, c, wy[w * kCgMaxQ + j].x, wy[w * kCgMaxQ + j].y);
+            if (FIRST) df_acc(s2, c2, wh[w * kCgMaxQ + j].x, wh[w * kCgMaxQ + j].y);
+        }
+        float hi, lo;
+        two_sum(s, c, hi, lo);
+        part[(size_t)blockIdx.x * q + j] = make_float2(hi, lo);
+        if (FIRST) {
+            two_sum(s2, c2, hi, lo);
+            part[((size_t)G + blockIdx.x) * q + j] = make_float2(hi, lo);
+        }
+    }
+    __threadfence();
+    __syncthreads();
+    __shared__ int is_last;
+    if (threadIdx.x == 0) is_last = (atomicAdd(counter, 1u) == (unsigned)(G - 1));
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    // ---- last block: y (and h) in block order, then the CG update ----
+    __syncthreads();   // the pool's per-warp sums are no longer read
+    float2 *sy = pool, *sh = sy + kCgMaxQ, *sd = sh + kCgMaxQ, *sap = sd + kCgMaxQ, *sz = sap + kCgMaxQ,
+           *sro = sz + kCgMaxQ, *sx = sro + kCgMaxQ, *sr = sx + kCgMaxQ;
+    float2 *sub = sr + kCgMaxQ;                                  // [subs][kCgMaxQ]
+    float2 *subh = sub + (kMfThreads / kCgMaxQ) * kCgMaxQ;       // [subs][kCgMaxQ]
+    __shared__ float2 red[8];
+    __shared__ float sw[kCgMaxQ];
+    const int subs = blockDim.x / kCgMaxQ;   // 4 interleaved sub-sums per column
+    {
+        const int col = threadIdx.x % kCgMaxQ, sb = threadIdx.x / kCgMaxQ;
+        float2 a = make_float2(0.f, 0.f), hh = a;
+        if (col < q) {
+            // eight loads in flight per step, added in block order
+            int b = sb;
+            for (; b + 7 * subs < G; b += 8 * subs) {
+                float2 v[8], w[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    v[u] = __ldcg(&part[(size_t)(b + u * subs) * q + col]);
+                    if (FIRST) w[u] = __ldcg(&part[((size_t)G + b + u * subs) * q + col]);
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    a = dfx_add(a, v[u]);
+                    if (FIRST) hh = dfx_add(hh, w[u]);
+                }
+            }
+            for (; b < G; b += subs) {
+                a = dfx_add(a, __ldcg(&part[(size_t)b * q + col]));
+                if (FIRST) hh = dfx_add(hh, __ldcg(&part[((size_t)G + b) * q + col]));
+            }
+        }
+        sub[sb * kCgMaxQ + col] = a;
+        subh[sb * kCgMaxQ + col] = hh;
+        __syncthreads();
+        if (sb == 0 && col < qp) {
+            float2 t = make_float2(0.f, 0.f), th = t;
+            if (col < q)
+                for (int k = 0; k < subs; ++k) {
+                    t = dfx_add(t, sub[k * kCgMaxQ + col]);
+                    th = dfx_add(th, subh[k * kCgMaxQ + col]);
+                }
+            sy[col] = t;
+            if (FIRST) { sh[col] = th; st->H[col] = th; }
+            else sh[col] = (col < q) ? st->H[col] : make_float2(0.f, 0.f);
+            sd[col] = (col < q) ? st->D[col] : make_float2(0.f, 0.f);
+            sx[col] = (col < q) ? st->X[col] : make_float2(0.f, 0.f);
+            sr[col] = (col < q) ? st->R[col] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+    }
+    const int tid = threadIdx.x;
+    const float2 hd = cg_dot(sh, sd, qp, red);
+    if (tid < qp) {   // Ap = d + sigma (y - h (h'd) / p)
+        const float2 corr = dfx_mul(sh[tid], dfx_mul(hd, rp));
+        sap[tid] = dfx_add(sd[tid], dfx_mul(sig, dfx_sub(sy[tid], corr)));
+    }
+    __syncthreads();
+    const float2 pap = cg_dot(sd, sap, qp, red);
+    const float2 rz = st->rz;
+    int it = st->it;
+    bool done;
+    float2 rr = make_float2(0.f, 0.f);
+    if (!(pap.x > 0.f)) {
+        done = true;   // breakdown: keep the current iterate
+        rr = cg_dot(sr, sr, qp, red);
+    } else {
+        const float2 al = dfx_div(rz, pap);
+        if (tid < qp) {
+            sx[tid] = dfx_add(sx[tid], dfx_mul(al, sd[tid]));
+            sro[tid] = sr[tid];
+            sr[tid] = dfx_sub(sr[tid], dfx_mul(al, sap[tid]));
+            sw[tid] = sr[tid].x + sr[tid].y;
+        }
+        __syncthreads();
+        ++it;
+        rr = cg_dot(sr, sr, qp, red);
+        done = !(rr.x > st->tol2) || it >= maxit;
+    }
+    if (!done) {
+        {   // z = Pinv r: all threads, a quarter of the k range each, loads batched
+            float *zq = reinterpret_cast<float *>(sub);   // [subs][kCgMaxQ]
+            const int col = tid % kCgMaxQ, qt = tid / kCgMaxQ;
+            const int k0 = qt * (qp / subs), k1 = k0 + qp / subs;
+            float z = 0.f;
+            if (col < qp) {
+#pragma unroll 8
+                for (int k = k0; k < k1; ++k) z = fmaf(__ldcg(&Pinv[k * qp + col]), sw[k], z);
+            }
+            zq[qt * kCgMaxQ + col] = z;
+            __syncthreads();
+            if (tid < qp) {
+                float t = 0.f;
+                for (int k = 0; k < subs; ++k) t += zq[k * kCgMaxQ + tid];
+                sz[tid] = make_float2(t, 0.f);
+            }
+        }
+        __syncthreads();
+        const float2 rzn = cg_dot(sr, sz, qp, red);
+        const float2 rzo = cg_dot(sro, sz, qp, red);
+        float2 beta = dfx_div(dfx_sub(rzn, rzo), rz);
+        if (!(beta.x > 0.f)) beta = make_float2(0.f, 0.f);
+        if (tid < q) st->D[tid] = dfx_add(sz[tid], dfx_mul(beta, sd[tid]));
+        if (tid == 0) st->rz = rzn;
+    }
+    if (tid < q) { st->X[tid] = sx[tid]; st->R[tid] = sr[tid]; }
+    if (tid == 0) {
+        st->it = it;
+        st->done = done ? 1 : 0;
+        *counter = 0u;
+    }
+    if (done || last) {
+        mf_finish(sx, q, qp, dv, g, vdot, rdots, sap, sz, red);
+        if (tid == 0 && info) {
+            info[0] = it;
+            info[1] = sqrt((double)fmaxf(rr.x, 0.f));
+            info[2] = st->shift;
+        }
+    }
+}
+
 static size_t cg_fast_smem(int q)
 {
     const size_t qp = (size_t)((q + 31) & ~31);
@@ -871,6 +1295,67 @@ static size_t cg_fast_smem(int q)
 static int g_cgs_attr = 0;
 
 static int g_chol_smem_set = 0;
+
+static int g_mf_attr = 0;
+
+cudaError_t newton_mf_alloc(Work &W)
+{
+    if (cudaMalloc((void **)&W.mf_st, sizeof(MfState)) != cudaSuccess) return cudaErrorMemoryAllocation;
+    if (cudaMalloc((void **)&W.mf_pinv, sizeof(float) * kCgMaxQ * kCgMaxQ) != cudaSuccess) return cudaErrorMemoryAllocation;
+    if (cudaMalloc((void **)&W.mf_counter, sizeof(unsigned)) != cudaSuccess) return cudaErrorMemoryAllocation;
+    return cudaMemsetAsync(W.mf_counter, 0, sizeof(unsigned), W.st);
+}
+
+static float2 split2(double v)
+{
+    const float hi = (float)v;
+    return make_float2(hi, (float)(v - (double)hi));
+}
+
+// Large free set: subsample Gram -> preconditioner -> matrix-free CG passes.
+static cudaError_t launch_newton_mf(Work &W, const int32_t *J, long long p, double sigma, const double *g, double *dv,
+                                    bool dots)
+{
+    const int q = (int)W.q;
+    const int s = kMfSample;
+    const long long stride = p / s;
+    const int nt = (q + kGT - 1) / kGT, ntiles = nt * (nt + 1) / 2;
+    const int ks = (s + 31) / 32 < W.nsm ? (s + 31) / 32 : W.nsm;
+    double *part = W.part;
+    double *hpart = W.part + (size_t)ks * q * q;
+    gram_df_kernel<<<dim3(ntiles, ks), 256, 0, W.st>>>((const float *)W.X, q, J, s, ks,
+                                                       reinterpret_cast<float2 *>(part),
+                                                       reinterpret_cast<float2 *>(hpart), stride);
+    // M_s = I + sigma (p / s) (G_s - h_s h_s' / s)
+    build_m_df_kernel<<<W.nsm * 2, 256, 0, W.st>>>(q, ks, reinterpret_cast<const float2 *>(part),
+                                                   reinterpret_cast<const float2 *>(hpart), split2(1.0 / s),
+                                                   split2(sigma * (double)p / s), W.Mf);
+    if (!g_mf_attr) {
+        const cudaError_t ea = cudaFuncSetAttribute(newton_mf_setup_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                    (int)cg_fast_smem(kCgMaxQ));
+        if (ea != cudaSuccess) return ea;
+        g_mf_attr = 1;
+    }
+    const double *vdot = dots ? W.v : nullptr;
+    newton_mf_setup_kernel<<<1, kCgThreads, cg_fast_smem(q), W.st>>>(q, W.Mf, g, dv, (float)W.eta, (float)W.tau,
+                                                                     W.mf_st, W.mf_pinv, W.err, vdot, W.red);
+    const float2 sig = split2(sigma), rp = split2(1.0 / (double)p);
+    float2 *pp = reinterpret_cast<float2 *>(W.part);
+    const int G = 2 * W.nsm;
+    for (int k = 0; k < kMfMaxPass; ++k) {
+        const int last = k == kMfMaxPass - 1;
+        if (k == 0)
+            newton_mf_pass_kernel<true><<<G, kMfThreads, 0, W.st>>>((const float *)W.X, J, p, q, sig, rp, W.mf_st,
+                                                                    W.mf_pinv, pp, W.mf_counter, last, W.cg_maxit,
+                                                                    dv, g, vdot, W.red, W.red + 12);
+        else
+            newton_mf_pass_kernel<false><<<G, kMfThreads, 0, W.st>>>((const float *)W.X, J, p, q, sig, rp, W.mf_st,
+                                                                     W.mf_pinv, pp, W.mf_counter, last, W.cg_maxit,
+                                                                     dv, g, vdot, W.red, W.red + 12);
+    }
+    W.nlaunch += 3 + kMfMaxPass;
+    return cudaGetLastError();
+}
 
 cudaError_t launch_newton(Work &W, const int32_t *J, long long p_host, const long long *p_dev, double sigma,
                           const double *g, double *dv, bool dots)
@@ -888,6 +1373,8 @@ cudaError_t launch_newton(Work &W, const int32_t *J, long long p_host, const lon
     if (KSmax > 4 * W.nsm) KSmax = 4 * W.nsm;
     if (ks > KSmax) ks = KSmax;
     const bool mixed = W.precision == 1 && W.xf32;
+    if (mixed && W.mf_st && q <= kCgMaxQ && q % 4 == 0 && p_host > kMfMinP)
+        return launch_newton_mf(W, J, p_host, sigma, g, dv, dots);
     // double-float partials are summed in one chain per element: one split per SM
     if (mixed && ks > W.nsm) ks = W.nsm;
     if (ks < 1) ks = 1;
@@ -896,7 +1383,7 @@ cudaError_t launch_newton(Work &W, const int32_t *J, long long p_host, const lon
     dim3 grid(ntiles, (unsigned)ks);
     if (mixed)
         gram_df_kernel<<<grid, 256, 0, W.st>>>((const float *)W.X, q, J, p_host, (int)ks,
-                                               reinterpret_cast<float2 *>(part), reinterpret_cast<float2 *>(hpart));
+                                               reinterpret_cast<float2 *>(part), reinterpret_cast<float2 *>(hpart), 1);
     else if (W.xf32)
         gram_kernel<float><<<grid, 256, 0, W.st>>>((const float *)W.X, q, J, p_host, (int)ks, part, hpart);
     else

@@ -92,7 +92,24 @@ __device__ void final_reduce_df(int G, int q, const float *__restrict__ part, co
         float2 S = make_float2(0.f, 0.f);
         float A = 0.f;
         if (col < q) {
-            for (int b = sub; b < G; b += subs) {
+            // eight blocks' loads in flight per step, added in block order
+            int b = sub;
+            for (; b + 7 * subs < G; b += 8 * subs) {
+                float h[8], l[8], ab[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const float *p = part + (size_t)(b + u * subs) * 3 * q;
+                    h[u] = __ldcg(p + col);
+                    l[u] = __ldcg(p + q + col);
+                    ab[u] = __ldcg(p + 2 * q + col);
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    S = dfx_add(S, make_float2(h[u], l[u]));
+                    A += ab[u];
+                }
+            }
+            for (; b < G; b += subs) {
                 const float *p = part + (size_t)b * 3 * q;
                 S = dfx_add(S, make_float2(__ldcg(p + col), __ldcg(p + q + col)));
                 A += __ldcg(p + 2 * q + col);

@@ -139,7 +139,7 @@ extern "C" const char *svm_ssnalm_last_error(const svm_ssnalm_t *h)
 static void free_work(Work &W)
 {
     void *ptrs[] = {W.alpha, W.z, W.dz, W.qa, W.tmpn, W.zf, W.dzf, W.qaf, W.alphaw, W.dw, W.dwa, W.atpa,
-                    W.atpa2, W.v, W.vt, W.dv, W.g, W.atp, W.atp2, W.h, W.w, W.tmpq, W.M, W.Lf, W.Mf, W.part, W.cnt,
+                    W.atpa2, W.mf_st, W.mf_pinv, W.mf_counter, W.v, W.vt, W.dv, W.g, W.atp, W.atp2, W.h, W.w, W.tmpq, W.M, W.Lf, W.Mf, W.part, W.cnt,
                     W.bar, W.rm_counter, W.err, W.pout, W.red, W.X_own, W.y_own};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -277,6 +277,7 @@ extern "C" svm_status svm_ssnalm_create(svm_ssnalm_t **out, const svm_problem *p
         bad = (W.df ? dalloc(&W.pb[b].uf, n) : dalloc(&W.pb[b].u, n)) || dalloc(&W.pb[b].pi, n) ||
               dalloc(&W.pb[b].wpi, n) ||
               dalloc(&W.pb[b].J, n) || dalloc(&W.pb[b].S, n);
+    if (!bad && W.df && q <= 128) bad = newton_mf_alloc(W) != cudaSuccess;
     if (bad) return fail(SVM_ERR_OOM, "device workspace allocation failed");
     if (cudaMallocHost(&W.h_pout, 4 * sizeof(ProjOut)) != cudaSuccess ||
         cudaMallocHost(&W.h_red, 16 * sizeof(double)) != cudaSuccess ||

@@ -166,7 +166,9 @@ def test_projection_flat_segment(kernel):
 @pytest.mark.parametrize("gscale", [1.0, 1e-5])
 @pytest.mark.parametrize("dtype,n,q,frac", [(np.float64, 400, 50, 0.3), (np.float32, 3000, 128, 0.2),
                                             (np.float32, 5000, 33, 0.01), (np.float64, 300, 150, 0.9),
-                                            (np.float32, 20000, 128, 0.5)])
+                                            (np.float32, 20000, 128, 0.5),
+                                            # p = 210,000: the matrix-free large-free-set solve (mixed form)
+                                            (np.float32, 420000, 128, 0.5)])
 def test_newton_direction(prec, gscale, dtype, n, q, frac):
     """Algorithm 3, Step 1.  PLAIN_FP64 solves the reduced system exactly
     (Cholesky); MIXED solves it by preconditioned CG to Algorithm 3's
