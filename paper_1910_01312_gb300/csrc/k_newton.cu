@@ -894,7 +894,7 @@ __global__ void __launch_bounds__(kCgThreads) newton_cg_fast_kernel(int q, const
 // ~300 us (setup kernel, unused pass launches), so it starts at 1e5 rows.
 constexpr long long kMfMinP = 100000;
 constexpr int kMfSample = 2048;
-constexpr int kMfMaxPass = 12;
+constexpr int kMfMaxPass = 6;
 constexpr int kMfThreads = 512;
 
 struct MfState {   // CG state carried between passes (global memory)
@@ -988,13 +988,19 @@ __global__ void __launch_bounds__(kCgThreads) newton_mf_setup_kernel(int q, cons
             for (int i = 0; i < kPb; ++i) Y[(kb + i) * ld + tid] = out[i];
         }
         __syncthreads();
-        const int rows = qp - kb - kPb, cols = kb + kPb;
-        for (int e = tid; e < rows * cols; e += nt) {
-            const int r = kb + kPb + e / cols, c = e % cols;
-            float a = 0.f;
+        {   // rows below, a warp per row: T_r -= L_rb Y_b over the columns <= kb + 7
+            const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+            for (int r = kb + kPb + warp; r < qp; r += nw) {
+                float lr[kPb];
 #pragma unroll
-            for (int k = 0; k < kPb; ++k) a = fmaf(S.L[lpos(r, kb + k)], Y[(kb + k) * ld + c], a);
-            Y[r * ld + c] -= a;
+                for (int k = 0; k < kPb; ++k) lr[k] = S.L[lpos(r, kb + k)];
+                for (int c = lane; c < kb + kPb; c += 32) {
+                    float a = 0.f;
+#pragma unroll
+                    for (int k = 0; k < kPb; ++k) a = fmaf(lr[k], Y[(kb + k) * ld + c], a);
+                    Y[r * ld + c] -= a;
+                }
+            }
         }
         __syncthreads();
     }
@@ -1319,14 +1325,25 @@ __global__ void __launch_bounds__(256) gram_tc_kernel(const float *__restrict__ 
     for (int j = 0; j < kCgMaxQ / 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
     // column sums: thread handles the float4 column group c4 = tid % 32 of its rows
     float hs[4] = {0.f, 0.f, 0.f, 0.f}, hc[4] = {0.f, 0.f, 0.f, 0.f};
+    __shared__ int jrow[kTcStage];
     for (long long rb = r0; rb < r1; rb += kTcStage) {
-        for (int e = threadIdx.x; e < kTcStage * 32; e += blockDim.x) {
-            const int rr = e >> 5, c4 = e & 31;
-            const long long r = rb + rr;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (r < r1 && c4 < nq4) v = __ldcs(reinterpret_cast<const float4 *>(X + (long long)J[r] * q) + c4);
-            *reinterpret_cast<float4 *>(&T[rr * kTcLd + 4 * c4]) = v;
-            const float xs[4] = {v.x, v.y, v.z, v.w};
+        // the stage's row indices first, then every row load of a thread in flight at once
+        if (threadIdx.x < kTcStage) jrow[threadIdx.x] = (rb + threadIdx.x < r1) ? J[rb + threadIdx.x] : -1;
+        __syncthreads();
+        constexpr int kPer = kTcStage * 32 / 256;
+        float4 v[kPer];
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+            const int e = threadIdx.x + 256 * u, rr = e >> 5, c4 = e & 31;
+            const int jr = jrow[rr];
+            v[u] = (jr >= 0 && c4 < nq4) ? __ldcs(reinterpret_cast<const float4 *>(X + (long long)jr * q) + c4)
+                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+            const int e = threadIdx.x + 256 * u, rr = e >> 5, c4 = e & 31;
+            *reinterpret_cast<float4 *>(&T[rr * kTcLd + 4 * c4]) = v[u];
+            const float xs[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 float sn, er;
@@ -1393,36 +1410,41 @@ __global__ void __launch_bounds__(256) gram_tc_kernel(const float *__restrict__ 
 // M_pre = I + sigma (G - h h' / p) from the TF32 Gram partials (FP32 sums in
 // block order) and the exact column sums h; written as (value, 0) pairs for
 // the factor of newton_mf_setup_kernel.
+// Eight lanes per entry sum interleaved eighths of the partials, combined by
+// shuffles in a fixed order.
 __global__ void build_m_tc_kernel(int q, int G, const float *__restrict__ cpart, const float2 *__restrict__ hpart,
                                   float2 rp, float2 sig, float2 *__restrict__ Mf)
 {
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < q * q; e += gridDim.x * blockDim.x) {
-        const int a = e / q, b = e - a * q;
-        if (b > a) continue;
+    const int lane = threadIdx.x & 31, sub = lane & 7;
+    const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwg = (gridDim.x * blockDim.x) >> 5;
+    // the trip count is uniform per warp (four entries per warp and step), so
+    // every lane takes part in the shuffles below
+    for (int base = wg * 4; base < q * q; base += nwg * 4) {
+        const int t = base + (lane >> 3);
+        const bool valid = t < q * q;
+        const int a = valid ? t / q : 0, b = valid ? t - a * q : 1;
         float gs = 0.f;
         float2 ha = make_float2(0.f, 0.f), hb = ha;
-        int k = 0;
-        for (; k + 7 < G; k += 8) {
-            float v[8];
-            float2 x[8], y[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                v[u] = __ldcg(&cpart[(size_t)(k + u) * q * q + e]);
-                x[u] = __ldcg(&hpart[(size_t)(k + u) * q + a]);
-                y[u] = __ldcg(&hpart[(size_t)(k + u) * q + b]);
+        if (valid && b <= a) {
+#pragma unroll 4
+            for (int k = sub; k < G; k += 8) {
+                gs += __ldcg(&cpart[(size_t)k * q * q + t]);
+                ha = dfx_add(ha, __ldcg(&hpart[(size_t)k * q + a]));
+                hb = dfx_add(hb, __ldcg(&hpart[(size_t)k * q + b]));
             }
+        }
 #pragma unroll
-            for (int u = 0; u < 8; ++u) { gs += v[u]; ha = dfx_add(ha, x[u]); hb = dfx_add(hb, y[u]); }
+        for (int o = 1; o < 8; o <<= 1) {
+            gs += __shfl_xor_sync(0xffffffffu, gs, o);
+            ha = dfx_add(ha, shfl_xor_f2(ha, o));
+            hb = dfx_add(hb, shfl_xor_f2(hb, o));
         }
-        for (; k < G; ++k) {
-            gs += __ldcg(&cpart[(size_t)k * q * q + e]);
-            ha = dfx_add(ha, __ldcg(&hpart[(size_t)k * q + a]));
-            hb = dfx_add(hb, __ldcg(&hpart[(size_t)k * q + b]));
+        if (sub == 0 && valid && b <= a) {
+            float2 m = dfx_mul(sig, dfx_sub(make_float2(gs, 0.f), dfx_mul(dfx_mul(ha, hb), rp)));
+            if (a == b) m = dfx_addf(m, 1.f);
+            Mf[(size_t)a * q + b] = m;
+            Mf[(size_t)b * q + a] = m;
         }
-        float2 m = dfx_mul(sig, dfx_sub(make_float2(gs, 0.f), dfx_mul(dfx_mul(ha, hb), rp)));
-        if (a == b) m = dfx_addf(m, 1.f);
-        Mf[(size_t)a * q + b] = m;
-        Mf[(size_t)b * q + a] = m;
     }
 }
 
@@ -1491,7 +1513,7 @@ static cudaError_t launch_newton_mf(Work &W, const int32_t *J, long long p, doub
                                                                      W.mf_st, W.mf_pinv, W.err, vdot, W.red);
     const float2 sig = split2(sigma), rp = split2(1.0 / (double)p);
     float2 *pp = reinterpret_cast<float2 *>(W.part);
-    const int G = 2 * W.nsm;
+    const int G = W.nsm;
     for (int k = 0; k < kMfMaxPass; ++k) {
         const int last = k == kMfMaxPass - 1;
         if (k == 0)
