@@ -77,3 +77,30 @@ def gauss1m(seed: int = 0, n: int = 1_000_000, q: int = 128):
     X, y = gaussian_two_class(n, q, 0.3, np.linspace(0.1, 2.0, q), 0.10, seed, np.float32,
                               "gauss1m")
     return X, y, 0.1
+
+
+def warm_instance(seed: int, n: int = 100_000, q: int = 128):
+    """One instance of the learned-warm-start workload: the gauss1m generator
+    with per-instance class-mean scale m ~ U[0.1, 0.5], label noise ~ U[0, 0.15]
+    and C = 10^U[-2, 1].  Returns (X [n x q] FP32, y int8, C)."""
+    rng = _rng("warm", seed)
+    m = rng.uniform(0.1, 0.5)
+    noise = rng.uniform(0.0, 0.15)
+    C = float(10.0 ** rng.uniform(-2.0, 1.0))
+    X, y = gaussian_two_class(n, q, m, np.linspace(0.1, 2.0, q), noise, 10_000 + int(seed), np.float32, "warm")
+    return X, y, C
+
+
+MLP_IN, MLP_H = 132, 256          # the warm-start network: 132 -> 256 -> 256 -> 3
+
+
+def mlp_init(seed: int = 0) -> np.ndarray:
+    """Initial parameters of the warm-start MLP as one flat FP32 vector in the
+    layout [W1 (132x256, row-major in x out), b1, W2 (256x256), b2, W3 (256x3),
+    b3]: weights ~ N(0, 2/fan_in) (He), biases 0."""
+    rng = np.random.default_rng([_IDS["warm"], 1_000_000 + int(seed)])
+    parts = []
+    for fi, fo in ((MLP_IN, MLP_H), (MLP_H, MLP_H), (MLP_H, 3)):
+        parts.append((rng.standard_normal((fi, fo)) * np.sqrt(2.0 / fi)).ravel())
+        parts.append(np.zeros(fo))
+    return np.concatenate(parts).astype(np.float32)
