@@ -14,7 +14,8 @@ definition of each step, in FP64 numpy:
             gelu(x) = x Phi(x) = x (1 + erf(x / sqrt 2)) / 2
   loss      L = (1/N) sum_i c_{l_i} (logsumexp(Z3_i) - Z3_i[l_i])  (class-weighted
             cross-entropy), and its gradient by the chain rule
-  Adam      Kingma and Ba (2015), bias-corrected moments
+  AdamW     Kingma and Ba (2015), bias-corrected moments, with the decoupled
+            weight decay of Loshchilov and Hutter (2019)
   start     alpha^0_i = 0, C/2 or C for the predicted class (then projected onto
             the feasible set by the solver's warm-start path)
 
@@ -105,13 +106,15 @@ def grad(theta, F, labels, cw):
     return pack([gW1, gb1, gW2, gb2, gW3, gb3])
 
 
-def adam_step(theta, m, v, g, t, lr, b1=0.9, b2=0.999, eps=1e-8):
-    """One Adam update (t = 1, 2, ...); returns (theta, m, v)."""
+def adam_step(theta, m, v, g, t, lr, b1=0.9, b2=0.999, eps=1e-8, wd=0.0):
+    """One AdamW update (t = 1, 2, ...): Adam's bias-corrected step plus the
+    decoupled weight decay lr * wd * theta of Loshchilov and Hutter (2019);
+    returns (theta, m, v)."""
     m = b1 * m + (1.0 - b1) * g
     v = b2 * v + (1.0 - b2) * g * g
     mh = m / (1.0 - b1 ** t)
     vh = v / (1.0 - b2 ** t)
-    return theta - lr * mh / (np.sqrt(vh) + eps), m, v
+    return theta - lr * (mh / (np.sqrt(vh) + eps) + wd * theta), m, v
 
 
 def classes_of(alpha, C):

@@ -53,7 +53,10 @@ class Stats(C.Structure):
 SYMBOLS = ["svm_default_params", "svm_ssnalm_create", "svm_ssnalm_solve", "svm_ssnalm_destroy",
            "svm_ssnalm_last_error", "svm_op_matvec", "svm_op_rmatvec", "svm_op_project",
            "svm_op_newton", "svm_op_kkt", "svm_ssnalm_set_timing", "svm_ssnalm_get_stats",
-           "svm_rmatvec_noalloc"]
+           "svm_rmatvec_noalloc", "svm_mlp_create", "svm_mlp_destroy", "svm_mlp_get_params",
+           "svm_mlp_features", "svm_mlp_labels", "svm_mlp_gather", "svm_mlp_forward", "svm_mlp_loss_grad", "svm_mlp_adam_step",
+           "svm_mlp_train_step", "svm_mlp_start_point", "svm_ssnalm_solve_mlp"]
+MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_NPARAM = 132, 256, 3, 100611
 
 _lock = threading.Lock()
 _lib = None
@@ -94,8 +97,25 @@ def load(build_if_missing: bool = False):
         L.svm_ssnalm_set_timing.argtypes = [vp, C.c_int]
         L.svm_ssnalm_get_stats.argtypes = [vp, C.POINTER(Stats), C.c_int]
         L.svm_rmatvec_noalloc.argtypes = [vp, vp, i64, i64, vp, vp, vp]
+        f32, dbl = C.c_float, C.c_double
+        L.svm_mlp_create.argtypes = [C.POINTER(vp), vp, i64, vp]
+        L.svm_mlp_destroy.argtypes = [vp]
+        L.svm_mlp_destroy.restype = None
+        L.svm_mlp_get_params.argtypes = [vp, vp]
+        L.svm_mlp_features.argtypes = [vp, vp, i64, i64, dbl, vp, vp]
+        L.svm_mlp_forward.argtypes = [vp, vp, i64, vp]
+        L.svm_mlp_labels.argtypes = [vp, i64, dbl, vp, vp]
+        L.svm_mlp_gather.argtypes = [vp, vp, vp, i64, vp, vp, vp]
+        L.svm_mlp_loss_grad.argtypes = [vp, vp, vp, i64, vp, vp, vp]
+        L.svm_mlp_adam_step.argtypes = [vp, vp, i64, f32, f32]
+        L.svm_mlp_train_step.argtypes = [vp, vp, vp, i64, vp, i64, f32, f32, vp]
+        L.svm_mlp_start_point.argtypes = [vp, vp, i64, dbl, vp]
+        L.svm_ssnalm_solve_mlp.argtypes = [vp, vp, C.POINTER(Result), C.POINTER(C.c_int32)]
         for f in ("svm_op_matvec", "svm_op_rmatvec", "svm_op_project", "svm_op_newton", "svm_op_kkt",
-                  "svm_ssnalm_set_timing", "svm_ssnalm_get_stats", "svm_rmatvec_noalloc"):
+                  "svm_ssnalm_set_timing", "svm_ssnalm_get_stats", "svm_rmatvec_noalloc", "svm_mlp_create",
+                  "svm_mlp_get_params", "svm_mlp_features", "svm_mlp_labels", "svm_mlp_gather", "svm_mlp_forward",
+                  "svm_mlp_loss_grad",
+                  "svm_mlp_adam_step", "svm_mlp_train_step", "svm_mlp_start_point", "svm_ssnalm_solve_mlp"):
             getattr(L, f).restype = C.c_int
         _lib = L
         return L
@@ -196,6 +216,18 @@ class Solver:
         out["status"] = st
         return out
 
+    def solve_mlp(self, mlp, alpha, w, allow=(OK, ERR_NOT_CONVERGED, ERR_DEGENERATE)):
+        """Warm-started solve from the network `mlp` (an MLP), cold fallback;
+        the returned dict adds "used_warm"."""
+        R = Result(alpha=_ptr(alpha), w=_ptr(w))
+        used = C.c_int32(0)
+        st = self._lib.svm_ssnalm_solve_mlp(self.h, mlp.h, C.byref(R), C.byref(used))
+        self._check(st, allow)
+        out = {k: getattr(R, k) for k, _ in Result._fields_ if k not in ("alpha", "w", "reserved0")}
+        out["status"] = st
+        out["used_warm"] = used.value
+        return out
+
     def set_timing(self, enable=True):
         self._check(self._lib.svm_ssnalm_set_timing(self.h, 1 if enable else 0))
 
@@ -225,3 +257,71 @@ class Solver:
         r, lam = C.c_double(0.0), C.c_double(0.0)
         self._check(self._lib.svm_op_kkt(self.h, _ptr(alpha), C.byref(r), C.byref(lam)))
         return r.value, lam.value
+
+
+def _mlp_check(st, what):
+    if st != OK:
+        raise SVMError(st, what)
+
+
+def mlp_features(X, y, C_, F, stream=None):
+    """F (n x 132, FP32) = warm-start features of the device problem (X FP32
+    n x 128, y int8)."""
+    n, q = X.shape
+    _mlp_check(load().svm_mlp_features(_ptr(X), _ptr(y), int(n), int(q), float(C_), _ptr(F), stream),
+               "svm_mlp_features")
+
+
+def mlp_labels(alpha, C_, labels, stream=None):
+    """labels (int32) = 0 / 1 / 2 where alpha (FP64) is at 0 / free / at C."""
+    _mlp_check(load().svm_mlp_labels(_ptr(alpha), int(alpha.shape[0]), float(C_), _ptr(labels), stream),
+               "svm_mlp_labels")
+
+
+def mlp_gather(F, labels, idx, Fb, Lb, stream=None):
+    """Fb[r] = F[idx[r]], Lb[r] = labels[idx[r]] (idx int64 on the device)."""
+    _mlp_check(load().svm_mlp_gather(_ptr(F), _ptr(labels), _ptr(idx), int(idx.shape[0]), _ptr(Fb), _ptr(Lb), stream),
+               "svm_mlp_gather")
+
+
+class MLP:
+    """Owns one svm_mlp_t (the warm-start network) on a stream; tensors are
+    device tensors (FP32 features and parameters, int32 labels)."""
+
+    def __init__(self, params, max_rows, stream=None):
+        self._lib = load()
+        self.h = C.c_void_p()
+        self.max_rows = int(max_rows)
+        _mlp_check(self._lib.svm_mlp_create(C.byref(self.h), _ptr(params), self.max_rows, stream), "svm_mlp_create")
+
+    def close(self):
+        if self.h:
+            self._lib.svm_mlp_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self, out):
+        _mlp_check(self._lib.svm_mlp_get_params(self.h, _ptr(out)), "svm_mlp_get_params")
+
+    def forward(self, F, logits):
+        _mlp_check(self._lib.svm_mlp_forward(self.h, _ptr(F), int(F.shape[0]), _ptr(logits)), "svm_mlp_forward")
+
+    def loss_grad(self, F, labels, cw, loss, grad):
+        _mlp_check(self._lib.svm_mlp_loss_grad(self.h, _ptr(F), _ptr(labels), int(F.shape[0]), _ptr(cw), _ptr(loss),
+                                               _ptr(grad)), "svm_mlp_loss_grad")
+
+    def adam_step(self, grad, t, lr, wd=0.0):
+        _mlp_check(self._lib.svm_mlp_adam_step(self.h, _ptr(grad), int(t), float(lr), float(wd)), "svm_mlp_adam_step")
+
+    def train_step(self, F, labels, cw, t, lr, wd=0.0, loss=None):
+        _mlp_check(self._lib.svm_mlp_train_step(self.h, _ptr(F), _ptr(labels), int(F.shape[0]), _ptr(cw), int(t),
+                                                float(lr), float(wd), _ptr(loss)), "svm_mlp_train_step")
+
+    def start_point(self, F, C_, alpha0):
+        _mlp_check(self._lib.svm_mlp_start_point(self.h, _ptr(F), int(F.shape[0]), float(C_), _ptr(alpha0)),
+                   "svm_mlp_start_point")

@@ -34,7 +34,7 @@ def _sources():
 
 def _deps():
     return _sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + \
-        [os.path.join(HERE, "..", "include", "svm_ssnalm.h"), os.path.abspath(__file__)]
+        sorted(glob.glob(os.path.join(HERE, "..", "include", "*.h"))) + [os.path.abspath(__file__)]
 
 
 def up_to_date() -> bool:

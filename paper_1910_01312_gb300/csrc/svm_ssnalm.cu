@@ -30,6 +30,7 @@
 #include <utility>
 #include <vector>
 
+#include "../../include/svm_mlp.h"
 #include "../../include/svm_ssnalm.h"
 #include "internal.cuh"
 
@@ -806,4 +807,48 @@ extern "C" svm_status svm_ssnalm_get_stats(svm_ssnalm_t *h, svm_stats *out, int 
         h->syncs = 0;
     }
     return SVM_OK;
+}
+
+// Warm start from the learned network (include/svm_mlp.h), with the cold solve
+// as fallback.  The paper's own warm start is a cheaper solve of an
+// approximating problem (Sec. 4.3); the network plays that role here.
+extern "C" svm_status svm_ssnalm_solve_mlp(svm_ssnalm_t *h, svm_mlp_t *m, svm_result *res, int32_t *used_warm)
+{
+    if (used_warm) *used_warm = 0;
+    if (!h || !m || !res) return SVM_ERR_INVALID_ARG;
+    Work &W = h->W;
+    if (!W.xf32 || W.q != SVM_MLP_IN - 4) {
+        h->err = "the warm-start network needs dense FP32 X with q = 128";
+        return SVM_ERR_UNSUPPORTED;
+    }
+    const long long n = W.n;
+    float *F = nullptr;
+    double *a0 = nullptr;
+    if (cudaMallocAsync(&F, sizeof(float) * n * SVM_MLP_IN, W.st) != cudaSuccess ||
+        cudaMallocAsync(&a0, sizeof(double) * n, W.st) != cudaSuccess) {
+        if (F) cudaFreeAsync(F, W.st);
+        h->err = "device allocation of the warm-start buffers failed";
+        return SVM_ERR_OOM;
+    }
+    svm_status st = svm_mlp_features((const float *)W.X, W.y, n, W.q, h->P.C, F, W.st);
+    if (st == SVM_OK) st = svm_mlp_start_point(m, F, n, h->P.C, a0);
+    std::vector<double> host_a0;
+    if (st == SVM_OK && h->prob.memory == SVM_MEM_HOST) {
+        host_a0.resize((size_t)n);
+        if (cudaMemcpyAsync(host_a0.data(), a0, sizeof(double) * n, cudaMemcpyDeviceToHost, W.st) != cudaSuccess ||
+            cudaStreamSynchronize(W.st) != cudaSuccess)
+            st = SVM_ERR_CUDA;
+    }
+    if (st != SVM_OK) {
+        cudaFreeAsync(F, W.st);
+        cudaFreeAsync(a0, W.st);
+        h->err = "warm-start features or network failed";
+        return st;
+    }
+    st = svm_ssnalm_solve(h, h->prob.memory == SVM_MEM_HOST ? host_a0.data() : a0, res);
+    cudaFreeAsync(F, W.st);
+    cudaFreeAsync(a0, W.st);
+    if (st == SVM_ERR_NOT_CONVERGED || st == SVM_ERR_NUMERIC) return svm_ssnalm_solve(h, nullptr, res);
+    if (used_warm) *used_warm = 1;
+    return st;
 }

@@ -68,6 +68,12 @@ def test_first_adam_step_closed_form():
     th, g = rng.normal(size=50), rng.normal(size=50)
     t1, m, v = mlp.adam_step(th, np.zeros(50), np.zeros(50), g, 1, 1e-3, eps=1e-8)
     np.testing.assert_allclose(t1, th - 1e-3 * g / (np.abs(g) + 1e-8), rtol=1e-12)
+    # decoupled decay: the first step moves by lr (sign-like step + wd theta)
+    t2, _, _ = mlp.adam_step(th, np.zeros(50), np.zeros(50), g, 1, 1e-3, eps=1e-8, wd=0.01)
+    np.testing.assert_allclose(t2, th - 1e-3 * (g / (np.abs(g) + 1e-8) + 0.01 * th), rtol=1e-12)
+    # second step with a constant gradient: m_hat = g, v_hat = g^2 again
+    t3, _, _ = mlp.adam_step(t1, *mlp.adam_step(th, np.zeros(50), np.zeros(50), g, 1, 1e-3)[1:], g, 2, 1e-3)
+    np.testing.assert_allclose(t3, th - 2e-3 * g / (np.abs(g) + 1e-8), rtol=1e-12)
 
 
 def test_features_hand_example():
