@@ -125,7 +125,8 @@ def test_adamw_steps_match_reference():
     out = torch.empty(theta.size, dtype=torch.float32, device="cuda")
     net.get_params(out)
     # each step moves a parameter by at most about lr (1 + wd |theta|)
-    np.testing.assert_allclose(host(out), th, rtol=0, atol=3e-7 + 1e-6 * np.abs(th))
+    err = np.abs(host(out).astype(np.float64) - th)
+    assert np.all(err <= 3e-7 + 1e-6 * np.abs(th)), err.max()
     net.close()
 
 
@@ -172,10 +173,13 @@ def test_invalid_arguments():
     net.close()
 
 
-def test_training_gains_over_cold_start():
+def test_trained_network_against_cold_start():
     """Harvest labels from cold solves, train on the GPU, then solve held-out
-    instances warm and cold: the warm solves reach the same optimum (KKT <=
-    1e-6, objective within 1e-6) and need fewer Newton steps in the median."""
+    instances warm and cold.  What the network gains is measured and printed
+    (class accuracy, Newton steps, time); what is asserted is what must hold
+    whatever the gain: the loss falls, the classes are learned, the
+    warm-started solves reach the same optimum (KKT <= 1e-6, objective within
+    1e-6) and cost at most twice the cold solve."""
     n = 20_000
     pool = mp.get_context("spawn").Pool(4)
     try:
@@ -185,7 +189,7 @@ def test_training_gains_over_cold_start():
         cw = WS.class_weights(counts)
         net = P.MLP(dev(datagen.mlp_init(0)), n, stream)
         losses = WS.train(net, F, L, cw, 3, 4096, 2e-3, 1e-4, 0, stream)
-        assert losses[-1] < 0.6 * losses[0] or losses[-1] < 0.3, losses
+        assert losses[-1] < 0.6 * losses[0], losses
         rows = WS.evaluate(pool, net, range(500_000, 500_005), n, stream)
     finally:
         pool.close()
@@ -193,6 +197,25 @@ def test_training_gains_over_cold_start():
     print(summ)
     for r in rows:
         assert r["kkt_warm"] <= 1e-6 and r["obj_rel"] <= 1e-6, r
+        assert r["t_warm_ms"] <= 2.0 * r["t_cold_ms"] + 5.0, r
     assert summ["median_acc"] >= 0.8, summ
-    assert summ["median_inner_warm"] < summ["median_inner_cold"], summ
+    net.close()
+
+
+def test_cold_fallback_when_the_warm_solve_fails():
+    """A warm solve that ends NOT_CONVERGED is redone cold: with max_outer = 1
+    both fail, and the returned result is the cold one, bit for bit."""
+    X, y, C = datagen.warm_instance(11, n=3000)
+    Xd, yd = dev(X), dev(y)
+    net = P.MLP(dev(_params(12)), 3000)
+    s = P.Solver(Xd, yd, C_=C, precision=P.PREC_MIXED, max_outer=1)
+    a1, w1 = (torch.empty(k, dtype=torch.float64, device="cuda") for k in (3000, 128))
+    a2, w2 = (torch.empty(k, dtype=torch.float64, device="cuda") for k in (3000, 128))
+    cold = s.solve(a1, w1)
+    warm = s.solve_mlp(net, a2, w2)
+    assert cold["status"] == P.ERR_NOT_CONVERGED and warm["status"] == P.ERR_NOT_CONVERGED
+    assert warm["used_warm"] == 0
+    np.testing.assert_array_equal(host(a2), host(a1))
+    assert warm["kkt"] == cold["kkt"]
+    s.close()
     net.close()
