@@ -104,3 +104,56 @@ def mlp_init(seed: int = 0) -> np.ndarray:
         parts.append((rng.standard_normal((fi, fo)) * np.sqrt(2.0 / fi)).ravel())
         parts.append(np.zeros(fo))
     return np.concatenate(parts).astype(np.float32)
+
+
+def sparse_text(seed: int = 0, n: int = 700_000, q: int = 47_000, nnz_row: int = 75, zipf: float = 1.1,
+                noise: float = 0.1, density_w: float = 0.1, dtype=np.float32):
+    """Text-like sparse two-class problem in CSR form: each row holds nnz_row
+    distinct columns drawn without replacement from a Zipf(zipf) law over the
+    q columns (successive draws, repeats discarded; at most 3 nnz_row draws,
+    so a row can fall short when q is small), column indices strictly
+    increasing, values lognormal(0, 1), each row scaled to unit L2 norm;
+    labels sign(X w* + noise eps) with w* nonzero (N(0, 1)) on a random
+    density_w fraction of the columns, eps ~ N(0, 1); C = 1.
+
+    Returns (indptr int64 [n+1], indices int32 [nnz], values dtype [nnz],
+    y int8 [n], C)."""
+    rng = _rng("csr", seed)
+    pr = 1.0 / np.arange(1, q + 1, dtype=np.float64) ** zipf
+    cdf = np.cumsum(pr)
+    cdf /= cdf[-1]
+    perm = rng.permutation(q)            # which column gets which frequency rank
+    indptr = np.zeros(n + 1, np.int64)
+    idx_parts, val_parts = [], []
+    step = 1 << 15
+    for s in range(0, n, step):
+        m = min(step, n - s)
+        K = 3 * nnz_row
+        D = perm[np.minimum(np.searchsorted(cdf, rng.random((m, K))), q - 1)]
+        order = np.argsort(D, axis=1, kind="stable")
+        Ds = np.take_along_axis(D, order, axis=1)
+        fs = np.ones_like(Ds, dtype=bool)
+        fs[:, 1:] = Ds[:, 1:] != Ds[:, :-1]
+        first = np.zeros_like(fs)
+        np.put_along_axis(first, order, fs, axis=1)          # first draw of each column
+        keep = first & (np.cumsum(first, axis=1) <= nnz_row)   # the first nnz_row distinct
+        cols = np.where(keep, D, q)
+        cols.sort(axis=1)
+        cols = cols[:, :nnz_row]
+        valid = cols < q
+        cnt = valid.sum(axis=1)
+        c = cols[valid].astype(np.int32)
+        v = rng.lognormal(0.0, 1.0, c.size)
+        starts = np.concatenate([[0], np.cumsum(cnt)[:-1]])
+        norms = np.sqrt(np.add.reduceat(v * v, starts))
+        v /= np.repeat(norms, cnt)
+        indptr[s + 1:s + m + 1] = indptr[s] + np.cumsum(cnt)
+        idx_parts.append(c)
+        val_parts.append(v.astype(dtype))
+    indices = np.concatenate(idx_parts)
+    values = np.concatenate(val_parts)
+    w = np.where(rng.random(q) < density_w, rng.standard_normal(q), 0.0)
+    rows = np.repeat(np.arange(n), np.diff(indptr))
+    margin = np.bincount(rows, weights=values.astype(np.float64) * w[indices], minlength=n)
+    y = np.where(margin + noise * rng.standard_normal(n) >= 0.0, 1, -1).astype(np.int8)
+    return indptr, indices, values, y, 1.0

@@ -68,15 +68,16 @@ typedef enum { SVM_MEM_DEVICE = 0, SVM_MEM_HOST = 1 } svm_memory;
 typedef struct {
     int64_t n;              /* number of samples (rows of X), >= 1             */
     int64_t q;              /* number of features (columns of X), >= 1         */
-    int32_t layout;         /* svm_layout; this build: SVM_DENSE_ROWMAJOR      */
+    int32_t layout;         /* svm_layout                                      */
     int32_t dtype;          /* svm_dtype of X                                  */
     int32_t memory;         /* svm_memory of X and y                           */
     int32_t reserved0;
     const void *X;          /* dense: n*q elements, row-major, 16-byte aligned */
-    const int64_t *indptr;  /* CSR (reserved)                                  */
-    const int32_t *indices; /* CSR (reserved)                                  */
-    const void *values;     /* CSR (reserved)                                  */
-    int64_t nnz;            /* CSR (reserved)                                  */
+    const int64_t *indptr;  /* CSR: n+1 row pointers, indptr[0] = 0, [n] = nnz */
+    const int32_t *indices; /* CSR: nnz column indices, strictly increasing
+                               within each row, each in [0, q)               */
+    const void *values;     /* CSR: nnz values of type dtype                  */
+    int64_t nnz;            /* CSR: number of stored entries (>= 0)            */
     const int8_t *y;        /* n labels, each +1 or -1                         */
 } svm_problem;
 
@@ -127,6 +128,12 @@ void svm_default_params(svm_params *p);
  * and unchanged until svm_ssnalm_destroy.  With SVM_MEM_HOST it copies them
  * to the device (the copy is timed as part of create).  The handle owns all
  * device workspace (O(n) vectors, O(q^2) Newton matrix).
+ * CSR (layout = SVM_CSR, any q < 2^31, Sec. 4's sparse datasets): create also
+ * checks the row structure and builds a CSC copy of X (O(nnz) device memory,
+ * borrowed arrays stay borrowed); the solve runs the FP64 form whatever the
+ * precision asks, with z = A v over the rows, A'c over the CSC columns and the
+ * Newton system (Prop. 3.5) by matrix-free Jacobi-preconditioned CG
+ * (Algorithm 3) instead of a q x q factorisation.
  * Returns SVM_ERR_INVALID_ARG, SVM_ERR_OOM, SVM_ERR_CUDA, SVM_ERR_UNSUPPORTED.
  * *out is NULL on failure. */
 svm_status svm_ssnalm_create(svm_ssnalm_t **out, const svm_problem *prob,

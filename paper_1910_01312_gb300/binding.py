@@ -161,15 +161,22 @@ class Solver:
     X, y: torch CUDA tensors (memory=DEVICE, borrowed: keep them alive) or
     host arrays -- numpy or torch CPU tensors, pinned or not -- (memory=HOST,
     copied to the device by create; the solve's outputs are then host arrays
-    too)."""
+    too).  For a sparse X pass csr=(indptr, indices, values, q) instead (same
+    memory rules; X is then ignored)."""
 
-    def __init__(self, X, y, C_=1.0, stream=None, **params):
+    def __init__(self, X, y, C_=1.0, stream=None, csr=None, **params):
         self._lib = load()
         self.h = C.c_void_p()
-        is_host = not bool(getattr(X, "is_cuda", False))
+        if csr is not None:
+            # csr = (indptr int64 [n+1], indices int32 [nnz], values FP32/FP64 [nnz], q); X unused
+            indptr, indices, values, q = csr
+            n, V = int(indptr.shape[0]) - 1, values
+        else:
+            n, q = X.shape
+            V = X
+        is_host = not bool(getattr(V, "is_cuda", False))
         self.memory = MEM_HOST if is_host else MEM_DEVICE
-        n, q = X.shape
-        dt = str(X.dtype)
+        dt = str(V.dtype)
         if dt.endswith("float32"):
             dtype = F32
         elif dt.endswith("float64"):
@@ -177,9 +184,14 @@ class Solver:
         else:
             raise TypeError(f"X dtype {dt} not supported")
         self.n, self.q = int(n), int(q)
-        self._keep = (X, y)
-        prob = Problem(n=n, q=q, layout=DENSE_ROWMAJOR, dtype=dtype, memory=self.memory, X=_ptr(X),
-                       indptr=None, indices=None, values=None, nnz=0, y=_ptr(y))
+        if csr is not None:
+            self._keep = (indptr, indices, values, y)
+            prob = Problem(n=n, q=q, layout=CSR, dtype=dtype, memory=self.memory, X=None, indptr=_ptr(indptr),
+                           indices=_ptr(indices), values=_ptr(values), nnz=int(values.shape[0]), y=_ptr(y))
+        else:
+            self._keep = (X, y)
+            prob = Problem(n=n, q=q, layout=DENSE_ROWMAJOR, dtype=dtype, memory=self.memory, X=_ptr(X),
+                           indptr=None, indices=None, values=None, nnz=0, y=_ptr(y))
         P = default_params(C=float(C_), **params)
         if stream is not None:
             P.stream = stream

@@ -77,11 +77,37 @@ struct ProjBuf {
     int32_t *J = nullptr, *S = nullptr;
 };
 
+struct CsrCg;
+
 struct Work {
     // problem
     int64_t n = 0, q = 0;
-    int xf32 = 1;            // X is FP32 (else FP64)
+    int xf32 = 1;            // X (dense) or the CSR values are FP32 (else FP64)
     const void *X = nullptr;
+    // CSR layout: row pointers, column indices (strictly increasing within a
+    // row) and values, their CSC copy (built at create), the column tasks of
+    // the transposed product (task t covers CSC entries [task_beg[t],
+    // task_beg[t+1]); column j owns tasks [col_task[j], col_task[j+1])) and the
+    // matrix-free Newton CG state
+    bool csr = false;
+    const int64_t *csr_ptr = nullptr;
+    const int32_t *csr_idx = nullptr;
+    const void *csr_val = nullptr;
+    int64_t nnz = 0;
+    int64_t *csc_ptr = nullptr;
+    int32_t *csc_row = nullptr;
+    void *csc_val = nullptr;
+    int64_t *task_beg = nullptr, *col_task = nullptr;
+    double *task_part = nullptr;
+    long long ntask = 0;
+    double *csr_tn = nullptr;   // n-vector: X_J d scattered to the rows of J
+    double *csr_q = nullptr;    // 6 q-vectors of the CG
+    CsrCg *csr_cg = nullptr;
+    int *h_csr_done = nullptr;  // pinned
+    int csr_cg_maxit = 500;
+    int64_t *csr_ptr_own = nullptr;
+    int32_t *csr_idx_own = nullptr;
+    void *csr_val_own = nullptr;
     const int8_t *y = nullptr;
     double C = 1.0;
     int precision = 1;
@@ -184,5 +210,14 @@ cudaError_t launch_newton(Work &W, const int32_t *J, long long p_host, const lon
                           double sigma, const double *g, double *dv, bool dots = false);
 // workspace of the large-free-set Newton solve (mixed form, FP32 X, q <= 128)
 cudaError_t newton_mf_alloc(Work &W);
+
+// CSR layout: structure/value checks (dev_flags[0]: structure, [1]: non-finite),
+// the CSC copy and column tasks, and the three products of the method
+cudaError_t csr_validate(Work &W, int *dev_flags);
+cudaError_t csr_setup(Work &W);
+cudaError_t launch_matvec_csr(Work &W, const double *v0, double *z0, const double *v1, double *z1);
+cudaError_t launch_rmatvec_csr(Work &W, const double *c, double *out, int scale_slot);
+cudaError_t launch_newton_csr(Work &W, const int32_t *J, long long p, double sigma, const double *g, double *dv,
+                              bool dots);
 
 }  // namespace svm

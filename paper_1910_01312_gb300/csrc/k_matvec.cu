@@ -220,12 +220,13 @@ static cudaError_t matvec_mx_dispatch(Work &W, const double *v0, void *z0, const
 
 cudaError_t launch_matvec_df(Work &W, const double *v0, float2 *z0, const double *v1, float2 *z1)
 {
-    if (!(W.xf32 && W.q % 4 == 0 && (uintptr_t)W.X % 16 == 0)) return cudaErrorInvalidValue;
+    if (!(!W.csr && W.xf32 && W.q % 4 == 0 && (uintptr_t)W.X % 16 == 0)) return cudaErrorInvalidValue;
     return v1 ? matvec_mx_dispatch<2, true>(W, v0, z0, v1, z1) : matvec_mx_dispatch<1, true>(W, v0, z0, v1, z1);
 }
 
 cudaError_t launch_matvec(Work &W, const double *v0, double *z0, const double *v1, double *z1)
 {
+    if (W.csr) return launch_matvec_csr(W, v0, z0, v1, z1);
     const size_t es = W.xf32 ? 4 : 8;
     const bool vec = ((W.q * es) % 16 == 0) && ((uintptr_t)W.X % 16 == 0);
     const bool two = v1 != nullptr;

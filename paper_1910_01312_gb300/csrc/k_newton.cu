@@ -1533,6 +1533,7 @@ cudaError_t launch_newton(Work &W, const int32_t *J, long long p_host, const lon
                           const double *g, double *dv, bool dots)
 {
     (void)p_dev;
+    if (W.csr) return launch_newton_csr(W, J, p_host, sigma, g, dv, dots);
     const int q = (int)W.q;
     if (p_host <= 0) {
         const cudaError_t e = launch_negcopy(W, g, dv);

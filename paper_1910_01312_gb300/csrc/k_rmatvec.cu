@@ -468,6 +468,7 @@ cudaError_t join_vector(Work &W, const float2 *a, bool signed_by_y, double *c)
 cudaError_t launch_rmatvec(Work &W, const double *c, const float2 *wc, const int32_t *idx, const long long *cnt_dev,
                            double *out, int scale_slot)
 {
+    if (W.csr) return launch_rmatvec_csr(W, c, out, scale_slot);
     if (W.precision == 1 && W.xf32 && wc)
         return rmatvec_mx(W, wc, nullptr, idx, cnt_dev, nullptr, nullptr, out, nullptr, scale_slot, GradOut());
     return W.xf32 ? rmatvec_t<float>(W, c, idx, cnt_dev, out, scale_slot)

@@ -141,7 +141,9 @@ static void free_work(Work &W)
 {
     void *ptrs[] = {W.alpha, W.z, W.dz, W.qa, W.tmpn, W.zf, W.dzf, W.qaf, W.alphaw, W.dw, W.dwa, W.atpa,
                     W.atpa2, W.mf_st, W.mf_pinv, W.mf_counter, W.v, W.vt, W.dv, W.g, W.atp, W.atp2, W.h, W.w, W.tmpq, W.M, W.Lf, W.Mf, W.part, W.cnt,
-                    W.bar, W.rm_counter, W.err, W.pout, W.red, W.X_own, W.y_own};
+                    W.bar, W.rm_counter, W.err, W.pout, W.red, W.X_own, W.y_own, W.csc_ptr, W.csc_row,
+                    W.csc_val, W.task_beg, W.col_task, W.task_part, W.csr_tn, W.csr_q, W.csr_cg,
+                    W.csr_ptr_own, W.csr_idx_own, W.csr_val_own};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (int b = 0; b < 2; ++b) {
@@ -152,6 +154,7 @@ static void free_work(Work &W)
     if (W.h_pout) cudaFreeHost(W.h_pout);
     if (W.h_red) cudaFreeHost(W.h_red);
     if (W.h_err) cudaFreeHost(W.h_err);
+    if (W.h_csr_done) cudaFreeHost(W.h_csr_done);
     W = Work();
 }
 
@@ -208,11 +211,14 @@ extern "C" svm_status svm_ssnalm_create(svm_ssnalm_t **out, const svm_problem *p
     if (prob->n > 0x7fffffffLL) { g_create_err = "n must fit in int32"; return SVM_ERR_UNSUPPORTED; }
     if (!(params->C > 0.0) || !isfinite(params->C)) { g_create_err = "C must be finite and > 0"; return SVM_ERR_INVALID_ARG; }
     if (!(params->tol > 0.0)) { g_create_err = "tol must be > 0"; return SVM_ERR_INVALID_ARG; }
-    if (!prob->X || !prob->y) { g_create_err = "X and y must be non-null"; return SVM_ERR_INVALID_ARG; }
-    if (prob->layout != SVM_DENSE_ROWMAJOR) { g_create_err = "only dense row-major X in this build"; return SVM_ERR_UNSUPPORTED; }
+    const bool csr = prob->layout == SVM_CSR;
+    if (prob->layout != SVM_DENSE_ROWMAJOR && !csr) { g_create_err = "layout must be dense row-major or CSR"; return SVM_ERR_INVALID_ARG; }
+    if (!prob->y || (!csr && !prob->X) || (csr && (!prob->indptr || (prob->nnz > 0 && (!prob->indices || !prob->values)))))
+    { g_create_err = "X (or the CSR arrays) and y must be non-null"; return SVM_ERR_INVALID_ARG; }
+    if (csr && (prob->nnz < 0 || prob->q > 0x7fffffffLL)) { g_create_err = "CSR: nnz >= 0 and q < 2^31 required"; return SVM_ERR_INVALID_ARG; }
     if (prob->dtype != SVM_F32 && prob->dtype != SVM_F64) { g_create_err = "dtype must be F32 or F64"; return SVM_ERR_INVALID_ARG; }
     if (prob->memory != SVM_MEM_DEVICE && prob->memory != SVM_MEM_HOST) { g_create_err = "bad memory kind"; return SVM_ERR_INVALID_ARG; }
-    if (prob->q > 1024) { g_create_err = "dense q > 1024 not supported in this build"; return SVM_ERR_UNSUPPORTED; }
+    if (!csr && prob->q > 1024) { g_create_err = "dense q > 1024 not supported in this build"; return SVM_ERR_UNSUPPORTED; }
     if (params->max_outer < 1 || params->max_inner < 1 || params->max_ls < 1) { g_create_err = "iteration caps must be >= 1"; return SVM_ERR_INVALID_ARG; }
     if (params->precision != SVM_PREC_PLAIN_FP64 && params->precision != SVM_PREC_MIXED) { g_create_err = "bad precision"; return SVM_ERR_INVALID_ARG; }
 
@@ -240,7 +246,31 @@ extern "C" svm_status svm_ssnalm_create(svm_ssnalm_t **out, const svm_problem *p
     cudaDeviceGetAttribute(&W.nsm, cudaDevAttrMultiProcessorCount, W.dev);
     const size_t n = (size_t)W.n, q = (size_t)W.q;
     const size_t xbytes = n * q * (W.xf32 ? 4 : 8);
-    if (prob->memory == SVM_MEM_HOST) {
+    W.csr = csr;
+    if (csr) {
+        W.nnz = prob->nnz;
+        const size_t nz = (size_t)prob->nnz, es = W.xf32 ? 4 : 8;
+        if (prob->memory == SVM_MEM_HOST) {
+            if (cudaMalloc(&W.csr_ptr_own, (n + 1) * sizeof(int64_t)) != cudaSuccess ||
+                cudaMalloc(&W.csr_idx_own, (nz ? nz : 1) * sizeof(int32_t)) != cudaSuccess ||
+                cudaMalloc(&W.csr_val_own, (nz ? nz : 1) * es) != cudaSuccess || dalloc(&W.y_own, n) != cudaSuccess)
+                return fail(SVM_ERR_OOM, "device allocation of the CSR/y copy failed");
+            if (cudaMemcpyAsync(W.csr_ptr_own, prob->indptr, (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, W.st) ||
+                (nz && cudaMemcpyAsync(W.csr_idx_own, prob->indices, nz * sizeof(int32_t), cudaMemcpyHostToDevice, W.st)) ||
+                (nz && cudaMemcpyAsync(W.csr_val_own, prob->values, nz * es, cudaMemcpyHostToDevice, W.st)) ||
+                cudaMemcpyAsync(W.y_own, prob->y, n, cudaMemcpyHostToDevice, W.st))
+                return fail(SVM_ERR_CUDA, "host-to-device copy of the CSR arrays/y failed");
+            W.csr_ptr = W.csr_ptr_own;
+            W.csr_idx = W.csr_idx_own;
+            W.csr_val = W.csr_val_own;
+            W.y = W.y_own;
+        } else {
+            W.csr_ptr = prob->indptr;
+            W.csr_idx = prob->indices;
+            W.csr_val = prob->values;
+            W.y = prob->y;
+        }
+    } else if (prob->memory == SVM_MEM_HOST) {
         if (cudaMalloc(&W.X_own, xbytes) != cudaSuccess || dalloc(&W.y_own, n) != cudaSuccess)
             return fail(SVM_ERR_OOM, "device allocation of X/y copy failed");
         if (cudaMemcpyAsync(W.X_own, prob->X, xbytes, cudaMemcpyHostToDevice, W.st) != cudaSuccess ||
@@ -252,16 +282,19 @@ extern "C" svm_status svm_ssnalm_create(svm_ssnalm_t **out, const svm_problem *p
         W.X = prob->X;
         W.y = prob->y;
     }
-    if ((uintptr_t)W.X % 16 != 0) return fail(SVM_ERR_INVALID_ARG, "X must be 16-byte aligned");
-    // double-float n-vectors wherever the mixed-form matvec applies (FP32 X, q % 4 == 0)
-    W.df = W.precision == SVM_PREC_MIXED && W.xf32 && q % 4 == 0;
+    if (!csr && (uintptr_t)W.X % 16 != 0) return fail(SVM_ERR_INVALID_ARG, "X must be 16-byte aligned");
+    // double-float n-vectors wherever the mixed-form matvec applies (dense FP32 X,
+    // q % 4 == 0); CSR runs the FP64 form
+    W.df = !csr && W.precision == SVM_PREC_MIXED && W.xf32 && q % 4 == 0;
     // workspace
     W.rm_grid = W.nsm * 4;
     // Gram split-K partials: at most 32 MiB (at least one q x q partial)
     size_t part_gram = (size_t)(4 * W.nsm) * (q * q + q);
     const size_t gram_cap = ((size_t)32 << 20) / sizeof(double);
     if (part_gram > gram_cap) part_gram = gram_cap > (q * q + q) ? gram_cap : (q * q + q);
-    const size_t part_rm = (size_t)2 * W.rm_grid * q;
+    size_t part_rm = (size_t)2 * W.rm_grid * q;
+    if (csr) part_gram = part_rm = 0;   // no dense Gram, no row-block partials
+    const size_t qq = csr ? 1 : q * q;   // the dense q x q Newton matrices
     const size_t part_proj = (size_t)3 * 8 * 4 * W.nsm * 4;
     W.part_len = part_gram > part_rm ? part_gram : part_rm;
     if (W.part_len < part_proj) W.part_len = part_proj;
@@ -272,7 +305,7 @@ extern "C" svm_status svm_ssnalm_create(svm_ssnalm_t **out, const svm_problem *p
                dalloc(&W.atpa, q) || dalloc(&W.atpa2, q) || dalloc(&W.vt, q) ||
                dalloc(&W.v, q) || dalloc(&W.dv, q) || dalloc(&W.g, q) ||
                dalloc(&W.atp, q) || dalloc(&W.atp2, q) || dalloc(&W.h, q) || dalloc(&W.w, q) || dalloc(&W.tmpq, q) ||
-               dalloc(&W.M, q * q) || dalloc(&W.Lf, q * (q + 1)) || dalloc(&W.Mf, q * q) || dalloc(&W.part, W.part_len) || dalloc(&W.bar, 4) || dalloc(&W.rm_counter, 4) || dalloc(&W.err, 4) ||
+               dalloc(&W.M, qq) || dalloc(&W.Lf, csr ? 1 : q * (q + 1)) || dalloc(&W.Mf, qq) || dalloc(&W.part, W.part_len) || dalloc(&W.bar, 4) || dalloc(&W.rm_counter, 4) || dalloc(&W.err, 4) ||
                dalloc(&W.pout, 4) || dalloc(&W.red, 16);
     for (int b = 0; b < 2 && !bad; ++b)
         bad = (W.df ? dalloc(&W.pb[b].uf, n) : dalloc(&W.pb[b].u, n)) || dalloc(&W.pb[b].pi, n) ||
@@ -297,15 +330,33 @@ extern "C" svm_status svm_ssnalm_create(svm_ssnalm_t **out, const svm_problem *p
     if (dalloc(&chk, 4)) return fail(SVM_ERR_OOM, "device allocation failed");
     cudaMemsetAsync(chk, 0, 4 * sizeof(int), W.st);
     check_labels_kernel<<<W.nsm * 2, 256, 0, W.st>>>(W.y, W.n, chk);
-    check_finite_kernel<<<W.nsm * 4, 256, 0, W.st>>>(W.X, W.xf32, (long long)(n * q), chk + 2);
+    int64_t ends[2] = {0, 0};
+    if (csr) {
+        // pointer ends, row structure and values (chk[2]: structure, chk[3]: non-finite)
+        cudaMemcpyAsync(&ends[0], W.csr_ptr, sizeof(int64_t), cudaMemcpyDeviceToHost, W.st);
+        cudaMemcpyAsync(&ends[1], W.csr_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, W.st);
+        e = cudaStreamSynchronize(W.st);
+        if (e == cudaSuccess && (ends[0] != 0 || ends[1] != W.nnz)) {
+            cudaFree(chk);
+            return fail(SVM_ERR_INVALID_ARG, "CSR: indptr[0] must be 0 and indptr[n] = nnz");
+        }
+        if (e == cudaSuccess) e = csr_validate(W, chk + 2);
+    } else {
+        check_finite_kernel<<<W.nsm * 4, 256, 0, W.st>>>(W.X, W.xf32, (long long)(n * q), chk + 2);
+    }
     int hchk[4] = {0, 0, 0, 0};
     cudaMemcpyAsync(hchk, chk, sizeof(hchk), cudaMemcpyDeviceToHost, W.st);
-    e = cudaStreamSynchronize(W.st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(W.st);
     cudaFree(chk);
     if (e != cudaSuccess) return fail(SVM_ERR_CUDA, std::string("create: ") + cudaGetErrorString(e));
     if (hchk[0]) return fail(SVM_ERR_INVALID_ARG, "labels must be +1 or -1");
-    if (hchk[2]) return fail(SVM_ERR_INVALID_ARG, "X has non-finite entries");
+    if (csr && hchk[2]) return fail(SVM_ERR_INVALID_ARG, "CSR: row pointers or column indices out of range, or columns not strictly increasing within a row");
+    if (csr ? hchk[3] : hchk[2]) return fail(SVM_ERR_INVALID_ARG, "X has non-finite entries");
     h->npos = hchk[1];
+    if (csr) {
+        e = csr_setup(W);
+        if (e != cudaSuccess) return fail(SVM_ERR_OOM, std::string("CSR setup: ") + cudaGetErrorString(e));
+    }
     {
         const char *tr = getenv("SVM_SSNALM_TRACE");
         h->trace = tr && tr[0] == '1';
@@ -817,7 +868,7 @@ extern "C" svm_status svm_ssnalm_solve_mlp(svm_ssnalm_t *h, svm_mlp_t *m, svm_re
     if (used_warm) *used_warm = 0;
     if (!h || !m || !res) return SVM_ERR_INVALID_ARG;
     Work &W = h->W;
-    if (!W.xf32 || W.q != SVM_MLP_IN - 4) {
+    if (W.csr || !W.xf32 || W.q != SVM_MLP_IN - 4) {
         h->err = "the warm-start network needs dense FP32 X with q = 128";
         return SVM_ERR_UNSUPPORTED;
     }
