@@ -100,6 +100,13 @@ struct Work {
     int64_t *task_beg = nullptr, *col_task = nullptr;
     double *task_part = nullptr;
     long long ntask = 0;
+    // the columns of the free set's rows, rebuilt for each Newton step
+    int64_t *jcsc_ptr = nullptr, *jtot = nullptr, *jcol_task = nullptr, *jtask_beg = nullptr;
+    int32_t *jcsc_row = nullptr;
+    void *jcsc_val = nullptr;
+    int *jcnt = nullptr;
+    double *jtask_part = nullptr;
+    long long jtask_cap = 0, jchunk_cap = 1;
     double *csr_tn = nullptr;   // n-vector: X_J d scattered to the rows of J
     double *csr_q = nullptr;    // 6 q-vectors of the CG
     CsrCg *csr_cg = nullptr;

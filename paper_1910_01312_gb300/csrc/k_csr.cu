@@ -17,9 +17,12 @@ namespace svm {
 
 // device state of the CSR Newton CG (Jacobi-preconditioned)
 struct CsrCg {
-    double rz, hp, tol2, rr;
+    double rz, hp, tol2, rr, alpha, beta;
     long long pc;
     int done, iters;
+    unsigned counter;   // last-block counter of the CG phase kernels (back to 0 after each)
+    int pad_;
+    double bpart[3 * 1024];   // block partials (at most 1024 blocks)
 };
 
 namespace {
@@ -63,12 +66,14 @@ __global__ void csr_check_kernel(const int64_t *__restrict__ rp, const int32_t *
 // counts column j in chunk c, then becomes the column's offset for that chunk,
 // and one warp per chunk places its rows in order (a row's columns are
 // distinct, so the lanes of a warp never touch the same counter at once).
-__global__ void csc_count_kernel(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci, long long n, int q,
-                                 long long rpc, int *__restrict__ cnt)
+__global__ void csc_count_kernel(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                 const int32_t *__restrict__ rows, long long n, int q, long long rpc,
+                                 int *__restrict__ cnt)
 {
     const int lane = threadIdx.x & 31;
-    for (long long i = gwarp(); i < n; i += nwarps()) {
-        const size_t c = (size_t)(i / rpc);
+    for (long long r = gwarp(); r < n; r += nwarps()) {
+        const long long i = rows ? (long long)rows[r] : r;
+        const size_t c = (size_t)(r / rpc);
         for (long long k = rp[i] + lane; k < rp[i + 1]; k += 32) atomicAdd(&cnt[c * q + ci[k]], 1);
     }
 }
@@ -112,14 +117,16 @@ __global__ void __launch_bounds__(1024) scan_kernel(long long m, const int64_t *
 
 template <typename TV>
 __global__ void csc_place_kernel(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
-                                 const TV *__restrict__ cv, long long n, int q, long long rpc, int R, int *cnt,
-                                 const int64_t *__restrict__ cp, int32_t *__restrict__ cr, TV *__restrict__ cvv)
+                                 const TV *__restrict__ cv, const int32_t *__restrict__ rows, long long n, int q,
+                                 long long rpc, int R, int *cnt, const int64_t *__restrict__ cp,
+                                 int32_t *__restrict__ cr, TV *__restrict__ cvv)
 {
     const int lane = threadIdx.x & 31;
     for (long long c = gwarp(); c < R; c += nwarps()) {
         const long long r0 = c * rpc, r1 = r0 + rpc < n ? r0 + rpc : n;
         volatile int *cc = cnt + (size_t)c * q;
-        for (long long i = r0; i < r1; ++i) {
+        for (long long r = r0; r < r1; ++r) {
+            const long long i = rows ? (long long)rows[r] : r;
             for (long long k = rp[i] + lane; k < rp[i + 1]; k += 32) {
                 const int j = ci[k];
                 const int o = cc[j];
@@ -131,6 +138,22 @@ __global__ void csc_place_kernel(const int64_t *__restrict__ rp, const int32_t *
             __syncwarp();
         }
     }
+}
+
+// tasks of at most kTaskLen entries per column: tc[j] = ceil(len_j / kTaskLen)
+__global__ void task_count_kernel(int q, const int64_t *__restrict__ cp, int64_t *__restrict__ tc)
+{
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < q; j += gridDim.x * blockDim.x)
+        tc[j] = (cp[j + 1] - cp[j] + kTaskLen - 1) / kTaskLen;
+}
+
+// tb[ct[j] + t] = cp[j] + t kTaskLen, and tb[ct[q]] = cp[q]
+__global__ void task_fill_kernel(int q, const int64_t *__restrict__ cp, const int64_t *__restrict__ ct,
+                                 int64_t *__restrict__ tb)
+{
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < q; j += gridDim.x * blockDim.x)
+        for (long long t = ct[j]; t < ct[j + 1]; ++t) tb[t] = cp[j] + (t - ct[j]) * kTaskLen;
+    if (blockIdx.x == 0 && threadIdx.x == 0) tb[ct[q]] = cp[q];
 }
 
 // --------------------------------------------------------- row products
@@ -176,16 +199,19 @@ __global__ void __launch_bounds__(256) csr_rows_kernel(const int64_t *__restrict
 
 // ------------------------------------------------------ column products
 // Task t sums the CSC entries [tb[t], tb[t+1]) of one column:
-//   MODE 0: part[t] = sum c_i y_i x_ij,  part[T + t] = sum |c_i| |x_ij|  (A'c and its roundoff scale)
-//   MODE 1: part[t] = sum c_i x_ij,      part[T + t] = sum c_i x_ij^2    (h and diag G for c = 1 on J)
+//   MODE 0: part[t] = sum c_i y_i x_ij,  part[cap + t] = sum |c_i| |x_ij|  (A'c and its roundoff scale)
+//   MODE 1: part[t] = sum c_i x_ij,      part[cap + t] = sum c_i x_ij^2    (h and diag G for c = 1 on J)
 //   MODE 2: part[t] = sum c_i x_ij                                       (X'c)
 template <typename TV, int MODE>
-__global__ void __launch_bounds__(256) csc_task_kernel(long long T, const int64_t *__restrict__ tb,
+// The task count is T, or *Tdev when Tdev is set (tasks built on the device).
+__global__ void __launch_bounds__(256) csc_task_kernel(long long T, const long long *__restrict__ Tdev, long long cap,
+                                                       const int64_t *__restrict__ tb,
                                                        const int32_t *__restrict__ cr, const TV *__restrict__ cvv,
                                                        const int8_t *__restrict__ y, const double *__restrict__ c,
                                                        double *__restrict__ part, const int *__restrict__ done)
 {
     if (done && *done) return;
+    if (Tdev) T = *Tdev;
     const int lane = threadIdx.x & 31;
     for (long long t = gwarp(); t < T; t += nwarps()) {
         double s = 0.0, a = 0.0;
@@ -207,36 +233,8 @@ __global__ void __launch_bounds__(256) csc_task_kernel(long long T, const int64_
         if (MODE != 2) a = warp_sum(a);
         if (lane == 0) {
             part[t] = s;
-            if (MODE != 2) part[T + t] = a;
+            if (MODE != 2) part[cap + t] = a;
         }
-    }
-}
-
-// out_j = sum of column j's task partials (in task order); with slot >= 0 also
-// red[slot] = sum_j (its abs-scale partials)^2.  One block of 1024 threads.
-__global__ void __launch_bounds__(1024) csc_final_kernel(int q, long long T, const int64_t *__restrict__ ct,
-                                                         const double *__restrict__ part, double *__restrict__ out,
-                                                         double *__restrict__ red, int slot)
-{
-    __shared__ double sh[32];
-    double sc = 0.0;
-    for (int j = threadIdx.x; j < q; j += 1024) {
-        double s = 0.0, a = 0.0;
-        for (long long t = ct[j]; t < ct[j + 1]; ++t) {
-            s += part[t];
-            a += part[T + t];
-        }
-        out[j] = s;
-        sc = fma(a, a, sc);
-    }
-    if (slot < 0) return;
-    sc = warp_sum(sc);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = sc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < 32; ++w) t += sh[w];
-        red[slot] = t;
     }
 }
 
@@ -258,22 +256,52 @@ __global__ void mark_kernel(long long p, const int32_t *__restrict__ J, double *
         tn[J[r]] = 1.0;
 }
 
+// Block partials of up to three sums; the last block to finish adds them in
+// block order (deterministic) and returns true with the totals in tot.
+template <int K>
+__device__ bool last_block_sums(double (&v)[K], double *sh, double *bpart, unsigned *counter, double (&tot)[K])
+{
+    __shared__ int is_last;
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = block_sum(v[k], sh);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) bpart[(size_t)k * gridDim.x + blockIdx.x] = v[k];
+        __threadfence();
+        is_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!is_last) return false;
+    __threadfence();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            double t = 0.0;
+            for (unsigned b = 0; b < gridDim.x; ++b) t += __ldcg(&bpart[(size_t)k * gridDim.x + b]);
+            tot[k] = t;
+        }
+        *counter = 0u;
+    }
+    return true;
+}
+
 // h, the Jacobi preconditioner 1/diag(M), x = 0, r = -g, z = Dinv r, d = z
-__global__ void __launch_bounds__(1024) cg_setup_kernel(int q, long long T, const int64_t *__restrict__ ct,
-                                                        const double *__restrict__ part, const double *__restrict__ g,
-                                                        double sigma, long long pc, double eta, double tau,
-                                                        CsrCg *st, double *__restrict__ h, double *__restrict__ dinv,
-                                                        double *__restrict__ x, double *__restrict__ r,
-                                                        double *__restrict__ z, double *__restrict__ d)
+__global__ void __launch_bounds__(256) cg_setup_kernel(int q, long long cap, const int64_t *__restrict__ ct,
+                                                       const double *__restrict__ part, const double *__restrict__ g,
+                                                       double sigma, long long pc, double eta, double tau,
+                                                       CsrCg *st, double *__restrict__ h, double *__restrict__ dinv,
+                                                       double *__restrict__ x, double *__restrict__ r,
+                                                       double *__restrict__ z, double *__restrict__ d,
+                                                       double *__restrict__ bpart, unsigned *__restrict__ counter)
 {
     __shared__ double sh[32];
     const double rp = 1.0 / (double)pc;
-    double rz = 0.0, hp = 0.0, gg = 0.0;
-    for (int j = threadIdx.x; j < q; j += 1024) {
+    double v[3] = {0.0, 0.0, 0.0};   // r'z, h'd, |g|^2
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < q; j += gridDim.x * blockDim.x) {
         double hj = 0.0, gjj = 0.0;
         for (long long t = ct[j]; t < ct[j + 1]; ++t) {
             hj += part[t];
-            gjj += part[T + t];
+            gjj += part[cap + t];
         }
         const double dj = 1.0 + sigma * (gjj - hj * hj * rp);
         const double di = dj > 0.0 ? 1.0 / dj : 1.0;
@@ -284,83 +312,125 @@ __global__ void __launch_bounds__(1024) cg_setup_kernel(int q, long long T, cons
         r[j] = rj;
         z[j] = zj;
         d[j] = zj;
-        rz = fma(rj, zj, rz);
-        hp = fma(hj, zj, hp);
-        gg = fma(rj, rj, gg);
+        v[0] = fma(rj, zj, v[0]);
+        v[1] = fma(hj, zj, v[1]);
+        v[2] = fma(rj, rj, v[2]);
     }
-    rz = block_sum(rz, sh);
-    hp = block_sum(hp, sh);
-    gg = block_sum(gg, sh);
-    if (threadIdx.x == 0) {
-        const double gn = sqrt(gg);
+    double tot[3];
+    if (last_block_sums<3>(v, sh, bpart, counter, tot) && threadIdx.x == 0) {
+        const double gn = sqrt(tot[2]);
         double tol = fmin(eta, pow(gn, 1.0 + tau));
         tol = fmin(tol, 1e-10 * gn);
-        st->rz = rz;
-        st->hp = hp;
+        st->rz = tot[0];
+        st->hp = tot[1];
         st->tol2 = tol * tol;
-        st->rr = gg;
+        st->rr = tot[2];
         st->pc = pc;
-        st->done = gg == 0.0;
+        st->done = tot[2] == 0.0;
         st->iters = 0;
     }
 }
 
-// One CG step after s = X_J'(X_J d) is in the task partials: M d = d + sigma (s - h (h'd)/p).
-__global__ void __launch_bounds__(1024) cg_step_kernel(int q, long long T, const int64_t *__restrict__ ct,
-                                                       const double *__restrict__ part, double sigma, int maxit,
-                                                       CsrCg *st, const double *__restrict__ h,
-                                                       const double *__restrict__ dinv, double *__restrict__ x,
-                                                       double *__restrict__ r, double *__restrict__ z,
-                                                       double *__restrict__ d, double *__restrict__ md)
+// One CG step in three launches once s = X_J'(X_J d) is in the task partials.
+// Phase 1: M d = d + sigma (s - h (h'd)/p), alpha = r'z / d'Md.
+__global__ void __launch_bounds__(256) cg_phase1_kernel(int q, const int64_t *__restrict__ ct,
+                                                        const double *__restrict__ part, double sigma, CsrCg *st,
+                                                        const double *__restrict__ h, const double *__restrict__ d,
+                                                        double *__restrict__ md, double *__restrict__ bpart,
+                                                        unsigned *__restrict__ counter)
 {
     __shared__ double sh[32];
-    __shared__ int stop;
     if (st->done) return;
     const double hpp = st->hp / (double)st->pc;
-    double dmd = 0.0;
-    for (int j = threadIdx.x; j < q; j += 1024) {
+    double v[1] = {0.0};
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < q; j += gridDim.x * blockDim.x) {
         double s = 0.0;
         for (long long t = ct[j]; t < ct[j + 1]; ++t) s += part[t];
-        const double mj = d[j] + sigma * (s - h[j] * hpp);
+        const double dj = d[j];
+        const double mj = dj + sigma * (s - h[j] * hpp);
         md[j] = mj;
-        dmd = fma(d[j], mj, dmd);
+        v[0] = fma(dj, mj, v[0]);
     }
-    dmd = block_sum(dmd, sh);
-    if (threadIdx.x == 0) stop = !(dmd > 0.0);
-    __syncthreads();
-    if (stop) {
-        if (threadIdx.x == 0) st->done = 2;
-        return;
+    double tot[1];
+    if (last_block_sums<1>(v, sh, bpart, counter, tot) && threadIdx.x == 0) {
+        if (tot[0] > 0.0) st->alpha = st->rz / tot[0];
+        else st->done = 2;   // no positive curvature: keep x
     }
-    const double a = st->rz / dmd;
-    double rz = 0.0, rr = 0.0;
-    for (int j = threadIdx.x; j < q; j += 1024) {
+}
+
+// Phase 2: x += alpha d, r -= alpha Md, z = Dinv r; stop test on |r|; beta.
+__global__ void __launch_bounds__(256) cg_phase2_kernel(int q, int maxit, CsrCg *st, const double *__restrict__ dinv,
+                                                        const double *__restrict__ d, const double *__restrict__ md,
+                                                        double *__restrict__ x, double *__restrict__ r,
+                                                        double *__restrict__ z, double *__restrict__ bpart,
+                                                        unsigned *__restrict__ counter)
+{
+    __shared__ double sh[32];
+    if (st->done) return;
+    const double a = st->alpha;
+    double v[2] = {0.0, 0.0};   // r'z, r'r
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < q; j += gridDim.x * blockDim.x) {
         x[j] = fma(a, d[j], x[j]);
         const double rj = fma(-a, md[j], r[j]);
         const double zj = dinv[j] * rj;
         r[j] = rj;
         z[j] = zj;
-        rz = fma(rj, zj, rz);
-        rr = fma(rj, rj, rr);
+        v[0] = fma(rj, zj, v[0]);
+        v[1] = fma(rj, rj, v[1]);
     }
-    rz = block_sum(rz, sh);
-    rr = block_sum(rr, sh);
-    const int it = st->iters + 1;
-    if (rr <= st->tol2 || it >= maxit) {
-        __syncthreads();
-        if (threadIdx.x == 0) { st->rr = rr; st->iters = it; st->done = 1; }
-        return;
+    double tot[2];
+    if (last_block_sums<2>(v, sh, bpart, counter, tot) && threadIdx.x == 0) {
+        const int it = st->iters + 1;
+        st->iters = it;
+        st->rr = tot[1];
+        if (tot[1] <= st->tol2 || it >= maxit) {
+            st->done = 1;
+        } else {
+            st->beta = tot[0] / st->rz;
+            st->rz = tot[0];
+        }
     }
-    const double b = rz / st->rz;
-    double hp = 0.0;
-    for (int j = threadIdx.x; j < q; j += 1024) {
+}
+
+// out_j = sum of column j's task partials (in task order); with slot >= 0 also
+// red[slot] = sum_j (its abs-scale partials)^2 (block partials, last block).
+__global__ void __launch_bounds__(256) csc_final_kernel(int q, long long cap, const int64_t *__restrict__ ct,
+                                                        const double *__restrict__ part, double *__restrict__ out,
+                                                        double *__restrict__ red, int slot, double *__restrict__ bpart,
+                                                        unsigned *__restrict__ counter)
+{
+    __shared__ double sh[32];
+    double v[1] = {0.0};
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < q; j += gridDim.x * blockDim.x) {
+        double s = 0.0, a = 0.0;
+        for (long long t = ct[j]; t < ct[j + 1]; ++t) {
+            s += part[t];
+            a += part[cap + t];
+        }
+        out[j] = s;
+        v[0] = fma(a, a, v[0]);
+    }
+    if (slot < 0) return;
+    double tot[1];
+    if (last_block_sums<1>(v, sh, bpart, counter, tot) && threadIdx.x == 0) red[slot] = tot[0];
+}
+
+// Phase 3: d = z + beta d and h'd.
+__global__ void __launch_bounds__(256) cg_phase3_kernel(int q, CsrCg *st, const double *__restrict__ h,
+                                                        const double *__restrict__ z, double *__restrict__ d,
+                                                        double *__restrict__ bpart, unsigned *__restrict__ counter)
+{
+    __shared__ double sh[32];
+    if (st->done) return;
+    const double b = st->beta;
+    double v[1] = {0.0};
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < q; j += gridDim.x * blockDim.x) {
         const double dj = fma(b, d[j], z[j]);
         d[j] = dj;
-        hp = fma(h[j], dj, hp);
+        v[0] = fma(h[j], dj, v[0]);
     }
-    hp = block_sum(hp, sh);
-    __syncthreads();
-    if (threadIdx.x == 0) { st->rz = rz; st->hp = hp; st->rr = rr; st->iters = it; }
+    double tot[1];
+    if (last_block_sums<1>(v, sh, bpart, counter, tot) && threadIdx.x == 0) st->hp = tot[0];
 }
 
 __global__ void cg_finish_kernel(int q, const CsrCg *st, const double *__restrict__ x, double *__restrict__ dv,
@@ -402,14 +472,36 @@ cudaError_t rows_launch(Work &W, long long nrows, const int32_t *rows, const dou
     return cudaGetLastError();
 }
 
-template <typename TV, int MODE>
-cudaError_t task_launch(Work &W, const double *c, const int *done)
+// A column view of X (the whole matrix, or the rows of a free set J): CSC
+// arrays, column tasks and their partial sums (second half at offset cap).
+struct ColSet {
+    const int32_t *row;
+    const void *val;
+    const int64_t *tb, *ct;
+    double *part;
+    long long T, cap;
+    const long long *Tdev;   // device task count (nullable: T)
+};
+
+ColSet full_cols(const Work &W)
 {
-    long long blocks = (W.ntask + 7) / 8;
+    return ColSet{W.csc_row, W.csc_val, W.task_beg, W.col_task, W.task_part, W.ntask, W.ntask, nullptr};
+}
+
+ColSet free_cols(const Work &W)
+{
+    return ColSet{W.jcsc_row, W.jcsc_val, W.jtask_beg, W.jcol_task, W.jtask_part, W.jtask_cap, W.jtask_cap,
+                  reinterpret_cast<const long long *>(W.jcol_task + W.q)};
+}
+
+template <typename TV, int MODE>
+cudaError_t task_launch(Work &W, const ColSet &cs, const double *c, const int *done)
+{
+    long long blocks = (cs.T + 7) / 8;
     if (blocks > (long long)W.nsm * 16) blocks = (long long)W.nsm * 16;
     if (blocks < 1) blocks = 1;
-    csc_task_kernel<TV, MODE><<<(unsigned)blocks, 256, 0, W.st>>>(W.ntask, W.task_beg, W.csc_row,
-                                                                  (const TV *)W.csc_val, W.y, c, W.task_part, done);
+    csc_task_kernel<TV, MODE><<<(unsigned)blocks, 256, 0, W.st>>>(cs.T, cs.Tdev, cs.cap, cs.tb, cs.row,
+                                                                  (const TV *)cs.val, W.y, c, cs.part, done);
     ++W.nlaunch;
     return cudaGetLastError();
 }
@@ -433,11 +525,12 @@ cudaError_t csc_build_t(Work &W)
     if ((e = cudaMalloc(&tot, sizeof(int64_t) * q)) != cudaSuccess) { cudaFree(cnt); return e; }
     cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)R * q, W.st);
     const TV *cv = (const TV *)W.csr_val;
-    csc_count_kernel<<<W.nsm * 8, 256, 0, W.st>>>(W.csr_ptr, W.csr_idx, n, q, rpc, cnt);
+    csc_count_kernel<<<W.nsm * 8, 256, 0, W.st>>>(W.csr_ptr, W.csr_idx, nullptr, n, q, rpc, cnt);
     csc_colscan_kernel<<<(q + 255) / 256, 256, 0, W.st>>>((int)R, q, cnt, tot);
     scan_kernel<<<1, 1024, 0, W.st>>>(q, tot, W.csc_ptr);
-    csc_place_kernel<TV><<<(unsigned)((R + 7) / 8), 256, 0, W.st>>>(W.csr_ptr, W.csr_idx, cv, n, q, rpc, (int)R, cnt,
-                                                                    W.csc_ptr, W.csc_row, (TV *)W.csc_val);
+    csc_place_kernel<TV><<<(unsigned)((R + 7) / 8), 256, 0, W.st>>>(W.csr_ptr, W.csr_idx, cv, nullptr, n, q, rpc,
+                                                                    (int)R, cnt, W.csc_ptr, W.csc_row,
+                                                                    (TV *)W.csc_val);
     W.nlaunch += 4;
     e = cudaGetLastError();
     // column tasks (host side, from the column pointers)
@@ -467,6 +560,34 @@ cudaError_t csc_build_t(Work &W)
     return cudaStreamSynchronize(W.st);   // the host vectors go out of scope
 }
 
+// Columns of the rows of J (ascending), built on the device: chunked counts,
+// column pointers, placement in row order, then column tasks.
+template <typename TV>
+cudaError_t free_cols_build(Work &W, const int32_t *J, long long p)
+{
+    const int q = (int)W.q;
+    long long R = p / 64;
+    if (R > W.jchunk_cap) R = W.jchunk_cap;
+    if (R < 1) R = 1;
+    const long long rpc = (p + R - 1) / R;
+    R = (p + rpc - 1) / rpc;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(W.jcnt, 0, sizeof(int) * (size_t)R * q, W.st)) != cudaSuccess) return e;
+    long long blocks = (p + 7) / 8;
+    if (blocks > (long long)W.nsm * 8) blocks = (long long)W.nsm * 8;
+    csc_count_kernel<<<(unsigned)blocks, 256, 0, W.st>>>(W.csr_ptr, W.csr_idx, J, p, q, rpc, W.jcnt);
+    csc_colscan_kernel<<<(q + 255) / 256, 256, 0, W.st>>>((int)R, q, W.jcnt, W.jtot);
+    scan_kernel<<<1, 1024, 0, W.st>>>(q, W.jtot, W.jcsc_ptr);
+    csc_place_kernel<TV><<<(unsigned)((R + 7) / 8), 256, 0, W.st>>>(W.csr_ptr, W.csr_idx, (const TV *)W.csr_val, J,
+                                                                    p, q, rpc, (int)R, W.jcnt, W.jcsc_ptr,
+                                                                    W.jcsc_row, (TV *)W.jcsc_val);
+    task_count_kernel<<<(q + 255) / 256, 256, 0, W.st>>>(q, W.jcsc_ptr, W.jtot);
+    scan_kernel<<<1, 1024, 0, W.st>>>(q, W.jtot, W.jcol_task);
+    task_fill_kernel<<<(q + 255) / 256, 256, 0, W.st>>>(q, W.jcsc_ptr, W.jcol_task, W.jtask_beg);
+    W.nlaunch += 7;
+    return cudaGetLastError();
+}
+
 template <typename TV>
 cudaError_t newton_csr_t(Work &W, const int32_t *J, long long p, double sigma, const double *g, double *dv, bool dots)
 {
@@ -475,22 +596,28 @@ cudaError_t newton_csr_t(Work &W, const int32_t *J, long long p, double sigma, c
     int *done = &st->done;
     double *tn = W.csr_tn;
     cudaError_t e;
+    if ((e = free_cols_build<TV>(W, J, p)) != cudaSuccess) return e;
+    const ColSet cs = free_cols(W);
     if ((e = cudaMemsetAsync(tn, 0, sizeof(double) * W.n, W.st)) != cudaSuccess) return e;
     mark_kernel<<<(unsigned)((p + 255) / 256 < 4096 ? (p + 255) / 256 : 4096), 256, 0, W.st>>>(p, J, tn);
     ++W.nlaunch;
-    if ((e = task_launch<TV, 1>(W, tn, nullptr)) != cudaSuccess) return e;
+    if ((e = task_launch<TV, 1>(W, cs, tn, nullptr)) != cudaSuccess) return e;
     double *x = W.csr_q, *r = x + q, *z = r + q, *d = z + q, *md = d + q, *dinv = md + q;
-    cg_setup_kernel<<<1, 1024, 0, W.st>>>(q, W.ntask, W.col_task, W.task_part, g, sigma, p, W.eta, W.tau, st, W.h,
-                                          dinv, x, r, z, d);
+    int G = (q + 255) / 256;
+    if (G > 2 * W.nsm) G = 2 * W.nsm;
+    if (G > 1024) G = 1024;
+    cg_setup_kernel<<<G, 256, 0, W.st>>>(q, cs.cap, cs.ct, cs.part, g, sigma, p, W.eta, W.tau, st, W.h, dinv, x, r, z,
+                                         d, st->bpart, &st->counter);
     ++W.nlaunch;
     const int maxit = W.csr_cg_maxit;
     for (int it = 0; it < maxit; it += kCgBatch) {
         for (int b = 0; b < kCgBatch; ++b) {
             if ((e = rows_launch<TV, 1, true, false>(W, p, J, d, nullptr, tn, nullptr, done)) != cudaSuccess) return e;
-            if ((e = task_launch<TV, 2>(W, tn, done)) != cudaSuccess) return e;
-            cg_step_kernel<<<1, 1024, 0, W.st>>>(q, W.ntask, W.col_task, W.task_part, sigma, maxit, st, W.h, dinv, x,
-                                                 r, z, d, md);
-            ++W.nlaunch;
+            if ((e = task_launch<TV, 2>(W, cs, tn, done)) != cudaSuccess) return e;
+            cg_phase1_kernel<<<G, 256, 0, W.st>>>(q, cs.ct, cs.part, sigma, st, W.h, d, md, st->bpart, &st->counter);
+            cg_phase2_kernel<<<G, 256, 0, W.st>>>(q, maxit, st, dinv, d, md, x, r, z, st->bpart, &st->counter);
+            cg_phase3_kernel<<<G, 256, 0, W.st>>>(q, st, W.h, z, d, st->bpart, &st->counter);
+            W.nlaunch += 3;
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if ((e = cudaMemcpyAsync(W.h_csr_done, done, sizeof(int), cudaMemcpyDeviceToHost, W.st)) != cudaSuccess) return e;
@@ -529,7 +656,21 @@ cudaError_t csr_setup(Work &W)
     if ((e = cudaMalloc(&W.csr_tn, sizeof(double) * W.n)) != cudaSuccess) return e;
     if ((e = cudaMalloc(&W.csr_q, sizeof(double) * 6 * W.q)) != cudaSuccess) return e;
     if ((e = cudaMalloc(&W.csr_cg, sizeof(CsrCg))) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(W.csr_cg, 0, sizeof(CsrCg), W.st)) != cudaSuccess) return e;
     if ((e = cudaMallocHost(&W.h_csr_done, sizeof(int))) != cudaSuccess) return e;
+    // the free set's columns (rebuilt for every Newton step): at most nnz entries
+    // and q + nnz / kTaskLen tasks; chunk counters for up to 256 chunks (64 MiB cap)
+    W.jtask_cap = W.q + (long long)(nz / kTaskLen) + 1;
+    long long jc = ((long long)16 << 20) / (W.q > 0 ? W.q : 1);
+    W.jchunk_cap = jc > 256 ? 256 : (jc < 1 ? 1 : jc);
+    if ((e = cudaMalloc(&W.jcsc_ptr, sizeof(int64_t) * (W.q + 1))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&W.jcsc_row, sizeof(int32_t) * nz)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&W.jcsc_val, es * nz)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&W.jtot, sizeof(int64_t) * W.q)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&W.jcnt, sizeof(int) * (size_t)W.jchunk_cap * W.q)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&W.jcol_task, sizeof(int64_t) * (W.q + 1))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&W.jtask_beg, sizeof(int64_t) * (W.jtask_cap + 1))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&W.jtask_part, sizeof(double) * 2 * W.jtask_cap)) != cudaSuccess) return e;
     return W.xf32 ? csc_build_t<float>(W) : csc_build_t<double>(W);
 }
 
@@ -544,9 +685,14 @@ cudaError_t launch_matvec_csr(Work &W, const double *v0, double *z0, const doubl
 
 cudaError_t launch_rmatvec_csr(Work &W, const double *c, double *out, int scale_slot)
 {
-    const cudaError_t e = W.xf32 ? task_launch<float, 0>(W, c, nullptr) : task_launch<double, 0>(W, c, nullptr);
+    const ColSet cs = full_cols(W);
+    const cudaError_t e = W.xf32 ? task_launch<float, 0>(W, cs, c, nullptr) : task_launch<double, 0>(W, cs, c, nullptr);
     if (e != cudaSuccess) return e;
-    csc_final_kernel<<<1, 1024, 0, W.st>>>((int)W.q, W.ntask, W.col_task, W.task_part, out, W.red, scale_slot);
+    int G = (int)((W.q + 255) / 256);
+    if (G > 2 * W.nsm) G = 2 * W.nsm;
+    if (G > 1024) G = 1024;
+    csc_final_kernel<<<G, 256, 0, W.st>>>((int)W.q, cs.cap, cs.ct, cs.part, out, W.red, scale_slot, W.csr_cg->bpart,
+                                          &W.csr_cg->counter);
     ++W.nlaunch;
     return cudaGetLastError();
 }

@@ -143,7 +143,8 @@ static void free_work(Work &W)
                     W.atpa2, W.mf_st, W.mf_pinv, W.mf_counter, W.v, W.vt, W.dv, W.g, W.atp, W.atp2, W.h, W.w, W.tmpq, W.M, W.Lf, W.Mf, W.part, W.cnt,
                     W.bar, W.rm_counter, W.err, W.pout, W.red, W.X_own, W.y_own, W.csc_ptr, W.csc_row,
                     W.csc_val, W.task_beg, W.col_task, W.task_part, W.csr_tn, W.csr_q, W.csr_cg,
-                    W.csr_ptr_own, W.csr_idx_own, W.csr_val_own};
+                    W.csr_ptr_own, W.csr_idx_own, W.csr_val_own, W.jcsc_ptr, W.jtot, W.jcol_task, W.jtask_beg,
+                    W.jcsc_row, W.jcsc_val, W.jcnt, W.jtask_part};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (int b = 0; b < 2; ++b) {

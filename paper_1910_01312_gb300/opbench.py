@@ -3,13 +3,18 @@
     python -m paper_1910_01312_gb300.opbench --op solve --n 400000
     python -m paper_1910_01312_gb300.opbench --op matvec --n 1000000 --reps 20
 
+    python -m paper_1910_01312_gb300.opbench --layout csr --op solve --n 700000 --q 47000
+
 Ops: ``solve`` (one cold solve after one warm-up, both forms of the stated
 precision), ``matvec`` (z = A v), ``rmatvec`` (A'c over all rows), ``project``
 (the projection at a random u), ``newton`` (the reduced Newton system on a
 random free set of size --p).  The data are the two-Gaussian workload of
-``datagen.gauss1m`` at the requested n and q.  Prints one JSON line with the
-mean time per call from CUDA events on the solver's stream.  Used for the
-profiles: a small case of the same kernels the solve runs.
+``datagen.gauss1m`` at the requested n and q, or with ``--layout csr`` the
+text-like sparse workload of ``datagen.sparse_text`` (--nnz-row entries per
+row).  Prints one JSON line with the mean time per call from CUDA events on
+the solver's stream (and, for the products, the algorithmic bytes per call
+and the rate they imply).  Used for the profiles: a small case of the same
+kernels the solve runs.
 """
 import argparse
 import json
@@ -26,6 +31,8 @@ def main(argv=None):
     ap.add_argument("--sigma", type=float, default=625.0)
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "plain"])
+    ap.add_argument("--layout", default="dense", choices=["dense", "csr"])
+    ap.add_argument("--nnz-row", type=int, default=75)
     args = ap.parse_args(argv)
 
     import torch
@@ -34,12 +41,24 @@ def main(argv=None):
     from . import binding as B
 
     B.load()
-    X, y, C = datagen.gauss1m(0, n=args.n, q=args.q)
-    n, q = X.shape
-    Xd, yd = torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda()
     stream = torch.cuda.current_stream()
     prec = B.PREC_MIXED if args.precision == "mixed" else B.PREC_PLAIN_FP64
-    s = B.Solver(Xd, yd, C_=C, tol=1e-6, precision=prec, stream=stream.cuda_stream)
+    if args.layout == "csr":
+        ip, ix, vals, y, C = datagen.sparse_text(0, n=args.n, q=args.q, nnz_row=args.nnz_row)
+        n, q, nnz = args.n, args.q, int(ix.size)
+        keep = [torch.from_numpy(a).cuda() for a in (ip, ix, vals, y)]
+        s = B.Solver(None, keep[3], C_=C, tol=1e-6, precision=prec, stream=stream.cuda_stream,
+                     csr=(keep[0], keep[1], keep[2], q))
+        # rows: values + indices + row pointers + label + FP64 output; columns: the same from the CSC copy
+        bytes_mv = nnz * 8 + (n + 1) * 8 + n + 8 * n
+        bytes_rmv = nnz * 8 + n * 9
+    else:
+        X, y, C = datagen.gauss1m(0, n=args.n, q=args.q)
+        n, q = X.shape
+        Xd, yd = torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda()
+        s = B.Solver(Xd, yd, C_=C, tol=1e-6, precision=prec, stream=stream.cuda_stream)
+        bytes_mv = n * q * 4 + n + 8 * n
+        bytes_rmv = n * q * 4 + n * 9
     rng = np.random.default_rng(0)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
@@ -72,8 +91,14 @@ def main(argv=None):
         out = call()
     e1.record(stream)
     torch.cuda.synchronize()
-    line = {"op": args.op, "n": n, "q": q, "precision": args.precision, "reps": args.reps,
-            "ms_per_call": e0.elapsed_time(e1) / args.reps}
+    ms = e0.elapsed_time(e1) / args.reps
+    line = {"op": args.op, "layout": args.layout, "n": n, "q": q, "precision": args.precision, "reps": args.reps,
+            "ms_per_call": ms}
+    if args.layout == "csr":
+        line["nnz"] = nnz
+    if args.op in ("matvec", "rmatvec"):
+        b = bytes_mv if args.op == "matvec" else bytes_rmv
+        line.update({"bytes_per_call": b, "GB_per_s": b / (ms * 1e-3) / 1e9})
     if args.op == "solve":
         line.update({"outer": out["outer_iters"], "inner": out["inner_iters_total"], "kkt": out["kkt"]})
     print(json.dumps(line), flush=True)
