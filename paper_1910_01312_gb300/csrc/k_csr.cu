@@ -172,17 +172,31 @@ __global__ void __launch_bounds__(256) csr_rows_kernel(const int64_t *__restrict
     const int lane = threadIdx.x & 31, sub = lane & (G - 1), grp = lane / G;
     for (long long base = gwarp() * RPW; base < nrows; base += nwarps() * RPW) {
         const long long r = base + grp;
-        double s0 = 0.0, s1 = 0.0;
+        // two accumulators per vector halve the dependent FMA chain
+        double s0 = 0.0, s1 = 0.0, t0 = 0.0, t1 = 0.0;
         long long i = 0;
         if (r < nrows) {
             i = ROWLIST ? (long long)rows[r] : r;
             const long long e = rp[i + 1];
-            for (long long k = rp[i] + sub; k < e; k += G) {
+            long long k = rp[i] + sub;
+            for (; k + G < e; k += 2 * G) {
+                const double xa = ldv(cv, k), xb = ldv(cv, k + G);
+                const int ja = ci[k], jb = ci[k + G];
+                s0 = fma(xa, __ldg(v0 + ja), s0);
+                t0 = fma(xb, __ldg(v0 + jb), t0);
+                if (NV == 2) {
+                    s1 = fma(xa, __ldg(v1 + ja), s1);
+                    t1 = fma(xb, __ldg(v1 + jb), t1);
+                }
+            }
+            if (k < e) {
                 const double x = ldv(cv, k);
                 const int j = ci[k];
                 s0 = fma(x, __ldg(v0 + j), s0);
                 if (NV == 2) s1 = fma(x, __ldg(v1 + j), s1);
             }
+            s0 += t0;
+            if (NV == 2) s1 += t1;
         }
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) {
@@ -214,14 +228,16 @@ __global__ void __launch_bounds__(256) csc_task_kernel(long long T, const long l
     if (Tdev) T = *Tdev;
     const int lane = threadIdx.x & 31;
     for (long long t = gwarp(); t < T; t += nwarps()) {
+        // MODE 0's abs scale is a roundoff estimate: FP32 is enough for it
         double s = 0.0, a = 0.0;
+        float af = 0.f;
         const long long e = tb[t + 1];
         for (long long k = tb[t] + lane; k < e; k += 32) {
             const int i = cr[k];
             const double x = ldv(cvv, k), ci = c[i];
             if (MODE == 0) {
                 s = fma(y[i] > 0 ? ci : -ci, x, s);
-                a = fma(fabs(ci), fabs(x), a);
+                af = fmaf(fabsf((float)ci), fabsf((float)x), af);
             } else if (MODE == 1) {
                 s = fma(ci, x, s);
                 a = fma(ci * x, x, a);
@@ -230,7 +246,8 @@ __global__ void __launch_bounds__(256) csc_task_kernel(long long T, const long l
             }
         }
         s = warp_sum(s);
-        if (MODE != 2) a = warp_sum(a);
+        if (MODE == 0) a = warp_sum((double)af);
+        else if (MODE == 1) a = warp_sum(a);
         if (lane == 0) {
             part[t] = s;
             if (MODE != 2) part[cap + t] = a;
@@ -443,10 +460,12 @@ __global__ void cg_finish_kernel(int q, const CsrCg *st, const double *__restric
     }
 }
 
+// Lanes per row: few enough that the FP64 shuffle reduction (log2 G adds per
+// lane) stays small against the row's own FMAs, and enough rows per warp.
 int row_group(const Work &W)
 {
     const double avg = W.n ? (double)W.nnz / (double)W.n : 0.0;
-    return avg <= 8.0 ? 4 : (avg <= 24.0 ? 8 : (avg <= 64.0 ? 16 : 32));
+    return avg <= 16.0 ? 4 : (avg <= 256.0 ? 8 : (avg <= 1024.0 ? 16 : 32));
 }
 
 template <typename TV, int NV, bool ROWLIST, bool USE_Y>
