@@ -108,6 +108,9 @@ struct Work {
     double *jtask_part = nullptr;
     long long jtask_cap = 0, jchunk_cap = 1;
     double *csr_tn = nullptr;   // n-vector: X_J d scattered to the rows of J
+    // mixed form (FP32 values): split q-vectors (2 inputs of A v; the CG's d),
+    // split y o c, and X_J d as double-float pairs
+    float2 *csr_vf = nullptr, *csr_df = nullptr, *csr_cf = nullptr, *csr_tnf = nullptr;
     double *csr_q = nullptr;    // 6 q-vectors of the CG
     CsrCg *csr_cg = nullptr;
     int *h_csr_done = nullptr;  // pinned

@@ -211,6 +211,73 @@ __global__ void __launch_bounds__(256) csr_rows_kernel(const int64_t *__restrict
     }
 }
 
+// Mixed form (FP32 values): the same products with FP32 arithmetic, Dot2 of
+// Ogita, Rump and Oishi (2005) against double-float (hi, lo) inputs: each
+// product x (hi + lo) is formed with TwoProd and accumulated with TwoSum, so
+// the row sums are as accurate as FP64 accumulation (~2^-48 of sum |terms|)
+// on the FP32 pipes, which this part runs 64 times faster than FP64.
+__global__ void split_q_kernel(int q, const double *__restrict__ v, float2 *__restrict__ vf)
+{
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < q; j += gridDim.x * blockDim.x) {
+        const double d = v[j];
+        const float h = (float)d;
+        vf[j] = make_float2(h, (float)(d - (double)h));
+    }
+}
+
+template <int G, int NV, bool ROWLIST, bool USE_Y, bool OUTDF>
+__global__ void __launch_bounds__(256) csr_rows_df_kernel(const int64_t *__restrict__ rp,
+                                                          const int32_t *__restrict__ ci, const float *__restrict__ cv,
+                                                          const int8_t *__restrict__ y, long long nrows,
+                                                          const int32_t *__restrict__ rows,
+                                                          const float2 *__restrict__ v0, const float2 *__restrict__ v1,
+                                                          void *__restrict__ z0, void *__restrict__ z1,
+                                                          const int *__restrict__ done)
+{
+    if (done && *done) return;
+    constexpr int RPW = 32 / G;
+    const int lane = threadIdx.x & 31, sub = lane & (G - 1), grp = lane / G;
+    for (long long base = gwarp() * RPW; base < nrows; base += nwarps() * RPW) {
+        const long long r = base + grp;
+        float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
+        long long i = 0;
+        if (r < nrows) {
+            i = ROWLIST ? (long long)rows[r] : r;
+            const long long e = rp[i + 1];
+            for (long long k = rp[i] + sub; k < e; k += G) {
+                const float x = cv[k];
+                const int j = ci[k];
+                dot2_step(x, __ldg(v0 + j), s0, c0);
+                if (NV == 2) dot2_step(x, __ldg(v1 + j), s1, c1);
+            }
+        }
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+            const float a = __shfl_xor_sync(0xffffffffu, s0, o), b = __shfl_xor_sync(0xffffffffu, c0, o);
+            df_acc(s0, c0, a, b);
+            if (NV == 2) {
+                const float a1 = __shfl_xor_sync(0xffffffffu, s1, o), b1 = __shfl_xor_sync(0xffffffffu, c1, o);
+                df_acc(s1, c1, a1, b1);
+            }
+        }
+        if (sub == 0 && r < nrows) {
+            const bool neg = USE_Y && y[i] < 0;
+            if (OUTDF) {
+                float hi, lo;
+                two_sum(s0, c0, hi, lo);
+                reinterpret_cast<float2 *>(z0)[i] = neg ? make_float2(-hi, -lo) : make_float2(hi, lo);
+            } else {
+                const double d0 = (double)s0 + (double)c0;
+                reinterpret_cast<double *>(z0)[i] = neg ? -d0 : d0;
+                if (NV == 2) {
+                    const double d1 = (double)s1 + (double)c1;
+                    reinterpret_cast<double *>(z1)[i] = neg ? -d1 : d1;
+                }
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------ column products
 // Task t sums the CSC entries [tb[t], tb[t+1]) of one column:
 //   MODE 0: part[t] = sum c_i y_i x_ij,  part[cap + t] = sum |c_i| |x_ij|  (A'c and its roundoff scale)
@@ -251,6 +318,42 @@ __global__ void __launch_bounds__(256) csc_task_kernel(long long T, const long l
         if (lane == 0) {
             part[t] = s;
             if (MODE != 2) part[cap + t] = a;
+        }
+    }
+}
+
+// Mixed form of the column products (FP32 values, double-float weights w):
+//   MODE 0: part[t] = sum w_i x_ij (w = y o c split), part[cap + t] = sum |w_i| |x_ij| (FP32)
+//   MODE 2: part[t] = sum w_i x_ij
+template <int MODE>
+__global__ void __launch_bounds__(256) csc_task_df_kernel(long long T, const long long *__restrict__ Tdev,
+                                                          long long cap, const int64_t *__restrict__ tb,
+                                                          const int32_t *__restrict__ cr,
+                                                          const float *__restrict__ cvv,
+                                                          const float2 *__restrict__ w, double *__restrict__ part,
+                                                          const int *__restrict__ done)
+{
+    if (done && *done) return;
+    if (Tdev) T = *Tdev;
+    const int lane = threadIdx.x & 31;
+    for (long long t = gwarp(); t < T; t += nwarps()) {
+        float s = 0.f, c = 0.f, af = 0.f;
+        const long long e = tb[t + 1];
+        for (long long k = tb[t] + lane; k < e; k += 32) {
+            const float x = cvv[k];
+            const float2 wi = w[cr[k]];
+            dot2_step(x, wi, s, c);
+            if (MODE == 0) af = fmaf(fabsf(wi.x), fabsf(x), af);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float a = __shfl_xor_sync(0xffffffffu, s, o), b = __shfl_xor_sync(0xffffffffu, c, o);
+            df_acc(s, c, a, b);
+            if (MODE == 0) af += __shfl_xor_sync(0xffffffffu, af, o);
+        }
+        if (lane == 0) {
+            part[t] = (double)s + (double)c;
+            if (MODE == 0) part[cap + t] = (double)af;
         }
     }
 }
@@ -309,7 +412,8 @@ __global__ void __launch_bounds__(256) cg_setup_kernel(int q, long long cap, con
                                                        CsrCg *st, double *__restrict__ h, double *__restrict__ dinv,
                                                        double *__restrict__ x, double *__restrict__ r,
                                                        double *__restrict__ z, double *__restrict__ d,
-                                                       double *__restrict__ bpart, unsigned *__restrict__ counter)
+                                                       float2 *__restrict__ dsplit, double *__restrict__ bpart,
+                                                       unsigned *__restrict__ counter)
 {
     __shared__ double sh[32];
     const double rp = 1.0 / (double)pc;
@@ -329,6 +433,10 @@ __global__ void __launch_bounds__(256) cg_setup_kernel(int q, long long cap, con
         r[j] = rj;
         z[j] = zj;
         d[j] = zj;
+        if (dsplit) {
+            const float hz = (float)zj;
+            dsplit[j] = make_float2(hz, (float)(zj - (double)hz));
+        }
         v[0] = fma(rj, zj, v[0]);
         v[1] = fma(hj, zj, v[1]);
         v[2] = fma(rj, rj, v[2]);
@@ -435,7 +543,8 @@ __global__ void __launch_bounds__(256) csc_final_kernel(int q, long long cap, co
 // Phase 3: d = z + beta d and h'd.
 __global__ void __launch_bounds__(256) cg_phase3_kernel(int q, CsrCg *st, const double *__restrict__ h,
                                                         const double *__restrict__ z, double *__restrict__ d,
-                                                        double *__restrict__ bpart, unsigned *__restrict__ counter)
+                                                        float2 *__restrict__ dsplit, double *__restrict__ bpart,
+                                                        unsigned *__restrict__ counter)
 {
     __shared__ double sh[32];
     if (st->done) return;
@@ -444,6 +553,10 @@ __global__ void __launch_bounds__(256) cg_phase3_kernel(int q, CsrCg *st, const 
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < q; j += gridDim.x * blockDim.x) {
         const double dj = fma(b, d[j], z[j]);
         d[j] = dj;
+        if (dsplit) {
+            const float hd = (float)dj;
+            dsplit[j] = make_float2(hd, (float)(dj - (double)hd));
+        }
         v[0] = fma(h[j], dj, v[0]);
     }
     double tot[1];
@@ -521,6 +634,53 @@ cudaError_t task_launch(Work &W, const ColSet &cs, const double *c, const int *d
     if (blocks < 1) blocks = 1;
     csc_task_kernel<TV, MODE><<<(unsigned)blocks, 256, 0, W.st>>>(cs.T, cs.Tdev, cs.cap, cs.tb, cs.row,
                                                                   (const TV *)cs.val, W.y, c, cs.part, done);
+    ++W.nlaunch;
+    return cudaGetLastError();
+}
+
+bool mixed_csr(const Work &W) { return W.precision == 1 && W.xf32; }
+
+template <int NV, bool ROWLIST, bool USE_Y, bool OUTDF>
+cudaError_t rows_df_launch(Work &W, long long nrows, const int32_t *rows, const float2 *v0, const float2 *v1, void *z0,
+                           void *z1, const int *done)
+{
+    const int G = row_group(W);
+    const long long warps = (nrows * G + 31) / 32;
+    long long blocks = (warps + 7) / 8;
+    if (blocks > (long long)W.nsm * 16) blocks = (long long)W.nsm * 16;
+    if (blocks < 1) blocks = 1;
+    const float *cv = (const float *)W.csr_val;
+#define RD_CASE(g)                                                                                              \
+    case g:                                                                                                     \
+        csr_rows_df_kernel<g, NV, ROWLIST, USE_Y, OUTDF><<<(unsigned)blocks, 256, 0, W.st>>>(                   \
+            W.csr_ptr, W.csr_idx, cv, W.y, nrows, rows, v0, v1, z0, z1, done);                                  \
+        break;
+    switch (G) {
+        RD_CASE(4) RD_CASE(8) RD_CASE(16) RD_CASE(32)
+    }
+#undef RD_CASE
+    ++W.nlaunch;
+    return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t task_df_launch(Work &W, const ColSet &cs, const float2 *w, const int *done)
+{
+    long long blocks = (cs.T + 7) / 8;
+    if (blocks > (long long)W.nsm * 16) blocks = (long long)W.nsm * 16;
+    if (blocks < 1) blocks = 1;
+    csc_task_df_kernel<MODE><<<(unsigned)blocks, 256, 0, W.st>>>(cs.T, cs.Tdev, cs.cap, cs.tb, cs.row,
+                                                                 (const float *)cs.val, w, cs.part, done);
+    ++W.nlaunch;
+    return cudaGetLastError();
+}
+
+cudaError_t split_q(Work &W, const double *v, float2 *vf)
+{
+    const int q = (int)W.q;
+    int blocks = (q + 255) / 256;
+    if (blocks > W.nsm * 4) blocks = W.nsm * 4;
+    split_q_kernel<<<blocks, 256, 0, W.st>>>(q, v, vf);
     ++W.nlaunch;
     return cudaGetLastError();
 }
@@ -625,17 +785,30 @@ cudaError_t newton_csr_t(Work &W, const int32_t *J, long long p, double sigma, c
     int G = (q + 255) / 256;
     if (G > 2 * W.nsm) G = 2 * W.nsm;
     if (G > 1024) G = 1024;
+    // mixed form: the CG's two products run in Dot2 on the split of d, with
+    // X_J d kept as double-float pairs (zero outside J)
+    const bool mx = mixed_csr(W);
+    float2 *dsp = mx ? W.csr_df : nullptr;
+    if (mx && (e = cudaMemsetAsync(W.csr_tnf, 0, sizeof(float2) * W.n, W.st)) != cudaSuccess) return e;
     cg_setup_kernel<<<G, 256, 0, W.st>>>(q, cs.cap, cs.ct, cs.part, g, sigma, p, W.eta, W.tau, st, W.h, dinv, x, r, z,
-                                         d, st->bpart, &st->counter);
+                                         d, dsp, st->bpart, &st->counter);
     ++W.nlaunch;
     const int maxit = W.csr_cg_maxit;
     for (int it = 0; it < maxit; it += kCgBatch) {
         for (int b = 0; b < kCgBatch; ++b) {
-            if ((e = rows_launch<TV, 1, true, false>(W, p, J, d, nullptr, tn, nullptr, done)) != cudaSuccess) return e;
-            if ((e = task_launch<TV, 2>(W, cs, tn, done)) != cudaSuccess) return e;
+            if (mx) {
+                if ((e = rows_df_launch<1, true, false, true>(W, p, J, dsp, nullptr, W.csr_tnf, nullptr, done)) !=
+                    cudaSuccess)
+                    return e;
+                if ((e = task_df_launch<2>(W, cs, W.csr_tnf, done)) != cudaSuccess) return e;
+            } else {
+                if ((e = rows_launch<TV, 1, true, false>(W, p, J, d, nullptr, tn, nullptr, done)) != cudaSuccess)
+                    return e;
+                if ((e = task_launch<TV, 2>(W, cs, tn, done)) != cudaSuccess) return e;
+            }
             cg_phase1_kernel<<<G, 256, 0, W.st>>>(q, cs.ct, cs.part, sigma, st, W.h, d, md, st->bpart, &st->counter);
             cg_phase2_kernel<<<G, 256, 0, W.st>>>(q, maxit, st, dinv, d, md, x, r, z, st->bpart, &st->counter);
-            cg_phase3_kernel<<<G, 256, 0, W.st>>>(q, st, W.h, z, d, st->bpart, &st->counter);
+            cg_phase3_kernel<<<G, 256, 0, W.st>>>(q, st, W.h, z, d, dsp, st->bpart, &st->counter);
             W.nlaunch += 3;
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -675,6 +848,12 @@ cudaError_t csr_setup(Work &W)
     if ((e = cudaMalloc(&W.csr_tn, sizeof(double) * W.n)) != cudaSuccess) return e;
     if ((e = cudaMalloc(&W.csr_q, sizeof(double) * 6 * W.q)) != cudaSuccess) return e;
     if ((e = cudaMalloc(&W.csr_cg, sizeof(CsrCg))) != cudaSuccess) return e;
+    if (mixed_csr(W)) {
+        if ((e = cudaMalloc(&W.csr_vf, sizeof(float2) * 2 * W.q)) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&W.csr_df, sizeof(float2) * W.q)) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&W.csr_cf, sizeof(float2) * W.n)) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&W.csr_tnf, sizeof(float2) * W.n)) != cudaSuccess) return e;
+    }
     if ((e = cudaMemsetAsync(W.csr_cg, 0, sizeof(CsrCg), W.st)) != cudaSuccess) return e;
     if ((e = cudaMallocHost(&W.h_csr_done, sizeof(int))) != cudaSuccess) return e;
     // the free set's columns (rebuilt for every Newton step): at most nnz entries
@@ -695,6 +874,14 @@ cudaError_t csr_setup(Work &W)
 
 cudaError_t launch_matvec_csr(Work &W, const double *v0, double *z0, const double *v1, double *z1)
 {
+    if (mixed_csr(W)) {
+        float2 *f0 = W.csr_vf, *f1 = W.csr_vf + W.q;
+        cudaError_t e = split_q(W, v0, f0);
+        if (e == cudaSuccess && v1) e = split_q(W, v1, f1);
+        if (e != cudaSuccess) return e;
+        return v1 ? rows_df_launch<2, false, true, false>(W, W.n, nullptr, f0, f1, z0, z1, nullptr)
+                  : rows_df_launch<1, false, true, false>(W, W.n, nullptr, f0, nullptr, z0, nullptr, nullptr);
+    }
     if (W.xf32)
         return v1 ? rows_launch<float, 2, false, true>(W, W.n, nullptr, v0, v1, z0, z1, nullptr)
                   : rows_launch<float, 1, false, true>(W, W.n, nullptr, v0, nullptr, z0, nullptr, nullptr);
@@ -705,7 +892,13 @@ cudaError_t launch_matvec_csr(Work &W, const double *v0, double *z0, const doubl
 cudaError_t launch_rmatvec_csr(Work &W, const double *c, double *out, int scale_slot)
 {
     const ColSet cs = full_cols(W);
-    const cudaError_t e = W.xf32 ? task_launch<float, 0>(W, cs, c, nullptr) : task_launch<double, 0>(W, cs, c, nullptr);
+    cudaError_t e;
+    if (mixed_csr(W)) {
+        e = split_weights(W, c, W.csr_cf);   // y o c as double-float pairs
+        if (e == cudaSuccess) e = task_df_launch<0>(W, cs, W.csr_cf, nullptr);
+    } else {
+        e = W.xf32 ? task_launch<float, 0>(W, cs, c, nullptr) : task_launch<double, 0>(W, cs, c, nullptr);
+    }
     if (e != cudaSuccess) return e;
     int G = (int)((W.q + 255) / 256);
     if (G > 2 * W.nsm) G = 2 * W.nsm;

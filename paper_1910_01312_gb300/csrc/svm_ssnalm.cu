@@ -144,7 +144,7 @@ static void free_work(Work &W)
                     W.bar, W.rm_counter, W.err, W.pout, W.red, W.X_own, W.y_own, W.csc_ptr, W.csc_row,
                     W.csc_val, W.task_beg, W.col_task, W.task_part, W.csr_tn, W.csr_q, W.csr_cg,
                     W.csr_ptr_own, W.csr_idx_own, W.csr_val_own, W.jcsc_ptr, W.jtot, W.jcol_task, W.jtask_beg,
-                    W.jcsc_row, W.jcsc_val, W.jcnt, W.jtask_part};
+                    W.jcsc_row, W.jcsc_val, W.jcnt, W.jtask_part, W.csr_vf, W.csr_df, W.csr_cf, W.csr_tnf};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (int b = 0; b < 2; ++b) {
