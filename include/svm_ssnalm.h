@@ -185,6 +185,16 @@ svm_status svm_op_project(svm_ssnalm_t *h, const double *u, double *pi, double *
 svm_status svm_op_newton(svm_ssnalm_t *h, const int32_t *J, int64_t p, double sigma,
                          const double *g, double *dv);
 
+/* Gram of the free rows as the large-free-set Newton step builds its
+ * preconditioner (Proposition 3.5: the reduced matrix I + sigma (G - h h'/p)):
+ * G = X_J' X_J (q x q, row-major FP64, device) and hsum = X_J' 1 (q, FP64,
+ * device), J device int32 with p row indices (any order; p = 0 gives zeros).
+ * G is formed on the tcgen05 tensor cores with TF32 products (10-bit
+ * mantissa) and FP32 sums within a block, blocks added in FP64; hsum is exact
+ * to double-float accuracy.  Dense FP32 X with q % 16 == 0 and q <= 128 only
+ * (else SVM_ERR_UNSUPPORTED).  Synchronises the stream. */
+svm_status svm_op_gram(svm_ssnalm_t *h, const int32_t *J, int64_t p, double *G, double *hsum);
+
 /* Relative KKT residual of eq. (4.1) at alpha (n, device).  *kkt and *lambda
  * (multiplier of the projection in the residual) are host outputs. */
 svm_status svm_op_kkt(svm_ssnalm_t *h, const double *alpha, double *kkt, double *lambda);

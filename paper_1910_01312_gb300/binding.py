@@ -52,7 +52,7 @@ class Stats(C.Structure):
 
 SYMBOLS = ["svm_default_params", "svm_ssnalm_create", "svm_ssnalm_solve", "svm_ssnalm_destroy",
            "svm_ssnalm_last_error", "svm_op_matvec", "svm_op_rmatvec", "svm_op_project",
-           "svm_op_newton", "svm_op_kkt", "svm_ssnalm_set_timing", "svm_ssnalm_get_stats",
+           "svm_op_newton", "svm_op_kkt", "svm_op_gram", "svm_ssnalm_set_timing", "svm_ssnalm_get_stats",
            "svm_rmatvec_noalloc", "svm_mlp_create", "svm_mlp_destroy", "svm_mlp_get_params",
            "svm_mlp_features", "svm_mlp_labels", "svm_mlp_gather", "svm_mlp_forward", "svm_mlp_loss_grad", "svm_mlp_adam_step",
            "svm_mlp_train_step", "svm_mlp_start_point", "svm_ssnalm_solve_mlp"]
@@ -94,6 +94,7 @@ def load(build_if_missing: bool = False):
                                      C.POINTER(i64)]
         L.svm_op_newton.argtypes = [vp, vp, i64, C.c_double, vp, vp]
         L.svm_op_kkt.argtypes = [vp, vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        L.svm_op_gram.argtypes = [vp, vp, i64, vp, vp]
         L.svm_ssnalm_set_timing.argtypes = [vp, C.c_int]
         L.svm_ssnalm_get_stats.argtypes = [vp, C.POINTER(Stats), C.c_int]
         L.svm_rmatvec_noalloc.argtypes = [vp, vp, i64, i64, vp, vp, vp]
@@ -111,7 +112,7 @@ def load(build_if_missing: bool = False):
         L.svm_mlp_train_step.argtypes = [vp, vp, vp, i64, vp, i64, f32, f32, vp]
         L.svm_mlp_start_point.argtypes = [vp, vp, i64, dbl, vp]
         L.svm_ssnalm_solve_mlp.argtypes = [vp, vp, C.POINTER(Result), C.POINTER(C.c_int32)]
-        for f in ("svm_op_matvec", "svm_op_rmatvec", "svm_op_project", "svm_op_newton", "svm_op_kkt",
+        for f in ("svm_op_matvec", "svm_op_rmatvec", "svm_op_project", "svm_op_newton", "svm_op_kkt", "svm_op_gram",
                   "svm_ssnalm_set_timing", "svm_ssnalm_get_stats", "svm_rmatvec_noalloc", "svm_mlp_create",
                   "svm_mlp_get_params", "svm_mlp_features", "svm_mlp_labels", "svm_mlp_gather", "svm_mlp_forward",
                   "svm_mlp_loss_grad",
@@ -264,6 +265,10 @@ class Solver:
 
     def newton(self, J, p, sigma, g, dv):
         self._check(self._lib.svm_op_newton(self.h, _ptr(J), int(p), float(sigma), _ptr(g), _ptr(dv)))
+
+    def gram(self, J, p, G, hsum):
+        """G = X_J' X_J (tcgen05 tensor cores, TF32 products) and hsum = X_J' 1."""
+        self._check(self._lib.svm_op_gram(self.h, _ptr(J), int(p), _ptr(G), _ptr(hsum)))
 
     def kkt(self, alpha):
         r, lam = C.c_double(0.0), C.c_double(0.0)

@@ -220,6 +220,15 @@ cudaError_t launch_newton(Work &W, const int32_t *J, long long p_host, const lon
                           double sigma, const double *g, double *dv, bool dots = false);
 // workspace of the large-free-set Newton solve (mixed form, FP32 X, q <= 128)
 cudaError_t newton_mf_alloc(Work &W);
+// Gram of the rows J on the tcgen05 tensor cores (k_umma.cu): per block b of
+// gram_umma_blocks(W), cpart[b] = X_S' X_S (q x q FP32, TF32 products) and
+// hpart[b] = X_S' 1 (double-float); dense FP32 X, q % 16 == 0, q <= 128.
+// The partials need gram_umma_part_floats(W) floats.
+int gram_umma_blocks(const Work &W);
+size_t gram_umma_part_floats(const Work &W);
+cudaError_t launch_gram_umma(Work &W, const int32_t *J, long long p, float *cpart, float2 *hpart);
+// G = sum_b cpart[b], h = sum_b hpart[b] in FP64 (block order)
+cudaError_t launch_gram_umma_sum(Work &W, const float *cpart, const float2 *hpart, double *G, double *h);
 
 // CSR layout: structure/value checks (dev_flags[0]: structure, [1]: non-finite),
 // the CSC copy and column tasks, and the three products of the method

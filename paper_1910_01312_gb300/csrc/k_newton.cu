@@ -1290,123 +1290,6 @@ __global__ void __launch_bounds__(kMfThreads) newton_mf_pass_kernel(
     }
 }
 
-// ---------------------------------------------------------------------------
-// Tensor-core Gram for the preconditioner of the large-free-set solve:
-// per block, C_b = X_S' X_S over its share S of the rows of J with TF32
-// products and FP32 sums (mma.sync m16n8k8), and the double-float column sums
-// h_b.  The CG operator stays exact (double-float, matrix-free), so the
-// Gram's TF32 rounding only sets how fast CG converges.  q % 16 == 0,
-// q <= 128: warp w owns rows 16w..16w+15 of C and all its columns.
-constexpr int kTcStage = 64;    // rows staged in shared memory per step
-constexpr int kTcLd = 136;      // staged row stride (floats): conflict-free fragment loads
-
-__device__ __forceinline__ unsigned to_tf32(float x)
-{
-    unsigned u;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
-    return u;
-}
-
-__global__ void __launch_bounds__(256) gram_tc_kernel(const float *__restrict__ X, int q, const int32_t *__restrict__ J,
-                                                      long long p, float *__restrict__ cpart, float2 *__restrict__ hpart)
-{
-    __shared__ __align__(16) float T[kTcStage * kTcLd];
-    __shared__ float2 hsm[8][kCgMaxQ];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int gid = lane >> 2, tig = lane & 3;
-    const int G = gridDim.x;
-    const long long per = (p + G - 1) / G;
-    const long long r0 = (long long)blockIdx.x * per;
-    const long long r1 = r0 + per < p ? r0 + per : p;
-    const int nq4 = q / 4, ntn = q / 8;
-    const bool mrow = 16 * warp < q;
-    float acc[kCgMaxQ / 8][4];
-#pragma unroll
-    for (int j = 0; j < kCgMaxQ / 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-    // column sums: thread handles the float4 column group c4 = tid % 32 of its rows
-    float hs[4] = {0.f, 0.f, 0.f, 0.f}, hc[4] = {0.f, 0.f, 0.f, 0.f};
-    __shared__ int jrow[kTcStage];
-    for (long long rb = r0; rb < r1; rb += kTcStage) {
-        // the stage's row indices first, then every row load of a thread in flight at once
-        if (threadIdx.x < kTcStage) jrow[threadIdx.x] = (rb + threadIdx.x < r1) ? J[rb + threadIdx.x] : -1;
-        __syncthreads();
-        constexpr int kPer = kTcStage * 32 / 256;
-        float4 v[kPer];
-#pragma unroll
-        for (int u = 0; u < kPer; ++u) {
-            const int e = threadIdx.x + 256 * u, rr = e >> 5, c4 = e & 31;
-            const int jr = jrow[rr];
-            v[u] = (jr >= 0 && c4 < nq4) ? __ldcs(reinterpret_cast<const float4 *>(X + (long long)jr * q) + c4)
-                                         : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-#pragma unroll
-        for (int u = 0; u < kPer; ++u) {
-            const int e = threadIdx.x + 256 * u, rr = e >> 5, c4 = e & 31;
-            *reinterpret_cast<float4 *>(&T[rr * kTcLd + 4 * c4]) = v[u];
-            const float xs[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                float sn, er;
-                two_sum(hs[k], xs[k], sn, er);
-                hs[k] = sn;
-                hc[k] += er;
-            }
-        }
-        __syncthreads();
-        if (mrow) {
-            const int m0 = 16 * warp;
-            for (int ks = 0; ks < kTcStage; ks += 8) {
-                const float *t0 = &T[(ks + tig) * kTcLd], *t4 = &T[(ks + tig + 4) * kTcLd];
-                const unsigned a0 = to_tf32(t0[m0 + gid]), a1 = to_tf32(t0[m0 + gid + 8]);
-                const unsigned a2 = to_tf32(t4[m0 + gid]), a3 = to_tf32(t4[m0 + gid + 8]);
-#pragma unroll
-                for (int j = 0; j < kCgMaxQ / 8; ++j) {
-                    if (j < ntn) {
-                        const unsigned b0 = to_tf32(t0[8 * j + gid]), b1 = to_tf32(t4[8 * j + gid]);
-                        asm volatile(
-                            "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-                            "{%8,%9}, {%0,%1,%2,%3};"
-                            : "+f"(acc[j][0]), "+f"(acc[j][1]), "+f"(acc[j][2]), "+f"(acc[j][3])
-                            : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-                    }
-                }
-            }
-        }
-        __syncthreads();
-    }
-    float *C = cpart + (size_t)blockIdx.x * q * q;
-    if (mrow) {
-        const int m = 16 * warp + gid;
-#pragma unroll
-        for (int j = 0; j < kCgMaxQ / 8; ++j) {
-            if (j < ntn) {
-                const int n = 8 * j + 2 * tig;
-                C[(size_t)m * q + n] = acc[j][0];
-                C[(size_t)m * q + n + 1] = acc[j][1];
-                C[(size_t)(m + 8) * q + n] = acc[j][2];
-                C[(size_t)(m + 8) * q + n + 1] = acc[j][3];
-            }
-        }
-    }
-    // column sums: the 8 threads of a column group in warp order
-    {
-        const int c4 = threadIdx.x & 31, w = threadIdx.x >> 5;
-        if (c4 < nq4)
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                float hi, lo;
-                two_sum(hs[k], hc[k], hi, lo);
-                hsm[w][4 * c4 + k] = make_float2(hi, lo);
-            }
-        __syncthreads();
-        if (threadIdx.x < q) {
-            float2 t = make_float2(0.f, 0.f);
-            for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) t = dfx_add(t, hsm[ww][threadIdx.x]);
-            hpart[(size_t)blockIdx.x * q + threadIdx.x] = t;
-        }
-    }
-}
-
 // M_pre = I + sigma (G - h h' / p) from the TF32 Gram partials (FP32 sums in
 // block order) and the exact column sums h; written as (value, 0) pairs for
 // the factor of newton_mf_setup_kernel.
@@ -1482,10 +1365,13 @@ static cudaError_t launch_newton_mf(Work &W, const int32_t *J, long long p, doub
     const int q = (int)W.q;
     if (q % 16 == 0) {
         // preconditioner from the TF32 tensor-core Gram of all p rows and the exact h
-        const int G = W.nsm;
+        // (tcgen05 tensor cores, k_umma.cu)
+        const int G = gram_umma_blocks(W);
+        if (gram_umma_part_floats(W) > 2 * W.part_len) return cudaErrorInvalidValue;
         float *cpart = reinterpret_cast<float *>(W.part);
         float2 *hpart = reinterpret_cast<float2 *>(cpart + (size_t)G * q * q);
-        gram_tc_kernel<<<G, 256, 0, W.st>>>((const float *)W.X, q, J, p, cpart, hpart);
+        const cudaError_t eg = launch_gram_umma(W, J, p, cpart, hpart);
+        if (eg != cudaSuccess) return eg;
         build_m_tc_kernel<<<W.nsm, 256, 0, W.st>>>(q, G, cpart, hpart, split2(1.0 / (double)p), split2(sigma), W.Mf);
     } else {
         // preconditioner from a stride subsample of s rows: M_s = I + sigma (p / s) (G_s - h_s h_s' / s)
@@ -1501,6 +1387,7 @@ static cudaError_t launch_newton_mf(Work &W, const int32_t *J, long long p, doub
         build_m_df_kernel<<<W.nsm * 2, 256, 0, W.st>>>(q, ks, reinterpret_cast<const float2 *>(part),
                                                        reinterpret_cast<const float2 *>(hpart), split2(1.0 / s),
                                                        split2(sigma * (double)p / s), W.Mf);
+        ++W.nlaunch;
     }
     if (!g_mf_attr) {
         const cudaError_t ea = cudaFuncSetAttribute(newton_mf_setup_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1525,7 +1412,7 @@ static cudaError_t launch_newton_mf(Work &W, const int32_t *J, long long p, doub
                                                                      W.mf_pinv, pp, W.mf_counter, last, W.cg_maxit,
                                                                      dv, g, vdot, W.red, W.red + 12);
     }
-    W.nlaunch += 3 + kMfMaxPass;
+    W.nlaunch += 2 + kMfMaxPass;   // + the Gram, counted by its launcher
     return cudaGetLastError();
 }
 

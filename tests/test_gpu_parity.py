@@ -199,6 +199,50 @@ def test_newton_direction(prec, gscale, dtype, n, q, frac):
         assert np.linalg.norm(host(dv) - dv_r) <= r * 1.01 + 1e-12 * np.linalg.norm(dv_r)
 
 
+@pytest.mark.parametrize("n,q,p,order", [(5000, 128, 3000, "sorted"), (20000, 64, 20000, "sorted"),
+                                         (300000, 128, 150000, "random"), (1000, 16, 1, "sorted"),
+                                         (700, 112, 333, "random"), (2000, 128, 0, "sorted"),
+                                         (4096, 32, 4000, "sorted")])
+def test_gram_tensor_cores(n, q, p, order):
+    """G = X_J' X_J as the preconditioner of the large-free-set Newton step
+    forms it on the tcgen05 tensor cores (TF32 products: inputs keep 10 of
+    their 23 mantissa bits, so each product is within 2^-9 of exact; FP32 sums
+    within a block of at most ~p/300 rows add < 1e-4 relative; blocks added in
+    FP64), against the FP64 product of the gathered rows, elementwise relative
+    to |X_J|'|X_J|.  h = X_J' 1 is double-float: 1e-10 of sum |x|.  Covers a
+    ragged last stage (p not a multiple of 64), blocks with no rows (p < number
+    of blocks), p = 0, q < 128 (zero-padded MMA rows) and unsorted J."""
+    rng = np.random.default_rng(1000 + q + p)
+    X = (rng.normal(size=(n, q)) * rng.uniform(0.1, 3.0, size=q)).astype(np.float32)
+    y = np.where(rng.random(n) < 0.5, 1, -1).astype(np.int8)
+    J = rng.choice(n, size=p, replace=False).astype(np.int32)
+    if order == "sorted":
+        J = np.sort(J)
+    s, _, _ = make(X, y, precision=P.PREC_MIXED)
+    G = torch.full((q, q), np.nan, dtype=torch.float64, device="cuda")
+    hs = torch.full((q,), np.nan, dtype=torch.float64, device="cuda")
+    s.gram(dev(J) if p > 0 else None, p, G, hs)
+    XJ = X[J].astype(np.float64)
+    Gr = XJ.T @ XJ
+    scale = np.abs(XJ).T @ np.abs(XJ)
+    err = np.abs(host(G) - Gr)
+    assert np.all(err <= 3e-3 * scale + 1e-30), float(np.max(err / (scale + 1e-300)))
+    if p >= 1000:
+        # the rounding is TF32-sized, not FP32-exact: the tensor path really ran
+        assert float(np.max(err / (scale + 1e-300))) > 1e-6
+    np.testing.assert_allclose(host(hs), XJ.sum(axis=0), rtol=0, atol=1e-10 * max(1.0, np.abs(XJ).sum()))
+
+
+def test_gram_tensor_cores_rejects_other_shapes():
+    X = np.ones((100, 20), np.float32)
+    s, _, _ = make(X, np.where(np.arange(100) % 2 == 0, 1, -1), precision=P.PREC_MIXED)
+    G = torch.empty((20, 20), dtype=torch.float64, device="cuda")
+    hs = torch.empty(20, dtype=torch.float64, device="cuda")
+    with pytest.raises(P.SVMError) as e:
+        s.gram(dev(np.arange(10, dtype=np.int32)), 10, G, hs)
+    assert e.value.status == P.ERR_UNSUPPORTED
+
+
 def test_newton_empty_free_set():
     X, y = datagen.small(50, 8, seed=0)
     s, _, _ = make(X, y)
