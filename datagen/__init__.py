@@ -13,7 +13,7 @@ from __future__ import annotations
 
 import numpy as np
 
-_IDS = {"small": 0, "gauss2000": 1, "gauss1m": 2, "csr": 3, "mnist_like": 4, "warm": 5}
+_IDS = {"small": 0, "gauss2000": 1, "gauss1m": 2, "csr": 3, "mnist_like": 4, "warm": 5, "ovr": 6}
 
 
 def _rng(kind: str, seed: int) -> np.random.Generator:
@@ -157,3 +157,40 @@ def sparse_text(seed: int = 0, n: int = 700_000, q: int = 47_000, nnz_row: int =
     margin = np.bincount(rows, weights=values.astype(np.float64) * w[indices], minlength=n)
     y = np.where(margin + noise * rng.standard_normal(n) >= 0.0, 1, -1).astype(np.int8)
     return indptr, indices, values, y, 1.0
+
+
+def ovr_path(seed: int = 0, n: int = 200_000, q: int = 784, n_classes: int = 10, n_C: int = 16,
+             density: float = 0.2, C_lo: float = -3.0, C_hi: float = 2.0, dtype=np.float32):
+    """Many SVMs over one data matrix: one-vs-rest problems of a multi-class
+    labelling, each on a path of C values.
+
+    X: n x q, each entry 0 with probability 1 - density, else U[0, 1] (an
+    image-like sparse nonnegative matrix, stored dense).  Class proportions
+    p ~ Dirichlet(0.5 * 1), labels c_i ~ Categorical(p), redrawn until every
+    class occurs.  Problem (c, j) has y_i = +1 iff c_i = c and C = 10^(C_lo +
+    (C_hi - C_lo) j / (n_C - 1)); the labels do not depend on X.
+
+    Returns (X, Y [n_classes * n_C x n] int8, C [n_classes * n_C] float64),
+    problems ordered class-major."""
+    rng = _rng("ovr", seed)
+    X = np.zeros((n, q), dtype=dtype)
+    step = max(1, (1 << 22) // q)
+    for s in range(0, n, step):
+        m = min(step, n - s)
+        vals = rng.random((m, q))
+        keep = rng.random((m, q)) < density
+        X[s:s + m] = np.where(keep, vals, 0.0).astype(dtype)
+    while True:
+        props = rng.dirichlet(0.5 * np.ones(n_classes))
+        c = rng.choice(n_classes, size=n, p=props)
+        if np.unique(c).size == n_classes:
+            break
+    Cs = 10.0 ** (C_lo + (C_hi - C_lo) * np.arange(n_C) / max(1, n_C - 1))
+    Y = np.empty((n_classes * n_C, n), np.int8)
+    Cv = np.empty(n_classes * n_C, np.float64)
+    for k in range(n_classes):
+        yk = np.where(c == k, 1, -1).astype(np.int8)
+        for j in range(n_C):
+            Y[k * n_C + j] = yk
+            Cv[k * n_C + j] = Cs[j]
+    return X, Y, Cv

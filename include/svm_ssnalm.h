@@ -148,6 +148,33 @@ svm_status svm_ssnalm_create(svm_ssnalm_t **out, const svm_problem *prob,
  * alpha = 0, b = NaN), SVM_ERR_NUMERIC, SVM_ERR_TIMEOUT, SVM_ERR_CUDA. */
 svm_status svm_ssnalm_solve(svm_ssnalm_t *h, const double *alpha0, svm_result *res);
 
+/* Solve B problems that share the handle's X (dense layout): problem b has
+ * labels Y[b*n .. b*n+n-1] (+1/-1) and bound C[b], with every other setting
+ * of the handle (precision, tolerance, iteration caps, sigma schedule).  This
+ * is the one-vs-rest / regularisation-path use of the method: Algorithm 1 with
+ * Algorithm 3 inside, run for all problems in lockstep -- each problem
+ * advances one phase (start of a subproblem, Newton step with its first
+ * Armijo trial, further trial, end of an outer iteration) per stream
+ * synchronisation, problems that have converged drop out, and the forward
+ * products A v of all problems in a phase share passes over X (1, 2, 4 or 8
+ * vectors per pass, split by an autotuner that times the pass widths on this
+ * X at the first call).  Each problem's iterates, and so its results, are
+ * bit-identical to svm_ssnalm_solve of the same problem (cold start).
+ * Memory kind as the handle's: Y (B*n int8), alpha (B*n FP64, row b = problem
+ * b) and w (B*q FP64) are device pointers for SVM_MEM_DEVICE, host pointers
+ * for SVM_MEM_HOST; C (B doubles) and results (B entries) are host memory.
+ * results[b] is filled as by svm_ssnalm_solve, with results[b].alpha/.w set to
+ * the problem's rows of alpha and w and results[b].status its own status.
+ * The first call with a given B creates B internal sub-handles (each owns an
+ * O(n) workspace like a handle of its own; they are kept for later calls and
+ * freed by svm_ssnalm_destroy).  Synchronises the stream.  Returns SVM_OK
+ * when every problem converged, else the most severe per-problem status
+ * (errors, then SVM_ERR_NOT_CONVERGED, then SVM_ERR_DEGENERATE);
+ * SVM_ERR_INVALID_ARG for B < 1, null pointers, C <= 0 or non-finite, or a
+ * label other than +1/-1; SVM_ERR_UNSUPPORTED for CSR handles. */
+svm_status svm_ssnalm_solve_batch(svm_ssnalm_t *h, int32_t B, const int8_t *Y, const double *C, double *alpha,
+                                  double *w, svm_result *results);
+
 /* Release the handle and its workspace.  NULL-safe. */
 void svm_ssnalm_destroy(svm_ssnalm_t *h);
 

@@ -10,6 +10,8 @@ import ctypes as C
 import os
 import threading
 
+import numpy as np
+
 from . import build as _build
 
 OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_NOT_CONVERGED, ERR_NUMERIC, ERR_DEGENERATE, \
@@ -52,7 +54,7 @@ class Stats(C.Structure):
 
 SYMBOLS = ["svm_default_params", "svm_ssnalm_create", "svm_ssnalm_solve", "svm_ssnalm_destroy",
            "svm_ssnalm_last_error", "svm_op_matvec", "svm_op_rmatvec", "svm_op_project",
-           "svm_op_newton", "svm_op_kkt", "svm_op_gram", "svm_ssnalm_set_timing", "svm_ssnalm_get_stats",
+           "svm_op_newton", "svm_op_kkt", "svm_op_gram", "svm_ssnalm_solve_batch", "svm_ssnalm_set_timing", "svm_ssnalm_get_stats",
            "svm_rmatvec_noalloc", "svm_mlp_create", "svm_mlp_destroy", "svm_mlp_get_params",
            "svm_mlp_features", "svm_mlp_labels", "svm_mlp_gather", "svm_mlp_forward", "svm_mlp_loss_grad", "svm_mlp_adam_step",
            "svm_mlp_train_step", "svm_mlp_start_point", "svm_ssnalm_solve_mlp"]
@@ -95,6 +97,7 @@ def load(build_if_missing: bool = False):
         L.svm_op_newton.argtypes = [vp, vp, i64, C.c_double, vp, vp]
         L.svm_op_kkt.argtypes = [vp, vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.svm_op_gram.argtypes = [vp, vp, i64, vp, vp]
+        L.svm_ssnalm_solve_batch.argtypes = [vp, C.c_int32, vp, vp, vp, vp, C.POINTER(Result)]
         L.svm_ssnalm_set_timing.argtypes = [vp, C.c_int]
         L.svm_ssnalm_get_stats.argtypes = [vp, C.POINTER(Stats), C.c_int]
         L.svm_rmatvec_noalloc.argtypes = [vp, vp, i64, i64, vp, vp, vp]
@@ -113,6 +116,7 @@ def load(build_if_missing: bool = False):
         L.svm_mlp_start_point.argtypes = [vp, vp, i64, dbl, vp]
         L.svm_ssnalm_solve_mlp.argtypes = [vp, vp, C.POINTER(Result), C.POINTER(C.c_int32)]
         for f in ("svm_op_matvec", "svm_op_rmatvec", "svm_op_project", "svm_op_newton", "svm_op_kkt", "svm_op_gram",
+                  "svm_ssnalm_solve_batch",
                   "svm_ssnalm_set_timing", "svm_ssnalm_get_stats", "svm_rmatvec_noalloc", "svm_mlp_create",
                   "svm_mlp_get_params", "svm_mlp_features", "svm_mlp_labels", "svm_mlp_gather", "svm_mlp_forward",
                   "svm_mlp_loss_grad",
@@ -228,6 +232,21 @@ class Solver:
         out = {k: getattr(R, k) for k, _ in Result._fields_ if k not in ("alpha", "w", "reserved0")}
         out["status"] = st
         return out
+
+    def solve_batch(self, Y, Cs, alpha, w, allow=(OK, ERR_NOT_CONVERGED, ERR_DEGENERATE)):
+        """B problems sharing this handle's X: labels Y (B x n int8), bounds Cs
+        (B floats), outputs alpha (B x n FP64) and w (B x q FP64) in the
+        handle's memory kind.  Returns (status, [per-problem result dicts])."""
+        Cs = np.ascontiguousarray(np.asarray(Cs, dtype=np.float64))
+        B = int(Cs.size)
+        R = (Result * B)()
+        st = self._lib.svm_ssnalm_solve_batch(self.h, B, _ptr(Y), Cs.ctypes.data_as(C.c_void_p), _ptr(alpha),
+                                              _ptr(w), R)
+        self._check(st, allow)
+        outs = []
+        for b in range(B):
+            outs.append({k: getattr(R[b], k) for k, _ in Result._fields_ if k not in ("alpha", "w", "reserved0")})
+        return st, outs
 
     def solve_mlp(self, mlp, alpha, w, allow=(OK, ERR_NOT_CONVERGED, ERR_DEGENERATE)):
         """Warm-started solve from the network `mlp` (an MLP), cold fallback;

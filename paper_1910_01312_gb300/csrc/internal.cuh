@@ -183,6 +183,16 @@ cudaError_t launch_matvec(Work &W, const double *v0, double *z0, const double *v
 // the same with double-float outputs (mixed form, FP32 X with q % 4 == 0)
 cudaError_t launch_matvec_df(Work &W, const double *v0, float2 *z0, const double *v1 = nullptr,
                              float2 *z1 = nullptr);
+// One vector of a batched forward product: z_i = y_i <x_i, v> as a
+// double-float pair (mixed form), labels y of that vector's problem.
+struct MvItem {
+    const double *v;
+    float2 *z;
+    const int8_t *y;
+};
+// nv (1, 2, 4 or 8) = count products in one pass over X (W's X, n, q and stream);
+// each is bit-identical to launch_matvec_df of the same vector.
+cudaError_t launch_matvec_df_multi(Work &W, const MvItem *items, int count, int nv);
 // out = sum_i c_i y_i x_i over the index list idx (cnt entries, read from
 // *cnt_dev on the device) or over all rows when idx == nullptr.  The mixed
 // form reads the weights as y_i c_i FP32 pairs from wc (when non-null).

@@ -88,23 +88,29 @@ __global__ void __launch_bounds__(256) matvec_kernel(const TX *__restrict__ X, c
 // 32/GL rows (GL lanes per row), then transposes so that lane L holds row
 // base + L: the FP64 epilogue and the z store are then one coalesced
 // warp-wide instruction per 32 rows.
+// NV vectors share each pass over X: vector k has its own labels y[k] (the
+// batched solve runs problems that share X but not y) and output z[k].  Each
+// vector's sums are formed in the same order whatever NV is, so a product is
+// bit-identical whether it ran alone or in a batch.
 // OUTDF: write y_i * (s + c) as a normalised double-float pair (float2)
 // instead of FP64 (no FP64 instruction at all in that case).
+template <int NV>
+struct MvArgs {
+    const double *v[NV];
+    void *z[NV];
+    const int8_t *y[NV];
+};
+
 template <int GL, int NV, bool OUTDF>
-__global__ void __launch_bounds__(256) matvec_mx_kernel(const float *__restrict__ X, const int8_t *__restrict__ y,
-                                                        long long n, int q, const double *__restrict__ v0,
-                                                        const double *__restrict__ v1, void *__restrict__ z0v,
-                                                        void *__restrict__ z1v)
+__global__ void __launch_bounds__(256) matvec_mx_kernel(const float *__restrict__ X, long long n, int q, MvArgs<NV> a)
 {
     extern __shared__ float2 svf[];   // [NV][q] FP32 (hi, lo) split of v
     for (int j = threadIdx.x; j < q; j += blockDim.x) {
-        double d = v0[j];
-        float h = (float)d;
-        svf[j] = make_float2(h, (float)(d - (double)h));
-        if (NV == 2) {
-            d = v1[j];
-            h = (float)d;
-            svf[q + j] = make_float2(h, (float)(d - (double)h));
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            const double d = a.v[k][j];
+            const float h = (float)d;
+            svf[k * q + j] = make_float2(h, (float)(d - (double)h));
         }
     }
     __syncthreads();
@@ -154,21 +160,17 @@ __global__ void __launch_bounds__(256) matvec_mx_kernel(const float *__restrict_
         }
         const long long i = base + lane;
         if (i < n) {
-            const bool pos = y[i] > 0;
-            if (OUTDF) {
 #pragma unroll
-                for (int k = 0; k < NV; ++k) {
+            for (int k = 0; k < NV; ++k) {
+                const bool pos = a.y[k][i] > 0;
+                if (OUTDF) {
                     const float hi = rs[k] + rc[k];
                     float2 v = make_float2(hi, rc[k] - (hi - rs[k]));
                     if (!pos) { v.x = -v.x; v.y = -v.y; }
-                    reinterpret_cast<float2 *>(k == 0 ? z0v : z1v)[i] = v;
-                }
-            } else {
-                const double d0 = (double)rs[0] + (double)rc[0];
-                reinterpret_cast<double *>(z0v)[i] = pos ? d0 : -d0;
-                if (NV == 2) {
-                    const double d1 = (double)rs[NV - 1] + (double)rc[NV - 1];
-                    reinterpret_cast<double *>(z1v)[i] = pos ? d1 : -d1;
+                    reinterpret_cast<float2 *>(a.z[k])[i] = v;
+                } else {
+                    const double d = (double)rs[k] + (double)rc[k];
+                    reinterpret_cast<double *>(a.z[k])[i] = pos ? d : -d;
                 }
             }
         }
@@ -197,31 +199,81 @@ static cudaError_t matvec_dispatch(Work &W, const double *v0, double *z0, const 
     return cudaGetLastError();
 }
 
-template <int NV, bool OUTDF>
-static cudaError_t matvec_mx_dispatch(Work &W, const double *v0, void *z0, const double *v1, void *z1)
+// GL (lanes per row) depends on q only, so every NV sums a vector in the same order.
+static int mx_lanes(long long q)
 {
-    const int nv4 = (int)(W.q / 4);
+    const int nv4 = (int)(q / 4);
     int gl = 1;
     while (gl < 32 && (nv4 + gl - 1) / gl > 8) gl <<= 1;
-    const int blocks = W.nsm * 8;
-    const size_t smem = (size_t)NV * W.q * sizeof(float2);
-    const float *X = (const float *)W.X;
-#define MX_CASE(G)                                                                                        \
-    case G:                                                                                               \
-        matvec_mx_kernel<G, NV, OUTDF><<<blocks, 256, smem, W.st>>>(X, W.y, W.n, (int)W.q, v0, v1, z0, z1); \
+    return gl;
+}
+
+template <int NV, bool OUTDF>
+static cudaError_t matvec_mx_dispatch(const float *X, long long n, int q, int nsm, cudaStream_t st, const MvArgs<NV> &a)
+{
+    const int gl = mx_lanes(q);
+    const int blocks = nsm * 8;
+    const size_t smem = (size_t)NV * q * sizeof(float2);
+    if (smem > 48 * 1024) {
+        // larger tiles of vectors (NV >= 8 at q > 384) need the opt-in shared memory
+        static int attr_set[6] = {0, 0, 0, 0, 0, 0};
+        static void *const kern[6] = {(void *)matvec_mx_kernel<1, NV, OUTDF>, (void *)matvec_mx_kernel<2, NV, OUTDF>,
+                                      (void *)matvec_mx_kernel<4, NV, OUTDF>, (void *)matvec_mx_kernel<8, NV, OUTDF>,
+                                      (void *)matvec_mx_kernel<16, NV, OUTDF>, (void *)matvec_mx_kernel<32, NV, OUTDF>};
+        int li = 0;
+        while ((1 << li) < gl) ++li;
+        if (!attr_set[li]) {
+            const cudaError_t e = cudaFuncSetAttribute(kern[li], cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+            if (e != cudaSuccess) return e;
+            attr_set[li] = 1;
+        }
+    }
+#define MX_CASE(G)                                                               \
+    case G:                                                                      \
+        matvec_mx_kernel<G, NV, OUTDF><<<blocks, 256, smem, st>>>(X, n, q, a); \
         break;
     switch (gl) {
         MX_CASE(1) MX_CASE(2) MX_CASE(4) MX_CASE(8) MX_CASE(16) MX_CASE(32)
     }
 #undef MX_CASE
-    ++W.nlaunch;
     return cudaGetLastError();
+}
+
+template <int NV, bool OUTDF>
+static cudaError_t matvec_mx_one(Work &W, const double *v0, void *z0, const double *v1, void *z1)
+{
+    MvArgs<NV> a;
+    a.v[0] = v0; a.z[0] = z0; a.y[0] = W.y;
+    if (NV == 2) { a.v[NV - 1] = v1; a.z[NV - 1] = z1; a.y[NV - 1] = W.y; }
+    ++W.nlaunch;
+    return matvec_mx_dispatch<NV, OUTDF>((const float *)W.X, W.n, (int)W.q, W.nsm, W.st, a);
 }
 
 cudaError_t launch_matvec_df(Work &W, const double *v0, float2 *z0, const double *v1, float2 *z1)
 {
     if (!(!W.csr && W.xf32 && W.q % 4 == 0 && (uintptr_t)W.X % 16 == 0)) return cudaErrorInvalidValue;
-    return v1 ? matvec_mx_dispatch<2, true>(W, v0, z0, v1, z1) : matvec_mx_dispatch<1, true>(W, v0, z0, v1, z1);
+    return v1 ? matvec_mx_one<2, true>(W, v0, z0, v1, z1) : matvec_mx_one<1, true>(W, v0, z0, v1, z1);
+}
+
+template <int NV>
+static cudaError_t multi_pass(const Work &W, const MvItem *it)
+{
+    MvArgs<NV> a;
+    for (int k = 0; k < NV; ++k) { a.v[k] = it[k].v; a.z[k] = it[k].z; a.y[k] = it[k].y; }
+    return matvec_mx_dispatch<NV, true>((const float *)W.X, W.n, (int)W.q, W.nsm, W.st, a);
+}
+
+cudaError_t launch_matvec_df_multi(Work &W, const MvItem *items, int count, int nv)
+{
+    if (!(!W.csr && W.xf32 && W.q % 4 == 0 && (uintptr_t)W.X % 16 == 0)) return cudaErrorInvalidValue;
+    if (count < 1 || (nv != 1 && nv != 2 && nv != 4 && nv != 8) || count != nv) return cudaErrorInvalidValue;
+    ++W.nlaunch;
+    switch (nv) {
+    case 1: return multi_pass<1>(W, items);
+    case 2: return multi_pass<2>(W, items);
+    case 4: return multi_pass<4>(W, items);
+    default: return multi_pass<8>(W, items);
+    }
 }
 
 cudaError_t launch_matvec(Work &W, const double *v0, double *z0, const double *v1, double *z1)
@@ -231,7 +283,7 @@ cudaError_t launch_matvec(Work &W, const double *v0, double *z0, const double *v
     const bool vec = ((W.q * es) % 16 == 0) && ((uintptr_t)W.X % 16 == 0);
     const bool two = v1 != nullptr;
     if (W.xf32 && vec && W.precision == 1)
-        return two ? matvec_mx_dispatch<2, false>(W, v0, z0, v1, z1) : matvec_mx_dispatch<1, false>(W, v0, z0, v1, z1);
+        return two ? matvec_mx_one<2, false>(W, v0, z0, v1, z1) : matvec_mx_one<1, false>(W, v0, z0, v1, z1);
     if (W.xf32) {
         if (vec) return two ? matvec_dispatch<float, true, 2>(W, v0, z0, v1, z1)
                             : matvec_dispatch<float, true, 1>(W, v0, z0, v1, z1);

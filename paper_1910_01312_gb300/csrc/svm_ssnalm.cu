@@ -54,6 +54,18 @@ struct svm_ssnalm {
     long long syncs = 0;
     long long launch_base = 0;
     bool trace = false;   // SVM_SSNALM_TRACE=1: one stderr line per Newton step
+    // batched solves (svm_ssnalm_solve_batch): one sub-handle per problem,
+    // sharing this handle's X and stream; the forward-product plan of the
+    // autotuner; per-problem label counts; staging for host memory
+    std::vector<svm_ssnalm *> subs;
+    bool mv_tuned = false;
+    float mv_ms[4] = {0.f, 0.f, 0.f, 0.f};   // ms per pass over X with 1, 2, 4, 8 vectors
+    std::vector<int> mv_plan;                  // mv_plan[c]: vectors in the first pass for c products
+    int *bat_cnt = nullptr;
+    int8_t *bat_y = nullptr;
+    double *bat_a = nullptr, *bat_w = nullptr;
+    int bat_cap = 0;
+    long long batch_ticks = 0;
 };
 
 enum { TK_MATVEC = 0, TK_RMATVEC = 1, TK_PROJ = 2, TK_NEWTON = 3 };
@@ -164,6 +176,10 @@ extern "C" void svm_ssnalm_destroy(svm_ssnalm_t *h)
     if (!h) return;
     if (h->W.st) cudaStreamSynchronize(h->W.st);
     for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
+    for (svm_ssnalm *sb : h->subs) svm_ssnalm_destroy(sb);
+    void *bp[] = {h->bat_cnt, h->bat_y, h->bat_a, h->bat_w};
+    for (void *p : bp)
+        if (p) cudaFree(p);
     free_work(h->W);
     delete h;
 }
@@ -204,7 +220,9 @@ static cudaError_t dalloc(T **p, size_t count)
     return cudaMalloc((void **)p, (count ? count : 1) * sizeof(T));
 }
 
-extern "C" svm_status svm_ssnalm_create(svm_ssnalm_t **out, const svm_problem *prob, const svm_params *params)
+// validate = false: the labels and X were checked by the caller (the
+// sub-handles of a batched solve, which share the parent's X)
+static svm_status create_impl(svm_ssnalm_t **out, const svm_problem *prob, const svm_params *params, bool validate)
 {
     if (out) *out = nullptr;
     if (!out || !prob || !params) { g_create_err = "null argument"; return SVM_ERR_INVALID_ARG; }
@@ -326,6 +344,10 @@ extern "C" svm_status svm_ssnalm_create(svm_ssnalm_t **out, const svm_problem *p
     cudaMemsetAsync(W.rm_counter, 0, 4 * sizeof(unsigned), W.st);
     cudaMemsetAsync(W.err, 0, 4 * sizeof(int), W.st);
     cudaMemsetAsync(W.pout, 0, 4 * sizeof(ProjOut), W.st);
+    if (!validate) {
+        *out = h;
+        return SVM_OK;
+    }
     // validate labels and data on the device
     int *chk = nullptr;
     if (dalloc(&chk, 4)) return fail(SVM_ERR_OOM, "device allocation failed");
@@ -366,17 +388,30 @@ extern "C" svm_status svm_ssnalm_create(svm_ssnalm_t **out, const svm_problem *p
     return SVM_OK;
 }
 
+extern "C" svm_status svm_ssnalm_create(svm_ssnalm_t **out, const svm_problem *prob, const svm_params *params)
+{
+    return create_impl(out, prob, params, true);
+}
+
 // ------------------------------------------------------------ helpers
 
-static svm_status sync_read(svm_ssnalm *h)
+// Scalar read-back of a phase: the projection records, the small reductions
+// and the device error flag, copied to pinned host memory (stream-ordered).
+static svm_status readback_issue(svm_ssnalm *h)
 {
     Work &W = h->W;
     CK(cudaMemcpyAsync(W.h_pout, W.pout, 4 * sizeof(ProjOut), cudaMemcpyDeviceToHost, W.st));
     CK(cudaMemcpyAsync(W.h_red, W.red, 16 * sizeof(double), cudaMemcpyDeviceToHost, W.st));
     CK(cudaMemcpyAsync(W.h_err, W.err, sizeof(int), cudaMemcpyDeviceToHost, W.st));
-    CK(cudaStreamSynchronize(W.st));
-    h->syncs++;
-    if (h->timing) flush_timing(h);
+    return SVM_OK;
+}
+
+// After the stream has been synchronised: complete the double-float records
+// and turn a device error flag into a status (the flag is cleared for the
+// next call).
+static svm_status readback_check(svm_ssnalm *h)
+{
+    Work &W = h->W;
     for (int k = 0; k < 4; ++k) {
         ProjOut &o = W.h_pout[k];
         if (!o.is_df) continue;
@@ -394,6 +429,16 @@ static svm_status sync_read(svm_ssnalm *h)
         return SVM_ERR_NUMERIC;
     }
     return SVM_OK;
+}
+
+static svm_status sync_read(svm_ssnalm *h)
+{
+    svm_status st = readback_issue(h);
+    if (st != SVM_OK) return st;
+    CK(cudaStreamSynchronize(h->W.st));
+    h->syncs++;
+    if (h->timing) flush_timing(h);
+    return readback_check(h);
 }
 
 // ProjOut slots: 0 step-level op, 1 + b for projection buffer b, 3 KKT.
@@ -478,198 +523,386 @@ __global__ void copyq_kernel(int q, const double *a, double *b)
 
 // ------------------------------------------------------------ solve
 
-extern "C" svm_status svm_ssnalm_solve(svm_ssnalm_t *h, const double *alpha0, svm_result *res)
+// One solve as a sequence of phases.  A phase issues kernels on the handle's
+// stream, possibly with forward products A v in the middle (run_pre issues
+// what comes before them and lists them in mv, run_post what comes after),
+// and ends with the read-back of the scalars that decide the next phase
+// (run_after, once the stream has been synchronised).  svm_ssnalm_solve runs
+// one Run and synchronises after every phase; svm_ssnalm_solve_batch runs
+// many in lockstep, with one pass over X for the forward products of all of
+// them and one synchronisation per phase for all of them.
+enum RunPhase { RP_INIT, RP_SUBSTART, RP_NEWTON, RP_TRIAL, RP_OUTER_END, RP_FINISH, RP_DONE };
+
+struct MvReq {
+    int nv = 0;
+    const double *v[2] = {nullptr, nullptr};
+    float2 *zf[2] = {nullptr, nullptr};   // double-float outputs (mixed form)
+    double *z[2] = {nullptr, nullptr};    // FP64 outputs (other forms)
+};
+
+struct Run {
+    svm_ssnalm *h = nullptr;
+    const double *alpha0 = nullptr;
+    svm_result *res = nullptr;
+    RunPhase ph = RP_INIT;
+    int cur = 0;          // projection buffer holding pi(u(v)) at the current point
+    int k = 0, j = 0, mtr = 0, inner_total = 0;
+    double sigma = 1.0, R = 0.0, Rprev = 0.0, t = 1.0, epsk = 0.1;
+    svm_status status = SVM_ERR_NOT_CONVERGED;   // convergence status
+    svm_status ret = SVM_OK;                     // return value once done
+    MvReq mv;
+    std::vector<double> hw;                      // w on the host (results)
+};
+
+static void mv_add(Work &W, MvReq &m, const double *v, float2 *zf, double *z)
 {
-    if (!h) return SVM_ERR_INVALID_ARG;
-    if (!res || !res->alpha || !res->w) { h->err = "result buffers must be non-null"; return SVM_ERR_INVALID_ARG; }
+    (void)W;
+    m.v[m.nv] = v;
+    m.zf[m.nv] = zf;
+    m.z[m.nv] = z;
+    ++m.nv;
+}
+
+// The requested products of one run, one launch (both vectors in one pass).
+static svm_status run_matvec_single(Run &r)
+{
+    svm_ssnalm *h = r.h;
+    Work &W = h->W;
+    const MvReq &m = r.mv;
+    if (!m.nv) return SVM_OK;
+    CK(timed(h, TK_MATVEC, [&] {
+        return W.df ? launch_matvec_df(W, m.v[0], m.zf[0], m.nv > 1 ? m.v[1] : nullptr, m.nv > 1 ? m.zf[1] : nullptr)
+                    : launch_matvec(W, m.v[0], m.z[0], m.nv > 1 ? m.v[1] : nullptr, m.nv > 1 ? m.z[1] : nullptr);
+    }));
+    return SVM_OK;
+}
+
+// A line-search trial at step t: project u - t sigma A dv into the other
+// buffer and, speculatively, form A'pi and the gradient there, so an accepted
+// trial is the next iterate's projection and gradient at no extra pass.
+static svm_status issue_trial(Run &r)
+{
+    svm_ssnalm *h = r.h;
+    Work &W = h->W;
+    const int cur = r.cur, nxt = 1 - cur;
+    const double t = r.t, sigma = r.sigma;
+    ProjBuf &B = W.pb[nxt];
+    if (W.df) {
+        ProjDF tr;
+        tr.a = W.pb[cur].uf; tr.b = W.dzf; tr.c1 = -t * sigma; tr.c2 = 0.0;
+        tr.sums = SF_PSID | SF_DPA; tr.alpha_w = W.alphaw; tr.base_w = W.pb[cur].wpi;
+        tr.lam0 = &W.pout[1 + cur].lamf;
+        tr.u_out = B.uf; tr.wpi_out = B.wpi; tr.dw_out = W.dw; tr.dwa_out = W.dwa; tr.J = B.J; tr.D = B.S;
+        CK(timed(h, TK_PROJ, [&] { return launch_project_df(W, tr, &W.pout[1 + nxt]); }));
+        // A'pi at the trial point and, in the epilogue, vt = v + t dv and
+        // g = vt - A'pi with |g|^2 (kept if the trial is accepted)
+        GradOut go;
+        go.v = W.v; go.dv = W.dv; go.t = t; go.g = W.tmpq; go.vt = W.vt;
+        CK(timed(h, TK_RMATVEC, [&] {
+            return launch_rmatvec_df(W, W.dw, W.dwa, B.S, &W.pout[1 + nxt].s, W.atp, W.atpa, W.atp2, W.atpa2, 1, go);
+        }));
+    } else {
+        ProjIn tr;
+        tr.a = W.pb[cur].u; tr.b = W.dz; tr.c1 = -t * sigma; tr.c2 = 0.0;
+        tr.sums = SF_PSID | SF_DPA; tr.alpha = W.alpha; tr.pi_base = W.pb[cur].pi;
+        tr.lam0 = &W.pout[1 + cur].lam;
+        tr.u_out = B.u; tr.pi_out = B.pi; tr.wpi_out = B.wpi; tr.J = B.J; tr.S = B.S;
+        CK(timed(h, TK_PROJ, [&] { return launch_project(W, tr, &W.pout[1 + nxt]); }));
+        CK(timed(h, TK_RMATVEC, [&] { return launch_rmatvec(W, B.pi, B.wpi, B.S, &W.pout[1 + nxt].s, W.atp2, 1); }));
+        grad_at_kernel<<<1, 1024, 0, W.st>>>((int)W.q, W.v, W.dv, t, W.atp2, W.tmpq, W.red);
+        ++W.nlaunch;
+        CK(cudaGetLastError());
+    }
+    return readback_issue(h);
+}
+
+// Degenerate labels (one class only): alpha = 0, b undefined.
+static svm_status run_degenerate(Run &r)
+{
+    svm_ssnalm *h = r.h;
+    Work &W = h->W;
+    svm_result *res = r.res;
+    const bool host_mem = h->prob.memory == SVM_MEM_HOST;
+    CK(cudaMemsetAsync(W.alpha, 0, W.n * sizeof(double), W.st));
+    CK(cudaMemsetAsync(W.w, 0, W.q * sizeof(double), W.st));
+    cudaMemcpyKind kd = host_mem ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    CK(cudaMemcpyAsync(res->alpha, W.alpha, W.n * sizeof(double), kd, W.st));
+    CK(cudaMemcpyAsync(res->w, W.w, W.q * sizeof(double), kd, W.st));
+    CK(cudaStreamSynchronize(W.st));
+    res->b = NAN; res->kkt = NAN; res->objective = 0.0; res->primal_objective = NAN; res->gap = NAN;
+    res->sigma = h->P.sigma0; res->outer_iters = 0; res->inner_iters_total = 0;
+    res->n_free = res->n_upper = res->n_sv = 0;
+    res->status = SVM_ERR_DEGENERATE;
+    h->err = "labels of one class only";
+    r.ret = SVM_ERR_DEGENERATE;
+    r.ph = RP_DONE;
+    return SVM_OK;
+}
+
+// Kernels of the phase before its forward products.
+static svm_status run_pre(Run &r)
+{
+    svm_ssnalm *h = r.h;
     Work &W = h->W;
     const svm_params &P = h->P;
     const bool host_mem = h->prob.memory == SVM_MEM_HOST;
     const long long n = W.n;
     const int q = (int)W.q;
     const bool df = W.df;
-    svm_status st;
-    h->err.clear();
-
-    // degenerate labels: one class only
-    if (h->npos == 0 || h->npos == n) {
-        CK(cudaMemsetAsync(W.alpha, 0, n * sizeof(double), W.st));
-        CK(cudaMemsetAsync(W.w, 0, q * sizeof(double), W.st));
-        cudaMemcpyKind k = host_mem ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
-        CK(cudaMemcpyAsync(res->alpha, W.alpha, n * sizeof(double), k, W.st));
-        CK(cudaMemcpyAsync(res->w, W.w, q * sizeof(double), k, W.st));
-        CK(cudaStreamSynchronize(W.st));
-        res->b = NAN; res->kkt = NAN; res->objective = 0.0; res->primal_objective = NAN; res->gap = NAN;
-        res->sigma = P.sigma0; res->outer_iters = 0; res->inner_iters_total = 0;
-        res->n_free = res->n_upper = res->n_sv = 0;
-        res->status = SVM_ERR_DEGENERATE;
-        h->err = "labels of one class only";
-        return SVM_ERR_DEGENERATE;
-    }
-
-    // lambda warm starts restart at 0
-    CK(cudaMemsetAsync(W.pout, 0, 4 * sizeof(ProjOut), W.st));
-    int cur = 0;   // projection buffer holding pi(u(v)) at the current point
-
-    // start point: alpha^0 = Pi(alpha0) (or 0); the ALM dual starts at v = A'alpha^0
-    // (w^0 = 0 when cold, Sec. 4.1)
-    if (alpha0) {
-        cudaMemcpyKind k = host_mem ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-        CK(cudaMemcpyAsync(W.tmpn, alpha0, n * sizeof(double), k, W.st));
-        if (df) {
-            // y o Pi(alpha0) and A'Pi(alpha0) (the delta list against 0 is the support)
-            CK(split_vector(W, W.tmpn, false, W.pb[1].uf));
-            ProjDF in;
-            in.a = W.pb[1].uf;
-            in.wpi_out = W.alphaw; in.dw_out = W.dw; in.dwa_out = W.dwa; in.D = W.pb[0].S;
-            CK(timed(h, TK_PROJ, [&] { return launch_project_df(W, in, &W.pout[SLOT_OP]); }));
-            CK(timed(h, TK_RMATVEC, [&] {
-                return launch_rmatvec_df(W, W.dw, W.dwa, W.pb[0].S, &W.pout[SLOT_OP].s, nullptr, nullptr, W.v, nullptr, -1);
-            }));
-        } else {
-            ProjIn in;
-            in.a = W.tmpn; in.pi_out = W.alpha; in.S = W.pb[0].S; in.wpi_out = W.pb[0].wpi;
-            CK(timed(h, TK_PROJ, [&] { return launch_project(W, in, &W.pout[SLOT_OP]); }));
-            CK(timed(h, TK_RMATVEC, [&] {
-                return launch_rmatvec(W, W.alpha, W.pb[0].wpi, W.pb[0].S, &W.pout[SLOT_OP].s, W.v, -1);
-            }));
-        }
-        copyq_kernel<<<1, 1024, 0, W.st>>>(q, W.v, W.w);
-        ++W.nlaunch;
-        CK(cudaGetLastError());
-        // Q alpha = A w and z = A v (equal here) in one pass
-        CK(timed(h, TK_MATVEC, [&] {
-            return df ? launch_matvec_df(W, W.w, W.qaf, W.v, W.zf) : launch_matvec(W, W.w, W.qa, W.v, W.z);
-        }));
-        CK(cudaMemsetAsync(W.pout, 0, sizeof(ProjOut), W.st));
-    } else {
-        CK(cudaMemsetAsync(W.v, 0, q * sizeof(double), W.st));
-        CK(cudaMemsetAsync(W.w, 0, q * sizeof(double), W.st));
-        if (df) {
-            CK(cudaMemsetAsync(W.alphaw, 0, n * sizeof(float2), W.st));
-            CK(cudaMemsetAsync(W.qaf, 0, n * sizeof(float2), W.st));
-            CK(cudaMemsetAsync(W.zf, 0, n * sizeof(float2), W.st));
-        } else {
-            CK(cudaMemsetAsync(W.alpha, 0, n * sizeof(double), W.st));
-            CK(cudaMemsetAsync(W.qa, 0, n * sizeof(double), W.st));
-            CK(cudaMemsetAsync(W.z, 0, n * sizeof(double), W.st));
-        }
-    }
-    double sigma = P.sigma0;
-    if ((st = df ? kkt_project_df(h, W.alphaw) : kkt_project(h, W.alpha)) != SVM_OK) return st;
-    if ((st = sync_read(h)) != SVM_OK) return st;
-    double R = kkt_value(W.h_pout[SLOT_KKT]), Rprev = R;
-    svm_status status = SVM_ERR_NOT_CONVERGED;
-    int k = 0, inner_total = 0;
-    if (R <= P.tol) status = SVM_OK;
-    for (k = 0; k < P.max_outer && status != SVM_OK; ++k) {
-        const double epsk = 0.1 * pow(0.5, (double)k);
-        // z = A v holds here (from the start or from the fused product below).
-        // u = alpha^k - sigma (z - e); pi = Pi(u); J   (eq. (3.3))
-        {
-            ProjBuf &B = W.pb[cur];
+    r.mv = MvReq();
+    switch (r.ph) {
+    case RP_INIT: {
+        // lambda warm starts restart at 0
+        CK(cudaMemsetAsync(W.pout, 0, 4 * sizeof(ProjOut), W.st));
+        r.cur = 0;
+        r.sigma = P.sigma0;
+        // start point: alpha^0 = Pi(alpha0) (or 0); the ALM dual starts at v = A'alpha^0
+        // (w^0 = 0 when cold, Sec. 4.1)
+        if (r.alpha0) {
+            cudaMemcpyKind kin = host_mem ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+            CK(cudaMemcpyAsync(W.tmpn, r.alpha0, n * sizeof(double), kin, W.st));
             if (df) {
-                // A'pi from scratch once per subproblem (the delta list against 0 is
-                // the support): the incremental products of the line search then
-                // carry roundoff from this subproblem only
+                // y o Pi(alpha0) and A'Pi(alpha0) (the delta list against 0 is the support)
+                CK(split_vector(W, W.tmpn, false, W.pb[1].uf));
                 ProjDF in;
-                in.a = W.alphaw; in.a_signed = true; in.b = W.zf; in.c1 = -sigma; in.c2 = sigma;
-                in.sums = SF_DPA; in.alpha_w = W.alphaw;
-                in.lam0 = &W.pout[1 + cur].lamf;
-                in.u_out = B.uf; in.wpi_out = B.wpi; in.dw_out = W.dw; in.dwa_out = W.dwa; in.J = B.J; in.D = B.S;
-                CK(timed(h, TK_PROJ, [&] { return launch_project_df(W, in, &W.pout[1 + cur]); }));
-                // ... and g = v - A'pi with |g|^2 in the same launch's epilogue
-                GradOut go;
-                go.v = W.v; go.g = W.g;
+                in.a = W.pb[1].uf;
+                in.wpi_out = W.alphaw; in.dw_out = W.dw; in.dwa_out = W.dwa; in.D = W.pb[0].S;
+                CK(timed(h, TK_PROJ, [&] { return launch_project_df(W, in, &W.pout[SLOT_OP]); }));
                 CK(timed(h, TK_RMATVEC, [&] {
-                    return launch_rmatvec_df(W, W.dw, W.dwa, B.S, &W.pout[1 + cur].s, nullptr, nullptr, W.atp, W.atpa, 1,
-                                             go);
+                    return launch_rmatvec_df(W, W.dw, W.dwa, W.pb[0].S, &W.pout[SLOT_OP].s, nullptr, nullptr, W.v,
+                                             nullptr, -1);
                 }));
             } else {
                 ProjIn in;
-                in.a = W.alpha; in.b = W.z; in.c1 = -sigma; in.c2 = sigma;
-                in.sums = SF_DPA; in.alpha = W.alpha;
-                in.lam0 = &W.pout[1 + cur].lam;
-                in.u_out = B.u; in.pi_out = B.pi; in.wpi_out = B.wpi; in.J = B.J; in.S = B.S;
-                CK(timed(h, TK_PROJ, [&] { return launch_project(W, in, &W.pout[1 + cur]); }));
-                // g = v - A'pi (eq. (3.10) in q coordinates) and its roundoff scale
+                in.a = W.tmpn; in.pi_out = W.alpha; in.S = W.pb[0].S; in.wpi_out = W.pb[0].wpi;
+                CK(timed(h, TK_PROJ, [&] { return launch_project(W, in, &W.pout[SLOT_OP]); }));
                 CK(timed(h, TK_RMATVEC, [&] {
-                    return launch_rmatvec(W, B.pi, B.wpi, B.S, &W.pout[1 + cur].s, W.atp, 1);
+                    return launch_rmatvec(W, W.alpha, W.pb[0].wpi, W.pb[0].S, &W.pout[SLOT_OP].s, W.v, -1);
                 }));
-                CK(launch_grad(W));
             }
-            if ((st = sync_read(h)) != SVM_OK) return st;
+            copyq_kernel<<<1, 1024, 0, W.st>>>(q, W.v, W.w);
+            ++W.nlaunch;
+            CK(cudaGetLastError());
+            // Q alpha = A w and z = A v (equal here) in one pass
+            mv_add(W, r.mv, W.w, W.qaf, W.qa);
+            mv_add(W, r.mv, W.v, W.zf, W.z);
+        } else {
+            CK(cudaMemsetAsync(W.v, 0, q * sizeof(double), W.st));
+            CK(cudaMemsetAsync(W.w, 0, q * sizeof(double), W.st));
+            if (df) {
+                CK(cudaMemsetAsync(W.alphaw, 0, n * sizeof(float2), W.st));
+                CK(cudaMemsetAsync(W.qaf, 0, n * sizeof(float2), W.st));
+                CK(cudaMemsetAsync(W.zf, 0, n * sizeof(float2), W.st));
+            } else {
+                CK(cudaMemsetAsync(W.alpha, 0, n * sizeof(double), W.st));
+                CK(cudaMemsetAsync(W.qa, 0, n * sizeof(double), W.st));
+                CK(cudaMemsetAsync(W.z, 0, n * sizeof(double), W.st));
+            }
         }
-        int j = 0;
-        for (j = 0;; ++j) {
-            const ProjOut &m = W.h_pout[1 + cur];
-            const double gn = sqrt(W.h_red[0]);
-            const double dx = sqrt(m.sum[0]);
-            const double tol_in = fmin(epsk, epsk * dx) / sqrt(sigma);
-            const double floor_g = (df ? 32e-15 : 1e-15) * sqrt(W.h_red[1]);
-            if (!isfinite(gn)) { h->err = "non-finite gradient"; return SVM_ERR_NUMERIC; }
-            if (h->trace)
-                fprintf(stderr, "[svm] k=%d j=%d sigma=%.3g p=%lld s=%lld |g|=%.3e tol=%.3e passes=%d lam=%.6g\n", k, j,
-                        sigma, (long long)m.p, (long long)m.s, gn, fmax(tol_in, floor_g), m.passes, m.lam);
-            if (gn <= fmax(tol_in, floor_g) || j >= P.max_inner) break;
-            // Algorithm 3, Step 1: Newton direction on the free set J
-            const long long p = m.p;
-            // (with the Armijo quantities g'dv, v'dv, dv'dv)
-            CK(timed(h, TK_NEWTON, [&] {
-                return launch_newton(W, W.pb[cur].J, p, &W.pout[1 + cur].p, sigma, W.g, W.dv, true);
+        return SVM_OK;
+    }
+    case RP_SUBSTART:
+    case RP_TRIAL:
+    case RP_FINISH:
+        return SVM_OK;
+    case RP_NEWTON: {
+        // Algorithm 3, Step 1: Newton direction on the free set J (with the
+        // Armijo quantities g'dv, v'dv, dv'dv), then A dv = Q d
+        const long long p = W.h_pout[1 + r.cur].p;
+        const double sigma = r.sigma;
+        const int cur = r.cur;
+        CK(timed(h, TK_NEWTON, [&] {
+            return launch_newton(W, W.pb[cur].J, p, &W.pout[1 + cur].p, sigma, W.g, W.dv, true);
+        }));
+        mv_add(W, r.mv, W.dv, W.dzf, W.dz);
+        return SVM_OK;
+    }
+    case RP_OUTER_END: {
+        // alpha^{k+1} = Pi(u(w^{k+1}))  (eq. (3.5)): the buffer holding pi becomes
+        // alpha (the old alpha buffer takes its place); A'alpha^{k+1} is the last A'pi
+        if (df) std::swap(W.alphaw, W.pb[r.cur].wpi);
+        else std::swap(W.alpha, W.pb[r.cur].pi);
+        std::swap(W.w, W.atp);   // the next subproblem forms A'pi afresh into the other buffer
+        // Q alpha = A w for the KKT test and z = A v for the next subproblem, one pass
+        mv_add(W, r.mv, W.w, W.qaf, W.qa);
+        mv_add(W, r.mv, W.v, W.zf, W.z);
+        return SVM_OK;
+    }
+    case RP_DONE:
+        return SVM_OK;
+    }
+    return SVM_OK;
+}
+
+// Kernels of the phase after its forward products, then the read-back.
+static svm_status run_post(Run &r)
+{
+    svm_ssnalm *h = r.h;
+    Work &W = h->W;
+    const bool host_mem = h->prob.memory == SVM_MEM_HOST;
+    const bool df = W.df;
+    svm_status st;
+    switch (r.ph) {
+    case RP_INIT:
+        if (r.alpha0) CK(cudaMemsetAsync(W.pout, 0, sizeof(ProjOut), W.st));
+        if ((st = df ? kkt_project_df(h, W.alphaw) : kkt_project(h, W.alpha)) != SVM_OK) return st;
+        return readback_issue(h);
+    case RP_SUBSTART: {
+        // z = A v holds here (from the start or from the fused product of the
+        // last phase).  u = alpha^k - sigma (z - e); pi = Pi(u); J   (eq. (3.3))
+        r.epsk = 0.1 * pow(0.5, (double)r.k);
+        const double sigma = r.sigma;
+        const int cur = r.cur;
+        ProjBuf &B = W.pb[cur];
+        if (df) {
+            // A'pi from scratch once per subproblem (the delta list against 0 is
+            // the support): the incremental products of the line search then
+            // carry roundoff from this subproblem only
+            ProjDF in;
+            in.a = W.alphaw; in.a_signed = true; in.b = W.zf; in.c1 = -sigma; in.c2 = sigma;
+            in.sums = SF_DPA; in.alpha_w = W.alphaw;
+            in.lam0 = &W.pout[1 + cur].lamf;
+            in.u_out = B.uf; in.wpi_out = B.wpi; in.dw_out = W.dw; in.dwa_out = W.dwa; in.J = B.J; in.D = B.S;
+            CK(timed(h, TK_PROJ, [&] { return launch_project_df(W, in, &W.pout[1 + cur]); }));
+            // ... and g = v - A'pi with |g|^2 in the same launch's epilogue
+            GradOut go;
+            go.v = W.v; go.g = W.g;
+            CK(timed(h, TK_RMATVEC, [&] {
+                return launch_rmatvec_df(W, W.dw, W.dwa, B.S, &W.pout[1 + cur].s, nullptr, nullptr, W.atp, W.atpa, 1,
+                                         go);
             }));
-            // A dv = Q d
-            CK(timed(h, TK_MATVEC, [&] { return df ? launch_matvec_df(W, W.dv, W.dzf) : launch_matvec(W, W.dv, W.dz); }));
-            // Step 2: Armijo line search.  Each trial projects u - t sigma A dv into the
-            // other buffer and, speculatively, forms the gradient there, so an accepted
-            // trial is the next iterate's projection and gradient at no extra pass.
-            double t = 1.0;
-            bool accepted = false;
-            const int nxt = 1 - cur;
-            for (int mtr = 0; mtr < P.max_ls; ++mtr) {
-                ProjBuf &B = W.pb[nxt];
-                if (df) {
-                    ProjDF tr;
-                    tr.a = W.pb[cur].uf; tr.b = W.dzf; tr.c1 = -t * sigma; tr.c2 = 0.0;
-                    tr.sums = SF_PSID | SF_DPA; tr.alpha_w = W.alphaw; tr.base_w = W.pb[cur].wpi;
-                    tr.lam0 = &W.pout[1 + cur].lamf;
-                    tr.u_out = B.uf; tr.wpi_out = B.wpi; tr.dw_out = W.dw; tr.dwa_out = W.dwa; tr.J = B.J; tr.D = B.S;
-                    CK(timed(h, TK_PROJ, [&] { return launch_project_df(W, tr, &W.pout[1 + nxt]); }));
-                    // A'pi at the trial point and, in the epilogue, vt = v + t dv and
-                    // g = vt - A'pi with |g|^2 (speculative: kept if the trial is accepted)
-                    GradOut go;
-                    go.v = W.v; go.dv = W.dv; go.t = t; go.g = W.tmpq; go.vt = W.vt;
-                    CK(timed(h, TK_RMATVEC, [&] {
-                        return launch_rmatvec_df(W, W.dw, W.dwa, B.S, &W.pout[1 + nxt].s, W.atp, W.atpa, W.atp2,
-                                                 W.atpa2, 1, go);
-                    }));
-                } else {
-                    ProjIn tr;
-                    tr.a = W.pb[cur].u; tr.b = W.dz; tr.c1 = -t * sigma; tr.c2 = 0.0;
-                    tr.sums = SF_PSID | SF_DPA; tr.alpha = W.alpha; tr.pi_base = W.pb[cur].pi;
-                    tr.lam0 = &W.pout[1 + cur].lam;
-                    tr.u_out = B.u; tr.pi_out = B.pi; tr.wpi_out = B.wpi; tr.J = B.J; tr.S = B.S;
-                    CK(timed(h, TK_PROJ, [&] { return launch_project(W, tr, &W.pout[1 + nxt]); }));
-                    CK(timed(h, TK_RMATVEC, [&] {
-                        return launch_rmatvec(W, B.pi, B.wpi, B.S, &W.pout[1 + nxt].s, W.atp2, 1);
-                    }));
-                    grad_at_kernel<<<1, 1024, 0, W.st>>>(q, W.v, W.dv, t, W.atp2, W.tmpq, W.red);
-                    ++W.nlaunch;
-                    CK(cudaGetLastError());
-                }
-                if ((st = sync_read(h)) != SVM_OK) return st;
-                const double slope = W.h_red[2], vdv = W.h_red[3], dvdv = W.h_red[4];
-                const double dpsi = t * vdv + 0.5 * t * t * dvdv + W.h_pout[1 + nxt].sum[1] / (2.0 * sigma);
-                if (h->trace)
-                    fprintf(stderr, "[svm]   trial t=%.3g dpsi=%.3e slope=%.3e passes=%d cg=%g cg_res=%.2e\n", t, dpsi,
-                            slope, W.h_pout[1 + nxt].passes, W.h_red[12], W.h_red[13]);
-                if (dpsi <= P.mu * t * slope) { accepted = true; break; }
-                t *= P.delta;
-            }
-            if (!accepted) break;   // line search failed: the subproblem ends at the current point
+        } else {
+            ProjIn in;
+            in.a = W.alpha; in.b = W.z; in.c1 = -sigma; in.c2 = sigma;
+            in.sums = SF_DPA; in.alpha = W.alpha;
+            in.lam0 = &W.pout[1 + cur].lam;
+            in.u_out = B.u; in.pi_out = B.pi; in.wpi_out = B.wpi; in.J = B.J; in.S = B.S;
+            CK(timed(h, TK_PROJ, [&] { return launch_project(W, in, &W.pout[1 + cur]); }));
+            // g = v - A'pi (eq. (3.10) in q coordinates) and its roundoff scale
+            CK(timed(h, TK_RMATVEC, [&] { return launch_rmatvec(W, B.pi, B.wpi, B.S, &W.pout[1 + cur].s, W.atp, 1); }));
+            CK(launch_grad(W));
+        }
+        return readback_issue(h);
+    }
+    case RP_NEWTON:
+        // Step 2: Armijo line search from t = 1
+        r.t = 1.0;
+        r.mtr = 0;
+        return issue_trial(r);
+    case RP_TRIAL:
+        return issue_trial(r);
+    case RP_OUTER_END:
+        if ((st = df ? kkt_project_df(h, W.alphaw) : kkt_project(h, W.alpha)) != SVM_OK) return st;
+        return readback_issue(h);
+    case RP_FINISH: {
+        // results: alpha, w = A'alpha, b = lambda of the KKT projection, objective,
+        // primal objective, gap, counts
+        const long long n = W.n;
+        const int q = (int)W.q;
+        if (df) CK(join_vector(W, W.alphaw, true, W.alpha));
+        cudaMemcpyKind kd = host_mem ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+        CK(cudaMemcpyAsync(r.res->alpha, W.alpha, n * sizeof(double), kd, W.st));
+        CK(cudaMemcpyAsync(r.res->w, W.w, q * sizeof(double), kd, W.st));
+        CK(cudaMemsetAsync(W.red + 8, 0, 3 * sizeof(double), W.st));
+        count_kernel<<<W.nsm * 2, 256, 0, W.st>>>(n, W.alpha, W.C, W.red + 8);
+        ++W.nlaunch;
+        CK(cudaGetLastError());
+        r.hw.resize((size_t)q);
+        CK(cudaMemcpyAsync(r.hw.data(), W.w, q * sizeof(double), cudaMemcpyDeviceToHost, W.st));
+        CK(cudaMemcpyAsync(W.h_red, W.red, 16 * sizeof(double), cudaMemcpyDeviceToHost, W.st));
+        return SVM_OK;
+    }
+    case RP_DONE:
+        return SVM_OK;
+    }
+    return SVM_OK;
+}
+
+// Algorithm 3's stopping test at the current point (host only): either
+// another Newton step or the end of the subproblem.
+static svm_status inner_check(Run &r)
+{
+    svm_ssnalm *h = r.h;
+    Work &W = h->W;
+    const svm_params &P = h->P;
+    const ProjOut &m = W.h_pout[1 + r.cur];
+    const double gn = sqrt(W.h_red[0]);
+    const double dx = sqrt(m.sum[0]);
+    const double tol_in = fmin(r.epsk, r.epsk * dx) / sqrt(r.sigma);
+    const double floor_g = (W.df ? 32e-15 : 1e-15) * sqrt(W.h_red[1]);
+    if (!isfinite(gn)) { h->err = "non-finite gradient"; return SVM_ERR_NUMERIC; }
+    if (h->trace)
+        fprintf(stderr, "[svm] k=%d j=%d sigma=%.3g p=%lld s=%lld |g|=%.3e tol=%.3e passes=%d lam=%.6g\n", r.k, r.j,
+                r.sigma, (long long)m.p, (long long)m.s, gn, fmax(tol_in, floor_g), m.passes, m.lam);
+    if (gn <= fmax(tol_in, floor_g) || r.j >= P.max_inner) {
+        r.inner_total += r.j;
+        r.ph = RP_OUTER_END;
+    } else {
+        r.ph = RP_NEWTON;
+    }
+    return SVM_OK;
+}
+
+// After the synchronisation that ends a phase: read its scalars and choose
+// the next phase.
+static svm_status run_after(Run &r)
+{
+    svm_ssnalm *h = r.h;
+    Work &W = h->W;
+    const svm_params &P = h->P;
+    svm_status st;
+    if (r.ph == RP_FINISH) {
+        svm_result *res = r.res;
+        const ProjOut &kk = W.h_pout[SLOT_KKT];
+        double wsq = 0.0;
+        for (double x : r.hw) wsq += x * x;
+        res->kkt = kkt_value(kk);
+        res->b = kk.lam;
+        res->objective = 0.5 * wsq - kk.sum[2];
+        res->primal_objective = 0.5 * wsq + W.C * kk.sum[3];
+        res->gap = res->primal_objective + res->objective;
+        res->sigma = r.sigma;
+        res->outer_iters = r.k;
+        res->inner_iters_total = r.inner_total;
+        res->status = r.status;
+        res->n_free = (int64_t)W.h_red[8];
+        res->n_upper = (int64_t)W.h_red[9];
+        res->n_sv = (int64_t)W.h_red[10];
+        if (r.status != SVM_OK && h->err.empty()) h->err = "iteration cap reached";
+        r.ret = r.status;
+        r.ph = RP_DONE;
+        return SVM_OK;
+    }
+    if ((st = readback_check(h)) != SVM_OK) return st;
+    switch (r.ph) {
+    case RP_INIT:
+        r.R = kkt_value(W.h_pout[SLOT_KKT]);
+        r.Rprev = r.R;
+        r.k = 0;
+        r.inner_total = 0;
+        if (r.R <= P.tol) {
+            r.status = SVM_OK;
+            r.ph = RP_FINISH;
+        } else {
+            r.ph = RP_SUBSTART;
+        }
+        return SVM_OK;
+    case RP_SUBSTART:
+        r.j = 0;
+        return inner_check(r);
+    case RP_NEWTON:
+    case RP_TRIAL: {
+        const int nxt = 1 - r.cur;
+        const double t = r.t;
+        const double slope = W.h_red[2], vdv = W.h_red[3], dvdv = W.h_red[4];
+        const double dpsi = t * vdv + 0.5 * t * t * dvdv + W.h_pout[1 + nxt].sum[1] / (2.0 * r.sigma);
+        if (h->trace)
+            fprintf(stderr, "[svm]   trial t=%.3g dpsi=%.3e slope=%.3e passes=%d cg=%g cg_res=%.2e\n", t, dpsi, slope,
+                    W.h_pout[1 + nxt].passes, W.h_red[12], W.h_red[13]);
+        if (dpsi <= P.mu * t * slope) {
             // Step 3 (z = A v is not read again before it is recomputed after the
             // inner loop: the trials project from the accepted point's u)
-            if (df) {
+            if (W.df) {
                 std::swap(W.v, W.vt);   // v + t dv, formed by the trial's epilogue
             } else {
                 CK(launch_vaxpy(W, t));
@@ -677,70 +910,353 @@ extern "C" svm_status svm_ssnalm_solve(svm_ssnalm_t *h, const double *alpha0, sv
             std::swap(W.g, W.tmpq);     // the gradient at the accepted trial
             std::swap(W.atp, W.atp2);   // A'pi of the accepted trial
             std::swap(W.atpa, W.atpa2);
-            cur = nxt;
+            r.cur = nxt;
+            ++r.j;
+            return inner_check(r);
         }
-        inner_total += j;
-        // alpha^{k+1} = Pi(u(w^{k+1}))  (eq. (3.5)): the buffer holding pi becomes
-        // alpha (the old alpha buffer takes its place); A'alpha^{k+1} is the last A'pi
-        if (df) std::swap(W.alphaw, W.pb[cur].wpi);
-        else std::swap(W.alpha, W.pb[cur].pi);
-        std::swap(W.w, W.atp);   // the next subproblem forms A'pi afresh into the other buffer
-        // Q alpha = A w for the KKT test and z = A v for the next subproblem, one pass
-        CK(timed(h, TK_MATVEC, [&] {
-            return df ? launch_matvec_df(W, W.w, W.qaf, W.v, W.zf) : launch_matvec(W, W.w, W.qa, W.v, W.z);
-        }));
-        if ((st = df ? kkt_project_df(h, W.alphaw) : kkt_project(h, W.alpha)) != SVM_OK) return st;
-        if ((st = sync_read(h)) != SVM_OK) return st;
-        R = kkt_value(W.h_pout[SLOT_KKT]);
-        if (h->trace)
-            fprintf(stderr, "[svm] outer k=%d inner=%d R_KKT=%.3e sigma=%.3g kkt_passes=%d\n", k, j, R, sigma,
-                    W.h_pout[SLOT_KKT].passes);
-        if (!isfinite(R)) { status = SVM_ERR_NUMERIC; h->err = "non-finite KKT residual"; break; }
-        if (R <= P.tol) { status = SVM_OK; ++k; break; }
-        if (R > 0.5 * Rprev) sigma = fmin(P.sigma_max, P.sigma_growth * sigma);
-        Rprev = R;
+        r.t *= P.delta;
+        if (++r.mtr < P.max_ls) {
+            r.ph = RP_TRIAL;
+        } else {
+            // line search failed: the subproblem ends at the current point
+            r.inner_total += r.j;
+            r.ph = RP_OUTER_END;
+        }
+        return SVM_OK;
     }
-    // results: alpha, w = A'alpha, b = lambda of the KKT projection, objective,
-    // primal objective, gap, counts
-    const ProjOut &kk = W.h_pout[SLOT_KKT];
-    {
-        if (df) CK(join_vector(W, W.alphaw, true, W.alpha));
-        cudaMemcpyKind kd = host_mem ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
-        CK(cudaMemcpyAsync(res->alpha, W.alpha, n * sizeof(double), kd, W.st));
-        CK(cudaMemcpyAsync(res->w, W.w, q * sizeof(double), kd, W.st));
-        CK(cudaMemsetAsync(W.red + 8, 0, 3 * sizeof(double), W.st));
-        count_kernel<<<W.nsm * 2, 256, 0, W.st>>>(n, W.alpha, W.C, W.red + 8);
-        ++W.nlaunch;
-        CK(cudaGetLastError());
-        double *hw = (double *)malloc(q * sizeof(double));
-        if (!hw) { h->err = "host allocation failed"; return SVM_ERR_OOM; }
-        cudaError_t e1 = cudaMemcpyAsync(hw, W.w, q * sizeof(double), cudaMemcpyDeviceToHost, W.st);
-        cudaError_t e2 = cudaMemcpyAsync(W.h_red, W.red, 16 * sizeof(double), cudaMemcpyDeviceToHost, W.st);
-        cudaError_t e3 = cudaStreamSynchronize(W.st);
-        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
-            free(hw);
-            h->err = "result copy failed";
-            return SVM_ERR_CUDA;
+    case RP_OUTER_END:
+        r.R = kkt_value(W.h_pout[SLOT_KKT]);
+        if (h->trace)
+            fprintf(stderr, "[svm] outer k=%d inner=%d R_KKT=%.3e sigma=%.3g kkt_passes=%d\n", r.k, r.j, r.R, r.sigma,
+                    W.h_pout[SLOT_KKT].passes);
+        if (!isfinite(r.R)) {
+            r.status = SVM_ERR_NUMERIC;
+            h->err = "non-finite KKT residual";
+            r.ph = RP_FINISH;
+            return SVM_OK;
         }
-        double wsq = 0.0;
-        for (int jj = 0; jj < q; ++jj) wsq += hw[jj] * hw[jj];
-        free(hw);
-        res->kkt = kkt_value(kk);
-        res->b = kk.lam;
-        res->objective = 0.5 * wsq - kk.sum[2];
-        res->primal_objective = 0.5 * wsq + W.C * kk.sum[3];
-        res->gap = res->primal_objective + res->objective;
-        res->sigma = sigma;
-        res->outer_iters = k;
-        res->inner_iters_total = inner_total;
-        res->status = status;
-        res->n_free = (int64_t)W.h_red[8];
-        res->n_upper = (int64_t)W.h_red[9];
-        res->n_sv = (int64_t)W.h_red[10];
+        if (r.R <= P.tol) {
+            r.status = SVM_OK;
+            ++r.k;
+            r.ph = RP_FINISH;
+            return SVM_OK;
+        }
+        if (r.R > 0.5 * r.Rprev) r.sigma = fmin(P.sigma_max, P.sigma_growth * r.sigma);
+        r.Rprev = r.R;
+        ++r.k;
+        r.ph = r.k < P.max_outer ? RP_SUBSTART : RP_FINISH;
+        return SVM_OK;
+    default:
+        return SVM_OK;
+    }
+}
+
+// Start a run: checks, then the degenerate case or the first phase.
+static svm_status run_begin(Run &r, svm_ssnalm *h, const double *alpha0, svm_result *res)
+{
+    r = Run();
+    r.h = h;
+    r.alpha0 = alpha0;
+    r.res = res;
+    h->err.clear();
+    if (h->npos == 0 || h->npos == h->W.n) return run_degenerate(r);
+    r.ph = RP_INIT;
+    return SVM_OK;
+}
+
+extern "C" svm_status svm_ssnalm_solve(svm_ssnalm_t *h, const double *alpha0, svm_result *res)
+{
+    if (!h) return SVM_ERR_INVALID_ARG;
+    if (!res || !res->alpha || !res->w) { h->err = "result buffers must be non-null"; return SVM_ERR_INVALID_ARG; }
+    Run r;
+    svm_status st = run_begin(r, h, alpha0, res);
+    if (st != SVM_OK) return st;
+    while (r.ph != RP_DONE) {
+        if ((st = run_pre(r)) != SVM_OK) return st;
+        if ((st = run_matvec_single(r)) != SVM_OK) return st;
+        if ((st = run_post(r)) != SVM_OK) return st;
+        CK(cudaStreamSynchronize(h->W.st));
+        h->syncs++;
+        if (h->timing) flush_timing(h);
+        if ((st = run_after(r)) != SVM_OK) return st;
+    }
+    return r.ret;
+}
+
+// ------------------------------------------------------------ batched solves
+
+// Per-problem label checks: cnt[2b] = invalid labels, cnt[2b + 1] = +1 labels.
+__global__ void batch_labels_kernel(const int8_t *__restrict__ Y, long long n, int *cnt)
+{
+    const int8_t *y = Y + (long long)blockIdx.y * n;
+    int bad = 0, pos = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int8_t v = y[i];
+        bad += (v != 1 && v != -1);
+        pos += (v == 1);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        bad += __shfl_xor_sync(0xffffffffu, bad, o);
+        pos += __shfl_xor_sync(0xffffffffu, pos, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (bad) atomicAdd(cnt + 2 * blockIdx.y, bad);
+        if (pos) atomicAdd(cnt + 2 * blockIdx.y + 1, pos);
+    }
+}
+
+// Severity order of per-problem outcomes for the batch's return value.
+static int status_rank(svm_status st)
+{
+    if (st == SVM_OK) return 0;
+    if (st == SVM_ERR_DEGENERATE) return 1;
+    if (st == SVM_ERR_NOT_CONVERGED) return 2;
+    return 3;
+}
+
+static const int kMvTile[4] = {1, 2, 4, 8};
+constexpr int kMvPlanMax = 16;
+
+// Autotuner of the batched forward product: time one pass over X with 1, 2,
+// 4 and 8 vectors (CUDA events, after a warm-up) and plan, for every count
+// c <= 16 of products, the split into passes of minimum measured time
+// (dynamic programming); larger counts take whole passes of the tile with
+// the lowest time per vector first.  The split changes no result: each
+// product is bit-identical whatever tile it runs in.
+static svm_status tune_batch_matvec(svm_ssnalm *h)
+{
+    Work &W = h->W;
+    const long long n = W.n;
+    const int q = (int)W.q;
+    double *vs = nullptr;
+    float2 *zs = nullptr;
+    CK(cudaMalloc(&vs, sizeof(double) * 8 * q));
+    if (cudaMalloc(&zs, sizeof(float2) * 8 * n) != cudaSuccess) {
+        cudaFree(vs);
+        h->err = "autotuner scratch allocation failed";
+        return SVM_ERR_OOM;
+    }
+    cudaMemsetAsync(vs, 0, sizeof(double) * 8 * q, W.st);
+    MvItem it[8];
+    for (int k = 0; k < 8; ++k) it[k] = MvItem{vs + (size_t)k * q, zs + (size_t)k * n, W.y};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaError_t err = cudaSuccess;
+    for (int ti = 0; ti < 4 && err == cudaSuccess; ++ti) {
+        const int nv = kMvTile[ti];
+        err = launch_matvec_df_multi(W, it, nv, nv);   // warm-up
+        cudaEventRecord(e0, W.st);
+        for (int r = 0; r < 3 && err == cudaSuccess; ++r) err = launch_matvec_df_multi(W, it, nv, nv);
+        cudaEventRecord(e1, W.st);
+        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+        h->mv_ms[ti] = ms / 3.f;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(vs);
+    cudaFree(zs);
+    if (err != cudaSuccess) {
+        h->err = std::string("autotuner: ") + cudaGetErrorString(err);
+        return SVM_ERR_CUDA;
+    }
+    std::vector<double> cost(kMvPlanMax + 1, 0.0);
+    h->mv_plan.assign(kMvPlanMax + 1, 1);
+    for (int c = 1; c <= kMvPlanMax; ++c) {
+        cost[c] = 1e300;
+        for (int ti = 0; ti < 4; ++ti) {
+            const int nv = kMvTile[ti];
+            if (nv > c) break;
+            const double cc = h->mv_ms[ti] + cost[c - nv];
+            if (cc < cost[c]) { cost[c] = cc; h->mv_plan[c] = nv; }
+        }
+    }
+    h->mv_tuned = true;
+    return SVM_OK;
+}
+
+// All forward products of a lockstep phase in as few passes over X as the plan says.
+static svm_status batch_matvec(svm_ssnalm *h, std::vector<MvItem> &items)
+{
+    Work &W = h->W;
+    int best = 0;
+    for (int ti = 1; ti < 4; ++ti)
+        if (h->mv_ms[ti] / kMvTile[ti] < h->mv_ms[best] / kMvTile[best]) best = ti;
+    size_t at = 0;
+    while (at < items.size()) {
+        const int left = (int)(items.size() - at);
+        const int nv = left > kMvPlanMax ? kMvTile[best] : h->mv_plan[left];
+        CK(timed(h, TK_MATVEC, [&] { return launch_matvec_df_multi(W, items.data() + at, nv, nv); }));
+        at += (size_t)nv;
+    }
+    return SVM_OK;
+}
+
+extern "C" svm_status svm_ssnalm_solve_batch(svm_ssnalm_t *h, int32_t B, const int8_t *Y, const double *C,
+                                             double *alpha, double *w, svm_result *results)
+{
+    if (!h) return SVM_ERR_INVALID_ARG;
+    h->err.clear();
+    if (B < 1 || !Y || !C || !alpha || !w || !results) {
+        h->err = "batch: B >= 1 and non-null Y, C, alpha, w, results required";
+        return SVM_ERR_INVALID_ARG;
+    }
+    for (int b = 0; b < B; ++b)
+        if (!(C[b] > 0.0) || !isfinite(C[b])) { h->err = "batch: every C must be finite and > 0"; return SVM_ERR_INVALID_ARG; }
+    Work &W = h->W;
+    if (W.csr) { h->err = "batch: dense X only"; return SVM_ERR_UNSUPPORTED; }
+    const long long n = W.n;
+    const int q = (int)W.q;
+    const bool host_mem = h->prob.memory == SVM_MEM_HOST;
+    // device copies of the labels and device outputs
+    if (B > h->bat_cap) {
+        void *bp[] = {h->bat_cnt, h->bat_y, h->bat_a, h->bat_w};
+        for (void *p : bp)
+            if (p) cudaFree(p);
+        h->bat_cnt = nullptr; h->bat_y = nullptr; h->bat_a = nullptr; h->bat_w = nullptr;
+        h->bat_cap = 0;
+        if (cudaMalloc(&h->bat_cnt, sizeof(int) * 2 * B) != cudaSuccess ||
+            (host_mem && (cudaMalloc(&h->bat_y, (size_t)B * n) != cudaSuccess ||
+                          cudaMalloc(&h->bat_a, sizeof(double) * B * n) != cudaSuccess ||
+                          cudaMalloc(&h->bat_w, sizeof(double) * B * q) != cudaSuccess))) {
+            h->err = "batch: device allocation failed";
+            return SVM_ERR_OOM;
+        }
+        h->bat_cap = B;
+    }
+    const int8_t *Yd = Y;
+    double *Ad = alpha, *Wd = w;
+    if (host_mem) {
+        CK(cudaMemcpyAsync(h->bat_y, Y, (size_t)B * n, cudaMemcpyHostToDevice, W.st));
+        Yd = h->bat_y;
+        Ad = h->bat_a;
+        Wd = h->bat_w;
+    }
+    CK(cudaMemsetAsync(h->bat_cnt, 0, sizeof(int) * 2 * B, W.st));
+    batch_labels_kernel<<<dim3(2, B), 256, 0, W.st>>>(Yd, n, h->bat_cnt);
+    ++W.nlaunch;
+    CK(cudaGetLastError());
+    std::vector<int> cnt((size_t)2 * B);
+    CK(cudaMemcpyAsync(cnt.data(), h->bat_cnt, sizeof(int) * 2 * B, cudaMemcpyDeviceToHost, W.st));
+    CK(cudaStreamSynchronize(W.st));
+    for (int b = 0; b < B; ++b)
+        if (cnt[2 * b]) { h->err = "batch: labels must be +1 or -1"; return SVM_ERR_INVALID_ARG; }
+    // one sub-handle per problem: X borrowed from this handle, its own y, C and workspace
+    while ((int)h->subs.size() < B) {
+        svm_problem pr = h->prob;
+        pr.memory = SVM_MEM_DEVICE;
+        pr.X = W.X;
+        pr.y = Yd;
+        svm_params pa = h->P;
+        pa.C = 1.0;
+        svm_ssnalm *sb = nullptr;
+        const svm_status st = create_impl(&sb, &pr, &pa, false);
+        if (st != SVM_OK) { h->err = "batch: " + g_create_err; return st; }
+        h->subs.push_back(sb);
+    }
+    const bool batched_mv = W.df;
+    if (batched_mv && !h->mv_tuned) {
+        const svm_status st = tune_batch_matvec(h);
+        if (st != SVM_OK) return st;
+    }
+    std::vector<svm_result> res((size_t)B);
+    std::vector<Run> runs((size_t)B);
+    std::vector<long long> launch0((size_t)B);
+    int active = 0;
+    for (int b = 0; b < B; ++b) {
+        svm_ssnalm *sb = h->subs[b];
+        Work &S = sb->W;
+        S.y = Yd + (size_t)b * n;
+        sb->prob.y = S.y;
+        S.C = C[b];
+        sb->P = h->P;
+        sb->P.C = C[b];
+        sb->npos = cnt[2 * b + 1];
+        sb->trace = h->trace;
+        sb->timing = h->timing;
+        launch0[b] = S.nlaunch;
+        res[b] = svm_result();
+        res[b].alpha = Ad + (size_t)b * n;
+        res[b].w = Wd + (size_t)b * q;
+        const svm_status st = run_begin(runs[b], sb, nullptr, &res[b]);
+        if (st != SVM_OK) { runs[b].ret = st; runs[b].ph = RP_DONE; res[b].status = st; }
+        if (runs[b].ph != RP_DONE) ++active;
+    }
+    // lockstep: every active problem advances one phase per synchronisation
+    std::vector<MvItem> items;
+    std::vector<char> live((size_t)B);
+    auto fail_run = [&](int b, svm_status st) {
+        runs[b].ret = st;
+        runs[b].ph = RP_DONE;
+        res[b].status = st;
+        live[b] = 0;
+        --active;
+    };
+    while (active > 0) {
+        items.clear();
+        for (int b = 0; b < B; ++b) {
+            live[b] = runs[b].ph != RP_DONE;
+            if (!live[b]) continue;
+            svm_status st = run_pre(runs[b]);
+            if (st != SVM_OK) { fail_run(b, st); continue; }
+            if (batched_mv) {
+                const MvReq &m = runs[b].mv;
+                for (int k = 0; k < m.nv; ++k) items.push_back(MvItem{m.v[k], m.zf[k], h->subs[b]->W.y});
+            } else if ((st = run_matvec_single(runs[b])) != SVM_OK) {
+                fail_run(b, st);
+            }
+        }
+        if (!items.empty()) {
+            const svm_status st = batch_matvec(h, items);
+            if (st != SVM_OK) return st;
+        }
+        for (int b = 0; b < B; ++b) {
+            if (!live[b]) continue;
+            const svm_status st = run_post(runs[b]);
+            if (st != SVM_OK) fail_run(b, st);
+        }
+        CK(cudaStreamSynchronize(W.st));
+        h->syncs++;
+        h->batch_ticks++;
+        for (int b = 0; b < B; ++b) {
+            if (!live[b]) continue;
+            svm_ssnalm *sb = h->subs[b];
+            if (sb->timing) flush_timing(sb);
+            const svm_status st = run_after(runs[b]);
+            if (st != SVM_OK) { fail_run(b, st); continue; }
+            if (runs[b].ph == RP_DONE) --active;
+        }
     }
     if (h->timing) flush_timing(h);
-    if (status != SVM_OK && h->err.empty()) h->err = "iteration cap reached";
-    return status;
+    if (host_mem) {
+        CK(cudaMemcpyAsync(alpha, Ad, sizeof(double) * B * n, cudaMemcpyDeviceToHost, W.st));
+        CK(cudaMemcpyAsync(w, Wd, sizeof(double) * B * q, cudaMemcpyDeviceToHost, W.st));
+        CK(cudaStreamSynchronize(W.st));
+    }
+    // results, and the problems' launches and step counts folded into this handle's counters
+    svm_status worst = SVM_OK;
+    for (int b = 0; b < B; ++b) {
+        svm_ssnalm *sb = h->subs[b];
+        results[b] = res[b];
+        results[b].alpha = alpha + (size_t)b * n;
+        results[b].w = w + (size_t)b * q;
+        const svm_status st = runs[b].ret;
+        results[b].status = st;
+        if (status_rank(st) > status_rank(worst)) {
+            worst = st;
+            h->err = "batch problem " + std::to_string(b) + ": " + sb->err;
+        }
+        W.nlaunch += sb->W.nlaunch - launch0[b];
+        for (int k = 0; k < 4; ++k) {
+            h->kcalls[k] += sb->kcalls[k];
+            h->kms[k] += sb->kms[k];
+            sb->kcalls[k] = 0;
+            sb->kms[k] = 0.0;
+        }
+    }
+    return worst;
 }
 
 // ------------------------------------------------------------ step-level ops
