@@ -228,6 +228,29 @@ cudaError_t launch_negcopy(Work &W, const double *g, double *dv); // dv = -g
 // when p_host < 0); with dots, also red[2] = g'dv, red[3] = v'dv, red[4] = dv'dv.
 cudaError_t launch_newton(Work &W, const int32_t *J, long long p_host, const long long *p_dev,
                           double sigma, const double *g, double *dv, bool dots = false);
+// One Newton step of the mixed form with a small free set (q <= 128): the
+// exact double-float Gram of the p rows J split over ks blocks (partials in
+// part/hpart), M = I + sigma (G - h h'/p) into Mf, and the preconditioned CG
+// for dv with the Armijo dot products (rdots[2..4], v = vdot; info = red + 12).
+// newton_task fills one for W (returns false when the step takes another
+// path: FP64 form, CSR, q > 128, p = 0 or the matrix-free large-p step);
+// launch_newton_batch runs ntask of them (table in device memory) in three
+// launches, each problem's arithmetic identical to launch_newton's.
+struct NewtonTask {
+    const int32_t *J;
+    long long p;
+    int ks, maxit;
+    float2 *part, *hpart, *Mf;
+    float2 pinv, sig;
+    float eta, tau;
+    const double *g;
+    double *dv, *info, *rdots;
+    int *err;
+    const double *vdot;
+};
+bool newton_task(const Work &W, const int32_t *J, long long p, double sigma, const double *g, double *dv, bool dots,
+                 NewtonTask *t);
+cudaError_t launch_newton_batch(Work &W, const NewtonTask *T_dev, int ntask, int ks_max);
 // workspace of the large-free-set Newton solve (mixed form, FP32 X, q <= 128)
 cudaError_t newton_mf_alloc(Work &W);
 // Gram of the rows J on the tcgen05 tensor cores (k_umma.cu): per block b of

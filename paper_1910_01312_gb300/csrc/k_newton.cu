@@ -163,9 +163,9 @@ __global__ void __launch_bounds__(1024) chol_solve_kernel(int q, double *__restr
 
 // Gram of FP32 rows with exact products (TwoProd) and double-float sums
 // (TwoSum) on the FP32 pipes; same tiling and outputs as gram_kernel.
-__global__ void __launch_bounds__(256) gram_df_kernel(const float *__restrict__ X, int q, const int32_t *__restrict__ J,
-                                                      long long p, int KS, float2 *__restrict__ part,
-                                                      float2 *__restrict__ hpart, long long stride)
+__device__ __forceinline__ void gram_df_body(const float *__restrict__ X, int q, const int32_t *__restrict__ J,
+                                             long long p, int KS, float2 *__restrict__ part,
+                                             float2 *__restrict__ hpart, long long stride)
 {
     int t = blockIdx.x;
     int ti = 0;
@@ -232,11 +232,29 @@ __global__ void __launch_bounds__(256) gram_df_kernel(const float *__restrict__ 
     }
 }
 
+__global__ void __launch_bounds__(256) gram_df_kernel(const float *__restrict__ X, int q, const int32_t *__restrict__ J,
+                                                      long long p, int KS, float2 *__restrict__ part,
+                                                      float2 *__restrict__ hpart, long long stride)
+{
+    gram_df_body(X, q, J, p, KS, part, hpart, stride);
+}
+
+// The same for a batch of Newton steps (one per problem, blockIdx.z); blocks
+// beyond a problem's own split count return at once.
+__global__ void __launch_bounds__(256) gram_df_batch_kernel(const float *__restrict__ X, int q,
+                                                            const NewtonTask *__restrict__ T)
+{
+    const NewtonTask &t = T[blockIdx.z];
+    if ((int)blockIdx.y >= t.ks) return;
+    gram_df_body(X, q, t.J, t.p, t.ks, t.part, t.hpart, 1);
+}
+
 // M = I + sigma (G - h h' / p) from the double-float split-K partials of
 // gram_df_kernel, summed in block order in double-float; written as the
 // (hi, lo) pair Mf of the CG operator (and the factor's input).
-__global__ void build_m_df_kernel(int q, int KS, const float2 *__restrict__ part, const float2 *__restrict__ hpart,
-                                  float2 pinv, float2 sig, float2 *__restrict__ Mf)
+__device__ __forceinline__ void build_m_df_body(int q, int KS, const float2 *__restrict__ part,
+                                                const float2 *__restrict__ hpart, float2 pinv, float2 sig,
+                                                float2 *__restrict__ Mf)
 {
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)q * q;
          e += (long long)gridDim.x * blockDim.x) {
@@ -253,6 +271,18 @@ __global__ void build_m_df_kernel(int q, int KS, const float2 *__restrict__ part
         Mf[(size_t)a * q + b] = m;
         Mf[(size_t)b * q + a] = m;
     }
+}
+
+__global__ void build_m_df_kernel(int q, int KS, const float2 *__restrict__ part, const float2 *__restrict__ hpart,
+                                  float2 pinv, float2 sig, float2 *__restrict__ Mf)
+{
+    build_m_df_body(q, KS, part, hpart, pinv, sig, Mf);
+}
+
+__global__ void build_m_df_batch_kernel(int q, const NewtonTask *__restrict__ T)
+{
+    const NewtonTask &t = T[blockIdx.z];
+    build_m_df_body(q, t.ks, t.part, t.hpart, t.pinv, t.sig, t.Mf);
 }
 
 __device__ __forceinline__ double block_dot(const double *a, const double *b, int q, double *red)
@@ -743,12 +773,11 @@ __device__ bool cg_load_factor(CgSmem &S, int q, const float2 *__restrict__ Mf, 
     return true;
 }
 
-__global__ void __launch_bounds__(kCgThreads) newton_cg_fast_kernel(int q, const float2 *__restrict__ Mf,
-                                                                    const double *__restrict__ g,
-                                                                    double *__restrict__ dv, float eta, float tau,
-                                                                    int maxit, double *__restrict__ info, int *err,
-                                                                    const double *__restrict__ vdot,
-                                                                    double *__restrict__ rdots)
+__device__ __forceinline__ void newton_cg_fast_body(int q, const float2 *__restrict__ Mf,
+                                                    const double *__restrict__ g, double *__restrict__ dv,
+                                                    float eta, float tau, int maxit, double *__restrict__ info,
+                                                    int *err, const double *__restrict__ vdot,
+                                                    double *__restrict__ rdots)
 {
     extern __shared__ float4 cg_sm4[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
@@ -873,6 +902,23 @@ __global__ void __launch_bounds__(kCgThreads) newton_cg_fast_kernel(int q, const
             rdots[4] = (double)d2.x + (double)d2.y;
         }
     }
+}
+
+__global__ void __launch_bounds__(kCgThreads) newton_cg_fast_kernel(int q, const float2 *__restrict__ Mf,
+                                                                    const double *__restrict__ g,
+                                                                    double *__restrict__ dv, float eta, float tau,
+                                                                    int maxit, double *__restrict__ info, int *err,
+                                                                    const double *__restrict__ vdot,
+                                                                    double *__restrict__ rdots)
+{
+    newton_cg_fast_body(q, Mf, g, dv, eta, tau, maxit, info, err, vdot, rdots);
+}
+
+// One block per problem of a batch (blockIdx.x).
+__global__ void __launch_bounds__(kCgThreads) newton_cg_fast_batch_kernel(int q, const NewtonTask *__restrict__ T)
+{
+    const NewtonTask &t = T[blockIdx.x];
+    newton_cg_fast_body(q, t.Mf, t.g, t.dv, t.eta, t.tau, t.maxit, t.info, t.err, t.vdot, t.rdots);
 }
 
 // ---------------------------------------------------------------------------
@@ -1416,6 +1462,78 @@ static cudaError_t launch_newton_mf(Work &W, const int32_t *J, long long p, doub
     return cudaGetLastError();
 }
 
+// Split-K count of the Gram of p gathered rows (~32 rows per block, bounded
+// by the partials' workspace; one split per SM for double-float partials).
+static long long gram_splits(const Work &W, long long p, bool mixed)
+{
+    const int q = (int)W.q;
+    long long ks = (p + 31) / 32;
+    int KSmax = (int)(W.part_len / ((size_t)q * q + q));
+    if (KSmax > 4 * W.nsm) KSmax = 4 * W.nsm;
+    if (ks > KSmax) ks = KSmax;
+    if (mixed && ks > W.nsm) ks = W.nsm;
+    if (ks < 1) ks = 1;
+    return ks;
+}
+
+bool newton_task(const Work &W, const int32_t *J, long long p, double sigma, const double *g, double *dv, bool dots,
+                 NewtonTask *t)
+{
+    const int q = (int)W.q;
+    const bool mixed = W.precision == 1 && W.xf32;
+    if (W.csr || !mixed || q > kCgMaxQ || p <= 0) return false;
+    if (W.mf_st && q % 4 == 0 && p > kMfMinP) return false;
+    const long long ks = gram_splits(W, p, true);
+    t->J = J;
+    t->p = p;
+    t->ks = (int)ks;
+    t->maxit = W.cg_maxit;
+    t->part = reinterpret_cast<float2 *>(W.part);
+    t->hpart = reinterpret_cast<float2 *>(W.part + (size_t)ks * q * q);
+    t->Mf = W.Mf;
+    t->pinv = split2(1.0 / (double)p);
+    t->sig = split2(sigma);
+    t->eta = (float)W.eta;
+    t->tau = (float)W.tau;
+    t->g = g;
+    t->dv = dv;
+    t->info = W.red + 12;
+    t->rdots = W.red;
+    t->err = W.err;
+    t->vdot = dots ? W.v : nullptr;
+    return true;
+}
+
+static cudaError_t cg_fast_attr()
+{
+    if (!g_cgs_attr) {
+        cudaError_t ea = cudaFuncSetAttribute(newton_cg_fast_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)cg_fast_smem(kCgMaxQ));
+        if (ea == cudaSuccess)
+            ea = cudaFuncSetAttribute(newton_cg_fast_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)cg_fast_smem(kCgMaxQ));
+        if (ea != cudaSuccess) return ea;
+        g_cgs_attr = 1;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_newton_batch(Work &W, const NewtonTask *T_dev, int ntask, int ks_max)
+{
+    const int q = (int)W.q;
+    if (ntask < 1) return cudaSuccess;
+    const int nt = (q + kGT - 1) / kGT;
+    const int ntiles = nt * (nt + 1) / 2;
+    const cudaError_t ea = cg_fast_attr();
+    if (ea != cudaSuccess) return ea;
+    gram_df_batch_kernel<<<dim3(ntiles, (unsigned)ks_max, (unsigned)ntask), 256, 0, W.st>>>((const float *)W.X, q,
+                                                                                             T_dev);
+    build_m_df_batch_kernel<<<dim3(W.nsm * 2, 1, (unsigned)ntask), 256, 0, W.st>>>(q, T_dev);
+    newton_cg_fast_batch_kernel<<<ntask, kCgThreads, cg_fast_smem(q), W.st>>>(q, T_dev);
+    W.nlaunch += 3;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_newton(Work &W, const int32_t *J, long long p_host, const long long *p_dev, double sigma,
                           const double *g, double *dv, bool dots)
 {
@@ -1425,6 +1543,23 @@ cudaError_t launch_newton(Work &W, const int32_t *J, long long p_host, const lon
     if (p_host <= 0) {
         const cudaError_t e = launch_negcopy(W, g, dv);
         return (e == cudaSuccess && dots) ? launch_dots(W) : e;
+    }
+    {
+        // mixed form, small free set: the three kernels of a NewtonTask
+        NewtonTask t;
+        if (newton_task(W, J, p_host, sigma, g, dv, dots, &t)) {
+            const int nt = (q + kGT - 1) / kGT;
+            const int ntiles = nt * (nt + 1) / 2;
+            const cudaError_t ea = cg_fast_attr();
+            if (ea != cudaSuccess) return ea;
+            gram_df_kernel<<<dim3(ntiles, (unsigned)t.ks), 256, 0, W.st>>>((const float *)W.X, q, J, p_host, t.ks,
+                                                                            t.part, t.hpart, 1);
+            build_m_df_kernel<<<W.nsm * 2, 256, 0, W.st>>>(q, t.ks, t.part, t.hpart, t.pinv, t.sig, t.Mf);
+            newton_cg_fast_kernel<<<1, kCgThreads, cg_fast_smem(q), W.st>>>(q, t.Mf, t.g, t.dv, t.eta, t.tau, t.maxit,
+                                                                            t.info, t.err, t.vdot, t.rdots);
+            W.nlaunch += 3;
+            return cudaGetLastError();
+        }
     }
     const int nt = (q + kGT - 1) / kGT;
     const int ntiles = nt * (nt + 1) / 2;

@@ -66,6 +66,8 @@ struct svm_ssnalm {
     double *bat_a = nullptr, *bat_w = nullptr;
     int bat_cap = 0;
     long long batch_ticks = 0;
+    NewtonTask *nt_host = nullptr, *nt_dev = nullptr;   // batched Newton steps (pinned / device table)
+    int nt_cap = 0;
 };
 
 enum { TK_MATVEC = 0, TK_RMATVEC = 1, TK_PROJ = 2, TK_NEWTON = 3 };
@@ -177,9 +179,10 @@ extern "C" void svm_ssnalm_destroy(svm_ssnalm_t *h)
     if (h->W.st) cudaStreamSynchronize(h->W.st);
     for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
     for (svm_ssnalm *sb : h->subs) svm_ssnalm_destroy(sb);
-    void *bp[] = {h->bat_cnt, h->bat_y, h->bat_a, h->bat_w};
+    void *bp[] = {h->bat_cnt, h->bat_y, h->bat_a, h->bat_w, h->nt_dev};
     for (void *p : bp)
         if (p) cudaFree(p);
+    if (h->nt_host) cudaFreeHost(h->nt_host);
     free_work(h->W);
     delete h;
 }
@@ -552,6 +555,9 @@ struct Run {
     svm_status ret = SVM_OK;                     // return value once done
     MvReq mv;
     std::vector<double> hw;                      // w on the host (results)
+    bool defer_newton = false;   // batched: leave a small-free-set Newton step to the batch launch
+    bool has_task = false;       // ... and this phase's step was left there
+    NewtonTask task;
 };
 
 static void mv_add(Work &W, MvReq &m, const double *v, float2 *zf, double *z)
@@ -650,6 +656,7 @@ static svm_status run_pre(Run &r)
     const int q = (int)W.q;
     const bool df = W.df;
     r.mv = MvReq();
+    r.has_task = false;
     switch (r.ph) {
     case RP_INIT: {
         // lambda warm starts restart at 0
@@ -711,9 +718,14 @@ static svm_status run_pre(Run &r)
         const long long p = W.h_pout[1 + r.cur].p;
         const double sigma = r.sigma;
         const int cur = r.cur;
-        CK(timed(h, TK_NEWTON, [&] {
-            return launch_newton(W, W.pb[cur].J, p, &W.pout[1 + cur].p, sigma, W.g, W.dv, true);
-        }));
+        r.has_task = r.defer_newton && newton_task(W, W.pb[cur].J, p, sigma, W.g, W.dv, true, &r.task);
+        if (r.has_task) {
+            h->kcalls[TK_NEWTON]++;
+        } else {
+            CK(timed(h, TK_NEWTON, [&] {
+                return launch_newton(W, W.pb[cur].J, p, &W.pout[1 + cur].p, sigma, W.g, W.dv, true);
+            }));
+        }
         mv_add(W, r.mv, W.dv, W.dzf, W.dz);
         return SVM_OK;
     }
@@ -1161,6 +1173,19 @@ extern "C" svm_status svm_ssnalm_solve_batch(svm_ssnalm_t *h, int32_t B, const i
         const svm_status st = tune_batch_matvec(h);
         if (st != SVM_OK) return st;
     }
+    if (B > h->nt_cap) {
+        if (h->nt_dev) cudaFree(h->nt_dev);
+        if (h->nt_host) cudaFreeHost(h->nt_host);
+        h->nt_dev = nullptr;
+        h->nt_host = nullptr;
+        h->nt_cap = 0;
+        if (cudaMalloc(&h->nt_dev, sizeof(NewtonTask) * B) != cudaSuccess ||
+            cudaMallocHost(&h->nt_host, sizeof(NewtonTask) * B) != cudaSuccess) {
+            h->err = "batch: allocation of the Newton task table failed";
+            return SVM_ERR_OOM;
+        }
+        h->nt_cap = B;
+    }
     std::vector<svm_result> res((size_t)B);
     std::vector<Run> runs((size_t)B);
     std::vector<long long> launch0((size_t)B);
@@ -1181,6 +1206,7 @@ extern "C" svm_status svm_ssnalm_solve_batch(svm_ssnalm_t *h, int32_t B, const i
         res[b].alpha = Ad + (size_t)b * n;
         res[b].w = Wd + (size_t)b * q;
         const svm_status st = run_begin(runs[b], sb, nullptr, &res[b]);
+        runs[b].defer_newton = true;
         if (st != SVM_OK) { runs[b].ret = st; runs[b].ph = RP_DONE; res[b].status = st; }
         if (runs[b].ph != RP_DONE) ++active;
     }
@@ -1207,6 +1233,18 @@ extern "C" svm_status svm_ssnalm_solve_batch(svm_ssnalm_t *h, int32_t B, const i
             } else if ((st = run_matvec_single(runs[b])) != SVM_OK) {
                 fail_run(b, st);
             }
+        }
+        // the small-free-set Newton steps of all problems: three launches
+        int ntask = 0, ks_max = 0;
+        for (int b = 0; b < B; ++b) {
+            if (!live[b] || !runs[b].has_task) continue;
+            h->nt_host[ntask++] = runs[b].task;
+            if (runs[b].task.ks > ks_max) ks_max = runs[b].task.ks;
+        }
+        if (ntask > 0) {
+            CK(cudaMemcpyAsync(h->nt_dev, h->nt_host, sizeof(NewtonTask) * ntask, cudaMemcpyHostToDevice, W.st));
+            CK(timed(h, TK_NEWTON, [&] { return launch_newton_batch(W, h->nt_dev, ntask, ks_max); }));
+            h->kcalls[TK_NEWTON]--;   // counted per problem when the steps were deferred
         }
         if (!items.empty()) {
             const svm_status st = batch_matvec(h, items);
