@@ -6,6 +6,11 @@ two-Gaussian workload n = 1,000,000 x q = 128 FP32, C = 0.1 (means
 +-0.3/sqrt(q) 1, covariance diag(linspace(0.1, 2, q)), 10% labels flipped),
 plus the achieved HBM bandwidth of the forward product A v against the
 measured copy bandwidth.  One "step" is one whole solve from alpha = 0.
+The line also carries the plain FP64 form's time on the same problem, the
+end-to-end time through the C ABI with host buffers, the oracle on a bounded
+sample (cpu_baseline), and a batched leg: 160 SVMs sharing one X (ten
+one-vs-rest classes x sixteen C values) solved in lockstep by
+svm_ssnalm_solve_batch against the same problems solved one by one.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -31,6 +36,7 @@ METRIC = "time-to-KKT<=1e-6 per SVM solve"
 N_FULL = 1_000_000
 N_CPU_SAMPLE = 50_000      # oracle sample for the cpu_baseline leg (~10-30 s)
 N_REF_SAMPLE = 20_000      # oracle sample per step of the reference arm
+BATCH_N, BATCH_Q, BATCH_CLASSES, BATCH_NC = 100_000, 128, 10, 16   # the batched (one-vs-rest x C path) leg
 
 
 def _peaks():
@@ -142,6 +148,53 @@ def run_reference(args, rank, world):
     return 0
 
 
+def run_batched(args, P, torch, datagen, sptr, stream, rank):
+    """B = classes x C values problems over one X (datagen.ovr_path): the
+    lockstep batched solve (svm_ssnalm_solve_batch, second call: sub-handles
+    and the autotuner's plan exist) against the same problems solved one by
+    one on handles created beforehand, both timed with CUDA events."""
+    n, q = args.batch_n, args.batch_q
+    X, Y, Cs = datagen.ovr_path(seed=rank, n=n, q=q, n_classes=BATCH_CLASSES, n_C=BATCH_NC)
+    B = len(Cs)
+    Xd = torch.from_numpy(X).cuda()
+    Yd = torch.from_numpy(Y).cuda()
+    A = torch.zeros((B, n), dtype=torch.float64, device="cuda")
+    W = torch.zeros((B, q), dtype=torch.float64, device="cuda")
+    s = P.Solver(Xd, Yd[0], C_=1.0, tol=1e-6, precision=P.PREC_MIXED, stream=sptr)
+    s.solve_batch(Yd, Cs, A, W)          # creates the sub-handles, runs the autotuner
+    s.stats(reset=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    st, rs = s.solve_batch(Yd, Cs, A, W)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_batch = e0.elapsed_time(e1)
+    sb = s.stats(reset=True)
+    s.close()
+    singles = [P.Solver(Xd, Yd[b], C_=float(Cs[b]), tol=1e-6, precision=P.PREC_MIXED, stream=sptr)
+               for b in range(B)]
+    a1 = torch.zeros(n, dtype=torch.float64, device="cuda")
+    w1 = torch.zeros(q, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    e0.record(stream)
+    same = 0
+    for b in range(B):
+        r1 = singles[b].solve(a1, w1)
+        same += int(r1["objective"] == rs[b]["objective"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_seq = e0.elapsed_time(e1)
+    for sg in singles:
+        sg.close()
+    return {"workload": (f"ovr_path: n={n} x q={q} FP32 (80% zeros, U[0,1]), {BATCH_CLASSES} one-vs-rest classes "
+                         f"(Dirichlet(0.5) proportions) x {BATCH_NC} C values 1e-3..1e2 = {B} problems"),
+            "ms_batch": t_batch, "ms_one_by_one": t_seq, "speedup": t_seq / t_batch,
+            "ms_per_problem": t_batch / B, "all_ok": all(r["status"] == P.OK for r in rs),
+            "max_kkt": max(r["kkt"] for r in rs), "identical_objectives": same,
+            "host_syncs": int(sb["host_syncs"]), "gpu_launches": int(sb["launches"])}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -151,6 +204,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-n", type=int, default=BATCH_N)
+    ap.add_argument("--batch-q", type=int, default=BATCH_Q)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -227,7 +283,7 @@ def main():
     achieved = alg_bytes / (mv_ms * 1e-3) / 1e9
     traffic = _traffic(os.path.join(ROOT, "paper_1910_01312_gb300", "csrc", "k_matvec.cu"), "matvec_gauss1m")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic, "kernel": "matvec_kernel (z = A v)",
+                "frac": achieved / peak, "traffic": traffic, "kernel": "matvec_mx_kernel (z = A v, Dot2 sums, double-float z)",
                 "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": mv_ms,
                 "launches_per_step": st["matvec_calls"] / args.steps, "peak_source": f"{peak_kind} hbm_gbs"}
     breakdown = {k: st[k] / args.steps for k in ("matvec_ms", "rmatvec_ms", "proj_ms", "newton_ms")}
@@ -275,6 +331,13 @@ def main():
     e2e = {"value": e2e_ms / world, "unit": "ms", "h2d_bytes_per_step": int(X.nbytes + y.nbytes),
            "d2h_bytes_per_step": int(8 * n + 8 * q)}
 
+    # ---- batched: one-vs-rest classes x a C path sharing one X, lockstep vs one by one ----
+    batched = None
+    if not args.no_batch:
+        del Xd, yd
+        torch.cuda.empty_cache()
+        batched = run_batched(args, P, torch, datagen, sptr, stream, rank)
+
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1) ----
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -294,7 +357,7 @@ def main():
                 "clocks": clk,
                 "solve": {"outer": r["outer_iters"], "inner": r["inner_iters_total"], "kkt": r["kkt"],
                           "objective": r["objective"], "n_free": r["n_free"], "n_upper": r["n_upper"]},
-                "plain_fp64": plain, "per_step": breakdown}
+                "plain_fp64": plain, "per_step": breakdown, "batched": batched}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()

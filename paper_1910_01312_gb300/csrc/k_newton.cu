@@ -285,237 +285,6 @@ __global__ void build_m_df_batch_kernel(int q, const NewtonTask *__restrict__ T)
     build_m_df_body(q, t.ks, t.part, t.hpart, t.pinv, t.sig, t.Mf);
 }
 
-__device__ __forceinline__ double block_dot(const double *a, const double *b, int q, double *red)
-{
-    double s = 0.0;
-    for (int j = threadIdx.x; j < q; j += blockDim.x) s = fma(a[j], b[j], s);
-    s = warp_sum(s);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-    __syncthreads();
-    double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-    __syncthreads();
-    return t;
-}
-
-// z = (L L')^{-1} r with the FP32 factor L (row stride ld), by warp 0:
-// lane l owns rows l, l+32, ...  (q <= 32 * kMaxRows)
-template <int kMaxRows>
-__device__ void chol_apply_warp(const float *L, const float *rdiag, int ld, int q, const double *r, double *z)
-{
-    const int lane = threadIdx.x & 31;
-    float b[kMaxRows];
-    const int nr = (q + 31) / 32;
-#pragma unroll
-    for (int m = 0; m < kMaxRows; ++m) b[m] = (m < nr && lane + 32 * m < q) ? (float)r[lane + 32 * m] : 0.f;
-    // forward: L y = b
-    for (int k = 0; k < q; ++k) {
-        const int own = k & 31, km = k >> 5;
-        float yk = 0.f;
-#pragma unroll
-        for (int m = 0; m < kMaxRows; ++m)
-            if (m == km) yk = b[m];
-        yk = __shfl_sync(0xffffffffu, yk, own) * rdiag[k];
-#pragma unroll
-        for (int m = 0; m < kMaxRows; ++m) {
-            const int i = lane + 32 * m;
-            if (m < nr && i > k && i < q) b[m] -= L[(size_t)i * ld + k] * yk;
-            if (m == km && lane == own) b[m] = yk;
-        }
-    }
-    // backward: L' x = y
-    for (int k = q - 1; k >= 0; --k) {
-        const int own = k & 31, km = k >> 5;
-        float xk = 0.f;
-#pragma unroll
-        for (int m = 0; m < kMaxRows; ++m)
-            if (m == km) xk = b[m];
-        xk = __shfl_sync(0xffffffffu, xk, own) * rdiag[k];
-#pragma unroll
-        for (int m = 0; m < kMaxRows; ++m) {
-            const int i = lane + 32 * m;
-            if (m < nr && i < k) b[m] -= L[(size_t)k * ld + i] * xk;
-            if (m == km && lane == own) b[m] = xk;
-        }
-    }
-#pragma unroll
-    for (int m = 0; m < kMaxRows; ++m)
-        if (m < nr && lane + 32 * m < q) z[lane + 32 * m] = (double)b[m];
-}
-
-// One block: FP32 Cholesky of fl32(M) (diagonal shift on breakdown) as the
-// preconditioner of a conjugate-gradient solve of M dv = -g -- the CG of
-// Algorithm 3, Step 1 -- stopped at |M dv + g| <= max(min(eta, |g|^{1+tau},
-// 1e-10 |g|), 1e-14 |g|) or after maxit steps.  The paper's bound min(eta,
-// |g|^{1+tau}) caps the residual; the 1e-10 |g| cap makes the step as exact as
-// a direct solve (the next gradient is this residual when J does not change),
-// at about one extra step, since each step gains ~6 digits with this
-// preconditioner.  The operator is applied in double-float
-// from the (hi, lo) FP32 split of M (relative accuracy ~2^-44, like FP64)
-// so that the one SM doing the solve never waits on the FP64 pipe.
-// Factorisation: right-looking, 32-wide panels: warp 0 factors the diagonal
-// block, one thread per row solves the panel, all threads update the
-// trailing matrix; three block barriers per panel.
-// SMEM: the factor lives in shared memory, else in Lg (row stride q + 1).
-// info[0] = CG steps, info[1] = final residual norm, info[2] = shift used.
-template <bool SMEM, int NR>
-__global__ void __launch_bounds__(1024) newton_pcg_kernel(int q, const double *__restrict__ M,
-                                                          const float2 *__restrict__ Mf, float *__restrict__ Lg,
-                                                          const double *__restrict__ g, double *__restrict__ dv,
-                                                          double eta, double tau, int maxit, double *__restrict__ info,
-                                                          int *err)
-{
-    extern __shared__ double dsm2[];
-    double *x = dsm2, *r = x + q, *z = r + q, *pp = z + q, *Ap = pp + q, *rold = Ap + q;
-    float2 *pf = reinterpret_cast<float2 *>(rold + q);   // df copy of pp
-    const int ld = q + 1;
-    float *L = SMEM ? reinterpret_cast<float *>(pf + q) : Lg;
-    __shared__ double red[32];
-    __shared__ int bad;
-    __shared__ float rdiag[1024];   // 1 / L_jj of the final factor (q <= 1024)
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-    // largest diagonal entry (block reduction), scale of the breakdown shift
-    double md = 0.0;
-    for (int j = tid; j < q; j += nt) md = fmax(md, (double)Mf[(size_t)j * q + j].x);
-    md = warp_max(md);
-    if (lane == 0) red[warp] = md;
-    __syncthreads();
-    double maxdiag = 0.0;
-    for (int w = 0; w < nw; ++w) maxdiag = fmax(maxdiag, red[w]);
-    __syncthreads();
-    float shift = 0.f;
-    for (int attempt = 0; attempt < 6; ++attempt) {
-        for (int i = warp; i < q; i += nw)
-            for (int j = lane; j <= i; j += 32) L[(size_t)i * ld + j] = Mf[(size_t)i * q + j].x + (i == j ? shift : 0.f);
-        if (tid == 0) bad = 0;
-        __syncthreads();
-        for (int kb = 0; kb < q; kb += 32) {
-            const int nb = (q - kb) < 32 ? (q - kb) : 32;
-            // (1) diagonal block, warp 0, lane i owns row kb + i
-            if (warp == 0) {
-                for (int j = 0; j < nb; ++j) {
-                    const float d = L[(size_t)(kb + j) * ld + kb + j];
-                    const bool okp = (d > 0.f) && isfinite(d);
-                    const float rs = okp ? rsqrtf(d) : 1.f;
-                    if (!okp && lane == 0) bad = 1;
-                    __syncwarp();
-                    if (lane > j && lane < nb) L[(size_t)(kb + lane) * ld + kb + j] *= rs;
-                    if (lane == j) { L[(size_t)(kb + j) * ld + kb + j] = okp ? d * rs : 1.f; rdiag[kb + j] = rs; }
-                    __syncwarp();
-                    if (lane > j && lane < nb) {
-                        const float lij = L[(size_t)(kb + lane) * ld + kb + j];
-                        for (int k = j + 1; k <= lane; ++k)
-                            L[(size_t)(kb + lane) * ld + kb + k] -= lij * L[(size_t)(kb + k) * ld + kb + j];
-                    }
-                    __syncwarp();
-                }
-            }
-            __syncthreads();
-            if (bad) break;
-            // (2) panel rows below the block: x L_b' = a, one thread per row
-            for (int i = kb + nb + tid; i < q; i += nt) {
-                float *row = L + (size_t)i * ld + kb;
-                for (int j = 0; j < nb; ++j) {
-                    float v = row[j];
-                    const float *lj = L + (size_t)(kb + j) * ld + kb;
-                    for (int m = 0; m < j; ++m) v -= row[m] * lj[m];
-                    row[j] = v * rdiag[kb + j];
-                }
-            }
-            __syncthreads();
-            // (3) trailing update, rows i = base + wy + 32a, columns k = base + wx + 32b, k <= i
-            const int base = kb + nb;
-            for (int i = base + warp; i < q; i += nw) {
-                const float *li = L + (size_t)i * ld + kb;
-                for (int k = base + lane; k <= i; k += 32) {
-                    const float *lk = L + (size_t)k * ld + kb;
-                    float acc = 0.f;
-#pragma unroll 8
-                    for (int m = 0; m < nb; ++m) acc = fmaf(li[m], lk[m], acc);
-                    L[(size_t)i * ld + k] -= acc;
-                }
-            }
-            __syncthreads();
-        }
-        __syncthreads();
-        if (!bad) break;
-        shift = (shift == 0.f) ? (float)(1e-7 * maxdiag) : shift * 100.f;
-        __syncthreads();
-    }
-    if (bad) {
-        if (tid == 0) set_err(err, DEV_CHOL);
-        return;
-    }
-    // CG on M dv = -g
-    for (int j = tid; j < q; j += nt) { x[j] = 0.0; r[j] = -g[j]; }
-    __syncthreads();
-    const double gn = sqrt(block_dot(r, r, q, red));
-    const double tol = fmax(fmin(fmin(eta, pow(gn, 1.0 + tau)), 1e-10 * gn), 1e-14 * gn);
-    if (tid < 32) chol_apply_warp<NR>(L, rdiag, ld, q, r, z);
-    __syncthreads();
-    for (int j = tid; j < q; j += nt) pp[j] = z[j];
-    __syncthreads();
-    double rz = block_dot(r, z, q, red);
-    double rn = gn;
-    int it = 0;
-    for (it = 0; it < maxit && rn > tol; ++it) {
-        for (int j = tid; j < q; j += nt) {
-            const float hi = (float)pp[j];
-            pf[j] = make_float2(hi, (float)(pp[j] - (double)hi));
-        }
-        __syncthreads();
-        // Ap = M p in double-float, warp per row
-        for (int i = warp; i < q; i += nw) {
-            float sh = 0.f, sc = 0.f;
-            const float2 *mrow = Mf + (size_t)i * q;
-            for (int j = lane; j < q; j += 32) {
-                const float2 a = mrow[j], b = pf[j];
-                float p0, e0, sn, t0;
-                two_prod(a.x, b.x, p0, e0);
-                e0 = fmaf(a.x, b.y, fmaf(a.y, b.x, e0));
-                two_sum(sh, p0, sn, t0);
-                sh = sn;
-                sc += t0 + e0;
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const float s2 = __shfl_xor_sync(0xffffffffu, sh, o), c2 = __shfl_xor_sync(0xffffffffu, sc, o);
-                float sn, e;
-                two_sum(sh, s2, sn, e);
-                e += sc + c2;
-                sh = sn + e;
-                sc = e - (sh - sn);
-            }
-            if (lane == 0) Ap[i] = (double)sh + (double)sc;
-        }
-        __syncthreads();
-        const double pAp = block_dot(pp, Ap, q, red);
-        if (!(pAp > 0.0)) break;
-        const double al = rz / pAp;
-        for (int j = tid; j < q; j += nt) {
-            x[j] = fma(al, pp[j], x[j]);
-            rold[j] = r[j];
-            r[j] = fma(-al, Ap[j], r[j]);
-        }
-        __syncthreads();
-        rn = sqrt(block_dot(r, r, q, red));
-        if (rn <= tol) { ++it; break; }
-        if (tid < 32) chol_apply_warp<NR>(L, rdiag, ld, q, r, z);
-        __syncthreads();
-        // flexible (Polak-Ribiere) beta: robust to the FP32 preconditioner
-        const double rz_new = block_dot(r, z, q, red);
-        const double rz_old = block_dot(rold, z, q, red);
-        const double beta = fmax(0.0, (rz_new - rz_old) / rz);
-        rz = rz_new;
-        for (int j = tid; j < q; j += nt) pp[j] = fma(beta, pp[j], z[j]);
-        __syncthreads();
-    }
-    for (int j = tid; j < q; j += nt) dv[j] = x[j];
-    if (tid == 0 && info) { info[0] = it; info[1] = rn; info[2] = shift; }
-    (void)M;
-}
-
 // ---- one-block dense SPD solver for q <= 200 (factor in shared memory) ----
 // L (FP32, row stride ld = q + 1, lower triangle) and rdiag = 1 / diag(L).
 // ---------------------------------------------------------------------------
@@ -679,15 +448,16 @@ __device__ __forceinline__ float2 cg_dot(const float2 *a, const float2 *b, int q
 // diagonal shift is added and the factor retried when a pivot is not
 // positive).  Block-uniform result; false (err set) when the copy or the
 // factor failed.  *sc_shift (shared) receives the shift used.
-__device__ bool cg_load_factor(CgSmem &S, int q, const float2 *__restrict__ Mf, int *err, float *sc_shift)
+__device__ bool cg_load_factor(CgSmem &S, int q, const float2 *__restrict__ Mf, int *err, float *sc_shift, int ld = -1)
 {
+    if (ld < 0) ld = q;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     const int qp = (q + 31) & ~31, nb = qp / kPb;
     __shared__ float sc_maxdiag;
     __shared__ int bad, copy_ok;
     __shared__ __align__(8) unsigned long long mbar;
     // M into shared memory: one bulk copy when its rows need no padding
-    if (q == qp) {
+    if (q == qp && ld == q) {
         if (tid == 0) {
             mbar_init(&mbar, 1);
             mbar_fence_init();
@@ -700,7 +470,7 @@ __device__ bool cg_load_factor(CgSmem &S, int q, const float2 *__restrict__ Mf, 
     } else {
         for (int i = warp; i < qp; i += nw)
             for (int j = lane; j < qp; j += 32)
-                S.M[i * qp + j] = (i < q && j < q) ? Mf[(size_t)i * q + j] : make_float2(0.f, 0.f);
+                S.M[i * qp + j] = (i < q && j < q) ? Mf[(size_t)i * ld + j] : make_float2(0.f, 0.f);
         if (tid == 0) copy_ok = 1;
     }
     if (tid == 0) *sc_shift = 0.f;
@@ -919,6 +689,177 @@ __global__ void __launch_bounds__(kCgThreads) newton_cg_fast_batch_kernel(int q,
 {
     const NewtonTask &t = T[blockIdx.x];
     newton_cg_fast_body(q, t.Mf, t.g, t.dv, t.eta, t.tau, t.maxit, t.info, t.err, t.vdot, t.rdots);
+}
+
+// ---------------------------------------------------------------------------
+// Newton solve for 128 < q <= 1024 (Algorithm 3, Step 1, on the reduced system
+// of Proposition 3.5): conjugate gradients on M dv = -g with the operator in
+// double-float from the (hi, lo) split of M, preconditioned by the FP32
+// Cholesky factors of M's diagonal 128 x 128 blocks (block Jacobi).  One
+// cooperative launch of G blocks: block b < ceil(q/128) factors diagonal
+// block b in its shared memory (the same 8-wide panel factor as the q <= 128
+// kernel) and applies it; every block computes a share of the rows of M p.
+// The q-vectors are replicated in every block's shared memory and updated
+// identically (every block forms the dot products in the same fixed order),
+// so each step needs only two grid barriers: after M p and after the
+// preconditioned residual are written to global memory.  Stop rule as the
+// q <= 128 kernel (Algorithm 3's bound, tightened to 1e-10 |g|), at most
+// maxit steps.  On a failed factor (after diagonal shifts) or a barrier that
+// timed out, every block leaves at the next barrier with err set.
+constexpr int kBjBlk = 128;
+constexpr int kBjMaxQ = 1024;
+
+// sum_j a_j b_j, j < q <= kBjMaxQ, double-float, fixed order; every thread of
+// the block returns the same value (and every block, given equal inputs)
+__device__ __forceinline__ float2 bj_dot(const float2 *a, const float2 *b, int q, float2 *red)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    float2 s = make_float2(0.f, 0.f);
+    for (int j = tid; j < q; j += blockDim.x) s = dfx_add(s, dfx_mul(a[j], b[j]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s = dfx_add(s, shfl_xor_f2(s, o));
+    if (lane == 0) red[warp] = s;
+    __syncthreads();
+    float2 t = red[0];
+    for (int w = 1; w < nw; ++w) t = dfx_add(t, red[w]);
+    __syncthreads();
+    return t;
+}
+
+__global__ void __launch_bounds__(kCgThreads) newton_bj_kernel(int q, const float2 *__restrict__ Mf,
+                                                               const double *__restrict__ g, double *__restrict__ dv,
+                                                               float eta, float tau, int maxit,
+                                                               double *__restrict__ info, int *err,
+                                                               const double *__restrict__ vdot,
+                                                               double *__restrict__ rdots, float2 *__restrict__ xch,
+                                                               unsigned *bar)
+{
+    extern __shared__ float4 cg_sm4[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int nblk = (q + kBjBlk - 1) / kBjBlk;
+    const int b = blockIdx.x;
+    const int ob = b * kBjBlk;
+    const int qb = b < nblk ? (q - ob < kBjBlk ? q - ob : kBjBlk) : 0;
+    const int qpb = (qb + 31) & ~31;
+    CgSmem S;   // laid out for a 128 x 128 block whatever qb is
+    S.M = reinterpret_cast<float2 *>(cg_sm4);
+    S.L = reinterpret_cast<float *>(S.M + kBjBlk * kBjBlk);
+    S.D = S.L + ((kBjBlk * (kBjBlk + 1)) >> 1);
+    S.t = S.D + (kBjBlk / kPb) * kPb * kPb;
+    __shared__ float2 red[kCgThreads / 32];
+    __shared__ float sc_shift;
+    float2 *apg = xch, *zg = xch + kBjMaxQ;   // exchange buffers in global memory
+    // phase A: factor the diagonal blocks (a failed factor sets err)
+    if (b < nblk) cg_load_factor(S, qb, Mf + (size_t)ob * q + ob, err, &sc_shift, q);
+    if (!grid_barrier(bar, err)) return;
+    if (ld_relaxed_i32(err)) return;
+    // replicated vectors where the copy of the block's M was
+    float2 *X = S.M, *R = X + kBjMaxQ, *P = R + kBjMaxQ, *RO = P + kBjMaxQ, *Z = RO + kBjMaxQ, *AP = Z + kBjMaxQ;
+    for (int j = tid; j < q; j += blockDim.x) {
+        const double v = -g[j];
+        const float hi = (float)v;
+        R[j] = make_float2(hi, (float)(v - (double)hi));
+        X[j] = make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    float2 rr = bj_dot(R, R, q, red);
+    const float gn = sqrtf(fmaxf(rr.x, 0.f));
+    const float tol = fmaxf(fminf(fminf(eta, powf(gn, 1.f + tau)), 1e-10f * gn), 1e-14f * gn);
+    const float tol2 = tol * tol;
+    // z = blockdiag(L_b L_b')^{-1} r, every block's segment through global memory
+    auto precond = [&]() -> bool {
+        if (b < nblk) {
+            for (int j = tid; j < qpb; j += blockDim.x) S.t[j] = j < qb ? R[ob + j].x + R[ob + j].y : 0.f;
+            __syncthreads();
+            cg_precond(S, qpb);
+            for (int j = tid; j < qb; j += blockDim.x) zg[ob + j] = make_float2(S.t[j], 0.f);
+        }
+        if (!grid_barrier(bar, err)) return false;
+        for (int j = tid; j < q; j += blockDim.x) Z[j] = __ldcg(&zg[j]);
+        __syncthreads();
+        return true;
+    };
+    if (!precond()) return;
+    for (int j = tid; j < q; j += blockDim.x) P[j] = Z[j];
+    __syncthreads();
+    float2 rz = bj_dot(R, Z, q, red);
+    int it = 0;
+    bool go = rr.x > tol2;
+    const int gw = b * nw + warp, ngw = gridDim.x * nw;
+    while (go && it < maxit) {
+        // AP = M P: a warp per row, Dot2-style sums of double-float products
+        for (int i = gw; i < q; i += ngw) {
+            const float2 *mrow = Mf + (size_t)i * q;
+            float sh = 0.f, sc = 0.f;
+            for (int j = lane; j < q; j += 32) {
+                const float2 a = __ldg(&mrow[j]), b2 = P[j];
+                float p0, e0, sn, t0;
+                two_prod(a.x, b2.x, p0, e0);
+                e0 = fmaf(a.x, b2.y, fmaf(a.y, b2.x, e0));
+                two_sum(sh, p0, sn, t0);
+                sh = sn;
+                sc += t0 + e0;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float s2 = __shfl_xor_sync(0xffffffffu, sh, o), c2 = __shfl_xor_sync(0xffffffffu, sc, o);
+                float sn, e;
+                two_sum(sh, s2, sn, e);
+                sh = sn;
+                sc += e + c2;
+            }
+            if (lane == 0) { float hi, lo; two_sum(sh, sc, hi, lo); apg[i] = make_float2(hi, lo); }
+        }
+        if (!grid_barrier(bar, err)) return;
+        for (int j = tid; j < q; j += blockDim.x) AP[j] = __ldcg(&apg[j]);
+        __syncthreads();
+        const float2 pap = bj_dot(P, AP, q, red);
+        if (!(pap.x > 0.f)) break;
+        const float2 al = dfx_div(rz, pap);
+        for (int j = tid; j < q; j += blockDim.x) {
+            X[j] = dfx_add(X[j], dfx_mul(al, P[j]));
+            RO[j] = R[j];
+            R[j] = dfx_sub(R[j], dfx_mul(al, AP[j]));
+        }
+        __syncthreads();
+        ++it;
+        rr = bj_dot(R, R, q, red);
+        go = rr.x > tol2;
+        if (!go) break;
+        if (!precond()) return;
+        const float2 rzn = bj_dot(R, Z, q, red);
+        const float2 rzo = bj_dot(RO, Z, q, red);
+        float2 beta = dfx_div(dfx_sub(rzn, rzo), rz);
+        if (!(beta.x > 0.f)) beta = make_float2(0.f, 0.f);
+        rz = rzn;
+        for (int j = tid; j < q; j += blockDim.x) P[j] = dfx_add(Z[j], dfx_mul(beta, P[j]));
+        __syncthreads();
+    }
+    if (b != 0) return;
+    for (int j = tid; j < q; j += blockDim.x) dv[j] = (double)X[j].x + (double)X[j].y;
+    if (tid == 0 && info) {
+        info[0] = it;
+        info[1] = sqrt((double)fmaxf(rr.x, 0.f));
+        info[2] = sc_shift;
+    }
+    if (vdot) {
+        // Algorithm 3, Step 2 quantities: rdots[2] = g'dv, rdots[3] = v'dv, rdots[4] = dv'dv
+        for (int j = tid; j < q; j += blockDim.x) {
+            const double a = g[j], c = vdot[j];
+            const float ah = (float)a, ch = (float)c;
+            R[j] = make_float2(ah, (float)(a - (double)ah));
+            P[j] = make_float2(ch, (float)(c - (double)ch));
+        }
+        __syncthreads();
+        const float2 d0 = bj_dot(R, X, q, red);
+        const float2 d1 = bj_dot(P, X, q, red);
+        const float2 d2 = bj_dot(X, X, q, red);
+        if (tid == 0) {
+            rdots[2] = (double)d0.x + (double)d0.y;
+            rdots[3] = (double)d1.x + (double)d1.y;
+            rdots[4] = (double)d2.x + (double)d2.y;
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1534,6 +1475,42 @@ cudaError_t launch_newton_batch(Work &W, const NewtonTask *T_dev, int ntask, int
     return cudaGetLastError();
 }
 
+static int g_bj_attr = 0;
+
+// 128 < q <= 1024: the block-Jacobi CG above, one cooperative launch; the
+// exchange buffers of M p and z use the Gram partials' workspace (consumed by
+// build_m before this launch).
+static cudaError_t launch_newton_bj(Work &W, const double *g, double *dv, double *info, bool dots)
+{
+    const int q = (int)W.q;
+    if (q > kBjMaxQ || W.part_len * sizeof(double) < 2 * kBjMaxQ * sizeof(float2)) return cudaErrorInvalidValue;
+    const size_t smem = cg_fast_smem(kCgMaxQ);
+    if (!g_bj_attr) {
+        const cudaError_t ea =
+            cudaFuncSetAttribute(newton_bj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (ea != cudaSuccess) return ea;
+        g_bj_attr = 1;
+    }
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, newton_bj_kernel, kCgThreads, smem);
+    if (e != cudaSuccess) return e;
+    const int nblk = (q + kBjBlk - 1) / kBjBlk;
+    int G = (q + (kCgThreads / 32) - 1) / (kCgThreads / 32);   // one row of M p per warp
+    if (G < nblk) G = nblk;
+    if (G > occ * W.nsm) G = occ * W.nsm;
+    if (G < nblk) return cudaErrorInvalidConfiguration;
+    int qq = q, maxit = 4 * W.cg_maxit;
+    const float2 *Mf = W.Mf;
+    float eta = (float)W.eta, tau = (float)W.tau;
+    int *err = W.err;
+    const double *vd = dots ? W.v : nullptr;
+    double *rd = W.red;
+    float2 *xch = reinterpret_cast<float2 *>(W.part);
+    unsigned *bar = W.bar;
+    void *args[] = {&qq, &Mf, &g, &dv, &eta, &tau, &maxit, &info, &err, &vd, &rd, &xch, &bar};
+    return cudaLaunchCooperativeKernel((const void *)newton_bj_kernel, dim3(G), dim3(kCgThreads), args, smem, W.st);
+}
+
 cudaError_t launch_newton(Work &W, const int32_t *J, long long p_host, const long long *p_dev, double sigma,
                           const double *g, double *dv, bool dots)
 {
@@ -1612,13 +1589,8 @@ cudaError_t launch_newton(Work &W, const int32_t *J, long long p_host, const lon
                                                                     W.cg_maxit, info, W.err, dots ? W.v : nullptr,
                                                                     W.red);
             return cudaGetLastError();
-        } else {
-            const size_t vec = (size_t)6 * q * sizeof(double) + (size_t)q * sizeof(float2);
-            newton_pcg_kernel<false, 32><<<1, 1024, vec, W.st>>>(q, W.M, W.Mf, W.Lf, g, dv, W.eta, W.tau, W.cg_maxit,
-                                                                 info, W.err);
         }
-        const cudaError_t e = cudaGetLastError();
-        return (e == cudaSuccess && dots) ? launch_dots(W) : e;
+        return launch_newton_bj(W, g, dv, info, dots);
     }
     size_t smem = ((size_t)q * q + q) * sizeof(double);
     if (q <= 144) {

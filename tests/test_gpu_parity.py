@@ -167,6 +167,9 @@ def test_projection_flat_segment(kernel):
 @pytest.mark.parametrize("dtype,n,q,frac", [(np.float64, 400, 50, 0.3), (np.float32, 3000, 128, 0.2),
                                             (np.float32, 5000, 33, 0.01), (np.float64, 300, 150, 0.9),
                                             (np.float32, 20000, 128, 0.5),
+                                            # q > 128: block-Jacobi preconditioned CG (mixed form)
+                                            (np.float32, 6000, 784, 0.2), (np.float32, 3000, 256, 0.05),
+                                            (np.float32, 2000, 200, 0.6),
                                             # p = 210,000: the matrix-free large-free-set solve (mixed form)
                                             (np.float32, 420000, 128, 0.5)])
 def test_newton_direction(prec, gscale, dtype, n, q, frac):
