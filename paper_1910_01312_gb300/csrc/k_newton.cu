@@ -443,6 +443,61 @@ __device__ __forceinline__ float2 cg_dot(const float2 *a, const float2 *b, int q
     return t;
 }
 
+// In-place FP32 Cholesky of the packed qp x qp matrix in S.L (qp % 32 == 0,
+// rows beyond the problem set to the identity), right-looking by 8-column
+// panels; S.D receives the inverses of the 8 x 8 diagonal blocks.  Block-
+// uniform result: false when a pivot is not positive.
+__device__ bool cg_factor_packed(CgSmem &S, int qp)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int nb = qp / kPb;
+    __shared__ int bad;
+    if (tid == 0) bad = 0;
+    __syncthreads();
+    for (int b = 0; b < nb; ++b) {
+        const int kb = b * kPb;
+        if (warp == 0) {
+            const bool ok = cg_diag8(S.L, kb, S.D + b * kPb * kPb);
+            if (!ok && lane == 0) bad = 1;
+        }
+        __syncthreads();
+        if (bad || b + 1 == nb) break;
+        {   // rows below: L_rc = sum_k A_rk Dinv_b[c][k]; 4 rows per warp, 8 lanes a row
+            const int grp = lane >> 3, c = lane & 7;
+            const float *Db = S.D + b * kPb * kPb;
+            float dr[kPb];
+#pragma unroll
+            for (int k = 0; k < kPb; ++k) dr[k] = Db[c * kPb + k];
+            for (int r0 = kb + kPb + warp * 4; r0 < qp; r0 += nw * 4) {
+                const int r = r0 + grp;
+                const float av = (r < qp) ? S.L[lpos(r, kb + c)] : 0.f;
+                float acc = 0.f;
+#pragma unroll
+                for (int k = 0; k < kPb; ++k) acc = fmaf(__shfl_sync(0xffffffffu, av, grp * 8 + k), dr[k], acc);
+                if (r < qp) S.L[lpos(r, kb + c)] = acc;
+            }
+        }
+        __syncthreads();
+        // trailing triangle, a warp per row: A_rc -= sum_k L_rk L_ck, kb + 8 <= c <= r
+        for (int r = kb + kPb + warp; r < qp; r += nw) {
+            float lr[kPb];
+#pragma unroll
+            for (int k = 0; k < kPb; ++k) lr[k] = S.L[lpos(r, kb + k)];
+            for (int c = kb + kPb + lane; c <= r; c += 32) {
+                const int pc = lpos(c, kb);
+                float acc = 0.f;
+#pragma unroll
+                for (int k = 0; k < kPb; ++k) acc = fmaf(lr[k], S.L[pc + k], acc);
+                S.L[lpos(r, c)] -= acc;
+            }
+        }
+        __syncthreads();
+    }
+    const bool ok = !bad;
+    __syncthreads();
+    return ok;
+}
+
 // M (q x q double-float pairs) into S.M, zero padded to qp (one bulk copy when
 // q = qp), and the FP32 Cholesky factor of fl32(M) + shift into S.L / S.D (a
 // diagonal shift is added and the factor retried when a pivot is not
@@ -452,9 +507,9 @@ __device__ bool cg_load_factor(CgSmem &S, int q, const float2 *__restrict__ Mf, 
 {
     if (ld < 0) ld = q;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    const int qp = (q + 31) & ~31, nb = qp / kPb;
+    const int qp = (q + 31) & ~31;
     __shared__ float sc_maxdiag;
-    __shared__ int bad, copy_ok;
+    __shared__ int copy_ok;
     __shared__ __align__(8) unsigned long long mbar;
     // M into shared memory: one bulk copy when its rows need no padding
     if (q == qp && ld == q) {
@@ -490,49 +545,8 @@ __device__ bool cg_load_factor(CgSmem &S, int q, const float2 *__restrict__ Mf, 
         for (int i = warp; i < qp; i += nw)
             for (int j = lane; j <= i; j += 32)
                 S.L[lpos(i, j)] = (i < q) ? S.M[i * qp + j].x + (i == j ? shift : 0.f) : (i == j ? 1.f : 0.f);
-        if (tid == 0) bad = 0;
         __syncthreads();
-        for (int b = 0; b < nb; ++b) {
-            const int kb = b * kPb;
-            if (warp == 0) {
-                const bool ok = cg_diag8(S.L, kb, S.D + b * kPb * kPb);
-                if (!ok && lane == 0) bad = 1;
-            }
-            __syncthreads();
-            if (bad || b + 1 == nb) break;
-            {   // rows below: L_rc = sum_k A_rk Dinv_b[c][k]; 4 rows per warp, 8 lanes a row
-                const int grp = lane >> 3, c = lane & 7;
-                const float *Db = S.D + b * kPb * kPb;
-                float dr[kPb];
-#pragma unroll
-                for (int k = 0; k < kPb; ++k) dr[k] = Db[c * kPb + k];
-                for (int r0 = kb + kPb + warp * 4; r0 < qp; r0 += nw * 4) {
-                    const int r = r0 + grp;
-                    const float av = (r < qp) ? S.L[lpos(r, kb + c)] : 0.f;
-                    float acc = 0.f;
-#pragma unroll
-                    for (int k = 0; k < kPb; ++k) acc = fmaf(__shfl_sync(0xffffffffu, av, grp * 8 + k), dr[k], acc);
-                    if (r < qp) S.L[lpos(r, kb + c)] = acc;
-                }
-            }
-            __syncthreads();
-            // trailing triangle, a warp per row: A_rc -= sum_k L_rk L_ck, kb + 8 <= c <= r
-            for (int r = kb + kPb + warp; r < qp; r += nw) {
-                float lr[kPb];
-#pragma unroll
-                for (int k = 0; k < kPb; ++k) lr[k] = S.L[lpos(r, kb + k)];
-                for (int c = kb + kPb + lane; c <= r; c += 32) {
-                    const int pc = lpos(c, kb);
-                    float acc = 0.f;
-#pragma unroll
-                    for (int k = 0; k < kPb; ++k) acc = fmaf(lr[k], S.L[pc + k], acc);
-                    S.L[lpos(r, c)] -= acc;
-                }
-            }
-            __syncthreads();
-        }
-        okf = !bad;
-        __syncthreads();
+        okf = cg_factor_packed(S, qp);
         if (!okf && tid == 0) *sc_shift = (shift == 0.f) ? 1e-7f * sc_maxdiag : shift * 100.f;
         __syncthreads();
     }
@@ -695,23 +709,31 @@ __global__ void __launch_bounds__(kCgThreads) newton_cg_fast_batch_kernel(int q,
 // Newton solve for 128 < q <= 1024 (Algorithm 3, Step 1, on the reduced system
 // of Proposition 3.5): conjugate gradients on M dv = -g with the operator in
 // double-float from the (hi, lo) split of M, preconditioned by the FP32
-// Cholesky factors of M's diagonal 128 x 128 blocks (block Jacobi).  One
-// cooperative launch of G blocks: block b < ceil(q/128) factors diagonal
-// block b in its shared memory (the same 8-wide panel factor as the q <= 128
-// kernel) and applies it; every block computes a share of the rows of M p.
-// The q-vectors are replicated in every block's shared memory and updated
-// identically (every block forms the dot products in the same fixed order),
-// so each step needs only two grid barriers: after M p and after the
-// preconditioned residual are written to global memory.  Stop rule as the
-// q <= 128 kernel (Algorithm 3's bound, tightened to 1e-10 |g|), at most
-// maxit steps.  On a failed factor (after diagonal shifts) or a barrier that
-// timed out, every block leaves at the next barrier with err set.
-constexpr int kBjBlk = 128;
-constexpr int kBjMaxQ = 1024;
+// Cholesky factor of fl32(M) -- as the q <= 128 kernel, but factored by many
+// blocks at once.  One cooperative launch of G blocks:
+//  * factor, right-looking by 128-wide panels, three grid barriers a panel:
+//    block 0 factors the diagonal block in shared memory (the 8-wide panel
+//    code of the q <= 128 kernel; the inverses of its 8 x 8 diagonal blocks go
+//    to global memory for the triangular solves), every block then solves a
+//    share of the panel's rows (x L_kk' = a, a warp per row), and every block
+//    updates a share of the 64 x 64 tiles of the trailing lower triangle.  A
+//    pivot that is not positive restarts the factor with a diagonal shift
+//    (1e-7 max diag, then x100, at most six attempts; err = DEV_CHOL after).
+//  * CG: every block holds the q-vectors in shared memory and updates them
+//    identically (same dot products in the same order); the rows of M p are
+//    shared out and exchanged through global memory (one grid barrier), and
+//    block 0 applies (L L')^{-1} by 8-wide blocked triangular solves against
+//    the factor in global memory (one grid barrier to publish z).
+// Stop rule as the q <= 128 kernel (Algorithm 3's bound, tightened to 1e-10
+// |g|), at most maxit steps.  Every block takes the same barriers; on a
+// barrier that timed out (err = DEV_TIMEOUT) every block leaves.
+constexpr int kBcNb = 128;     // panel width of the blocked factor
+constexpr int kBcTile = 64;    // trailing-update tile
+constexpr int kBcMaxQ = 1024;
 
-// sum_j a_j b_j, j < q <= kBjMaxQ, double-float, fixed order; every thread of
+// sum_j a_j b_j, j < q <= kBcMaxQ, double-float, fixed order; every thread of
 // the block returns the same value (and every block, given equal inputs)
-__device__ __forceinline__ float2 bj_dot(const float2 *a, const float2 *b, int q, float2 *red)
+__device__ __forceinline__ float2 bc_dot(const float2 *a, const float2 *b, int q, float2 *red)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     float2 s = make_float2(0.f, 0.f);
@@ -726,35 +748,216 @@ __device__ __forceinline__ float2 bj_dot(const float2 *a, const float2 *b, int q
     return t;
 }
 
-__global__ void __launch_bounds__(kCgThreads) newton_bj_kernel(int q, const float2 *__restrict__ Mf,
-                                                               const double *__restrict__ g, double *__restrict__ dv,
-                                                               float eta, float tau, int maxit,
-                                                               double *__restrict__ info, int *err,
-                                                               const double *__restrict__ vdot,
-                                                               double *__restrict__ rdots, float2 *__restrict__ xch,
-                                                               unsigned *bar)
+// t <- (L L')^{-1} t with the row-major factor Lg (row stride q) and the
+// inverses Dg of its 8 x 8 diagonal blocks; t in shared memory, zero beyond
+// q up to a multiple of 8.  One block.
+__device__ void bc_chol_solve(const float *__restrict__ Lg, const float *__restrict__ Dg, int q, float *t)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nb8 = (q + kPb - 1) / kPb;
+    for (int b = 0; b < nb8; ++b) {   // forward: L y = t
+        const int kb = b * kPb;
+        if (warp == 0) {
+            const float tv = lane < kPb ? t[kb + lane] : 0.f;
+            const float *Db = Dg + (size_t)b * kPb * kPb;
+            float acc = 0.f;
+#pragma unroll
+            for (int k = 0; k < kPb; ++k)
+                acc = fmaf(lane < kPb ? __ldcg(&Db[lane * kPb + k]) : 0.f, __shfl_sync(0xffffffffu, tv, k), acc);
+            if (lane < kPb) t[kb + lane] = acc;
+        }
+        __syncthreads();
+        for (int r = kb + kPb + tid; r < q; r += blockDim.x) {
+            const float *lr = Lg + (size_t)r * q + kb;
+            float s = t[r];
+#pragma unroll
+            for (int k = 0; k < kPb; ++k)
+                if (kb + k < q) s = fmaf(-__ldcg(&lr[k]), t[kb + k], s);
+            t[r] = s;
+        }
+        __syncthreads();
+    }
+    for (int b = nb8 - 1; b >= 0; --b) {   // backward: L' x = y
+        const int kb = b * kPb;
+        if (warp == 0) {
+            const float tv = lane < kPb ? t[kb + lane] : 0.f;
+            const float *Db = Dg + (size_t)b * kPb * kPb;
+            float acc = 0.f;
+#pragma unroll
+            for (int k = 0; k < kPb; ++k)
+                acc = fmaf(lane < kPb ? __ldcg(&Db[k * kPb + lane]) : 0.f, __shfl_sync(0xffffffffu, tv, k), acc);
+            if (lane < kPb) t[kb + lane] = acc;
+        }
+        __syncthreads();
+        for (int r = tid; r < kb; r += blockDim.x) {
+            float s = t[r];
+#pragma unroll
+            for (int k = 0; k < kPb; ++k)
+                if (kb + k < q) s = fmaf(-__ldcg(&Lg[(size_t)(kb + k) * q + r]), t[kb + k], s);
+            t[r] = s;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kCgThreads) newton_bchol_kernel(int q, const float2 *__restrict__ Mf,
+                                                                  const double *__restrict__ g, double *__restrict__ dv,
+                                                                  float eta, float tau, int maxit,
+                                                                  double *__restrict__ info, int *err,
+                                                                  const double *__restrict__ vdot,
+                                                                  double *__restrict__ rdots, float *__restrict__ Lg,
+                                                                  float *__restrict__ Dg, float2 *__restrict__ xch,
+                                                                  int *fflag, unsigned *bar)
 {
     extern __shared__ float4 cg_sm4[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    const int nblk = (q + kBjBlk - 1) / kBjBlk;
-    const int b = blockIdx.x;
-    const int ob = b * kBjBlk;
-    const int qb = b < nblk ? (q - ob < kBjBlk ? q - ob : kBjBlk) : 0;
-    const int qpb = (qb + 31) & ~31;
-    CgSmem S;   // laid out for a 128 x 128 block whatever qb is
+    const int b = blockIdx.x, G = gridDim.x;
+    const int gw = b * nw + warp, ngw = G * nw;
+    CgSmem S;   // a 128 x 128 panel's factor; the region of M holds tiles and vectors
     S.M = reinterpret_cast<float2 *>(cg_sm4);
-    S.L = reinterpret_cast<float *>(S.M + kBjBlk * kBjBlk);
-    S.D = S.L + ((kBjBlk * (kBjBlk + 1)) >> 1);
-    S.t = S.D + (kBjBlk / kPb) * kPb * kPb;
+    S.L = reinterpret_cast<float *>(S.M + kBcNb * kBcNb);
+    S.D = S.L + ((kBcNb * (kBcNb + 1)) >> 1);
+    S.t = S.D + (kBcNb / kPb) * kPb * kPb;
     __shared__ float2 red[kCgThreads / 32];
-    __shared__ float sc_shift;
-    float2 *apg = xch, *zg = xch + kBjMaxQ;   // exchange buffers in global memory
-    // phase A: factor the diagonal blocks (a failed factor sets err)
-    if (b < nblk) cg_load_factor(S, qb, Mf + (size_t)ob * q + ob, err, &sc_shift, q);
-    if (!grid_barrier(bar, err)) return;
-    if (ld_relaxed_i32(err)) return;
-    // replicated vectors where the copy of the block's M was
-    float2 *X = S.M, *R = X + kBjMaxQ, *P = R + kBjMaxQ, *RO = P + kBjMaxQ, *Z = RO + kBjMaxQ, *AP = Z + kBjMaxQ;
+    float2 *apg = xch, *zg = xch + kBcMaxQ;
+    // the largest diagonal entry (scale of the breakdown shift), in every block
+    float md = 0.f;
+    for (int j = tid; j < q; j += blockDim.x) md = fmaxf(md, Mf[(size_t)j * q + j].x);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) md = fmaxf(md, __shfl_xor_sync(0xffffffffu, md, o));
+    if (lane == 0) red[warp].x = md;
+    __syncthreads();
+    float maxdiag = 0.f;
+    for (int w = 0; w < nw; ++w) maxdiag = fmaxf(maxdiag, red[w].x);
+    __syncthreads();
+    float shift = 0.f;
+    bool factored = false;
+    for (int attempt = 0; attempt < 6 && !factored; ++attempt) {
+        // fl32(M) + shift, lower triangle, into Lg
+        for (long long e = (long long)b * blockDim.x + tid; e < (long long)q * q; e += (long long)G * blockDim.x) {
+            const int i = (int)(e / q), j = (int)(e - (long long)i * q);
+            if (j <= i) Lg[e] = Mf[e].x + (i == j ? shift : 0.f);
+        }
+        if (b == 0 && tid == 0) *fflag = 0;
+        if (!grid_barrier(bar, err)) return;
+        bool bad = false;
+        for (int kb = 0; kb < q && !bad; kb += kBcNb) {
+            const int nbk = q - kb < kBcNb ? q - kb : kBcNb;
+            const int qpk = (nbk + 31) & ~31;
+            // (1) block 0: the diagonal block
+            if (b == 0) {
+                for (int i = warp; i < qpk; i += nw)
+                    for (int j = lane; j <= i; j += 32)
+                        S.L[lpos(i, j)] = (i < nbk) ? __ldcg(&Lg[(size_t)(kb + i) * q + kb + j]) : (i == j ? 1.f : 0.f);
+                __syncthreads();
+                const bool ok = cg_factor_packed(S, qpk);
+                if (!ok) {
+                    if (tid == 0) atomicExch(fflag, 1);
+                } else {
+                    for (int i = warp; i < nbk; i += nw)
+                        for (int j = lane; j <= i; j += 32) Lg[(size_t)(kb + i) * q + kb + j] = S.L[lpos(i, j)];
+                    for (int e = tid; e < ((nbk + kPb - 1) / kPb) * kPb * kPb; e += blockDim.x)
+                        Dg[(size_t)kb * kPb + e] = S.D[e];
+                }
+            }
+            if (!grid_barrier(bar, err)) return;
+            if (ld_relaxed_i32(fflag)) {
+                // every block has read the flag before block 0 clears it for the next attempt
+                bad = true;
+                if (!grid_barrier(bar, err)) return;
+                break;
+            }
+            if (kb + nbk >= q) break;
+            // (2) the panel's rows below: x L_kk' = a, a warp per row (every block
+            // first copies L_kk into its shared memory, with 1 / L_cc in S.t)
+            if (b != 0) {
+                for (int i = warp; i < nbk; i += nw)
+                    for (int j = lane; j <= i; j += 32) S.L[lpos(i, j)] = __ldcg(&Lg[(size_t)(kb + i) * q + kb + j]);
+            }
+            __syncthreads();
+            for (int c = tid; c < nbk; c += blockDim.x) S.t[c] = 1.f / S.L[lpos(c, c)];
+            __syncthreads();
+            for (int r = kb + nbk + gw; r < q; r += ngw) {
+                float a[kBcNb / 32];
+#pragma unroll
+                for (int m = 0; m < kBcNb / 32; ++m) {
+                    const int j = lane + 32 * m;
+                    a[m] = j < nbk ? __ldcg(&Lg[(size_t)r * q + kb + j]) : 0.f;
+                }
+                for (int c = 0; c < nbk; ++c) {
+                    const int own = c & 31, slot = c >> 5;
+                    float ac = 0.f;
+#pragma unroll
+                    for (int m = 0; m < kBcNb / 32; ++m)
+                        if (m == slot) ac = a[m];
+                    const float xc = __shfl_sync(0xffffffffu, ac, own) * S.t[c];
+#pragma unroll
+                    for (int m = 0; m < kBcNb / 32; ++m) {
+                        const int j = lane + 32 * m;
+                        if (j > c && j < nbk) a[m] = fmaf(-S.L[lpos(j, c)], xc, a[m]);
+                        if (j == c) a[m] = xc;
+                    }
+                }
+#pragma unroll
+                for (int m = 0; m < kBcNb / 32; ++m) {
+                    const int j = lane + 32 * m;
+                    if (j < nbk) Lg[(size_t)r * q + kb + j] = a[m];
+                }
+            }
+            if (!grid_barrier(bar, err)) return;
+            // (3) trailing update A_ij -= L_i,panel L_j,panel' over 64 x 64 tiles, j <= i
+            {
+                const int t0 = kb + nbk;
+                const int nt = (q - t0 + kBcTile - 1) / kBcTile;
+                const int ntiles = nt * (nt + 1) / 2;
+                float *TA = reinterpret_cast<float *>(S.M);                 // [64][nbk + 1]
+                float *TB = TA + kBcTile * (kBcNb + 1);                    // [64][nbk + 1]
+                const int ld = kBcNb + 1;
+                for (int tt = b; tt < ntiles; tt += G) {
+                    int ti = 0, rem = tt;
+                    while (rem > ti) { rem -= ti + 1; ++ti; }
+                    const int tj = rem;
+                    const int i0 = t0 + ti * kBcTile, j0 = t0 + tj * kBcTile;
+                    for (int e = tid; e < kBcTile * nbk; e += blockDim.x) {
+                        const int rr = e / nbk, m = e - rr * nbk;
+                        TA[rr * ld + m] = (i0 + rr < q) ? __ldcg(&Lg[(size_t)(i0 + rr) * q + kb + m]) : 0.f;
+                        TB[rr * ld + m] = (j0 + rr < q) ? __ldcg(&Lg[(size_t)(j0 + rr) * q + kb + m]) : 0.f;
+                    }
+                    __syncthreads();
+                    const int ii = tid >> 3, jc = tid & 7;   // row ii, columns jc + 8u
+                    float acc[kBcTile / 8];
+#pragma unroll
+                    for (int u = 0; u < kBcTile / 8; ++u) acc[u] = 0.f;
+                    for (int m = 0; m < nbk; ++m) {
+                        const float av = TA[ii * ld + m];
+#pragma unroll
+                        for (int u = 0; u < kBcTile / 8; ++u) acc[u] = fmaf(av, TB[(jc + 8 * u) * ld + m], acc[u]);
+                    }
+                    const int i = i0 + ii;
+#pragma unroll
+                    for (int u = 0; u < kBcTile / 8; ++u) {
+                        const int j = j0 + jc + 8 * u;
+                        if (i < q && j < q && j <= i) {
+                            float *lij = Lg + (size_t)i * q + j;
+                            *lij = __ldcg(lij) - acc[u];   // other blocks updated it in earlier panels
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+            if (!grid_barrier(bar, err)) return;
+        }
+        factored = !bad;
+        if (!factored) shift = (shift == 0.f) ? 1e-7f * maxdiag : shift * 100.f;
+    }
+    if (!factored) {
+        if (b == 0 && tid == 0) set_err(err, DEV_CHOL);
+        return;
+    }
+    // CG: replicated vectors where the tiles were
+    float2 *X = S.M, *R = X + kBcMaxQ, *P = R + kBcMaxQ, *RO = P + kBcMaxQ, *Z = RO + kBcMaxQ, *AP = Z + kBcMaxQ;
+    float *tz = reinterpret_cast<float *>(AP + kBcMaxQ);
+    const int q8 = (q + kPb - 1) / kPb * kPb;
     for (int j = tid; j < q; j += blockDim.x) {
         const double v = -g[j];
         const float hi = (float)v;
@@ -762,17 +965,16 @@ __global__ void __launch_bounds__(kCgThreads) newton_bj_kernel(int q, const floa
         X[j] = make_float2(0.f, 0.f);
     }
     __syncthreads();
-    float2 rr = bj_dot(R, R, q, red);
+    float2 rr = bc_dot(R, R, q, red);
     const float gn = sqrtf(fmaxf(rr.x, 0.f));
     const float tol = fmaxf(fminf(fminf(eta, powf(gn, 1.f + tau)), 1e-10f * gn), 1e-14f * gn);
     const float tol2 = tol * tol;
-    // z = blockdiag(L_b L_b')^{-1} r, every block's segment through global memory
     auto precond = [&]() -> bool {
-        if (b < nblk) {
-            for (int j = tid; j < qpb; j += blockDim.x) S.t[j] = j < qb ? R[ob + j].x + R[ob + j].y : 0.f;
+        if (b == 0) {
+            for (int j = tid; j < q8; j += blockDim.x) tz[j] = j < q ? R[j].x + R[j].y : 0.f;
             __syncthreads();
-            cg_precond(S, qpb);
-            for (int j = tid; j < qb; j += blockDim.x) zg[ob + j] = make_float2(S.t[j], 0.f);
+            bc_chol_solve(Lg, Dg, q, tz);
+            for (int j = tid; j < q; j += blockDim.x) zg[j] = make_float2(tz[j], 0.f);
         }
         if (!grid_barrier(bar, err)) return false;
         for (int j = tid; j < q; j += blockDim.x) Z[j] = __ldcg(&zg[j]);
@@ -782,10 +984,9 @@ __global__ void __launch_bounds__(kCgThreads) newton_bj_kernel(int q, const floa
     if (!precond()) return;
     for (int j = tid; j < q; j += blockDim.x) P[j] = Z[j];
     __syncthreads();
-    float2 rz = bj_dot(R, Z, q, red);
+    float2 rz = bc_dot(R, Z, q, red);
     int it = 0;
     bool go = rr.x > tol2;
-    const int gw = b * nw + warp, ngw = gridDim.x * nw;
     while (go && it < maxit) {
         // AP = M P: a warp per row, Dot2-style sums of double-float products
         for (int i = gw; i < q; i += ngw) {
@@ -813,7 +1014,7 @@ __global__ void __launch_bounds__(kCgThreads) newton_bj_kernel(int q, const floa
         if (!grid_barrier(bar, err)) return;
         for (int j = tid; j < q; j += blockDim.x) AP[j] = __ldcg(&apg[j]);
         __syncthreads();
-        const float2 pap = bj_dot(P, AP, q, red);
+        const float2 pap = bc_dot(P, AP, q, red);
         if (!(pap.x > 0.f)) break;
         const float2 al = dfx_div(rz, pap);
         for (int j = tid; j < q; j += blockDim.x) {
@@ -823,12 +1024,12 @@ __global__ void __launch_bounds__(kCgThreads) newton_bj_kernel(int q, const floa
         }
         __syncthreads();
         ++it;
-        rr = bj_dot(R, R, q, red);
+        rr = bc_dot(R, R, q, red);
         go = rr.x > tol2;
         if (!go) break;
         if (!precond()) return;
-        const float2 rzn = bj_dot(R, Z, q, red);
-        const float2 rzo = bj_dot(RO, Z, q, red);
+        const float2 rzn = bc_dot(R, Z, q, red);
+        const float2 rzo = bc_dot(RO, Z, q, red);
         float2 beta = dfx_div(dfx_sub(rzn, rzo), rz);
         if (!(beta.x > 0.f)) beta = make_float2(0.f, 0.f);
         rz = rzn;
@@ -840,7 +1041,7 @@ __global__ void __launch_bounds__(kCgThreads) newton_bj_kernel(int q, const floa
     if (tid == 0 && info) {
         info[0] = it;
         info[1] = sqrt((double)fmaxf(rr.x, 0.f));
-        info[2] = sc_shift;
+        info[2] = shift;
     }
     if (vdot) {
         // Algorithm 3, Step 2 quantities: rdots[2] = g'dv, rdots[3] = v'dv, rdots[4] = dv'dv
@@ -851,9 +1052,9 @@ __global__ void __launch_bounds__(kCgThreads) newton_bj_kernel(int q, const floa
             P[j] = make_float2(ch, (float)(c - (double)ch));
         }
         __syncthreads();
-        const float2 d0 = bj_dot(R, X, q, red);
-        const float2 d1 = bj_dot(P, X, q, red);
-        const float2 d2 = bj_dot(X, X, q, red);
+        const float2 d0 = bc_dot(R, X, q, red);
+        const float2 d1 = bc_dot(P, X, q, red);
+        const float2 d2 = bc_dot(X, X, q, red);
         if (tid == 0) {
             rdots[2] = (double)d0.x + (double)d0.y;
             rdots[3] = (double)d1.x + (double)d1.y;
@@ -1475,40 +1676,48 @@ cudaError_t launch_newton_batch(Work &W, const NewtonTask *T_dev, int ntask, int
     return cudaGetLastError();
 }
 
-static int g_bj_attr = 0;
+static int g_bc_attr = 0;
 
-// 128 < q <= 1024: the block-Jacobi CG above, one cooperative launch; the
-// exchange buffers of M p and z use the Gram partials' workspace (consumed by
-// build_m before this launch).
-static cudaError_t launch_newton_bj(Work &W, const double *g, double *dv, double *info, bool dots)
+// 128 < q <= 1024: the blocked-Cholesky CG above, one cooperative launch.  The
+// factor lives in W.Lf (q x q row-major); the exchange vectors of M p and z,
+// the 8 x 8 diagonal inverses and the restart flag use the Gram partials'
+// workspace (consumed by build_m before this launch).
+static cudaError_t launch_newton_bchol(Work &W, const double *g, double *dv, double *info, bool dots)
 {
     const int q = (int)W.q;
-    if (q > kBjMaxQ || W.part_len * sizeof(double) < 2 * kBjMaxQ * sizeof(float2)) return cudaErrorInvalidValue;
+    const size_t dg_floats = (size_t)((q + kPb - 1) / kPb) * kPb * kPb;
+    const size_t need = 2 * kBcMaxQ * sizeof(float2) + dg_floats * sizeof(float) + 16;
+    if (q > kBcMaxQ || W.part_len * sizeof(double) < need) return cudaErrorInvalidValue;
     const size_t smem = cg_fast_smem(kCgMaxQ);
-    if (!g_bj_attr) {
+    if (!g_bc_attr) {
         const cudaError_t ea =
-            cudaFuncSetAttribute(newton_bj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(newton_bchol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (ea != cudaSuccess) return ea;
-        g_bj_attr = 1;
+        g_bc_attr = 1;
     }
     int occ = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, newton_bj_kernel, kCgThreads, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, newton_bchol_kernel, kCgThreads, smem);
     if (e != cudaSuccess) return e;
-    const int nblk = (q + kBjBlk - 1) / kBjBlk;
-    int G = (q + (kCgThreads / 32) - 1) / (kCgThreads / 32);   // one row of M p per warp
-    if (G < nblk) G = nblk;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    // enough blocks for one row of M p per warp and one trailing tile per block
+    const int nt = (q + kBcTile - 1) / kBcTile;
+    int G = nt * (nt + 1) / 2;
+    const int rows = (q + (kCgThreads / 32) - 1) / (kCgThreads / 32);
+    if (G < rows) G = rows;
     if (G > occ * W.nsm) G = occ * W.nsm;
-    if (G < nblk) return cudaErrorInvalidConfiguration;
-    int qq = q, maxit = 4 * W.cg_maxit;
+    int qq = q, maxit = W.cg_maxit;
     const float2 *Mf = W.Mf;
     float eta = (float)W.eta, tau = (float)W.tau;
     int *err = W.err;
     const double *vd = dots ? W.v : nullptr;
     double *rd = W.red;
+    float *Lg = W.Lf;
     float2 *xch = reinterpret_cast<float2 *>(W.part);
+    float *Dg = reinterpret_cast<float *>(xch + 2 * kBcMaxQ);
+    int *fflag = reinterpret_cast<int *>(Dg + dg_floats);
     unsigned *bar = W.bar;
-    void *args[] = {&qq, &Mf, &g, &dv, &eta, &tau, &maxit, &info, &err, &vd, &rd, &xch, &bar};
-    return cudaLaunchCooperativeKernel((const void *)newton_bj_kernel, dim3(G), dim3(kCgThreads), args, smem, W.st);
+    void *args[] = {&qq, &Mf, &g, &dv, &eta, &tau, &maxit, &info, &err, &vd, &rd, &Lg, &Dg, &xch, &fflag, &bar};
+    return cudaLaunchCooperativeKernel((const void *)newton_bchol_kernel, dim3(G), dim3(kCgThreads), args, smem, W.st);
 }
 
 cudaError_t launch_newton(Work &W, const int32_t *J, long long p_host, const long long *p_dev, double sigma,
@@ -1590,7 +1799,7 @@ cudaError_t launch_newton(Work &W, const int32_t *J, long long p_host, const lon
                                                                     W.red);
             return cudaGetLastError();
         }
-        return launch_newton_bj(W, g, dv, info, dots);
+        return launch_newton_bchol(W, g, dv, info, dots);
     }
     size_t smem = ((size_t)q * q + q) * sizeof(double);
     if (q <= 144) {
