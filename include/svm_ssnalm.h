@@ -130,8 +130,9 @@ void svm_default_params(svm_params *p);
  * device workspace (O(n) vectors, O(q^2) Newton matrix).
  * CSR (layout = SVM_CSR, any q < 2^31, Sec. 4's sparse datasets): create also
  * checks the row structure and builds a CSC copy of X (O(nnz) device memory,
- * borrowed arrays stay borrowed); the solve runs the FP64 form whatever the
- * precision asks, with z = A v over the rows, A'c over the CSC columns and the
+ * borrowed arrays stay borrowed); the solve keeps its vectors in FP64 (with
+ * FP32 values and SVM_PREC_MIXED the products run in compensated FP32
+ * arithmetic), with z = A v over the rows, A'c over the CSC columns and the
  * Newton system (Prop. 3.5) by matrix-free Jacobi-preconditioned CG
  * (Algorithm 3) instead of a q x q factorisation.
  * Returns SVM_ERR_INVALID_ARG, SVM_ERR_OOM, SVM_ERR_CUDA, SVM_ERR_UNSUPPORTED.

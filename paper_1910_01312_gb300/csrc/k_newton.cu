@@ -250,26 +250,44 @@ __global__ void __launch_bounds__(256) gram_df_batch_kernel(const float *__restr
 }
 
 // M = I + sigma (G - h h' / p) from the double-float split-K partials of
-// gram_df_kernel, summed in block order in double-float; written as the
+// gram_df_kernel, summed in a fixed order in double-float; written as the
 // (hi, lo) pair Mf of the CG operator (and the factor's input).
 __device__ __forceinline__ void build_m_df_body(int q, int KS, const float2 *__restrict__ part,
                                                 const float2 *__restrict__ hpart, float2 pinv, float2 sig,
                                                 float2 *__restrict__ Mf)
 {
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)q * q;
-         e += (long long)gridDim.x * blockDim.x) {
-        const int a = (int)(e / q), b = (int)(e % q);
-        if (b > a || a / kGT < b / kGT) continue;
+    // eight lanes per entry sum interleaved eighths of the KS partials, then
+    // combine them by shuffles in a fixed order; four entries per warp step
+    // (a warp-uniform trip count, so every lane takes part in the shuffles)
+    const int lane = threadIdx.x & 31, sub = lane & 7;
+    const long long wg = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwg = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long qq = (long long)q * q;
+    for (long long base = wg * 4; base < qq; base += nwg * 4) {
+        const long long e = base + (lane >> 3);
+        const bool valid = e < qq;
+        const int a = valid ? (int)(e / q) : 0, b = valid ? (int)(e - (long long)a * q) : 1;
+        const bool act = valid && b <= a;
         float2 gsum = make_float2(0.f, 0.f), ha = gsum, hb = gsum;
-        for (int ks = 0; ks < KS; ++ks) {
-            gsum = dfx_add(gsum, part[(size_t)ks * q * q + (size_t)a * q + b]);
-            ha = dfx_add(ha, hpart[(size_t)ks * q + a]);
-            hb = dfx_add(hb, hpart[(size_t)ks * q + b]);
+        if (act) {
+            for (int ks = sub; ks < KS; ks += 8) {
+                gsum = dfx_add(gsum, __ldcg(&part[(size_t)ks * qq + e]));
+                ha = dfx_add(ha, __ldcg(&hpart[(size_t)ks * q + a]));
+                hb = dfx_add(hb, __ldcg(&hpart[(size_t)ks * q + b]));
+            }
         }
-        float2 m = dfx_mul(sig, dfx_sub(gsum, dfx_mul(dfx_mul(ha, hb), pinv)));
-        if (a == b) m = dfx_addf(m, 1.f);
-        Mf[(size_t)a * q + b] = m;
-        Mf[(size_t)b * q + a] = m;
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            gsum = dfx_add(gsum, shfl_xor_f2(gsum, o));
+            ha = dfx_add(ha, shfl_xor_f2(ha, o));
+            hb = dfx_add(hb, shfl_xor_f2(hb, o));
+        }
+        if (sub == 0 && act) {
+            float2 m = dfx_mul(sig, dfx_sub(gsum, dfx_mul(dfx_mul(ha, hb), pinv)));
+            if (a == b) m = dfx_addf(m, 1.f);
+            Mf[(size_t)a * q + b] = m;
+            Mf[(size_t)b * q + a] = m;
+        }
     }
 }
 
