@@ -13,7 +13,7 @@ from __future__ import annotations
 
 import numpy as np
 
-_IDS = {"small": 0, "gauss2000": 1, "gauss1m": 2, "csr": 3, "mnist_like": 4, "warm": 5, "ovr": 6}
+_IDS = {"small": 0, "gauss2000": 1, "gauss1m": 2, "csr": 3, "mnist_like": 4, "warm": 5, "ovr": 6, "rff": 7}
 
 
 def _rng(kind: str, seed: int) -> np.random.Generator:
@@ -194,3 +194,11 @@ def ovr_path(seed: int = 0, n: int = 200_000, q: int = 784, n_classes: int = 10,
             Y[k * n_C + j] = yk
             Cv[k * n_C + j] = Cs[j]
     return X, Y, Cv
+
+
+def rff_omega(seed: int, q: int, N: int, alpha: float, dtype=np.float32):
+    """The N frequencies of random Fourier features for the RBF kernel
+    exp(-|x - y|^2 / (2 alpha)): columns omega_j ~ N(0, I_q / alpha), returned
+    as a q x N matrix (row-major) in dtype; both sides read these values."""
+    rng = _rng("rff", seed)
+    return (rng.standard_normal((q, N)) / np.sqrt(alpha)).astype(dtype)
