@@ -252,6 +252,25 @@ svm_status svm_ssnalm_set_timing(svm_ssnalm_t *h, int enable);
 svm_status svm_ssnalm_get_stats(svm_ssnalm_t *h, svm_stats *out, int reset);
 
 /* ---------------------------------------------------------------------
+ * Random Fourier features front-end (Sec. 4.3): the RBF-kernel C-SVC with
+ * k(x, y) = exp(-|x - y|^2 / (2 alpha)) becomes the linear C-SVC on Z.
+ * ------------------------------------------------------------------- */
+
+/* Z (n x 2N, row-major FP32, device) from X (n x q, row-major FP32, device)
+ * and the frequencies Omega (q x N, row-major FP32, device; column j is
+ * omega_j, drawn by the caller from N(0, I/alpha)):
+ *     Z[i][2j] = cos(<x_i, omega_j>) / sqrt(N),  Z[i][2j+1] = sin(<x_i, omega_j>) / sqrt(N),
+ * so that Z Z' is the sample average (1/N) sum_j cos(omega_j'(x_i - x_k)) of
+ * the paper's Bochner estimate.  The phases <x_i, omega_j> are FP32 sums in k
+ * order.  Pass Z as the X of svm_ssnalm_create (q = 2N) to solve the
+ * approximated problem.  Allocates nothing; stream-ordered (stream may be
+ * NULL), returns without synchronising.  SVM_ERR_INVALID_ARG for null
+ * pointers or n, q, N < 1; SVM_ERR_UNSUPPORTED when Z is not 8-byte aligned
+ * or N > 2^28; SVM_ERR_CUDA when the launch fails. */
+svm_status svm_rff_features(const float *X, int64_t n, int64_t q, const float *Omega, int64_t N, float *Z,
+                            void *stream);
+
+/* ---------------------------------------------------------------------
  * Allocation-free transposed product.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate memory.
  * ------------------------------------------------------------------- */

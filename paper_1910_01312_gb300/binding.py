@@ -54,7 +54,7 @@ class Stats(C.Structure):
 
 SYMBOLS = ["svm_default_params", "svm_ssnalm_create", "svm_ssnalm_solve", "svm_ssnalm_destroy",
            "svm_ssnalm_last_error", "svm_op_matvec", "svm_op_rmatvec", "svm_op_project",
-           "svm_op_newton", "svm_op_kkt", "svm_op_gram", "svm_ssnalm_solve_batch", "svm_ssnalm_set_timing", "svm_ssnalm_get_stats",
+           "svm_op_newton", "svm_op_kkt", "svm_op_gram", "svm_ssnalm_solve_batch", "svm_rff_features", "svm_ssnalm_set_timing", "svm_ssnalm_get_stats",
            "svm_rmatvec_noalloc", "svm_mlp_create", "svm_mlp_destroy", "svm_mlp_get_params",
            "svm_mlp_features", "svm_mlp_labels", "svm_mlp_gather", "svm_mlp_forward", "svm_mlp_loss_grad", "svm_mlp_adam_step",
            "svm_mlp_train_step", "svm_mlp_start_point", "svm_ssnalm_solve_mlp"]
@@ -98,6 +98,7 @@ def load(build_if_missing: bool = False):
         L.svm_op_kkt.argtypes = [vp, vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.svm_op_gram.argtypes = [vp, vp, i64, vp, vp]
         L.svm_ssnalm_solve_batch.argtypes = [vp, C.c_int32, vp, vp, vp, vp, C.POINTER(Result)]
+        L.svm_rff_features.argtypes = [vp, i64, i64, vp, i64, vp, vp]
         L.svm_ssnalm_set_timing.argtypes = [vp, C.c_int]
         L.svm_ssnalm_get_stats.argtypes = [vp, C.POINTER(Stats), C.c_int]
         L.svm_rmatvec_noalloc.argtypes = [vp, vp, i64, i64, vp, vp, vp]
@@ -116,7 +117,7 @@ def load(build_if_missing: bool = False):
         L.svm_mlp_start_point.argtypes = [vp, vp, i64, dbl, vp]
         L.svm_ssnalm_solve_mlp.argtypes = [vp, vp, C.POINTER(Result), C.POINTER(C.c_int32)]
         for f in ("svm_op_matvec", "svm_op_rmatvec", "svm_op_project", "svm_op_newton", "svm_op_kkt", "svm_op_gram",
-                  "svm_ssnalm_solve_batch",
+                  "svm_ssnalm_solve_batch", "svm_rff_features",
                   "svm_ssnalm_set_timing", "svm_ssnalm_get_stats", "svm_rmatvec_noalloc", "svm_mlp_create",
                   "svm_mlp_get_params", "svm_mlp_features", "svm_mlp_labels", "svm_mlp_gather", "svm_mlp_forward",
                   "svm_mlp_loss_grad",
@@ -147,6 +148,14 @@ def rmatvec_noalloc(X, y, c, out, stream=None) -> int:
     y, FP64 c and out); returns the svm_status code."""
     n, q = X.shape
     return load().svm_rmatvec_noalloc(_ptr(X), _ptr(y), int(n), int(q), _ptr(c), _ptr(out), stream)
+
+
+def rff_features(X, Omega, Z, stream=None) -> int:
+    """Random Fourier features Z (n x 2N) of X (n x q) for the frequencies
+    Omega (q x N), all device FP32; returns the svm_status code."""
+    n, q = X.shape
+    N = Omega.shape[1]
+    return load().svm_rff_features(_ptr(X), int(n), int(q), _ptr(Omega), int(N), _ptr(Z), stream)
 
 
 def _ptr(t):

@@ -8,7 +8,8 @@
 Ops: ``solve`` (one cold solve after one warm-up, both forms of the stated
 precision), ``matvec`` (z = A v), ``rmatvec`` (A'c over all rows), ``project``
 (the projection at a random u), ``newton`` (the reduced Newton system on a
-random free set of size --p).  The data are the two-Gaussian workload of
+random free set of size --p), ``rff`` (random Fourier features of X with
+--nfreq frequencies).  The data are the two-Gaussian workload of
 ``datagen.gauss1m`` at the requested n and q, or with ``--layout csr`` the
 text-like sparse workload of ``datagen.sparse_text`` (--nnz-row entries per
 row).  Prints one JSON line with the mean time per call from CUDA events on
@@ -24,7 +25,8 @@ import numpy as np
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--op", default="solve", choices=["solve", "matvec", "rmatvec", "project", "newton"])
+    ap.add_argument("--op", default="solve", choices=["solve", "matvec", "rmatvec", "project", "newton", "rff"])
+    ap.add_argument("--nfreq", type=int, default=512)
     ap.add_argument("--n", type=int, default=400_000)
     ap.add_argument("--q", type=int, default=128)
     ap.add_argument("--p", type=int, default=150)
@@ -62,7 +64,11 @@ def main(argv=None):
     rng = np.random.default_rng(0)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
-    if args.op == "solve":
+    if args.op == "rff":
+        Om = dev(datagen.rff_omega(0, q, args.nfreq, float(q)))
+        Zr = torch.empty((n, 2 * args.nfreq), dtype=torch.float32, device="cuda")
+        call = lambda: B.rff_features(Xd, Om, Zr, stream.cuda_stream)
+    elif args.op == "solve":
         alpha = torch.zeros(n, dtype=torch.float64, device="cuda")
         w = torch.zeros(q, dtype=torch.float64, device="cuda")
         call = lambda: s.solve(alpha, w)
@@ -96,6 +102,10 @@ def main(argv=None):
             "ms_per_call": ms}
     if args.layout == "csr":
         line["nnz"] = nnz
+    if args.op == "rff":
+        flops = 2.0 * n * q * args.nfreq
+        line.update({"nfreq": args.nfreq, "gemm_TFLOP_per_s": flops / (ms * 1e-3) / 1e12,
+                     "Z_bytes": 8 * n * args.nfreq, "Z_GB_per_s": 8 * n * args.nfreq / (ms * 1e-3) / 1e9})
     if args.op in ("matvec", "rmatvec"):
         b = bytes_mv if args.op == "matvec" else bytes_rmv
         line.update({"bytes_per_call": b, "GB_per_s": b / (ms * 1e-3) / 1e9})
