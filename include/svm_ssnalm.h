@@ -172,7 +172,7 @@ svm_status svm_ssnalm_solve(svm_ssnalm_t *h, const double *alpha0, svm_result *r
  * when every problem converged, else the most severe per-problem status
  * (errors, then SVM_ERR_NOT_CONVERGED, then SVM_ERR_DEGENERATE);
  * SVM_ERR_INVALID_ARG for B < 1, null pointers, C <= 0 or non-finite, or a
- * label other than +1/-1; SVM_ERR_UNSUPPORTED for CSR handles. */
+ * label other than +1/-1; SVM_ERR_UNSUPPORTED for CSR handles or B > 65535. */
 svm_status svm_ssnalm_solve_batch(svm_ssnalm_t *h, int32_t B, const int8_t *Y, const double *C, double *alpha,
                                   double *w, svm_result *results);
 

@@ -1119,6 +1119,7 @@ extern "C" svm_status svm_ssnalm_solve_batch(svm_ssnalm_t *h, int32_t B, const i
         if (!(C[b] > 0.0) || !isfinite(C[b])) { h->err = "batch: every C must be finite and > 0"; return SVM_ERR_INVALID_ARG; }
     Work &W = h->W;
     if (W.csr) { h->err = "batch: dense X only"; return SVM_ERR_UNSUPPORTED; }
+    if (B > 65535) { h->err = "batch: at most 65535 problems per call"; return SVM_ERR_UNSUPPORTED; }
     const long long n = W.n;
     const int q = (int)W.q;
     const bool host_mem = h->prob.memory == SVM_MEM_HOST;
