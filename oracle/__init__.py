@@ -5,8 +5,12 @@ benchmark's CPU-baseline leg are the only callers.  The product path (the CUDA
 library and its binding) never imports this package, and this package imports
 nothing from it.
 
-The arithmetic lives in ``svm_oracle.c`` (plain C, FP64, single thread); this
-module only compiles it with gcc and marshals numpy arrays through ctypes.
+The C-SVC method's arithmetic lives in ``svm_oracle.c`` (plain C, FP64,
+single thread); this module only compiles it with gcc and marshals numpy
+arrays through ctypes.  Beside it, in FP64 numpy: ``mlp.py`` (the learned
+warm start's network), ``rff.py`` (random Fourier features, Sec. 4.3) and
+``gqp.py`` (the method for the unified QP of eq. (1.5), with the SVR dual of
+eq. (1.4) as a case).
 """
 from __future__ import annotations
 
