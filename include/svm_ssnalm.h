@@ -25,7 +25,11 @@
  *  - Errors: every call returns an svm_status; svm_ssnalm_last_error() gives a
  *    one-line reason for the last failure on a handle.  On error the contents
  *    of output buffers are unspecified unless stated.
- *  - Threads: a handle is used by one host thread at a time.
+ *  - Threads: a handle is used by one host thread at a time.  Do not run
+ *    solves of different handles concurrently on one GPU (different streams
+ *    or threads): the projection and the Newton step for q > 128 are
+ *    cooperative launches sized to the whole GPU, whose blocks wait on one
+ *    another.  For many problems over one X use svm_ssnalm_solve_batch.
  */
 #ifndef SVM_SSNALM_H
 #define SVM_SSNALM_H
