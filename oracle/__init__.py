@@ -8,8 +8,8 @@ nothing from it.
 The C-SVC method's arithmetic lives in ``svm_oracle.c`` (plain C, FP64,
 single thread); this module only compiles it with gcc and marshals numpy
 arrays through ctypes.  Beside it, in FP64 numpy: ``mlp.py`` (the learned
-warm start's network), ``rff.py`` (random Fourier features, Sec. 4.3) and
-``gqp.py`` (the method for the unified QP of eq. (1.5), with the SVR dual of
+warm start's network), ``rff.py`` (random Fourier features, Sec. 4.3), ``nystrom.py`` (the
+Nystrom front-end of the same section) and ``gqp.py`` (the method for the unified QP of eq. (1.5), with the SVR dual of
 eq. (1.4) as a case).
 """
 from __future__ import annotations
