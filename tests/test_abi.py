@@ -50,3 +50,25 @@ def test_create_rejects_bad_args_without_gpu_work():
     with pytest.raises(P.SVMError) as e:
         P.Solver(np.zeros((4, 2000), np.float32), y, C_=1.0)
     assert e.value.status == P.ERR_UNSUPPORTED
+
+
+def test_entry_points_reject_bad_arguments_before_any_gpu_work():
+    """Argument checks come before any CUDA call, so they hold without a GPU."""
+    import numpy as np
+    L = P.load()
+    buf = np.zeros(64, np.float32)
+    p = buf.ctypes.data
+    # random features: null pointers and empty sizes, then an unaligned output
+    assert L.svm_rff_features(None, 4, 3, p, 2, p, None) == P.ERR_INVALID_ARG
+    assert L.svm_rff_features(p, 0, 3, p, 2, p, None) == P.ERR_INVALID_ARG
+    assert L.svm_rff_features(p, 4, 3, p, 0, p, None) == P.ERR_INVALID_ARG
+    assert L.svm_rff_features(p, 4, 3, p, 2, p + 4, None) == P.ERR_UNSUPPORTED
+    # batched solve and step-level entry points on a null handle
+    R = (P.binding.Result * 2)()
+    cs = np.ones(2)
+    assert L.svm_ssnalm_solve_batch(None, 2, p, cs.ctypes.data, p, p, R) == P.ERR_INVALID_ARG
+    assert L.svm_op_gram(None, p, 1, p, p) == P.ERR_INVALID_ARG
+    assert L.svm_ssnalm_solve(None, None, None) == P.ERR_INVALID_ARG
+    # the allocation-free product: sizes beyond its limit, null pointers
+    assert L.svm_rmatvec_noalloc(p, p, 10, 4096, p, p, None) == P.ERR_UNSUPPORTED
+    assert L.svm_rmatvec_noalloc(None, p, 10, 4, p, p, None) == P.ERR_INVALID_ARG
