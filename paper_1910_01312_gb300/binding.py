@@ -163,9 +163,11 @@ def _ptr(t):
     if t is None:
         return None
     if hasattr(t, "data_ptr"):
-        assert t.is_contiguous()
+        if not t.is_contiguous():
+            raise ValueError("the C ABI takes contiguous (row-major) tensors")
         return t.data_ptr()
-    assert t.flags["C_CONTIGUOUS"]
+    if not t.flags["C_CONTIGUOUS"]:
+        raise ValueError("the C ABI takes C-contiguous (row-major) arrays")
     return t.ctypes.data
 
 

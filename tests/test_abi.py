@@ -72,3 +72,11 @@ def test_entry_points_reject_bad_arguments_before_any_gpu_work():
     # the allocation-free product: sizes beyond its limit, null pointers
     assert L.svm_rmatvec_noalloc(p, p, 10, 4096, p, p, None) == P.ERR_UNSUPPORTED
     assert L.svm_rmatvec_noalloc(None, p, 10, 4, p, p, None) == P.ERR_INVALID_ARG
+
+
+def test_binding_rejects_non_contiguous_buffers():
+    import numpy as np
+    X = np.zeros((6, 4), order="F")
+    with pytest.raises(ValueError):
+        P.binding._ptr(X)
+    assert P.binding._ptr(np.zeros((6, 4))) != 0 and P.binding._ptr(None) is None
