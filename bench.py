@@ -7,10 +7,11 @@ two-Gaussian workload n = 1,000,000 x q = 128 FP32, C = 0.1 (means
 plus the achieved HBM bandwidth of the forward product A v against the
 measured copy bandwidth.  One "step" is one whole solve from alpha = 0.
 The line also carries the plain FP64 form's time on the same problem, the
-end-to-end time through the C ABI with host buffers, the oracle on a bounded
-sample (cpu_baseline), and a batched leg: 160 SVMs sharing one X (ten
-one-vs-rest classes x sixteen C values) solved in lockstep by
-svm_ssnalm_solve_batch against the same problems solved one by one.
+end-to-end time through the C ABI with host buffers, the FP64 oracle solving
+the same full-size problem on the host (cpu_baseline: the OpenMP build on all
+host cores, and the single-threaded build), and a batched leg: 160 SVMs
+sharing one X (ten one-vs-rest classes x sixteen C values) solved in lockstep
+by svm_ssnalm_solve_batch against the same problems solved one by one.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -35,8 +36,8 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "gauss1m: dense two-Gaussian C-SVC, n=1000000 x q=128 FP32, C=0.1, 10% label noise"
 METRIC = "time-to-KKT<=1e-6 per SVM solve"
 N_FULL = 1_000_000
-N_CPU_SAMPLE = 50_000      # oracle sample for the cpu_baseline leg (~10-30 s)
-N_REF_SAMPLE = 20_000      # oracle sample per step of the reference arm
+N_REF_WARM = 50_000        # warm-up solves of the reference arm run on a 50,000-row sample
+REF_BUDGET_S = 150.0       # the reference arm stops adding timed solves after this long
 BATCH_N, BATCH_Q, BATCH_CLASSES, BATCH_NC = 100_000, 128, 10, 16   # the batched (one-vs-rest x C path) leg
 
 
@@ -116,37 +117,89 @@ def _traffic(kernel_src: str, key: str):
         return None
 
 
-def cpu_baseline(n_sample, seed=0):
+def host_cpu():
+    """The host's CPU model and core count (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return {"model": model or "unknown", "nproc": os.cpu_count() or 1}
+
+
+def oracle_solve_timed(X, y, C, omp):
+    """One oracle solve to R_KKT <= 1e-6 (wall time in s, result)."""
     import oracle
-    import datagen
-    X, y, C = datagen.gauss1m(seed, n=n_sample)
     t0 = time.perf_counter()
-    r = oracle.solve(X, y, C, tol=1e-6)
-    dt = time.perf_counter() - t0
-    return dt, r
+    r = oracle.solve(X, y, C, tol=1e-6, omp=omp)
+    return time.perf_counter() - t0, r
+
+
+def cpu_baseline_full(X, y, C):
+    """The FP64 oracle on the whole benchmark problem: the OpenMP build on all
+    host cores (the reported value), then the single-threaded build."""
+    import oracle
+    cpu = host_cpu()
+    t_all, r_all = oracle_solve_timed(X, y, C, omp=True)
+    t_one, r_one = oracle_solve_timed(X, y, C, omp=False)
+    same = bool(r_all["objective"] == r_one["objective"] and r_all["inner_total"] == r_one["inner_total"])
+    return {"value": 1e3 * t_all, "unit": "ms", "cores": oracle.omp_threads(), "kind": "oracle",
+            "sample": (f"the full workload (n={X.shape[0]}, q={X.shape[1]}), one solve to R_KKT<=1e-6 "
+                       f"({r_all['outer']} outer / {r_all['inner_total']} Newton iterations) by the oracle's "
+                       f"OpenMP build on all host cores; the single-threaded build's solve is single_thread"),
+            "cpu_model": cpu["model"], "nproc": cpu["nproc"],
+            "single_thread": {"value": 1e3 * t_one, "unit": "ms", "cores": 1},
+            "builds_agree": same, "objective": r_all["objective"], "kkt": r_all["kkt"]}
 
 
 def run_reference(args, rank, world):
-    """Reference arm: the FP64 CPU oracle, as it stands, on the host cores."""
+    """Reference arm: the FP64 CPU oracle, as it stands (OpenMP build, all
+    host cores), solving the full benchmark problem once per timed step."""
     if rank != 0:
         return 0
-    times = []
-    r = None
-    for it in range(args.warmup + args.steps):
-        dt, r = cpu_baseline(N_REF_SAMPLE, seed=it % 3)
-        if it >= args.warmup:
-            times.append(dt)
-    scale = N_FULL / N_REF_SAMPLE
-    ms = 1e3 * statistics.mean(times) * scale
-    sample = (f"oracle (plain C, FP64, 1 thread) on n={N_REF_SAMPLE} rows of the same distribution, "
-              f"one solve to R_KKT<=1e-6 per step; time scaled linearly by n to n={N_FULL}")
+    import datagen
+    import oracle
+    cpu = host_cpu()
+    n_ref = args.ref_n
+    Xw, yw, Cw = datagen.gauss1m(0, n=min(N_REF_WARM, n_ref))
+    for _ in range(args.warmup):
+        oracle_solve_timed(Xw, yw, Cw, omp=True)
+    X, y, C = datagen.gauss1m(0, n=n_ref)
+    times, r = [], None
+    t_start = time.perf_counter()
+    for _ in range(args.steps):
+        dt, r = oracle_solve_timed(X, y, C, omp=True)
+        times.append(dt)
+        if time.perf_counter() - t_start > REF_BUDGET_S and len(times) >= 3:
+            break
+    ms = 1e3 * statistics.mean(times)
+    sample = (f"the {'full ' if n_ref == N_FULL else ''}workload (n={n_ref}, q=128), one oracle solve to "
+              f"R_KKT<=1e-6 per timed step "
+              f"(OpenMP build, {oracle.omp_threads()} threads); {len(times)} of the {args.steps} requested "
+              f"steps timed (the arm stops adding steps after {REF_BUDGET_S:.0f} s); warm-up solves on a "
+              f"{N_REF_WARM}-row sample")
     line = {"impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD},
-            "cpu_baseline": {"value": ms, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample},
+            "steps": len(times), "steps_requested": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD if n_ref == N_FULL else WORKLOAD.replace(str(N_FULL), str(n_ref))},
+            "cpu_baseline": {"value": ms, "unit": "ms", "cores": oracle.omp_threads(), "kind": "oracle",
+                             "sample": sample, "cpu_model": cpu["model"], "nproc": cpu["nproc"]},
             "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-            "solve": {"outer": r["outer"], "inner": r["inner_total"], "kkt": r["kkt"]}}
+            "solve": {"outer": r["outer"], "inner": r["inner_total"], "kkt": r["kkt"],
+                      "objective": r["objective"]}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -210,6 +263,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-n", type=int, default=BATCH_N)
     ap.add_argument("--batch-q", type=int, default=BATCH_Q)
+    ap.add_argument("--ref-n", type=int, default=N_FULL, help="rows of the reference arm's problem (checks only)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -341,14 +395,10 @@ def main():
         torch.cuda.empty_cache()
         batched = run_batched(args, P, torch, datagen, sptr, stream, rank)
 
-    # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1) ----
+    # ---- CPU baseline: the oracle on the same full problem (rank 0, N = 1) ----
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        dt, rr = cpu_baseline(N_CPU_SAMPLE)
-        cpu = {"value": 1e3 * dt * N_FULL / N_CPU_SAMPLE, "unit": "ms", "cores": 1, "kind": "oracle",
-               "sample": (f"oracle (plain C, FP64, 1 thread) solving n={N_CPU_SAMPLE} rows of the same "
-                          f"distribution to R_KKT<=1e-6 in {dt:.2f} s ({rr['outer']} outer / "
-                          f"{rr['inner_total']} Newton iterations); scaled linearly by n to n={N_FULL}")}
+        cpu = cpu_baseline_full(X, y, C)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "ms", "n_gpus": world, "steps": args.steps,

@@ -97,6 +97,23 @@ svm_status svm_mlp_start_point(svm_mlp_t *m, const float *F, int64_t n, double C
  * SVM_ERR_UNSUPPORTED. */
 svm_status svm_ssnalm_solve_mlp(svm_ssnalm_t *h, svm_mlp_t *m, svm_result *res, int32_t *used_warm);
 
+/* Attach a trained warm-start network to the handle (the learned counterpart
+ * of the paper's warm start from an approximate solve, Sec. 4.3).
+ * mlp_weights: device pointer to SVM_MLP_NPARAM FP32 parameters in the layout
+ * above; they are copied, so the caller's buffer may be freed afterwards.
+ * Afterwards every svm_ssnalm_solve(h, NULL, res) of this handle runs as
+ * svm_ssnalm_solve_mlp with the attached network, cold fallback included; a
+ * solve given a non-NULL alpha0 still starts from alpha0, and
+ * svm_ssnalm_solve_batch still starts every problem cold.  mlp_weights = NULL
+ * detaches the network (cold starts again).  The handle owns the network and
+ * its workspace (about 6 KB of device memory per sample: the hidden
+ * activations of all n rows); svm_ssnalm_destroy frees it.  Stream-ordered on
+ * the handle's stream.  Returns SVM_ERR_INVALID_ARG for a NULL handle,
+ * SVM_ERR_UNSUPPORTED unless the handle's problem is dense FP32 with q = 128
+ * (the network's input width), SVM_ERR_OOM / SVM_ERR_CUDA when the network
+ * cannot be created (the handle is then left without a network). */
+svm_status svm_ssnalm_set_warmstart_model(svm_ssnalm_t *h, const float *mlp_weights);
+
 #ifdef __cplusplus
 }
 #endif

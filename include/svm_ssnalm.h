@@ -57,14 +57,30 @@ typedef enum {
 typedef enum { SVM_DENSE_ROWMAJOR = 0, SVM_CSR = 1 } svm_layout;
 typedef enum { SVM_F32 = 0, SVM_F64 = 1 } svm_dtype;
 
-/* Arithmetic of the solve.
+/* Arithmetic of the solve (requested in svm_params.precision).
  * PLAIN_FP64: every vector, product and reduction in IEEE FP64 (X is read in
- *   its storage type and widened exactly).
+ *   its storage type and widened exactly); dense X: direct Cholesky solve of
+ *   the reduced Newton system.
  * MIXED: FP32 products; FP64 accuracy recovered where the method needs it by
  *   FP32 error-free transformations (compensated sums and products); FP64
  *   kept for the multiplier/sigma updates, the KKT/gap reductions and the
- *   small Newton factorisation. */
+ *   small Newton factorisation.  The full mixed form needs dense FP32 X with
+ *   q % 4 == 0.  MIXED on other problems is accepted and runs the form below
+ *   that fits; the form that actually ran is reported in svm_result.form. */
 typedef enum { SVM_PREC_PLAIN_FP64 = 0, SVM_PREC_MIXED = 1 } svm_precision;
+
+/* The arithmetic a solve actually ran (svm_result.form).
+ * FP64_DIRECT: IEEE FP64 vectors and products, direct reduced Newton solve
+ *   (PLAIN_FP64 on dense X).
+ * MIXED: the mixed form (MIXED on dense FP32 X with q % 4 == 0): FP32
+ *   compensated products, double-float n-vectors, CG Newton solve
+ *   preconditioned by an FP32 Cholesky factor.
+ * COMPENSATED: FP64 n-vectors; products with FP32 X in compensated FP32
+ *   arithmetic; CG Newton solve (MIXED on dense FP32 X with q % 4 != 0, or on
+ *   CSR FP32 X).
+ * FP64_CG: FP64 vectors and products; CG Newton solve (MIXED on FP64 X, and
+ *   every CSR solve with FP64 values or PLAIN_FP64). */
+typedef enum { SVM_FORM_FP64_DIRECT = 0, SVM_FORM_MIXED = 1, SVM_FORM_COMPENSATED = 2, SVM_FORM_FP64_CG = 3 } svm_form;
 
 /* Where the problem arrays and the result arrays live. */
 typedef enum { SVM_MEM_DEVICE = 0, SVM_MEM_HOST = 1 } svm_memory;
@@ -117,7 +133,7 @@ typedef struct {
     int32_t outer_iters;
     int32_t inner_iters_total;
     int32_t status;          /* same as the return value of the solve         */
-    int32_t reserved0;
+    int32_t form;            /* svm_form: the arithmetic this solve ran       */
     int64_t n_free;          /* 0 < alpha_i < C                               */
     int64_t n_upper;         /* alpha_i = C                                   */
     int64_t n_sv;            /* alpha_i > 0                                   */
@@ -298,10 +314,12 @@ svm_status svm_rff_features(const float *X, int64_t n, int64_t q, const float *O
  * allocation routine: it only looks up the array's device address, clears
  * the counter (cudaMemsetAsync) and launches one kernel.
  *
- * The first call on a device (with that device current) performs that
- * device's one-time set-up (address look-up, kernel attribute); make that
- * first call before any stream capture.  The call is stream-ordered and
- * returns without synchronising.  All calls on a device share the one
+ * The call runs on the current device: X, y, c and out must be that device's
+ * memory, and a non-NULL stream must belong to it (a stream of another device
+ * returns SVM_ERR_INVALID_ARG).  The first call on a device (with that device
+ * current) performs that device's one-time set-up (address look-up, kernel
+ * attribute); make that first call before any stream capture.  The call is
+ * stream-ordered and returns without synchronising.  All calls on a device share the one
  * scratch array: calls whose kernels could overlap on the GPU (different
  * streams or host threads) race and give wrong results -- serialise them. */
 svm_status svm_rmatvec_noalloc(const float *X, const int8_t *y, int64_t n, int64_t q,

@@ -7,7 +7,9 @@ nothing from it.
 
 The C-SVC method's arithmetic lives in ``svm_oracle.c`` (plain C, FP64,
 single thread); this module only compiles it with gcc and marshals numpy
-arrays through ctypes.  Beside it, in FP64 numpy: ``mlp.py`` (the learned
+arrays through ctypes.  ``solve(..., omp=True)`` runs the same source built
+with OpenMP on all host cores (the benchmark's all-core CPU baseline); its
+results are bit-identical to the single-threaded build's.  Beside it, in FP64 numpy: ``mlp.py`` (the learned
 warm start's network), ``rff.py`` (random Fourier features, Sec. 4.3), ``nystrom.py`` (the
 Nystrom front-end of the same section) and ``gqp.py`` (the method for the unified QP of eq. (1.5), with the SVR dual of
 eq. (1.4) as a case).
@@ -24,8 +26,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "svm_oracle.c")
 _LIB = os.path.join(_HERE, "_build", "libsvm_oracle.so")
+_LIB_OMP = os.path.join(_HERE, "_build", "libsvm_oracle_omp.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {False: None, True: None}
 
 OK, ERR_ARG, ERR_OOM, ERR_NOT_CONVERGED, ERR_NUMERIC, ERR_DEGENERATE = 0, 1, 3, 4, 5, 6
 
@@ -52,22 +55,23 @@ class Trace(C.Structure):
                 ("p", C.c_int64)]
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (IEEE semantics, no FMA contraction)."""
-    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".{os.getpid()}.tmp"
+def build(force: bool = False, omp: bool = False) -> str:
+    """Compile the oracle with gcc (IEEE semantics, no FMA contraction); with
+    omp=True the same source with -fopenmp (all host cores)."""
+    out = _LIB_OMP if omp else _LIB
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        tmp = out + f".{os.getpid()}.tmp"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-                               "-fno-fast-math", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+                               "-fno-fast-math", *(["-fopenmp"] if omp else []), "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, out)
+    return out
 
 
-def lib():
-    global _lib
+def lib(omp: bool = False):
     with _lock:
-        if _lib is None:
-            L = C.CDLL(build())
+        if _libs[omp] is None:
+            L = C.CDLL(build(omp=omp))
             d, i64, vp, i8p, dp, i64p = C.c_double, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p
             L.orc_matvec.argtypes = [vp, C.c_int, i8p, i64, i64, dp, dp]
             L.orc_rmatvec.argtypes = [vp, C.c_int, i8p, i64, i64, dp, dp, dp]
@@ -83,11 +87,21 @@ def lib():
             L.orc_bias.restype = d
             L.orc_primal.argtypes = [vp, C.c_int, i8p, i64, i64, d, dp, d]
             L.orc_primal.restype = d
+            L.orc_matvec_csr.argtypes = [vp, vp, vp, C.c_int, i8p, i64, i64, dp, dp]
+            L.orc_rmatvec_csr.argtypes = [vp, vp, vp, C.c_int, i8p, i64, i64, dp, dp]
+            L.orc_kkt_csr.argtypes = [vp, vp, vp, C.c_int, i8p, i64, i64, d, dp, dp, dp]
+            L.orc_kkt_csr.restype = d
             L.orc_default_params.argtypes = [C.POINTER(Params)]
             L.orc_solve.argtypes = [vp, C.c_int, i8p, i64, i64, d, C.POINTER(Params), dp, C.c_int,
                                     dp, C.POINTER(Result), C.POINTER(Trace)]
-            _lib = L
-    return _lib
+            _libs[omp] = L
+    return _libs[omp]
+
+
+def omp_threads() -> int:
+    """Threads the OpenMP build uses (OMP_NUM_THREADS, else the host's cores)."""
+    v = os.environ.get("OMP_NUM_THREADS", "")
+    return int(v) if v.isdigit() and int(v) > 0 else (os.cpu_count() or 1)
 
 
 def _p(a):
@@ -208,8 +222,9 @@ def default_params(**kw) -> Params:
     return P
 
 
-def solve(X, y, C_, alpha0=None, trace=False, **kw):
-    """Run SSsNAL; returns dict(alpha, w, status, objective, kkt, b, ...)."""
+def solve(X, y, C_, alpha0=None, trace=False, omp=False, **kw):
+    """Run SSsNAL; returns dict(alpha, w, status, objective, kkt, b, ...).
+    omp=True: the OpenMP build on all host cores (same results)."""
     X, f32 = _xarg(X)
     y = _yarg(y)
     n, q = X.shape
@@ -218,7 +233,7 @@ def solve(X, y, C_, alpha0=None, trace=False, **kw):
     w = np.zeros(q, np.float64)
     res = Result()
     tr = (Trace * max(P.max_outer, 1))() if trace else None
-    st = lib().orc_solve(_p(X), f32, _p(y), n, q, float(C_), C.byref(P), _p(alpha),
+    st = lib(omp).orc_solve(_p(X), f32, _p(y), n, q, float(C_), C.byref(P), _p(alpha),
                          0 if alpha0 is None else 1, _p(w), C.byref(res),
                          tr if trace else None)
     out = {k: getattr(res, k) for k, _ in Result._fields_ if k != "pad"}
@@ -229,3 +244,48 @@ def solve(X, y, C_, alpha0=None, trace=False, **kw):
         out["trace"] = [{k: getattr(tr[i], k) for k, _ in Trace._fields_ if k != "pad"}
                         for i in range(res.outer)]
     return out
+
+
+def _csrarg(indptr, indices, values):
+    ip = np.ascontiguousarray(indptr, dtype=np.int64)
+    ix = np.ascontiguousarray(indices, dtype=np.int32)
+    v = np.ascontiguousarray(values)
+    if v.dtype != np.float32:
+        v = np.ascontiguousarray(v, dtype=np.float64)
+    return ip, ix, v, int(v.dtype == np.float32)
+
+
+def matvec_csr(indptr, indices, values, q, y, v):
+    """z = A v for X in CSR form (n = len(indptr) - 1 rows, q columns)."""
+    ip, ix, vals, f32 = _csrarg(indptr, indices, values)
+    y = _yarg(y)
+    n = ip.size - 1
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    z = np.empty(n, np.float64)
+    assert lib().orc_matvec_csr(_p(ip), _p(ix), _p(vals), f32, _p(y), n, int(q), _p(v), _p(z)) == OK
+    return z
+
+
+def rmatvec_csr(indptr, indices, values, q, y, p):
+    """A' p for X in CSR form (q-vector)."""
+    ip, ix, vals, f32 = _csrarg(indptr, indices, values)
+    y = _yarg(y)
+    n = ip.size - 1
+    p = np.ascontiguousarray(p, dtype=np.float64)
+    out = np.empty(int(q), np.float64)
+    assert lib().orc_rmatvec_csr(_p(ip), _p(ix), _p(vals), f32, _p(y), n, int(q), _p(p), _p(out)) == OK
+    return out
+
+
+def kkt_csr(indptr, indices, values, q, y, C_, alpha, with_extras=False, omp=False):
+    """R_KKT of eq. (4.1) for X in CSR form; with_extras also returns
+    (lambda, A'alpha).  omp=True: the OpenMP build (same result)."""
+    ip, ix, vals, f32 = _csrarg(indptr, indices, values)
+    y = _yarg(y)
+    n = ip.size - 1
+    alpha = np.ascontiguousarray(alpha, dtype=np.float64)
+    lam = C.c_double(0.0)
+    w = np.empty(int(q), np.float64)
+    r = lib(omp).orc_kkt_csr(_p(ip), _p(ix), _p(vals), f32, _p(y), n, int(q), float(C_), _p(alpha),
+                             C.byref(lam), _p(w))
+    return (r, lam.value, w) if with_extras else r

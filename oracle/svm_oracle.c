@@ -29,6 +29,16 @@
  *
  * Reductions over n use pairwise (recursive halving) summation in FP64.
  *
+ * Threads.  The default build (oracle.build()) is single-threaded.  The same
+ * source compiled with -fopenmp (oracle.build(omp=True)) runs on all host
+ * cores for the timed CPU baseline and computes the same numbers bit for
+ * bit: only loops whose iterations are independent are split across threads,
+ * every sum keeps its order (the pairwise trees are evaluated as tasks, the
+ * Gram and the column sums let each thread own whole output entries), and the
+ * breakpoint sort is a merge of sorted chunks (a sorted array is the same
+ * whatever algorithm produced it).  Without -fopenmp the pragmas are ignored
+ * and the _OPENMP blocks are compiled out.
+ *
  * Parity status: every exported function is pinned by the CPU test-suite
  * (brute-force active-set enumeration, closed forms, finite differences,
  * invariants); see tests/test_oracle_*.py.
@@ -37,6 +47,20 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* loops and sums shorter than this stay on one thread in the OpenMP build */
+#define ORC_PAR_MIN 16384
+
+/* Inside a parallel region: this thread's index and the team size (0 and 1
+ * in the single-threaded build). */
+#ifdef _OPENMP
+#define ORC_TEAM(id, nt) int id = omp_get_thread_num(), nt = omp_get_num_threads()
+#else
+#define ORC_TEAM(id, nt) int id = 0, nt = 1
+#endif
 
 #define ORC_OK 0
 #define ORC_ERR_ARG 1
@@ -55,7 +79,7 @@ static double x_at(const void *X, int x_f32, int64_t q, int64_t i, int64_t j)
 }
 
 /* Pairwise summation of a[0..n). */
-static double pair_sum(const double *a, int64_t n)
+static double pair_sum_rec(const double *a, int64_t n)
 {
     if (n <= 16) {
         double s = 0.0;
@@ -63,7 +87,31 @@ static double pair_sum(const double *a, int64_t n)
         return s;
     }
     int64_t h = n / 2;
-    return pair_sum(a, h) + pair_sum(a + h, n - h);
+#ifdef _OPENMP
+    if (n > ORC_PAR_MIN) {   /* the same tree: the two halves as tasks */
+        double l = 0.0, r = 0.0;
+#pragma omp task shared(l)
+        l = pair_sum_rec(a, h);
+        r = pair_sum_rec(a + h, n - h);
+#pragma omp taskwait
+        return l + r;
+    }
+#endif
+    return pair_sum_rec(a, h) + pair_sum_rec(a + h, n - h);
+}
+
+static double pair_sum(const double *a, int64_t n)
+{
+#ifdef _OPENMP
+    if (n > ORC_PAR_MIN && !omp_in_parallel()) {
+        double s = 0.0;
+#pragma omp parallel
+#pragma omp single
+        s = pair_sum_rec(a, n);
+        return s;
+    }
+#endif
+    return pair_sum_rec(a, n);
 }
 
 static double dot_q(const double *a, const double *b, int64_t q)
@@ -80,6 +128,7 @@ int orc_matvec(const void *X, int x_f32, const int8_t *y, int64_t n, int64_t q,
                const double *v, double *z)
 {
     if (!X || !y || !v || !z || n < 0 || q < 0) return ORC_ERR_ARG;
+#pragma omp parallel for schedule(static) if (n > ORC_PAR_MIN)
     for (int64_t i = 0; i < n; ++i) {
         double s = 0.0;
         for (int64_t j = 0; j < q; ++j) s += x_at(X, x_f32, q, i, j) * v[j];
@@ -110,6 +159,23 @@ static void rmatvec_rec(const void *X, int x_f32, const int8_t *y, int64_t q,
     double *right = tmp_pool;            /* q doubles for the right half */
     double *pool2 = tmp_pool + q;        /* deeper levels */
     memset(right, 0, (size_t)q * sizeof(double));
+#ifdef _OPENMP
+    if (!absout && hi - lo > ORC_PAR_MIN) {
+        /* the same tree: the right half as a task with scratch of its own */
+        int levels = 2;
+        for (int64_t m = hi - mid; m > 32; m /= 2) ++levels;
+        double *pool_r = (double *)calloc((size_t)levels * (size_t)q, sizeof(double));
+        if (pool_r) {
+#pragma omp task
+            rmatvec_rec(X, x_f32, y, q, p, mid, hi, right, NULL, pool_r);
+            rmatvec_rec(X, x_f32, y, q, p, lo, mid, out, NULL, pool2);
+#pragma omp taskwait
+            free(pool_r);
+            for (int64_t j = 0; j < q; ++j) out[j] += right[j];
+            return;
+        }
+    }
+#endif
     rmatvec_rec(X, x_f32, y, q, p, lo, mid, out, absout, pool2);
     rmatvec_rec(X, x_f32, y, q, p, mid, hi, right, absout, pool2);
     for (int64_t j = 0; j < q; ++j) out[j] += right[j];
@@ -127,7 +193,96 @@ int orc_rmatvec(const void *X, int x_f32, const int8_t *y, int64_t n, int64_t q,
     if (!pool) return ORC_ERR_OOM;
     memset(out, 0, (size_t)q * sizeof(double));
     if (absscale) memset(absscale, 0, (size_t)q * sizeof(double));
+#ifdef _OPENMP
+    if (n > ORC_PAR_MIN && !omp_in_parallel()) {
+#pragma omp parallel
+#pragma omp single
+        rmatvec_rec(X, x_f32, y, q, p, 0, n, out, NULL, pool);
+        free(pool);
+        if (absscale) {
+            /* sum_i |p_i y_i x_ij| in row order, as the leaves above add it:
+             * each thread owns a block of the columns and walks all rows */
+#pragma omp parallel
+            {
+                ORC_TEAM(id, nt);
+                int64_t j0 = q * id / nt, j1 = q * (id + 1) / nt;
+                double *acc = (double *)calloc((size_t)(j1 - j0 + 1), sizeof(double));   /* own cache lines */
+                for (int64_t i = 0; acc && i < n; ++i) {
+                    double c = p[i] * (double)y[i];
+                    if (c == 0.0) continue;
+                    for (int64_t j = j0; j < j1; ++j) acc[j - j0] += fabs(c * x_at(X, x_f32, q, i, j));
+                }
+                for (int64_t j = j0; acc && j < j1; ++j) absscale[j] = acc[j - j0];
+                if (!acc && j0 < j1) absscale[j0] = NAN;
+                free(acc);
+            }
+        }
+        return ORC_OK;
+    }
+#endif
     rmatvec_rec(X, x_f32, y, q, p, 0, n, out, absscale, pool);
+    free(pool);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------ the same products, CSR X */
+
+/* Element k of a CSR value array, FP32 or FP64. */
+static double csr_val(const void *vals, int v_f32, int64_t k)
+{
+    if (v_f32) return (double)((const float *)vals)[k];
+    return ((const double *)vals)[k];
+}
+
+/* z = A v for X in CSR form (row i: columns ix[ip[i]..ip[i+1]), values
+ * vals, ascending columns); the stored entries are summed in column order,
+ * which is the dense loop of orc_matvec with its zero terms left out. */
+int orc_matvec_csr(const int64_t *ip, const int32_t *ix, const void *vals, int v_f32,
+                   const int8_t *y, int64_t n, int64_t q, const double *v, double *z)
+{
+    if (!ip || !y || !v || !z || n < 0 || q < 0) return ORC_ERR_ARG;
+#pragma omp parallel for schedule(static) if (n > ORC_PAR_MIN)
+    for (int64_t i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int64_t k = ip[i]; k < ip[i + 1]; ++k) s += csr_val(vals, v_f32, k) * v[ix[k]];
+        z[i] = (double)y[i] * s;
+    }
+    return ORC_OK;
+}
+
+/* out += sum_{i in [lo,hi)} p_i y_i x_i over CSR rows, pairwise over rows
+ * exactly as rmatvec_rec (the zero entries it adds change nothing). */
+static void rmatvec_csr_rec(const int64_t *ip, const int32_t *ix, const void *vals, int v_f32,
+                            const int8_t *y, int64_t q, const double *p, int64_t lo, int64_t hi,
+                            double *out, double *tmp_pool)
+{
+    if (hi - lo <= 32) {
+        for (int64_t i = lo; i < hi; ++i) {
+            double c = p[i] * (double)y[i];
+            if (c == 0.0) continue;
+            for (int64_t k = ip[i]; k < ip[i + 1]; ++k) out[ix[k]] += c * csr_val(vals, v_f32, k);
+        }
+        return;
+    }
+    int64_t mid = lo + (hi - lo) / 2;
+    double *right = tmp_pool, *pool2 = tmp_pool + q;
+    memset(right, 0, (size_t)q * sizeof(double));
+    rmatvec_csr_rec(ip, ix, vals, v_f32, y, q, p, lo, mid, out, pool2);
+    rmatvec_csr_rec(ip, ix, vals, v_f32, y, q, p, mid, hi, right, pool2);
+    for (int64_t j = 0; j < q; ++j) out[j] += right[j];
+}
+
+/* out = A' p for CSR X (q-vector). */
+int orc_rmatvec_csr(const int64_t *ip, const int32_t *ix, const void *vals, int v_f32,
+                    const int8_t *y, int64_t n, int64_t q, const double *p, double *out)
+{
+    if (!ip || !y || !p || !out || n < 0 || q < 0) return ORC_ERR_ARG;
+    int depth = 2;
+    for (int64_t m = n; m > 32; m /= 2) ++depth;
+    double *pool = (double *)calloc((size_t)(depth + 1) * (size_t)(q > 0 ? q : 1), sizeof(double));
+    if (!pool) return ORC_ERR_OOM;
+    memset(out, 0, (size_t)q * sizeof(double));
+    rmatvec_csr_rec(ip, ix, vals, v_f32, y, q, p, 0, n, out, pool);
     free(pool);
     return ORC_OK;
 }
@@ -147,6 +302,7 @@ static double clip0C(double t, double C)
 static double grad_phi(const double *u, const int8_t *y, int64_t n, double C,
                        double lam, double *tmp)
 {
+#pragma omp parallel for schedule(static) if (n > ORC_PAR_MIN)
     for (int64_t i = 0; i < n; ++i) {
         double yi = (double)y[i];
         tmp[i] = yi * clip0C(u[i] - lam * yi, C);
@@ -160,6 +316,40 @@ static int cmp_double(const void *a, const void *b)
     return (x > z) - (x < z);
 }
 
+/* Sort t[0..m) ascending.  The OpenMP build sorts one chunk per thread and
+ * merges the sorted chunks pairwise; the sorted array is the same. */
+static void sort_doubles(double *t, int64_t m)
+{
+#ifdef _OPENMP
+    int P = omp_get_max_threads();
+    double *buf = (P > 1 && m > ORC_PAR_MIN) ? (double *)malloc((size_t)m * sizeof(double)) : NULL;
+    int64_t *bnd = buf ? (int64_t *)malloc((size_t)(P + 1) * sizeof(int64_t)) : NULL;
+    if (bnd) {
+        for (int k = 0; k <= P; ++k) bnd[k] = m * k / P;
+#pragma omp parallel for schedule(static, 1)
+        for (int k = 0; k < P; ++k) qsort(t + bnd[k], (size_t)(bnd[k + 1] - bnd[k]), sizeof(double), cmp_double);
+        double *src = t, *dst = buf;
+        for (int w = 1; w < P; w *= 2) {
+#pragma omp parallel for schedule(static, 1)
+            for (int k = 0; k < P; k += 2 * w) {
+                int64_t lo = bnd[k], mid = bnd[k + w < P ? k + w : P], hi = bnd[k + 2 * w < P ? k + 2 * w : P];
+                int64_t a = lo, b = mid, o = lo;
+                while (a < mid && b < hi) dst[o++] = (src[a] <= src[b]) ? src[a++] : src[b++];
+                while (a < mid) dst[o++] = src[a++];
+                while (b < hi) dst[o++] = src[b++];
+            }
+            double *x = src; src = dst; dst = x;
+        }
+        if (src != t) memcpy(t, src, (size_t)m * sizeof(double));
+        free(bnd);
+        free(buf);
+        return;
+    }
+    free(buf);
+#endif
+    qsort(t, (size_t)m, sizeof(double), cmp_double);
+}
+
 /* Pi_{K cap L}(u) by Algorithm 2 (breakpoint search of Helgason et al.),
  * followed by the componentwise clip.  Writes pi (n) and returns lambda-hat
  * through *lam_out.  The breakpoints (v_i - u_i)/a_i, (v_i - l_i)/a_i of the
@@ -171,13 +361,14 @@ int orc_project(const double *u, const int8_t *y, int64_t n, double C,
     double *t = (double *)malloc((size_t)(2 * n) * sizeof(double));
     double *tmp = (double *)malloc((size_t)n * sizeof(double));
     if (!t || !tmp) { free(t); free(tmp); return ORC_ERR_OOM; }
+#pragma omp parallel for schedule(static) if (n > ORC_PAR_MIN)
     for (int64_t i = 0; i < n; ++i) {
         double yi = (double)y[i];
         t[2 * i] = yi * (u[i] - C);
         t[2 * i + 1] = yi * u[i];
     }
     /* Initialization: sort ascending t(1) <= ... <= t(2n). */
-    qsort(t, (size_t)(2 * n), sizeof(double), cmp_double);
+    sort_doubles(t, 2 * n);
     int64_t Il = 0, Iu = 2 * n - 1;         /* 0-based I_l = 1, I_u = 2n */
     double fl = grad_phi(u, y, n, C, t[Il], tmp);
     double fu = grad_phi(u, y, n, C, t[Iu], tmp);
@@ -190,6 +381,7 @@ int orc_project(const double *u, const int8_t *y, int64_t n, double C,
     double lam;
     if (fu == 0.0 && fl == 0.0) lam = t[Il];
     else lam = t[Il] - fl / (fu - fl) * (t[Iu] - t[Il]);
+#pragma omp parallel for schedule(static) if (n > ORC_PAR_MIN)
     for (int64_t i = 0; i < n; ++i) pi[i] = clip0C(u[i] - lam * (double)y[i], C);
     *lam_out = lam;
     free(t);
@@ -222,6 +414,7 @@ double orc_psi(const double *v, int64_t q, const double *u, const double *pi,
     double *tmp = (double *)malloc((size_t)n * sizeof(double));
     double *tmp2 = (double *)malloc((size_t)n * sizeof(double));
     if (!tmp || !tmp2) { free(tmp); free(tmp2); return NAN; }
+#pragma omp parallel for schedule(static) if (n > ORC_PAR_MIN)
     for (int64_t i = 0; i < n; ++i) {
         tmp[i] = pi[i] * (2.0 * u[i] - pi[i]);
         tmp2[i] = alpha[i] * alpha[i];
@@ -301,22 +494,38 @@ int orc_newton_direction(const void *X, int x_f32, const int8_t *y, int64_t n,
     /* h = A_J' a_J = sum_{i in J} (y_i x_i) y_i */
     double *h = (double *)calloc((size_t)q, sizeof(double));
     if (!h) return ORC_ERR_OOM;
-    for (int64_t r = 0; r < p; ++r) {
-        int64_t i = J[r];
-        double yy = (double)y[i] * (double)y[i];
-        for (int64_t j = 0; j < q; ++j) h[j] += yy * x_at(X, x_f32, q, i, j);
+    /* (OpenMP build: each thread owns a block of the columns, rows in order) */
+#pragma omp parallel if (p > 1024)
+    {
+        ORC_TEAM(id, nt);
+        int64_t j0 = q * id / nt, j1 = q * (id + 1) / nt;
+        double *acc = (double *)calloc((size_t)(j1 - j0 + 1), sizeof(double));   /* own cache lines */
+        for (int64_t r = 0; acc && r < p; ++r) {
+            int64_t i = J[r];
+            double yy = (double)y[i] * (double)y[i];
+            for (int64_t j = j0; j < j1; ++j) acc[j - j0] += yy * x_at(X, x_f32, q, i, j);
+        }
+        for (int64_t j = j0; acc && j < j1; ++j) h[j] = acc[j - j0];
+        if (!acc && j0 < j1) h[j0] = NAN;
+        free(acc);
     }
     double pp = (double)p;
     int rc = ORC_OK;
     if (form == 1) {
         double *M = (double *)calloc((size_t)(q * q), sizeof(double));
         if (!M) { free(h); return ORC_ERR_OOM; }
-        for (int64_t r = 0; r < p; ++r) {           /* A_J'A_J */
-            int64_t i = J[r];
-            for (int64_t a = 0; a < q; ++a) {
-                double xa = (double)y[i] * x_at(X, x_f32, q, i, a);
-                for (int64_t b = 0; b <= a; ++b)
-                    M[a * q + b] += xa * ((double)y[i] * x_at(X, x_f32, q, i, b));
+        /* A_J'A_J (OpenMP build: each thread owns every nt-th row of M and
+         * adds the free rows in order) */
+#pragma omp parallel if (p > 1024)
+        {
+            ORC_TEAM(id, nt);
+            for (int64_t r = 0; r < p; ++r) {
+                int64_t i = J[r];
+                for (int64_t a = id; a < q; a += nt) {
+                    double xa = (double)y[i] * x_at(X, x_f32, q, i, a);
+                    for (int64_t b = 0; b <= a; ++b)
+                        M[a * q + b] += xa * ((double)y[i] * x_at(X, x_f32, q, i, b));
+                }
             }
         }
         for (int64_t a = 0; a < q; ++a)
@@ -401,15 +610,44 @@ double orc_kkt(const void *X, int x_f32, const int8_t *y, int64_t n, int64_t q,
     if (!w || !Qa || !r || !pr) { free(w); free(Qa); free(r); free(pr); return NAN; }
     orc_rmatvec(X, x_f32, y, n, q, alpha, w, NULL);
     orc_matvec(X, x_f32, y, n, q, w, Qa);
+#pragma omp parallel for schedule(static) if (n > ORC_PAR_MIN)
     for (int64_t i = 0; i < n; ++i) r[i] = alpha[i] - Qa[i] + 1.0;
     double lam = 0.0;
     orc_project(r, y, n, C, pr, &lam);
+#pragma omp parallel for schedule(static) if (n > ORC_PAR_MIN)
     for (int64_t i = 0; i < n; ++i) { double d = alpha[i] - pr[i]; r[i] = d * d; pr[i] = alpha[i] * alpha[i]; }
     double num = sqrt(pair_sum(r, n)), na = sqrt(pair_sum(pr, n));
     if (lam_out) *lam_out = lam;
     if (w_out) memcpy(w_out, w, (size_t)q * sizeof(double));
     free(w); free(Qa); free(r); free(pr);
     return num / (1.0 + na);
+}
+
+/* R_KKT of eq. (4.1) for CSR X: the steps of orc_kkt with the CSR products. */
+double orc_kkt_csr(const int64_t *ip, const int32_t *ix, const void *vals, int v_f32,
+                   const int8_t *y, int64_t n, int64_t q, double C, const double *alpha,
+                   double *lam_out, double *w_out)
+{
+    double *w = (double *)malloc((size_t)(q > 0 ? q : 1) * sizeof(double));
+    double *Qa = (double *)malloc((size_t)n * sizeof(double));
+    double *r = (double *)malloc((size_t)n * sizeof(double));
+    double *pr = (double *)malloc((size_t)n * sizeof(double));
+    if (!w || !Qa || !r || !pr) { free(w); free(Qa); free(r); free(pr); return NAN; }
+    double res = NAN, lam = 0.0;
+    if (orc_rmatvec_csr(ip, ix, vals, v_f32, y, n, q, alpha, w) == ORC_OK &&
+        orc_matvec_csr(ip, ix, vals, v_f32, y, n, q, w, Qa) == ORC_OK) {
+#pragma omp parallel for schedule(static) if (n > ORC_PAR_MIN)
+        for (int64_t i = 0; i < n; ++i) r[i] = alpha[i] - Qa[i] + 1.0;
+        if (orc_project(r, y, n, C, pr, &lam) == ORC_OK) {
+#pragma omp parallel for schedule(static) if (n > ORC_PAR_MIN)
+            for (int64_t i = 0; i < n; ++i) { double d = alpha[i] - pr[i]; r[i] = d * d; pr[i] = alpha[i] * alpha[i]; }
+            res = sqrt(pair_sum(r, n)) / (1.0 + sqrt(pair_sum(pr, n)));
+        }
+    }
+    if (lam_out) *lam_out = lam;
+    if (w_out) memcpy(w_out, w, (size_t)q * sizeof(double));
+    free(w); free(Qa); free(r); free(pr);
+    return res;
 }
 
 /* Bias b (reading: the paper never defines b for the C-SVC).  b is a
@@ -423,13 +661,15 @@ double orc_bias(const void *X, int x_f32, const int8_t *y, int64_t n, int64_t q,
     double *k = (double *)malloc((size_t)n * sizeof(double));
     if (!k) return NAN;
     int64_t npos = 0;
+    for (int64_t i = 0; i < n; ++i)
+        if (y[i] > 0) ++npos;
+#pragma omp parallel for schedule(static) if (n > ORC_PAR_MIN)
     for (int64_t i = 0; i < n; ++i) {
         double m = 0.0;
         for (int64_t j = 0; j < q; ++j) m += x_at(X, x_f32, q, i, j) * w[j];
         k[i] = (double)y[i] - m;
-        if (y[i] > 0) ++npos;
     }
-    qsort(k, (size_t)n, sizeof(double), cmp_double);
+    sort_doubles(k, n);
     double lo, hi;
     if (npos == 0) { lo = -INFINITY; hi = k[0]; }
     else if (npos == n) { lo = k[n - 1]; hi = INFINITY; }
@@ -446,6 +686,7 @@ double orc_primal(const void *X, int x_f32, const int8_t *y, int64_t n, int64_t 
 {
     double *h = (double *)malloc((size_t)n * sizeof(double));
     if (!h) return NAN;
+#pragma omp parallel for schedule(static) if (n > ORC_PAR_MIN)
     for (int64_t i = 0; i < n; ++i) {
         double m = 0.0;
         for (int64_t j = 0; j < q; ++j) m += x_at(X, x_f32, q, i, j) * w[j];
@@ -504,6 +745,7 @@ void orc_default_params(orc_params *P)
 
 static double norm2(const double *a, int64_t n, double *tmp)
 {
+#pragma omp parallel for schedule(static) if (n > ORC_PAR_MIN)
     for (int64_t i = 0; i < n; ++i) tmp[i] = a[i] * a[i];
     return sqrt(pair_sum(tmp, n));
 }
@@ -556,6 +798,7 @@ int orc_solve(const void *X, int x_f32, const int8_t *y, int64_t n, int64_t q,
         /* reading: inner tolerances eps_k = delta_k = 0.1 * 0.5^k */
         double epsk = 0.1 * pow(0.5, (double)k);
         double asq = 0.0;
+#pragma omp parallel for schedule(static) if (n > ORC_PAR_MIN)
         for (int64_t i = 0; i < n; ++i) tmp[i] = alpha[i] * alpha[i];
         asq = pair_sum(tmp, n);
         orc_matvec(X, x_f32, y, n, q, v, z);            /* z = A v = Q w */
@@ -564,6 +807,7 @@ int orc_solve(const void *X, int x_f32, const int8_t *y, int64_t n, int64_t q,
         int64_t p = 0;
         for (j = 0; ; ++j) {
             /* u(w) = x^k - sigma (Q w + c), c = -e  (eq. (3.3)) */
+#pragma omp parallel for schedule(static) if (n > ORC_PAR_MIN)
             for (int64_t i = 0; i < n; ++i) u[i] = alpha[i] - sigma * (z[i] - 1.0);
             orc_project(u, y, n, C, pi, &lam);
             /* grad psi = Q w - Q Pi(u) = A g,  g = v - A'pi  (eq. (3.10)) */
@@ -571,6 +815,7 @@ int orc_solve(const void *X, int x_f32, const int8_t *y, int64_t n, int64_t q,
             for (int64_t c = 0; c < q; ++c) g[c] = v[c] - atp[c];
             gn = sqrt(dot_q(g, g, q));
             /* stopping tests (A') and (B') in q-space, with a roundoff floor */
+#pragma omp parallel for schedule(static) if (n > ORC_PAR_MIN)
             for (int64_t i = 0; i < n; ++i) { double d = pi[i] - alpha[i]; tmp[i] = d * d; }
             double dx = sqrt(pair_sum(tmp, n));
             double tol_in = fmin(epsk, epsk * dx) / sqrt(sigma);
@@ -587,8 +832,10 @@ int orc_solve(const void *X, int x_f32, const int8_t *y, int64_t n, int64_t q,
             double t = 1.0;
             int m, accepted = 0;
             for (m = 0; m < P->max_ls; ++m) {
+#pragma omp parallel for schedule(static) if (n > ORC_PAR_MIN)
                 for (int64_t i = 0; i < n; ++i) ut[i] = u[i] - t * sigma * dz[i];
                 orc_project(ut, y, n, C, pit, &lam_t);
+#pragma omp parallel for schedule(static) if (n > ORC_PAR_MIN)
                 for (int64_t i = 0; i < n; ++i)
                     tmp[i] = pit[i] * (2.0 * ut[i] - pit[i]) - pi[i] * (2.0 * u[i] - pi[i]);
                 double dpsi = t * vdv + 0.5 * t * t * dvdv + pair_sum(tmp, n) / (2.0 * sigma);
@@ -598,11 +845,13 @@ int orc_solve(const void *X, int x_f32, const int8_t *y, int64_t n, int64_t q,
             if (!accepted) { ls_fail = 1; continue; }
             /* Step 3 */
             for (int64_t c = 0; c < q; ++c) v[c] += t * dv[c];
+#pragma omp parallel for schedule(static) if (n > ORC_PAR_MIN)
             for (int64_t i = 0; i < n; ++i) z[i] += t * dz[i];
         }
         inner_total += j;
         (void)asq;
         /* Step 2 of Algorithm 1 in the simplified form of eq. (3.5) */
+#pragma omp parallel for schedule(static) if (n > ORC_PAR_MIN)
         for (int64_t i = 0; i < n; ++i) alpha[i] = pi[i];
         R = orc_kkt(X, x_f32, y, n, q, C, alpha, NULL, NULL);
         if (trace) {
@@ -632,6 +881,7 @@ done:
         res->kkt = orc_kkt(X, x_f32, y, n, q, C, alpha, &lamk, w);
         res->lam_kkt = lamk;
         double wsq = dot_q(w, w, q);
+#pragma omp parallel for schedule(static) if (n > ORC_PAR_MIN)
         for (int64_t i = 0; i < n; ++i) tmp[i] = alpha[i];
         double sa = pair_sum(tmp, n);
         res->objective = 0.5 * wsq - sa;

@@ -19,6 +19,7 @@ OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_NOT_CONVERGED, ERR_NUMERIC, ERR_DEGE
 DENSE_ROWMAJOR, CSR = 0, 1
 F32, F64 = 0, 1
 PREC_PLAIN_FP64, PREC_MIXED = 0, 1
+FORM_FP64_DIRECT, FORM_MIXED, FORM_COMPENSATED, FORM_FP64_CG = range(4)
 MEM_DEVICE, MEM_HOST = 0, 1
 
 
@@ -41,8 +42,24 @@ class Result(C.Structure):
     _fields_ = [("alpha", C.c_void_p), ("w", C.c_void_p), ("b", C.c_double), ("kkt", C.c_double),
                 ("objective", C.c_double), ("primal_objective", C.c_double), ("gap", C.c_double),
                 ("sigma", C.c_double), ("outer_iters", C.c_int32), ("inner_iters_total", C.c_int32),
-                ("status", C.c_int32), ("reserved0", C.c_int32), ("n_free", C.c_int64),
+                ("status", C.c_int32), ("form", C.c_int32), ("n_free", C.c_int64),
                 ("n_upper", C.c_int64), ("n_sv", C.c_int64)]
+
+
+GQP_DENSE, GQP_STACKED = 0, 1
+
+
+class GqpProblem(C.Structure):
+    _fields_ = [("n", C.c_int64), ("q", C.c_int64), ("layout", C.c_int32), ("dtype", C.c_int32),
+                ("memory", C.c_int32), ("reserved0", C.c_int32), ("B", C.c_void_p), ("c", C.c_void_p),
+                ("a", C.c_void_p), ("l", C.c_void_p), ("u", C.c_void_p), ("d", C.c_double)]
+
+
+class GqpResult(C.Structure):
+    _fields_ = [("x", C.c_void_p), ("w", C.c_void_p), ("lam", C.c_double), ("kkt", C.c_double),
+                ("objective", C.c_double), ("feasibility", C.c_double), ("sigma", C.c_double),
+                ("outer_iters", C.c_int32), ("inner_iters_total", C.c_int32), ("status", C.c_int32),
+                ("reserved0", C.c_int32), ("n_free", C.c_int64)]
 
 
 class Stats(C.Structure):
@@ -57,7 +74,9 @@ SYMBOLS = ["svm_default_params", "svm_ssnalm_create", "svm_ssnalm_solve", "svm_s
            "svm_op_newton", "svm_op_kkt", "svm_op_gram", "svm_ssnalm_solve_batch", "svm_rff_features", "svm_ssnalm_set_timing", "svm_ssnalm_get_stats",
            "svm_rmatvec_noalloc", "svm_mlp_create", "svm_mlp_destroy", "svm_mlp_get_params",
            "svm_mlp_features", "svm_mlp_labels", "svm_mlp_gather", "svm_mlp_forward", "svm_mlp_loss_grad", "svm_mlp_adam_step",
-           "svm_mlp_train_step", "svm_mlp_start_point", "svm_ssnalm_solve_mlp"]
+           "svm_mlp_train_step", "svm_mlp_start_point", "svm_ssnalm_solve_mlp", "svm_ssnalm_set_warmstart_model",
+           "svm_gqp_create", "svm_svr_create", "svm_gqp_solve", "svm_gqp_destroy", "svm_gqp_last_error",
+           "svm_gqp_op_project", "svm_gqp_op_newton", "svm_gqp_op_matvec", "svm_gqp_op_rmatvec"]
 MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_NPARAM = 132, 256, 3, 100611
 
 _lock = threading.Lock()
@@ -116,12 +135,27 @@ def load(build_if_missing: bool = False):
         L.svm_mlp_train_step.argtypes = [vp, vp, vp, i64, vp, i64, f32, f32, vp]
         L.svm_mlp_start_point.argtypes = [vp, vp, i64, dbl, vp]
         L.svm_ssnalm_solve_mlp.argtypes = [vp, vp, C.POINTER(Result), C.POINTER(C.c_int32)]
+        L.svm_ssnalm_set_warmstart_model.argtypes = [vp, vp]
+        L.svm_gqp_create.argtypes = [C.POINTER(vp), C.POINTER(GqpProblem), C.POINTER(Params)]
+        L.svm_svr_create.argtypes = [C.POINTER(vp), vp, i64, i64, C.c_int32, C.c_int32, vp, C.c_double,
+                                     C.POINTER(Params)]
+        L.svm_gqp_solve.argtypes = [vp, C.POINTER(GqpResult)]
+        L.svm_gqp_destroy.argtypes = [vp]
+        L.svm_gqp_destroy.restype = None
+        L.svm_gqp_last_error.argtypes = [vp]
+        L.svm_gqp_last_error.restype = C.c_char_p
+        L.svm_gqp_op_project.argtypes = [vp, vp, vp, C.POINTER(C.c_double), vp, C.POINTER(i64)]
+        L.svm_gqp_op_newton.argtypes = [vp, vp, i64, C.c_double, vp, vp]
+        L.svm_gqp_op_matvec.argtypes = [vp, vp, vp]
+        L.svm_gqp_op_rmatvec.argtypes = [vp, vp, vp]
         for f in ("svm_op_matvec", "svm_op_rmatvec", "svm_op_project", "svm_op_newton", "svm_op_kkt", "svm_op_gram",
                   "svm_ssnalm_solve_batch", "svm_rff_features",
                   "svm_ssnalm_set_timing", "svm_ssnalm_get_stats", "svm_rmatvec_noalloc", "svm_mlp_create",
                   "svm_mlp_get_params", "svm_mlp_features", "svm_mlp_labels", "svm_mlp_gather", "svm_mlp_forward",
                   "svm_mlp_loss_grad",
-                  "svm_mlp_adam_step", "svm_mlp_train_step", "svm_mlp_start_point", "svm_ssnalm_solve_mlp"):
+                  "svm_mlp_adam_step", "svm_mlp_train_step", "svm_mlp_start_point", "svm_ssnalm_solve_mlp",
+                  "svm_ssnalm_set_warmstart_model", "svm_gqp_create", "svm_svr_create", "svm_gqp_solve",
+                  "svm_gqp_op_project", "svm_gqp_op_newton", "svm_gqp_op_matvec", "svm_gqp_op_rmatvec"):
             getattr(L, f).restype = C.c_int
         _lib = L
         return L
@@ -143,9 +177,36 @@ def default_params(**kw) -> Params:
     return P
 
 
+def _check_noalloc_args(X, y, c, out):
+    """Types, shapes and devices of svm_rmatvec_noalloc's buffers: the C call
+    trusts them, so a wrong one would make the kernel read or write outside a
+    buffer.  Raises TypeError / ValueError."""
+    for name, t in (("X", X), ("y", y), ("c", c), ("out", out)):
+        if not hasattr(t, "data_ptr"):
+            raise TypeError(f"{name} must be a torch tensor")
+    want = (("X", X, "float32"), ("y", y, "int8"), ("c", c, "float64"), ("out", out, "float64"))
+    for name, t, dt in want:
+        if not str(t.dtype).endswith(dt):
+            raise TypeError(f"{name} must be {dt}, got {t.dtype}")
+    if X.dim() != 2:
+        raise ValueError("X must be 2-D (n x q)")
+    n, q = X.shape
+    for name, t, m in (("y", y, n), ("c", c, n), ("out", out, q)):
+        if tuple(t.shape) != (m,):
+            raise ValueError(f"{name} must have shape ({m},), got {tuple(t.shape)}")
+    devs = {(t.device.type, t.device.index) for t in (X, y, c, out)}
+    if any(d[0] != "cuda" for d in devs) or len(devs) != 1:
+        raise ValueError("X, y, c and out must be CUDA tensors on one device")
+    import torch
+    if next(iter(devs))[1] != torch.cuda.current_device():
+        raise ValueError("the buffers must be on the current CUDA device")
+
+
 def rmatvec_noalloc(X, y, c, out, stream=None) -> int:
-    """out = A'c through the allocation-free entry point (device FP32 X, int8
-    y, FP64 c and out); returns the svm_status code."""
+    """out = A'c through the allocation-free entry point (device FP32 X (n x q),
+    int8 y (n), FP64 c (n) and out (q), all on the current device); returns the
+    svm_status code.  Raises TypeError / ValueError for other buffers."""
+    _check_noalloc_args(X, y, c, out)
     n, q = X.shape
     return load().svm_rmatvec_noalloc(_ptr(X), _ptr(y), int(n), int(q), _ptr(c), _ptr(out), stream)
 
@@ -240,7 +301,7 @@ class Solver:
         R = Result(alpha=_ptr(alpha), w=_ptr(w))
         st = self._lib.svm_ssnalm_solve(self.h, _ptr(alpha0), C.byref(R))
         self._check(st, allow)
-        out = {k: getattr(R, k) for k, _ in Result._fields_ if k not in ("alpha", "w", "reserved0")}
+        out = {k: getattr(R, k) for k, _ in Result._fields_ if k not in ("alpha", "w")}
         out["status"] = st
         return out
 
@@ -256,7 +317,7 @@ class Solver:
         self._check(st, allow)
         outs = []
         for b in range(B):
-            outs.append({k: getattr(R[b], k) for k, _ in Result._fields_ if k not in ("alpha", "w", "reserved0")})
+            outs.append({k: getattr(R[b], k) for k, _ in Result._fields_ if k not in ("alpha", "w")})
         return st, outs
 
     def solve_mlp(self, mlp, alpha, w, allow=(OK, ERR_NOT_CONVERGED, ERR_DEGENERATE)):
@@ -266,10 +327,15 @@ class Solver:
         used = C.c_int32(0)
         st = self._lib.svm_ssnalm_solve_mlp(self.h, mlp.h, C.byref(R), C.byref(used))
         self._check(st, allow)
-        out = {k: getattr(R, k) for k, _ in Result._fields_ if k not in ("alpha", "w", "reserved0")}
+        out = {k: getattr(R, k) for k, _ in Result._fields_ if k not in ("alpha", "w")}
         out["status"] = st
         out["used_warm"] = used.value
         return out
+
+    def set_warmstart_model(self, params=None):
+        """Attach a trained network (device FP32 parameter vector, copied) so
+        that solve() without alpha0 starts from its prediction; None detaches."""
+        self._check(self._lib.svm_ssnalm_set_warmstart_model(self.h, _ptr(params)))
 
     def set_timing(self, enable=True):
         self._check(self._lib.svm_ssnalm_set_timing(self.h, 1 if enable else 0))
@@ -372,3 +438,99 @@ class MLP:
     def start_point(self, F, C_, alpha0):
         _mlp_check(self._lib.svm_mlp_start_point(self.h, _ptr(F), int(F.shape[0]), float(C_), _ptr(alpha0)),
                    "svm_mlp_start_point")
+
+
+class GQP:
+    """Owns one svm_gqp_t: SSsNAL for the unified QP of eq. (1.5),
+    min 1/2 x'BB'x + c'x s.t. a'x = d, l <= x <= u.  B (n x q, or X (n/2 x q)
+    with stacked=True for B = [X; -X]) and the FP64 vectors c, a, l, u are all
+    torch CUDA tensors (borrowed: keep them alive) or all host arrays (copied)."""
+
+    def __init__(self, B, c, a, l, u, d=0.0, stacked=False, stream=None, _h=None, _keep=None, **params):
+        self._lib = load()
+        self.h = C.c_void_p()
+        P = default_params(**params)
+        if stream is not None:
+            P.stream = stream
+        self.params = P
+        if _h is not None:           # built by GQP.svr
+            self.h, (self.n, self.q, self.memory), self._keep = _h, _keep[0], _keep[1]
+            return
+        is_host = not bool(getattr(B, "is_cuda", False))
+        self.memory = MEM_HOST if is_host else MEM_DEVICE
+        dt = str(B.dtype)
+        dtype = F32 if dt.endswith("float32") else F64 if dt.endswith("float64") else None
+        if dtype is None:
+            raise TypeError(f"B dtype {dt} not supported")
+        m, q = B.shape
+        n = 2 * m if stacked else m
+        self.n, self.q = int(n), int(q)
+        self._keep = (B, c, a, l, u)
+        prob = GqpProblem(n=n, q=q, layout=GQP_STACKED if stacked else GQP_DENSE, dtype=dtype, memory=self.memory,
+                          B=_ptr(B), c=_ptr(c), a=_ptr(a), l=_ptr(l), u=_ptr(u), d=float(d))
+        st = self._lib.svm_gqp_create(C.byref(self.h), C.byref(prob), C.byref(P))
+        if st != OK:
+            raise SVMError(st, self._lib.svm_gqp_last_error(None).decode())
+
+    @classmethod
+    def svr(cls, X, y, eps, C_, stream=None, **params):
+        """The linear SVR dual (eq. (1.4)) over X (m x q) and targets y (FP64, m)."""
+        L = load()
+        P = default_params(C=float(C_), **params)
+        if stream is not None:
+            P.stream = stream
+        is_host = not bool(getattr(X, "is_cuda", False))
+        dt = str(X.dtype)
+        dtype = F32 if dt.endswith("float32") else F64 if dt.endswith("float64") else None
+        if dtype is None:
+            raise TypeError(f"X dtype {dt} not supported")
+        m, q = X.shape
+        h = C.c_void_p()
+        st = L.svm_svr_create(C.byref(h), _ptr(X), int(m), int(q), dtype, MEM_HOST if is_host else MEM_DEVICE,
+                              _ptr(y), float(eps), C.byref(P))
+        if st != OK:
+            raise SVMError(st, L.svm_gqp_last_error(None).decode())
+        return cls(None, None, None, None, None, stream=stream, _h=h,
+                   _keep=((2 * int(m), int(q), MEM_HOST if is_host else MEM_DEVICE), (X,)), **params)
+
+    def close(self):
+        if self.h:
+            self._lib.svm_gqp_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def last_error(self) -> str:
+        return self._lib.svm_gqp_last_error(self.h).decode()
+
+    def _check(self, st, allow=(OK,)):
+        if st not in allow:
+            raise SVMError(st, self.last_error())
+        return st
+
+    def solve(self, x, w, allow=(OK, ERR_NOT_CONVERGED)):
+        """x (n), w (q): FP64 output buffers in the problem's memory kind."""
+        R = GqpResult(x=_ptr(x), w=_ptr(w))
+        st = self._lib.svm_gqp_solve(self.h, C.byref(R))
+        self._check(st, allow)
+        out = {k: getattr(R, k) for k, _ in GqpResult._fields_ if k not in ("x", "w", "reserved0")}
+        out["status"] = st
+        return out
+
+    def project(self, w, x, J=None):
+        lam, p = C.c_double(0.0), C.c_int64(0)
+        self._check(self._lib.svm_gqp_op_project(self.h, _ptr(w), _ptr(x), C.byref(lam), _ptr(J), C.byref(p)))
+        return lam.value, p.value
+
+    def newton(self, J, p, sigma, g, dv):
+        self._check(self._lib.svm_gqp_op_newton(self.h, _ptr(J), int(p), float(sigma), _ptr(g), _ptr(dv)))
+
+    def matvec(self, v, z):
+        self._check(self._lib.svm_gqp_op_matvec(self.h, _ptr(v), _ptr(z)))
+
+    def rmatvec(self, y, out):
+        self._check(self._lib.svm_gqp_op_rmatvec(self.h, _ptr(y), _ptr(out)))

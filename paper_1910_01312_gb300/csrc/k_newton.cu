@@ -1835,4 +1835,21 @@ cudaError_t launch_newton(Work &W, const int32_t *J, long long p_host, const lon
     return (e == cudaSuccess && dots) ? launch_dots(W) : e;
 }
 
+// The FP64 Cholesky solve above for another caller (the unified-QP solver).
+cudaError_t launch_chol_solve(int q, double *M, const double *g, double *dv, int *err, cudaStream_t st)
+{
+    if (q <= 144) {
+        if (!g_chol_smem_set) {
+            const cudaError_t ea =
+                cudaFuncSetAttribute(chol_solve_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            if (ea != cudaSuccess) return ea;
+            g_chol_smem_set = 1;
+        }
+        chol_solve_kernel<true><<<1, 1024, ((size_t)q * q + q) * sizeof(double), st>>>(q, M, g, dv, err);
+    } else {
+        chol_solve_kernel<false><<<1, 1024, 0, st>>>(q, M, g, dv, err);
+    }
+    return cudaGetLastError();
+}
+
 }  // namespace svm

@@ -146,6 +146,13 @@ extern "C" svm_status svm_rmatvec_noalloc(const float *X, const int8_t *y, int64
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return SVM_ERR_CUDA;
     if (dev < 0 || dev >= kMaxDevices) return SVM_ERR_UNSUPPORTED;
+    if (stream) {
+        // the scratch address and the SM count below are the current device's:
+        // a stream of another device would run the kernel on memory it cannot use
+        int sdev = -1;
+        if (cudaStreamGetDevice((cudaStream_t)stream, &sdev) != cudaSuccess) return SVM_ERR_CUDA;
+        if (sdev != dev) return SVM_ERR_INVALID_ARG;
+    }
     void *scr = nullptr;
     int nsm = 0;
     {

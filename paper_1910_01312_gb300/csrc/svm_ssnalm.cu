@@ -68,6 +68,7 @@ struct svm_ssnalm {
     long long batch_ticks = 0;
     NewtonTask *nt_host = nullptr, *nt_dev = nullptr;   // batched Newton steps (pinned / device table)
     int nt_cap = 0;
+    svm_mlp_t *wsm = nullptr;   // warm-start network of svm_ssnalm_set_warmstart_model (owned)
 };
 
 enum { TK_MATVEC = 0, TK_RMATVEC = 1, TK_PROJ = 2, TK_NEWTON = 3 };
@@ -183,6 +184,7 @@ extern "C" void svm_ssnalm_destroy(svm_ssnalm_t *h)
     for (void *p : bp)
         if (p) cudaFree(p);
     if (h->nt_host) cudaFreeHost(h->nt_host);
+    svm_mlp_destroy(h->wsm);
     free_work(h->W);
     delete h;
 }
@@ -964,22 +966,34 @@ static svm_status run_after(Run &r)
 }
 
 // Start a run: checks, then the degenerate case or the first phase.
+// The arithmetic a solve of this handle runs (svm_form of the header).
+static int32_t solve_form(const Work &W)
+{
+    const bool mixed = W.precision == SVM_PREC_MIXED;
+    if (W.csr) return (mixed && W.xf32) ? SVM_FORM_COMPENSATED : SVM_FORM_FP64_CG;
+    if (W.df) return SVM_FORM_MIXED;
+    if (mixed) return W.xf32 ? SVM_FORM_COMPENSATED : SVM_FORM_FP64_CG;
+    return SVM_FORM_FP64_DIRECT;
+}
+
 static svm_status run_begin(Run &r, svm_ssnalm *h, const double *alpha0, svm_result *res)
 {
     r = Run();
     r.h = h;
     r.alpha0 = alpha0;
     r.res = res;
+    res->form = solve_form(h->W);
     h->err.clear();
     if (h->npos == 0 || h->npos == h->W.n) return run_degenerate(r);
     r.ph = RP_INIT;
     return SVM_OK;
 }
 
-extern "C" svm_status svm_ssnalm_solve(svm_ssnalm_t *h, const double *alpha0, svm_result *res)
+static svm_status solve_mlp_impl(svm_ssnalm *h, svm_mlp_t *m, svm_result *res, int32_t *used_warm);
+
+// One solve from alpha0 (NULL: the cold start), never the learned warm start.
+static svm_status solve_direct(svm_ssnalm *h, const double *alpha0, svm_result *res)
 {
-    if (!h) return SVM_ERR_INVALID_ARG;
-    if (!res || !res->alpha || !res->w) { h->err = "result buffers must be non-null"; return SVM_ERR_INVALID_ARG; }
     Run r;
     svm_status st = run_begin(r, h, alpha0, res);
     if (st != SVM_OK) return st;
@@ -993,6 +1007,14 @@ extern "C" svm_status svm_ssnalm_solve(svm_ssnalm_t *h, const double *alpha0, sv
         if ((st = run_after(r)) != SVM_OK) return st;
     }
     return r.ret;
+}
+
+extern "C" svm_status svm_ssnalm_solve(svm_ssnalm_t *h, const double *alpha0, svm_result *res)
+{
+    if (!h) return SVM_ERR_INVALID_ARG;
+    if (!res || !res->alpha || !res->w) { h->err = "result buffers must be non-null"; return SVM_ERR_INVALID_ARG; }
+    if (!alpha0 && h->wsm) return solve_mlp_impl(h, h->wsm, res, nullptr);
+    return solve_direct(h, alpha0, res);
 }
 
 // ------------------------------------------------------------ batched solves
@@ -1439,10 +1461,9 @@ extern "C" svm_status svm_ssnalm_get_stats(svm_ssnalm_t *h, svm_stats *out, int 
 // Warm start from the learned network (include/svm_mlp.h), with the cold solve
 // as fallback.  The paper's own warm start is a cheaper solve of an
 // approximating problem (Sec. 4.3); the network plays that role here.
-extern "C" svm_status svm_ssnalm_solve_mlp(svm_ssnalm_t *h, svm_mlp_t *m, svm_result *res, int32_t *used_warm)
+static svm_status solve_mlp_impl(svm_ssnalm *h, svm_mlp_t *m, svm_result *res, int32_t *used_warm)
 {
     if (used_warm) *used_warm = 0;
-    if (!h || !m || !res) return SVM_ERR_INVALID_ARG;
     Work &W = h->W;
     if (W.csr || !W.xf32 || W.q != SVM_MLP_IN - 4) {
         h->err = "the warm-start network needs dense FP32 X with q = 128";
@@ -1472,10 +1493,36 @@ extern "C" svm_status svm_ssnalm_solve_mlp(svm_ssnalm_t *h, svm_mlp_t *m, svm_re
         h->err = "warm-start features or network failed";
         return st;
     }
-    st = svm_ssnalm_solve(h, h->prob.memory == SVM_MEM_HOST ? host_a0.data() : a0, res);
+    st = solve_direct(h, h->prob.memory == SVM_MEM_HOST ? host_a0.data() : a0, res);
     cudaFreeAsync(F, W.st);
     cudaFreeAsync(a0, W.st);
-    if (st == SVM_ERR_NOT_CONVERGED || st == SVM_ERR_NUMERIC) return svm_ssnalm_solve(h, nullptr, res);
+    if (st == SVM_ERR_NOT_CONVERGED || st == SVM_ERR_NUMERIC) return solve_direct(h, nullptr, res);
     if (used_warm) *used_warm = 1;
+    return st;
+}
+
+extern "C" svm_status svm_ssnalm_solve_mlp(svm_ssnalm_t *h, svm_mlp_t *m, svm_result *res, int32_t *used_warm)
+{
+    if (used_warm) *used_warm = 0;
+    if (!h || !m || !res || !res->alpha || !res->w) return SVM_ERR_INVALID_ARG;
+    return solve_mlp_impl(h, m, res, used_warm);
+}
+
+extern "C" svm_status svm_ssnalm_set_warmstart_model(svm_ssnalm_t *h, const float *mlp_weights)
+{
+    if (!h) return SVM_ERR_INVALID_ARG;
+    svm_mlp_destroy(h->wsm);
+    h->wsm = nullptr;
+    if (!mlp_weights) return SVM_OK;
+    const Work &W = h->W;
+    if (W.csr || !W.xf32 || W.q != SVM_MLP_IN - 4) {
+        h->err = "the warm-start network needs dense FP32 X with q = 128";
+        return SVM_ERR_UNSUPPORTED;
+    }
+    const svm_status st = svm_mlp_create(&h->wsm, mlp_weights, W.n, W.st);
+    if (st != SVM_OK) {
+        h->wsm = nullptr;
+        h->err = "could not create the warm-start network (allocation or copy failed)";
+    }
     return st;
 }

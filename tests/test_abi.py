@@ -80,3 +80,34 @@ def test_binding_rejects_non_contiguous_buffers():
     with pytest.raises(ValueError):
         P.binding._ptr(X)
     assert P.binding._ptr(np.zeros((6, 4))) != 0 and P.binding._ptr(None) is None
+
+
+def test_noalloc_binding_rejects_wrong_buffers_before_the_call():
+    """The allocation-free product trusts its pointers, so the binding checks
+    dtypes, shapes and devices first (no GPU needed: the checks raise before
+    any C call)."""
+    torch = pytest.importorskip("torch")
+    n, q = 6, 4
+    X = torch.zeros((n, q), dtype=torch.float32)
+    y = torch.ones(n, dtype=torch.int8)
+    c = torch.zeros(n, dtype=torch.float64)
+    out = torch.zeros(q, dtype=torch.float64)
+    chk = P.binding._check_noalloc_args
+    with pytest.raises(TypeError):
+        chk(X.double(), y, c, out)                  # FP64 X
+    with pytest.raises(TypeError):
+        chk(X, y.to(torch.int32), c, out)            # labels not int8
+    with pytest.raises(TypeError):
+        chk(X, y, c.float(), out)                    # FP32 weights: the kernel would read 8n bytes
+    with pytest.raises(TypeError):
+        chk(X, y, c, out.float())                    # FP32 output: the kernel would write 8q bytes
+    with pytest.raises(ValueError):
+        chk(X, y, c[:-1], out)                       # short c
+    with pytest.raises(ValueError):
+        chk(X, y, c, torch.zeros(q - 1, dtype=torch.float64))   # short out
+    with pytest.raises(ValueError):
+        chk(X.reshape(-1), y, c, out)                # X not 2-D
+    with pytest.raises(ValueError):
+        chk(X, y, c, out)                            # host tensors
+    with pytest.raises(TypeError):
+        chk(X.numpy(), y, c, out)                    # not a tensor

@@ -1,6 +1,7 @@
 """The benchmark's reference arm runs on the host cores (the FP64 oracle), so
 its JSON line can be checked here without a GPU: one line, the contract's
-keys, the same metric and workload as the GPU arm, and a converged solve."""
+keys, the same metric and workload as the GPU arm, and a converged solve
+(on a 20,000-row problem here; the arm itself solves the full workload)."""
 import json
 import os
 import subprocess
@@ -11,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def test_reference_arm_json_line():
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                          "--warmup", "3"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+                          "--warmup", "3", "--ref-n", "20000"], capture_output=True, text=True, timeout=600, cwd=ROOT)
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
     assert len(lines) == 1
@@ -22,7 +23,8 @@ def test_reference_arm_json_line():
     assert line["impl"] == "reference"
     assert line["metric"] == "time-to-KKT<=1e-6 per SVM solve" and line["unit"] == "ms"
     assert line["higher_is_better"] is False and line["steps"] == 1 and line["warmup"] == 3
-    assert line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["cpu_baseline"]["nproc"] >= 1 and line["cpu_baseline"]["cpu_model"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
     assert line["config"]["workload"].startswith("gauss1m")
     assert line["solve"]["kkt"] <= 1e-6
@@ -33,7 +35,7 @@ def test_reference_arm_under_two_ranks_prints_once():
     and prints the line; rank 1 exits 0 without work."""
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
            "--master-addr", "127.0.0.1", "--master-port", "29517", os.path.join(ROOT, "bench.py"),
-           "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "3"]
+           "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "3", "--ref-n", "20000"]
     out = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=ROOT)
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [l for l in out.stdout.splitlines() if l.startswith("{")]

@@ -219,3 +219,41 @@ def test_cold_fallback_when_the_warm_solve_fails():
     assert warm["kkt"] == cold["kkt"]
     s.close()
     net.close()
+
+
+def test_attached_network_drives_solve_without_alpha0():
+    """svm_ssnalm_set_warmstart_model: once a network is attached, solve()
+    without alpha0 is the warm-started solve (bit-identical to solve_mlp with
+    the same parameters); detaching restores the cold solve bit for bit."""
+    X, y, C = datagen.warm_instance(13, n=4000)
+    Xd, yd = dev(X), dev(y)
+    theta = dev(_params(14))
+    net = P.MLP(theta, 4000)
+    s = P.Solver(Xd, yd, C_=C, precision=P.PREC_MIXED)
+    bufs = [(torch.empty(4000, dtype=torch.float64, device="cuda"),
+             torch.empty(128, dtype=torch.float64, device="cuda")) for _ in range(4)]
+    cold = s.solve(*bufs[0])
+    ref = s.solve_mlp(net, *bufs[1])
+    s.set_warmstart_model(theta)
+    att = s.solve(*bufs[2])
+    s.set_warmstart_model(None)
+    cold2 = s.solve(*bufs[3])
+    assert ref["status"] == P.OK
+    np.testing.assert_array_equal(host(bufs[2][0]), host(bufs[1][0]))
+    assert att["kkt"] == ref["kkt"] and att["outer_iters"] == ref["outer_iters"]
+    np.testing.assert_array_equal(host(bufs[3][0]), host(bufs[0][0]))
+    assert cold2["inner_iters_total"] == cold["inner_iters_total"]
+    s.close()
+    net.close()
+
+
+def test_attach_rejects_other_problems():
+    X = np.ones((8, 64), np.float32)
+    X[::2] *= -1
+    y = np.array([1, -1] * 4, np.int8)
+    s = P.Solver(dev(X), dev(y), C_=1.0)
+    with pytest.raises(P.SVMError) as e:
+        s.set_warmstart_model(dev(_params(0)))         # q = 64: not the network's input width
+    assert e.value.status == P.ERR_UNSUPPORTED
+    s.set_warmstart_model(None)                         # detaching is always allowed
+    s.close()

@@ -420,3 +420,17 @@ def test_kkt_zero_at_bruteforce_optimum_positive_elsewhere():
     a = r["alpha"].copy()
     a[:2] = a[:2][::-1] + 0.01
     assert oracle.kkt(X, y, 0.5, a) > 1e-4
+
+
+@pytest.mark.parametrize("ex", ["1", "2"])
+def test_kkt_hand_worked_examples(ex):
+    """R_KKT of eq. (4.1) on two hand-worked cases (tests/golden/kkt_worked.txt):
+    the numerator's projection multiplier and the (1 + |alpha|) denominator are
+    both pinned (|alpha| or 1 + |alpha|^2 in its place gives a different value)."""
+    g = _read_golden("kkt_worked.txt")
+    y = g["y" + ex].astype(np.int8)
+    n = y.size
+    X = g["X" + ex].reshape(n, -1)
+    r, lam, w = oracle.kkt(X, y, g["C" + ex][0], g["alpha" + ex], with_extras=True)
+    assert r == pytest.approx(g["R" + ex][0], rel=1e-14)
+    assert lam == pytest.approx(g["lambda" + ex][0], abs=1e-14)

@@ -26,7 +26,9 @@ def _lib():
     P.load()
 
 
-@pytest.mark.parametrize("n,q", [(5003, 128), (20011, 50), (3001, 1000)])
+# (5, 3): most of the 160 blocks get an empty row range; (37, 1024): the widest
+# q with rows fewer than blocks; (161, 33): one row per block, ragged columns
+@pytest.mark.parametrize("n,q", [(5003, 128), (20011, 50), (3001, 1000), (5, 3), (37, 1024), (161, 33)])
 def test_noalloc_matches_handle_product_twice(n, q):
     X, y = datagen.small(n, q, seed=7 + q, dtype=np.float32)
     Xd = torch.from_numpy(X).cuda()
@@ -55,3 +57,36 @@ def test_noalloc_rejects_sizes_beyond_its_limit():
     c = torch.zeros(4, dtype=torch.float64, device="cuda")
     out = torch.zeros(1025, dtype=torch.float64, device="cuda")
     assert P.rmatvec_noalloc(X, y, c, out) == P.ERR_UNSUPPORTED
+
+
+def test_noalloc_leaves_device_memory_unchanged():
+    """After the first call (the device's one-time set-up), further calls
+    change the device's free memory by nothing: no allocation happens."""
+    n, q = 20011, 128
+    X, y = datagen.small(n, q, seed=3, dtype=np.float32)
+    Xd = torch.from_numpy(X).cuda()
+    yd = torch.from_numpy(y).cuda()
+    cd = torch.from_numpy(np.random.default_rng(5).uniform(0.0, 1.0, n)).cuda()
+    out = torch.empty(q, dtype=torch.float64, device="cuda")
+    assert P.rmatvec_noalloc(Xd, yd, cd, out) == P.OK
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(5):
+        assert P.rmatvec_noalloc(Xd, yd, cd, out) == P.OK
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
+
+
+def test_noalloc_rejects_a_stream_of_another_device():
+    """The stream must belong to the current device (checked when a second GPU
+    is visible; with one GPU there is no other device to test against)."""
+    if torch.cuda.device_count() < 2:
+        pytest.skip("one visible GPU")
+    X = torch.zeros((4, 8), dtype=torch.float32, device="cuda:0")
+    y = torch.ones(4, dtype=torch.int8, device="cuda:0")
+    c = torch.zeros(4, dtype=torch.float64, device="cuda:0")
+    out = torch.zeros(8, dtype=torch.float64, device="cuda:0")
+    s1 = torch.cuda.Stream(device=1)
+    with torch.cuda.device(0):
+        assert P.rmatvec_noalloc(X, y, c, out, stream=s1.cuda_stream) == P.ERR_INVALID_ARG
