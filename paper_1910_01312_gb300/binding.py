@@ -76,7 +76,8 @@ SYMBOLS = ["svm_default_params", "svm_ssnalm_create", "svm_ssnalm_solve", "svm_s
            "svm_mlp_features", "svm_mlp_labels", "svm_mlp_gather", "svm_mlp_forward", "svm_mlp_loss_grad", "svm_mlp_adam_step",
            "svm_mlp_train_step", "svm_mlp_start_point", "svm_ssnalm_solve_mlp", "svm_ssnalm_set_warmstart_model",
            "svm_gqp_create", "svm_svr_create", "svm_gqp_solve", "svm_gqp_destroy", "svm_gqp_last_error",
-           "svm_gqp_op_project", "svm_gqp_op_newton", "svm_gqp_op_matvec", "svm_gqp_op_rmatvec"]
+           "svm_gqp_op_project", "svm_gqp_op_newton", "svm_gqp_op_matvec", "svm_gqp_op_rmatvec",
+           "svm_nystrom_kmeans", "svm_nystrom_features"]
 MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_NPARAM = 132, 256, 3, 100611
 
 _lock = threading.Lock()
@@ -148,6 +149,8 @@ def load(build_if_missing: bool = False):
         L.svm_gqp_op_newton.argtypes = [vp, vp, i64, C.c_double, vp, vp]
         L.svm_gqp_op_matvec.argtypes = [vp, vp, vp]
         L.svm_gqp_op_rmatvec.argtypes = [vp, vp, vp]
+        L.svm_nystrom_kmeans.argtypes = [vp, i64, i64, vp, i64, C.c_int32, vp, vp, vp]
+        L.svm_nystrom_features.argtypes = [vp, i64, i64, vp, i64, C.c_double, C.c_double, vp, C.c_int32, vp]
         for f in ("svm_op_matvec", "svm_op_rmatvec", "svm_op_project", "svm_op_newton", "svm_op_kkt", "svm_op_gram",
                   "svm_ssnalm_solve_batch", "svm_rff_features",
                   "svm_ssnalm_set_timing", "svm_ssnalm_get_stats", "svm_rmatvec_noalloc", "svm_mlp_create",
@@ -155,7 +158,8 @@ def load(build_if_missing: bool = False):
                   "svm_mlp_loss_grad",
                   "svm_mlp_adam_step", "svm_mlp_train_step", "svm_mlp_start_point", "svm_ssnalm_solve_mlp",
                   "svm_ssnalm_set_warmstart_model", "svm_gqp_create", "svm_svr_create", "svm_gqp_solve",
-                  "svm_gqp_op_project", "svm_gqp_op_newton", "svm_gqp_op_matvec", "svm_gqp_op_rmatvec"):
+                  "svm_gqp_op_project", "svm_gqp_op_newton", "svm_gqp_op_matvec", "svm_gqp_op_rmatvec",
+                  "svm_nystrom_kmeans", "svm_nystrom_features"):
             getattr(L, f).restype = C.c_int
         _lib = L
         return L
@@ -217,6 +221,32 @@ def rff_features(X, Omega, Z, stream=None) -> int:
     n, q = X.shape
     N = Omega.shape[1]
     return load().svm_rff_features(_ptr(X), int(n), int(q), _ptr(Omega), int(N), _ptr(Z), stream)
+
+
+def nystrom_kmeans(X, centres, iters, labels=None, stream=None):
+    """Lloyd's k-means on the rows of X (device FP32, n x q) from the initial
+    centres (device FP64, r x q, updated in place); labels (device int32, n,
+    optional) receives the last assignment.  Returns the objective of each
+    iteration (numpy array); raises SVMError on failure."""
+    n, q = X.shape
+    r = centres.shape[0]
+    obj = np.zeros(int(iters), np.float64)
+    st = load().svm_nystrom_kmeans(_ptr(X), int(n), int(q), _ptr(centres), int(r), int(iters), _ptr(labels),
+                                   obj.ctypes.data_as(C.c_void_p), stream)
+    if st != OK:
+        raise SVMError(st, "svm_nystrom_kmeans")
+    return obj
+
+
+def nystrom_features(X, centres, alpha, Z, shift=1e-3, stream=None):
+    """Z = K_nr L^{-T}, L L' = K_rr + shift I (Z device, n x r, FP32 or FP64)."""
+    n, q = X.shape
+    r = centres.shape[0]
+    zd = F32 if str(Z.dtype).endswith("float32") else F64
+    st = load().svm_nystrom_features(_ptr(X), int(n), int(q), _ptr(centres), int(r), float(alpha), float(shift),
+                                     _ptr(Z), zd, stream)
+    if st != OK:
+        raise SVMError(st, "svm_nystrom_features")
 
 
 def _ptr(t):

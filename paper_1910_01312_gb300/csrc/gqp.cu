@@ -287,6 +287,9 @@ extern "C" svm_status svm_svr_create(svm_gqp_t **out, const void *X, int64_t m, 
     if ((uintptr_t)W.X % 16 != 0) return fail(SVM_ERR_INVALID_ARG, "X must be 16-byte aligned");
     double *c = h->vec_own, *a = c + n, *lo = c + 2 * n, *hi = c + 3 * n;
     W.c = c; W.a = a; W.lo = lo; W.hi = hi;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&W.nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return fail(SVM_ERR_CUDA, "device query failed");
     if (gqp::svr_vectors(W, ydev, eps, params->C, c, a, lo, hi) != cudaSuccess) return fail(SVM_ERR_CUDA, "SVR set-up failed");
     const svm_status st = create_common(h, params);
     if (st != SVM_OK) return fail(st, h->err == "c, a, l or u has non-finite entries" ? "y has non-finite entries" : h->err);

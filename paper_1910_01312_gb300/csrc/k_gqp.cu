@@ -32,6 +32,10 @@ __device__ __forceinline__ double ldx(const void *X, long long k)
 
 __device__ __forceinline__ double lane0(double v) { return __shfl_sync(0xffffffffu, v, 0); }
 
+// w - lambda a rounded as written (a product, then a difference; no FMA), so
+// that the projection is clip(w - lambda a, l, u) of the definition exactly.
+__device__ __forceinline__ double shifted(double w, double lam, double a) { return __dsub_rn(w, __dmul_rn(lam, a)); }
+
 // ---------------------------------------------------------------- z = B v
 
 // Eight lanes per stored row (a warp takes four rows); lanes stride the
@@ -182,7 +186,7 @@ struct Comp {
 __device__ __forceinline__ Comp comp_at(double w, double a, double ainv, double lo, double hi, double lam)
 {
     Comp o;
-    const double r = fma(-lam, a, w);
+    const double r = shifted(w, lam, a);
     o.pi = r >= hi ? hi : (r <= lo ? lo : r);   // ties go to the bound (Sec. 3.2.1)
     o.fa = a * o.pi;
     const bool in_r = a > 0.0 ? (lo < r && r <= hi) : (lo <= r && r < hi);   // r moves by -eps a
@@ -326,7 +330,7 @@ __global__ void __launch_bounds__(kPT) proj_kernel(PArgs A)
     long long pc = 0, nfx = 0;
     for (long long i = i0 + tid; i < i1; i += kPT) {
         const double w = A.w_out[i], a = A.a[i], lo = A.lo[i], hi = A.hi[i];
-        const double r = fma(-lh, a, w);
+        const double r = shifted(w, lh, a);
         const double pi = r >= hi ? hi : (r <= lo ? lo : r);
         A.pi_out[i] = pi;
         const double xi = A.x[i];
@@ -377,7 +381,7 @@ __global__ void __launch_bounds__(kPT) proj_kernel(PArgs A)
             const long long i = t0 + tid;
             bool fr = false;
             if (i < i1) {
-                const double r = fma(-lh, A.a[i], A.w_out[i]);
+                const double r = shifted(A.w_out[i], lh, A.a[i]);
                 fr = r > A.lo[i] && r < A.hi[i];
             }
             const unsigned bal = __ballot_sync(0xffffffffu, fr);

@@ -7,7 +7,11 @@ The GPU path is FP64 throughout, so steps agree with the reference to a few
 ulps of the summed magnitudes (1e-12 of the absolute-sum scale), index sets
 exactly except for components within roundoff of a bound, and whole solves on
 what is unique: the objective (relative 1e-6), both sides' R_KKT <= 1e-6,
-feasibility and, for the SVR, the zero primal-dual gap.
+feasibility and, for the SVR, the zero primal-dual gap.  The references are
+solved to R_KKT <= 1e-9 (general QPs) and 1e-8 (SVR duals): tighter targets
+are below the FP64 reference's own roundoff floor on some of these problems
+(it then spends its 200 outer iterations raising sigma), and these already
+fix the objective far inside the 1e-6 being checked.
 """
 import numpy as np
 import pytest
@@ -200,7 +204,7 @@ def _check_solve(r, x, w, B, c, a, d, lo, hi, ref):
 def test_solve_general_qp(n, q, seed, dtype):
     rng = np.random.default_rng(seed)
     B, c, a, d, lo, hi = _general_problem(rng, n, q, dtype)
-    ref = gqp.solve(B.astype(np.float64), c, a, d, lo, hi, tol=1e-10)
+    ref = gqp.solve(B.astype(np.float64), c, a, d, lo, hi, tol=1e-9)
     assert ref["status"] == "ok"
     h, keep = _handle(B, c, a, d, lo, hi, tol=1e-6)
     x = torch.empty(n, dtype=torch.float64, device="cuda")
@@ -213,7 +217,7 @@ def test_solve_general_qp(n, q, seed, dtype):
 def test_solve_host_memory():
     rng = np.random.default_rng(9)
     B, c, a, d, lo, hi = _general_problem(rng, 500, 8)
-    ref = gqp.solve(B, c, a, d, lo, hi, tol=1e-10)
+    ref = gqp.solve(B, c, a, d, lo, hi, tol=1e-9)
     h = P.GQP(B, c, a, lo, hi, d=d, tol=1e-6)
     x, w = np.zeros(500), np.zeros(8)
     r = h.solve(x, w)
@@ -288,7 +292,7 @@ def test_svr_matches_reference_with_zero_gap(m, q, eps, C, dtype):
     wt = rng.normal(size=q)
     y = X.astype(np.float64) @ wt + 0.3 * rng.normal(size=m)
     Xf = X.astype(np.float64)
-    ref = gqp.solve(*gqp.svr_problem(Xf, y, eps, C), tol=1e-10)
+    ref = gqp.solve(*gqp.svr_problem(Xf, y, eps, C), tol=1e-8)
     assert ref["status"] == "ok"
     keep = (dev(X), dev(y))
     h = P.GQP.svr(keep[0], keep[1], eps, C, tol=1e-6)
