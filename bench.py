@@ -333,18 +333,31 @@ def main():
     value = t_max / (args.steps * world)
     r = results[-1]
 
-    # roofline of the dominant kernel: the forward product z = A v
+    # roofline of the dominant kernel: the forward product matvec_mx_kernel, in its
+    # one-vector form (z = A dv, 4 of 5 launches) and its two-vector form (A alpha
+    # and A v in one pass over X at the end of each outer iteration)
     peak, peak_kind = _peaks()
-    alg_bytes = n * q * X.itemsize + n * 1 + n * 8 + q * 8       # X + y read, z written, v read
-    mv_ms = st["matvec_ms"] / max(st["matvec_calls"], 1)
+    alg1 = n * q * X.itemsize + n * 1 + n * 8 + q * 8        # X + y read, z (double-float) written, v read
+    alg2 = n * q * X.itemsize + n * 1 + 2 * n * 8 + 2 * q * 8
+    c1, c2 = st["matvec_calls"], st["matvec2_calls"]
+    ms1, ms2 = st["matvec_ms"], st["matvec2_ms"]
+    mv_ms = (ms1 + ms2) / max(c1 + c2, 1)
+    alg_bytes = (c1 * alg1 + c2 * alg2) / max(c1 + c2, 1)
     achieved = alg_bytes / (mv_ms * 1e-3) / 1e9
     traffic = _traffic(os.path.join(ROOT, "paper_1910_01312_gb300", "csrc", "k_matvec.cu"), "matvec_gauss1m")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic, "kernel": "matvec_mx_kernel (z = A v, Dot2 sums, double-float z)",
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": "matvec_mx_kernel (z = A v, Dot2 sums, double-float z; one- and two-vector passes)",
                 "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": mv_ms,
-                "launches_per_step": st["matvec_calls"] / args.steps, "peak_source": f"{peak_kind} hbm_gbs"}
-    breakdown = {k: st[k] / args.steps for k in ("matvec_ms", "rmatvec_ms", "proj_ms", "newton_ms")}
-    breakdown.update({k: st[k] / args.steps for k in ("matvec_calls", "rmatvec_calls", "proj_calls",
+                "launches_per_step": (c1 + c2) / args.steps, "peak_source": f"{peak_kind} hbm_gbs",
+                "by_form": {"one_vector": {"launches_per_step": c1 / args.steps, "avg_launch_ms": ms1 / max(c1, 1),
+                                           "alg_bytes_per_launch": alg1,
+                                           "achieved": alg1 / (ms1 / max(c1, 1) * 1e-3) / 1e9 if c1 else None},
+                            "two_vector": {"launches_per_step": c2 / args.steps, "avg_launch_ms": ms2 / max(c2, 1),
+                                           "alg_bytes_per_launch": alg2,
+                                           "achieved": alg2 / (ms2 / max(c2, 1) * 1e-3) / 1e9 if c2 else None}}}
+    breakdown = {k: st[k] / args.steps for k in ("matvec_ms", "matvec2_ms", "rmatvec_ms", "proj_ms", "newton_ms")}
+    breakdown.update({k: st[k] / args.steps for k in ("matvec_calls", "matvec2_calls", "rmatvec_calls", "proj_calls",
                                                        "newton_calls", "host_syncs")})
     gpu_launches = int(st["launches"])
     s.close()

@@ -252,7 +252,7 @@ svm_status svm_op_kkt(svm_ssnalm_t *h, const double *alpha, double *kkt, double 
  * ------------------------------------------------------------------- */
 typedef struct {
     int64_t launches;          /* kernels launched by this handle since reset  */
-    int64_t matvec_calls;      /* z = A v products (one kernel each)           */
+    int64_t matvec_calls;      /* one-vector products z = A v (one kernel each) */
     double matvec_ms;          /* their summed CUDA-event time (timing on)     */
     int64_t rmatvec_calls;     /* A' c products (two kernels each)             */
     double rmatvec_ms;
@@ -261,6 +261,8 @@ typedef struct {
     int64_t newton_calls;      /* Newton-system solves                          */
     double newton_ms;
     int64_t host_syncs;        /* stream synchronisations for scalar read-back */
+    int64_t matvec2_calls;     /* two-vector passes [A v0, A v1] over X          */
+    double matvec2_ms;
 } svm_stats;
 
 /* Enable (1) or disable (0) CUDA-event timing of the step kinds above.  When

@@ -66,7 +66,7 @@ class Stats(C.Structure):
     _fields_ = [("launches", C.c_int64), ("matvec_calls", C.c_int64), ("matvec_ms", C.c_double),
                 ("rmatvec_calls", C.c_int64), ("rmatvec_ms", C.c_double), ("proj_calls", C.c_int64),
                 ("proj_ms", C.c_double), ("newton_calls", C.c_int64), ("newton_ms", C.c_double),
-                ("host_syncs", C.c_int64)]
+                ("host_syncs", C.c_int64), ("matvec2_calls", C.c_int64), ("matvec2_ms", C.c_double)]
 
 
 SYMBOLS = ["svm_default_params", "svm_ssnalm_create", "svm_ssnalm_solve", "svm_ssnalm_destroy",

@@ -44,6 +44,7 @@ namespace {
 constexpr int kMaxPassDF = 256;
 constexpr float kMargin = 9.5367431640625e-07f;   // 2^-20
 constexpr int kStrideF = 16;                      // floats per block partial
+constexpr int kStageG = 512;                      // grids up to this size stage partials in shared memory
 
 struct PDArgs {
     const float2 *a;
@@ -221,6 +222,7 @@ __global__ void __launch_bounds__(kTPB, EPT >= 16 ? 1 : 2) projdf_kernel(PDArgs 
 
     __shared__ float4 sh_wf[kWarps];
     __shared__ int4 sh_wi[kWarps];
+    __shared__ float4 sh_stage[3 * kStageG];   // staged block partials (2 per pass partial, 3 per final one)
     __shared__ float2 sh_dl;
     __shared__ int sh_done;
     if (tid == 0) sh_dl = make_float2(0.f, 0.f);
@@ -267,14 +269,23 @@ __global__ void __launch_bounds__(kTPB, EPT >= 16 ? 1 : 2) projdf_kernel(PDArgs 
             }
         }
         if (!grid_barrier(A.bar, A.err)) { alive = false; break; }
+        const float *slot = A.part + (size_t)(pass & 1) * G * kStrideF;
+        const bool staged = G <= kStageG;
+        if (staged) {
+            // every thread of the block fetches a share of the G partials at once
+            // (one L2 round trip instead of G/32 dependent ones for warp 0)
+            for (int e = tid; e < 2 * G; e += kTPB)
+                sh_stage[e] = __ldcg(reinterpret_cast<const float4 *>(slot + (size_t)(e >> 1) * kStrideF) + (e & 1));
+            __syncthreads();
+        }
         if (warp == 0) {
             // every block reduces all partials in the same order
             Acc t;
             acc_zero(t);
-            const float *slot = A.part + (size_t)(pass & 1) * G * kStrideF;
             for (int bb = lane; bb < G; bb += 32) {
-                const float4 f = __ldcg(reinterpret_cast<const float4 *>(slot + (size_t)bb * kStrideF));
-                const int4 c = __ldcg(reinterpret_cast<const int4 *>(slot + (size_t)bb * kStrideF + 4));
+                const float4 f = staged ? sh_stage[2 * bb] : __ldcg(reinterpret_cast<const float4 *>(slot + (size_t)bb * kStrideF));
+                const float4 cf = staged ? sh_stage[2 * bb + 1] : __ldcg(reinterpret_cast<const float4 *>(slot + (size_t)bb * kStrideF + 4));
+                const int4 c = make_int4(__float_as_int(cf.x), __float_as_int(cf.y), __float_as_int(cf.z), __float_as_int(cf.w));
                 t.D = dfx_add(t.D, make_float2(f.x, f.y));
                 t.bhi = fminf(t.bhi, f.z);
                 t.blo = fmaxf(t.blo, f.w);
@@ -507,6 +518,13 @@ __global__ void __launch_bounds__(kTPB, EPT >= 16 ? 1 : 2) projdf_kernel(PDArgs 
         if (lane == 0) { sh_tot2[k][0] = tj; sh_tot2[k][1] = td; sh_off[k][0] = pj; sh_off[k][1] = pd; }
     }
     __syncthreads();
+    const bool staged_sums = blk == 0 && A.sums && G <= kStageG;
+    if (staged_sums) {
+        // block 0 fetches the final-phase partials with all its threads at once
+        for (int e = tid; e < 3 * G; e += kTPB)
+            sh_stage[e] = __ldcg(reinterpret_cast<const float4 *>(A.part + ((size_t)2 * G + e / 3) * kStrideF) + e % 3);
+        __syncthreads();
+    }
     if (blk == 0 && warp == 0) {
         // block 0 publishes lambda-hat and the sums (fixed-order reduction)
         Sums t;
@@ -516,13 +534,13 @@ __global__ void __launch_bounds__(kTPB, EPT >= 16 ? 1 : 2) projdf_kernel(PDArgs 
         if (A.sums) {
             for (int bb = lane; bb < G; bb += 32) {
                 const float *p = A.part + ((size_t)2 * G + bb) * kStrideF;
-                const float4 f0 = __ldcg(reinterpret_cast<const float4 *>(p));
-                const float4 f1 = __ldcg(reinterpret_cast<const float4 *>(p + 4));
+                const float4 f0 = staged_sums ? sh_stage[3 * bb] : __ldcg(reinterpret_cast<const float4 *>(p));
+                const float4 f1 = staged_sums ? sh_stage[3 * bb + 1] : __ldcg(reinterpret_cast<const float4 *>(p + 4));
                 t.s[0] = dfx_add(t.s[0], make_float2(f0.x, f0.y));
                 t.s[1] = dfx_add(t.s[1], make_float2(f0.z, f0.w));
                 t.s[2] = dfx_add(t.s[2], make_float2(f1.x, f1.y));
                 t.s[3] = dfx_add(t.s[3], make_float2(f1.z, f1.w));
-                t.nupa += __ldcg(reinterpret_cast<const int *>(p + 8));
+                t.nupa += staged_sums ? __float_as_int(sh_stage[3 * bb + 2].x) : __ldcg(reinterpret_cast<const int *>(p + 8));
             }
             sums_warp_reduce(t);
         }

@@ -49,8 +49,8 @@ struct svm_ssnalm {
     size_t evused = 0;
     struct Rec { int kind, e0, e1; };
     std::vector<Rec> recs;
-    long long kcalls[4] = {0, 0, 0, 0};
-    double kms[4] = {0, 0, 0, 0};
+    long long kcalls[5] = {0, 0, 0, 0, 0};
+    double kms[5] = {0, 0, 0, 0, 0};
     long long syncs = 0;
     long long launch_base = 0;
     bool trace = false;   // SVM_SSNALM_TRACE=1: one stderr line per Newton step
@@ -71,7 +71,7 @@ struct svm_ssnalm {
     svm_mlp_t *wsm = nullptr;   // warm-start network of svm_ssnalm_set_warmstart_model (owned)
 };
 
-enum { TK_MATVEC = 0, TK_RMATVEC = 1, TK_PROJ = 2, TK_NEWTON = 3 };
+enum { TK_MATVEC = 0, TK_RMATVEC = 1, TK_PROJ = 2, TK_NEWTON = 3, TK_MATVEC2 = 4 };
 
 static int ev_take(svm_ssnalm *h)
 {
@@ -578,7 +578,8 @@ static svm_status run_matvec_single(Run &r)
     Work &W = h->W;
     const MvReq &m = r.mv;
     if (!m.nv) return SVM_OK;
-    CK(timed(h, TK_MATVEC, [&] {
+    // one-vector and two-vector passes are timed apart (the second does twice the arithmetic per byte)
+    CK(timed(h, m.nv > 1 ? TK_MATVEC2 : TK_MATVEC, [&] {
         return W.df ? launch_matvec_df(W, m.v[0], m.zf[0], m.nv > 1 ? m.v[1] : nullptr, m.nv > 1 ? m.zf[1] : nullptr)
                     : launch_matvec(W, m.v[0], m.z[0], m.nv > 1 ? m.v[1] : nullptr, m.nv > 1 ? m.z[1] : nullptr);
     }));
@@ -1450,9 +1451,11 @@ extern "C" svm_status svm_ssnalm_get_stats(svm_ssnalm_t *h, svm_stats *out, int 
     out->newton_calls = h->kcalls[TK_NEWTON];
     out->newton_ms = h->kms[TK_NEWTON];
     out->host_syncs = h->syncs;
+    out->matvec2_calls = h->kcalls[TK_MATVEC2];
+    out->matvec2_ms = h->kms[TK_MATVEC2];
     if (reset) {
         h->launch_base = h->W.nlaunch;
-        for (int k = 0; k < 4; ++k) { h->kcalls[k] = 0; h->kms[k] = 0.0; }
+        for (int k = 0; k < 5; ++k) { h->kcalls[k] = 0; h->kms[k] = 0.0; }
         h->syncs = 0;
     }
     return SVM_OK;

@@ -9,7 +9,12 @@ Ops: ``solve`` (one cold solve after one warm-up, both forms of the stated
 precision), ``matvec`` (z = A v), ``rmatvec`` (A'c over all rows), ``project``
 (the projection at a random u), ``newton`` (the reduced Newton system on a
 random free set of size --p), ``rff`` (random Fourier features of X with
---nfreq frequencies).  The data are the two-Gaussian workload of
+--nfreq frequencies), ``gqp_csvc`` (the same C-SVC posed as the unified QP of
+eq. (1.5): B = Diag(y) X, c = -e, a = y, l = 0, u = C, through
+svm_gqp_solve), ``gqp`` (a general unified QP on the same X: signed non-unit
+a, per-component boxes, d != 0), ``svr`` (the linear SVR dual of eq. (1.4) on
+y = X w* + noise, 2n variables), ``nystrom`` (--iters k-means iterations and
+the features for --nfreq landmarks).  The data are the two-Gaussian workload of
 ``datagen.gauss1m`` at the requested n and q, or with ``--layout csr`` the
 text-like sparse workload of ``datagen.sparse_text`` (--nnz-row entries per
 row).  Prints one JSON line with the mean time per call from CUDA events on
@@ -25,7 +30,9 @@ import numpy as np
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--op", default="solve", choices=["solve", "matvec", "rmatvec", "project", "newton", "rff"])
+    ap.add_argument("--op", default="solve", choices=["solve", "matvec", "rmatvec", "project", "newton", "rff",
+                                                      "gqp_csvc", "gqp", "svr", "nystrom"])
+    ap.add_argument("--iters", type=int, default=10)
     ap.add_argument("--nfreq", type=int, default=512)
     ap.add_argument("--n", type=int, default=400_000)
     ap.add_argument("--q", type=int, default=128)
@@ -64,7 +71,52 @@ def main(argv=None):
     rng = np.random.default_rng(0)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
-    if args.op == "rff":
+    extra = {}
+    if args.op in ("gqp_csvc", "gqp", "svr"):
+        Xf = X.astype(np.float64)
+        yf = y.astype(np.float64)
+        if args.op == "gqp_csvc":
+            keep = [dev((X * y[:, None]).astype(np.float32)), dev(-np.ones(n)), dev(yf), dev(np.zeros(n)),
+                    dev(np.full(n, C))]
+            g = B.GQP(*keep, d=0.0, tol=1e-6, stream=stream.cuda_stream)
+            nv = n
+        elif args.op == "gqp":
+            a_ = rng.normal(size=n) * rng.uniform(0.2, 3.0, size=n)
+            lo = rng.normal(size=n) * 0.1
+            hi = lo + rng.uniform(0.05, 0.2, size=n)
+            c_ = -np.ones(n) + 0.1 * rng.normal(size=n)
+            keep = [Xd, dev(c_), dev(a_), dev(lo), dev(hi)]
+            g = B.GQP(*keep, d=float(a_ @ (0.5 * (lo + hi))), tol=1e-6, stream=stream.cuda_stream)
+            nv = n
+        else:
+            wt = rng.normal(size=q) / np.sqrt(q)
+            yt = Xf @ wt + 0.3 * rng.normal(size=n)
+            keep = [Xd, dev(yt)]
+            g = B.GQP.svr(Xd, keep[1], 0.1, 1.0, tol=1e-6, stream=stream.cuda_stream)
+            nv = 2 * n
+        xo = torch.empty(nv, dtype=torch.float64, device="cuda")
+        wo = torch.empty(q, dtype=torch.float64, device="cuda")
+        call = lambda: g.solve(xo, wo)
+    elif args.op == "nystrom":
+        r = args.nfreq
+        C0 = X[rng.choice(n, size=r, replace=False)].astype(np.float64)
+        Cd = dev(C0)
+        Zn = torch.empty((n, r), dtype=torch.float32, device="cuda")
+
+        def call():
+            Cd.copy_(dev(C0))
+            P0 = torch.cuda.Event(enable_timing=True)
+            P1 = torch.cuda.Event(enable_timing=True)
+            P2 = torch.cuda.Event(enable_timing=True)
+            P0.record(stream)
+            B.nystrom_kmeans(Xd, Cd, args.iters, stream=stream.cuda_stream)
+            P1.record(stream)
+            B.nystrom_features(Xd, Cd, float(q), Zn, stream=stream.cuda_stream)
+            P2.record(stream)
+            torch.cuda.synchronize()
+            extra["kmeans_ms"] = P0.elapsed_time(P1)
+            extra["features_ms"] = P1.elapsed_time(P2)
+    elif args.op == "rff":
         Om = dev(datagen.rff_omega(0, q, args.nfreq, float(q)))
         Zr = torch.empty((n, 2 * args.nfreq), dtype=torch.float32, device="cuda")
         call = lambda: B.rff_features(Xd, Om, Zr, stream.cuda_stream)
@@ -109,8 +161,12 @@ def main(argv=None):
     if args.op in ("matvec", "rmatvec"):
         b = bytes_mv if args.op == "matvec" else bytes_rmv
         line.update({"bytes_per_call": b, "GB_per_s": b / (ms * 1e-3) / 1e9})
-    if args.op == "solve":
-        line.update({"outer": out["outer_iters"], "inner": out["inner_iters_total"], "kkt": out["kkt"]})
+    if args.op in ("solve", "gqp_csvc", "gqp", "svr"):
+        line.update({"outer": out["outer_iters"], "inner": out["inner_iters_total"], "kkt": out["kkt"],
+                     "objective": out["objective"]})
+    if args.op == "nystrom":
+        line.update({"landmarks": args.nfreq, "iters": args.iters, **extra,
+                     "kmeans_GFLOP_per_s_fp64": 3.0 * n * args.nfreq * q * args.iters / (extra["kmeans_ms"] * 1e-3) / 1e9})
     print(json.dumps(line), flush=True)
     s.close()
     return 0
