@@ -79,6 +79,32 @@ struct ProjBuf {
 
 struct CsrCg;
 
+// Arguments of one double-float projection launch (k_projdf.cu); the batched
+// form takes a device table of them, one per problem.
+struct PDArgs {
+    const float2 *a;
+    int a_signed;
+    const float2 *b;
+    float2 c1, c2;
+    const int8_t *y;
+    long long n;
+    float2 Cd;               // C as a double-float pair
+    int sums;
+    const float2 *lam0;
+    float2 *u_out;
+    float2 *wpi_out;
+    const float2 *alpha_w;
+    const float2 *base_w;
+    float2 *dw_out;
+    float *dwa_out;
+    int32_t *J, *D;
+    float *part;             // cooperative form: [3][G][16] block partials
+    int *cnt;                // cooperative form: [EPT][G][2] list counts
+    unsigned *bar;
+    int *err;
+    ProjOut *out;
+};
+
 struct Work {
     // problem
     int64_t n = 0, q = 0;
@@ -165,6 +191,9 @@ struct Work {
     int *h_err = nullptr;
     // cooperative-launch geometry of the projection kernel
     int proj_grid = 0, proj_ept = 0;
+    // the double-float projection's cluster form (n small enough for one cluster
+    // per problem): cluster size (0: the cooperative form) and components per thread
+    int proj_cl = 0, proj_cept = 0;
     // rmatvec geometry
     int rm_grid = 0;
     // kernels launched through this workspace (all kinds)
@@ -175,6 +204,13 @@ struct Work {
 cudaError_t proj_setup(Work &W);
 cudaError_t launch_project(Work &W, const ProjIn &in, ProjOut *out);
 cudaError_t launch_project_df(Work &W, const ProjDF &in, ProjOut *out);
+// the arguments of one double-float projection (for a batched launch)
+cudaError_t make_pdargs(const Work &W, const ProjDF &in, ProjOut *out, PDArgs *A);
+// nprob projections in one launch of the cluster form (table in device memory;
+// every problem must have W's n and cluster geometry)
+cudaError_t launch_project_df_table(Work &W, const PDArgs *table_dev, int nprob);
+// choose the cluster form of the double-float projection when n allows it
+cudaError_t projdf_cluster_setup(Work &W);
 void *projdf_kernel_for(int ept);   // for the occupancy query of proj_setup
 
 // z0 = A v0 (and z1 = A v1 when v1 != nullptr, in the same pass over X)

@@ -45,30 +45,39 @@ constexpr int kMaxPassDF = 256;
 constexpr float kMargin = 9.5367431640625e-07f;   // 2^-20
 constexpr int kStrideF = 16;                      // floats per block partial
 constexpr int kStageG = 512;                      // grids up to this size stage partials in shared memory
+constexpr int kTPBC = 1024;                       // threads per CTA of the cluster form
 
-struct PDArgs {
-    const float2 *a;
-    int a_signed;
-    const float2 *b;
-    float2 c1, c2;
-    const int8_t *y;
-    long long n;
-    float2 Cd;               // C as a double-float pair
-    int sums;
-    const float2 *lam0;
-    float2 *u_out;
-    float2 *wpi_out;
-    const float2 *alpha_w;
-    const float2 *base_w;
-    float2 *dw_out;
-    float *dwa_out;
-    int32_t *J, *D;
-    float *part;             // [3][G][kStrideF]
-    int *cnt;                // [EPT][G][2]
-    unsigned *bar;
-    int *err;
-    ProjOut *out;
-};
+// ---- thread-block clusters: the cluster form of the kernel (one problem per
+// cluster) exchanges its partials through distributed shared memory and
+// synchronises with the hardware cluster barrier instead of a grid barrier ----
+__device__ __forceinline__ unsigned cl_rank() { unsigned r; asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r)); return r; }
+__device__ __forceinline__ unsigned cl_size() { unsigned r; asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r)); return r; }
+__device__ __forceinline__ unsigned cl_id() { unsigned r; asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r)); return r; }
+__device__ __forceinline__ void cl_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// address of `p` (this CTA's shared memory) in CTA `rank` of the cluster
+__device__ __forceinline__ unsigned cl_map(const void *p, unsigned rank)
+{
+    unsigned a;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(a) : "r"(smem_u32(p)), "r"(rank));
+    return a;
+}
+__device__ __forceinline__ float4 cl_ld4(unsigned a)
+{
+    float4 v;
+    asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ int2 cl_ld2i(unsigned a)
+{
+    int2 v;
+    asm volatile("ld.shared::cluster.v2.s32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(a) : "memory");
+    return v;
+}
+
 
 __device__ __forceinline__ float2 u_at(const PDArgs &A, long long i, bool pos)
 {
@@ -186,12 +195,18 @@ __device__ __forceinline__ void sums_warp_reduce(Sums &v)
         for (int k = 0; k < 4; ++k) v.s[k] = dfx_add(v.s[k], shfl_xor_f2(v.s[k], o));
 }
 
-template <int EPT>
-__global__ void __launch_bounds__(kTPB, EPT >= 16 ? 1 : 2) projdf_kernel(PDArgs A)
+// The body of both forms.  CLU = false: G blocks of one cooperative launch
+// (grid barrier, partials in global memory); CLU = true: the G CTAs of one
+// cluster (cluster barrier, partials in distributed shared memory; every CTA
+// runs the same sequence of cluster barriers, and a last one keeps each CTA's
+// shared memory alive until the others have read it).
+template <int EPT, bool CLU, int TPB>
+__device__ __forceinline__ void projdf_body(const PDArgs &A, const int G, const int blk)
 {
-    const int G = gridDim.x, blk = blockIdx.x, tid = threadIdx.x;
+    constexpr int WARPS = TPB / 32;
+    const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
-    const long long NT = (long long)G * kTPB;
+    const long long NT = (long long)G * TPB;
     const float2 Cd = A.Cd;
 
     __shared__ float2 sh_l0;
@@ -208,7 +223,7 @@ __global__ void __launch_bounds__(kTPB, EPT >= 16 ? 1 : 2) projdf_kernel(PDArgs 
     unsigned posm = 0u, valm = 0u;
 #pragma unroll
     for (int k = 0; k < EPT; ++k) {
-        const long long i = k * NT + (long long)blk * kTPB + tid;
+        const long long i = k * NT + (long long)blk * TPB + tid;
         d[k] = make_float2(0.f, 0.f);
         if (i < A.n) {
             const bool pos = A.y[i] > 0;
@@ -220,9 +235,12 @@ __global__ void __launch_bounds__(kTPB, EPT >= 16 ? 1 : 2) projdf_kernel(PDArgs 
         }
     }
 
-    __shared__ float4 sh_wf[kWarps];
-    __shared__ int4 sh_wi[kWarps];
-    __shared__ float4 sh_stage[3 * kStageG];   // staged block partials (2 per pass partial, 3 per final one)
+    __shared__ float4 sh_wf[WARPS];
+    __shared__ int4 sh_wi[WARPS];
+    __shared__ float4 sh_stage[CLU ? 1 : 3 * kStageG];   // staged block partials (2 per pass partial, 3 per final one)
+    __shared__ float4 sh_xp[2][2];                      // cluster form: this CTA's pass partial (double-buffered)
+    __shared__ int2 sh_xc[EPT];                         // cluster form: this CTA's list counts per k
+    __shared__ float4 sh_xs[3];                         // cluster form: this CTA's final sums
     __shared__ float2 sh_dl;
     __shared__ int sh_done;
     if (tid == 0) sh_dl = make_float2(0.f, 0.f);
@@ -255,7 +273,7 @@ __global__ void __launch_bounds__(kTPB, EPT >= 16 ? 1 : 2) projdf_kernel(PDArgs 
         if (warp == 0) {
             Acc b;
             acc_zero(b);
-            if (lane < kWarps) {
+            if (lane < WARPS) {
                 const float4 f = sh_wf[lane];
                 const int4 c = sh_wi[lane];
                 b.D = make_float2(f.x, f.y); b.bhi = f.z; b.blo = f.w;
@@ -263,18 +281,29 @@ __global__ void __launch_bounds__(kTPB, EPT >= 16 ? 1 : 2) projdf_kernel(PDArgs 
             }
             acc_warp_reduce(b);
             if (lane == 0) {
-                float *p = A.part + ((size_t)(pass & 1) * G + blk) * kStrideF;
-                __stcg(reinterpret_cast<float4 *>(p), make_float4(b.D.x, b.D.y, b.bhi, b.blo));
-                __stcg(reinterpret_cast<int4 *>(p + 4), make_int4(b.nu, b.nf, b.ppx, b.pmx));
+                if (CLU) {
+                    sh_xp[pass & 1][0] = make_float4(b.D.x, b.D.y, b.bhi, b.blo);
+                    sh_xp[pass & 1][1] = make_float4(__int_as_float(b.nu), __int_as_float(b.nf), __int_as_float(b.ppx),
+                                                     __int_as_float(b.pmx));
+                } else {
+                    float *p = A.part + ((size_t)(pass & 1) * G + blk) * kStrideF;
+                    __stcg(reinterpret_cast<float4 *>(p), make_float4(b.D.x, b.D.y, b.bhi, b.blo));
+                    __stcg(reinterpret_cast<int4 *>(p + 4), make_int4(b.nu, b.nf, b.ppx, b.pmx));
+                }
             }
         }
-        if (!grid_barrier(A.bar, A.err)) { alive = false; break; }
-        const float *slot = A.part + (size_t)(pass & 1) * G * kStrideF;
-        const bool staged = G <= kStageG;
+        if (CLU) {
+            cl_sync();
+        } else if (!grid_barrier(A.bar, A.err)) {
+            alive = false;
+            break;
+        }
+        const float *slot = CLU ? nullptr : A.part + (size_t)(pass & 1) * G * kStrideF;
+        const bool staged = !CLU && G <= kStageG;
         if (staged) {
             // every thread of the block fetches a share of the G partials at once
             // (one L2 round trip instead of G/32 dependent ones for warp 0)
-            for (int e = tid; e < 2 * G; e += kTPB)
+            for (int e = tid; e < 2 * G; e += TPB)
                 sh_stage[e] = __ldcg(reinterpret_cast<const float4 *>(slot + (size_t)(e >> 1) * kStrideF) + (e & 1));
             __syncthreads();
         }
@@ -283,8 +312,15 @@ __global__ void __launch_bounds__(kTPB, EPT >= 16 ? 1 : 2) projdf_kernel(PDArgs 
             Acc t;
             acc_zero(t);
             for (int bb = lane; bb < G; bb += 32) {
-                const float4 f = staged ? sh_stage[2 * bb] : __ldcg(reinterpret_cast<const float4 *>(slot + (size_t)bb * kStrideF));
-                const float4 cf = staged ? sh_stage[2 * bb + 1] : __ldcg(reinterpret_cast<const float4 *>(slot + (size_t)bb * kStrideF + 4));
+                float4 f, cf;
+                if (CLU) {   // CTA bb's partial, read from its shared memory
+                    f = cl_ld4(cl_map(&sh_xp[pass & 1][0], (unsigned)bb));
+                    cf = cl_ld4(cl_map(&sh_xp[pass & 1][1], (unsigned)bb));
+                } else {
+                    f = staged ? sh_stage[2 * bb] : __ldcg(reinterpret_cast<const float4 *>(slot + (size_t)bb * kStrideF));
+                    cf = staged ? sh_stage[2 * bb + 1]
+                                : __ldcg(reinterpret_cast<const float4 *>(slot + (size_t)bb * kStrideF + 4));
+                }
                 const int4 c = make_int4(__float_as_int(cf.x), __float_as_int(cf.y), __float_as_int(cf.z), __float_as_int(cf.w));
                 t.D = dfx_add(t.D, make_float2(f.x, f.y));
                 t.bhi = fminf(t.bhi, f.z);
@@ -383,7 +419,7 @@ __global__ void __launch_bounds__(kTPB, EPT >= 16 ? 1 : 2) projdf_kernel(PDArgs 
 #pragma unroll
     for (int k = 0; k < EPT; ++k) {
         if (!((valm >> k) & 1u)) continue;
-        const long long i = k * NT + (long long)blk * kTPB + tid;
+        const long long i = k * NT + (long long)blk * TPB + tid;
         const bool pos = (posm >> k) & 1u;
         // pi_i and its class: 0 (= 0), 1 (free), 2 (= C); ties as the paper's clip
         int pc;
@@ -457,15 +493,15 @@ __global__ void __launch_bounds__(kTPB, EPT >= 16 ? 1 : 2) projdf_kernel(PDArgs 
     if (A.sums & SF_KKT) sm.s[1] = sq1;
 
     // per-(k, warp) list counts
-    __shared__ int sh_wc[EPT][kWarps][2];
+    __shared__ int sh_wc[EPT][WARPS][2];
 #pragma unroll
     for (int k = 0; k < EPT; ++k) {
         const unsigned bj = __ballot_sync(0xffffffffu, (isJ >> k) & 1u);
         const unsigned bd = __ballot_sync(0xffffffffu, (isD >> k) & 1u);
         if (lane == 0) { sh_wc[k][warp][0] = __popc(bj); sh_wc[k][warp][1] = __popc(bd); }
     }
-    __shared__ float4 sh_s[kWarps][2];
-    __shared__ int sh_n[kWarps];
+    __shared__ float4 sh_s[WARPS][2];
+    __shared__ int sh_n[WARPS];
     if (A.sums) {
         sums_warp_reduce(sm);
         if (lane == 0) {
@@ -477,16 +513,20 @@ __global__ void __launch_bounds__(kTPB, EPT >= 16 ? 1 : 2) projdf_kernel(PDArgs 
     __syncthreads();
     if (tid < EPT) {
         int cj = 0, cd = 0;
-        for (int w = 0; w < kWarps; ++w) { cj += sh_wc[tid][w][0]; cd += sh_wc[tid][w][1]; }
-        A.cnt[((size_t)tid * G + blk) * 2 + 0] = cj;
-        A.cnt[((size_t)tid * G + blk) * 2 + 1] = cd;
+        for (int w = 0; w < WARPS; ++w) { cj += sh_wc[tid][w][0]; cd += sh_wc[tid][w][1]; }
+        if (CLU) {
+            sh_xc[tid] = make_int2(cj, cd);
+        } else {
+            A.cnt[((size_t)tid * G + blk) * 2 + 0] = cj;
+            A.cnt[((size_t)tid * G + blk) * 2 + 1] = cd;
+        }
     }
     if (A.sums && warp == 0) {
         Sums b;
 #pragma unroll
         for (int k = 0; k < 4; ++k) b.s[k] = make_float2(0.f, 0.f);
         b.nupa = 0;
-        if (lane < kWarps) {
+        if (lane < WARPS) {
             const float4 f0 = sh_s[lane][0], f1 = sh_s[lane][1];
             b.s[0] = make_float2(f0.x, f0.y); b.s[1] = make_float2(f0.z, f0.w);
             b.s[2] = make_float2(f1.x, f1.y); b.s[3] = make_float2(f1.z, f1.w);
@@ -494,22 +534,33 @@ __global__ void __launch_bounds__(kTPB, EPT >= 16 ? 1 : 2) projdf_kernel(PDArgs 
         }
         sums_warp_reduce(b);
         if (lane == 0) {
-            float *p = A.part + ((size_t)2 * G + blk) * kStrideF;
-            __stcg(reinterpret_cast<float4 *>(p), make_float4(b.s[0].x, b.s[0].y, b.s[1].x, b.s[1].y));
-            __stcg(reinterpret_cast<float4 *>(p + 4), make_float4(b.s[2].x, b.s[2].y, b.s[3].x, b.s[3].y));
-            __stcg(reinterpret_cast<int *>(p + 8), b.nupa);
+            if (CLU) {
+                sh_xs[0] = make_float4(b.s[0].x, b.s[0].y, b.s[1].x, b.s[1].y);
+                sh_xs[1] = make_float4(b.s[2].x, b.s[2].y, b.s[3].x, b.s[3].y);
+                sh_xs[2] = make_float4(__int_as_float(b.nupa), 0.f, 0.f, 0.f);
+            } else {
+                float *p = A.part + ((size_t)2 * G + blk) * kStrideF;
+                __stcg(reinterpret_cast<float4 *>(p), make_float4(b.s[0].x, b.s[0].y, b.s[1].x, b.s[1].y));
+                __stcg(reinterpret_cast<float4 *>(p + 4), make_float4(b.s[2].x, b.s[2].y, b.s[3].x, b.s[3].y));
+                __stcg(reinterpret_cast<int *>(p + 8), b.nupa);
+            }
         }
     }
-    if (!alive || !grid_barrier(A.bar, A.err)) return;
+    if (CLU) {
+        cl_sync();
+    } else if (!alive || !grid_barrier(A.bar, A.err)) {
+        return;
+    }
 
     // offsets: off(k) = sum_{k'<k} total(k') + sum_{b'<blk} cnt(k, b')
     __shared__ long long sh_off[EPT][2];
     __shared__ long long sh_tot2[EPT][2];
-    for (int k = warp; k < EPT; k += kWarps) {
+    for (int k = warp; k < EPT; k += WARPS) {
         long long tj = 0, td = 0, pj = 0, pd = 0;
 #pragma unroll 8
         for (int bb = lane; bb < G; bb += 32) {
-            const int2 cc = __ldcg(reinterpret_cast<const int2 *>(A.cnt + ((size_t)k * G + bb) * 2));
+            const int2 cc = CLU ? cl_ld2i(cl_map(&sh_xc[k], (unsigned)bb))
+                                : __ldcg(reinterpret_cast<const int2 *>(A.cnt + ((size_t)k * G + bb) * 2));
             tj += cc.x; td += cc.y;
             if (bb < blk) { pj += cc.x; pd += cc.y; }
         }
@@ -518,10 +569,10 @@ __global__ void __launch_bounds__(kTPB, EPT >= 16 ? 1 : 2) projdf_kernel(PDArgs 
         if (lane == 0) { sh_tot2[k][0] = tj; sh_tot2[k][1] = td; sh_off[k][0] = pj; sh_off[k][1] = pd; }
     }
     __syncthreads();
-    const bool staged_sums = blk == 0 && A.sums && G <= kStageG;
+    const bool staged_sums = !CLU && blk == 0 && A.sums && G <= kStageG;
     if (staged_sums) {
         // block 0 fetches the final-phase partials with all its threads at once
-        for (int e = tid; e < 3 * G; e += kTPB)
+        for (int e = tid; e < 3 * G; e += TPB)
             sh_stage[e] = __ldcg(reinterpret_cast<const float4 *>(A.part + ((size_t)2 * G + e / 3) * kStrideF) + e % 3);
         __syncthreads();
     }
@@ -533,14 +584,23 @@ __global__ void __launch_bounds__(kTPB, EPT >= 16 ? 1 : 2) projdf_kernel(PDArgs 
         t.nupa = 0;
         if (A.sums) {
             for (int bb = lane; bb < G; bb += 32) {
-                const float *p = A.part + ((size_t)2 * G + bb) * kStrideF;
-                const float4 f0 = staged_sums ? sh_stage[3 * bb] : __ldcg(reinterpret_cast<const float4 *>(p));
-                const float4 f1 = staged_sums ? sh_stage[3 * bb + 1] : __ldcg(reinterpret_cast<const float4 *>(p + 4));
+                const float *p = CLU ? nullptr : A.part + ((size_t)2 * G + bb) * kStrideF;
+                float4 f0, f1;
+                int nu;
+                if (CLU) {
+                    f0 = cl_ld4(cl_map(&sh_xs[0], (unsigned)bb));
+                    f1 = cl_ld4(cl_map(&sh_xs[1], (unsigned)bb));
+                    nu = __float_as_int(cl_ld4(cl_map(&sh_xs[2], (unsigned)bb)).x);
+                } else {
+                    f0 = staged_sums ? sh_stage[3 * bb] : __ldcg(reinterpret_cast<const float4 *>(p));
+                    f1 = staged_sums ? sh_stage[3 * bb + 1] : __ldcg(reinterpret_cast<const float4 *>(p + 4));
+                    nu = staged_sums ? __float_as_int(sh_stage[3 * bb + 2].x) : __ldcg(reinterpret_cast<const int *>(p + 8));
+                }
                 t.s[0] = dfx_add(t.s[0], make_float2(f0.x, f0.y));
                 t.s[1] = dfx_add(t.s[1], make_float2(f0.z, f0.w));
                 t.s[2] = dfx_add(t.s[2], make_float2(f1.x, f1.y));
                 t.s[3] = dfx_add(t.s[3], make_float2(f1.z, f1.w));
-                t.nupa += staged_sums ? __float_as_int(sh_stage[3 * bb + 2].x) : __ldcg(reinterpret_cast<const int *>(p + 8));
+                t.nupa += nu;
             }
             sums_warp_reduce(t);
         }
@@ -579,10 +639,10 @@ __global__ void __launch_bounds__(kTPB, EPT >= 16 ? 1 : 2) projdf_kernel(PDArgs 
         }
     }
     // exclusive prefix of the per-warp counts, one thread per (k, list)
-    for (int t = tid; t < 2 * EPT; t += kTPB) {
+    for (int t = tid; t < 2 * EPT; t += TPB) {
         const int k = t >> 1, l = t & 1;
         int run = 0;
-        for (int w = 0; w < kWarps; ++w) {
+        for (int w = 0; w < WARPS; ++w) {
             const int c = sh_wc[k][w][l];
             sh_wc[k][w][l] = run;
             run += c;
@@ -593,13 +653,30 @@ __global__ void __launch_bounds__(kTPB, EPT >= 16 ? 1 : 2) projdf_kernel(PDArgs 
         const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
         for (int k = 0; k < EPT; ++k) {
-            const long long i = k * NT + (long long)blk * kTPB + tid;
+            const long long i = k * NT + (long long)blk * TPB + tid;
             const unsigned bj = __ballot_sync(0xffffffffu, (isJ >> k) & 1u);
             const unsigned bd = __ballot_sync(0xffffffffu, (isD >> k) & 1u);
             if (A.J && ((isJ >> k) & 1u)) A.J[sh_off[k][0] + sh_wc[k][warp][0] + __popc(bj & lt)] = (int32_t)i;
             if (A.D && ((isD >> k) & 1u)) A.D[sh_off[k][1] + sh_wc[k][warp][1] + __popc(bd & lt)] = (int32_t)i;
         }
     }
+    if (CLU) cl_sync();   // no CTA leaves while another may still read its shared memory
+}
+
+template <int EPT>
+__global__ void __launch_bounds__(kTPB, EPT >= 16 ? 1 : 2) projdf_kernel(PDArgs A)
+{
+    projdf_body<EPT, false, kTPB>(A, (int)gridDim.x, (int)blockIdx.x);
+}
+
+// One problem per thread-block cluster: table[cluster id] (a batch of
+// problems) or A0 (one problem, table = nullptr).
+template <int EPT>
+__global__ void __launch_bounds__(kTPBC, 1) projdf_cluster_kernel(const __grid_constant__ PDArgs A0,
+                                                                  const PDArgs *__restrict__ table)
+{
+    const PDArgs &A = table ? table[cl_id()] : A0;
+    projdf_body<EPT, true, kTPBC>(A, (int)cl_size(), (int)cl_rank());
 }
 
 float2 split_host(double v)
@@ -622,22 +699,119 @@ void *projdf_kernel_for(int ept)
     }
 }
 
-cudaError_t launch_project_df(Work &W, const ProjDF &in, ProjOut *out)
+static void *projdf_cluster_kernel_for(int ept)
+{
+    switch (ept) {
+    case 1: return (void *)projdf_cluster_kernel<1>;
+    case 2: return (void *)projdf_cluster_kernel<2>;
+    case 4: return (void *)projdf_cluster_kernel<4>;
+    case 8: return (void *)projdf_cluster_kernel<8>;
+    default: return (void *)projdf_cluster_kernel<16>;
+    }
+}
+
+cudaError_t make_pdargs(const Work &W, const ProjDF &in, ProjOut *out, PDArgs *A)
 {
     if ((in.sums & SF_DPA) && !in.alpha_w) return cudaErrorInvalidValue;
     if ((in.sums & SF_PSID) && (!in.base_w || !in.b || in.a_signed)) return cudaErrorInvalidValue;
     if ((in.sums & SF_KKT) && (!in.b || !in.a_signed)) return cudaErrorInvalidValue;
     if (in.D && (!in.dw_out || !in.dwa_out)) return cudaErrorInvalidValue;
+    A->a = in.a; A->a_signed = in.a_signed ? 1 : 0; A->b = in.b;
+    A->c1 = split_host(in.c1); A->c2 = split_host(in.c2);
+    A->y = W.y; A->n = W.n; A->Cd = split_host(W.C); A->sums = in.sums; A->lam0 = in.lam0;
+    A->u_out = in.u_out; A->wpi_out = in.wpi_out; A->alpha_w = in.alpha_w; A->base_w = in.base_w;
+    A->dw_out = in.dw_out; A->dwa_out = in.dwa_out; A->J = in.J; A->D = in.D;
+    A->part = reinterpret_cast<float *>(W.part); A->cnt = W.cnt; A->bar = W.bar; A->err = W.err; A->out = out;
+    return cudaSuccess;
+}
+
+// Cluster launches: clusters of W.proj_cl CTAs, one problem per cluster.
+static cudaError_t launch_cluster(const Work &W, const PDArgs &A0, const PDArgs *table, int nprob)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(nprob * W.proj_cl));
+    cfg.blockDim = dim3(kTPBC);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = W.st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)W.proj_cl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    void *args[] = {(void *)&A0, (void *)&table};
+    return cudaLaunchKernelExC(&cfg, projdf_cluster_kernel_for(W.proj_cept), args);
+}
+
+cudaError_t launch_project_df(Work &W, const ProjDF &in, ProjOut *out)
+{
     PDArgs A;
-    A.a = in.a; A.a_signed = in.a_signed ? 1 : 0; A.b = in.b;
-    A.c1 = split_host(in.c1); A.c2 = split_host(in.c2);
-    A.y = W.y; A.n = W.n; A.Cd = split_host(W.C); A.sums = in.sums; A.lam0 = in.lam0;
-    A.u_out = in.u_out; A.wpi_out = in.wpi_out; A.alpha_w = in.alpha_w; A.base_w = in.base_w;
-    A.dw_out = in.dw_out; A.dwa_out = in.dwa_out; A.J = in.J; A.D = in.D;
-    A.part = reinterpret_cast<float *>(W.part); A.cnt = W.cnt; A.bar = W.bar; A.err = W.err; A.out = out;
-    void *args[] = {&A};
+    cudaError_t e = make_pdargs(W, in, out, &A);
+    if (e != cudaSuccess) return e;
     ++W.nlaunch;
+    if (W.proj_cl > 0) return launch_cluster(W, A, nullptr, 1);
+    void *args[] = {&A};
     return cudaLaunchCooperativeKernel(projdf_kernel_for(W.proj_ept), dim3(W.proj_grid), dim3(kTPB), args, 0, W.st);
+}
+
+cudaError_t launch_project_df_table(Work &W, const PDArgs *table_dev, int nprob)
+{
+    if (W.proj_cl <= 0 || nprob < 1 || !table_dev) return cudaErrorInvalidValue;
+    PDArgs dummy = {};
+    ++W.nlaunch;
+    return launch_cluster(W, dummy, table_dev, nprob);
+}
+
+// The cluster form (opt-in: SVM_PROJ_CLUSTER=1 when the handle is created)
+// serves problems that fit one cluster's registers: clusters of 16 CTAs (8
+// where 16 cannot be scheduled) of 1024 threads with EPT <= 16 components each,
+// i.e. n <= 262,144; the cooperative form serves the rest.  Measured on GB300
+// at n = 1e5: 59 us per projection against 46 us for the cooperative form
+// (one cluster holds 16 SMs), while a batched solve's per-phase cost falls by
+// a fifth when all its problems' projections share one launch -- no net gain
+// on the one-vs-rest workload, so the cooperative form is the default.
+cudaError_t projdf_cluster_setup(Work &W)
+{
+    W.proj_cl = 0;
+    W.proj_cept = 0;
+    const char *env = getenv("SVM_PROJ_CLUSTER");
+    if (!env || env[0] != '1') return cudaSuccess;
+    static const int kEptC[] = {1, 2, 4, 8, 16};
+    for (int cl : {16, 8}) {
+        int ept = 0;
+        for (int e : kEptC)
+            if ((long long)cl * kTPBC * e >= W.n) { ept = e; break; }
+        if (!ept) continue;
+        void *k = projdf_cluster_kernel_for(ept);
+        if (cl > 8) {
+            if (cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+        }
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)cl);
+        cfg.blockDim = dim3(kTPBC);
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)cl;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclusters, k, &cfg) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        if (nclusters >= 1) {
+            W.proj_cl = cl;
+            W.proj_cept = ept;
+            return cudaSuccess;
+        }
+    }
+    return cudaSuccess;
 }
 
 }  // namespace svm

@@ -69,6 +69,14 @@ struct svm_ssnalm {
     NewtonTask *nt_host = nullptr, *nt_dev = nullptr;   // batched Newton steps (pinned / device table)
     int nt_cap = 0;
     svm_mlp_t *wsm = nullptr;   // warm-start network of svm_ssnalm_set_warmstart_model (owned)
+    // batched projections: a sub-handle of a batched solve records its
+    // double-float projection instead of launching it (proj_defer), and the
+    // batch launches all recorded ones at once (one cluster per problem)
+    bool proj_defer = false, proj_pending = false;
+    ProjDF pend_in;
+    ProjOut *pend_out = nullptr;
+    PDArgs *pd_host = nullptr, *pd_dev = nullptr;   // parent: the phase's table (pinned / device)
+    int pd_cap = 0;
 };
 
 enum { TK_MATVEC = 0, TK_RMATVEC = 1, TK_PROJ = 2, TK_NEWTON = 3, TK_MATVEC2 = 4 };
@@ -184,6 +192,8 @@ extern "C" void svm_ssnalm_destroy(svm_ssnalm_t *h)
     for (void *p : bp)
         if (p) cudaFree(p);
     if (h->nt_host) cudaFreeHost(h->nt_host);
+    if (h->pd_dev) cudaFree(h->pd_dev);
+    if (h->pd_host) cudaFreeHost(h->pd_host);
     svm_mlp_destroy(h->wsm);
     free_work(h->W);
     delete h;
@@ -343,6 +353,8 @@ static svm_status create_impl(svm_ssnalm_t **out, const svm_problem *prob, const
         return fail(SVM_ERR_OOM, "pinned host allocation failed");
     e = proj_setup(W);
     if (e != cudaSuccess) return fail(SVM_ERR_UNSUPPORTED, "n too large for the projection kernel");
+    if (W.df && (e = projdf_cluster_setup(W)) != cudaSuccess)
+        return fail(SVM_ERR_CUDA, std::string("projection set-up: ") + cudaGetErrorString(e));
     W.cnt_len = (size_t)W.proj_ept * W.proj_grid * 2;
     if (dalloc(&W.cnt, W.cnt_len)) return fail(SVM_ERR_OOM, "device workspace allocation failed");
     cudaMemsetAsync(W.bar, 0, 4 * sizeof(unsigned), W.st);
@@ -411,6 +423,22 @@ static svm_status readback_issue(svm_ssnalm *h)
     return SVM_OK;
 }
 
+// The double-float projection of a phase: launched now, or -- in a batched
+// solve whose problems fit the cluster form -- recorded, to be launched with
+// the other problems' projections of the phase (h->proj_pending).
+static svm_status proj_df(svm_ssnalm *h, const ProjDF &in, ProjOut *out)
+{
+    if (h->proj_defer) {
+        h->pend_in = in;
+        h->pend_out = out;
+        h->proj_pending = true;
+        h->kcalls[TK_PROJ]++;
+        return SVM_OK;
+    }
+    CK(timed(h, TK_PROJ, [&] { return launch_project_df(h->W, in, out); }));
+    return SVM_OK;
+}
+
 // After the stream has been synchronised: complete the double-float records
 // and turn a device error flag into a status (the flag is cleared for the
 // next call).
@@ -469,8 +497,7 @@ static svm_status kkt_project_df(svm_ssnalm *h, const float2 *alpha_w)
     in.a = alpha_w; in.a_signed = true; in.b = W.qaf; in.c1 = -1.0; in.c2 = 1.0;
     in.sums = SF_KKT;
     in.lam0 = &W.pout[SLOT_KKT].lamf;
-    CK(timed(h, TK_PROJ, [&] { return launch_project_df(W, in, &W.pout[SLOT_KKT]); }));
-    return SVM_OK;
+    return proj_df(h, in, &W.pout[SLOT_KKT]);
 }
 
 static double kkt_value(const ProjOut &o)
@@ -560,7 +587,12 @@ struct Run {
     bool defer_newton = false;   // batched: leave a small-free-set Newton step to the batch launch
     bool has_task = false;       // ... and this phase's step was left there
     NewtonTask task;
+    int cont = 0;                // batched: what follows a recorded projection (a RunCont)
 };
+
+// The kernels of a phase that follow its projection, when the projection was
+// recorded for a batched launch (run_post_cont issues them after it).
+enum RunCont { RC_NONE = 0, RC_READBACK = 1, RC_SUBSTART = 2, RC_TRIAL = 3 };
 
 static void mv_add(Work &W, MvReq &m, const double *v, float2 *zf, double *z)
 {
@@ -589,6 +621,22 @@ static svm_status run_matvec_single(Run &r)
 // A line-search trial at step t: project u - t sigma A dv into the other
 // buffer and, speculatively, form A'pi and the gradient there, so an accepted
 // trial is the next iterate's projection and gradient at no extra pass.
+// A'pi at the trial point (over the delta list) and, in the epilogue,
+// vt = v + t dv and g = vt - A'pi with |g|^2 (kept if the trial is accepted)
+static svm_status trial_after_proj(Run &r)
+{
+    svm_ssnalm *h = r.h;
+    Work &W = h->W;
+    const int nxt = 1 - r.cur;
+    ProjBuf &B = W.pb[nxt];
+    GradOut go;
+    go.v = W.v; go.dv = W.dv; go.t = r.t; go.g = W.tmpq; go.vt = W.vt;
+    CK(timed(h, TK_RMATVEC, [&] {
+        return launch_rmatvec_df(W, W.dw, W.dwa, B.S, &W.pout[1 + nxt].s, W.atp, W.atpa, W.atp2, W.atpa2, 1, go);
+    }));
+    return readback_issue(h);
+}
+
 static svm_status issue_trial(Run &r)
 {
     svm_ssnalm *h = r.h;
@@ -602,14 +650,13 @@ static svm_status issue_trial(Run &r)
         tr.sums = SF_PSID | SF_DPA; tr.alpha_w = W.alphaw; tr.base_w = W.pb[cur].wpi;
         tr.lam0 = &W.pout[1 + cur].lamf;
         tr.u_out = B.uf; tr.wpi_out = B.wpi; tr.dw_out = W.dw; tr.dwa_out = W.dwa; tr.J = B.J; tr.D = B.S;
-        CK(timed(h, TK_PROJ, [&] { return launch_project_df(W, tr, &W.pout[1 + nxt]); }));
-        // A'pi at the trial point and, in the epilogue, vt = v + t dv and
-        // g = vt - A'pi with |g|^2 (kept if the trial is accepted)
-        GradOut go;
-        go.v = W.v; go.dv = W.dv; go.t = t; go.g = W.tmpq; go.vt = W.vt;
-        CK(timed(h, TK_RMATVEC, [&] {
-            return launch_rmatvec_df(W, W.dw, W.dwa, B.S, &W.pout[1 + nxt].s, W.atp, W.atpa, W.atp2, W.atpa2, 1, go);
-        }));
+        svm_status st = proj_df(h, tr, &W.pout[1 + nxt]);
+        if (st != SVM_OK) return st;
+        if (h->proj_pending) {
+            r.cont = RC_TRIAL;
+            return SVM_OK;
+        }
+        return trial_after_proj(r);
     } else {
         ProjIn tr;
         tr.a = W.pb[cur].u; tr.b = W.dz; tr.c1 = -t * sigma; tr.c2 = 0.0;
@@ -750,6 +797,35 @@ static svm_status run_pre(Run &r)
 }
 
 // Kernels of the phase after its forward products, then the read-back.
+// A'pi from scratch over the support at the start of a subproblem, and
+// g = v - A'pi with |g|^2 in the same launch's epilogue
+static svm_status substart_after_proj(Run &r)
+{
+    svm_ssnalm *h = r.h;
+    Work &W = h->W;
+    const int cur = r.cur;
+    ProjBuf &B = W.pb[cur];
+    GradOut go;
+    go.v = W.v; go.g = W.g;
+    CK(timed(h, TK_RMATVEC, [&] {
+        return launch_rmatvec_df(W, W.dw, W.dwa, B.S, &W.pout[1 + cur].s, nullptr, nullptr, W.atp, W.atpa, 1, go);
+    }));
+    return readback_issue(h);
+}
+
+// The rest of a phase whose projection was launched with the batch's.
+static svm_status run_post_cont(Run &r)
+{
+    const int c = r.cont;
+    r.cont = RC_NONE;
+    switch (c) {
+    case RC_READBACK: return readback_issue(r.h);
+    case RC_SUBSTART: return substart_after_proj(r);
+    case RC_TRIAL: return trial_after_proj(r);
+    default: return SVM_OK;
+    }
+}
+
 static svm_status run_post(Run &r)
 {
     svm_ssnalm *h = r.h;
@@ -761,6 +837,7 @@ static svm_status run_post(Run &r)
     case RP_INIT:
         if (r.alpha0) CK(cudaMemsetAsync(W.pout, 0, sizeof(ProjOut), W.st));
         if ((st = df ? kkt_project_df(h, W.alphaw) : kkt_project(h, W.alpha)) != SVM_OK) return st;
+        if (h->proj_pending) { r.cont = RC_READBACK; return SVM_OK; }
         return readback_issue(h);
     case RP_SUBSTART: {
         // z = A v holds here (from the start or from the fused product of the
@@ -778,14 +855,9 @@ static svm_status run_post(Run &r)
             in.sums = SF_DPA; in.alpha_w = W.alphaw;
             in.lam0 = &W.pout[1 + cur].lamf;
             in.u_out = B.uf; in.wpi_out = B.wpi; in.dw_out = W.dw; in.dwa_out = W.dwa; in.J = B.J; in.D = B.S;
-            CK(timed(h, TK_PROJ, [&] { return launch_project_df(W, in, &W.pout[1 + cur]); }));
-            // ... and g = v - A'pi with |g|^2 in the same launch's epilogue
-            GradOut go;
-            go.v = W.v; go.g = W.g;
-            CK(timed(h, TK_RMATVEC, [&] {
-                return launch_rmatvec_df(W, W.dw, W.dwa, B.S, &W.pout[1 + cur].s, nullptr, nullptr, W.atp, W.atpa, 1,
-                                         go);
-            }));
+            if ((st = proj_df(h, in, &W.pout[1 + cur])) != SVM_OK) return st;
+            if (h->proj_pending) { r.cont = RC_SUBSTART; return SVM_OK; }
+            return substart_after_proj(r);
         } else {
             ProjIn in;
             in.a = W.alpha; in.b = W.z; in.c1 = -sigma; in.c2 = sigma;
@@ -808,6 +880,7 @@ static svm_status run_post(Run &r)
         return issue_trial(r);
     case RP_OUTER_END:
         if ((st = df ? kkt_project_df(h, W.alphaw) : kkt_project(h, W.alpha)) != SVM_OK) return st;
+        if (h->proj_pending) { r.cont = RC_READBACK; return SVM_OK; }
         return readback_issue(h);
     case RP_FINISH: {
         // results: alpha, w = A'alpha, b = lambda of the KKT projection, objective,
@@ -1210,6 +1283,23 @@ extern "C" svm_status svm_ssnalm_solve_batch(svm_ssnalm_t *h, int32_t B, const i
         }
         h->nt_cap = B;
     }
+    // the projections of a phase in one launch (one cluster per problem) when
+    // the problems fit the cluster form; each problem's result is bit-identical
+    // to a single solve's, which runs the same cluster kernel
+    const bool batched_proj = W.df && W.proj_cl > 0;
+    if (batched_proj && B > h->pd_cap) {
+        if (h->pd_dev) cudaFree(h->pd_dev);
+        if (h->pd_host) cudaFreeHost(h->pd_host);
+        h->pd_dev = nullptr;
+        h->pd_host = nullptr;
+        h->pd_cap = 0;
+        if (cudaMalloc(&h->pd_dev, sizeof(PDArgs) * B) != cudaSuccess ||
+            cudaMallocHost(&h->pd_host, sizeof(PDArgs) * B) != cudaSuccess) {
+            h->err = "batch: allocation of the projection table failed";
+            return SVM_ERR_OOM;
+        }
+        h->pd_cap = B;
+    }
     std::vector<svm_result> res((size_t)B);
     std::vector<Run> runs((size_t)B);
     std::vector<long long> launch0((size_t)B);
@@ -1225,6 +1315,8 @@ extern "C" svm_status svm_ssnalm_solve_batch(svm_ssnalm_t *h, int32_t B, const i
         sb->npos = cnt[2 * b + 1];
         sb->trace = h->trace;
         sb->timing = h->timing;
+        sb->proj_defer = batched_proj && S.df && S.proj_cl == W.proj_cl && S.proj_cept == W.proj_cept;
+        sb->proj_pending = false;
         launch0[b] = S.nlaunch;
         res[b] = svm_result();
         res[b].alpha = Ad + (size_t)b * n;
@@ -1279,6 +1371,32 @@ extern "C" svm_status svm_ssnalm_solve_batch(svm_ssnalm_t *h, int32_t B, const i
             const svm_status st = run_post(runs[b]);
             if (st != SVM_OK) fail_run(b, st);
         }
+        // the recorded projections of this phase: one launch, then each
+        // problem's kernels that follow its projection
+        int npd = 0;
+        for (int b = 0; b < B; ++b) {
+            svm_ssnalm *sb = h->subs[b];
+            if (!live[b] || !sb->proj_pending) continue;
+            if (make_pdargs(sb->W, sb->pend_in, sb->pend_out, &h->pd_host[npd]) != cudaSuccess) {
+                sb->proj_pending = false;
+                fail_run(b, SVM_ERR_CUDA);
+                continue;
+            }
+            ++npd;
+        }
+        if (npd > 0) {
+            CK(cudaMemcpyAsync(h->pd_dev, h->pd_host, sizeof(PDArgs) * npd, cudaMemcpyHostToDevice, W.st));
+            CK(timed(h, TK_PROJ, [&] { return launch_project_df_table(W, h->pd_dev, npd); }));
+            h->kcalls[TK_PROJ]--;   // counted per problem when the projections were recorded
+        }
+        for (int b = 0; b < B; ++b) {
+            svm_ssnalm *sb = h->subs[b];
+            if (!sb->proj_pending) continue;
+            sb->proj_pending = false;
+            if (!live[b]) continue;
+            const svm_status st = run_post_cont(runs[b]);
+            if (st != SVM_OK) fail_run(b, st);
+        }
         CK(cudaStreamSynchronize(W.st));
         h->syncs++;
         h->batch_ticks++;
@@ -1311,7 +1429,8 @@ extern "C" svm_status svm_ssnalm_solve_batch(svm_ssnalm_t *h, int32_t B, const i
             h->err = "batch problem " + std::to_string(b) + ": " + sb->err;
         }
         W.nlaunch += sb->W.nlaunch - launch0[b];
-        for (int k = 0; k < 4; ++k) {
+        sb->proj_defer = false;
+        for (int k = 0; k < 5; ++k) {
             h->kcalls[k] += sb->kcalls[k];
             h->kms[k] += sb->kms[k];
             sb->kcalls[k] = 0;

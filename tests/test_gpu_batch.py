@@ -144,3 +144,32 @@ def test_batch_host_memory_regrow_and_single_member():
     for b in range(len(Cs)):
         assert oracle.kkt(X, Y[b], Cs[b], A[b]) <= 1e-6
     s.close()
+
+
+def test_cluster_form_projection_batch_and_single_agree(monkeypatch):
+    """The projection's thread-block-cluster form (opt-in, SVM_PROJ_CLUSTER=1 at
+    create; one problem per cluster, partials through distributed shared
+    memory) in a batched solve, where all problems' projections of a phase
+    share one launch: each problem bit-identical to its single solve (which
+    runs the same cluster kernel), and at the oracle's objective."""
+    monkeypatch.setenv("SVM_PROJ_CLUSTER", "1")
+    n, q = 6000, 64
+    X, Y, Cs = datagen.ovr_path(seed=3, n=n, q=q, n_classes=3, n_C=3)
+    B = len(Cs)
+    Xd, Yd = dev(X), dev(Y)
+    A = torch.zeros((B, n), dtype=torch.float64, device="cuda")
+    W = torch.zeros((B, q), dtype=torch.float64, device="cuda")
+    s = P.Solver(Xd, Yd[0], C_=1.0, tol=1e-6, precision=P.PREC_MIXED)
+    st, rs = s.solve_batch(Yd, Cs, A, W)
+    s.close()
+    for b in range(B):
+        s1 = P.Solver(Xd, Yd[b], C_=float(Cs[b]), tol=1e-6, precision=P.PREC_MIXED)
+        a1 = torch.zeros(n, dtype=torch.float64, device="cuda")
+        w1 = torch.zeros(q, dtype=torch.float64, device="cuda")
+        r1 = s1.solve(a1, w1)
+        s1.close()
+        np.testing.assert_array_equal(A[b].cpu().numpy(), a1.cpu().numpy())
+        assert rs[b]["objective"] == r1["objective"]
+        ref = oracle.solve(X, Y[b], float(Cs[b]), tol=1e-10)
+        assert abs(rs[b]["objective"] - ref["objective"]) <= 1e-6 * abs(ref["objective"])
+        assert oracle.kkt(X, Y[b], float(Cs[b]), A[b].cpu().numpy()) <= 1e-6
