@@ -1097,8 +1097,21 @@ __global__ void __launch_bounds__(kCgThreads) newton_bchol_kernel(int q, const f
 // Measured on gauss1m (q = 128, TF32 tensor-core preconditioner, CG in 2-3
 // passes): p = 1.6e4: 207 us exact Gram vs 379 us matrix-free; p = 1e5: 587 vs
 // 535 us; p = 5e5: 2437 vs 1260 us.  The matrix-free solve carries a fixed
-// ~300 us (setup kernel, unused pass launches), so it starts at 1e5 rows.
-constexpr long long kMfMinP = 100000;
+// ~300 us (setup kernel, unused pass launches).  It starts above 5e4 rows: on
+// the one-vs-rest problems (n = 1e5, q = 128, free sets of 5e4-1e5 rows) eight
+// whole solves took 59 ms with that threshold against 94 ms at 1e5 (and 59 ms
+// at 2e4 or 5e3: no step falls between), gauss1m unchanged.
+constexpr long long kMfMinP = 50000;
+// the threshold in use (SVM_MF_MIN_P overrides it, for measurements)
+static long long mf_min_p()
+{
+    static long long v = -1;
+    if (v < 0) {
+        const char *e = getenv("SVM_MF_MIN_P");
+        v = (e && atoll(e) > 0) ? atoll(e) : kMfMinP;
+    }
+    return v;
+}
 constexpr int kMfSample = 2048;
 constexpr int kMfMaxPass = 6;
 constexpr int kMfThreads = 512;
@@ -1642,7 +1655,7 @@ bool newton_task(const Work &W, const int32_t *J, long long p, double sigma, con
     const int q = (int)W.q;
     const bool mixed = W.precision == 1 && W.xf32;
     if (W.csr || !mixed || q > kCgMaxQ || p <= 0) return false;
-    if (W.mf_st && q % 4 == 0 && p > kMfMinP) return false;
+    if (W.mf_st && q % 4 == 0 && p > mf_min_p()) return false;
     const long long ks = gram_splits(W, p, true);
     t->J = J;
     t->p = p;
@@ -1772,7 +1785,7 @@ cudaError_t launch_newton(Work &W, const int32_t *J, long long p_host, const lon
     if (KSmax > 4 * W.nsm) KSmax = 4 * W.nsm;
     if (ks > KSmax) ks = KSmax;
     const bool mixed = W.precision == 1 && W.xf32;
-    if (mixed && W.mf_st && q <= kCgMaxQ && q % 4 == 0 && p_host > kMfMinP)
+    if (mixed && W.mf_st && q <= kCgMaxQ && q % 4 == 0 && p_host > mf_min_p())
         return launch_newton_mf(W, J, p_host, sigma, g, dv, dots);
     // double-float partials are summed in one chain per element: one split per SM
     if (mixed && ks > W.nsm) ks = W.nsm;
