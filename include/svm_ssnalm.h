@@ -239,7 +239,9 @@ svm_status svm_op_newton(svm_ssnalm_t *h, const int32_t *J, int64_t p, double si
  * device), J device int32 with p row indices (any order; p = 0 gives zeros).
  * G is formed on the tcgen05 tensor cores with TF32 products (10-bit
  * mantissa) and FP32 sums within a block, blocks added in FP64; hsum is exact
- * to double-float accuracy.  Dense FP32 X with q % 16 == 0 and q <= 128 only
+ * to double-float accuracy.  q <= 128: one 128 x q accumulator per block;
+ * 128 < q <= 1024: (128-feature x 256-feature) tiles of the lower triangle,
+ * G symmetrised from it.  Dense FP32 X with q % 16 == 0 and q <= 1024 only
  * (else SVM_ERR_UNSUPPORTED).  Synchronises the stream. */
 svm_status svm_op_gram(svm_ssnalm_t *h, const int32_t *J, int64_t p, double *G, double *hsum);
 

@@ -28,7 +28,8 @@ struct ProjOut {
 enum ProjSums : int {
     SF_DPA = 1,    // sum[0] = |pi - alpha|^2                      (needs alpha)
     SF_PSID = 2,   // sum[1] = sum [pi(2u - pi) - pib(2ub - pib)]  (psi difference;
-                   //          base u is `a`, base pi is pi_base)
+                   //          base u is `a`, base pi is pi_base; the double-float
+                   //          kernel takes lam0 as the base's lambda-hat)
     SF_KKT = 4     // sum[0] = |alpha - pi|^2, sum[1] = |alpha|^2, sum[2] = sum alpha,
                    // sum[3] = sum max(0, 1 - (Qalpha_i + y_i lambda)); alpha = a, Qalpha = b
 };
@@ -296,8 +297,23 @@ cudaError_t newton_mf_alloc(Work &W);
 int gram_umma_blocks(const Work &W);
 size_t gram_umma_part_floats(const Work &W);
 cudaError_t launch_gram_umma(Work &W, const int32_t *J, long long p, float *cpart, float2 *hpart);
-// G = sum_b cpart[b], h = sum_b hpart[b] in FP64 (block order)
-cudaError_t launch_gram_umma_sum(Work &W, const float *cpart, const float2 *hpart, double *G, double *h);
+// The same Gram for 128 < q <= 1024 (q % 16 == 0), split over (row tile,
+// column chunk) pairs and KS row splits: cpart[ks] (q x q, the entries b <= a
+// and some above) and hpart[ks] (q double-float column sums) for ks < KS;
+// gram_wide_splits(W, p) is the KS that fits the workspace.
+int gram_wide_pairs(int q);
+int gram_wide_splits(const Work &W, long long p);
+cudaError_t launch_gram_umma_wide(Work &W, const int32_t *J, long long p, int KS, float *cpart, float2 *hpart);
+// M_pre = I + sigma (G - h h'/p) into W.Mf from G partials of TF32 Grams
+// (FP32, G of them) and double-float column sums; h itself into H (nullable)
+cudaError_t launch_build_m_tc(Work &W, int G, const float *cpart, const float2 *hpart, long long p, double sigma,
+                              float2 *H);
+// The Newton step for a large free set at 128 < q <= 1024 (k_newton_wide.cu)
+cudaError_t launch_newton_mfw(Work &W, const int32_t *J, long long p, double sigma, const double *g, double *dv,
+                              bool dots);
+// G = sum_b cpart[b], h = sum_b hpart[b] over nb partials in FP64 (block
+// order), both triangles of G from the partials' lower one
+cudaError_t launch_gram_umma_sum(Work &W, int nb, const float *cpart, const float2 *hpart, double *G, double *h);
 
 // CSR layout: structure/value checks (dev_flags[0]: structure, [1]: non-finite),
 // the CSC copy and column tasks, and the three products of the method

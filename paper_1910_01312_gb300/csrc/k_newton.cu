@@ -15,6 +15,7 @@
 #include <math.h>
 
 #include "internal.cuh"
+#include "newton_dev.cuh"
 
 namespace svm {
 
@@ -326,70 +327,6 @@ __global__ void build_m_df_batch_kernel(int q, const NewtonTask *__restrict__ T)
 // the Dinv_b.  CG stops at |M dv + g| <= max(min(eta, |g|^{1+tau}, 1e-10
 // |g|), 1e-14 |g|) (the tolerance itself in FP32) or after maxit steps; beta
 // is the flexible (Polak-Ribiere) form, robust to the FP32 preconditioner.
-constexpr int kCgThreads = 512;
-constexpr int kCgMaxQ = 128;
-constexpr int kPb = 8;   // panel width
-
-__device__ __forceinline__ int lpos(int i, int j)   // packed lower triangle, row-major
-{
-    return ((i * (i + 1)) >> 1) + j;
-}
-
-struct CgSmem {
-    float2 *M;    // qp x qp double-float M (zero padded)
-    float *L;     // packed lower triangle of the factor
-    float *D;     // (qp / kPb) blocks kPb x kPb: Dinv_b, row-major
-    float *t;     // qp: preconditioner work vector
-    float2 *X, *R, *P, *AP, *Z, *RO;
-};
-
-// warp 0, lanes 0..7: factor the diagonal block at kb and store its inverse;
-// false if a pivot is not positive
-__device__ __forceinline__ bool cg_diag8(float *L, int kb, float *Db)
-{
-    const int lane = threadIdx.x & 31;
-    const bool on = lane < kPb;
-    float a[kPb];
-#pragma unroll
-    for (int k = 0; k < kPb; ++k) a[k] = (on && k <= lane) ? L[lpos(kb + lane, kb + k)] : 0.f;
-    bool ok = true;
-    float rsd = 1.f;   // this lane's 1 / L_ii
-#pragma unroll
-    for (int j = 0; j < kPb; ++j) {
-        const float d = __shfl_sync(0xffffffffu, a[j], j);
-        const bool okj = (d > 0.f) && isfinite(d);
-        ok = ok && okj;
-        const float rs = okj ? rsqrtf(d) : 1.f;
-        if (lane == j) { a[j] = okj ? d * rs : 1.f; rsd = rs; }
-        else if (lane > j) a[j] *= rs;
-#pragma unroll
-        for (int k = 1; k < kPb; ++k) {
-            if (k > j) {
-                const float lkj = __shfl_sync(0xffffffffu, a[j], k);
-                if (lane >= k) a[k] = fmaf(-a[j], lkj, a[k]);
-            }
-        }
-    }
-    // lane c: column c of the inverse, x_i = (delta_ic - sum_{m<i} L_im x_m) / L_ii
-    float x[kPb];
-#pragma unroll
-    for (int i = 0; i < kPb; ++i) {
-        float s = (i == lane) ? 1.f : 0.f;
-#pragma unroll
-        for (int m = 0; m < kPb; ++m)
-            if (m < i) s = fmaf(-__shfl_sync(0xffffffffu, a[m], i), x[m], s);
-        const float ri = __shfl_sync(0xffffffffu, rsd, i);   // every lane takes part in the shuffle
-        x[i] = (i >= lane) ? s * ri : 0.f;
-    }
-    if (on) {
-#pragma unroll
-        for (int k = 0; k < kPb; ++k) {
-            if (k <= lane) L[lpos(kb + lane, kb + k)] = a[k];
-            Db[k * kPb + lane] = x[k];
-        }
-    }
-    return ok;
-}
 
 // t <- (L L')^{-1} t (blocked triangular solves through the Dinv_b)
 __device__ __forceinline__ void cg_precond(const CgSmem &S, int qp)
@@ -461,60 +398,6 @@ __device__ __forceinline__ float2 cg_dot(const float2 *a, const float2 *b, int q
     return t;
 }
 
-// In-place FP32 Cholesky of the packed qp x qp matrix in S.L (qp % 32 == 0,
-// rows beyond the problem set to the identity), right-looking by 8-column
-// panels; S.D receives the inverses of the 8 x 8 diagonal blocks.  Block-
-// uniform result: false when a pivot is not positive.
-__device__ bool cg_factor_packed(CgSmem &S, int qp)
-{
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    const int nb = qp / kPb;
-    __shared__ int bad;
-    if (tid == 0) bad = 0;
-    __syncthreads();
-    for (int b = 0; b < nb; ++b) {
-        const int kb = b * kPb;
-        if (warp == 0) {
-            const bool ok = cg_diag8(S.L, kb, S.D + b * kPb * kPb);
-            if (!ok && lane == 0) bad = 1;
-        }
-        __syncthreads();
-        if (bad || b + 1 == nb) break;
-        {   // rows below: L_rc = sum_k A_rk Dinv_b[c][k]; 4 rows per warp, 8 lanes a row
-            const int grp = lane >> 3, c = lane & 7;
-            const float *Db = S.D + b * kPb * kPb;
-            float dr[kPb];
-#pragma unroll
-            for (int k = 0; k < kPb; ++k) dr[k] = Db[c * kPb + k];
-            for (int r0 = kb + kPb + warp * 4; r0 < qp; r0 += nw * 4) {
-                const int r = r0 + grp;
-                const float av = (r < qp) ? S.L[lpos(r, kb + c)] : 0.f;
-                float acc = 0.f;
-#pragma unroll
-                for (int k = 0; k < kPb; ++k) acc = fmaf(__shfl_sync(0xffffffffu, av, grp * 8 + k), dr[k], acc);
-                if (r < qp) S.L[lpos(r, kb + c)] = acc;
-            }
-        }
-        __syncthreads();
-        // trailing triangle, a warp per row: A_rc -= sum_k L_rk L_ck, kb + 8 <= c <= r
-        for (int r = kb + kPb + warp; r < qp; r += nw) {
-            float lr[kPb];
-#pragma unroll
-            for (int k = 0; k < kPb; ++k) lr[k] = S.L[lpos(r, kb + k)];
-            for (int c = kb + kPb + lane; c <= r; c += 32) {
-                const int pc = lpos(c, kb);
-                float acc = 0.f;
-#pragma unroll
-                for (int k = 0; k < kPb; ++k) acc = fmaf(lr[k], S.L[pc + k], acc);
-                S.L[lpos(r, c)] -= acc;
-            }
-        }
-        __syncthreads();
-    }
-    const bool ok = !bad;
-    __syncthreads();
-    return ok;
-}
 
 // M (q x q double-float pairs) into S.M, zero padded to qp (one bulk copy when
 // q = qp), and the FP32 Cholesky factor of fl32(M) + shift into S.L / S.D (a
@@ -745,26 +628,6 @@ __global__ void __launch_bounds__(kCgThreads) newton_cg_fast_batch_kernel(int q,
 // Stop rule as the q <= 128 kernel (Algorithm 3's bound, tightened to 1e-10
 // |g|), at most maxit steps.  Every block takes the same barriers; on a
 // barrier that timed out (err = DEV_TIMEOUT) every block leaves.
-constexpr int kBcNb = 128;     // panel width of the blocked factor
-constexpr int kBcTile = 64;    // trailing-update tile
-constexpr int kBcMaxQ = 1024;
-
-// sum_j a_j b_j, j < q <= kBcMaxQ, double-float, fixed order; every thread of
-// the block returns the same value (and every block, given equal inputs)
-__device__ __forceinline__ float2 bc_dot(const float2 *a, const float2 *b, int q, float2 *red)
-{
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    float2 s = make_float2(0.f, 0.f);
-    for (int j = tid; j < q; j += blockDim.x) s = dfx_add(s, dfx_mul(a[j], b[j]));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s = dfx_add(s, shfl_xor_f2(s, o));
-    if (lane == 0) red[warp] = s;
-    __syncthreads();
-    float2 t = red[0];
-    for (int w = 1; w < nw; ++w) t = dfx_add(t, red[w]);
-    __syncthreads();
-    return t;
-}
 
 // t <- (L L')^{-1} t with the row-major factor Lg (row stride q) and the
 // inverses Dg of its 8 x 8 diagonal blocks; t in shared memory, zero beyond
@@ -838,138 +701,10 @@ __global__ void __launch_bounds__(kCgThreads) newton_bchol_kernel(int q, const f
     S.t = S.D + (kBcNb / kPb) * kPb * kPb;
     __shared__ float2 red[kCgThreads / 32];
     float2 *apg = xch, *zg = xch + kBcMaxQ;
-    // the largest diagonal entry (scale of the breakdown shift), in every block
-    float md = 0.f;
-    for (int j = tid; j < q; j += blockDim.x) md = fmaxf(md, Mf[(size_t)j * q + j].x);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) md = fmaxf(md, __shfl_xor_sync(0xffffffffu, md, o));
-    if (lane == 0) red[warp].x = md;
-    __syncthreads();
-    float maxdiag = 0.f;
-    for (int w = 0; w < nw; ++w) maxdiag = fmaxf(maxdiag, red[w].x);
-    __syncthreads();
     float shift = 0.f;
-    bool factored = false;
-    for (int attempt = 0; attempt < 6 && !factored; ++attempt) {
-        // fl32(M) + shift, lower triangle, into Lg
-        for (long long e = (long long)b * blockDim.x + tid; e < (long long)q * q; e += (long long)G * blockDim.x) {
-            const int i = (int)(e / q), j = (int)(e - (long long)i * q);
-            if (j <= i) Lg[e] = Mf[e].x + (i == j ? shift : 0.f);
-        }
-        if (b == 0 && tid == 0) *fflag = 0;
-        if (!grid_barrier(bar, err)) return;
-        bool bad = false;
-        for (int kb = 0; kb < q && !bad; kb += kBcNb) {
-            const int nbk = q - kb < kBcNb ? q - kb : kBcNb;
-            const int qpk = (nbk + 31) & ~31;
-            // (1) block 0: the diagonal block
-            if (b == 0) {
-                for (int i = warp; i < qpk; i += nw)
-                    for (int j = lane; j <= i; j += 32)
-                        S.L[lpos(i, j)] = (i < nbk) ? __ldcg(&Lg[(size_t)(kb + i) * q + kb + j]) : (i == j ? 1.f : 0.f);
-                __syncthreads();
-                const bool ok = cg_factor_packed(S, qpk);
-                if (!ok) {
-                    if (tid == 0) atomicExch(fflag, 1);
-                } else {
-                    for (int i = warp; i < nbk; i += nw)
-                        for (int j = lane; j <= i; j += 32) Lg[(size_t)(kb + i) * q + kb + j] = S.L[lpos(i, j)];
-                    for (int e = tid; e < ((nbk + kPb - 1) / kPb) * kPb * kPb; e += blockDim.x)
-                        Dg[(size_t)kb * kPb + e] = S.D[e];
-                }
-            }
-            if (!grid_barrier(bar, err)) return;
-            if (ld_relaxed_i32(fflag)) {
-                // every block has read the flag before block 0 clears it for the next attempt
-                bad = true;
-                if (!grid_barrier(bar, err)) return;
-                break;
-            }
-            if (kb + nbk >= q) break;
-            // (2) the panel's rows below: x L_kk' = a, a warp per row (every block
-            // first copies L_kk into its shared memory, with 1 / L_cc in S.t)
-            if (b != 0) {
-                for (int i = warp; i < nbk; i += nw)
-                    for (int j = lane; j <= i; j += 32) S.L[lpos(i, j)] = __ldcg(&Lg[(size_t)(kb + i) * q + kb + j]);
-            }
-            __syncthreads();
-            for (int c = tid; c < nbk; c += blockDim.x) S.t[c] = 1.f / S.L[lpos(c, c)];
-            __syncthreads();
-            for (int r = kb + nbk + gw; r < q; r += ngw) {
-                float a[kBcNb / 32];
-#pragma unroll
-                for (int m = 0; m < kBcNb / 32; ++m) {
-                    const int j = lane + 32 * m;
-                    a[m] = j < nbk ? __ldcg(&Lg[(size_t)r * q + kb + j]) : 0.f;
-                }
-                for (int c = 0; c < nbk; ++c) {
-                    const int own = c & 31, slot = c >> 5;
-                    float ac = 0.f;
-#pragma unroll
-                    for (int m = 0; m < kBcNb / 32; ++m)
-                        if (m == slot) ac = a[m];
-                    const float xc = __shfl_sync(0xffffffffu, ac, own) * S.t[c];
-#pragma unroll
-                    for (int m = 0; m < kBcNb / 32; ++m) {
-                        const int j = lane + 32 * m;
-                        if (j > c && j < nbk) a[m] = fmaf(-S.L[lpos(j, c)], xc, a[m]);
-                        if (j == c) a[m] = xc;
-                    }
-                }
-#pragma unroll
-                for (int m = 0; m < kBcNb / 32; ++m) {
-                    const int j = lane + 32 * m;
-                    if (j < nbk) Lg[(size_t)r * q + kb + j] = a[m];
-                }
-            }
-            if (!grid_barrier(bar, err)) return;
-            // (3) trailing update A_ij -= L_i,panel L_j,panel' over 64 x 64 tiles, j <= i
-            {
-                const int t0 = kb + nbk;
-                const int nt = (q - t0 + kBcTile - 1) / kBcTile;
-                const int ntiles = nt * (nt + 1) / 2;
-                float *TA = reinterpret_cast<float *>(S.M);                 // [64][nbk + 1]
-                float *TB = TA + kBcTile * (kBcNb + 1);                    // [64][nbk + 1]
-                const int ld = kBcNb + 1;
-                for (int tt = b; tt < ntiles; tt += G) {
-                    int ti = 0, rem = tt;
-                    while (rem > ti) { rem -= ti + 1; ++ti; }
-                    const int tj = rem;
-                    const int i0 = t0 + ti * kBcTile, j0 = t0 + tj * kBcTile;
-                    for (int e = tid; e < kBcTile * nbk; e += blockDim.x) {
-                        const int rr = e / nbk, m = e - rr * nbk;
-                        TA[rr * ld + m] = (i0 + rr < q) ? __ldcg(&Lg[(size_t)(i0 + rr) * q + kb + m]) : 0.f;
-                        TB[rr * ld + m] = (j0 + rr < q) ? __ldcg(&Lg[(size_t)(j0 + rr) * q + kb + m]) : 0.f;
-                    }
-                    __syncthreads();
-                    const int ii = tid >> 3, jc = tid & 7;   // row ii, columns jc + 8u
-                    float acc[kBcTile / 8];
-#pragma unroll
-                    for (int u = 0; u < kBcTile / 8; ++u) acc[u] = 0.f;
-                    for (int m = 0; m < nbk; ++m) {
-                        const float av = TA[ii * ld + m];
-#pragma unroll
-                        for (int u = 0; u < kBcTile / 8; ++u) acc[u] = fmaf(av, TB[(jc + 8 * u) * ld + m], acc[u]);
-                    }
-                    const int i = i0 + ii;
-#pragma unroll
-                    for (int u = 0; u < kBcTile / 8; ++u) {
-                        const int j = j0 + jc + 8 * u;
-                        if (i < q && j < q && j <= i) {
-                            float *lij = Lg + (size_t)i * q + j;
-                            *lij = __ldcg(lij) - acc[u];   // other blocks updated it in earlier panels
-                        }
-                    }
-                    __syncthreads();
-                }
-            }
-            if (!grid_barrier(bar, err)) return;
-        }
-        factored = !bad;
-        if (!factored) shift = (shift == 0.f) ? 1e-7f * maxdiag : shift * 100.f;
-    }
-    if (!factored) {
-        if (b == 0 && tid == 0) set_err(err, DEV_CHOL);
+    const int fr = bc_factor(q, Mf, Lg, Dg, fflag, bar, err, S, red, &shift);
+    if (fr <= 0) {
+        if (fr == 0 && b == 0 && tid == 0) set_err(err, DEV_CHOL);
         return;
     }
     // CG: replicated vectors where the tiles were
@@ -1112,6 +847,18 @@ static long long mf_min_p()
     }
     return v;
 }
+// The same at 128 < q <= 1024 (k_newton_wide.cu): the exact Gram's cost grows
+// as p q^2, the matrix-free one as p q per CG step plus a fixed ~q^3 set-up.
+constexpr long long kMfwMinP = 20000;
+static long long mfw_min_p()
+{
+    static long long v = -1;
+    if (v < 0) {
+        const char *e = getenv("SVM_MFW_MIN_P");
+        v = (e && atoll(e) > 0) ? atoll(e) : kMfwMinP;
+    }
+    return v;
+}
 constexpr int kMfSample = 2048;
 constexpr int kMfMaxPass = 6;
 constexpr int kMfThreads = 512;
@@ -1180,49 +927,10 @@ __global__ void __launch_bounds__(kCgThreads) newton_mf_setup_kernel(int q, cons
         if (tid == 0) st->done = 1;
         return;
     }
-    // Y = L^{-1} in the (now free) M area, row-major, ld = qp + 1: blocked
-    // forward substitution on I, Y_b = Dinv_b T_b, then T_r -= L_rb Y_b below
+    // Y = L^{-1} in the (now free) M area, row-major, ld = qp + 1
     float *Y = reinterpret_cast<float *>(S.M);
     const int ld = qp + 1;
-    for (int e = tid; e < qp * qp; e += nt) {
-        const int i = e / qp, j = e - i * qp;
-        Y[i * ld + j] = (i == j) ? 1.f : 0.f;
-    }
-    __syncthreads();
-    for (int b = 0; b < nb; ++b) {
-        const int kb = b * kPb;
-        if (tid <= kb + kPb - 1) {   // column tid of the block rows
-            const float *Db = S.D + b * kPb * kPb;
-            float yv[kPb], out[kPb];
-#pragma unroll
-            for (int k = 0; k < kPb; ++k) yv[k] = Y[(kb + k) * ld + tid];
-#pragma unroll
-            for (int i = 0; i < kPb; ++i) {
-                float a = 0.f;
-#pragma unroll
-                for (int k = 0; k < kPb; ++k) a = fmaf(Db[i * kPb + k], yv[k], a);
-                out[i] = a;
-            }
-#pragma unroll
-            for (int i = 0; i < kPb; ++i) Y[(kb + i) * ld + tid] = out[i];
-        }
-        __syncthreads();
-        {   // rows below, a warp per row: T_r -= L_rb Y_b over the columns <= kb + 7
-            const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-            for (int r = kb + kPb + warp; r < qp; r += nw) {
-                float lr[kPb];
-#pragma unroll
-                for (int k = 0; k < kPb; ++k) lr[k] = S.L[lpos(r, kb + k)];
-                for (int c = lane; c < kb + kPb; c += 32) {
-                    float a = 0.f;
-#pragma unroll
-                    for (int k = 0; k < kPb; ++k) a = fmaf(lr[k], Y[(kb + k) * ld + c], a);
-                    Y[r * ld + c] -= a;
-                }
-            }
-        }
-        __syncthreads();
-    }
+    tri_inverse_packed(S, qp, Y, ld);
     // Pinv = Y'Y (symmetric; Y lower triangular)
     for (int e = tid; e < qp * qp; e += nt) {
         const int i = e / qp, j = e - i * qp;
@@ -1511,11 +1219,11 @@ __global__ void __launch_bounds__(kMfThreads) newton_mf_pass_kernel(
 
 // M_pre = I + sigma (G - h h' / p) from the TF32 Gram partials (FP32 sums in
 // block order) and the exact column sums h; written as (value, 0) pairs for
-// the factor of newton_mf_setup_kernel.
+// the factor (and h itself, double-float, to H when H != nullptr).
 // Eight lanes per entry sum interleaved eighths of the partials, combined by
 // shuffles in a fixed order.
 __global__ void build_m_tc_kernel(int q, int G, const float *__restrict__ cpart, const float2 *__restrict__ hpart,
-                                  float2 rp, float2 sig, float2 *__restrict__ Mf)
+                                  float2 rp, float2 sig, float2 *__restrict__ Mf, float2 *__restrict__ H)
 {
     const int lane = threadIdx.x & 31, sub = lane & 7;
     const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwg = (gridDim.x * blockDim.x) >> 5;
@@ -1546,16 +1254,11 @@ __global__ void build_m_tc_kernel(int q, int G, const float *__restrict__ cpart,
             if (a == b) m = dfx_addf(m, 1.f);
             Mf[(size_t)a * q + b] = m;
             Mf[(size_t)b * q + a] = m;
+            if (a == b && H) H[a] = ha;
         }
     }
 }
 
-static size_t cg_fast_smem(int q)
-{
-    const size_t qp = (size_t)((q + 31) & ~31);
-    return qp * qp * sizeof(float2) + ((qp * (qp + 1)) / 2 + (qp / kPb) * kPb * kPb + qp) * sizeof(float) +
-           6 * qp * sizeof(float2);
-}
 
 static int g_cgs_attr = 0;
 
@@ -1577,6 +1280,15 @@ static float2 split2(double v)
     return make_float2(hi, (float)(v - (double)hi));
 }
 
+cudaError_t launch_build_m_tc(Work &W, int G, const float *cpart, const float2 *hpart, long long p, double sigma,
+                              float2 *H)
+{
+    build_m_tc_kernel<<<W.nsm * 2, 256, 0, W.st>>>((int)W.q, G, cpart, hpart, split2(1.0 / (double)p), split2(sigma),
+                                                   W.Mf, H);
+    ++W.nlaunch;
+    return cudaGetLastError();
+}
+
 // Large free set: subsample Gram -> preconditioner -> matrix-free CG passes.
 static cudaError_t launch_newton_mf(Work &W, const int32_t *J, long long p, double sigma, const double *g, double *dv,
                                     bool dots)
@@ -1591,7 +1303,8 @@ static cudaError_t launch_newton_mf(Work &W, const int32_t *J, long long p, doub
         float2 *hpart = reinterpret_cast<float2 *>(cpart + (size_t)G * q * q);
         const cudaError_t eg = launch_gram_umma(W, J, p, cpart, hpart);
         if (eg != cudaSuccess) return eg;
-        build_m_tc_kernel<<<W.nsm, 256, 0, W.st>>>(q, G, cpart, hpart, split2(1.0 / (double)p), split2(sigma), W.Mf);
+        build_m_tc_kernel<<<W.nsm, 256, 0, W.st>>>(q, G, cpart, hpart, split2(1.0 / (double)p), split2(sigma), W.Mf,
+                                                   nullptr);
     } else {
         // preconditioner from a stride subsample of s rows: M_s = I + sigma (p / s) (G_s - h_s h_s' / s)
         const int s = kMfSample;
@@ -1787,6 +1500,8 @@ cudaError_t launch_newton(Work &W, const int32_t *J, long long p_host, const lon
     const bool mixed = W.precision == 1 && W.xf32;
     if (mixed && W.mf_st && q <= kCgMaxQ && q % 4 == 0 && p_host > mf_min_p())
         return launch_newton_mf(W, J, p_host, sigma, g, dv, dots);
+    if (mixed && q > kCgMaxQ && q <= kBcMaxQ && q % 16 == 0 && p_host > mfw_min_p())
+        return launch_newton_mfw(W, J, p_host, sigma, g, dv, dots);
     // double-float partials are summed in one chain per element: one split per SM
     if (mixed && ks > W.nsm) ks = W.nsm;
     if (ks < 1) ks = 1;

@@ -1,0 +1,568 @@
+// k_newton_wide.cu -- the reduced Newton system of Proposition 3.5,
+//     (I_q + sigma (G - h h'/p)) dv = -g,   G = X_J'X_J,  h = X_J'1,  p = |J|,
+// for a large free set at 128 < q <= 1024 (mixed form: FP32 X, q % 16 == 0).
+//
+// The exact double-float Gram costs p q^2 / 2 double-float terms on the FP32
+// pipes (16 ms at p = 1e5, q = 784).  Instead, as for q <= 128 (k_newton.cu),
+// CG runs on the exact operator applied matrix-free,
+//     M d = d + sigma (X_J'(X_J d) - h (h'd) / p),
+// one pass over the rows of J per CG step in double-float (Dot2), and the
+// preconditioner comes from the Gram on the tensor cores:
+//  1. gram_umma_wide_kernel (k_umma.cu): TF32 products, FP32 sums, the exact
+//     column sums h beside it;
+//  2. build_m_tc_kernel (k_newton.cu): M_pre = I + sigma (G_tf32 - h h'/p);
+//  3. newton_mfw_setup_kernel (cooperative): the FP32 Cholesky factor L of
+//     M_pre by the grid (bc_factor), the inverses of its 128 x 128 diagonal
+//     tiles, then Pinv = (L L')^{-1} column by column -- two block triangular
+//     solves per column, eight columns per block at once, the column stored
+//     as a row (Pinv is symmetric up to rounding);
+//  4. newton_mfw_cg_kernel (cooperative): the whole CG of Algorithm 3, Step 1.
+//     Every block holds the q-vectors in shared memory and updates them
+//     identically (the same dot products in the same order).  A step is one
+//     pass (each block a contiguous share of J, a warp per row: t = x.d by
+//     Dot2 and a butterfly, then its share of X_J't), the block partials
+//     summed by column slices in block order, and z = Pinv r by rows across
+//     the grid: three grid barriers.
+// Stop rule as the other Newton solvers (Algorithm 3's bound, tightened to
+// 1e-10 |g|), at most maxit steps; beta in the flexible (Polak-Ribiere) form.
+// Every wait is bounded (grid_barrier records DEV_TIMEOUT and every block
+// leaves).
+#include <math.h>
+
+#include "internal.cuh"
+#include "newton_dev.cuh"
+
+namespace svm {
+
+namespace {
+
+constexpr int kWdBlk = 128;   // diagonal tile of the inverse factor
+constexpr int kWdCols = 8;    // columns of Pinv one block solves together
+
+__global__ void __launch_bounds__(kCgThreads) newton_mfw_setup_kernel(int q, const float2 *__restrict__ Mf,
+                                                                      float *__restrict__ Lg, float *__restrict__ Dg,
+                                                                      float *__restrict__ Linv,
+                                                                      float *__restrict__ Pinv, int *fflag,
+                                                                      unsigned *bar, int *err, double *info)
+{
+    extern __shared__ float4 cg_sm4[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int G = gridDim.x;
+    CgSmem S;   // one 128 x 128 tile's packed factor; the region of M holds the work arrays
+    S.M = reinterpret_cast<float2 *>(cg_sm4);
+    S.L = reinterpret_cast<float *>(S.M + kBcNb * kBcNb);
+    S.D = S.L + ((kBcNb * (kBcNb + 1)) >> 1);
+    S.t = S.D + (kBcNb / kPb) * kPb * kPb;
+    __shared__ float2 red[kCgThreads / 32];
+    float shift = 0.f;
+    const int fr = bc_factor(q, Mf, Lg, Dg, fflag, bar, err, S, red, &shift);
+    if (fr <= 0) {
+        if (fr == 0 && blockIdx.x == 0 && tid == 0) set_err(err, DEV_CHOL);
+        return;
+    }
+    if (blockIdx.x == 0 && tid == 0 && info) info[2] = shift;
+    const int nblk = (q + kWdBlk - 1) / kWdBlk;
+
+    // (1) Y_tt = L_tt^{-1} for the diagonal tiles (zero above the diagonal)
+    for (int tb = blockIdx.x; tb < nblk; tb += G) {
+        const int kb = tb * kWdBlk;
+        const int nbk = q - kb < kWdBlk ? q - kb : kWdBlk;
+        const int qpk = (nbk + 31) & ~31;
+        for (int i = warp; i < qpk; i += nw)
+            for (int j = lane; j <= i; j += 32)
+                S.L[lpos(i, j)] = (i < nbk) ? __ldcg(&Lg[(size_t)(kb + i) * q + kb + j]) : (i == j ? 1.f : 0.f);
+        for (int e = tid; e < (qpk / kPb) * kPb * kPb; e += blockDim.x) {
+            const int b8 = e / (kPb * kPb), w = e - b8 * kPb * kPb;
+            S.D[e] = (b8 * kPb < nbk) ? __ldcg(&Dg[(size_t)kb * kPb + e]) : ((w / kPb == w % kPb) ? 1.f : 0.f);
+        }
+        __syncthreads();
+        float *Y = reinterpret_cast<float *>(S.M);
+        const int ld = qpk + 1;
+        tri_inverse_packed(S, qpk, Y, ld);
+        float *Lt = Linv + (size_t)tb * kWdBlk * kWdBlk;
+        for (int e = tid; e < kWdBlk * kWdBlk; e += blockDim.x) {
+            const int i = e / kWdBlk, j = e - i * kWdBlk;
+            Lt[e] = (i < nbk && j <= i) ? Y[i * ld + j] : 0.f;
+        }
+        __syncthreads();
+    }
+    if (!grid_barrier(bar, err)) return;
+
+    // (2) columns c of Pinv: L y = e_c by block rows (T = E_i - L_i,<i Y_<i,
+    // Y_i = Y_ii T), then L' z = y backwards (T = Y_i - L_>i,i' Z_>i, Z_i = Y_ii' T)
+    const int ldv = nblk * kWdBlk;
+    float *V = reinterpret_cast<float *>(S.M);   // [kWdCols][ldv]: y, then z
+    float *T = V + kWdCols * ldv;                // [kWdCols][kWdBlk]
+    float *P4 = T + kWdCols * kWdBlk;            // [slices][kWdCols][kWdBlk] partial sums
+    const int nsl = blockDim.x / kWdBlk;         // column-parallel layout: jj fast, slice sl
+    const int jj = tid % kWdBlk, sl = tid / kWdBlk;
+    for (long long base = blockIdx.x; base < q; base += (long long)kWdCols * G) {
+        int cm[kWdCols];
+#pragma unroll
+        for (int m = 0; m < kWdCols; ++m) cm[m] = (base + (long long)m * G < q) ? (int)(base + (long long)m * G) : -1;
+        for (int e = tid; e < kWdCols * ldv; e += blockDim.x) V[e] = 0.f;
+        __syncthreads();
+        for (int i = 0; i < nblk; ++i) {
+            const int r0 = i * kWdBlk, nbi = q - r0 < kWdBlk ? q - r0 : kWdBlk;
+            for (int j = warp; j < nbi; j += nw) {   // a warp per row of the block row
+                float acc[kWdCols];
+#pragma unroll
+                for (int m = 0; m < kWdCols; ++m) acc[m] = 0.f;
+                const float *Lr = Lg + (size_t)(r0 + j) * q;
+#pragma unroll 4
+                for (int k = lane; k < r0; k += 32) {
+                    const float l = __ldcg(Lr + k);
+#pragma unroll
+                    for (int m = 0; m < kWdCols; ++m) acc[m] = fmaf(l, V[m * ldv + k], acc[m]);
+                }
+#pragma unroll
+                for (int m = 0; m < kWdCols; ++m) acc[m] = warp_sumf(acc[m]);
+                if (lane == 0) {
+#pragma unroll
+                    for (int m = 0; m < kWdCols; ++m) T[m * kWdBlk + j] = ((r0 + j) == cm[m] ? 1.f : 0.f) - acc[m];
+                }
+            }
+            __syncthreads();
+            const float *Lt = Linv + (size_t)i * kWdBlk * kWdBlk;
+            for (int j = warp; j < nbi; j += nw) {
+                float acc[kWdCols];
+#pragma unroll
+                for (int m = 0; m < kWdCols; ++m) acc[m] = 0.f;
+                for (int l = lane; l <= j; l += 32) {
+                    const float v = __ldcg(Lt + j * kWdBlk + l);
+#pragma unroll
+                    for (int m = 0; m < kWdCols; ++m) acc[m] = fmaf(v, T[m * kWdBlk + l], acc[m]);
+                }
+#pragma unroll
+                for (int m = 0; m < kWdCols; ++m) acc[m] = warp_sumf(acc[m]);
+                if (lane == 0) {
+#pragma unroll
+                    for (int m = 0; m < kWdCols; ++m) V[m * ldv + r0 + j] = acc[m];
+                }
+            }
+            __syncthreads();
+        }
+        for (int i = nblk - 1; i >= 0; --i) {
+            const int r0 = i * kWdBlk, nbi = q - r0 < kWdBlk ? q - r0 : kWdBlk;
+            float acc[kWdCols];
+#pragma unroll
+            for (int m = 0; m < kWdCols; ++m) acc[m] = 0.f;
+            if (jj < nbi) {
+#pragma unroll 4
+                for (int k = r0 + kWdBlk + sl; k < q; k += nsl) {
+                    const float l = __ldcg(&Lg[(size_t)k * q + r0 + jj]);
+#pragma unroll
+                    for (int m = 0; m < kWdCols; ++m) acc[m] = fmaf(l, V[m * ldv + k], acc[m]);
+                }
+            }
+#pragma unroll
+            for (int m = 0; m < kWdCols; ++m) P4[(sl * kWdCols + m) * kWdBlk + jj] = acc[m];
+            __syncthreads();
+            if (sl == 0 && jj < nbi) {
+#pragma unroll
+                for (int m = 0; m < kWdCols; ++m) {
+                    float s = P4[m * kWdBlk + jj];
+                    for (int t = 1; t < nsl; ++t) s += P4[(t * kWdCols + m) * kWdBlk + jj];
+                    T[m * kWdBlk + jj] = V[m * ldv + r0 + jj] - s;
+                }
+            }
+            __syncthreads();
+            const float *Lt = Linv + (size_t)i * kWdBlk * kWdBlk;
+#pragma unroll
+            for (int m = 0; m < kWdCols; ++m) acc[m] = 0.f;
+            if (jj < nbi) {
+                for (int l = jj + sl; l < nbi; l += nsl) {
+                    const float v = __ldcg(Lt + l * kWdBlk + jj);
+#pragma unroll
+                    for (int m = 0; m < kWdCols; ++m) acc[m] = fmaf(v, T[m * kWdBlk + l], acc[m]);
+                }
+            }
+#pragma unroll
+            for (int m = 0; m < kWdCols; ++m) P4[(sl * kWdCols + m) * kWdBlk + jj] = acc[m];
+            __syncthreads();
+            if (sl == 0 && jj < nbi) {
+#pragma unroll
+                for (int m = 0; m < kWdCols; ++m) {
+                    float s = P4[m * kWdBlk + jj];
+                    for (int t = 1; t < nsl; ++t) s += P4[(t * kWdCols + m) * kWdBlk + jj];
+                    V[m * ldv + r0 + jj] = s;
+                }
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int m = 0; m < kWdCols; ++m) {
+            if (cm[m] < 0) continue;
+            for (int r = tid; r < q; r += blockDim.x) Pinv[(size_t)cm[m] * q + r] = V[m * ldv + r];
+        }
+        __syncthreads();
+    }
+}
+
+struct MfwArgs {
+    const float *X;
+    const int32_t *J;
+    long long p;
+    int q;
+    float2 sig, rp;        // sigma and 1 / p, double-float
+    const float2 *H;       // h = X_J'1, double-float
+    const float *Pinv;     // q x q, row-major
+    const double *g;
+    double *dv;
+    float eta, tau;
+    int maxit;
+    double *info;          // [0] CG steps, [1] |residual| ([2] the factor's shift, from the set-up)
+    int *err;
+    const double *vdot;    // nullable: Armijo quantities into rdots[2..4]
+    double *rdots;
+    float2 *part;          // gridDim.x x q block partials of X_J'(X_J d)
+    float2 *yg;            // q: their sum
+    float *zg;             // q: Pinv r
+    unsigned *bar;
+};
+
+// dynamic shared memory of newton_mfw_cg_kernel<NF4>
+constexpr size_t mfw_smem(int nf4)
+{
+    return (size_t)nf4 * 128 * (4 * sizeof(float2) + 3 * sizeof(float) + (kCgThreads / 32) * sizeof(float2));
+}
+
+template <int NF4>
+__global__ void __launch_bounds__(kCgThreads, 1) newton_mfw_cg_kernel(const __grid_constant__ MfwArgs A)
+{
+    extern __shared__ float4 mw_sm4[];
+    constexpr int QW = NF4 * 128;   // padded width: NF4 float4 per lane
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int b = blockIdx.x, G = gridDim.x;
+    const int q = A.q;
+    float2 *Xv = reinterpret_cast<float2 *>(mw_sm4);
+    float2 *Rv = Xv + QW, *Dv = Rv + QW, *Hv = Dv + QW;
+    float *Dh = reinterpret_cast<float *>(Hv + QW), *Dl = Dh + QW, *Rf = Dl + QW;
+    float2 *wb = reinterpret_cast<float2 *>(Rf + QW);                  // [nw][QW] per-warp sums of a pass
+    float2 *APv = wb, *Yv = wb + QW, *Zv = Yv + QW, *ROv = Zv + QW;    // the same memory between passes
+    __shared__ float2 red[kCgThreads / 32];
+
+    for (int j = tid; j < QW; j += blockDim.x) {
+        float2 r = make_float2(0.f, 0.f);
+        if (j < q) {
+            const double v = -A.g[j];
+            const float hi = (float)v;
+            r = make_float2(hi, (float)(v - (double)hi));
+        }
+        Rv[j] = r;
+        Rf[j] = r.x + r.y;
+        Xv[j] = make_float2(0.f, 0.f);
+        Dv[j] = make_float2(0.f, 0.f);
+        Hv[j] = j < q ? __ldcg(&A.H[j]) : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    float2 rr = bc_dot(Rv, Rv, q, red);
+    const float gn = sqrtf(fmaxf(rr.x, 0.f));
+    const float tol = fmaxf(fminf(fminf(A.eta, powf(gn, 1.f + A.tau)), 1e-10f * gn), 1e-14f * gn);
+    const float tol2 = tol * tol;
+
+    // z = Pinv r, rows shared out over the grid's warps; Zv = (z, 0)
+    auto precond = [&]() -> bool {
+        const int gw = b * nw + warp, ngw = G * nw;
+        for (int i = gw; i < q; i += ngw) {
+            const float4 *pr = reinterpret_cast<const float4 *>(A.Pinv + (size_t)i * q);
+            float s = 0.f;
+            for (int c = lane; 4 * c < q; c += 32) {
+                const float4 pv = __ldcg(pr + c);
+                const float4 rv = *reinterpret_cast<const float4 *>(Rf + 4 * c);
+                s = fmaf(pv.x, rv.x, s);
+                s = fmaf(pv.y, rv.y, s);
+                s = fmaf(pv.z, rv.z, s);
+                s = fmaf(pv.w, rv.w, s);
+            }
+            s = warp_sumf(s);
+            if (lane == 0) A.zg[i] = s;
+        }
+        if (!grid_barrier(A.bar, A.err)) return false;
+        for (int j = tid; j < QW; j += blockDim.x) Zv[j] = make_float2(j < q ? __ldcg(&A.zg[j]) : 0.f, 0.f);
+        __syncthreads();
+        return true;
+    };
+    auto set_d = [&](float2 beta) {
+        for (int j = tid; j < QW; j += blockDim.x) {
+            const float2 d = dfx_add(Zv[j], dfx_mul(beta, Dv[j]));
+            Dv[j] = d;
+            Dh[j] = d.x;
+            Dl[j] = d.y;
+        }
+        __syncthreads();
+    };
+
+    int it = 0;
+    bool go = rr.x > tol2;
+    float2 rz = make_float2(0.f, 0.f);
+    if (go) {
+        if (!precond()) return;
+        set_d(make_float2(0.f, 0.f));
+        rz = bc_dot(Rv, Zv, q, red);
+    }
+    const float4 *Dh4 = reinterpret_cast<const float4 *>(Dh), *Dl4 = reinterpret_cast<const float4 *>(Dl);
+    while (go && it < A.maxit) {
+        // ---- y_b = X_Jb'(X_Jb d) over this block's rows ----
+        {
+            float as[4 * NF4], ac[4 * NF4];
+#pragma unroll
+            for (int k = 0; k < 4 * NF4; ++k) as[k] = ac[k] = 0.f;
+            const long long per = (A.p + G - 1) / G;
+            const long long rbeg = (long long)b * per;
+            const long long rend = rbeg + per < A.p ? rbeg + per : A.p;
+            for (long long c0 = rbeg + (long long)warp * 32; c0 < rend; c0 += (long long)nw * 32) {
+                const int myi = (c0 + lane < rend) ? __ldg(&A.J[c0 + lane]) : 0;
+                const int here = (int)(rend - c0 < 32 ? rend - c0 : 32);
+                for (int u = 0; u < here; ++u) {
+                    const int ii = __shfl_sync(0xffffffffu, myi, u);
+                    const float4 *row = reinterpret_cast<const float4 *>(A.X + (long long)ii * q);
+                    float4 xv[NF4];
+#pragma unroll
+                    for (int f = 0; f < NF4; ++f) {
+                        const int c = lane + 32 * f;
+                        xv[f] = (4 * c < q) ? __ldcs(row + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                    float s = 0.f, cc = 0.f;
+#pragma unroll
+                    for (int f = 0; f < NF4; ++f) {
+                        const int c = lane + 32 * f;
+                        const float4 dh = Dh4[c], dl = Dl4[c];   // zero beyond q
+                        dot2_step(xv[f].x, make_float2(dh.x, dl.x), s, cc);
+                        dot2_step(xv[f].y, make_float2(dh.y, dl.y), s, cc);
+                        dot2_step(xv[f].z, make_float2(dh.z, dl.z), s, cc);
+                        dot2_step(xv[f].w, make_float2(dh.w, dl.w), s, cc);
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        const float s2 = __shfl_xor_sync(0xffffffffu, s, o), c2 = __shfl_xor_sync(0xffffffffu, cc, o);
+                        float sn, e;
+                        two_sum(s, s2, sn, e);
+                        s = sn;
+                        cc += c2 + e;
+                    }
+                    float th, tl;
+                    two_sum(s, cc, th, tl);
+                    const float2 t = make_float2(th, tl);
+#pragma unroll
+                    for (int f = 0; f < NF4; ++f) {
+                        dot2_step(xv[f].x, t, as[4 * f + 0], ac[4 * f + 0]);
+                        dot2_step(xv[f].y, t, as[4 * f + 1], ac[4 * f + 1]);
+                        dot2_step(xv[f].z, t, as[4 * f + 2], ac[4 * f + 2]);
+                        dot2_step(xv[f].w, t, as[4 * f + 3], ac[4 * f + 3]);
+                    }
+                }
+            }
+            // warps in order -> the block partial (double-float)
+#pragma unroll
+            for (int f = 0; f < NF4; ++f) {
+                const int c = lane + 32 * f;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    float hi, lo;
+                    two_sum(as[4 * f + k], ac[4 * f + k], hi, lo);
+                    wb[warp * QW + 4 * c + k] = make_float2(hi, lo);
+                }
+            }
+            __syncthreads();
+            for (int j = tid; j < q; j += blockDim.x) {
+                float s = 0.f, c = 0.f;
+                for (int w = 0; w < nw; ++w) df_acc(s, c, wb[w * QW + j].x, wb[w * QW + j].y);
+                float hi, lo;
+                two_sum(s, c, hi, lo);
+                A.part[(size_t)b * q + j] = make_float2(hi, lo);
+            }
+            if (!grid_barrier(A.bar, A.err)) return;
+        }
+        // ---- y = sum of the block partials in block order, by column slices ----
+        {
+            const int cs = (q + G - 1) / G;
+            for (int k = warp; k < cs; k += nw) {
+                const int j = b * cs + k;
+                if (j >= q) break;
+                float2 s = make_float2(0.f, 0.f);
+                for (int bb = lane; bb < G; bb += 32) s = dfx_add(s, __ldcg(&A.part[(size_t)bb * q + j]));
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) s = dfx_add(s, shfl_xor_f2(s, o));
+                if (lane == 0) A.yg[j] = s;
+            }
+            if (!grid_barrier(A.bar, A.err)) return;
+        }
+        for (int j = tid; j < QW; j += blockDim.x) Yv[j] = j < q ? __ldcg(&A.yg[j]) : make_float2(0.f, 0.f);
+        __syncthreads();
+        // ---- the CG step (identical in every block) ----
+        const float2 hd = bc_dot(Hv, Dv, q, red);
+        const float2 hdp = dfx_mul(hd, A.rp);
+        for (int j = tid; j < QW; j += blockDim.x) {   // Ap = d + sigma (y - h (h'd) / p)
+            const float2 corr = dfx_mul(Hv[j], hdp);
+            APv[j] = j < q ? dfx_add(Dv[j], dfx_mul(A.sig, dfx_sub(Yv[j], corr))) : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        const float2 pap = bc_dot(Dv, APv, q, red);
+        if (!(pap.x > 0.f)) break;   // breakdown: keep the current iterate
+        const float2 al = dfx_div(rz, pap);
+        for (int j = tid; j < QW; j += blockDim.x) {
+            Xv[j] = dfx_add(Xv[j], dfx_mul(al, Dv[j]));
+            ROv[j] = Rv[j];
+            const float2 r = dfx_sub(Rv[j], dfx_mul(al, APv[j]));
+            Rv[j] = r;
+            Rf[j] = r.x + r.y;
+        }
+        __syncthreads();
+        ++it;
+        rr = bc_dot(Rv, Rv, q, red);
+        go = rr.x > tol2;
+        if (!go || it >= A.maxit) break;
+        if (!precond()) return;
+        const float2 rzn = bc_dot(Rv, Zv, q, red);
+        const float2 rzo = bc_dot(ROv, Zv, q, red);
+        float2 beta = dfx_div(dfx_sub(rzn, rzo), rz);
+        if (!(beta.x > 0.f)) beta = make_float2(0.f, 0.f);
+        rz = rzn;
+        set_d(beta);
+    }
+    if (b != 0) return;
+    for (int j = tid; j < q; j += blockDim.x) A.dv[j] = (double)Xv[j].x + (double)Xv[j].y;
+    if (tid == 0 && A.info) {
+        A.info[0] = it;
+        A.info[1] = sqrt((double)fmaxf(rr.x, 0.f));
+    }
+    if (A.vdot) {
+        // Algorithm 3, Step 2 quantities: rdots[2] = g'dv, rdots[3] = v'dv, rdots[4] = dv'dv
+        for (int j = tid; j < q; j += blockDim.x) {
+            const double a = A.g[j], c = A.vdot[j];
+            const float ah = (float)a, ch = (float)c;
+            APv[j] = make_float2(ah, (float)(a - (double)ah));
+            Yv[j] = make_float2(ch, (float)(c - (double)ch));
+        }
+        __syncthreads();
+        const float2 d0 = bc_dot(APv, Xv, q, red);
+        const float2 d1 = bc_dot(Yv, Xv, q, red);
+        const float2 d2 = bc_dot(Xv, Xv, q, red);
+        if (tid == 0) {
+            A.rdots[2] = (double)d0.x + (double)d0.y;
+            A.rdots[3] = (double)d1.x + (double)d1.y;
+            A.rdots[4] = (double)d2.x + (double)d2.y;
+        }
+    }
+}
+
+template <int NF4>
+cudaError_t launch_cg(const MfwArgs &a, int G, cudaStream_t st)
+{
+    static int attr = 0;
+    const size_t smem = mfw_smem(NF4);
+    if (!attr) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(newton_mfw_cg_kernel<NF4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = 1;
+    }
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, newton_mfw_cg_kernel<NF4>, kCgThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    MfwArgs aa = a;
+    void *args[] = {&aa};
+    return cudaLaunchCooperativeKernel((const void *)newton_mfw_cg_kernel<NF4>, dim3(G), dim3(kCgThreads), args, smem,
+                                       st);
+}
+
+int g_setup_attr = 0;
+
+float2 split2w(double v)
+{
+    const float hi = (float)v;
+    return make_float2(hi, (float)(v - (double)hi));
+}
+
+}  // namespace
+
+// Large free set, 128 < q <= 1024 (dense FP32 X, q % 16 == 0): tensor-core
+// Gram -> preconditioner -> matrix-free CG.  Workspace: the Gram partials in
+// W.part (consumed by build_m_tc), then W.part holds the 8 x 8 diagonal
+// inverses, the inverse tiles, the CG's exchange vectors and the factor's flag;
+// Pinv and h sit in W.M (unused by the mixed form), the factor in W.Lf.
+cudaError_t launch_newton_mfw(Work &W, const int32_t *J, long long p, double sigma, const double *g, double *dv,
+                              bool dots)
+{
+    const int q = (int)W.q;
+    if (q <= kCgMaxQ || q > kBcMaxQ || q % 16 != 0 || !W.xf32 || p < 1) return cudaErrorInvalidValue;
+    const int nf4 = (q + 127) / 128;
+    const int nblk = (q + kWdBlk - 1) / kWdBlk;
+    const int G = W.nsm;
+    const size_t need = (size_t)q * kPb + (size_t)nblk * kWdBlk * kWdBlk + 2 * (size_t)G * q + 3 * (size_t)q + 4;
+    if (need > 2 * W.part_len) return cudaErrorInvalidValue;
+    const int KS = gram_wide_splits(W, p);
+    float *cpart = reinterpret_cast<float *>(W.part);
+    float2 *hpart = reinterpret_cast<float2 *>(cpart + (size_t)KS * q * q);
+    float *Pinv = reinterpret_cast<float *>(W.M);
+    float2 *H = reinterpret_cast<float2 *>(Pinv + (size_t)q * q);
+    cudaError_t e = launch_gram_umma_wide(W, J, p, KS, cpart, hpart);
+    if (e == cudaSuccess) e = launch_build_m_tc(W, KS, cpart, hpart, p, sigma, H);
+    if (e != cudaSuccess) return e;
+    float *Dg = reinterpret_cast<float *>(W.part);
+    float *Linv = Dg + (size_t)q * kPb;
+    float2 *cgp = reinterpret_cast<float2 *>(Linv + (size_t)nblk * kWdBlk * kWdBlk);
+    float2 *yg = cgp + (size_t)G * q;
+    float *zg = reinterpret_cast<float *>(yg + q);
+    int *fflag = reinterpret_cast<int *>(zg + q);
+    double *info = W.red + 12;
+    // the factor and Pinv: every resident block
+    const size_t smem = cg_fast_smem(kCgMaxQ);
+    if (!g_setup_attr) {
+        e = cudaFuncSetAttribute(newton_mfw_setup_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        g_setup_attr = 1;
+    }
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, newton_mfw_setup_kernel, kCgThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    {
+        int qq = q;
+        const float2 *Mf = W.Mf;
+        float *Lg = W.Lf;
+        int *err = W.err;
+        unsigned *bar = W.bar;
+        void *args[] = {&qq, &Mf, &Lg, &Dg, &Linv, &Pinv, &fflag, &bar, &err, &info};
+        e = cudaLaunchCooperativeKernel((const void *)newton_mfw_setup_kernel, dim3(occ * W.nsm), dim3(kCgThreads),
+                                        args, smem, W.st);
+        if (e != cudaSuccess) return e;
+    }
+    MfwArgs a;
+    a.X = (const float *)W.X;
+    a.J = J;
+    a.p = p;
+    a.q = q;
+    a.sig = split2w(sigma);
+    a.rp = split2w(1.0 / (double)p);
+    a.H = H;
+    a.Pinv = Pinv;
+    a.g = g;
+    a.dv = dv;
+    a.eta = (float)W.eta;
+    a.tau = (float)W.tau;
+    a.maxit = W.cg_maxit;
+    a.info = info;
+    a.err = W.err;
+    a.vdot = dots ? W.v : nullptr;
+    a.rdots = W.red;
+    a.part = cgp;
+    a.yg = yg;
+    a.zg = zg;
+    a.bar = W.bar;
+    switch (nf4) {
+    case 2: e = launch_cg<2>(a, G, W.st); break;
+    case 3: e = launch_cg<3>(a, G, W.st); break;
+    case 4: e = launch_cg<4>(a, G, W.st); break;
+    case 5: e = launch_cg<5>(a, G, W.st); break;
+    case 6: e = launch_cg<6>(a, G, W.st); break;
+    case 7: e = launch_cg<7>(a, G, W.st); break;
+    default: e = launch_cg<8>(a, G, W.st); break;
+    }
+    W.nlaunch += 2;   // + the Gram and M_pre, counted by their launchers
+    return e;
+}
+
+}  // namespace svm

@@ -31,8 +31,12 @@
 // the components whose y_i pi_i differs from a base point, with the weights
 // that update A'pi from the base point's product (the mixed form never
 // recomputes A'pi over all rows).  Sums for the line search (SF_PSID: the
-// psi difference term by term), the inner stopping test (SF_DPA) and the KKT
-// residual (SF_KKT) come back as double-float pairs.
+// psi difference term by term; for a component free at both points as
+// (u - ub)(u + ub) - (lambda^2 - lambda_b^2), the lambda part once for all of
+// them -- formed as two products of size u^2 each, the double-float rounding
+// of ~|u|^2 2^-46 per component would swamp the decrease the Armijo test
+// looks for near a subproblem's solution), the inner stopping test (SF_DPA)
+// and the KKT residual (SF_KKT) come back as double-float pairs.
 #include <math.h>
 
 #include "internal.cuh"
@@ -462,6 +466,15 @@ __device__ __forceinline__ void projdf_body(const PDArgs &A, const int G, const 
             const int pbc = (bw.x == 0.f) ? 0 : (dfx_same(pb, Cd) ? 2 : 1);
             if (pc == 2 && pbc == 2) {
                 sm.s[2] = dfx_add(sm.s[2], A.b[i]);   // 2C (u - ub) = 2C c1 b_i, factor applied below
+            } else if (pc == 1 && pbc == 1) {
+                // both free: pi (2u - pi) = u^2 - lambda^2 (u - pi = lambda y), so the
+                // term is (u - ub)(u + ub) less lambda^2 - lambda_b^2, which block 0
+                // subtracts once per such element (counted in nupa; lambda_b = l0):
+                // no cancellation between two products of size |u|^2 per element
+                const float2 du = dfx_add(dfx_mul(A.c1, A.b[i]), A.c2);
+                const float2 ub = A.a[i];
+                sm.s[1] = dfx_add(sm.s[1], dfx_mul(du, dfx_add(dfx_add(ub, ub), du)));
+                ++sm.nupa;
             } else if (pc != 0 || pbc != 0) {
                 const float2 u = u_at(A, i, pos);
                 const float2 ub = A.a[i];
@@ -609,8 +622,9 @@ __device__ __forceinline__ void projdf_body(const PDArgs &A, const int G, const 
             for (int k = 0; k < EPT; ++k) { tj += sh_tot2[k][0]; td += sh_tot2[k][1]; }
             float2 s1 = t.s[1], s2 = t.s[2];
             if (A.sums & SF_PSID) {
-                // + 2C c1 sum_{both at C} b_i
+                // + 2C c1 sum_{both at C} b_i - n_free,free (lambda^2 - l0^2), lambda = l0 + dh
                 s1 = dfx_add(s1, dfx_mul(dfx_mul(make_float2(2.f * Cd.x, 2.f * Cd.y), A.c1), s2));
+                s1 = dfx_sub(s1, dfx_mul(dfx_from_ll(t.nupa), dfx_mul(dh, dfx_add(dfx_add(l0, l0), dh))));
                 s2 = make_float2(0.f, 0.f);
             }
             if (A.sums & SF_KKT) {
@@ -713,7 +727,8 @@ static void *projdf_cluster_kernel_for(int ept)
 cudaError_t make_pdargs(const Work &W, const ProjDF &in, ProjOut *out, PDArgs *A)
 {
     if ((in.sums & SF_DPA) && !in.alpha_w) return cudaErrorInvalidValue;
-    if ((in.sums & SF_PSID) && (!in.base_w || !in.b || in.a_signed)) return cudaErrorInvalidValue;
+    if ((in.sums & SF_PSID) && (!in.base_w || !in.b || in.a_signed || !in.lam0 || (in.sums & SF_KKT)))
+        return cudaErrorInvalidValue;
     if ((in.sums & SF_KKT) && (!in.b || !in.a_signed)) return cudaErrorInvalidValue;
     if (in.D && (!in.dw_out || !in.dwa_out)) return cudaErrorInvalidValue;
     A->a = in.a; A->a_signed = in.a_signed ? 1 : 0; A->b = in.b;

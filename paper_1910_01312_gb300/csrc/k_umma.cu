@@ -227,7 +227,233 @@ __global__ void __launch_bounds__(kUmThreads) gram_umma_kernel(const float *__re
     }
 }
 
-// G = sum_b C_b and h = sum_b h_b in FP64, in block order (the step-level entry point)
+// ---------------------------------------------------------------------------
+// The same Gram for 128 < q <= 1024 (q % 16 == 0), where one tensor-memory
+// accumulator cannot hold q x q.  The lower triangle is cut into pairs (ti, cj)
+// -- features 128 ti .. 128 ti + 127 (the MMA's M = 128 rows, A) against
+// features 256 cj .. 256 cj + 255 (N <= 256 columns, B) for each chunk cj that
+// reaches the diagonal of row tile ti -- and blockIdx.y splits the rows of J
+// (split-K).  A stage gathers 32 rows: B's features always, A's only when they
+// lie outside B's range (otherwise A's descriptor points into B's panel).  A
+// thread loads 16 bytes (4 features of one row; 8 lanes cover 128 contiguous
+// bytes of a row) and stores the 4 values in a rotated order, so that the 32
+// lanes of a warp write 32 distinct banks of the core-matrix layout.  The
+// pair whose chunk holds A's features also sums A's columns (h).  Each
+// feature is gathered by several pairs (about 6 x the rows' bytes at q =
+// 784); products are TF32, sums FP32 -- the preconditioner's Gram, as above.
+constexpr int kWgK = 32;                                 // gathered rows per stage
+constexpr int kWgBN = 256;                               // B features (MMA N, max)
+constexpr int kWgAM = 128;                               // A features (MMA M)
+constexpr unsigned kWgSbo = (kWgK / 4) * 128;            // next 8 features: after K/4 core matrices
+constexpr int kWgBBytes = kWgBN * kWgK * 4;              // 32 KB
+constexpr int kWgABytes = kWgAM * kWgK * 4;              // 16 KB
+constexpr int kWgStageBytes = kWgBBytes + kWgABytes;
+constexpr int kWgCols = 256;                             // tensor-memory columns
+constexpr size_t kWgSmem = 2 * (size_t)kWgStageBytes + 1024;
+
+__host__ __device__ inline int wg_chunks(int ti, int q)   // column chunks of row tile ti
+{
+    const int last = (128 * ti + 127 < q - 1) ? 128 * ti + 127 : q - 1;
+    return last / kWgBN + 1;
+}
+
+__host__ __device__ inline int wg_pairs(int q)
+{
+    int n = 0;
+    for (int ti = 0; ti * kWgAM < q; ++ti) n += wg_chunks(ti, q);
+    return n;
+}
+
+__device__ __forceinline__ float f4_at(const float4 &v, int j)
+{
+    return j == 0 ? v.x : (j == 1 ? v.y : (j == 2 ? v.z : v.w));
+}
+
+// 32 rows x 4 features of one lane into the K-major core-matrix panel at st
+// (feature-local index m0 + j, row k), in the rotated order
+__device__ __forceinline__ void wg_store4(unsigned char *st, int m0, int k, int rot, const float4 &v)
+{
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+        const int j = (jj + rot) & 3, m = m0 + j;
+        const unsigned off = (unsigned)(m >> 3) * kWgSbo + (unsigned)(k >> 2) * 128u + (unsigned)(m & 7) * 16u +
+                             (unsigned)(k & 3) * 4u;
+        *reinterpret_cast<float *>(st + off) = f4_at(v, j);
+    }
+}
+
+__global__ void __launch_bounds__(kUmThreads) gram_umma_wide_kernel(const float *__restrict__ X, int q,
+                                                                    const int32_t *__restrict__ J, long long p,
+                                                                    float *__restrict__ cpart,
+                                                                    float2 *__restrict__ hpart, int *err)
+{
+    extern __shared__ unsigned char um_dyn[];
+    __shared__ __align__(8) unsigned long long mbar[2];
+    __shared__ unsigned tmem_slot;
+    __shared__ int jrow[kWgK];
+    __shared__ float2 hsm[kUmThreads / 32][kWgAM];
+    unsigned char *base =
+        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(um_dyn) + 1023) & ~(uintptr_t)1023);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int t = blockIdx.x, ti = 0;
+    while (t >= wg_chunks(ti, q)) {
+        t -= wg_chunks(ti, q);
+        ++ti;
+    }
+    const int cj = t;
+    const int b0 = kWgBN * cj, a0 = kWgAM * ti;
+    const int nb = (q - b0 < kWgBN) ? q - b0 : kWgBN;   // a multiple of 16
+    const bool inside = (ti >> 1) == cj;                // A's features are B's 128 (ti & 1) .. + 127
+    const int KS = gridDim.y, ks = blockIdx.y;
+    const long long per = (p + KS - 1) / KS;
+    const long long r0 = (long long)ks * per;
+    const long long r1 = r0 + per < p ? r0 + per : p;
+    const int nst = r1 > r0 ? (int)((r1 - r0 + kWgK - 1) / kWgK) : 0;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(kWgCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 32) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        mbar_fence_init();
+    }
+    for (int i = threadIdx.x; i < 2 * kWgStageBytes / 16; i += kUmThreads)
+        reinterpret_cast<float4 *>(base)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = tmem_slot;
+    const unsigned idesc = umma_idesc_tf32(kWgAM, nb);
+    const int kr = 4 * warp + (lane & 3);    // the stage row this lane loads
+    const int c4 = lane >> 2;                // its 4-feature group within 32 features
+    const int rot = (lane >> 3) & 3;
+    const int gA = (ti & 1) * 4;             // A's first 32-feature group inside B
+
+    float hs[16], hc[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) hs[i] = hc[i] = 0.f;
+    int ok = 1;
+    for (int it = 0; it < nst; ++it) {
+        const int b = it & 1;
+        if (it >= 2 && ok) ok = mbar_wait_bounded(&mbar[b], (unsigned)((it - 2) >> 1) & 1u, err) ? 1 : 0;
+        const long long rb = r0 + (long long)it * kWgK;
+        if (threadIdx.x < kWgK) jrow[threadIdx.x] = (rb + threadIdx.x < r1) ? J[rb + threadIdx.x] : -1;
+        if (!__syncthreads_and(ok)) { ok = 0; break; }
+        const int jr = jrow[kr];
+        const float *row = X + (long long)(jr < 0 ? 0 : jr) * q;
+        float4 vb[kWgBN / 32];
+#pragma unroll
+        for (int g = 0; g < kWgBN / 32; ++g) {
+            const int m = b0 + 32 * g + 4 * c4;
+            vb[g] = (jr >= 0 && m < q) ? __ldcs(reinterpret_cast<const float4 *>(row + m))
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        float4 va[kWgAM / 32];
+        if (!inside) {
+#pragma unroll
+            for (int g = 0; g < kWgAM / 32; ++g) {
+                const int m = a0 + 32 * g + 4 * c4;
+                va[g] = (jr >= 0 && m < q) ? __ldcs(reinterpret_cast<const float4 *>(row + m))
+                                           : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+        unsigned char *st = base + b * kWgStageBytes;
+#pragma unroll
+        for (int g = 0; g < kWgBN / 32; ++g) wg_store4(st, 32 * g + 4 * c4, kr, rot, vb[g]);
+        if (!inside) {
+#pragma unroll
+            for (int g = 0; g < kWgAM / 32; ++g) wg_store4(st + kWgBBytes, 32 * g + 4 * c4, kr, rot, va[g]);
+        } else {
+#pragma unroll
+            for (int gg = 0; gg < kWgAM / 32; ++gg) {
+                const float4 v = gA ? vb[4 + gg] : vb[gg];
+                const float xs[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    float sn, er;
+                    two_sum(hs[4 * gg + j], xs[j], sn, er);
+                    hs[4 * gg + j] = sn;
+                    hc[4 * gg + j] += er;
+                }
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tc_fence_after();
+            const unsigned sb = smem_u32(st);
+            const unsigned sa = inside ? sb + (unsigned)(ti & 1) * 16u * kWgSbo : sb + (unsigned)kWgBBytes;
+#pragma unroll
+            for (int s = 0; s < kWgK / 8; ++s) {
+                const unsigned long long ad = umma_desc(sa + s * 256u, 128u, kWgSbo);
+                const unsigned long long bd = umma_desc(sb + s * 256u, 128u, kWgSbo);
+                tc_mma_tf32(tmem, ad, bd, idesc, (it > 0 || s > 0) ? 1 : 0);
+            }
+            tc_commit(&mbar[b]);
+        }
+    }
+    if (nst > 0 && ok) ok = mbar_wait_bounded(&mbar[(nst - 1) & 1], (unsigned)((nst - 1) >> 1) & 1u, err) ? 1 : 0;
+    tc_fence_after();
+    ok = __syncthreads_and(ok);
+
+    // D rows from tensor memory: warp w reads lanes 32 (w & 3) .. + 31 (A's
+    // features), columns 128 (w >> 2) .. + 127 of B
+    {
+        float *C = cpart + (size_t)ks * q * q;
+        const int quarter = warp & 3, half = warp >> 2;
+        const int a = a0 + 32 * quarter + lane;
+        const int cend = (128 * half + 128 < nb) ? 128 * half + 128 : nb;
+        for (int c0 = 128 * half; c0 < cend; c0 += 16) {
+            unsigned r[16];
+            if (nst > 0 && ok) {
+                tc_ld16(tmem + ((unsigned)(32 * quarter) << 16) + (unsigned)c0, r);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) r[j] = 0u;
+            }
+            if (a < q) {
+#pragma unroll
+                for (int j = 0; j < 16; j += 4)
+                    *reinterpret_cast<float4 *>(&C[(size_t)a * q + b0 + c0 + j]) =
+                        make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]), __uint_as_float(r[j + 2]),
+                                    __uint_as_float(r[j + 3]));
+            }
+        }
+    }
+    if (inside) {
+        // A's column sums: the four lanes of a 4-feature group (lane & 3 = the
+        // row), then the eight warps in order
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            float hi, lo;
+            two_sum(hs[i], hc[i], hi, lo);
+            float2 v = make_float2(hi, lo);
+            v = dfx_add(v, shfl_xor_f2(v, 1));
+            v = dfx_add(v, shfl_xor_f2(v, 2));
+            if ((lane & 3) == 0) hsm[warp][32 * (i >> 2) + 4 * c4 + (i & 3)] = v;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (inside && threadIdx.x < kWgAM && a0 + (int)threadIdx.x < q) {
+        float2 v = make_float2(0.f, 0.f);
+        for (int w = 0; w < kUmThreads / 32; ++w) v = dfx_add(v, hsm[w][threadIdx.x]);
+        hpart[(size_t)ks * q + a0 + threadIdx.x] = v;
+    }
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kWgCols) : "memory");
+    }
+}
+
+int g_wg_attr = 0;
+
+// G = sum_b C_b and h = sum_b h_b in FP64, in block order (the step-level
+// entry point); both triangles of G from the lower one of the partials
 __global__ void gram_sum_kernel(int q, int nb, const float *__restrict__ cpart, const float2 *__restrict__ hpart,
                                 double *__restrict__ Gout, double *__restrict__ hout)
 {
@@ -236,7 +462,9 @@ __global__ void gram_sum_kernel(int q, int nb, const float *__restrict__ cpart, 
          t += (long long)gridDim.x * blockDim.x) {
         double s = 0.0;
         if (t < qq) {
-            for (int b = 0; b < nb; ++b) s += (double)cpart[(size_t)b * qq + t];
+            const long long a = t / q, c = t - a * q;
+            const long long src = c <= a ? t : c * q + a;
+            for (int b = 0; b < nb; ++b) s += (double)cpart[(size_t)b * qq + src];
             Gout[t] = s;
         } else {
             const long long j = t - qq;
@@ -280,9 +508,43 @@ cudaError_t launch_gram_umma(Work &W, const int32_t *J, long long p, float *cpar
     return cudaGetLastError();
 }
 
-cudaError_t launch_gram_umma_sum(Work &W, const float *cpart, const float2 *hpart, double *G, double *h)
+int gram_wide_pairs(int q)
 {
-    gram_sum_kernel<<<W.nsm, 256, 0, W.st>>>((int)W.q, gram_umma_blocks(W), cpart, hpart, G, h);
+    return wg_pairs(q);
+}
+
+int gram_wide_splits(const Work &W, long long p)
+{
+    const long long q = W.q;
+    const long long np = wg_pairs((int)q);
+    long long cap = (long long)((2 * W.part_len) / (size_t)(q * q + 2 * q));
+    long long ks = (2 * W.nsm + np - 1) / np;
+    if (ks > cap) ks = cap;
+    const long long rows = (p + kWgK - 1) / kWgK;
+    if (ks > rows) ks = rows;
+    return ks < 1 ? 1 : (int)ks;
+}
+
+cudaError_t launch_gram_umma_wide(Work &W, const int32_t *J, long long p, int KS, float *cpart, float2 *hpart)
+{
+    const int q = (int)W.q;
+    if (q <= kUmMaxQ || q > 1024 || q % 16 != 0 || !W.xf32 || KS < 1) return cudaErrorInvalidValue;
+    if ((size_t)KS * ((size_t)q * q + 2 * q) > 2 * W.part_len) return cudaErrorInvalidValue;
+    if (!g_wg_attr) {
+        const cudaError_t ea =
+            cudaFuncSetAttribute(gram_umma_wide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgSmem);
+        if (ea != cudaSuccess) return ea;
+        g_wg_attr = 1;
+    }
+    gram_umma_wide_kernel<<<dim3((unsigned)wg_pairs(q), (unsigned)KS), kUmThreads, kWgSmem, W.st>>>(
+        (const float *)W.X, q, J, p, cpart, hpart, W.err);
+    ++W.nlaunch;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gram_umma_sum(Work &W, int nb, const float *cpart, const float2 *hpart, double *G, double *h)
+{
+    gram_sum_kernel<<<W.nsm, 256, 0, W.st>>>((int)W.q, nb, cpart, hpart, G, h);
     ++W.nlaunch;
     return cudaGetLastError();
 }

@@ -1505,18 +1505,25 @@ extern "C" svm_status svm_op_gram(svm_ssnalm_t *h, const int32_t *J, int64_t p, 
     if (!h || !G || !hsum || p < 0 || (p > 0 && !J)) return SVM_ERR_INVALID_ARG;
     Work &W = h->W;
     const int64_t q = W.q;
-    if (W.csr || !W.xf32 || q % 16 != 0 || q > 128) {
-        h->err = "svm_op_gram: dense FP32 X with q % 16 == 0 and q <= 128 only";
-        return SVM_ERR_UNSUPPORTED;
-    }
-    if (gram_umma_part_floats(W) > 2 * W.part_len) {
-        h->err = "svm_op_gram: workspace too small";
+    if (W.csr || !W.xf32 || q % 16 != 0 || q > 1024) {
+        h->err = "svm_op_gram: dense FP32 X with q % 16 == 0 and q <= 1024 only";
         return SVM_ERR_UNSUPPORTED;
     }
     float *cpart = reinterpret_cast<float *>(W.part);
-    float2 *hpart = reinterpret_cast<float2 *>(cpart + (size_t)gram_umma_blocks(W) * q * q);
-    CK(timed(h, TK_NEWTON, [&] { return launch_gram_umma(W, J, p, cpart, hpart); }));
-    CK(launch_gram_umma_sum(W, cpart, hpart, G, hsum));
+    if (q <= 128) {
+        if (gram_umma_part_floats(W) > 2 * W.part_len) {
+            h->err = "svm_op_gram: workspace too small";
+            return SVM_ERR_UNSUPPORTED;
+        }
+        float2 *hpart = reinterpret_cast<float2 *>(cpart + (size_t)gram_umma_blocks(W) * q * q);
+        CK(timed(h, TK_NEWTON, [&] { return launch_gram_umma(W, J, p, cpart, hpart); }));
+        CK(launch_gram_umma_sum(W, gram_umma_blocks(W), cpart, hpart, G, hsum));
+    } else {
+        const int KS = gram_wide_splits(W, p);
+        float2 *hpart = reinterpret_cast<float2 *>(cpart + (size_t)KS * q * q);
+        CK(timed(h, TK_NEWTON, [&] { return launch_gram_umma_wide(W, J, p, KS, cpart, hpart); }));
+        CK(launch_gram_umma_sum(W, KS, cpart, hpart, G, hsum));
+    }
     return sync_read(h);
 }
 

@@ -171,7 +171,11 @@ def test_projection_flat_segment(kernel):
                                             (np.float32, 6000, 784, 0.2), (np.float32, 3000, 256, 0.05),
                                             (np.float32, 2000, 200, 0.6),
                                             # p = 210,000: the matrix-free large-free-set solve (mixed form)
-                                            (np.float32, 420000, 128, 0.5)])
+                                            (np.float32, 420000, 128, 0.5),
+                                            # 128 < q <= 1024, p > 2e4: matrix-free CG preconditioned by the
+                                            # factor of the tcgen05 Gram (mixed form)
+                                            (np.float32, 60000, 784, 0.5), (np.float32, 50000, 144, 0.45),
+                                            (np.float32, 30000, 1024, 0.8), (np.float32, 41000, 400, 0.9)])
 def test_newton_direction(prec, gscale, dtype, n, q, frac):
     """Algorithm 3, Step 1.  PLAIN_FP64 solves the reduced system exactly
     (Cholesky); MIXED solves it by preconditioned CG to Algorithm 3's
@@ -205,7 +209,11 @@ def test_newton_direction(prec, gscale, dtype, n, q, frac):
 @pytest.mark.parametrize("n,q,p,order", [(5000, 128, 3000, "sorted"), (20000, 64, 20000, "sorted"),
                                          (300000, 128, 150000, "random"), (1000, 16, 1, "sorted"),
                                          (700, 112, 333, "random"), (2000, 128, 0, "sorted"),
-                                         (4096, 32, 4000, "sorted")])
+                                         (4096, 32, 4000, "sorted"),
+                                         # 128 < q <= 1024: 128 x 256 tiles of the lower triangle
+                                         (30000, 784, 25001, "random"), (3000, 144, 2999, "sorted"),
+                                         (9000, 1024, 8000, "random"), (2000, 400, 37, "sorted"),
+                                         (500, 256, 0, "sorted"), (6000, 512, 5000, "random")])
 def test_gram_tensor_cores(n, q, p, order):
     """G = X_J' X_J as the preconditioner of the large-free-set Newton step
     forms it on the tcgen05 tensor cores (TF32 products: inputs keep 10 of
@@ -214,7 +222,9 @@ def test_gram_tensor_cores(n, q, p, order):
     FP64), against the FP64 product of the gathered rows, elementwise relative
     to |X_J|'|X_J|.  h = X_J' 1 is double-float: 1e-10 of sum |x|.  Covers a
     ragged last stage (p not a multiple of 64), blocks with no rows (p < number
-    of blocks), p = 0, q < 128 (zero-padded MMA rows) and unsorted J."""
+    of blocks), p = 0, q < 128 (zero-padded MMA rows) and unsorted J; for q >
+    128 also row tiles only partly inside q (q = 144, 400, 784), a last column
+    chunk narrower than 256 and the largest q."""
     rng = np.random.default_rng(1000 + q + p)
     X = (rng.normal(size=(n, q)) * rng.uniform(0.1, 3.0, size=q)).astype(np.float32)
     y = np.where(rng.random(n) < 0.5, 1, -1).astype(np.int8)
