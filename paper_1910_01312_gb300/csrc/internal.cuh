@@ -27,9 +27,10 @@ struct ProjOut {
 // What a projection launch reduces besides lambda-hat, J and S (bit flags).
 enum ProjSums : int {
     SF_DPA = 1,    // sum[0] = |pi - alpha|^2                      (needs alpha)
-    SF_PSID = 2,   // sum[1] = sum [pi(2u - pi) - pib(2ub - pib)]  (psi difference;
-                   //          base u is `a`, base pi is pi_base; the double-float
-                   //          kernel takes lam0 as the base's lambda-hat)
+    SF_PSID = 2,   // sum[1] = sum [pi(2u - pi) - pib(2ub - pib)]  (psi difference,
+                   //          evaluated term by term in the multiplier-stationary
+                   //          form pi (2u - pi - 2 lambda y); base u is `a`, base
+                   //          pi is pi_base, lam0 must be the base's lambda-hat)
     SF_KKT = 4     // sum[0] = |alpha - pi|^2, sum[1] = |alpha|^2, sum[2] = sum alpha,
                    // sum[3] = sum max(0, 1 - (Qalpha_i + y_i lambda)); alpha = a, Qalpha = b
 };
@@ -169,6 +170,10 @@ struct Work {
     struct MfState *mf_st = nullptr;
     float *mf_pinv = nullptr;
     unsigned *mf_counter = nullptr;
+    // wide matrix-free Newton state (mixed form, 128 < q <= 1024): the free
+    // set (n bits) and sigma the preconditioner in M was built for
+    unsigned *mfw_mask = nullptr;
+    struct MfwState *mfw_st = nullptr;
     double *M = nullptr;      // q*q Newton matrix / Cholesky factor
     float *Lf = nullptr;      // q*(q+1) FP32 factor when it does not fit in shared memory
     float2 *Mf = nullptr;     // q*q FP32 (hi, lo) split of M (double-float CG operator)
@@ -303,14 +308,20 @@ cudaError_t launch_gram_umma(Work &W, const int32_t *J, long long p, float *cpar
 // gram_wide_splits(W, p) is the KS that fits the workspace.
 int gram_wide_pairs(int q);
 int gram_wide_splits(const Work &W, long long p);
-cudaError_t launch_gram_umma_wide(Work &W, const int32_t *J, long long p, int KS, float *cpart, float2 *hpart);
+// skip (nullable, device): when *skip != 0 the launch does nothing.
+cudaError_t launch_gram_umma_wide(Work &W, const int32_t *J, long long p, int KS, float *cpart, float2 *hpart,
+                                  const int *skip = nullptr);
 // M_pre = I + sigma (G - h h'/p) into W.Mf from G partials of TF32 Grams
 // (FP32, G of them) and double-float column sums; h itself into H (nullable)
 cudaError_t launch_build_m_tc(Work &W, int G, const float *cpart, const float2 *hpart, long long p, double sigma,
-                              float2 *H);
+                              float2 *H, const int *skip = nullptr);
 // The Newton step for a large free set at 128 < q <= 1024 (k_newton_wide.cu)
+// and its workspace (allocated at create for the mixed form)
 cudaError_t launch_newton_mfw(Work &W, const int32_t *J, long long p, double sigma, const double *g, double *dv,
                               bool dots);
+cudaError_t newton_mfw_alloc(Work &W);
+// forget the preconditioner (the next wide Newton step builds one)
+cudaError_t newton_mfw_reset(Work &W);
 // G = sum_b cpart[b], h = sum_b hpart[b] over nb partials in FP64 (block
 // order), both triangles of G from the partials' lower one
 cudaError_t launch_gram_umma_sum(Work &W, int nb, const float *cpart, const float2 *hpart, double *G, double *h);

@@ -1223,8 +1223,10 @@ __global__ void __launch_bounds__(kMfThreads) newton_mf_pass_kernel(
 // Eight lanes per entry sum interleaved eighths of the partials, combined by
 // shuffles in a fixed order.
 __global__ void build_m_tc_kernel(int q, int G, const float *__restrict__ cpart, const float2 *__restrict__ hpart,
-                                  float2 rp, float2 sig, float2 *__restrict__ Mf, float2 *__restrict__ H)
+                                  float2 rp, float2 sig, float2 *__restrict__ Mf, float2 *__restrict__ H,
+                                  const int *skip)
 {
+    if (skip && __ldcg(skip)) return;
     const int lane = threadIdx.x & 31, sub = lane & 7;
     const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwg = (gridDim.x * blockDim.x) >> 5;
     // the trip count is uniform per warp (four entries per warp and step), so
@@ -1281,10 +1283,10 @@ static float2 split2(double v)
 }
 
 cudaError_t launch_build_m_tc(Work &W, int G, const float *cpart, const float2 *hpart, long long p, double sigma,
-                              float2 *H)
+                              float2 *H, const int *skip)
 {
     build_m_tc_kernel<<<W.nsm * 2, 256, 0, W.st>>>((int)W.q, G, cpart, hpart, split2(1.0 / (double)p), split2(sigma),
-                                                   W.Mf, H);
+                                                   W.Mf, H, skip);
     ++W.nlaunch;
     return cudaGetLastError();
 }
@@ -1304,7 +1306,7 @@ static cudaError_t launch_newton_mf(Work &W, const int32_t *J, long long p, doub
         const cudaError_t eg = launch_gram_umma(W, J, p, cpart, hpart);
         if (eg != cudaSuccess) return eg;
         build_m_tc_kernel<<<W.nsm, 256, 0, W.st>>>(q, G, cpart, hpart, split2(1.0 / (double)p), split2(sigma), W.Mf,
-                                                   nullptr);
+                                                   nullptr, nullptr);
     } else {
         // preconditioner from a stride subsample of s rows: M_s = I + sigma (p / s) (G_s - h_s h_s' / s)
         const int s = kMfSample;

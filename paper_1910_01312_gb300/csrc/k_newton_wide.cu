@@ -27,6 +27,15 @@
 // 1e-10 |g|), at most maxit steps; beta in the flexible (Polak-Ribiere) form.
 // Every wait is bounded (grid_barrier records DEV_TIMEOUT and every block
 // leaves).
+//
+// Reuse: consecutive Newton steps of a subproblem often share almost all of
+// J, and only the preconditioner depends on it.  A first kernel counts the
+// rows of J missing from the set the current preconditioner was built for (a
+// bitmap) and those that left it; when together they are at most 1 % of p,
+// sigma is unchanged and the last CG took at most 8 steps, steps 1-3 are
+// skipped (their kernels return at once) and h comes from a column-sum pass
+// instead.  CG still runs on the exact operator of the current J, so only its
+// step count depends on this.
 #include <math.h>
 
 #include "internal.cuh"
@@ -43,8 +52,10 @@ __global__ void __launch_bounds__(kCgThreads) newton_mfw_setup_kernel(int q, con
                                                                       float *__restrict__ Lg, float *__restrict__ Dg,
                                                                       float *__restrict__ Linv,
                                                                       float *__restrict__ Pinv, int *fflag,
-                                                                      unsigned *bar, int *err, double *info)
+                                                                      unsigned *bar, int *err, double *info,
+                                                                      const int *skip)
 {
+    if (__ldcg(skip)) return;   // the same value in every block: no barrier is taken
     extern __shared__ float4 cg_sm4[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     const int G = gridDim.x;
@@ -197,6 +208,136 @@ __global__ void __launch_bounds__(kCgThreads) newton_mfw_setup_kernel(int q, con
         }
         __syncthreads();
     }
+}
+
+constexpr double kMfwReuseFrac = 0.01;   // changed rows of J, relative to p, that keep the preconditioner
+constexpr int kMfwStaleIt = 8;           // CG steps above which it is rebuilt at the next step
+
+}  // namespace
+
+struct MfwState {
+    double sigma;      // sigma the preconditioner was built for
+    long long p;       // |J| it was built for (the bitmap holds that J)
+    unsigned added;    // this step: rows of J not in the bitmap (summed by the blocks)
+    unsigned done;     // finished blocks (last-block reductions)
+    int valid;         // a preconditioner exists
+    int skip;          // this step reuses it
+};
+
+namespace {
+
+// skip = 1 when J differs from the bitmap's set in at most frac p rows, sigma
+// is the same and the last CG took at most stale_it steps; else 0 and the
+// state records this J's size and sigma (the bitmap is rewritten next).
+__global__ void __launch_bounds__(256) mfw_decide_kernel(const int32_t *__restrict__ J, long long p, double sigma,
+                                                         const unsigned *__restrict__ mask, MfwState *st,
+                                                         const double *info, double frac, int stale_it)
+{
+    unsigned c = 0;
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < p; r += (long long)gridDim.x * blockDim.x) {
+        const int i = J[r];
+        c += ((mask[i >> 5] >> (i & 31)) & 1u) ? 0u : 1u;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    __shared__ unsigned ws[8];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    unsigned t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+    atomicAdd(&st->added, t);
+    __threadfence();
+    if (atomicAdd(&st->done, 1u) != gridDim.x - 1) return;
+    __threadfence();
+    const long long added = (long long)atomicAdd(&st->added, 0u);
+    const long long removed = st->p - (p - added);
+    const bool stale = st->valid == 0 || st->sigma != sigma || (double)(added + removed) > frac * (double)p ||
+                       !(info[0] <= (double)stale_it);
+    st->skip = stale ? 0 : 1;
+    if (stale) {
+        st->valid = 1;
+        st->sigma = sigma;
+        st->p = p;
+    }
+    st->added = 0u;
+    st->done = 0u;
+}
+
+// the bitmap := J, on a rebuild (two launches: clear, then set)
+__global__ void mfw_mask_clear_kernel(unsigned *__restrict__ mask, long long nwords, const MfwState *st)
+{
+    if (__ldcg(&st->skip)) return;
+    for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < nwords; w += (long long)gridDim.x * blockDim.x)
+        mask[w] = 0u;
+}
+
+__global__ void mfw_mask_set_kernel(const int32_t *__restrict__ J, long long p, unsigned *__restrict__ mask,
+                                    const MfwState *st)
+{
+    if (__ldcg(&st->skip)) return;
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < p; r += (long long)gridDim.x * blockDim.x) {
+        const int i = J[r];
+        atomicOr(&mask[i >> 5], 1u << (i & 31));
+    }
+}
+
+// h = X_J'1 (double-float) when the Gram is skipped: each block a contiguous
+// share of J, a thread per 4 columns, rows in order (TwoSum); the last block
+// adds the block partials in block order.
+__global__ void __launch_bounds__(256) mfw_colsum_kernel(const float *__restrict__ X, int q,
+                                                         const int32_t *__restrict__ J, long long p,
+                                                         float2 *__restrict__ part, MfwState *st,
+                                                         float2 *__restrict__ H)
+{
+    if (!__ldcg(&st->skip)) return;
+    const int G = gridDim.x, c = threadIdx.x;
+    const bool has = 4 * c < q;
+    const long long per = (p + G - 1) / G;
+    const long long rbeg = (long long)blockIdx.x * per;
+    const long long rend = rbeg + per < p ? rbeg + per : p;
+    float hs[4] = {0.f, 0.f, 0.f, 0.f}, hc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (long long r0 = rbeg; r0 < rend; r0 += 4) {
+        float4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const long long r = r0 + u;
+            v[u] = (has && r < rend) ? __ldcs(reinterpret_cast<const float4 *>(X + (long long)J[r] * q) + c)
+                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float xs[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                float sn, e;
+                two_sum(hs[k], xs[k], sn, e);
+                hs[k] = sn;
+                hc[k] += e;
+            }
+        }
+    }
+    if (has) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float hi, lo;
+            two_sum(hs[k], hc[k], hi, lo);
+            part[(size_t)blockIdx.x * q + 4 * c + k] = make_float2(hi, lo);
+        }
+    }
+    __threadfence();
+    __syncthreads();
+    __shared__ int last;
+    if (threadIdx.x == 0) last = atomicAdd(&st->done, 1u) == (unsigned)(G - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int j = threadIdx.x; j < q; j += blockDim.x) {
+        float2 t = make_float2(0.f, 0.f);
+        for (int b = 0; b < G; ++b) t = dfx_add(t, __ldcg(&part[(size_t)b * q + j]));
+        H[j] = t;
+    }
+    if (threadIdx.x == 0) st->done = 0u;
 }
 
 struct MfwArgs {
@@ -470,6 +611,18 @@ cudaError_t launch_cg(const MfwArgs &a, int G, cudaStream_t st)
 
 int g_setup_attr = 0;
 
+// the reuse fraction in use (SVM_MFW_REUSE overrides it, 0 turns reuse off; for measurements)
+double mfw_reuse_frac()
+{
+    static double v = -1.0;
+    if (v < 0.0) {
+        const char *e = getenv("SVM_MFW_REUSE");
+        v = (e && atof(e) >= 0.0) ? atof(e) : kMfwReuseFrac;
+        if (v < 0.0) v = 0.0;
+    }
+    return v;
+}
+
 float2 split2w(double v)
 {
     const float hi = (float)v;
@@ -477,6 +630,21 @@ float2 split2w(double v)
 }
 
 }  // namespace
+
+cudaError_t newton_mfw_alloc(Work &W)
+{
+    const size_t nwords = (size_t)((W.n + 31) / 32);
+    if (cudaMalloc((void **)&W.mfw_mask, nwords * sizeof(unsigned)) != cudaSuccess) return cudaErrorMemoryAllocation;
+    if (cudaMalloc((void **)&W.mfw_st, sizeof(MfwState)) != cudaSuccess) return cudaErrorMemoryAllocation;
+    cudaError_t e = cudaMemsetAsync(W.mfw_mask, 0, nwords * sizeof(unsigned), W.st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(W.mfw_st, 0, sizeof(MfwState), W.st);
+    return e;
+}
+
+cudaError_t newton_mfw_reset(Work &W)
+{
+    return cudaMemsetAsync(W.mfw_st, 0, sizeof(MfwState), W.st);
+}
 
 // Large free set, 128 < q <= 1024 (dense FP32 X, q % 16 == 0): tensor-core
 // Gram -> preconditioner -> matrix-free CG.  Workspace: the Gram partials in
@@ -487,27 +655,38 @@ cudaError_t launch_newton_mfw(Work &W, const int32_t *J, long long p, double sig
                               bool dots)
 {
     const int q = (int)W.q;
-    if (q <= kCgMaxQ || q > kBcMaxQ || q % 16 != 0 || !W.xf32 || p < 1) return cudaErrorInvalidValue;
+    if (q <= kCgMaxQ || q > kBcMaxQ || q % 16 != 0 || !W.xf32 || p < 1 || !W.mfw_st) return cudaErrorInvalidValue;
     const int nf4 = (q + 127) / 128;
     const int nblk = (q + kWdBlk - 1) / kWdBlk;
-    const int G = W.nsm;
-    const size_t need = (size_t)q * kPb + (size_t)nblk * kWdBlk * kWdBlk + 2 * (size_t)G * q + 3 * (size_t)q + 4;
+    const int G = W.nsm, Gc = 4 * W.nsm;   // CG blocks; column-sum blocks
+    const size_t need = (size_t)q * kPb + (size_t)nblk * kWdBlk * kWdBlk + 2 * (size_t)Gc * q + 3 * (size_t)q + 4;
     if (need > 2 * W.part_len) return cudaErrorInvalidValue;
+    double *info = W.red + 12;
+    MfwState *st = W.mfw_st;
+    const int *skip = &st->skip;
+    // reuse decision and, on a rebuild, the bitmap of this J
+    mfw_decide_kernel<<<W.nsm, 256, 0, W.st>>>(J, p, sigma, W.mfw_mask, st, info, mfw_reuse_frac(), kMfwStaleIt);
+    mfw_mask_clear_kernel<<<W.nsm, 256, 0, W.st>>>(W.mfw_mask, (W.n + 31) / 32, st);
+    mfw_mask_set_kernel<<<2 * W.nsm, 256, 0, W.st>>>(J, p, W.mfw_mask, st);
+    W.nlaunch += 3;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     const int KS = gram_wide_splits(W, p);
     float *cpart = reinterpret_cast<float *>(W.part);
     float2 *hpart = reinterpret_cast<float2 *>(cpart + (size_t)KS * q * q);
     float *Pinv = reinterpret_cast<float *>(W.M);
     float2 *H = reinterpret_cast<float2 *>(Pinv + (size_t)q * q);
-    cudaError_t e = launch_gram_umma_wide(W, J, p, KS, cpart, hpart);
-    if (e == cudaSuccess) e = launch_build_m_tc(W, KS, cpart, hpart, p, sigma, H);
+    e = launch_gram_umma_wide(W, J, p, KS, cpart, hpart, skip);
+    if (e == cudaSuccess) e = launch_build_m_tc(W, KS, cpart, hpart, p, sigma, H, skip);
     if (e != cudaSuccess) return e;
     float *Dg = reinterpret_cast<float *>(W.part);
     float *Linv = Dg + (size_t)q * kPb;
     float2 *cgp = reinterpret_cast<float2 *>(Linv + (size_t)nblk * kWdBlk * kWdBlk);
-    float2 *yg = cgp + (size_t)G * q;
+    float2 *yg = cgp + (size_t)Gc * q;
     float *zg = reinterpret_cast<float *>(yg + q);
     int *fflag = reinterpret_cast<int *>(zg + q);
-    double *info = W.red + 12;
+    mfw_colsum_kernel<<<Gc, 256, 0, W.st>>>((const float *)W.X, q, J, p, cgp, st, H);
+    ++W.nlaunch;
     // the factor and Pinv: every resident block
     const size_t smem = cg_fast_smem(kCgMaxQ);
     if (!g_setup_attr) {
@@ -525,7 +704,7 @@ cudaError_t launch_newton_mfw(Work &W, const int32_t *J, long long p, double sig
         float *Lg = W.Lf;
         int *err = W.err;
         unsigned *bar = W.bar;
-        void *args[] = {&qq, &Mf, &Lg, &Dg, &Linv, &Pinv, &fflag, &bar, &err, &info};
+        void *args[] = {&qq, &Mf, &Lg, &Dg, &Linv, &Pinv, &fflag, &bar, &err, &info, (void *)&skip};
         e = cudaLaunchCooperativeKernel((const void *)newton_mfw_setup_kernel, dim3(occ * W.nsm), dim3(kCgThreads),
                                         args, smem, W.st);
         if (e != cudaSuccess) return e;
@@ -561,7 +740,7 @@ cudaError_t launch_newton_mfw(Work &W, const int32_t *J, long long p, double sig
     case 7: e = launch_cg<7>(a, G, W.st); break;
     default: e = launch_cg<8>(a, G, W.st); break;
     }
-    W.nlaunch += 2;   // + the Gram and M_pre, counted by their launchers
+    W.nlaunch += 2;   // + the others, counted above and by their launchers
     return e;
 }
 

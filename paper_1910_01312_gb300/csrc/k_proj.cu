@@ -349,13 +349,23 @@ __global__ void __launch_bounds__(kTPB, EPT >= 16 ? 1 : 2) proj_kernel(ProjArgs 
             }
         }
         if (A.sums & SF_PSID) {
-            // psi difference term by term: pi(2u - pi) - pib(2ub - pib)
+            // psi difference term by term in the multiplier-stationary form of
+            // k_projdf.cu: pi^2 when free, C (2 (u - lambda y) - C) at C, 0 at 0
             const double pb = A.pi_base[i];
             const long long pbb = __double_as_longlong(pb);
             const int pbc = (pbb == Cbits) ? 2 : ((pbb << 1) == 0 ? 0 : 1);
             const double ub = A.a[i];
-            if (pc == 2 && pbc == 2) acc2 += u - ub;   // 2C(u - ub), factor applied below
-            else if (pc != 0 || pbc != 0) acc1 += pk * (2.0 * u - pk) - pb * (2.0 * ub - pb);
+            if (pc == 2 && pbc == 2) {
+                acc2 += u - ub;             // 2C (u - ub), factor applied below
+                acc3 += pos ? 1.0 : -1.0;   // - 2C (lambda - lambda_b) y_i, below
+            } else if (pc == 1 && pbc == 1) {
+                acc1 = fma(pk - pb, pk + pb, acc1);
+            } else if (pc != 0 || pbc != 0) {
+                const double yl = pos ? lh : -lh, ylb = pos ? lam0 : -lam0;
+                const double f = (pc == 1) ? pk * pk : ((pc == 2) ? C * (2.0 * (u - yl) - C) : 0.0);
+                const double fb = (pbc == 1) ? pb * pb : ((pbc == 2) ? C * (2.0 * (ub - ylb) - C) : 0.0);
+                acc1 += f - fb;
+            }
         }
         if (A.sums & SF_KKT) {
             const double al = A.alpha[i];
@@ -370,8 +380,8 @@ __global__ void __launch_bounds__(kTPB, EPT >= 16 ? 1 : 2) proj_kernel(ProjArgs 
             acc3 += fmax(0.0, 1.0 - marg);
         }
     }
-    if (A.sums & SF_PSID) acc1 = fma(2.0 * C, acc2, acc1);
-    if (!(A.sums & SF_KKT)) acc2 = 0.0;
+    if (A.sums & SF_PSID) acc1 = fma(2.0 * C, acc2, acc1) - 2.0 * C * (lh - lam0) * acc3;
+    if (!(A.sums & SF_KKT)) acc2 = acc3 = 0.0;
     // per-(k, warp) compaction counts
     __shared__ int sh_wc[EPT][kWarps][2];
 #pragma unroll
@@ -516,6 +526,8 @@ cudaError_t proj_setup(Work &W)
 
 cudaError_t launch_project(Work &W, const ProjIn &in, ProjOut *out)
 {
+    // the psi difference takes lam0 as the base point's lambda-hat
+    if ((in.sums & SF_PSID) && (!in.lam0 || !in.pi_base || (in.sums & SF_KKT))) return cudaErrorInvalidValue;
     ProjArgs A;
     A.a = in.a; A.b = in.b; A.c1 = in.c1; A.c2 = in.c2;
     A.y = W.y; A.n = W.n; A.C = W.C; A.sums = in.sums; A.lam0 = in.lam0;

@@ -31,12 +31,19 @@
 // the components whose y_i pi_i differs from a base point, with the weights
 // that update A'pi from the base point's product (the mixed form never
 // recomputes A'pi over all rows).  Sums for the line search (SF_PSID: the
-// psi difference term by term; for a component free at both points as
-// (u - ub)(u + ub) - (lambda^2 - lambda_b^2), the lambda part once for all of
-// them -- formed as two products of size u^2 each, the double-float rounding
-// of ~|u|^2 2^-46 per component would swamp the decrease the Armijo test
-// looks for near a subproblem's solution), the inner stopping test (SF_DPA)
-// and the KKT residual (SF_KKT) come back as double-float pairs.
+// psi difference term by term), the inner stopping test (SF_DPA) and the KKT
+// residual (SF_KKT) come back as double-float pairs.
+//
+// The psi difference.  With u_i - pi_i = lambda y_i for a free component, the
+// sum of pi_i (2 u_i - pi_i) is |u|^2 - |u - pi|^2, and adding -2 lambda y'pi
+// (zero at the root) makes each term stationary in lambda: pi_i^2 when free,
+// C (2 (u_i - lambda y_i) - C) at C, 0 at 0 -- the dual function of the
+// projection, max over lambda of sum_i min_{0<=x_i<=C} [(u_i - x_i)^2 +
+// 2 lambda y_i x_i].  The plain terms pi (2u - pi) are of size |u| |pi| with
+// |u| ~ sigma, so the root's own precision (a shift of lambda by eps moves
+// their sum by 2 lambda eps |J|) and the rounding of 2u - pi left a constant
+// offset in the differences of trial points at large sigma that hid the
+// Armijo decrease; the stationary terms are of size pi^2 and C |u - lambda y|.
 #include <math.h>
 
 #include "internal.cuh"
@@ -460,27 +467,34 @@ __device__ __forceinline__ void projdf_body(const PDArgs &A, const int G, const 
             }
         }
         if (A.sums & SF_PSID) {
-            // psi difference term by term: pi(2u - pi) - pib(2ub - pib); pib from the
-            // base point (y o pi_base), ub = a (the base point's u)
+            // psi difference term by term, each term in its multiplier-stationary
+            // form pi (2u - pi - 2 lambda y) (equal to pi (2u - pi) summed, since
+            // y'pi = 0): pi^2 when free, C (2 (u - lambda y) - C) at C, 0 at 0
             const float2 pb = pos ? bw : dfx_neg(bw);
             const int pbc = (bw.x == 0.f) ? 0 : (dfx_same(pb, Cd) ? 2 : 1);
             if (pc == 2 && pbc == 2) {
                 sm.s[2] = dfx_add(sm.s[2], A.b[i]);   // 2C (u - ub) = 2C c1 b_i, factor applied below
+                sm.nupa += pos ? 1 : -1;               // - 2C (lambda - lambda_b) y_i, below
             } else if (pc == 1 && pbc == 1) {
-                // both free: pi (2u - pi) = u^2 - lambda^2 (u - pi = lambda y), so the
-                // term is (u - ub)(u + ub) less lambda^2 - lambda_b^2, which block 0
-                // subtracts once per such element (counted in nupa; lambda_b = l0):
-                // no cancellation between two products of size |u|^2 per element
-                const float2 du = dfx_add(dfx_mul(A.c1, A.b[i]), A.c2);
-                const float2 ub = A.a[i];
-                sm.s[1] = dfx_add(sm.s[1], dfx_mul(du, dfx_add(dfx_add(ub, ub), du)));
-                ++sm.nupa;
+                sm.s[1] = dfx_add(sm.s[1], dfx_mul(dfx_sub(pk, pb), dfx_add(pk, pb)));
             } else if (pc != 0 || pbc != 0) {
-                const float2 u = u_at(A, i, pos);
-                const float2 ub = A.a[i];
-                const float2 t1 = dfx_mul(pk, dfx_sub(dfx_add(u, u), pk));
-                const float2 t2 = dfx_mul(pb, dfx_sub(dfx_add(ub, ub), pb));
-                sm.s[1] = dfx_add(sm.s[1], dfx_sub(t1, t2));
+                float2 f = make_float2(0.f, 0.f), fb = f;
+                if (pc == 1) {
+                    f = dfx_mul(pk, pk);
+                } else if (pc == 2) {
+                    const float2 e = dfx_sub(d[k], dh);              // y u - lambda
+                    const float2 t = pos ? e : dfx_neg(e);           // u - lambda y
+                    f = dfx_mul(Cd, dfx_sub(dfx_add(t, t), Cd));
+                }
+                if (pbc == 1) {
+                    fb = dfx_mul(pb, pb);
+                } else if (pbc == 2) {
+                    const float2 ub = A.a[i];
+                    const float2 eb = dfx_sub(pos ? ub : dfx_neg(ub), l0);   // y ub - lambda_b
+                    const float2 tb = pos ? eb : dfx_neg(eb);
+                    fb = dfx_mul(Cd, dfx_sub(dfx_add(tb, tb), Cd));
+                }
+                sm.s[1] = dfx_add(sm.s[1], dfx_sub(f, fb));
             }
         }
         if (A.sums & SF_KKT) {
@@ -622,9 +636,11 @@ __device__ __forceinline__ void projdf_body(const PDArgs &A, const int G, const 
             for (int k = 0; k < EPT; ++k) { tj += sh_tot2[k][0]; td += sh_tot2[k][1]; }
             float2 s1 = t.s[1], s2 = t.s[2];
             if (A.sums & SF_PSID) {
-                // + 2C c1 sum_{both at C} b_i - n_free,free (lambda^2 - l0^2), lambda = l0 + dh
-                s1 = dfx_add(s1, dfx_mul(dfx_mul(make_float2(2.f * Cd.x, 2.f * Cd.y), A.c1), s2));
-                s1 = dfx_sub(s1, dfx_mul(dfx_from_ll(t.nupa), dfx_mul(dh, dfx_add(dfx_add(l0, l0), dh))));
+                // + 2C c1 sum_{both at C} b_i - 2C (lambda - lambda_b) sum_{both at C} y_i,
+                // lambda - lambda_b = dh (lambda_b = l0)
+                const float2 c2x = make_float2(2.f * Cd.x, 2.f * Cd.y);
+                s1 = dfx_add(s1, dfx_mul(dfx_mul(c2x, A.c1), s2));
+                s1 = dfx_sub(s1, dfx_mul(dfx_mul(c2x, dh), dfx_from_ll(t.nupa)));
                 s2 = make_float2(0.f, 0.f);
             }
             if (A.sums & SF_KKT) {

@@ -285,8 +285,10 @@ __device__ __forceinline__ void wg_store4(unsigned char *st, int m0, int k, int 
 __global__ void __launch_bounds__(kUmThreads) gram_umma_wide_kernel(const float *__restrict__ X, int q,
                                                                     const int32_t *__restrict__ J, long long p,
                                                                     float *__restrict__ cpart,
-                                                                    float2 *__restrict__ hpart, int *err)
+                                                                    float2 *__restrict__ hpart, int *err,
+                                                                    const int *skip)
 {
+    if (skip && __ldcg(skip)) return;
     extern __shared__ unsigned char um_dyn[];
     __shared__ __align__(8) unsigned long long mbar[2];
     __shared__ unsigned tmem_slot;
@@ -525,7 +527,8 @@ int gram_wide_splits(const Work &W, long long p)
     return ks < 1 ? 1 : (int)ks;
 }
 
-cudaError_t launch_gram_umma_wide(Work &W, const int32_t *J, long long p, int KS, float *cpart, float2 *hpart)
+cudaError_t launch_gram_umma_wide(Work &W, const int32_t *J, long long p, int KS, float *cpart, float2 *hpart,
+                                  const int *skip)
 {
     const int q = (int)W.q;
     if (q <= kUmMaxQ || q > 1024 || q % 16 != 0 || !W.xf32 || KS < 1) return cudaErrorInvalidValue;
@@ -537,7 +540,7 @@ cudaError_t launch_gram_umma_wide(Work &W, const int32_t *J, long long p, int KS
         g_wg_attr = 1;
     }
     gram_umma_wide_kernel<<<dim3((unsigned)wg_pairs(q), (unsigned)KS), kUmThreads, kWgSmem, W.st>>>(
-        (const float *)W.X, q, J, p, cpart, hpart, W.err);
+        (const float *)W.X, q, J, p, cpart, hpart, W.err, skip);
     ++W.nlaunch;
     return cudaGetLastError();
 }

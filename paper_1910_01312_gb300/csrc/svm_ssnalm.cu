@@ -17,7 +17,9 @@
 //    absolute-sum scale of A'pi (the roundoff level of g); at most 50
 //    Newton steps; a failed line search ends the subproblem.
 //  - Armijo: mu = 1e-4, delta = 0.5, at most 40 trials; psi differences are
-//    summed term by term.
+//    summed term by term (the oracle's terms pi (2u - pi); here each less
+//    2 lambda y pi, which sums to zero at the root but makes the terms
+//    stationary in lambda and of size pi^2: see k_projdf.cu).
 //  - z = A v is recomputed at the start of every subproblem.
 #include <cuda_runtime.h>
 #include <math.h>
@@ -163,7 +165,7 @@ extern "C" const char *svm_ssnalm_last_error(const svm_ssnalm_t *h)
 static void free_work(Work &W)
 {
     void *ptrs[] = {W.alpha, W.z, W.dz, W.qa, W.tmpn, W.zf, W.dzf, W.qaf, W.alphaw, W.dw, W.dwa, W.atpa,
-                    W.atpa2, W.mf_st, W.mf_pinv, W.mf_counter, W.v, W.vt, W.dv, W.g, W.atp, W.atp2, W.h, W.w, W.tmpq, W.M, W.Lf, W.Mf, W.part, W.cnt,
+                    W.atpa2, W.mf_st, W.mf_pinv, W.mf_counter, W.mfw_mask, W.mfw_st, W.v, W.vt, W.dv, W.g, W.atp, W.atp2, W.h, W.w, W.tmpq, W.M, W.Lf, W.Mf, W.part, W.cnt,
                     W.bar, W.rm_counter, W.err, W.pout, W.red, W.X_own, W.y_own, W.csc_ptr, W.csc_row,
                     W.csc_val, W.task_beg, W.col_task, W.task_part, W.csr_tn, W.csr_q, W.csr_cg,
                     W.csr_ptr_own, W.csr_idx_own, W.csr_val_own, W.jcsc_ptr, W.jtot, W.jcol_task, W.jtask_beg,
@@ -346,6 +348,7 @@ static svm_status create_impl(svm_ssnalm_t **out, const svm_problem *prob, const
               dalloc(&W.pb[b].wpi, n) ||
               dalloc(&W.pb[b].J, n) || dalloc(&W.pb[b].S, n);
     if (!bad && W.df && q <= 128) bad = newton_mf_alloc(W) != cudaSuccess;
+    if (!bad && W.df && q > 128 && q <= 1024 && q % 16 == 0) bad = newton_mfw_alloc(W) != cudaSuccess;
     if (bad) return fail(SVM_ERR_OOM, "device workspace allocation failed");
     if (cudaMallocHost(&W.h_pout, 4 * sizeof(ProjOut)) != cudaSuccess ||
         cudaMallocHost(&W.h_red, 16 * sizeof(double)) != cudaSuccess ||
@@ -1058,6 +1061,12 @@ static svm_status run_begin(Run &r, svm_ssnalm *h, const double *alpha0, svm_res
     r.res = res;
     res->form = solve_form(h->W);
     h->err.clear();
+    // every solve builds its own Newton preconditioners: results never depend on
+    // what the handle solved before
+    if (h->W.mfw_st && newton_mfw_reset(h->W) != cudaSuccess) {
+        h->err = "cudaMemsetAsync failed";
+        return SVM_ERR_CUDA;
+    }
     if (h->npos == 0 || h->npos == h->W.n) return run_degenerate(r);
     r.ph = RP_INIT;
     return SVM_OK;

@@ -100,6 +100,31 @@ def test_batch_uneven_classes_wide_features():
     assert stats["host_syncs"] < sum(r["inner_iters_total"] for r in rs)
 
 
+def test_batch_wide_features_large_free_sets():
+    """Free sets above 2e4 rows at q = 784: the Newton steps run matrix-free
+    with the tensor-core preconditioner (kept between steps whose free sets
+    barely differ).  Every solve builds its own preconditioners, so the batch
+    stays bit-identical to single solves -- also on a handle that solved
+    before (the second batch call) -- and each alpha passes the oracle's
+    R_KKT."""
+    X, Y, Cs = datagen.ovr_path(3, n=60000, q=784, n_classes=2, n_C=2, C_lo=-1.0, C_hi=0.0)
+    Xd = dev(X)
+    s, st, rs, A, W = batch(Xd, Y, Cs, P.PREC_MIXED)
+    assert st == P.OK, [r["status"] for r in rs]
+    A2 = torch.zeros((len(Cs), X.shape[0]), dtype=torch.float64, device="cuda")
+    W2 = torch.zeros((len(Cs), X.shape[1]), dtype=torch.float64, device="cuda")
+    st2, rs2 = s.solve_batch(dev(Y), Cs, A2, W2)
+    s.close()
+    assert st2 == P.OK
+    np.testing.assert_array_equal(A2.cpu().numpy(), A)
+    assert max(r["n_free"] for r in rs) > 20000
+    for b in range(len(Cs)):
+        r1, a1, _ = single(Xd, Y[b], Cs[b], P.PREC_MIXED)
+        np.testing.assert_array_equal(A[b], a1)
+        assert rs[b]["kkt"] <= 1e-6
+        assert oracle.kkt(X, Y[b], Cs[b], A[b]) <= 1e-6
+
+
 def test_batch_degenerate_member_and_invalid_labels():
     X, Y, Cs = datagen.ovr_path(2, n=1500, q=32, n_classes=2, n_C=2, C_lo=-1.0, C_hi=0.0)
     Y = np.concatenate([Y, np.ones((1, Y.shape[1]), np.int8)])

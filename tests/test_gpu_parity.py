@@ -206,6 +206,35 @@ def test_newton_direction(prec, gscale, dtype, n, q, frac):
         assert np.linalg.norm(host(dv) - dv_r) <= r * 1.01 + 1e-12 * np.linalg.norm(dv_r)
 
 
+@pytest.mark.parametrize("q,swap", [(784, 100), (784, 0), (256, 150), (784, 2000)])
+def test_newton_wide_consecutive_steps(q, swap):
+    """Consecutive Newton steps at 128 < q <= 1024 on one handle: the second
+    free set differs from the first in `swap` rows (under 1 % of p: the
+    preconditioner built for the first is kept, h comes from the column-sum
+    pass; 2000 rows: it is rebuilt).  Each direction must solve its own
+    system to CG's tolerance (1e-10 |g|), checked against the FP64 matrix."""
+    n, frac, sigma = 60000, 0.5, 2.5
+    X, y = datagen.small(n, q, seed=q + swap, dtype=np.float32)
+    rng = np.random.default_rng(q + swap)
+    J1 = np.sort(rng.choice(n, size=int(frac * n), replace=False))
+    out = np.setdiff1d(np.arange(n), J1)
+    J2 = J1.copy()
+    if swap:
+        J2 = np.sort(np.concatenate([np.delete(J1, rng.choice(J1.size, size=swap, replace=False)),
+                                     rng.choice(out, size=swap, replace=False)]))
+    s, _, _ = make(X, y, precision=P.PREC_MIXED)
+    A = X.astype(np.float64) * y[:, None]
+    for J in (J1, J2, J2):
+        g = rng.normal(size=q)
+        dv = torch.empty(q, dtype=torch.float64, device="cuda")
+        s.newton(dev(J.astype(np.int32)), J.size, sigma, dev(g), dv)
+        AJ = A[J]
+        h = AJ.T @ y[J].astype(np.float64)
+        M = np.eye(q) + sigma * (AJ.T @ AJ - np.outer(h, h) / J.size)
+        r = np.linalg.norm(M @ host(dv) + g)
+        assert r <= 1e-8 * np.linalg.norm(g), r / np.linalg.norm(g)
+
+
 @pytest.mark.parametrize("n,q,p,order", [(5000, 128, 3000, "sorted"), (20000, 64, 20000, "sorted"),
                                          (300000, 128, 150000, "random"), (1000, 16, 1, "sorted"),
                                          (700, 112, 333, "random"), (2000, 128, 0, "sorted"),
