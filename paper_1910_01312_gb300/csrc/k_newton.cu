@@ -847,15 +847,19 @@ static long long mf_min_p()
     }
     return v;
 }
-// The same at 128 < q <= 1024 (k_newton_wide.cu): the exact Gram's cost grows
-// as p q^2, the matrix-free one as p q per CG step plus a fixed ~q^3 set-up.
-constexpr long long kMfwMinP = 20000;
+// The same at 128 < q <= 1024 (k_newton_wide.cu) for every free set: at q = 784
+// (opbench newton, n = 2e5) p = 1514: 0.42 ms against 1.50 ms for the exact
+// Gram and newton_bchol_kernel (whose CG applies the factor by triangular
+// solves in one block, ~0.1 ms a CG step); p = 5e3: 0.50 vs 2.01; p = 2e4:
+// 0.52 vs 4.23; p = 1e5: 3.1 vs 16.0.  newton_bchol_kernel remains for q % 16
+// != 0.  SVM_MFW_MIN_P sets a lower bound on p for measurements.
+constexpr long long kMfwMinP = 0;
 static long long mfw_min_p()
 {
     static long long v = -1;
     if (v < 0) {
         const char *e = getenv("SVM_MFW_MIN_P");
-        v = (e && atoll(e) > 0) ? atoll(e) : kMfwMinP;
+        v = (e && atoll(e) >= 0) ? atoll(e) : kMfwMinP;
     }
     return v;
 }
@@ -1502,7 +1506,7 @@ cudaError_t launch_newton(Work &W, const int32_t *J, long long p_host, const lon
     const bool mixed = W.precision == 1 && W.xf32;
     if (mixed && W.mf_st && q <= kCgMaxQ && q % 4 == 0 && p_host > mf_min_p())
         return launch_newton_mf(W, J, p_host, sigma, g, dv, dots);
-    if (mixed && q > kCgMaxQ && q <= kBcMaxQ && q % 16 == 0 && p_host > mfw_min_p())
+    if (mixed && W.mfw_st && q > kCgMaxQ && q <= kBcMaxQ && q % 16 == 0 && p_host > mfw_min_p())
         return launch_newton_mfw(W, J, p_host, sigma, g, dv, dots);
     // double-float partials are summed in one chain per element: one split per SM
     if (mixed && ks > W.nsm) ks = W.nsm;

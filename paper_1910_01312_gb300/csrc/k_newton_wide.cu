@@ -252,8 +252,8 @@ __global__ void __launch_bounds__(256) mfw_decide_kernel(const int32_t *__restri
     __threadfence();
     const long long added = (long long)atomicAdd(&st->added, 0u);
     const long long removed = st->p - (p - added);
-    const bool stale = st->valid == 0 || st->sigma != sigma || (double)(added + removed) > frac * (double)p ||
-                       !(info[0] <= (double)stale_it);
+    const bool stale = st->valid == 0 || st->sigma != sigma || !(frac > 0.0) ||
+                       (double)(added + removed) > frac * (double)p || !(info[0] <= (double)stale_it);
     st->skip = stale ? 0 : 1;
     if (stale) {
         st->valid = 1;
@@ -332,10 +332,16 @@ __global__ void __launch_bounds__(256) mfw_colsum_kernel(const float *__restrict
     __syncthreads();
     if (!last) return;
     __threadfence();
-    for (int j = threadIdx.x; j < q; j += blockDim.x) {
+    // eight lanes per column sum interleaved eighths of the partials, combined
+    // by shuffles in a fixed order (a warp-uniform trip count)
+    const int lane = threadIdx.x & 31, sub = lane & 7;
+    for (int j0 = (threadIdx.x >> 3); j0 < ((q + 3) & ~3); j0 += blockDim.x >> 3) {
+        const int j = j0 < q ? j0 : q - 1;
         float2 t = make_float2(0.f, 0.f);
-        for (int b = 0; b < G; ++b) t = dfx_add(t, __ldcg(&part[(size_t)b * q + j]));
-        H[j] = t;
+        for (int b = sub; b < G; b += 8) t = dfx_add(t, __ldcg(&part[(size_t)b * q + j]));
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) t = dfx_add(t, shfl_xor_f2(t, o));
+        if (sub == 0 && j0 < q) H[j] = t;
     }
     if (threadIdx.x == 0) st->done = 0u;
 }
@@ -685,7 +691,9 @@ cudaError_t launch_newton_mfw(Work &W, const int32_t *J, long long p, double sig
     float2 *yg = cgp + (size_t)Gc * q;
     float *zg = reinterpret_cast<float *>(yg + q);
     int *fflag = reinterpret_cast<int *>(zg + q);
-    mfw_colsum_kernel<<<Gc, 256, 0, W.st>>>((const float *)W.X, q, J, p, cgp, st, H);
+    // column sums: about 64 rows per block, at most 4 blocks per SM
+    const long long gcs = (p + 63) / 64 < Gc ? (p + 63) / 64 : Gc;
+    mfw_colsum_kernel<<<(unsigned)gcs, 256, 0, W.st>>>((const float *)W.X, q, J, p, cgp, st, H);
     ++W.nlaunch;
     // the factor and Pinv: every resident block
     const size_t smem = cg_fast_smem(kCgMaxQ);

@@ -167,13 +167,14 @@ def test_projection_flat_segment(kernel):
 @pytest.mark.parametrize("dtype,n,q,frac", [(np.float64, 400, 50, 0.3), (np.float32, 3000, 128, 0.2),
                                             (np.float32, 5000, 33, 0.01), (np.float64, 300, 150, 0.9),
                                             (np.float32, 20000, 128, 0.5),
-                                            # q > 128: CG preconditioned by the blocked FP32 Cholesky factor (mixed form)
+                                            # q > 128 (mixed form): q % 16 == 0 matrix-free CG preconditioned by the
+                                            # factor of the tcgen05 Gram; q = 200 CG on the exact matrix with the
+                                            # blocked FP32 Cholesky factor
                                             (np.float32, 6000, 784, 0.2), (np.float32, 3000, 256, 0.05),
                                             (np.float32, 2000, 200, 0.6),
                                             # p = 210,000: the matrix-free large-free-set solve (mixed form)
                                             (np.float32, 420000, 128, 0.5),
-                                            # 128 < q <= 1024, p > 2e4: matrix-free CG preconditioned by the
-                                            # factor of the tcgen05 Gram (mixed form)
+                                            # 128 < q <= 1024 at large p
                                             (np.float32, 60000, 784, 0.5), (np.float32, 50000, 144, 0.45),
                                             (np.float32, 30000, 1024, 0.8), (np.float32, 41000, 400, 0.9)])
 def test_newton_direction(prec, gscale, dtype, n, q, frac):
