@@ -10,8 +10,9 @@ The line also carries the plain FP64 form's time on the same problem, the
 end-to-end time through the C ABI with host buffers, the FP64 oracle solving
 the same full-size problem on the host (cpu_baseline: the OpenMP build on all
 host cores, and the single-threaded build), and a batched leg: 160 SVMs
-sharing one X (ten one-vs-rest classes x sixteen C values) solved in lockstep
-by svm_ssnalm_solve_batch against the same problems solved one by one.
+sharing one X (ten one-vs-rest classes x sixteen C values on the dense
+n = 200,000 x q = 784 one-vs-rest workload) solved in lockstep by
+svm_ssnalm_solve_batch against the same problems solved one by one.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -38,7 +39,7 @@ METRIC = "time-to-KKT<=1e-6 per SVM solve"
 N_FULL = 1_000_000
 N_REF_WARM = 50_000        # warm-up solves of the reference arm run on a 50,000-row sample
 REF_BUDGET_S = 150.0       # the reference arm stops adding timed solves after this long
-BATCH_N, BATCH_Q, BATCH_CLASSES, BATCH_NC = 100_000, 128, 10, 16   # the batched (one-vs-rest x C path) leg
+BATCH_N, BATCH_Q, BATCH_CLASSES, BATCH_NC = 200_000, 784, 10, 16   # the batched (one-vs-rest x C path) leg
 
 
 def _peaks():

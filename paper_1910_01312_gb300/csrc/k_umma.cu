@@ -234,17 +234,19 @@ __global__ void __launch_bounds__(kUmThreads) gram_umma_kernel(const float *__re
 // features 256 cj .. 256 cj + 255 (N <= 256 columns, B) for each chunk cj that
 // reaches the diagonal of row tile ti -- and blockIdx.y splits the rows of J
 // (split-K).  A stage gathers 32 rows: B's features always, A's only when they
-// lie outside B's range (otherwise A's descriptor points into B's panel).  A
-// thread loads 16 bytes (4 features of one row; 8 lanes cover 128 contiguous
-// bytes of a row) and stores the 4 values in a rotated order, so that the 32
-// lanes of a warp write 32 distinct banks of the core-matrix layout.  The
+// lie outside B's range (otherwise A's descriptor points into B's panel).  The
+// panels are K-major in the 128-byte swizzled layout (32 rows = 128 bytes of K
+// per feature).  A thread loads 16 bytes (4 features of one row) and stores
+// the 4 values at offsets fixed for the thread, the 32 lanes of a warp on 32
+// distinct banks; the rows of the next stage load while a stage is stored and
+// its MMAs issued.  The
 // pair whose chunk holds A's features also sums A's columns (h).  Each
 // feature is gathered by several pairs (about 6 x the rows' bytes at q =
 // 784); products are TF32, sums FP32 -- the preconditioner's Gram, as above.
 constexpr int kWgK = 32;                                 // gathered rows per stage
 constexpr int kWgBN = 256;                               // B features (MMA N, max)
 constexpr int kWgAM = 128;                               // A features (MMA M)
-constexpr unsigned kWgSbo = (kWgK / 4) * 128;            // next 8 features: after K/4 core matrices
+constexpr unsigned kWgSbo = 8 * kWgK * 4;                // next 8 features: one 1024-byte swizzle atom
 constexpr int kWgBBytes = kWgBN * kWgK * 4;              // 32 KB
 constexpr int kWgABytes = kWgAM * kWgK * 4;              // 16 KB
 constexpr int kWgStageBytes = kWgBBytes + kWgABytes;
@@ -264,25 +266,34 @@ __host__ __device__ inline int wg_pairs(int q)
     return n;
 }
 
-__device__ __forceinline__ float f4_at(const float4 &v, int j)
+// Shared-memory descriptor of a K-major operand in the 128-byte swizzled
+// layout: each M/N row holds its 32 K values (128 bytes) with 16-byte chunk c
+// stored at chunk c ^ (row & 7), eight rows form a 1024-byte atom, atoms SBO
+// bytes apart (layout type 2 at bits 61-63; the leading offset is unused for
+// this layout and set to 1).  A K step of 8 TF32 values advances the start
+// address by 32 bytes inside the atom.
+__device__ __forceinline__ unsigned long long umma_desc_sw128(unsigned saddr, unsigned sbo)
 {
-    return j == 0 ? v.x : (j == 1 ? v.y : (j == 2 ? v.z : v.w));
+    unsigned long long d = 0;
+    d |= (unsigned long long)((saddr >> 4) & 0x3FFFu);
+    d |= 1ull << 16;
+    d |= (unsigned long long)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= 1ull << 46;
+    d |= 2ull << 61;
+    return d;
 }
 
-// 32 rows x 4 features of one lane into the K-major core-matrix panel at st
-// (feature-local index m0 + j, row k), in the rotated order
-__device__ __forceinline__ void wg_store4(unsigned char *st, int m0, int k, int rot, const float4 &v)
+// the 4 values of one lane (4 consecutive features of one gathered row) into
+// the swizzled panel at st, at the lane's fixed offsets
+__device__ __forceinline__ void wg_store4(unsigned char *st, const unsigned (&soff)[4], const float4 &v)
 {
-#pragma unroll
-    for (int jj = 0; jj < 4; ++jj) {
-        const int j = (jj + rot) & 3, m = m0 + j;
-        const unsigned off = (unsigned)(m >> 3) * kWgSbo + (unsigned)(k >> 2) * 128u + (unsigned)(m & 7) * 16u +
-                             (unsigned)(k & 3) * 4u;
-        *reinterpret_cast<float *>(st + off) = f4_at(v, j);
-    }
+    *reinterpret_cast<float *>(st + soff[0]) = v.x;
+    *reinterpret_cast<float *>(st + soff[1]) = v.y;
+    *reinterpret_cast<float *>(st + soff[2]) = v.z;
+    *reinterpret_cast<float *>(st + soff[3]) = v.w;
 }
 
-__global__ void __launch_bounds__(kUmThreads) gram_umma_wide_kernel(const float *__restrict__ X, int q,
+__global__ void __launch_bounds__(kUmThreads, 2) gram_umma_wide_kernel(const float *__restrict__ X, int q,
                                                                     const int32_t *__restrict__ J, long long p,
                                                                     float *__restrict__ cpart,
                                                                     float2 *__restrict__ hpart, int *err,
@@ -292,8 +303,7 @@ __global__ void __launch_bounds__(kUmThreads) gram_umma_wide_kernel(const float 
     extern __shared__ unsigned char um_dyn[];
     __shared__ __align__(8) unsigned long long mbar[2];
     __shared__ unsigned tmem_slot;
-    __shared__ int jrow[kWgK];
-    __shared__ float2 hsm[kUmThreads / 32][kWgAM];
+    __shared__ float2 hsm[2][kWgAM];
     unsigned char *base =
         reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(um_dyn) + 1023) & ~(uintptr_t)1023);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -330,45 +340,63 @@ __global__ void __launch_bounds__(kUmThreads) gram_umma_wide_kernel(const float 
     tc_fence_after();
     const unsigned tmem = tmem_slot;
     const unsigned idesc = umma_idesc_tf32(kWgAM, nb);
-    const int kr = 4 * warp + (lane & 3);    // the stage row this lane loads
-    const int c4 = lane >> 2;                // its 4-feature group within 32 features
-    const int rot = (lane >> 3) & 3;
+    // lane -> data: lane bits 0-3 give the stage row within the warp's half of
+    // the stage (rows 16 (w & 1) .. + 15), lane bit 4 and w >> 1 the lane's
+    // 4-feature group c4 within each 32 features (two lanes cover 32
+    // contiguous bytes of a row).  Feature m = 32 g + 4 c4 + j of row k sits at
+    // g * 4096 + soff[j]; for a fixed j the 32 lanes of a warp hit 32 distinct
+    // banks: (k >> 2) ^ (m & 7) takes 8 values, k & 3 four.
+    const int kr = 16 * (warp & 1) + (lane & 15);
+    const int c4 = 2 * (warp >> 1) + (lane >> 4);
+    unsigned soff[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int mj = 4 * (c4 & 1) + j;
+        soff[j] = (unsigned)(c4 >> 1) * kWgSbo + (unsigned)mj * 128u + ((unsigned)((kr >> 2) ^ mj) << 4) +
+                  (unsigned)(kr & 3) * 4u;
+    }
     const int gA = (ti & 1) * 4;             // A's first 32-feature group inside B
 
     float hs[16], hc[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) hs[i] = hc[i] = 0.f;
-    int ok = 1;
-    for (int it = 0; it < nst; ++it) {
-        const int b = it & 1;
-        if (it >= 2 && ok) ok = mbar_wait_bounded(&mbar[b], (unsigned)((it - 2) >> 1) & 1u, err) ? 1 : 0;
-        const long long rb = r0 + (long long)it * kWgK;
-        if (threadIdx.x < kWgK) jrow[threadIdx.x] = (rb + threadIdx.x < r1) ? J[rb + threadIdx.x] : -1;
-        if (!__syncthreads_and(ok)) { ok = 0; break; }
-        const int jr = jrow[kr];
+    // software pipeline: the rows of stage it + 1 load into registers while
+    // stage it is stored and its MMAs issued; row indices two stages ahead
+    auto row_of = [&](int st) -> int {
+        const long long r = r0 + (long long)st * kWgK + kr;
+        return (st < nst && r < r1) ? __ldg(&J[r]) : -1;
+    };
+    float4 vb[kWgBN / 32], va[kWgAM / 32];
+    auto load_rows = [&](int jr) {
         const float *row = X + (long long)(jr < 0 ? 0 : jr) * q;
-        float4 vb[kWgBN / 32];
 #pragma unroll
         for (int g = 0; g < kWgBN / 32; ++g) {
             const int m = b0 + 32 * g + 4 * c4;
-            vb[g] = (jr >= 0 && m < q) ? __ldcs(reinterpret_cast<const float4 *>(row + m))
+            vb[g] = (jr >= 0 && m < q) ? __ldcg(reinterpret_cast<const float4 *>(row + m))
                                        : make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        float4 va[kWgAM / 32];
         if (!inside) {
 #pragma unroll
             for (int g = 0; g < kWgAM / 32; ++g) {
                 const int m = a0 + 32 * g + 4 * c4;
-                va[g] = (jr >= 0 && m < q) ? __ldcs(reinterpret_cast<const float4 *>(row + m))
+                va[g] = (jr >= 0 && m < q) ? __ldcg(reinterpret_cast<const float4 *>(row + m))
                                            : make_float4(0.f, 0.f, 0.f, 0.f);
             }
         }
+    };
+    int jnext = row_of(1);
+    load_rows(row_of(0));
+    int ok = 1;
+    for (int it = 0; it < nst; ++it) {
+        const int b = it & 1;
+        if (it >= 2 && ok) ok = mbar_wait_bounded(&mbar[b], (unsigned)((it - 2) >> 1) & 1u, err) ? 1 : 0;
+        if (!__syncthreads_and(ok)) { ok = 0; break; }
         unsigned char *st = base + b * kWgStageBytes;
 #pragma unroll
-        for (int g = 0; g < kWgBN / 32; ++g) wg_store4(st, 32 * g + 4 * c4, kr, rot, vb[g]);
+        for (int g = 0; g < kWgBN / 32; ++g) wg_store4(st + g * 4 * kWgSbo, soff, vb[g]);
         if (!inside) {
 #pragma unroll
-            for (int g = 0; g < kWgAM / 32; ++g) wg_store4(st + kWgBBytes, 32 * g + 4 * c4, kr, rot, va[g]);
+            for (int g = 0; g < kWgAM / 32; ++g) wg_store4(st + kWgBBytes + g * 4 * kWgSbo, soff, va[g]);
         } else {
 #pragma unroll
             for (int gg = 0; gg < kWgAM / 32; ++gg) {
@@ -383,6 +411,10 @@ __global__ void __launch_bounds__(kUmThreads) gram_umma_wide_kernel(const float 
                 }
             }
         }
+        // the next stage's rows (this stage's values are in shared memory now)
+        const int jn2 = row_of(it + 2);
+        load_rows(jnext);
+        jnext = jn2;
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -391,8 +423,8 @@ __global__ void __launch_bounds__(kUmThreads) gram_umma_wide_kernel(const float 
             const unsigned sa = inside ? sb + (unsigned)(ti & 1) * 16u * kWgSbo : sb + (unsigned)kWgBBytes;
 #pragma unroll
             for (int s = 0; s < kWgK / 8; ++s) {
-                const unsigned long long ad = umma_desc(sa + s * 256u, 128u, kWgSbo);
-                const unsigned long long bd = umma_desc(sb + s * 256u, 128u, kWgSbo);
+                const unsigned long long ad = umma_desc_sw128(sa + s * 32u, kWgSbo);
+                const unsigned long long bd = umma_desc_sw128(sb + s * 32u, kWgSbo);
                 tc_mma_tf32(tmem, ad, bd, idesc, (it > 0 || s > 0) ? 1 : 0);
             }
             tc_commit(&mbar[b]);
@@ -427,25 +459,22 @@ __global__ void __launch_bounds__(kUmThreads) gram_umma_wide_kernel(const float 
         }
     }
     if (inside) {
-        // A's column sums: the four lanes of a 4-feature group (lane & 3 = the
-        // row), then the eight warps in order
+        // A's column sums: the 16 lanes of a 4-feature group (lane bits 0-3 =
+        // the row), then the two halves of the stage rows in order
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
             float hi, lo;
             two_sum(hs[i], hc[i], hi, lo);
             float2 v = make_float2(hi, lo);
-            v = dfx_add(v, shfl_xor_f2(v, 1));
-            v = dfx_add(v, shfl_xor_f2(v, 2));
-            if ((lane & 3) == 0) hsm[warp][32 * (i >> 2) + 4 * c4 + (i & 3)] = v;
+#pragma unroll
+            for (int o = 1; o < 16; o <<= 1) v = dfx_add(v, shfl_xor_f2(v, o));
+            if ((lane & 15) == 0) hsm[warp & 1][32 * (i >> 2) + 4 * c4 + (i & 3)] = v;
         }
     }
     tc_fence_before();
     __syncthreads();
-    if (inside && threadIdx.x < kWgAM && a0 + (int)threadIdx.x < q) {
-        float2 v = make_float2(0.f, 0.f);
-        for (int w = 0; w < kUmThreads / 32; ++w) v = dfx_add(v, hsm[w][threadIdx.x]);
-        hpart[(size_t)ks * q + a0 + threadIdx.x] = v;
-    }
+    if (inside && threadIdx.x < kWgAM && a0 + (int)threadIdx.x < q)
+        hpart[(size_t)ks * q + a0 + threadIdx.x] = dfx_add(hsm[0][threadIdx.x], hsm[1][threadIdx.x]);
     if (warp == 0) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kWgCols) : "memory");

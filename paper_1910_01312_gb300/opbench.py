@@ -14,7 +14,8 @@ eq. (1.5): B = Diag(y) X, c = -e, a = y, l = 0, u = C, through
 svm_gqp_solve), ``gqp`` (a general unified QP on the same X: signed non-unit
 a, per-component boxes, d != 0), ``svr`` (the linear SVR dual of eq. (1.4) on
 y = X w* + noise, 2n variables), ``nystrom`` (--iters k-means iterations and
-the features for --nfreq landmarks).  The data are the two-Gaussian workload of
+the features for --nfreq landmarks), ``ovr`` (the --problems of the
+one-vs-rest x C-path workload datagen.ovr_path at --n x --q, each solved once).  The data are the two-Gaussian workload of
 ``datagen.gauss1m`` at the requested n and q, or with ``--layout csr`` the
 text-like sparse workload of ``datagen.sparse_text`` (--nnz-row entries per
 row).  Prints one JSON line with the mean time per call from CUDA events on
@@ -28,10 +29,33 @@ import json
 import numpy as np
 
 
+def run_ovr(args, torch, datagen, B, stream):
+    """Problems of the one-vs-rest x C-path workload (datagen.ovr_path, seed 0,
+    ten classes x sixteen C values, at --n x --q), each solved once from
+    alpha = 0 on its own handle; one JSON line per problem (CUDA-event time)."""
+    X, Y, Cs = datagen.ovr_path(0, n=args.n, q=args.q, n_classes=10, n_C=16)
+    Xd = torch.from_numpy(X).cuda()
+    Yd = torch.from_numpy(Y).cuda()
+    a = torch.zeros(args.n, dtype=torch.float64, device="cuda")
+    w = torch.zeros(args.q, dtype=torch.float64, device="cuda")
+    for b in (int(t) for t in args.problems.split(",")):
+        s = B.Solver(Xd, Yd[b], C_=float(Cs[b]), tol=1e-6, precision=B.PREC_MIXED, stream=stream.cuda_stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = s.solve(a, w)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        print(json.dumps({"op": "ovr", "problem": b, "C": float(Cs[b]), "n": args.n, "q": args.q,
+                          "ms": e0.elapsed_time(e1), "outer": r["outer_iters"], "inner": r["inner_iters_total"],
+                          "n_free": r["n_free"], "kkt": r["kkt"], "status": r["status"]}), flush=True)
+        s.close()
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--op", default="solve", choices=["solve", "matvec", "rmatvec", "project", "newton", "rff",
-                                                      "gqp_csvc", "gqp", "svr", "nystrom"])
+                                                      "gqp_csvc", "gqp", "svr", "nystrom", "ovr"])
+    ap.add_argument("--problems", default="3,35,70,108", help="ovr: the one-vs-rest x C problems to solve")
     ap.add_argument("--iters", type=int, default=10)
     ap.add_argument("--nfreq", type=int, default=512)
     ap.add_argument("--n", type=int, default=400_000)
@@ -51,6 +75,8 @@ def main(argv=None):
 
     B.load()
     stream = torch.cuda.current_stream()
+    if args.op == "ovr":
+        return run_ovr(args, torch, datagen, B, stream)
     prec = B.PREC_MIXED if args.precision == "mixed" else B.PREC_PLAIN_FP64
     if args.layout == "csr":
         ip, ix, vals, y, C = datagen.sparse_text(0, n=args.n, q=args.q, nnz_row=args.nnz_row)
