@@ -281,6 +281,124 @@ __global__ void __launch_bounds__(NCH * VW >= 8 ? 256 : 1024) rmatvec_mx_part_ke
     }
 }
 
+// The same for 128 < q <= 1024 (q % 4 == 0): a lane holding all q columns'
+// sums needs ~3q/32 registers, which leaves one block of eight warps per SM
+// with two rows in flight each.  Here the columns are cut into NSL slices of
+// 256 (two float4 per lane) and the block's 16 warps are 16/NSL row groups x
+// NSL slices: each warp streams its row group's 32-row chunks of the block's
+// share for its slice, R rows in flight, so every byte of a row is read once
+// per block.  Block partials and the last-block reduction as above.
+constexpr int kRcThreads = 512;
+template <int NSL>
+__global__ void __launch_bounds__(kRcThreads, 1) rmatvec_mx_cols_kernel(
+    const float *__restrict__ X, long long n, int q, const float2 *__restrict__ wc, const float *__restrict__ wa,
+    const int32_t *__restrict__ idx, const long long *__restrict__ cnt_dev, float *__restrict__ part,
+    unsigned *__restrict__ counter, const double *__restrict__ base, const float *__restrict__ abase,
+    double *__restrict__ out, float *__restrict__ aout, double *__restrict__ red, int slot, const GradOut go)
+{
+    constexpr int NRG = (kRcThreads / 32) / NSL;
+    constexpr int R = 8;
+    const long long cnt = idx ? *cnt_dev : n;
+    const int G = gridDim.x;
+    const long long per = (cnt + G - 1) / G;
+    const long long r_beg = (long long)blockIdx.x * per;
+    const long long r_end = r_beg + per < cnt ? r_beg + per : cnt;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int sl = warp % NSL, rg = warp / NSL;
+    const int nf4 = q / 4;
+    float s[8], c[8], ab[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) { s[k] = 0.f; c[k] = 0.f; ab[k] = 0.f; }
+    for (long long c0 = r_beg + (long long)rg * 32; c0 < r_end; c0 += (long long)NRG * 32) {
+        const long long rl = c0 + lane;
+        int myi = -1;
+        float2 myw = make_float2(0.f, 0.f);
+        float mya = 0.f;
+        if (rl < r_end) {
+            myi = idx ? idx[rl] : (int)rl;
+            myw = wc[myi];
+            mya = wa ? wa[myi] : fabsf(myw.x);
+        }
+        const int here = (int)((r_end - c0) < 32 ? (r_end - c0) : 32);
+        for (int u0 = 0; u0 < here; u0 += R) {
+            int ii[R];
+            float2 w[R];
+            float wab[R];
+#pragma unroll
+            for (int u = 0; u < R; ++u) {
+                const int src = (u0 + u) & 31;
+                ii[u] = __shfl_sync(0xffffffffu, myi, src);
+                w[u].x = __shfl_sync(0xffffffffu, myw.x, src);
+                w[u].y = __shfl_sync(0xffffffffu, myw.y, src);
+                wab[u] = __shfl_sync(0xffffffffu, mya, src);
+                if (u0 + u >= here) ii[u] = -1;
+            }
+            float4 xv[R][2];
+#pragma unroll
+            for (int u = 0; u < R; ++u)
+#pragma unroll
+                for (int f = 0; f < 2; ++f) {
+                    const int c4 = sl * 64 + 32 * f + lane;
+                    xv[u][f] = (ii[u] >= 0 && c4 < nf4)
+                                   ? __ldcs(reinterpret_cast<const float4 *>(X + (long long)ii[u] * q) + c4)
+                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+#pragma unroll
+            for (int u = 0; u < R; ++u)
+#pragma unroll
+                for (int f = 0; f < 2; ++f) {
+                    const float xs[4] = {xv[u][f].x, xv[u][f].y, xv[u][f].z, xv[u][f].w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        dot2_step(xs[e], w[u], s[4 * f + e], c[4 * f + e]);
+                        ab[4 * f + e] = fmaf(fabsf(xs[e]), wab[u], ab[4 * f + e]);
+                    }
+                }
+        }
+    }
+    // per-row-group results to shared memory: [rg][3][q], then the row groups in order
+    extern __shared__ float sredf[];
+#pragma unroll
+    for (int f = 0; f < 2; ++f) {
+        const int c4 = sl * 64 + 32 * f + lane;
+        if (c4 < nf4) {
+            float *b = sredf + (size_t)rg * 3 * q;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int j = 4 * c4 + e;
+                b[j] = s[4 * f + e];
+                b[q + j] = c[4 * f + e];
+                b[2 * q + j] = ab[4 * f + e];
+            }
+        }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < q; j += blockDim.x) {
+        float ss = 0.f, cc = 0.f, aa = 0.f;
+        for (int g = 0; g < NRG; ++g) {
+            const float *b = sredf + (size_t)g * 3 * q;
+            df_acc(ss, cc, b[j], b[q + j]);
+            aa += b[2 * q + j];
+        }
+        float hi, lo;
+        two_sum(ss, cc, hi, lo);
+        float *pb = part + (size_t)blockIdx.x * 3 * q;
+        pb[j] = hi;
+        pb[q + j] = lo;
+        pb[2 * q + j] = aa;
+    }
+    __threadfence();
+    __syncthreads();
+    __shared__ int is_last;
+    if (threadIdx.x == 0) is_last = (atomicAdd(counter, 1u) == (unsigned)(G - 1));
+    __syncthreads();
+    if (is_last) {
+        __threadfence();
+        final_reduce_df(G, q, part, base, abase, out, aout, red, slot, sredf, go);
+        if (threadIdx.x == 0) *counter = 0u;
+    }
+}
+
 // out_j = sum_b part[b][j] in a fixed order (8 interleaved sub-sums per
 // column, then the 8 combined in order); red[slot] = sum_j (sum_b apart[b][j])^2.
 // One block of 1024 threads: 128 columns x 8 sub-sums per round.
@@ -347,6 +465,7 @@ static cudaError_t rmatvec_t(Work &W, const double *c, const int32_t *idx, const
 }
 
 static int g_rmx_attr = 0;
+static int g_rmc_attr = 0;
 
 static cudaError_t rmatvec_mx(Work &W, const float2 *wc, const float *wa, const int32_t *idx,
                               const long long *cnt_dev, const double *base, const float *abase, double *out,
@@ -377,7 +496,23 @@ static cudaError_t rmatvec_mx(Work &W, const float2 *wc, const float *wa, const 
     }
     const float *X = (const float *)W.X;
 #define RX_ARGS X, W.n, q, wc, wa, idx, cnt_dev, part, W.rm_counter, base, abase, out, aout, W.red, scale_slot, go
-    if (vec) {
+    if (vec && q > 128 && q <= 1024) {
+        // column slices: one block of 16 warps per SM
+        const int Gc = W.nsm;
+        const int nsl = q <= 512 ? 2 : 4;
+        const size_t smc = (size_t)((kRcThreads / 32) / nsl) * 3 * q * sizeof(float);
+        if (!g_rmc_attr) {
+            cudaError_t ea = cudaFuncSetAttribute(rmatvec_mx_cols_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  64 * 1024);
+            if (ea == cudaSuccess)
+                ea = cudaFuncSetAttribute(rmatvec_mx_cols_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          64 * 1024);
+            if (ea != cudaSuccess) return ea;
+            g_rmc_attr = 1;
+        }
+        if (nsl == 2) rmatvec_mx_cols_kernel<2><<<Gc, kRcThreads, smc, W.st>>>(RX_ARGS);
+        else rmatvec_mx_cols_kernel<4><<<Gc, kRcThreads, smc, W.st>>>(RX_ARGS);
+    } else if (vec) {
         if (nch <= 1) rmatvec_mx_part_kernel<4, 1><<<G, threads, smem, W.st>>>(RX_ARGS);
         else if (nch <= 2) rmatvec_mx_part_kernel<4, 2><<<G, threads, smem, W.st>>>(RX_ARGS);
         else if (nch <= 4) rmatvec_mx_part_kernel<4, 4><<<G, threads, smem, W.st>>>(RX_ARGS);
