@@ -681,7 +681,7 @@ __device__ void bc_chol_solve(const float *__restrict__ Lg, const float *__restr
     }
 }
 
-__global__ void __launch_bounds__(kCgThreads) newton_bchol_kernel(int q, const float2 *__restrict__ Mf,
+__global__ void __launch_bounds__(kCgThreads, 1) newton_bchol_kernel(int q, const float2 *__restrict__ Mf,
                                                                   const double *__restrict__ g, double *__restrict__ dv,
                                                                   float eta, float tau, int maxit,
                                                                   double *__restrict__ info, int *err,

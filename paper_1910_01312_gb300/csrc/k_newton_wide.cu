@@ -48,7 +48,7 @@ namespace {
 constexpr int kWdBlk = 128;   // diagonal tile of the inverse factor
 constexpr int kWdCols = 8;    // columns of Pinv one block solves together
 
-__global__ void __launch_bounds__(kCgThreads) newton_mfw_setup_kernel(int q, const float2 *__restrict__ Mf,
+__global__ void __launch_bounds__(kCgThreads, 1) newton_mfw_setup_kernel(int q, const float2 *__restrict__ Mf,
                                                                       float *__restrict__ Lg, float *__restrict__ Dg,
                                                                       float *__restrict__ Linv,
                                                                       float *__restrict__ Pinv, int *fflag,
@@ -79,9 +79,7 @@ __global__ void __launch_bounds__(kCgThreads) newton_mfw_setup_kernel(int q, con
         const int kb = tb * kWdBlk;
         const int nbk = q - kb < kWdBlk ? q - kb : kWdBlk;
         const int qpk = (nbk + 31) & ~31;
-        for (int i = warp; i < qpk; i += nw)
-            for (int j = lane; j <= i; j += 32)
-                S.L[lpos(i, j)] = (i < nbk) ? __ldcg(&Lg[(size_t)(kb + i) * q + kb + j]) : (i == j ? 1.f : 0.f);
+        load_lower(S.L, LayPacked(), Lg + (size_t)kb * q + kb, (size_t)q, nbk, qpk);
         for (int e = tid; e < (qpk / kPb) * kPb * kPb; e += blockDim.x) {
             const int b8 = e / (kPb * kPb), w = e - b8 * kPb * kPb;
             S.D[e] = (b8 * kPb < nbk) ? __ldcg(&Dg[(size_t)kb * kPb + e]) : ((w / kPb == w % kPb) ? 1.f : 0.f);

@@ -24,15 +24,27 @@ struct CgSmem {
     float2 *X, *R, *P, *AP, *Z, *RO;
 };
 
+// Shared-memory layouts of a lower triangle: packed row by row (the one-block
+// solver, short of room) or full rows of stride ld (ld odd: consecutive rows
+// fall on different banks).
+struct LayPacked {
+    __device__ __forceinline__ int operator()(int i, int j) const { return lpos(i, j); }
+};
+struct LayFull {
+    int ld;
+    __device__ __forceinline__ int operator()(int i, int j) const { return i * ld + j; }
+};
+
 // warp 0, lanes 0..7: factor the diagonal block at kb and store its inverse;
 // false if a pivot is not positive
-__device__ __forceinline__ bool cg_diag8(float *L, int kb, float *Db)
+template <class Lay>
+__device__ __forceinline__ bool cg_diag8_t(float *L, int kb, float *Db, Lay lay)
 {
     const int lane = threadIdx.x & 31;
     const bool on = lane < kPb;
     float a[kPb];
 #pragma unroll
-    for (int k = 0; k < kPb; ++k) a[k] = (on && k <= lane) ? L[lpos(kb + lane, kb + k)] : 0.f;
+    for (int k = 0; k < kPb; ++k) a[k] = (on && k <= lane) ? L[lay(kb + lane, kb + k)] : 0.f;
     bool ok = true;
     float rsd = 1.f;   // this lane's 1 / L_ii
 #pragma unroll
@@ -65,18 +77,48 @@ __device__ __forceinline__ bool cg_diag8(float *L, int kb, float *Db)
     if (on) {
 #pragma unroll
         for (int k = 0; k < kPb; ++k) {
-            if (k <= lane) L[lpos(kb + lane, kb + k)] = a[k];
+            if (k <= lane) L[lay(kb + lane, kb + k)] = a[k];
             Db[k * kPb + lane] = x[k];
         }
     }
     return ok;
 }
 
-// In-place FP32 Cholesky of the packed qp x qp matrix in S.L (qp % 32 == 0,
-// rows beyond the problem set to the identity), right-looking by 8-column
+// dst[lay(i, j)] = src[i * ld + j] for the lower triangle j <= i of an np x np
+// tile (rows i >= n: the identity), by the whole block with eight loads in
+// flight per thread (a load-then-store loop waits one L2 round trip per element)
+template <class Lay>
+__device__ __forceinline__ void load_lower(float *dst, Lay lay, const float *__restrict__ src, size_t ld, int n, int np)
+{
+    const int total = np * np;
+    for (int e0 = threadIdx.x; e0 < total; e0 += 8 * blockDim.x) {
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = e0 + u * blockDim.x;
+            const int i = e / np, j = e - i * np;
+            v[u] = (e < total && j <= i && i < n) ? __ldcg(src + (size_t)i * ld + j) : (i == j ? 1.f : 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = e0 + u * blockDim.x;
+            const int i = e / np, j = e - i * np;
+            if (e < total && j <= i) dst[lay(i, j)] = v[u];
+        }
+    }
+}
+
+__device__ __forceinline__ bool cg_diag8(float *L, int kb, float *Db)
+{
+    return cg_diag8_t(L, kb, Db, LayPacked());
+}
+
+// In-place FP32 Cholesky of the qp x qp matrix in S.L (layout lay; qp % 32 ==
+// 0, rows beyond the problem set to the identity), right-looking by 8-column
 // panels; S.D receives the inverses of the 8 x 8 diagonal blocks.  Block-
 // uniform result: false when a pivot is not positive.
-static __device__ bool cg_factor_packed(CgSmem &S, int qp)
+template <class Lay>
+static __device__ bool cg_factor_t(CgSmem &S, int qp, Lay lay)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     const int nb = qp / kPb;
@@ -86,7 +128,7 @@ static __device__ bool cg_factor_packed(CgSmem &S, int qp)
     for (int b = 0; b < nb; ++b) {
         const int kb = b * kPb;
         if (warp == 0) {
-            const bool ok = cg_diag8(S.L, kb, S.D + b * kPb * kPb);
+            const bool ok = cg_diag8_t(S.L, kb, S.D + b * kPb * kPb, lay);
             if (!ok && lane == 0) bad = 1;
         }
         __syncthreads();
@@ -99,11 +141,11 @@ static __device__ bool cg_factor_packed(CgSmem &S, int qp)
             for (int k = 0; k < kPb; ++k) dr[k] = Db[c * kPb + k];
             for (int r0 = kb + kPb + warp * 4; r0 < qp; r0 += nw * 4) {
                 const int r = r0 + grp;
-                const float av = (r < qp) ? S.L[lpos(r, kb + c)] : 0.f;
+                const float av = (r < qp) ? S.L[lay(r, kb + c)] : 0.f;
                 float acc = 0.f;
 #pragma unroll
                 for (int k = 0; k < kPb; ++k) acc = fmaf(__shfl_sync(0xffffffffu, av, grp * 8 + k), dr[k], acc);
-                if (r < qp) S.L[lpos(r, kb + c)] = acc;
+                if (r < qp) S.L[lay(r, kb + c)] = acc;
             }
         }
         __syncthreads();
@@ -111,13 +153,13 @@ static __device__ bool cg_factor_packed(CgSmem &S, int qp)
         for (int r = kb + kPb + warp; r < qp; r += nw) {
             float lr[kPb];
 #pragma unroll
-            for (int k = 0; k < kPb; ++k) lr[k] = S.L[lpos(r, kb + k)];
+            for (int k = 0; k < kPb; ++k) lr[k] = S.L[lay(r, kb + k)];
             for (int c = kb + kPb + lane; c <= r; c += 32) {
-                const int pc = lpos(c, kb);
+                const int pc = lay(c, kb);
                 float acc = 0.f;
 #pragma unroll
                 for (int k = 0; k < kPb; ++k) acc = fmaf(lr[k], S.L[pc + k], acc);
-                S.L[lpos(r, c)] -= acc;
+                S.L[lay(r, c)] -= acc;
             }
         }
         __syncthreads();
@@ -125,6 +167,11 @@ static __device__ bool cg_factor_packed(CgSmem &S, int qp)
     const bool ok = !bad;
     __syncthreads();
     return ok;
+}
+
+static __device__ bool cg_factor_packed(CgSmem &S, int qp)
+{
+    return cg_factor_t(S, qp, LayPacked());
 }
 
 constexpr int kBcNb = 128;     // panel width of the blocked factor
@@ -167,6 +214,10 @@ static __device__ int bc_factor(int q, const float2 *__restrict__ Mf, float *__r
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     const int b = blockIdx.x, G = gridDim.x;
     const int gw = b * nw + warp, ngw = G * nw;
+    constexpr int kLdF = kBcNb + 1;                     // odd row stride: rows on distinct banks
+    float *LF = reinterpret_cast<float *>(S.M);         // a 128-panel's diagonal block (kBcNb x kLdF)
+    CgSmem SF = S;
+    SF.L = LF;
     // the largest diagonal entry (scale of the breakdown shift), in every block
     float md = 0.f;
     for (int j = tid; j < q; j += blockDim.x) md = fmaxf(md, Mf[(size_t)j * q + j].x);
@@ -191,18 +242,17 @@ static __device__ int bc_factor(int q, const float2 *__restrict__ Mf, float *__r
         for (int kb = 0; kb < q && !bad; kb += kBcNb) {
             const int nbk = q - kb < kBcNb ? q - kb : kBcNb;
             const int qpk = (nbk + 31) & ~31;
-            // (1) block 0: the diagonal block
+            // (1) block 0: the diagonal block, in full rows of stride kLdF in the
+            // (free) M region
             if (b == 0) {
-                for (int i = warp; i < qpk; i += nw)
-                    for (int j = lane; j <= i; j += 32)
-                        S.L[lpos(i, j)] = (i < nbk) ? __ldcg(&Lg[(size_t)(kb + i) * q + kb + j]) : (i == j ? 1.f : 0.f);
+                load_lower(LF, LayFull{kLdF}, Lg + (size_t)kb * q + kb, (size_t)q, nbk, qpk);
                 __syncthreads();
-                const bool ok = cg_factor_packed(S, qpk);
+                const bool ok = cg_factor_t(SF, qpk, LayFull{kLdF});
                 if (!ok) {
                     if (tid == 0) atomicExch(fflag, 1);
                 } else {
                     for (int i = warp; i < nbk; i += nw)
-                        for (int j = lane; j <= i; j += 32) Lg[(size_t)(kb + i) * q + kb + j] = S.L[lpos(i, j)];
+                        for (int j = lane; j <= i; j += 32) Lg[(size_t)(kb + i) * q + kb + j] = LF[i * kLdF + j];
                     for (int e = tid; e < ((nbk + kPb - 1) / kPb) * kPb * kPb; e += blockDim.x)
                         Dg[(size_t)kb * kPb + e] = S.D[e];
                 }
@@ -217,12 +267,9 @@ static __device__ int bc_factor(int q, const float2 *__restrict__ Mf, float *__r
             if (kb + nbk >= q) break;
             // (2) the panel's rows below: x L_kk' = a, a warp per row (every block
             // first copies L_kk into its shared memory, with 1 / L_cc in S.t)
-            if (b != 0) {
-                for (int i = warp; i < nbk; i += nw)
-                    for (int j = lane; j <= i; j += 32) S.L[lpos(i, j)] = __ldcg(&Lg[(size_t)(kb + i) * q + kb + j]);
-            }
+            if (b != 0) load_lower(LF, LayFull{kLdF}, Lg + (size_t)kb * q + kb, (size_t)q, nbk, nbk);
             __syncthreads();
-            for (int c = tid; c < nbk; c += blockDim.x) S.t[c] = 1.f / S.L[lpos(c, c)];
+            for (int c = tid; c < nbk; c += blockDim.x) S.t[c] = 1.f / LF[c * kLdF + c];
             __syncthreads();
             for (int r = kb + nbk + gw; r < q; r += ngw) {
                 float a[kBcNb / 32];
@@ -241,7 +288,7 @@ static __device__ int bc_factor(int q, const float2 *__restrict__ Mf, float *__r
 #pragma unroll
                     for (int m = 0; m < kBcNb / 32; ++m) {
                         const int j = lane + 32 * m;
-                        if (j > c && j < nbk) a[m] = fmaf(-S.L[lpos(j, c)], xc, a[m]);
+                        if (j > c && j < nbk) a[m] = fmaf(-LF[j * kLdF + c], xc, a[m]);
                         if (j == c) a[m] = xc;
                     }
                 }
@@ -265,10 +312,26 @@ static __device__ int bc_factor(int q, const float2 *__restrict__ Mf, float *__r
                     while (rem > ti) { rem -= ti + 1; ++ti; }
                     const int tj = rem;
                     const int i0 = t0 + ti * kBcTile, j0 = t0 + tj * kBcTile;
-                    for (int e = tid; e < kBcTile * nbk; e += blockDim.x) {
-                        const int rr = e / nbk, m = e - rr * nbk;
-                        TA[rr * ld + m] = (i0 + rr < q) ? __ldcg(&Lg[(size_t)(i0 + rr) * q + kb + m]) : 0.f;
-                        TB[rr * ld + m] = (j0 + rr < q) ? __ldcg(&Lg[(size_t)(j0 + rr) * q + kb + m]) : 0.f;
+                    // the two 64-row strips of the panel, four loads of each in flight per thread
+                    for (int e0 = tid; e0 < kBcTile * nbk; e0 += 4 * blockDim.x) {
+                        float va[4], vb[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int e = e0 + u * blockDim.x;
+                            const int rr = e / nbk, m = e - rr * nbk;
+                            const bool in = e < kBcTile * nbk;
+                            va[u] = (in && i0 + rr < q) ? __ldcg(&Lg[(size_t)(i0 + rr) * q + kb + m]) : 0.f;
+                            vb[u] = (in && j0 + rr < q) ? __ldcg(&Lg[(size_t)(j0 + rr) * q + kb + m]) : 0.f;
+                        }
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int e = e0 + u * blockDim.x;
+                            const int rr = e / nbk, m = e - rr * nbk;
+                            if (e < kBcTile * nbk) {
+                                TA[rr * ld + m] = va[u];
+                                TB[rr * ld + m] = vb[u];
+                            }
+                        }
                     }
                     __syncthreads();
                     const int ii = tid >> 3, jc = tid & 7;   // row ii, columns jc + 8u
