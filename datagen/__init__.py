@@ -79,13 +79,16 @@ def gauss1m(seed: int = 0, n: int = 1_000_000, q: int = 128):
     return X, y, 0.1
 
 
-def warm_instance(seed: int, n: int = 100_000, q: int = 128):
+def warm_instance(seed: int, n: int = 100_000, q: int = 128, m_range=(0.1, 0.5), noise_max: float = 0.15):
     """One instance of the learned-warm-start workload: the gauss1m generator
-    with per-instance class-mean scale m ~ U[0.1, 0.5], label noise ~ U[0, 0.15]
-    and C = 10^U[-2, 1].  Returns (X [n x q] FP32, y int8, C)."""
+    with per-instance class-mean scale m ~ U[m_range], label noise ~ U[0,
+    noise_max] and C = 10^U[-2, 1] (the defaults: overlapping, noisy classes,
+    most samples support vectors; m_range = (1, 2), noise_max = 0.01: nearly
+    separable classes, few support vectors).  Returns (X [n x q] FP32, y
+    int8, C)."""
     rng = _rng("warm", seed)
-    m = rng.uniform(0.1, 0.5)
-    noise = rng.uniform(0.0, 0.15)
+    m = rng.uniform(*m_range)
+    noise = rng.uniform(0.0, noise_max)
     C = float(10.0 ** rng.uniform(-2.0, 1.0))
     X, y = gaussian_two_class(n, q, m, np.linspace(0.1, 2.0, q), noise, 10_000 + int(seed), np.float32, "warm")
     return X, y, C

@@ -2,10 +2,10 @@
  *
  * The paper starts SSsNAL from a random-feature solution (Sec. 4.3); here a
  * small network predicts, for every sample, whether its dual variable ends at
- * 0, strictly inside (0, C) or at C, from the sample and four statistics, and
- * the prediction becomes the starting point alpha^0 passed to
- * svm_ssnalm_solve (which projects it onto the feasible set; the cold start
- * alpha^0 = 0 remains the fallback).  The network is trained on labels
+ * 0, strictly inside (0, C) or at C, from the sample and four statistics; the
+ * rows not predicted at 0 form a reduced problem whose solution starts the
+ * full solve (svm_ssnalm_solve_mlp; the cold start alpha^0 = 0 remains the
+ * fallback).  The network is trained on labels
  * harvested from the solver's own solutions.
  *
  * Network: F (n x 132) -> Z1 = F W1 + b1 -> H1 = gelu(Z1) -> Z2 = H1 W2 + b2 ->
@@ -87,11 +87,17 @@ svm_status svm_mlp_train_step(svm_mlp_t *m, const float *F, const int32_t *label
  * the logits) of each of the n <= max_rows rows of F (FP64 output, n). */
 svm_status svm_mlp_start_point(svm_mlp_t *m, const float *F, int64_t n, double C, double *alpha0);
 
-/* Warm-started solve of the problem behind h (dense FP32, q = 128, device
- * memory, n <= the network's max_rows): features, start point, then
- * svm_ssnalm_solve(h, alpha0, res).  If that solve ends with
- * SVM_ERR_NOT_CONVERGED or SVM_ERR_NUMERIC (the warm start spent the cold
- * solve's iteration budget, or broke down), the problem is solved again from
+/* Warm-started solve of the problem behind h (dense FP32, q = 128, n <= the
+ * network's max_rows).  The network's logits give the working set J0: the
+ * rows whose predicted probability of alpha_i = 0 is below 0.9 (the
+ * complement of the predicted active set at the lower bound).  When J0 holds
+ * at most n/2 rows of both classes, the SVM restricted to J0 is solved first
+ * (cold, the same C and tolerance, on an internal handle over a gathered copy
+ * of those rows: stream-ordered allocations, freed before returning) and its
+ * solution, zero elsewhere, is alpha^0 of svm_ssnalm_solve(h, alpha0, res);
+ * when J0 holds every support vector that solve stops at its first KKT test.
+ * Otherwise the problem is solved cold.  If the warm-started solve ends with
+ * SVM_ERR_NOT_CONVERGED or SVM_ERR_NUMERIC, the problem is solved again from
  * alpha^0 = 0 and that result is returned.  *used_warm (nullable) is 1 when
  * the returned result is the warm-started one.  Other problems return
  * SVM_ERR_UNSUPPORTED. */

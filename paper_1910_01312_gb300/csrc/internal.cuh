@@ -336,3 +336,11 @@ cudaError_t launch_newton_csr(Work &W, const int32_t *J, long long p, double sig
                               bool dots);
 
 }  // namespace svm
+
+// The working set of the reduced warm-start solve (k_mlp.cu, global scope like
+// the network's handle): the rows whose predicted probability of alpha_i = 0
+// is below p0max, ascending in idx; total[0] their number, total[1] how many
+// have y = +1 (blk: G int2 of scratch).
+struct svm_mlp;
+cudaError_t mlp_working_set(svm_mlp *m, const float *F, long long n, const int8_t *y, float p0max, int G,
+                            int2 *blk, int32_t *idx, long long *total);

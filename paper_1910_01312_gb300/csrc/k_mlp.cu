@@ -501,6 +501,93 @@ extern "C" svm_status svm_mlp_train_step(svm_mlp_t *m, const float *F, const int
     return s == SVM_OK ? svm_mlp_adam_step(m, m->grad, t, lr, wd) : s;
 }
 
+// ---- the working set of the reduced warm-start solve (svm_ssnalm.cu) ----
+// Row i is in the set when the network's probability of alpha_i = 0 (softmax
+// of the logits) is below p0max: e^(z1 - z0) + e^(z2 - z0) > 1 / p0max - 1.
+// Block b owns rows [b per, (b + 1) per); pass 1 counts its rows (and their
+// positive labels), pass 2 writes them in ascending order at the block's
+// offset (the counts of the blocks before it), warp ballots within a block.
+__device__ __forceinline__ bool ws_in(const float *Z3, int i, float thr)
+{
+    const float z0 = Z3[3 * i], z1 = Z3[3 * i + 1], z2 = Z3[3 * i + 2];
+    return expf(z1 - z0) + expf(z2 - z0) > thr;
+}
+
+__global__ void ws_count_kernel(int n, const float *__restrict__ Z3, const int8_t *__restrict__ y, float thr,
+                                int2 *__restrict__ blk)
+{
+    const int per = (n + gridDim.x - 1) / gridDim.x;
+    const int r0 = blockIdx.x * per, r1 = r0 + per < n ? r0 + per : n;
+    int c = 0, cp = 0;
+    for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x)
+        if (ws_in(Z3, i, thr)) {
+            ++c;
+            cp += y[i] > 0;
+        }
+    __shared__ int sc[32], sp[32];
+    for (int o = 16; o > 0; o >>= 1) {
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+        cp += __shfl_xor_sync(0xffffffffu, cp, o);
+    }
+    if ((threadIdx.x & 31) == 0) { sc[threadIdx.x >> 5] = c; sp[threadIdx.x >> 5] = cp; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0, tp = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { t += sc[w]; tp += sp[w]; }
+        blk[blockIdx.x] = make_int2(t, tp);
+    }
+}
+
+__global__ void ws_compact_kernel(int n, const float *__restrict__ Z3, float thr, const int2 *__restrict__ blk,
+                                  int32_t *__restrict__ idx, long long *__restrict__ total)
+{
+    const int per = (n + gridDim.x - 1) / gridDim.x;
+    const int r0 = blockIdx.x * per, r1 = r0 + per < n ? r0 + per : n;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __shared__ int s_off;
+    __shared__ int s_w[32];
+    if (threadIdx.x == 0) {
+        int o = 0;
+        for (int b = 0; b < (int)blockIdx.x; ++b) o += blk[b].x;
+        s_off = o;
+        if (blockIdx.x == 0) {
+            long long t = 0, tp = 0;
+            for (int b = 0; b < (int)gridDim.x; ++b) { t += blk[b].x; tp += blk[b].y; }
+            total[0] = t;
+            total[1] = tp;
+        }
+    }
+    __syncthreads();
+    for (int base = r0; base < r1; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        const bool in = i < r1 && ws_in(Z3, i, thr);
+        const unsigned bal = __ballot_sync(0xffffffffu, in);
+        if (lane == 0) s_w[warp] = __popc(bal);
+        __syncthreads();
+        int before = 0, all = 0;
+        for (int w = 0; w < nw; ++w) {
+            if (w < warp) before += s_w[w];
+            all += s_w[w];
+        }
+        if (in) idx[s_off + before + __popc(bal & ((1u << lane) - 1u))] = i;
+        __syncthreads();
+        if (threadIdx.x == 0) s_off += all;
+        __syncthreads();
+    }
+}
+
+cudaError_t mlp_working_set(svm_mlp_t *m, const float *F, long long n, const int8_t *y, float p0max, int G,
+                            int2 *blk, int32_t *idx, long long *total)
+{
+    if (!m || !F || n < 1 || n > m->max_rows || !(p0max > 0.f && p0max < 1.f) || G < 1) return cudaErrorInvalidValue;
+    const cudaError_t e = forward_keep(m, F, (int)n);
+    if (e != cudaSuccess) return e;
+    const float thr = 1.f / p0max - 1.f;
+    ws_count_kernel<<<G, 256, 0, m->st>>>((int)n, m->Z3, y, thr, blk);
+    ws_compact_kernel<<<G, 256, 0, m->st>>>((int)n, m->Z3, thr, blk, idx, total);
+    return cudaGetLastError();
+}
+
 extern "C" svm_status svm_mlp_start_point(svm_mlp_t *m, const float *F, int64_t n, double C, double *alpha0)
 {
     if (!m || !F || !alpha0 || n < 1 || n > m->max_rows || !(C > 0.0)) return SVM_ERR_INVALID_ARG;

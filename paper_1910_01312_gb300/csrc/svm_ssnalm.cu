@@ -27,6 +27,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <chrono>
 #include <new>
 #include <string>
 #include <utility>
@@ -1599,6 +1600,54 @@ extern "C" svm_status svm_ssnalm_get_stats(svm_ssnalm_t *h, svm_stats *out, int 
 // Warm start from the learned network (include/svm_mlp.h), with the cold solve
 // as fallback.  The paper's own warm start is a cheaper solve of an
 // approximating problem (Sec. 4.3); the network plays that role here.
+// rows idx[0 .. m) of X (n x q FP32) and y into Xw (m x q) and yw
+__global__ void gather_rows_kernel(const float *__restrict__ X, const int8_t *__restrict__ y, int q,
+                                   const int32_t *__restrict__ idx, long long m, float *__restrict__ Xw,
+                                   int8_t *__restrict__ yw)
+{
+    const int q4 = q / 4;
+    for (long long r = blockIdx.x; r < m; r += gridDim.x) {
+        const long long i = idx[r];
+        const float4 *src = reinterpret_cast<const float4 *>(X + i * q);
+        float4 *dst = reinterpret_cast<float4 *>(Xw + r * q);
+        for (int c = threadIdx.x; c < q4; c += blockDim.x) dst[c] = __ldcs(src + c);
+        if (threadIdx.x == 0) yw[r] = y[i];
+    }
+}
+
+// a0 = 0, then a0[idx[r]] = aw[r]
+__global__ void scatter_alpha_kernel(long long n, const int32_t *__restrict__ idx, long long m,
+                                     const double *__restrict__ aw, double *__restrict__ a0)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        a0[i] = 0.0;
+}
+__global__ void scatter_alpha2_kernel(const int32_t *__restrict__ idx, long long m, const double *__restrict__ aw,
+                                      double *__restrict__ a0)
+{
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < m; r += (long long)gridDim.x * blockDim.x)
+        a0[idx[r]] = aw[r];
+}
+
+// Probability of alpha_i = 0 below which a row joins the reduced solve's working
+// set (SVM_WS_P0 overrides it for measurements).
+static float ws_p0max()
+{
+    static float v = -1.f;
+    if (v < 0.f) {
+        const char *e = getenv("SVM_WS_P0");
+        v = (e && atof(e) > 0.0 && atof(e) < 1.0) ? (float)atof(e) : 0.9f;
+    }
+    return v;
+}
+
+// The learned warm start: the network's working set J0 (rows not predicted to
+// end at alpha = 0 with probability >= 0.9) is solved as an SVM of its own
+// (same C and tolerance, cold), and its solution, zero elsewhere, starts the
+// full solve; when J0 holds every support vector the full solve stops at its
+// first KKT test.  A reduced problem larger than half of the rows costs about
+// a full solve, and one that is degenerate (one class) is no problem at all:
+// then the full problem is solved cold.
 static svm_status solve_mlp_impl(svm_ssnalm *h, svm_mlp_t *m, svm_result *res, int32_t *used_warm)
 {
     if (used_warm) *used_warm = 0;
@@ -1608,32 +1657,99 @@ static svm_status solve_mlp_impl(svm_ssnalm *h, svm_mlp_t *m, svm_result *res, i
         return SVM_ERR_UNSUPPORTED;
     }
     const long long n = W.n;
-    float *F = nullptr;
-    double *a0 = nullptr;
+    const int q = (int)W.q;
+    const int G = 2 * W.nsm;
+    float *F = nullptr, *Xw = nullptr;
+    double *a0 = nullptr, *aw = nullptr, *ww = nullptr;
+    int32_t *idx = nullptr;
+    int8_t *yw = nullptr;
+    int2 *blk = nullptr;
+    long long *tot = nullptr;
+    auto release = [&]() {
+        void *p[] = {F, Xw, a0, aw, ww, idx, yw, blk, tot};
+        for (void *x : p)
+            if (x) cudaFreeAsync(x, W.st);
+    };
     if (cudaMallocAsync(&F, sizeof(float) * n * SVM_MLP_IN, W.st) != cudaSuccess ||
-        cudaMallocAsync(&a0, sizeof(double) * n, W.st) != cudaSuccess) {
-        if (F) cudaFreeAsync(F, W.st);
+        cudaMallocAsync(&a0, sizeof(double) * n, W.st) != cudaSuccess ||
+        cudaMallocAsync(&idx, sizeof(int32_t) * n, W.st) != cudaSuccess ||
+        cudaMallocAsync(&blk, sizeof(int2) * G, W.st) != cudaSuccess ||
+        cudaMallocAsync(&tot, sizeof(long long) * 2, W.st) != cudaSuccess) {
+        release();
         h->err = "device allocation of the warm-start buffers failed";
         return SVM_ERR_OOM;
     }
     svm_status st = svm_mlp_features((const float *)W.X, W.y, n, W.q, h->P.C, F, W.st);
-    if (st == SVM_OK) st = svm_mlp_start_point(m, F, n, h->P.C, a0);
+    long long ht[2] = {0, 0};
+    if (st == SVM_OK &&
+        (mlp_working_set(m, F, n, W.y, ws_p0max(), G, blk, idx, tot) != cudaSuccess ||
+         cudaMemcpyAsync(ht, tot, sizeof(ht), cudaMemcpyDeviceToHost, W.st) != cudaSuccess ||
+         cudaStreamSynchronize(W.st) != cudaSuccess))
+        st = SVM_ERR_CUDA;
+    bool reduced = false;
+    const long long mw = ht[0];
+    if (st == SVM_OK && mw >= 2 && 2 * mw <= n && ht[1] > 0 && ht[1] < mw) {
+        if (cudaMallocAsync(&Xw, sizeof(float) * mw * q, W.st) != cudaSuccess ||
+            cudaMallocAsync(&yw, mw, W.st) != cudaSuccess ||
+            cudaMallocAsync(&aw, sizeof(double) * mw, W.st) != cudaSuccess ||
+            cudaMallocAsync(&ww, sizeof(double) * q, W.st) != cudaSuccess) {
+            release();
+            h->err = "device allocation of the warm-start buffers failed";
+            return SVM_ERR_OOM;
+        }
+        gather_rows_kernel<<<(unsigned)(mw < 4096 ? mw : 4096), 32, 0, W.st>>>((const float *)W.X, W.y, q, idx, mw,
+                                                                                Xw, yw);
+        svm_problem pw = h->prob;
+        pw.n = mw;
+        pw.layout = SVM_DENSE_ROWMAJOR;
+        pw.dtype = SVM_F32;
+        pw.memory = SVM_MEM_DEVICE;
+        pw.X = Xw;
+        pw.y = yw;
+        svm_ssnalm_t *sub = nullptr;
+        const auto t0 = std::chrono::steady_clock::now();
+        svm_status sc = cudaGetLastError() == cudaSuccess ? create_impl(&sub, &pw, &h->P, false) : SVM_ERR_CUDA;
+        if (sc == SVM_OK) {
+            sub->npos = ht[1];
+            svm_result rw{};
+            rw.alpha = aw;
+            rw.w = ww;
+            if (h->trace) cudaStreamSynchronize(W.st);
+            const auto t1 = std::chrono::steady_clock::now();
+            sc = solve_direct(sub, nullptr, &rw);
+            if (h->trace) {
+                cudaStreamSynchronize(W.st);
+                const auto t2 = std::chrono::steady_clock::now();
+                fprintf(stderr, "[svm] warm start: working set %lld of %lld rows; create %.2f ms, reduced solve %.2f ms "
+                        "(%d outer, R_KKT %.2e)\n", mw, n, std::chrono::duration<double, std::milli>(t1 - t0).count(),
+                        std::chrono::duration<double, std::milli>(t2 - t1).count(), rw.outer_iters, rw.kkt);
+            }
+            if (sc == SVM_OK || sc == SVM_ERR_NOT_CONVERGED) {
+                scatter_alpha_kernel<<<W.nsm * 4, 256, 0, W.st>>>(n, idx, mw, aw, a0);
+                scatter_alpha2_kernel<<<W.nsm * 4, 256, 0, W.st>>>(idx, mw, aw, a0);
+                reduced = cudaGetLastError() == cudaSuccess;
+            }
+            svm_ssnalm_destroy(sub);
+        }
+    }
     std::vector<double> host_a0;
-    if (st == SVM_OK && h->prob.memory == SVM_MEM_HOST) {
+    if (st == SVM_OK && reduced && h->prob.memory == SVM_MEM_HOST) {
         host_a0.resize((size_t)n);
         if (cudaMemcpyAsync(host_a0.data(), a0, sizeof(double) * n, cudaMemcpyDeviceToHost, W.st) != cudaSuccess ||
             cudaStreamSynchronize(W.st) != cudaSuccess)
             st = SVM_ERR_CUDA;
     }
     if (st != SVM_OK) {
-        cudaFreeAsync(F, W.st);
-        cudaFreeAsync(a0, W.st);
+        release();
         h->err = "warm-start features or network failed";
         return st;
     }
+    if (!reduced) {
+        release();
+        return solve_direct(h, nullptr, res);
+    }
     st = solve_direct(h, h->prob.memory == SVM_MEM_HOST ? host_a0.data() : a0, res);
-    cudaFreeAsync(F, W.st);
-    cudaFreeAsync(a0, W.st);
+    release();
     if (st == SVM_ERR_NOT_CONVERGED || st == SVM_ERR_NUMERIC) return solve_direct(h, nullptr, res);
     if (used_warm) *used_warm = 1;
     return st;

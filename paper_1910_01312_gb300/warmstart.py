@@ -26,19 +26,22 @@ import numpy as np
 N_CLASSES = 3
 
 
+FAMILIES = {"overlapping": {}, "separated": {"m_range": (1.0, 2.0), "noise_max": 0.01}}
+
+
 def _instance(args):
     import datagen
-    seed, n, q = args
-    X, y, C = datagen.warm_instance(seed, n=n, q=q)
+    seed, n, q, family = args
+    X, y, C = datagen.warm_instance(seed, n=n, q=q, **FAMILIES[family])
     return seed, X, y, C
 
 
-def instances(pool, seeds, n, q=128):
+def instances(pool, seeds, n, q=128, family="overlapping"):
     """Yields (seed, X, y, C) in seed order, generated by the pool."""
-    yield from pool.imap(_instance, [(int(s), n, q) for s in seeds], chunksize=1)
+    yield from pool.imap(_instance, [(int(s), n, q, family) for s in seeds], chunksize=1)
 
 
-def harvest(pool, seeds, n, stream, dev="cuda"):
+def harvest(pool, seeds, n, stream, dev="cuda", family="overlapping"):
     """Cold solves of the training instances -> device features F (rows x 132),
     labels L (int32) and per-class counts."""
     import torch
@@ -50,7 +53,7 @@ def harvest(pool, seeds, n, stream, dev="cuda"):
     alpha = torch.empty(n, dtype=torch.float64, device=dev)
     w = torch.empty(128, dtype=torch.float64, device=dev)
     info = []
-    for k, (seed, X, y, C) in enumerate(instances(pool, seeds, n)):
+    for k, (seed, X, y, C) in enumerate(instances(pool, seeds, n, family=family)):
         Xd, yd = torch.from_numpy(X).to(dev), torch.from_numpy(y).to(dev)
         s = B.Solver(Xd, yd, C_=C, precision=B.PREC_MIXED, stream=stream)
         r = s.solve(alpha, w)
@@ -107,7 +110,7 @@ def _timed(fn, stream):
     return r, e0.elapsed_time(e1)
 
 
-def evaluate(pool, net, seeds, n, stream, dev="cuda"):
+def evaluate(pool, net, seeds, n, stream, dev="cuda", family="overlapping"):
     """Cold vs warm-started solves of held-out instances."""
     import torch
 
@@ -118,7 +121,7 @@ def evaluate(pool, net, seeds, n, stream, dev="cuda"):
     a0 = torch.empty(n, dtype=torch.float64, device=dev)
     lab = torch.empty(n, dtype=torch.int32, device=dev)
     rows = []
-    for seed, X, y, C in instances(pool, seeds, n):
+    for seed, X, y, C in instances(pool, seeds, n, family=family):
         Xd, yd = torch.from_numpy(X).to(dev), torch.from_numpy(y).to(dev)
         s = B.Solver(Xd, yd, C_=C, precision=B.PREC_MIXED, stream=stream)
         s.solve(alpha, w)
@@ -168,6 +171,8 @@ def main(argv=None):
     ap.add_argument("--wd", type=float, default=1e-4)
     ap.add_argument("--procs", type=int, default=8)
     ap.add_argument("--save", default=None, help="write the trained parameters (FP32 .npy)")
+    ap.add_argument("--family", default="overlapping", choices=sorted(FAMILIES),
+                    help="instance family: the default workload, or nearly separable classes")
     args = ap.parse_args(argv)
 
     pool = mp.get_context("spawn").Pool(args.procs)   # before the first GPU call
@@ -178,7 +183,7 @@ def main(argv=None):
     B.load()
     stream = torch.cuda.current_stream().cuda_stream
     t0 = time.time()
-    F, L, counts, info = harvest(pool, range(args.train), args.n, stream)
+    F, L, counts, info = harvest(pool, range(args.train), args.n, stream, family=args.family)
     t1 = time.time()
     cw = class_weights(counts)
     theta = torch.from_numpy(datagen.mlp_init(0)).cuda()
@@ -189,13 +194,14 @@ def main(argv=None):
     torch.cuda.synchronize()
     t3 = time.time()
     del F, L
-    rows = evaluate(pool, net, range(1_000_000, 1_000_000 + args.heldout), args.n, stream)
+    rows = evaluate(pool, net, range(1_000_000, 1_000_000 + args.heldout), args.n, stream, family=args.family)
     pool.close()
     if args.save:
         p = torch.empty(B.MLP_NPARAM, dtype=torch.float32, device="cuda")
         net.get_params(p)
         np.save(args.save, p.cpu().numpy())
-    out = {"train_instances": args.train, "n": args.n, "rows": int(counts.sum()), "class_counts": counts.tolist(),
+    out = {"family": args.family, "train_instances": args.train, "n": args.n, "rows": int(counts.sum()),
+           "class_counts": counts.tolist(),
            "class_weights": cw.tolist(), "epochs": args.epochs, "batch": args.batch,
            "harvest_s": t1 - t0, "train_s": t3 - t2, "epoch_loss": losses,
            "harvest_max_kkt": max(r["kkt"] for r in info)}

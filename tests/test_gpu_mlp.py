@@ -202,6 +202,30 @@ def test_trained_network_against_cold_start():
     net.close()
 
 
+def test_reduced_solve_on_separable_instances():
+    """Nearly separable classes leave few support vectors: the network trained
+    on such instances marks a working set J0 of well under half the rows, the
+    SVM restricted to J0 is solved first and its solution starts the full
+    solve (used_warm = 1).  Asserted: the warm-started solve reaches the cold
+    optimum (R_KKT <= 1e-6, objective within 1e-6); the times are printed."""
+    n = 20_000
+    pool = mp.get_context("spawn").Pool(4)
+    try:
+        stream = torch.cuda.current_stream().cuda_stream
+        F, L, counts, info = WS.harvest(pool, range(24), n, stream, family="separated")
+        assert counts[0] > 0.5 * counts.sum()       # most samples end at alpha = 0
+        net = P.MLP(dev(datagen.mlp_init(0)), n, stream)
+        WS.train(net, F, L, WS.class_weights(counts), 3, 4096, 2e-3, 1e-4, 0, stream)
+        rows = WS.evaluate(pool, net, range(600_000, 600_004), n, stream, family="separated")
+    finally:
+        pool.close()
+    print(WS.summarize(rows))
+    assert sum(r["used_warm"] for r in rows) >= 3, rows
+    for r in rows:
+        assert r["kkt_warm"] <= 1e-6 and r["obj_rel"] <= 1e-6, r
+    net.close()
+
+
 def test_cold_fallback_when_the_warm_solve_fails():
     """A warm solve that ends NOT_CONVERGED is redone cold: with max_outer = 1
     both fail, and the returned result is the cold one, bit for bit."""
