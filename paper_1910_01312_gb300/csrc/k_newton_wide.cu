@@ -46,6 +46,7 @@ namespace svm {
 namespace {
 
 constexpr int kWdBlk = 128;   // diagonal tile of the inverse factor
+constexpr int kMfwThreads = 256;   // CG kernel: 8 warps, up to 255 registers (two rows in flight per warp)
 constexpr int kWdCols = 8;    // columns of Pinv one block solves together
 
 __global__ void __launch_bounds__(kCgThreads, 1) newton_mfw_setup_kernel(int q, const float2 *__restrict__ Mf,
@@ -369,11 +370,11 @@ struct MfwArgs {
 // dynamic shared memory of newton_mfw_cg_kernel<NF4>
 constexpr size_t mfw_smem(int nf4)
 {
-    return (size_t)nf4 * 128 * (4 * sizeof(float2) + 3 * sizeof(float) + (kCgThreads / 32) * sizeof(float2));
+    return (size_t)nf4 * 128 * (4 * sizeof(float2) + 3 * sizeof(float) + (kMfwThreads / 32) * sizeof(float2));
 }
 
 template <int NF4>
-__global__ void __launch_bounds__(kCgThreads, 1) newton_mfw_cg_kernel(const __grid_constant__ MfwArgs A)
+__global__ void __launch_bounds__(kMfwThreads, 1) newton_mfw_cg_kernel(const __grid_constant__ MfwArgs A)
 {
     extern __shared__ float4 mw_sm4[];
     constexpr int QW = NF4 * 128;   // padded width: NF4 float4 per lane
@@ -385,7 +386,7 @@ __global__ void __launch_bounds__(kCgThreads, 1) newton_mfw_cg_kernel(const __gr
     float *Dh = reinterpret_cast<float *>(Hv + QW), *Dl = Dh + QW, *Rf = Dl + QW;
     float2 *wb = reinterpret_cast<float2 *>(Rf + QW);                  // [nw][QW] per-warp sums of a pass
     float2 *APv = wb, *Yv = wb + QW, *Zv = Yv + QW, *ROv = Zv + QW;    // the same memory between passes
-    __shared__ float2 red[kCgThreads / 32];
+    __shared__ float2 red[kMfwThreads / 32];
 
     for (int j = tid; j < QW; j += blockDim.x) {
         float2 r = make_float2(0.f, 0.f);
@@ -456,46 +457,58 @@ __global__ void __launch_bounds__(kCgThreads, 1) newton_mfw_cg_kernel(const __gr
             const long long per = (A.p + G - 1) / G;
             const long long rbeg = (long long)b * per;
             const long long rend = rbeg + per < A.p ? rbeg + per : A.p;
+            // the row's dot with d (Dot2, butterfly), then its share of X_J't
+            auto row_step = [&](const float4 (&xv)[NF4]) {
+                float s = 0.f, cc = 0.f;
+#pragma unroll
+                for (int f = 0; f < NF4; ++f) {
+                    const int c = lane + 32 * f;
+                    const float4 dh = Dh4[c], dl = Dl4[c];   // zero beyond q
+                    dot2_step(xv[f].x, make_float2(dh.x, dl.x), s, cc);
+                    dot2_step(xv[f].y, make_float2(dh.y, dl.y), s, cc);
+                    dot2_step(xv[f].z, make_float2(dh.z, dl.z), s, cc);
+                    dot2_step(xv[f].w, make_float2(dh.w, dl.w), s, cc);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float s2 = __shfl_xor_sync(0xffffffffu, s, o), c2 = __shfl_xor_sync(0xffffffffu, cc, o);
+                    float sn, e;
+                    two_sum(s, s2, sn, e);
+                    s = sn;
+                    cc += c2 + e;
+                }
+                float th, tl;
+                two_sum(s, cc, th, tl);
+                const float2 t = make_float2(th, tl);
+#pragma unroll
+                for (int f = 0; f < NF4; ++f) {
+                    dot2_step(xv[f].x, t, as[4 * f + 0], ac[4 * f + 0]);
+                    dot2_step(xv[f].y, t, as[4 * f + 1], ac[4 * f + 1]);
+                    dot2_step(xv[f].z, t, as[4 * f + 2], ac[4 * f + 2]);
+                    dot2_step(xv[f].w, t, as[4 * f + 3], ac[4 * f + 3]);
+                }
+            };
+            auto load_row = [&](float4 (&xv)[NF4], int ii) {
+                const float4 *row = reinterpret_cast<const float4 *>(A.X + (long long)ii * q);
+#pragma unroll
+                for (int f = 0; f < NF4; ++f) {
+                    const int c = lane + 32 * f;
+                    xv[f] = (4 * c < q) ? __ldcs(row + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            };
+            // two rows in flight: the next row loads while this one is computed
+            float4 xa[NF4], xb[NF4];
             for (long long c0 = rbeg + (long long)warp * 32; c0 < rend; c0 += (long long)nw * 32) {
                 const int myi = (c0 + lane < rend) ? __ldg(&A.J[c0 + lane]) : 0;
                 const int here = (int)(rend - c0 < 32 ? rend - c0 : 32);
-                for (int u = 0; u < here; ++u) {
-                    const int ii = __shfl_sync(0xffffffffu, myi, u);
-                    const float4 *row = reinterpret_cast<const float4 *>(A.X + (long long)ii * q);
-                    float4 xv[NF4];
-#pragma unroll
-                    for (int f = 0; f < NF4; ++f) {
-                        const int c = lane + 32 * f;
-                        xv[f] = (4 * c < q) ? __ldcs(row + c) : make_float4(0.f, 0.f, 0.f, 0.f);
-                    }
-                    float s = 0.f, cc = 0.f;
-#pragma unroll
-                    for (int f = 0; f < NF4; ++f) {
-                        const int c = lane + 32 * f;
-                        const float4 dh = Dh4[c], dl = Dl4[c];   // zero beyond q
-                        dot2_step(xv[f].x, make_float2(dh.x, dl.x), s, cc);
-                        dot2_step(xv[f].y, make_float2(dh.y, dl.y), s, cc);
-                        dot2_step(xv[f].z, make_float2(dh.z, dl.z), s, cc);
-                        dot2_step(xv[f].w, make_float2(dh.w, dl.w), s, cc);
-                    }
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        const float s2 = __shfl_xor_sync(0xffffffffu, s, o), c2 = __shfl_xor_sync(0xffffffffu, cc, o);
-                        float sn, e;
-                        two_sum(s, s2, sn, e);
-                        s = sn;
-                        cc += c2 + e;
-                    }
-                    float th, tl;
-                    two_sum(s, cc, th, tl);
-                    const float2 t = make_float2(th, tl);
-#pragma unroll
-                    for (int f = 0; f < NF4; ++f) {
-                        dot2_step(xv[f].x, t, as[4 * f + 0], ac[4 * f + 0]);
-                        dot2_step(xv[f].y, t, as[4 * f + 1], ac[4 * f + 1]);
-                        dot2_step(xv[f].z, t, as[4 * f + 2], ac[4 * f + 2]);
-                        dot2_step(xv[f].w, t, as[4 * f + 3], ac[4 * f + 3]);
-                    }
+                load_row(xa, __shfl_sync(0xffffffffu, myi, 0));
+                for (int u = 0; u < here; u += 2) {
+                    const int ib = __shfl_sync(0xffffffffu, myi, (u + 1) & 31);
+                    const int ia = __shfl_sync(0xffffffffu, myi, (u + 2) & 31);
+                    if (u + 1 < here) load_row(xb, ib);
+                    row_step(xa);
+                    if (u + 2 < here) load_row(xa, ia);
+                    if (u + 1 < here) row_step(xb);
                 }
             }
             // warps in order -> the block partial (double-float)
@@ -604,12 +617,12 @@ cudaError_t launch_cg(const MfwArgs &a, int G, cudaStream_t st)
         attr = 1;
     }
     int occ = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, newton_mfw_cg_kernel<NF4>, kCgThreads, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, newton_mfw_cg_kernel<NF4>, kMfwThreads, smem);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
     MfwArgs aa = a;
     void *args[] = {&aa};
-    return cudaLaunchCooperativeKernel((const void *)newton_mfw_cg_kernel<NF4>, dim3(G), dim3(kCgThreads), args, smem,
+    return cudaLaunchCooperativeKernel((const void *)newton_mfw_cg_kernel<NF4>, dim3(G), dim3(kMfwThreads), args, smem,
                                        st);
 }
 
