@@ -40,13 +40,15 @@ __device__ __forceinline__ int ld_relaxed_i32(const int *p)
 // the counter needs no reset between launches.  The wait is bounded: after
 // 2^24 polls (seconds) it records DEV_TIMEOUT and returns false instead of spinning on.
 // Every block executes the same sequence of barriers.
-__device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err)
+// The same barrier over a group of G blocks of one cooperative launch (b = this
+// block's rank in the group, bar = the group's own counter).
+__device__ __forceinline__ bool group_barrier(unsigned *bar, int *err, int b, int G)
 {
     __syncthreads();
     __shared__ int ok_sh;
     if (threadIdx.x == 0) {
         int ok = 1;
-        unsigned add = (blockIdx.x == 0) ? (0x80000000u - (gridDim.x - 1u)) : 1u;
+        unsigned add = (b == 0) ? (0x80000000u - ((unsigned)G - 1u)) : 1u;
         __threadfence();
         unsigned old = atomicAdd(bar, add);
         // poll without sleeping: a sleep here is far coarser than the wait itself;
@@ -64,6 +66,11 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err)
     }
     __syncthreads();
     return ok_sh != 0;
+}
+
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err)
+{
+    return group_barrier(bar, err, (int)blockIdx.x, (int)gridDim.x);
 }
 
 __device__ __forceinline__ double warp_sum(double v)

@@ -107,6 +107,42 @@ struct PDArgs {
     ProjOut *out;
 };
 
+// The cooperative kernels of the wide Newton step (k_newton_wide.cu): the
+// preconditioner's set-up and the CG, for one problem by a whole launch or by
+// a group of blocks of a launch over several problems.
+struct MfwSetupArgs {
+    int q;
+    const float2 *Mf;      // M_pre (value, 0) pairs
+    float *Lg, *Dg, *Linv, *Pinv;
+    int *fflag;
+    unsigned *bar;         // the problem's own barrier counter
+    int *err;
+    double *info;
+    const int *skip;       // this step keeps the preconditioner
+};
+struct MfwArgs {   // the CG
+    const float *X;
+    const int32_t *J;
+    long long p;
+    int q;
+    float2 sig, rp;        // sigma and 1 / p, double-float
+    const float2 *H;       // h = X_J'1, double-float
+    const float *Pinv;     // q x q, row-major
+    const double *g;
+    double *dv;
+    float eta, tau;
+    int maxit;
+    double *info;          // [0] CG steps, [1] |residual| ([2] the factor's shift, from the set-up)
+    int *err;
+    const double *vdot;    // nullable: Armijo quantities into rdots[2..4]
+    double *rdots;
+    int vc;                // chunks of the rows of J (the same for any number of blocks)
+    float2 *part;          // vc x q chunk partials of X_J'(X_J d)
+    float2 *yg;            // q: their sum
+    float *zg;             // q: Pinv r
+    unsigned *bar;
+};
+
 struct Work {
     // problem
     int64_t n = 0, q = 0;
@@ -174,6 +210,8 @@ struct Work {
     // set (n bits) and sigma the preconditioner in M was built for
     unsigned *mfw_mask = nullptr;
     struct MfwState *mfw_st = nullptr;
+    MfwSetupArgs mfw_s{};   // the step prepared by newton_mfw_prepare
+    MfwArgs mfw_c{};
     double *M = nullptr;      // q*q Newton matrix / Cholesky factor
     float *Lf = nullptr;      // q*(q+1) FP32 factor when it does not fit in shared memory
     float2 *Mf = nullptr;     // q*q FP32 (hi, lo) split of M (double-float CG operator)
@@ -320,6 +358,17 @@ cudaError_t launch_build_m_tc(Work &W, int G, const float *cpart, const float2 *
 cudaError_t launch_newton_mfw(Work &W, const int32_t *J, long long p, double sigma, const double *g, double *dv,
                               bool dots);
 cudaError_t newton_mfw_alloc(Work &W);
+// The wide step in two halves: prepare (reuse decision, Gram, M_pre, column
+// sums: ordinary launches) fills W.mfw_s / W.mfw_c; run launches the set-up and
+// the CG for this problem alone.  launch_newton_mfw is both.  The batched
+// solve prepares several problems and runs them together (newton_mfw_run_group:
+// one launch of the set-up and one of the CG, a group of blocks per problem;
+// the same result as running each alone).
+bool newton_is_wide(const Work &W, long long p);
+cudaError_t newton_mfw_prepare(Work &W, const int32_t *J, long long p, double sigma, const double *g, double *dv,
+                               bool dots);
+cudaError_t newton_mfw_run(Work &W);
+cudaError_t newton_mfw_run_group(Work &Wl, int q, const MfwSetupArgs *Ts_dev, const MfwArgs *Tc_dev, int ntask);
 // forget the preconditioner (the next wide Newton step builds one)
 cudaError_t newton_mfw_reset(Work &W);
 // G = sum_b cpart[b], h = sum_b hpart[b] over nb partials in FP64 (block

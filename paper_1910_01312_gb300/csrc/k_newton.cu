@@ -702,7 +702,7 @@ __global__ void __launch_bounds__(kCgThreads, 1) newton_bchol_kernel(int q, cons
     __shared__ float2 red[kCgThreads / 32];
     float2 *apg = xch, *zg = xch + kBcMaxQ;
     float shift = 0.f;
-    const int fr = bc_factor(q, Mf, Lg, Dg, fflag, bar, err, S, red, &shift);
+    const int fr = bc_factor(q, Mf, Lg, Dg, fflag, bar, err, S, red, &shift, (int)blockIdx.x, (int)gridDim.x);
     if (fr <= 0) {
         if (fr == 0 && b == 0 && tid == 0) set_err(err, DEV_CHOL);
         return;
@@ -863,6 +863,14 @@ static long long mfw_min_p()
     }
     return v;
 }
+// launch_newton takes the wide path of k_newton_wide.cu
+bool newton_is_wide(const Work &W, long long p)
+{
+    const int q = (int)W.q;
+    return !W.csr && W.precision == 1 && W.xf32 && W.mfw_st && q > kCgMaxQ && q <= kBcMaxQ && q % 16 == 0 &&
+           p > mfw_min_p();
+}
+
 constexpr int kMfSample = 2048;
 constexpr int kMfMaxPass = 6;
 constexpr int kMfThreads = 512;
@@ -1507,7 +1515,7 @@ cudaError_t launch_newton(Work &W, const int32_t *J, long long p_host, const lon
     if (mixed && W.mf_st && q <= kCgMaxQ && q % 4 == 0 && p_host > mf_min_p())
         return launch_newton_mf(W, J, p_host, sigma, g, dv, dots);
     if (mixed && W.mfw_st && q > kCgMaxQ && q <= kBcMaxQ && q % 16 == 0 && p_host > mfw_min_p())
-        return launch_newton_mfw(W, J, p_host, sigma, g, dv, dots);
+        return launch_newton_mfw(W, J, p_host, sigma, g, dv, dots);   // the same condition as newton_is_wide
     // double-float partials are summed in one chain per element: one split per SM
     if (mixed && ks > W.nsm) ks = W.nsm;
     if (ks < 1) ks = 1;

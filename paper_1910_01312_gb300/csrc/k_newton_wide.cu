@@ -49,17 +49,24 @@ constexpr int kWdBlk = 128;   // diagonal tile of the inverse factor
 constexpr int kMfwThreads = 256;   // CG kernel: 8 warps, up to 255 registers (two rows in flight per warp)
 constexpr int kWdCols = 8;    // columns of Pinv one block solves together
 
-__global__ void __launch_bounds__(kCgThreads, 1) newton_mfw_setup_kernel(int q, const float2 *__restrict__ Mf,
-                                                                      float *__restrict__ Lg, float *__restrict__ Dg,
-                                                                      float *__restrict__ Linv,
-                                                                      float *__restrict__ Pinv, int *fflag,
-                                                                      unsigned *bar, int *err, double *info,
-                                                                      const int *skip)
+
+// The set-up of one problem by G blocks (b = this block's rank): a whole
+// cooperative launch, or one group of a launch over several problems.  Every
+// step's arithmetic is the same whatever G is (tiles, rows and columns are
+// computed by whichever block takes them, in the same order).
+__device__ void mfw_setup_body(const MfwSetupArgs &A, const int b, const int G)
 {
-    if (__ldcg(skip)) return;   // the same value in every block: no barrier is taken
+    const int q = A.q;
+    const float2 *__restrict__ Mf = A.Mf;
+    float *__restrict__ Lg = A.Lg;
+    float *__restrict__ Dg = A.Dg;
+    float *__restrict__ Linv = A.Linv;
+    float *__restrict__ Pinv = A.Pinv;
+    unsigned *bar = A.bar;
+    int *err = A.err;
+    if (__ldcg(A.skip)) return;   // the same value in every block of the group: no barrier is taken
     extern __shared__ float4 cg_sm4[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    const int G = gridDim.x;
     CgSmem S;   // one 128 x 128 tile's packed factor; the region of M holds the work arrays
     S.M = reinterpret_cast<float2 *>(cg_sm4);
     S.L = reinterpret_cast<float *>(S.M + kBcNb * kBcNb);
@@ -67,16 +74,16 @@ __global__ void __launch_bounds__(kCgThreads, 1) newton_mfw_setup_kernel(int q, 
     S.t = S.D + (kBcNb / kPb) * kPb * kPb;
     __shared__ float2 red[kCgThreads / 32];
     float shift = 0.f;
-    const int fr = bc_factor(q, Mf, Lg, Dg, fflag, bar, err, S, red, &shift);
+    const int fr = bc_factor(q, Mf, Lg, Dg, A.fflag, bar, err, S, red, &shift, b, G);
     if (fr <= 0) {
-        if (fr == 0 && blockIdx.x == 0 && tid == 0) set_err(err, DEV_CHOL);
+        if (fr == 0 && b == 0 && tid == 0) set_err(err, DEV_CHOL);
         return;
     }
-    if (blockIdx.x == 0 && tid == 0 && info) info[2] = shift;
+    if (b == 0 && tid == 0 && A.info) A.info[2] = shift;
     const int nblk = (q + kWdBlk - 1) / kWdBlk;
 
     // (1) Y_tt = L_tt^{-1} for the diagonal tiles (zero above the diagonal)
-    for (int tb = blockIdx.x; tb < nblk; tb += G) {
+    for (int tb = b; tb < nblk; tb += G) {
         const int kb = tb * kWdBlk;
         const int nbk = q - kb < kWdBlk ? q - kb : kWdBlk;
         const int qpk = (nbk + 31) & ~31;
@@ -96,7 +103,7 @@ __global__ void __launch_bounds__(kCgThreads, 1) newton_mfw_setup_kernel(int q, 
         }
         __syncthreads();
     }
-    if (!grid_barrier(bar, err)) return;
+    if (!group_barrier(bar, err, b, G)) return;
 
     // (2) columns c of Pinv: L y = e_c by block rows (T = E_i - L_i,<i Y_<i,
     // Y_i = Y_ii T), then L' z = y backwards (T = Y_i - L_>i,i' Z_>i, Z_i = Y_ii' T)
@@ -106,7 +113,7 @@ __global__ void __launch_bounds__(kCgThreads, 1) newton_mfw_setup_kernel(int q, 
     float *P4 = T + kWdCols * kWdBlk;            // [slices][kWdCols][kWdBlk] partial sums
     const int nsl = blockDim.x / kWdBlk;         // column-parallel layout: jj fast, slice sl
     const int jj = tid % kWdBlk, sl = tid / kWdBlk;
-    for (long long base = blockIdx.x; base < q; base += (long long)kWdCols * G) {
+    for (long long base = b; base < q; base += (long long)kWdCols * G) {
         int cm[kWdCols];
 #pragma unroll
         for (int m = 0; m < kWdCols; ++m) cm[m] = (base + (long long)m * G < q) ? (int)(base + (long long)m * G) : -1;
@@ -207,6 +214,20 @@ __global__ void __launch_bounds__(kCgThreads, 1) newton_mfw_setup_kernel(int q, 
         }
         __syncthreads();
     }
+}
+
+__global__ void __launch_bounds__(kCgThreads, 1) newton_mfw_setup_kernel(const __grid_constant__ MfwSetupArgs A)
+{
+    mfw_setup_body(A, (int)blockIdx.x, (int)gridDim.x);
+}
+
+// several problems: groups of Gp consecutive blocks, group g sets up problem g
+__global__ void __launch_bounds__(kCgThreads, 1) newton_mfw_setup_group_kernel(const MfwSetupArgs *__restrict__ T,
+                                                                            int ntask, int Gp)
+{
+    const int g = (int)blockIdx.x / Gp;
+    if (g >= ntask) return;
+    mfw_setup_body(T[g], (int)blockIdx.x - g * Gp, Gp);
 }
 
 constexpr double kMfwReuseFrac = 0.01;   // changed rows of J, relative to p, that keep the preconditioner
@@ -345,27 +366,6 @@ __global__ void __launch_bounds__(256) mfw_colsum_kernel(const float *__restrict
     if (threadIdx.x == 0) st->done = 0u;
 }
 
-struct MfwArgs {
-    const float *X;
-    const int32_t *J;
-    long long p;
-    int q;
-    float2 sig, rp;        // sigma and 1 / p, double-float
-    const float2 *H;       // h = X_J'1, double-float
-    const float *Pinv;     // q x q, row-major
-    const double *g;
-    double *dv;
-    float eta, tau;
-    int maxit;
-    double *info;          // [0] CG steps, [1] |residual| ([2] the factor's shift, from the set-up)
-    int *err;
-    const double *vdot;    // nullable: Armijo quantities into rdots[2..4]
-    double *rdots;
-    float2 *part;          // gridDim.x x q block partials of X_J'(X_J d)
-    float2 *yg;            // q: their sum
-    float *zg;             // q: Pinv r
-    unsigned *bar;
-};
 
 // dynamic shared memory of newton_mfw_cg_kernel<NF4>
 constexpr size_t mfw_smem(int nf4)
@@ -373,13 +373,16 @@ constexpr size_t mfw_smem(int nf4)
     return (size_t)nf4 * 128 * (4 * sizeof(float2) + 3 * sizeof(float) + (kMfwThreads / 32) * sizeof(float2));
 }
 
+// The CG of one problem by G blocks (b = this block's rank).  The rows of J
+// are cut into A.vc chunks whatever G is: a block takes chunks b, b + G, ...
+// and each chunk's partial, and the sum of the partials in chunk order, are the
+// same for any G -- so the result is too.
 template <int NF4>
-__global__ void __launch_bounds__(kMfwThreads, 1) newton_mfw_cg_kernel(const __grid_constant__ MfwArgs A)
+__device__ void mfw_cg_body(const MfwArgs &A, const int b, const int G)
 {
     extern __shared__ float4 mw_sm4[];
     constexpr int QW = NF4 * 128;   // padded width: NF4 float4 per lane
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    const int b = blockIdx.x, G = gridDim.x;
     const int q = A.q;
     float2 *Xv = reinterpret_cast<float2 *>(mw_sm4);
     float2 *Rv = Xv + QW, *Dv = Rv + QW, *Hv = Dv + QW;
@@ -424,7 +427,7 @@ __global__ void __launch_bounds__(kMfwThreads, 1) newton_mfw_cg_kernel(const __g
             s = warp_sumf(s);
             if (lane == 0) A.zg[i] = s;
         }
-        if (!grid_barrier(A.bar, A.err)) return false;
+        if (!group_barrier(A.bar, A.err, b, G)) return false;
         for (int j = tid; j < QW; j += blockDim.x) Zv[j] = make_float2(j < q ? __ldcg(&A.zg[j]) : 0.f, 0.f);
         __syncthreads();
         return true;
@@ -449,13 +452,13 @@ __global__ void __launch_bounds__(kMfwThreads, 1) newton_mfw_cg_kernel(const __g
     }
     const float4 *Dh4 = reinterpret_cast<const float4 *>(Dh), *Dl4 = reinterpret_cast<const float4 *>(Dl);
     while (go && it < A.maxit) {
-        // ---- y_b = X_Jb'(X_Jb d) over this block's rows ----
-        {
+        // ---- the chunk partials y_c = X_Jc'(X_Jc d) of this block's chunks ----
+        for (int ch = b; ch < A.vc; ch += G) {
             float as[4 * NF4], ac[4 * NF4];
 #pragma unroll
             for (int k = 0; k < 4 * NF4; ++k) as[k] = ac[k] = 0.f;
-            const long long per = (A.p + G - 1) / G;
-            const long long rbeg = (long long)b * per;
+            const long long per = (A.p + A.vc - 1) / A.vc;
+            const long long rbeg = (long long)ch * per;
             const long long rend = rbeg + per < A.p ? rbeg + per : A.p;
             // the row's dot with d (Dot2, butterfly), then its share of X_J't
             auto row_step = [&](const float4 (&xv)[NF4]) {
@@ -528,23 +531,24 @@ __global__ void __launch_bounds__(kMfwThreads, 1) newton_mfw_cg_kernel(const __g
                 for (int w = 0; w < nw; ++w) df_acc(s, c, wb[w * QW + j].x, wb[w * QW + j].y);
                 float hi, lo;
                 two_sum(s, c, hi, lo);
-                A.part[(size_t)b * q + j] = make_float2(hi, lo);
+                A.part[(size_t)ch * q + j] = make_float2(hi, lo);
             }
-            if (!grid_barrier(A.bar, A.err)) return;
+            __syncthreads();   // wb is written again by the next chunk
         }
-        // ---- y = sum of the block partials in block order, by column slices ----
+        if (!group_barrier(A.bar, A.err, b, G)) return;
+        // ---- y = sum of the chunk partials in chunk order, by column slices ----
         {
             const int cs = (q + G - 1) / G;
             for (int k = warp; k < cs; k += nw) {
                 const int j = b * cs + k;
                 if (j >= q) break;
                 float2 s = make_float2(0.f, 0.f);
-                for (int bb = lane; bb < G; bb += 32) s = dfx_add(s, __ldcg(&A.part[(size_t)bb * q + j]));
+                for (int bb = lane; bb < A.vc; bb += 32) s = dfx_add(s, __ldcg(&A.part[(size_t)bb * q + j]));
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) s = dfx_add(s, shfl_xor_f2(s, o));
                 if (lane == 0) A.yg[j] = s;
             }
-            if (!grid_barrier(A.bar, A.err)) return;
+            if (!group_barrier(A.bar, A.err, b, G)) return;
         }
         for (int j = tid; j < QW; j += blockDim.x) Yv[j] = j < q ? __ldcg(&A.yg[j]) : make_float2(0.f, 0.f);
         __syncthreads();
@@ -606,27 +610,86 @@ __global__ void __launch_bounds__(kMfwThreads, 1) newton_mfw_cg_kernel(const __g
 }
 
 template <int NF4>
-cudaError_t launch_cg(const MfwArgs &a, int G, cudaStream_t st)
+__global__ void __launch_bounds__(kMfwThreads, 1) newton_mfw_cg_kernel(const __grid_constant__ MfwArgs A)
+{
+    mfw_cg_body<NF4>(A, (int)blockIdx.x, (int)gridDim.x);
+}
+
+// several problems (the same q): groups of Gp consecutive blocks
+template <int NF4>
+__global__ void __launch_bounds__(kMfwThreads, 1) newton_mfw_cg_group_kernel(const MfwArgs *__restrict__ T, int ntask,
+                                                                         int Gp)
+{
+    const int g = (int)blockIdx.x / Gp;
+    if (g >= ntask) return;
+    mfw_cg_body<NF4>(T[g], (int)blockIdx.x - g * Gp, Gp);
+}
+
+template <int NF4>
+cudaError_t cg_attr()
 {
     static int attr = 0;
-    const size_t smem = mfw_smem(NF4);
     if (!attr) {
-        const cudaError_t e =
-            cudaFuncSetAttribute(newton_mfw_cg_kernel<NF4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(newton_mfw_cg_kernel<NF4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)mfw_smem(NF4));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(newton_mfw_cg_group_kernel<NF4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)mfw_smem(NF4));
         if (e != cudaSuccess) return e;
         attr = 1;
     }
+    return cudaSuccess;
+}
+
+// one problem (T = nullptr: a) or ntask problems in groups of Gp blocks (T: device table)
+template <int NF4>
+cudaError_t launch_cg(const MfwArgs &a, const MfwArgs *T, int ntask, int Gp, int G, cudaStream_t st)
+{
+    const size_t smem = mfw_smem(NF4);
+    cudaError_t e = cg_attr<NF4>();
+    if (e != cudaSuccess) return e;
     int occ = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, newton_mfw_cg_kernel<NF4>, kMfwThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, newton_mfw_cg_kernel<NF4>, kMfwThreads, smem);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
-    MfwArgs aa = a;
-    void *args[] = {&aa};
-    return cudaLaunchCooperativeKernel((const void *)newton_mfw_cg_kernel<NF4>, dim3(G), dim3(kMfwThreads), args, smem,
-                                       st);
+    if (!T) {
+        MfwArgs aa = a;
+        void *args[] = {&aa};
+        return cudaLaunchCooperativeKernel((const void *)newton_mfw_cg_kernel<NF4>, dim3(G), dim3(kMfwThreads), args,
+                                           smem, st);
+    }
+    void *args[] = {(void *)&T, &ntask, &Gp};
+    return cudaLaunchCooperativeKernel((const void *)newton_mfw_cg_group_kernel<NF4>, dim3(ntask * Gp),
+                                       dim3(kMfwThreads), args, smem, st);
+}
+
+cudaError_t launch_cg_nf4(int q, const MfwArgs &a, const MfwArgs *T, int ntask, int Gp, int G, cudaStream_t st)
+{
+    switch ((q + 127) / 128) {
+    case 2: return launch_cg<2>(a, T, ntask, Gp, G, st);
+    case 3: return launch_cg<3>(a, T, ntask, Gp, G, st);
+    case 4: return launch_cg<4>(a, T, ntask, Gp, G, st);
+    case 5: return launch_cg<5>(a, T, ntask, Gp, G, st);
+    case 6: return launch_cg<6>(a, T, ntask, Gp, G, st);
+    case 7: return launch_cg<7>(a, T, ntask, Gp, G, st);
+    default: return launch_cg<8>(a, T, ntask, Gp, G, st);
+    }
 }
 
 int g_setup_attr = 0;
+
+cudaError_t setup_attr()
+{
+    if (!g_setup_attr) {
+        const int smem = (int)cg_fast_smem(kCgMaxQ);
+        cudaError_t e = cudaFuncSetAttribute(newton_mfw_setup_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(newton_mfw_setup_group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        g_setup_attr = 1;
+    }
+    return cudaSuccess;
+}
 
 // the reuse fraction in use (SVM_MFW_REUSE overrides it, 0 turns reuse off; for measurements)
 double mfw_reuse_frac()
@@ -668,14 +731,13 @@ cudaError_t newton_mfw_reset(Work &W)
 // W.part (consumed by build_m_tc), then W.part holds the 8 x 8 diagonal
 // inverses, the inverse tiles, the CG's exchange vectors and the factor's flag;
 // Pinv and h sit in W.M (unused by the mixed form), the factor in W.Lf.
-cudaError_t launch_newton_mfw(Work &W, const int32_t *J, long long p, double sigma, const double *g, double *dv,
-                              bool dots)
+cudaError_t newton_mfw_prepare(Work &W, const int32_t *J, long long p, double sigma, const double *g, double *dv,
+                               bool dots)
 {
     const int q = (int)W.q;
     if (q <= kCgMaxQ || q > kBcMaxQ || q % 16 != 0 || !W.xf32 || p < 1 || !W.mfw_st) return cudaErrorInvalidValue;
-    const int nf4 = (q + 127) / 128;
     const int nblk = (q + kWdBlk - 1) / kWdBlk;
-    const int G = W.nsm, Gc = 4 * W.nsm;   // CG blocks; column-sum blocks
+    const int Gc = 4 * W.nsm;   // column-sum blocks (and room for the W.nsm chunk partials of the CG)
     const size_t need = (size_t)q * kPb + (size_t)nblk * kWdBlk * kWdBlk + 2 * (size_t)Gc * q + 3 * (size_t)q + 4;
     if (need > 2 * W.part_len) return cudaErrorInvalidValue;
     double *info = W.red + 12;
@@ -706,29 +768,19 @@ cudaError_t launch_newton_mfw(Work &W, const int32_t *J, long long p, double sig
     const long long gcs = (p + 63) / 64 < Gc ? (p + 63) / 64 : Gc;
     mfw_colsum_kernel<<<(unsigned)gcs, 256, 0, W.st>>>((const float *)W.X, q, J, p, cgp, st, H);
     ++W.nlaunch;
-    // the factor and Pinv: every resident block
-    const size_t smem = cg_fast_smem(kCgMaxQ);
-    if (!g_setup_attr) {
-        e = cudaFuncSetAttribute(newton_mfw_setup_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        g_setup_attr = 1;
-    }
-    int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, newton_mfw_setup_kernel, kCgThreads, smem);
-    if (e != cudaSuccess) return e;
-    if (occ < 1) return cudaErrorInvalidConfiguration;
-    {
-        int qq = q;
-        const float2 *Mf = W.Mf;
-        float *Lg = W.Lf;
-        int *err = W.err;
-        unsigned *bar = W.bar;
-        void *args[] = {&qq, &Mf, &Lg, &Dg, &Linv, &Pinv, &fflag, &bar, &err, &info, (void *)&skip};
-        e = cudaLaunchCooperativeKernel((const void *)newton_mfw_setup_kernel, dim3(occ * W.nsm), dim3(kCgThreads),
-                                        args, smem, W.st);
-        if (e != cudaSuccess) return e;
-    }
-    MfwArgs a;
+    MfwSetupArgs &s = W.mfw_s;
+    s.q = q;
+    s.Mf = W.Mf;
+    s.Lg = W.Lf;
+    s.Dg = Dg;
+    s.Linv = Linv;
+    s.Pinv = Pinv;
+    s.fflag = fflag;
+    s.bar = W.bar;
+    s.err = W.err;
+    s.info = info;
+    s.skip = skip;
+    MfwArgs &a = W.mfw_c;
     a.X = (const float *)W.X;
     a.J = J;
     a.p = p;
@@ -746,21 +798,67 @@ cudaError_t launch_newton_mfw(Work &W, const int32_t *J, long long p, double sig
     a.err = W.err;
     a.vdot = dots ? W.v : nullptr;
     a.rdots = W.red;
+    a.vc = W.nsm;
     a.part = cgp;
     a.yg = yg;
     a.zg = zg;
     a.bar = W.bar;
-    switch (nf4) {
-    case 2: e = launch_cg<2>(a, G, W.st); break;
-    case 3: e = launch_cg<3>(a, G, W.st); break;
-    case 4: e = launch_cg<4>(a, G, W.st); break;
-    case 5: e = launch_cg<5>(a, G, W.st); break;
-    case 6: e = launch_cg<6>(a, G, W.st); break;
-    case 7: e = launch_cg<7>(a, G, W.st); break;
-    default: e = launch_cg<8>(a, G, W.st); break;
+    return cudaGetLastError();
+}
+
+cudaError_t newton_mfw_run(Work &W)
+{
+    cudaError_t e = setup_attr();
+    if (e != cudaSuccess) return e;
+    const size_t smem = cg_fast_smem(kCgMaxQ);
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, newton_mfw_setup_kernel, kCgThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    {
+        MfwSetupArgs sa = W.mfw_s;
+        void *args[] = {&sa};
+        e = cudaLaunchCooperativeKernel((const void *)newton_mfw_setup_kernel, dim3(occ * W.nsm), dim3(kCgThreads),
+                                        args, smem, W.st);
+        if (e != cudaSuccess) return e;
     }
-    W.nlaunch += 2;   // + the others, counted above and by their launchers
+    e = launch_cg_nf4((int)W.q, W.mfw_c, nullptr, 1, W.nsm, W.nsm, W.st);
+    W.nlaunch += 2;
     return e;
+}
+
+cudaError_t launch_newton_mfw(Work &W, const int32_t *J, long long p, double sigma, const double *g, double *dv,
+                              bool dots)
+{
+    const cudaError_t e = newton_mfw_prepare(W, J, p, sigma, g, dv, dots);
+    return e == cudaSuccess ? newton_mfw_run(W) : e;
+}
+
+// The prepared steps of ntask problems of one q (tables of their W.mfw_s /
+// W.mfw_c in device memory): the set-up and the CG each in launches of up to
+// nsm / 8 problems, a group of nsm / (problems in the launch) blocks each.
+cudaError_t newton_mfw_run_group(Work &Wl, int q, const MfwSetupArgs *Ts, const MfwArgs *Tc, int ntask)
+{
+    if (ntask < 1) return cudaSuccess;
+    if (q <= kCgMaxQ || q > kBcMaxQ || q % 16 != 0) return cudaErrorInvalidValue;
+    cudaError_t e = setup_attr();
+    if (e != cudaSuccess) return e;
+    const int per_launch = Wl.nsm / 8 > 0 ? Wl.nsm / 8 : 1;
+    const size_t smem = cg_fast_smem(kCgMaxQ);
+    const MfwArgs unused{};
+    for (int k0 = 0; k0 < ntask; k0 += per_launch) {
+        int nt = ntask - k0 < per_launch ? ntask - k0 : per_launch;
+        int Gp = Wl.nsm / nt;
+        const MfwSetupArgs *Tsk = Ts + k0;
+        void *args[] = {(void *)&Tsk, &nt, &Gp};
+        e = cudaLaunchCooperativeKernel((const void *)newton_mfw_setup_group_kernel, dim3(nt * Gp), dim3(kCgThreads),
+                                        args, smem, Wl.st);
+        if (e != cudaSuccess) return e;
+        e = launch_cg_nf4(q, unused, Tc + k0, nt, Gp, nt * Gp, Wl.st);
+        if (e != cudaSuccess) return e;
+        Wl.nlaunch += 2;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace svm

@@ -207,12 +207,13 @@ __device__ __forceinline__ float2 bc_dot(const float2 *a, const float2 *b, int q
 // one 128-panel's packed factor (cg_fast_smem(kCgMaxQ) bytes); red has one
 // slot per warp.  Returns 1 when factored (*shift_out = the shift used), 0
 // when every attempt failed, -1 when a grid barrier timed out; the same value
-// in every block.
+// in every block.  b, G: this block's rank and the number of blocks that
+// factor this matrix (a group of a larger cooperative launch, or all of it).
 static __device__ int bc_factor(int q, const float2 *__restrict__ Mf, float *__restrict__ Lg, float *__restrict__ Dg,
-                                int *fflag, unsigned *bar, int *err, CgSmem &S, float2 *red, float *shift_out)
+                                int *fflag, unsigned *bar, int *err, CgSmem &S, float2 *red, float *shift_out,
+                                int b, int G)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    const int b = blockIdx.x, G = gridDim.x;
     const int gw = b * nw + warp, ngw = G * nw;
     constexpr int kLdF = kBcNb + 1;                     // odd row stride: rows on distinct banks
     float *LF = reinterpret_cast<float *>(S.M);         // a 128-panel's diagonal block (kBcNb x kLdF)
@@ -237,7 +238,7 @@ static __device__ int bc_factor(int q, const float2 *__restrict__ Mf, float *__r
             if (j <= i) Lg[e] = Mf[e].x + (i == j ? shift : 0.f);
         }
         if (b == 0 && tid == 0) *fflag = 0;
-        if (!grid_barrier(bar, err)) return -1;
+        if (!group_barrier(bar, err, b, G)) return -1;
         bool bad = false;
         for (int kb = 0; kb < q && !bad; kb += kBcNb) {
             const int nbk = q - kb < kBcNb ? q - kb : kBcNb;
@@ -257,11 +258,11 @@ static __device__ int bc_factor(int q, const float2 *__restrict__ Mf, float *__r
                         Dg[(size_t)kb * kPb + e] = S.D[e];
                 }
             }
-            if (!grid_barrier(bar, err)) return -1;
+            if (!group_barrier(bar, err, b, G)) return -1;
             if (ld_relaxed_i32(fflag)) {
                 // every block has read the flag before block 0 clears it for the next attempt
                 bad = true;
-                if (!grid_barrier(bar, err)) return -1;
+                if (!group_barrier(bar, err, b, G)) return -1;
                 break;
             }
             if (kb + nbk >= q) break;
@@ -298,7 +299,7 @@ static __device__ int bc_factor(int q, const float2 *__restrict__ Mf, float *__r
                     if (j < nbk) Lg[(size_t)r * q + kb + j] = a[m];
                 }
             }
-            if (!grid_barrier(bar, err)) return -1;
+            if (!group_barrier(bar, err, b, G)) return -1;
             // (3) trailing update A_ij -= L_i,panel L_j,panel' over 64 x 64 tiles, j <= i
             {
                 const int t0 = kb + nbk;
@@ -355,7 +356,7 @@ static __device__ int bc_factor(int q, const float2 *__restrict__ Mf, float *__r
                     __syncthreads();
                 }
             }
-            if (!grid_barrier(bar, err)) return -1;
+            if (!group_barrier(bar, err, b, G)) return -1;
         }
         factored = !bad;
         if (!factored) shift = (shift == 0.f) ? 1e-7f * maxdiag : shift * 100.f;

@@ -71,6 +71,11 @@ struct svm_ssnalm {
     long long batch_ticks = 0;
     NewtonTask *nt_host = nullptr, *nt_dev = nullptr;   // batched Newton steps (pinned / device table)
     int nt_cap = 0;
+    // batched wide Newton steps (128 < q <= 1024): the prepared set-up and CG
+    // arguments of each problem (pinned / device tables)
+    MfwSetupArgs *wt_s_host = nullptr, *wt_s_dev = nullptr;
+    MfwArgs *wt_c_host = nullptr, *wt_c_dev = nullptr;
+    int wt_cap = 0;
     svm_mlp_t *wsm = nullptr;   // warm-start network of svm_ssnalm_set_warmstart_model (owned)
     // batched projections: a sub-handle of a batched solve records its
     // double-float projection instead of launching it (proj_defer), and the
@@ -191,10 +196,12 @@ extern "C" void svm_ssnalm_destroy(svm_ssnalm_t *h)
     if (h->W.st) cudaStreamSynchronize(h->W.st);
     for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
     for (svm_ssnalm *sb : h->subs) svm_ssnalm_destroy(sb);
-    void *bp[] = {h->bat_cnt, h->bat_y, h->bat_a, h->bat_w, h->nt_dev};
+    void *bp[] = {h->bat_cnt, h->bat_y, h->bat_a, h->bat_w, h->nt_dev, h->wt_s_dev, h->wt_c_dev};
     for (void *p : bp)
         if (p) cudaFree(p);
     if (h->nt_host) cudaFreeHost(h->nt_host);
+    if (h->wt_s_host) cudaFreeHost(h->wt_s_host);
+    if (h->wt_c_host) cudaFreeHost(h->wt_c_host);
     if (h->pd_dev) cudaFree(h->pd_dev);
     if (h->pd_host) cudaFreeHost(h->pd_host);
     svm_mlp_destroy(h->wsm);
@@ -591,6 +598,7 @@ struct Run {
     bool defer_newton = false;   // batched: leave a small-free-set Newton step to the batch launch
     bool has_task = false;       // ... and this phase's step was left there
     NewtonTask task;
+    bool has_wtask = false;      // a wide step was prepared and left to the batch launch
     int cont = 0;                // batched: what follows a recorded projection (a RunCont)
 };
 
@@ -711,6 +719,7 @@ static svm_status run_pre(Run &r)
     const bool df = W.df;
     r.mv = MvReq();
     r.has_task = false;
+    r.has_wtask = false;
     switch (r.ph) {
     case RP_INIT: {
         // lambda warm starts restart at 0
@@ -773,8 +782,12 @@ static svm_status run_pre(Run &r)
         const double sigma = r.sigma;
         const int cur = r.cur;
         r.has_task = r.defer_newton && newton_task(W, W.pb[cur].J, p, sigma, W.g, W.dv, true, &r.task);
+        r.has_wtask = !r.has_task && r.defer_newton && newton_is_wide(W, p);
         if (r.has_task) {
             h->kcalls[TK_NEWTON]++;
+        } else if (r.has_wtask) {
+            // Gram, M_pre and the column sums now; the set-up and the CG in the batch launch
+            CK(timed(h, TK_NEWTON, [&] { return newton_mfw_prepare(W, W.pb[cur].J, p, sigma, W.g, W.dv, true); }));
         } else {
             CK(timed(h, TK_NEWTON, [&] {
                 return launch_newton(W, W.pb[cur].J, p, &W.pout[1 + cur].p, sigma, W.g, W.dv, true);
@@ -1293,6 +1306,25 @@ extern "C" svm_status svm_ssnalm_solve_batch(svm_ssnalm_t *h, int32_t B, const i
         }
         h->nt_cap = B;
     }
+    if (B > h->wt_cap) {
+        if (h->wt_s_dev) cudaFree(h->wt_s_dev);
+        if (h->wt_c_dev) cudaFree(h->wt_c_dev);
+        if (h->wt_s_host) cudaFreeHost(h->wt_s_host);
+        if (h->wt_c_host) cudaFreeHost(h->wt_c_host);
+        h->wt_s_dev = nullptr;
+        h->wt_c_dev = nullptr;
+        h->wt_s_host = nullptr;
+        h->wt_c_host = nullptr;
+        h->wt_cap = 0;
+        if (cudaMalloc(&h->wt_s_dev, sizeof(MfwSetupArgs) * B) != cudaSuccess ||
+            cudaMalloc(&h->wt_c_dev, sizeof(MfwArgs) * B) != cudaSuccess ||
+            cudaMallocHost(&h->wt_s_host, sizeof(MfwSetupArgs) * B) != cudaSuccess ||
+            cudaMallocHost(&h->wt_c_host, sizeof(MfwArgs) * B) != cudaSuccess) {
+            h->err = "batch: allocation of the wide Newton tables failed";
+            return SVM_ERR_OOM;
+        }
+        h->wt_cap = B;
+    }
     // the projections of a phase in one launch (one cluster per problem) when
     // the problems fit the cluster form; each problem's result is bit-identical
     // to a single solve's, which runs the same cluster kernel
@@ -1371,6 +1403,20 @@ extern "C" svm_status svm_ssnalm_solve_batch(svm_ssnalm_t *h, int32_t B, const i
             CK(cudaMemcpyAsync(h->nt_dev, h->nt_host, sizeof(NewtonTask) * ntask, cudaMemcpyHostToDevice, W.st));
             CK(timed(h, TK_NEWTON, [&] { return launch_newton_batch(W, h->nt_dev, ntask, ks_max); }));
             h->kcalls[TK_NEWTON]--;   // counted per problem when the steps were deferred
+        }
+        // the prepared wide Newton steps: their set-ups in one launch, their CGs in another
+        int nwt = 0;
+        for (int b = 0; b < B; ++b) {
+            if (!live[b] || !runs[b].has_wtask) continue;
+            h->wt_s_host[nwt] = h->subs[b]->W.mfw_s;
+            h->wt_c_host[nwt] = h->subs[b]->W.mfw_c;
+            ++nwt;
+        }
+        if (nwt > 0) {
+            CK(cudaMemcpyAsync(h->wt_s_dev, h->wt_s_host, sizeof(MfwSetupArgs) * nwt, cudaMemcpyHostToDevice, W.st));
+            CK(cudaMemcpyAsync(h->wt_c_dev, h->wt_c_host, sizeof(MfwArgs) * nwt, cudaMemcpyHostToDevice, W.st));
+            CK(timed(h, TK_NEWTON, [&] { return newton_mfw_run_group(W, q, h->wt_s_dev, h->wt_c_dev, nwt); }));
+            h->kcalls[TK_NEWTON]--;
         }
         if (!items.empty()) {
             const svm_status st = batch_matvec(h, items);

@@ -125,6 +125,28 @@ def test_batch_wide_features_large_free_sets():
         assert oracle.kkt(X, Y[b], Cs[b], A[b]) <= 1e-6
 
 
+def test_batch_grouped_wide_newton_steps():
+    """q = 144 (above the one-block Newton solver's 128): every Newton step
+    takes the wide path, and the batch runs the steps of all problems that
+    reach one in the same phase together -- the preconditioner set-ups in one
+    cooperative launch, the CGs in another, a group of blocks per problem, at
+    most one problem per eight SMs in a launch (24 problems here, so a phase
+    can take two launches of each).  The CG's row chunks do not depend
+    on how many blocks a problem gets, so every problem stays bit-identical to
+    its single solve."""
+    X, Y, Cs = datagen.ovr_path(4, n=3000, q=144, n_classes=12, n_C=2, C_lo=-1.0, C_hi=0.5)
+    Xd = dev(X)
+    s, st, rs, A, W = batch(Xd, Y, Cs, P.PREC_MIXED)
+    s.close()
+    assert st == P.OK, [r["status"] for r in rs]
+    for b in range(len(Cs)):
+        r1, a1, w1 = single(Xd, Y[b], Cs[b], P.PREC_MIXED)
+        assert (rs[b]["outer_iters"], rs[b]["inner_iters_total"]) == (r1["outer_iters"], r1["inner_iters_total"])
+        np.testing.assert_array_equal(A[b], a1)
+        np.testing.assert_array_equal(W[b], w1)
+        assert oracle.kkt(X, Y[b], Cs[b], A[b]) <= 1e-6
+
+
 def test_batch_degenerate_member_and_invalid_labels():
     X, Y, Cs = datagen.ovr_path(2, n=1500, q=32, n_classes=2, n_C=2, C_lo=-1.0, C_hi=0.0)
     Y = np.concatenate([Y, np.ones((1, Y.shape[1]), np.int8)])
