@@ -237,12 +237,15 @@ svm_status svm_op_newton(svm_ssnalm_t *h, const int32_t *J, int64_t p, double si
  * preconditioner (Proposition 3.5: the reduced matrix I + sigma (G - h h'/p)):
  * G = X_J' X_J (q x q, row-major FP64, device) and hsum = X_J' 1 (q, FP64,
  * device), J device int32 with p row indices (any order; p = 0 gives zeros).
- * G is formed on the tcgen05 tensor cores with TF32 products (10-bit
- * mantissa) and FP32 sums within a block, blocks added in FP64; hsum is exact
- * to double-float accuracy.  q <= 128: one 128 x q accumulator per block;
- * 128 < q <= 1024: (128-feature x 256-feature) tiles of the lower triangle,
- * G symmetrised from it.  Dense FP32 X with q % 16 == 0 and q <= 1024 only
- * (else SVM_ERR_UNSUPPORTED).  Synchronises the stream. */
+ * G is formed on the tcgen05 tensor cores with FP32 sums within a block,
+ * blocks added in FP64; hsum is exact to double-float accuracy.  q <= 128:
+ * TF32 products (10-bit mantissa), one 128 x q accumulator per block;
+ * 128 < q <= 1024: FP16 products of an FP16 copy of X scaled per feature by
+ * a power of two (11-bit significand; the copy, n x q x 2 bytes, is made on
+ * the first call and kept with the handle), (128-feature x 256-feature)
+ * tiles of the lower triangle, G symmetrised from it.  Dense FP32 X with
+ * q % 16 == 0 and q <= 1024 only (else SVM_ERR_UNSUPPORTED).  Synchronises
+ * the stream. */
 svm_status svm_op_gram(svm_ssnalm_t *h, const int32_t *J, int64_t p, double *G, double *hsum);
 
 /* Relative KKT residual of eq. (4.1) at alpha (n, device).  *kkt and *lambda

@@ -212,6 +212,13 @@ struct Work {
     struct MfwState *mfw_st = nullptr;
     MfwSetupArgs mfw_s{};   // the step prepared by newton_mfw_prepare
     MfwArgs mfw_c{};
+    // the FP16 copy of a dense FP32 X for the wide Gram (made on first use,
+    // or borrowed from the handle of a batched solve): X16_if = fl16(x_if
+    // 2^k_f), the per-feature exponents k_f, and its tensor map (a CUtensorMap)
+    void *x16 = nullptr;
+    int *x16_k = nullptr;
+    bool x16_own = false;
+    alignas(64) unsigned char xmap[128] = {};
     double *M = nullptr;      // q*q Newton matrix / Cholesky factor
     float *Lf = nullptr;      // q*(q+1) FP32 factor when it does not fit in shared memory
     float2 *Mf = nullptr;     // q*q FP32 (hi, lo) split of M (double-float CG operator)
@@ -340,19 +347,28 @@ cudaError_t newton_mf_alloc(Work &W);
 int gram_umma_blocks(const Work &W);
 size_t gram_umma_part_floats(const Work &W);
 cudaError_t launch_gram_umma(Work &W, const int32_t *J, long long p, float *cpart, float2 *hpart);
-// The same Gram for 128 < q <= 1024 (q % 16 == 0), split over (row tile,
-// column chunk) pairs and KS row splits: cpart[ks] (q x q, the entries b <= a
-// and some above) and hpart[ks] (q double-float column sums) for ks < KS;
-// gram_wide_splits(W, p) is the KS that fits the workspace.
+// The same Gram for 128 < q <= 1024 (q % 16 == 0) from the FP16 copy of X,
+// split over (row tile, column chunk) pairs and KS row splits: cpart[ks] (q x
+// q, the entries b <= a and some above) for ks < KS (the column sums come
+// from launch_colsum); gram_wide_splits(W, p) is the KS that fits the
+// workspace.
 int gram_wide_pairs(int q);
 int gram_wide_splits(const Work &W, long long p);
 // skip (nullable, device): when *skip != 0 the launch does nothing.
-cudaError_t launch_gram_umma_wide(Work &W, const int32_t *J, long long p, int KS, float *cpart, float2 *hpart,
+cudaError_t launch_gram_umma_wide(Work &W, const int32_t *J, long long p, int KS, float *cpart,
                                   const int *skip = nullptr);
-// M_pre = I + sigma (G - h h'/p) into W.Mf from G partials of TF32 Grams
-// (FP32, G of them) and double-float column sums; h itself into H (nullable)
-cudaError_t launch_build_m_tc(Work &W, int G, const float *cpart, const float2 *hpart, long long p, double sigma,
-                              float2 *H, const int *skip = nullptr);
+// the FP16 copy of X for launch_gram_umma_wide (a no-op once made or borrowed)
+cudaError_t x16_prepare(Work &W);
+// H = X_J' 1 exactly (double-float, column sums in row order within each of
+// nb blocks, the blocks' sums in block order); part: nb x q float2 scratch,
+// nb = colsum_blocks(W, p) at most max_blocks
+int colsum_blocks(const Work &W, long long p, int max_blocks);
+cudaError_t launch_colsum(Work &W, const int32_t *J, long long p, int nb, float2 *part, float2 *H);
+// M_pre = I + sigma (G - h h'/p) into W.Mf from G partials of tensor-core
+// Grams (FP32) and Gh partials of the double-float column sums; h itself into
+// H (nullable)
+cudaError_t launch_build_m_tc(Work &W, int G, const float *cpart, int Gh, const float2 *hpart, long long p,
+                              double sigma, float2 *H, const int *skip = nullptr);
 // The Newton step for a large free set at 128 < q <= 1024 (k_newton_wide.cu)
 // and its workspace (allocated at create for the mixed form)
 cudaError_t launch_newton_mfw(Work &W, const int32_t *J, long long p, double sigma, const double *g, double *dv,
@@ -373,7 +389,8 @@ cudaError_t newton_mfw_run_group(Work &Wl, int q, const MfwSetupArgs *Ts_dev, co
 cudaError_t newton_mfw_reset(Work &W);
 // G = sum_b cpart[b], h = sum_b hpart[b] over nb partials in FP64 (block
 // order), both triangles of G from the partials' lower one
-cudaError_t launch_gram_umma_sum(Work &W, int nb, const float *cpart, const float2 *hpart, double *G, double *h);
+cudaError_t launch_gram_umma_sum(Work &W, int nb, const float *cpart, int nbh, const float2 *hpart, double *G,
+                                double *h);
 
 // CSR layout: structure/value checks (dev_flags[0]: structure, [1]: non-finite),
 // the CSC copy and column tasks, and the three products of the method

@@ -1234,9 +1234,9 @@ __global__ void __launch_bounds__(kMfThreads) newton_mf_pass_kernel(
 // the factor (and h itself, double-float, to H when H != nullptr).
 // Eight lanes per entry sum interleaved eighths of the partials, combined by
 // shuffles in a fixed order.
-__global__ void build_m_tc_kernel(int q, int G, const float *__restrict__ cpart, const float2 *__restrict__ hpart,
-                                  float2 rp, float2 sig, float2 *__restrict__ Mf, float2 *__restrict__ H,
-                                  const int *skip)
+__global__ void build_m_tc_kernel(int q, int G, const float *__restrict__ cpart, int Gh,
+                                  const float2 *__restrict__ hpart, float2 rp, float2 sig, float2 *__restrict__ Mf,
+                                  float2 *__restrict__ H, const int *skip)
 {
     if (skip && __ldcg(skip)) return;
     const int lane = threadIdx.x & 31, sub = lane & 7;
@@ -1251,8 +1251,9 @@ __global__ void build_m_tc_kernel(int q, int G, const float *__restrict__ cpart,
         float2 ha = make_float2(0.f, 0.f), hb = ha;
         if (valid && b <= a) {
 #pragma unroll 4
-            for (int k = sub; k < G; k += 8) {
-                gs += __ldcg(&cpart[(size_t)k * q * q + t]);
+            for (int k = sub; k < G; k += 8) gs += __ldcg(&cpart[(size_t)k * q * q + t]);
+#pragma unroll 4
+            for (int k = sub; k < Gh; k += 8) {
                 ha = dfx_add(ha, __ldcg(&hpart[(size_t)k * q + a]));
                 hb = dfx_add(hb, __ldcg(&hpart[(size_t)k * q + b]));
             }
@@ -1294,11 +1295,11 @@ static float2 split2(double v)
     return make_float2(hi, (float)(v - (double)hi));
 }
 
-cudaError_t launch_build_m_tc(Work &W, int G, const float *cpart, const float2 *hpart, long long p, double sigma,
-                              float2 *H, const int *skip)
+cudaError_t launch_build_m_tc(Work &W, int G, const float *cpart, int Gh, const float2 *hpart, long long p,
+                              double sigma, float2 *H, const int *skip)
 {
-    build_m_tc_kernel<<<W.nsm * 2, 256, 0, W.st>>>((int)W.q, G, cpart, hpart, split2(1.0 / (double)p), split2(sigma),
-                                                   W.Mf, H, skip);
+    build_m_tc_kernel<<<W.nsm * 2, 256, 0, W.st>>>((int)W.q, G, cpart, Gh, hpart, split2(1.0 / (double)p),
+                                                   split2(sigma), W.Mf, H, skip);
     ++W.nlaunch;
     return cudaGetLastError();
 }
@@ -1317,8 +1318,8 @@ static cudaError_t launch_newton_mf(Work &W, const int32_t *J, long long p, doub
         float2 *hpart = reinterpret_cast<float2 *>(cpart + (size_t)G * q * q);
         const cudaError_t eg = launch_gram_umma(W, J, p, cpart, hpart);
         if (eg != cudaSuccess) return eg;
-        build_m_tc_kernel<<<W.nsm, 256, 0, W.st>>>(q, G, cpart, hpart, split2(1.0 / (double)p), split2(sigma), W.Mf,
-                                                   nullptr, nullptr);
+        build_m_tc_kernel<<<W.nsm, 256, 0, W.st>>>(q, G, cpart, G, hpart, split2(1.0 / (double)p), split2(sigma),
+                                                   W.Mf, nullptr, nullptr);
     } else {
         // preconditioner from a stride subsample of s rows: M_s = I + sigma (p / s) (G_s - h_s h_s' / s)
         const int s = kMfSample;

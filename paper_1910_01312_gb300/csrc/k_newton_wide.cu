@@ -8,9 +8,10 @@
 //     M d = d + sigma (X_J'(X_J d) - h (h'd) / p),
 // one pass over the rows of J per CG step in double-float (Dot2), and the
 // preconditioner comes from the Gram on the tensor cores:
-//  1. gram_umma_wide_kernel (k_umma.cu): TF32 products, FP32 sums, the exact
-//     column sums h beside it;
-//  2. build_m_tc_kernel (k_newton.cu): M_pre = I + sigma (G_tf32 - h h'/p);
+//  1. colsum_kernel (k_umma.cu): the exact column sums h (double-float), then
+//     gram_f16_wide_kernel (k_umma.cu): G_16 from FP16 products of X16 (X
+//     scaled per feature by a power of two; TF32's precision), FP32 sums;
+//  2. build_m_tc_kernel (k_newton.cu): M_pre = I + sigma (G_16 - h h'/p);
 //  3. newton_mfw_setup_kernel (cooperative): the FP32 Cholesky factor L of
 //     M_pre by the grid (bc_factor), the inverses of its 128 x 128 diagonal
 //     tiles, then Pinv = (L L')^{-1} column by column -- two block triangular
@@ -32,10 +33,10 @@
 // J, and only the preconditioner depends on it.  A first kernel counts the
 // rows of J missing from the set the current preconditioner was built for (a
 // bitmap) and those that left it; when together they are at most 1 % of p,
-// sigma is unchanged and the last CG took at most 8 steps, steps 1-3 are
-// skipped (their kernels return at once) and h comes from a column-sum pass
-// instead.  CG still runs on the exact operator of the current J, so only its
-// step count depends on this.
+// sigma is unchanged and the last CG took at most 8 steps, the Gram and
+// steps 2-3 are skipped (their kernels return at once); h is summed afresh.
+// CG still runs on the exact operator of the current J, so only its step
+// count depends on this.
 #include <math.h>
 
 #include "internal.cuh"
@@ -305,68 +306,6 @@ __global__ void mfw_mask_set_kernel(const int32_t *__restrict__ J, long long p, 
 // h = X_J'1 (double-float) when the Gram is skipped: each block a contiguous
 // share of J, a thread per 4 columns, rows in order (TwoSum); the last block
 // adds the block partials in block order.
-__global__ void __launch_bounds__(256) mfw_colsum_kernel(const float *__restrict__ X, int q,
-                                                         const int32_t *__restrict__ J, long long p,
-                                                         float2 *__restrict__ part, MfwState *st,
-                                                         float2 *__restrict__ H)
-{
-    if (!__ldcg(&st->skip)) return;
-    const int G = gridDim.x, c = threadIdx.x;
-    const bool has = 4 * c < q;
-    const long long per = (p + G - 1) / G;
-    const long long rbeg = (long long)blockIdx.x * per;
-    const long long rend = rbeg + per < p ? rbeg + per : p;
-    float hs[4] = {0.f, 0.f, 0.f, 0.f}, hc[4] = {0.f, 0.f, 0.f, 0.f};
-    for (long long r0 = rbeg; r0 < rend; r0 += 4) {
-        float4 v[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const long long r = r0 + u;
-            v[u] = (has && r < rend) ? __ldcs(reinterpret_cast<const float4 *>(X + (long long)J[r] * q) + c)
-                                     : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const float xs[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                float sn, e;
-                two_sum(hs[k], xs[k], sn, e);
-                hs[k] = sn;
-                hc[k] += e;
-            }
-        }
-    }
-    if (has) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            float hi, lo;
-            two_sum(hs[k], hc[k], hi, lo);
-            part[(size_t)blockIdx.x * q + 4 * c + k] = make_float2(hi, lo);
-        }
-    }
-    __threadfence();
-    __syncthreads();
-    __shared__ int last;
-    if (threadIdx.x == 0) last = atomicAdd(&st->done, 1u) == (unsigned)(G - 1);
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    // eight lanes per column sum interleaved eighths of the partials, combined
-    // by shuffles in a fixed order (a warp-uniform trip count)
-    const int lane = threadIdx.x & 31, sub = lane & 7;
-    for (int j0 = (threadIdx.x >> 3); j0 < ((q + 3) & ~3); j0 += blockDim.x >> 3) {
-        const int j = j0 < q ? j0 : q - 1;
-        float2 t = make_float2(0.f, 0.f);
-        for (int b = sub; b < G; b += 8) t = dfx_add(t, __ldcg(&part[(size_t)b * q + j]));
-#pragma unroll
-        for (int o = 1; o < 8; o <<= 1) t = dfx_add(t, shfl_xor_f2(t, o));
-        if (sub == 0 && j0 < q) H[j] = t;
-    }
-    if (threadIdx.x == 0) st->done = 0u;
-}
-
-
 // dynamic shared memory of newton_mfw_cg_kernel<NF4>
 constexpr size_t mfw_smem(int nf4)
 {
@@ -752,22 +691,22 @@ cudaError_t newton_mfw_prepare(Work &W, const int32_t *J, long long p, double si
     if (e != cudaSuccess) return e;
     const int KS = gram_wide_splits(W, p);
     float *cpart = reinterpret_cast<float *>(W.part);
-    float2 *hpart = reinterpret_cast<float2 *>(cpart + (size_t)KS * q * q);
     float *Pinv = reinterpret_cast<float *>(W.M);
     float2 *H = reinterpret_cast<float2 *>(Pinv + (size_t)q * q);
-    e = launch_gram_umma_wide(W, J, p, KS, cpart, hpart, skip);
-    if (e == cudaSuccess) e = launch_build_m_tc(W, KS, cpart, hpart, p, sigma, H, skip);
-    if (e != cudaSuccess) return e;
     float *Dg = reinterpret_cast<float *>(W.part);
     float *Linv = Dg + (size_t)q * kPb;
     float2 *cgp = reinterpret_cast<float2 *>(Linv + (size_t)nblk * kWdBlk * kWdBlk);
     float2 *yg = cgp + (size_t)Gc * q;
     float *zg = reinterpret_cast<float *>(yg + q);
     int *fflag = reinterpret_cast<int *>(zg + q);
-    // column sums: about 64 rows per block, at most 4 blocks per SM
-    const long long gcs = (p + 63) / 64 < Gc ? (p + 63) / 64 : Gc;
-    mfw_colsum_kernel<<<(unsigned)gcs, 256, 0, W.st>>>((const float *)W.X, q, J, p, cgp, st, H);
-    ++W.nlaunch;
+    // the exact h (the CG's operator needs it; M_pre too), its scratch the CG's
+    // chunk partials (free until the CG); then the Gram and M_pre, which return
+    // at once when the preconditioner is kept (the Gram partials reuse the
+    // scratch after the column sums are done)
+    e = launch_colsum(W, J, p, colsum_blocks(W, p, Gc), cgp, H);
+    if (e == cudaSuccess) e = launch_gram_umma_wide(W, J, p, KS, cpart, skip);
+    if (e == cudaSuccess) e = launch_build_m_tc(W, KS, cpart, 1, H, p, sigma, nullptr, skip);
+    if (e != cudaSuccess) return e;
     MfwSetupArgs &s = W.mfw_s;
     s.q = q;
     s.Mf = W.Mf;

@@ -3,6 +3,7 @@
 // Newton solve (Proposition 3.5: the reduced matrix I + sigma (G - h h'/p)
 // with G = X_J' X_J and h = X_J' 1).
 //
+// q <= 128 (gram_umma_kernel; the wide form for 128 < q <= 1024 follows it).
 // Each block takes a contiguous share of J and accumulates C_b = X_S' X_S
 // (S = its rows) in tensor memory: D[m][n] += sum_k A[m][k] B[n][k] with
 // A = B = the stage's rows transposed (feature m, sample k), one
@@ -16,8 +17,18 @@
 // mantissa), sums FP32: the CG operator stays exact, so this rounding only
 // sets how fast CG converges.
 //
-// Every wait is bounded: a commit that does not arrive within ~1 s records
-// DEV_TIMEOUT, the block frees its tensor memory and returns.
+// TF32 operands must be K-major (samples contiguous), which X's rows are
+// not: with the operand-transpose bits set, kind::tf32 returned zeros on
+// sm_103a, while kind::f16 takes MN-major operands -- hence the gathered
+// register staging here and the FP16 copy of X for the wide form.
+//
+// Every wait is bounded: a commit or copy that does not arrive within ~1 s
+// records DEV_TIMEOUT, the block waits for what it issued, frees its tensor
+// memory and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_fp16.h>
+
 #include "internal.cuh"
 
 namespace svm {
@@ -233,77 +244,114 @@ __global__ void __launch_bounds__(kUmThreads) gram_umma_kernel(const float *__re
 // -- features 128 ti .. 128 ti + 127 (the MMA's M = 128 rows, A) against
 // features 256 cj .. 256 cj + 255 (N <= 256 columns, B) for each chunk cj that
 // reaches the diagonal of row tile ti -- and blockIdx.y splits the rows of J
-// (split-K).  A stage gathers 32 rows: B's features always, A's only when they
-// lie outside B's range (otherwise A's descriptor points into B's panel).  The
-// panels are K-major in the 128-byte swizzled layout (32 rows = 128 bytes of K
-// per feature).  A thread loads 16 bytes (4 features of one row) and stores
-// the 4 values at offsets fixed for the thread, the 32 lanes of a warp on 32
-// distinct banks; the rows of the next stage load while a stage is stored and
-// its MMAs issued.  The
-// pair whose chunk holds A's features also sums A's columns (h).  Each
-// feature is gathered by several pairs (about 6 x the rows' bytes at q =
-// 784); products are TF32, sums FP32 -- the preconditioner's Gram, as above.
-constexpr int kWgK = 32;                                 // gathered rows per stage
-constexpr int kWgBN = 256;                               // B features (MMA N, max)
-constexpr int kWgAM = 128;                               // A features (MMA M)
-constexpr unsigned kWgSbo = 8 * kWgK * 4;                // next 8 features: one 1024-byte swizzle atom
-constexpr int kWgBBytes = kWgBN * kWgK * 4;              // 32 KB
-constexpr int kWgABytes = kWgAM * kWgK * 4;              // 16 KB
-constexpr int kWgStageBytes = kWgBBytes + kWgABytes;
-constexpr int kWgCols = 256;                             // tensor-memory columns
-constexpr size_t kWgSmem = 2 * (size_t)kWgStageBytes + 1024;
+// (split-K).
+//
+// The operands come from X16, an FP16 copy of X with a power-of-two scale
+// 2^k_f per feature (made once per X, x16_prepare): FP16's 11-bit significand
+// is TF32's, and the scale keeps every column inside FP16's range.  The rows
+// are gathered by the tensor memory accelerator -- one cp.async.bulk.tensor
+// tile::gather4 copies 128 bytes (64 features) of 4 arbitrary rows, 128-byte
+// swizzled -- straight into the MMA's operand layout: MN-major (features
+// contiguous, as in X), a 64-feature block of a stage is 32 rows x 128 bytes,
+// blocks 4 KB apart (the descriptor's leading offset), rows 8 at a time in
+// 1024-byte swizzle atoms (the stride offset).  A stage holds B's blocks and
+// A's when A's features lie outside B's (otherwise A's descriptor points into
+// B's panel).  Warp 0 issues the copies (four stages in flight), warp 1 the
+// MMAs (one elected lane, kind::f16, K = 16 rows each, FP32 accumulation in
+// tensor memory) after zeroing the rows past the end of the block's share in
+// its last stage; no thread touches the data otherwise.  The epilogue undoes
+// the scales (C_ab = D_ab 2^-(k_a + k_b)).  The exact column sums h come from
+// a separate pass over the FP32 rows.
+constexpr int kTgK = 32;                                 // gathered rows per stage
+constexpr int kTgNS = 4;                                 // stages
+constexpr int kTgBN = 256;                               // B features (MMA N, max)
+constexpr int kTgAM = 128;                               // A features (MMA M)
+constexpr int kTgF = 64;                                 // features of a 128-byte row of a block
+constexpr int kTgBlk = kTgK * 128;                       // one 64-feature block of a stage: 4 KB
+constexpr int kTgBBytes = (kTgBN / kTgF) * kTgBlk;       // 16 KB
+constexpr int kTgABytes = (kTgAM / kTgF) * kTgBlk;       // 8 KB
+constexpr int kTgStage = kTgBBytes + kTgABytes;          // 24 KB
+constexpr int kTgCols = 256;                             // tensor-memory columns
+constexpr size_t kTgSmem = kTgNS * (size_t)kTgStage + 1024;
 
 __host__ __device__ inline int wg_chunks(int ti, int q)   // column chunks of row tile ti
 {
     const int last = (128 * ti + 127 < q - 1) ? 128 * ti + 127 : q - 1;
-    return last / kWgBN + 1;
+    return last / kTgBN + 1;
 }
 
 __host__ __device__ inline int wg_pairs(int q)
 {
     int n = 0;
-    for (int ti = 0; ti * kWgAM < q; ++ti) n += wg_chunks(ti, q);
+    for (int ti = 0; ti * kTgAM < q; ++ti) n += wg_chunks(ti, q);
     return n;
 }
 
-// Shared-memory descriptor of a K-major operand in the 128-byte swizzled
-// layout: each M/N row holds its 32 K values (128 bytes) with 16-byte chunk c
-// stored at chunk c ^ (row & 7), eight rows form a 1024-byte atom, atoms SBO
-// bytes apart (layout type 2 at bits 61-63; the leading offset is unused for
-// this layout and set to 1).  A K step of 8 TF32 values advances the start
-// address by 32 bytes inside the atom.
-__device__ __forceinline__ unsigned long long umma_desc_sw128(unsigned saddr, unsigned sbo)
+// Shared-memory descriptor of an MN-major operand in the 128-byte swizzled
+// layout: 128-byte rows of consecutive features (16-byte chunk c of row k at
+// chunk c ^ (k & 7)), 8 rows (K) to a 1024-byte atom, K atoms SBO bytes
+// apart, feature blocks (one row each) LBO bytes apart (layout type 2 at bits
+// 61-63).
+__device__ __forceinline__ unsigned long long umma_desc_mn_sw128(unsigned saddr, unsigned lbo, unsigned sbo)
 {
     unsigned long long d = 0;
     d |= (unsigned long long)((saddr >> 4) & 0x3FFFu);
-    d |= 1ull << 16;
+    d |= (unsigned long long)((lbo >> 4) & 0x3FFFu) << 16;
     d |= (unsigned long long)((sbo >> 4) & 0x3FFFu) << 32;
     d |= 1ull << 46;
     d |= 2ull << 61;
     return d;
 }
 
-// the 4 values of one lane (4 consecutive features of one gathered row) into
-// the swizzled panel at st, at the lane's fixed offsets
-__device__ __forceinline__ void wg_store4(unsigned char *st, const unsigned (&soff)[4], const float4 &v)
+// Instruction descriptor of kind::f16 with FP16 A and B (bits 7-9, 10-12 = 0),
+// FP32 D (bits 4-5 = 1), both operands MN-major (bits 15, 16), N >> 3 at bit
+// 17, M >> 4 at bit 24.
+__host__ __device__ constexpr unsigned umma_idesc_f16_mn(int M, int N)
 {
-    *reinterpret_cast<float *>(st + soff[0]) = v.x;
-    *reinterpret_cast<float *>(st + soff[1]) = v.y;
-    *reinterpret_cast<float *>(st + soff[2]) = v.z;
-    *reinterpret_cast<float *>(st + soff[3]) = v.w;
+    return (1u << 4) | (1u << 15) | (1u << 16) | ((unsigned)(N >> 3) << 17) | ((unsigned)(M >> 4) << 24);
 }
 
-__global__ void __launch_bounds__(kUmThreads, 2) gram_umma_wide_kernel(const float *__restrict__ X, int q,
-                                                                    const int32_t *__restrict__ J, long long p,
-                                                                    float *__restrict__ cpart,
-                                                                    float2 *__restrict__ hpart, int *err,
-                                                                    const int *skip)
+__device__ __forceinline__ void tc_mma_f16(unsigned dtmem, unsigned long long adesc, unsigned long long bdesc,
+                                           unsigned idesc, int accumulate)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// 4 rows (y0..y3) x 128 bytes from x of the 2-D map into dst (128-byte
+// aligned, 512 bytes), completing on bar
+__device__ __forceinline__ void tma_gather4(unsigned dst, const void *tmap, int x, int y0, int y1, int y2, int y3,
+                                            unsigned bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y0), "r"(y1), "r"(y2), "r"(y3), "r"(bar)
+        : "memory");
+}
+
+// the lane-0 result of a bounded wait, in every lane of the warp
+__device__ __forceinline__ bool warp_wait(unsigned long long *bar, unsigned parity, int *err, int lane)
+{
+    int ok = 1;
+    if (lane == 0) ok = mbar_wait_bounded(bar, parity, err) ? 1 : 0;
+    return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+__global__ void __launch_bounds__(kUmThreads, 2) gram_f16_wide_kernel(const __grid_constant__ CUtensorMap xmap, int q,
+                                                                   const int *__restrict__ kf,
+                                                                   const int32_t *__restrict__ J, long long p,
+                                                                   float *__restrict__ cpart, int *err,
+                                                                   const int *skip)
 {
     if (skip && __ldcg(skip)) return;
     extern __shared__ unsigned char um_dyn[];
-    __shared__ __align__(8) unsigned long long mbar[2];
+    __shared__ __align__(8) unsigned long long full[kTgNS], empty[kTgNS], done;
     __shared__ unsigned tmem_slot;
-    __shared__ float2 hsm[2][kWgAM];
+    __shared__ int abort_flag, mma_count;
     unsigned char *base =
         reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(um_dyn) + 1023) & ~(uintptr_t)1023);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -313,133 +361,144 @@ __global__ void __launch_bounds__(kUmThreads, 2) gram_umma_wide_kernel(const flo
         ++ti;
     }
     const int cj = t;
-    const int b0 = kWgBN * cj, a0 = kWgAM * ti;
-    const int nb = (q - b0 < kWgBN) ? q - b0 : kWgBN;   // a multiple of 16
+    const int b0 = kTgBN * cj, a0 = kTgAM * ti;
+    const int nb = (q - b0 < kTgBN) ? q - b0 : kTgBN;   // a multiple of 16
     const bool inside = (ti >> 1) == cj;                // A's features are B's 128 (ti & 1) .. + 127
+    const int nbB = (nb + kTgF - 1) / kTgF;             // 64-feature blocks copied per stage
+    const int nbA = inside ? 0 : ((q - a0 < kTgAM ? q - a0 : kTgAM) + kTgF - 1) / kTgF;
     const int KS = gridDim.y, ks = blockIdx.y;
     const long long per = (p + KS - 1) / KS;
     const long long r0 = (long long)ks * per;
     const long long r1 = r0 + per < p ? r0 + per : p;
-    const int nst = r1 > r0 ? (int)((r1 - r0 + kWgK - 1) / kWgK) : 0;
+    const int nst = r1 > r0 ? (int)((r1 - r0 + kTgK - 1) / kTgK) : 0;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                     "r"(kWgCols)
+                     "r"(kTgCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (threadIdx.x == 32) {
-        mbar_init(&mbar[0], 1);
-        mbar_init(&mbar[1], 1);
+        for (int s = 0; s < kTgNS; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);   // the MMAs' commit
+        }
+        mbar_init(&done, 1);
         mbar_fence_init();
+        abort_flag = 0;
+        mma_count = 0;
     }
-    for (int i = threadIdx.x; i < 2 * kWgStageBytes / 16; i += kUmThreads)
+    // blocks that are never copied (features past q) stay zero
+    for (int i = threadIdx.x; i < kTgNS * kTgStage / 16; i += kUmThreads)
         reinterpret_cast<float4 *>(base)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const unsigned tmem = tmem_slot;
-    const unsigned idesc = umma_idesc_tf32(kWgAM, nb);
-    // lane -> data: lane bits 0-3 give the stage row within the warp's half of
-    // the stage (rows 16 (w & 1) .. + 15), lane bit 4 and w >> 1 the lane's
-    // 4-feature group c4 within each 32 features (two lanes cover 32
-    // contiguous bytes of a row).  Feature m = 32 g + 4 c4 + j of row k sits at
-    // g * 4096 + soff[j]; for a fixed j the 32 lanes of a warp hit 32 distinct
-    // banks: (k >> 2) ^ (m & 7) takes 8 values, k & 3 four.
-    const int kr = 16 * (warp & 1) + (lane & 15);
-    const int c4 = 2 * (warp >> 1) + (lane >> 4);
-    unsigned soff[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int mj = 4 * (c4 & 1) + j;
-        soff[j] = (unsigned)(c4 >> 1) * kWgSbo + (unsigned)mj * 128u + ((unsigned)((kr >> 2) ^ mj) << 4) +
-                  (unsigned)(kr & 3) * 4u;
-    }
-    const int gA = (ti & 1) * 4;             // A's first 32-feature group inside B
+    const unsigned sbase = smem_u32(base);
+    int issued = 0;   // stages whose copies were issued (warp 0)
 
-    float hs[16], hc[16];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) hs[i] = hc[i] = 0.f;
-    // software pipeline: the rows of stage it + 1 load into registers while
-    // stage it is stored and its MMAs issued; row indices two stages ahead
-    auto row_of = [&](int st) -> int {
-        const long long r = r0 + (long long)st * kWgK + kr;
-        return (st < nst && r < r1) ? __ldg(&J[r]) : -1;
-    };
-    float4 vb[kWgBN / 32], va[kWgAM / 32];
-    auto load_rows = [&](int jr) {
-        const float *row = X + (long long)(jr < 0 ? 0 : jr) * q;
-#pragma unroll
-        for (int g = 0; g < kWgBN / 32; ++g) {
-            const int m = b0 + 32 * g + 4 * c4;
-            vb[g] = (jr >= 0 && m < q) ? __ldcg(reinterpret_cast<const float4 *>(row + m))
-                                       : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        if (!inside) {
-#pragma unroll
-            for (int g = 0; g < kWgAM / 32; ++g) {
-                const int m = a0 + 32 * g + 4 * c4;
-                va[g] = (jr >= 0 && m < q) ? __ldcg(reinterpret_cast<const float4 *>(row + m))
-                                           : make_float4(0.f, 0.f, 0.f, 0.f);
+    if (warp == 0) {
+        // ---- producer: the copies of stage it once its previous use is done ----
+        const int ncopy = (nbB + nbA) * (kTgK / 4);
+        const unsigned bytes = (unsigned)(nbB + nbA) * kTgBlk;
+        for (int it = 0; it < nst; ++it) {
+            const int s = it % kTgNS;
+            if (it >= kTgNS && !warp_wait(&empty[s], (unsigned)((it / kTgNS) - 1) & 1u, err, lane)) {
+                abort_flag = 1;
+                break;
             }
-        }
-    };
-    int jnext = row_of(1);
-    load_rows(row_of(0));
-    int ok = 1;
-    for (int it = 0; it < nst; ++it) {
-        const int b = it & 1;
-        if (it >= 2 && ok) ok = mbar_wait_bounded(&mbar[b], (unsigned)((it - 2) >> 1) & 1u, err) ? 1 : 0;
-        if (!__syncthreads_and(ok)) { ok = 0; break; }
-        unsigned char *st = base + b * kWgStageBytes;
-#pragma unroll
-        for (int g = 0; g < kWgBN / 32; ++g) wg_store4(st + g * 4 * kWgSbo, soff, vb[g]);
-        if (!inside) {
-#pragma unroll
-            for (int g = 0; g < kWgAM / 32; ++g) wg_store4(st + kWgBBytes + g * 4 * kWgSbo, soff, va[g]);
-        } else {
-#pragma unroll
-            for (int gg = 0; gg < kWgAM / 32; ++gg) {
-                const float4 v = gA ? vb[4 + gg] : vb[gg];
-                const float xs[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    float sn, er;
-                    two_sum(hs[4 * gg + j], xs[j], sn, er);
-                    hs[4 * gg + j] = sn;
-                    hc[4 * gg + j] += er;
+            if (*(volatile int *)&abort_flag) break;
+            const long long rb = r0 + (long long)it * kTgK;
+            // lane k holds the stage's row k (past the end: the share's last row, zeroed later)
+            const int myrow = __ldg(&J[rb + lane < r1 ? rb + lane : r1 - 1]);
+            if (lane == 0) mbar_arrive_expect_tx(&full[s], bytes);
+            __syncwarp();
+            const unsigned st = sbase + (unsigned)s * kTgStage;
+            for (int i0 = 0; i0 < ncopy; i0 += 32) {
+                const int i = i0 + lane;
+                const int quad = i % (kTgK / 4), blk = i / (kTgK / 4);
+                const int y0 = __shfl_sync(0xffffffffu, myrow, 4 * quad + 0);
+                const int y1 = __shfl_sync(0xffffffffu, myrow, 4 * quad + 1);
+                const int y2 = __shfl_sync(0xffffffffu, myrow, 4 * quad + 2);
+                const int y3 = __shfl_sync(0xffffffffu, myrow, 4 * quad + 3);
+                if (i < ncopy) {
+                    const bool isb = blk < nbB;
+                    const int x = isb ? b0 + kTgF * blk : a0 + kTgF * (blk - nbB);
+                    const unsigned dst =
+                        st + (isb ? (unsigned)blk * kTgBlk : (unsigned)kTgBBytes + (unsigned)(blk - nbB) * kTgBlk) +
+                        (unsigned)quad * 512u;
+                    tma_gather4(dst, &xmap, x, y0, y1, y2, y3, smem_u32(&full[s]));
                 }
             }
+            issued = it + 1;
         }
-        // the next stage's rows (this stage's values are in shared memory now)
-        const int jn2 = row_of(it + 2);
-        load_rows(jnext);
-        jnext = jn2;
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            tc_fence_after();
-            const unsigned sb = smem_u32(st);
-            const unsigned sa = inside ? sb + (unsigned)(ti & 1) * 16u * kWgSbo : sb + (unsigned)kWgBBytes;
-#pragma unroll
-            for (int s = 0; s < kWgK / 8; ++s) {
-                const unsigned long long ad = umma_desc_sw128(sa + s * 32u, kWgSbo);
-                const unsigned long long bd = umma_desc_sw128(sb + s * 32u, kWgSbo);
-                tc_mma_tf32(tmem, ad, bd, idesc, (it > 0 || s > 0) ? 1 : 0);
+    } else if (warp == 1) {
+        // ---- the MMAs of each stage (rows past the share's end zeroed first) ----
+        const unsigned idesc = umma_idesc_f16_mn(kTgAM, nb);
+        int mmas = 0;
+        for (int it = 0; it < nst; ++it) {
+            const int s = it % kTgNS;
+            if (!warp_wait(&full[s], (unsigned)(it / kTgNS) & 1u, err, lane)) {
+                abort_flag = 1;
+                break;
             }
-            tc_commit(&mbar[b]);
+            const long long rb = r0 + (long long)it * kTgK;
+            const int valid = (int)(r1 - rb < kTgK ? r1 - rb : kTgK);
+            unsigned char *stp = base + (size_t)s * kTgStage;
+            if (valid < kTgK) {
+                const int nz = kTgK - valid;
+                for (int e = lane; e < (nbB + nbA) * nz * 8; e += 32) {
+                    const int blk = e / (nz * 8), rem = e - blk * nz * 8;
+                    const int k = valid + rem / 8, c = rem % 8;
+                    unsigned char *bp = blk < nbB ? stp + blk * kTgBlk : stp + kTgBBytes + (blk - nbB) * kTgBlk;
+                    *reinterpret_cast<float4 *>(bp + k * 128 + c * 16) = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+            }
+            if (lane == 0) {
+                tc_fence_after();
+                const unsigned sb = sbase + (unsigned)s * kTgStage;
+                const unsigned sa = inside ? sb + (unsigned)(ti & 1) * 2u * kTgBlk : sb + (unsigned)kTgBBytes;
+                for (int h = 0; 16 * h < valid; ++h) {
+                    const unsigned long long ad = umma_desc_mn_sw128(sa + h * 2048u, kTgBlk, 1024);
+                    const unsigned long long bd = umma_desc_mn_sw128(sb + h * 2048u, kTgBlk, 1024);
+                    tc_mma_f16(tmem, ad, bd, idesc, (it > 0 || h > 0) ? 1 : 0);
+                }
+                tc_commit(&empty[s]);
+            }
+            __syncwarp();
+            mmas = it + 1;
+        }
+        // done completes once every MMA issued has (on the normal path and after a wait gave up)
+        if (lane == 0) {
+            if (mmas > 0) tc_commit(&done);
+            mma_count = mmas;
         }
     }
-    if (nst > 0 && ok) ok = mbar_wait_bounded(&mbar[(nst - 1) & 1], (unsigned)((nst - 1) >> 1) & 1u, err) ? 1 : 0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (mma_count > 0 && !mbar_wait_bounded(&done, 0u, err)) abort_flag = 1;
+        if (abort_flag) {
+            // a wait gave up: the copies already issued land before the block leaves
+            for (int it = issued - kTgNS < 0 ? 0 : issued - kTgNS; it < issued; ++it)
+                mbar_wait_bounded(&full[it % kTgNS], (unsigned)(it / kTgNS) & 1u, err);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
     tc_fence_after();
-    ok = __syncthreads_and(ok);
+    const int ok = !abort_flag && mma_count == nst;
 
     // D rows from tensor memory: warp w reads lanes 32 (w & 3) .. + 31 (A's
-    // features), columns 128 (w >> 2) .. + 127 of B
+    // features), columns 128 (w >> 2) .. + 127 of B; the scales undone
     {
         float *C = cpart + (size_t)ks * q * q;
         const int quarter = warp & 3, half = warp >> 2;
         const int a = a0 + 32 * quarter + lane;
+        const int ka = a < q ? __ldg(&kf[a]) : 0;
         const int cend = (128 * half + 128 < nb) ? 128 * half + 128 : nb;
         for (int c0 = 128 * half; c0 < cend; c0 += 16) {
             unsigned r[16];
@@ -450,43 +509,149 @@ __global__ void __launch_bounds__(kUmThreads, 2) gram_umma_wide_kernel(const flo
                 for (int j = 0; j < 16; ++j) r[j] = 0u;
             }
             if (a < q) {
+                float v[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) v[j] = ldexpf(__uint_as_float(r[j]), -(ka + __ldg(&kf[b0 + c0 + j])));
 #pragma unroll
                 for (int j = 0; j < 16; j += 4)
                     *reinterpret_cast<float4 *>(&C[(size_t)a * q + b0 + c0 + j]) =
-                        make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]), __uint_as_float(r[j + 2]),
-                                    __uint_as_float(r[j + 3]));
+                        make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
             }
-        }
-    }
-    if (inside) {
-        // A's column sums: the 16 lanes of a 4-feature group (lane bits 0-3 =
-        // the row), then the two halves of the stage rows in order
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            float hi, lo;
-            two_sum(hs[i], hc[i], hi, lo);
-            float2 v = make_float2(hi, lo);
-#pragma unroll
-            for (int o = 1; o < 16; o <<= 1) v = dfx_add(v, shfl_xor_f2(v, o));
-            if ((lane & 15) == 0) hsm[warp & 1][32 * (i >> 2) + 4 * c4 + (i & 3)] = v;
         }
     }
     tc_fence_before();
     __syncthreads();
-    if (inside && threadIdx.x < kWgAM && a0 + (int)threadIdx.x < q)
-        hpart[(size_t)ks * q + a0 + threadIdx.x] = dfx_add(hsm[0][threadIdx.x], hsm[1][threadIdx.x]);
     if (warp == 0) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kWgCols) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTgCols) : "memory");
+    }
+}
+
+// ---- the FP16 copy of X ----
+// k_f = 15 - e_f with max_i |x_if| = m 2^e_f, m in [0.5, 1): the scaled
+// column's largest magnitude lies in [2^14, 2^15), below FP16's 65504
+__global__ void x16_colmax_kernel(const float *__restrict__ X, long long n, int q, unsigned *__restrict__ cmax)
+{
+    for (int f = threadIdx.x; f < q; f += blockDim.x) {
+        unsigned m = 0u;
+        for (long long i = blockIdx.x; i < n; i += gridDim.x) m = max(m, __float_as_uint(fabsf(X[i * q + f])));
+        atomicMax(&cmax[f], m);
+    }
+}
+
+__global__ void x16_scale_kernel(int q, const unsigned *__restrict__ cmax, int *__restrict__ kf)
+{
+    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < q; f += gridDim.x * blockDim.x) {
+        const float m = __uint_as_float(cmax[f]);
+        int e = 0;
+        if (m > 0.f && isfinite(m)) frexpf(m, &e);
+        kf[f] = m > 0.f && isfinite(m) ? 15 - e : 0;
+    }
+}
+
+__global__ void x16_convert_kernel(const float *__restrict__ X, long long n, int q, const int *__restrict__ kf,
+                                   __half *__restrict__ X16)
+{
+    const long long total = n * q;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int f = (int)(e % q);
+        X16[e] = __float2half_rn(ldexpf(X[e], __ldg(&kf[f])));
     }
 }
 
 int g_wg_attr = 0;
 
+// Exact column sums of the gathered rows: block b sums its contiguous share
+// of J in row order (TwoSum per feature, four features per thread), the last
+// block to finish adds the nb partials in block order (eight lanes per column,
+// a fixed shuffle order).
+__global__ void __launch_bounds__(256) colsum_kernel(const float *__restrict__ X, int q,
+                                                     const int32_t *__restrict__ J, long long p,
+                                                     float2 *__restrict__ part, unsigned *counter,
+                                                     float2 *__restrict__ H)
+{
+    const int G = gridDim.x, c = threadIdx.x;
+    const bool has = 4 * c < q;
+    const long long per = (p + G - 1) / G;
+    const long long rbeg = (long long)blockIdx.x * per;
+    const long long rend = rbeg + per < p ? rbeg + per : p;
+    float hs[4] = {0.f, 0.f, 0.f, 0.f}, hc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (long long r0 = rbeg; r0 < rend; r0 += 4) {
+        float4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const long long r = r0 + u;
+            v[u] = (has && r < rend) ? __ldcs(reinterpret_cast<const float4 *>(X + (long long)J[r] * q) + c)
+                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float xs[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                float sn, e;
+                two_sum(hs[k], xs[k], sn, e);
+                hs[k] = sn;
+                hc[k] += e;
+            }
+        }
+    }
+    if (has) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float hi, lo;
+            two_sum(hs[k], hc[k], hi, lo);
+            part[(size_t)blockIdx.x * q + 4 * c + k] = make_float2(hi, lo);
+        }
+    }
+    __threadfence();
+    __syncthreads();
+    __shared__ int last;
+    if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == (unsigned)(G - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int lane = threadIdx.x & 31, sub = lane & 7;
+    for (int j0 = (threadIdx.x >> 3); j0 < ((q + 3) & ~3); j0 += blockDim.x >> 3) {
+        const int j = j0 < q ? j0 : q - 1;
+        float2 t = make_float2(0.f, 0.f);
+        for (int b = sub; b < G; b += 8) t = dfx_add(t, __ldcg(&part[(size_t)b * q + j]));
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) t = dfx_add(t, shfl_xor_f2(t, o));
+        if (sub == 0 && j0 < q) H[j] = t;
+    }
+    if (threadIdx.x == 0) *counter = 0u;
+}
+
+// The tensor map of X16 (n x q FP16, row-major) for tile::gather4: 64-feature
+// (128-byte) boxes one row high, 128-byte swizzle.  The encoder is the
+// driver's, reached through the runtime (no link against libcuda).
+cudaError_t encode_xmap(Work &W)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult qr = cudaDriverEntryPointSymbolNotFound;
+        const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                                               &qr);
+        if (e != cudaSuccess || qr != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const cuuint64_t dims[2] = {(cuuint64_t)W.q, (cuuint64_t)W.n};
+    const cuuint64_t strides[1] = {(cuuint64_t)W.q * sizeof(__half)};
+    const cuuint32_t box[2] = {kTgF, 1};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = encode(reinterpret_cast<CUtensorMap *>(W.xmap), CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, W.x16, dims,
+                              strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 // G = sum_b C_b and h = sum_b h_b in FP64, in block order (the step-level
 // entry point); both triangles of G from the lower one of the partials
-__global__ void gram_sum_kernel(int q, int nb, const float *__restrict__ cpart, const float2 *__restrict__ hpart,
-                                double *__restrict__ Gout, double *__restrict__ hout)
+__global__ void gram_sum_kernel(int q, int nb, const float *__restrict__ cpart, int nbh,
+                                const float2 *__restrict__ hpart, double *__restrict__ Gout, double *__restrict__ hout)
 {
     const long long qq = (long long)q * q;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < qq + q;
@@ -499,7 +664,7 @@ __global__ void gram_sum_kernel(int q, int nb, const float *__restrict__ cpart, 
             Gout[t] = s;
         } else {
             const long long j = t - qq;
-            for (int b = 0; b < nb; ++b) {
+            for (int b = 0; b < nbh; ++b) {
                 const float2 v = hpart[(size_t)b * q + j];
                 s += (double)v.x + (double)v.y;
             }
@@ -551,32 +716,76 @@ int gram_wide_splits(const Work &W, long long p)
     long long cap = (long long)((2 * W.part_len) / (size_t)(q * q + 2 * q));
     long long ks = (2 * W.nsm + np - 1) / np;
     if (ks > cap) ks = cap;
-    const long long rows = (p + kWgK - 1) / kWgK;
+    const long long rows = (p + kTgK - 1) / kTgK;
     if (ks > rows) ks = rows;
     return ks < 1 ? 1 : (int)ks;
 }
 
-cudaError_t launch_gram_umma_wide(Work &W, const int32_t *J, long long p, int KS, float *cpart, float2 *hpart,
-                                  const int *skip)
+cudaError_t x16_prepare(Work &W)
+{
+    if (W.x16) return cudaSuccess;
+    const int q = (int)W.q;
+    if (!W.xf32 || W.csr || q % 16 != 0 || W.n < 1 || W.n > 0x7fffffffLL) return cudaErrorInvalidValue;
+    void *x16 = nullptr;
+    int *kf = nullptr;
+    if (cudaMalloc(&x16, (size_t)W.n * q * sizeof(__half)) != cudaSuccess) return cudaErrorMemoryAllocation;
+    if (cudaMalloc((void **)&kf, 2 * (size_t)q * sizeof(int)) != cudaSuccess) {
+        cudaFree(x16);
+        return cudaErrorMemoryAllocation;
+    }
+    W.x16 = x16;
+    W.x16_k = kf;
+    W.x16_own = true;
+    unsigned *cmax = reinterpret_cast<unsigned *>(kf + q);
+    cudaError_t e = cudaMemsetAsync(cmax, 0, (size_t)q * sizeof(unsigned), W.st);
+    if (e != cudaSuccess) return e;
+    x16_colmax_kernel<<<4 * W.nsm, 256, 0, W.st>>>((const float *)W.X, W.n, q, cmax);
+    x16_scale_kernel<<<(q + 255) / 256, 256, 0, W.st>>>(q, cmax, kf);
+    x16_convert_kernel<<<8 * W.nsm, 256, 0, W.st>>>((const float *)W.X, W.n, q, kf, reinterpret_cast<__half *>(x16));
+    W.nlaunch += 3;
+    e = cudaGetLastError();
+    return e == cudaSuccess ? encode_xmap(W) : e;
+}
+
+cudaError_t launch_gram_umma_wide(Work &W, const int32_t *J, long long p, int KS, float *cpart, const int *skip)
 {
     const int q = (int)W.q;
     if (q <= kUmMaxQ || q > 1024 || q % 16 != 0 || !W.xf32 || KS < 1) return cudaErrorInvalidValue;
     if ((size_t)KS * ((size_t)q * q + 2 * q) > 2 * W.part_len) return cudaErrorInvalidValue;
+    cudaError_t e = x16_prepare(W);
+    if (e != cudaSuccess) return e;
     if (!g_wg_attr) {
-        const cudaError_t ea =
-            cudaFuncSetAttribute(gram_umma_wide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgSmem);
-        if (ea != cudaSuccess) return ea;
+        e = cudaFuncSetAttribute(gram_f16_wide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTgSmem);
+        if (e != cudaSuccess) return e;
         g_wg_attr = 1;
     }
-    gram_umma_wide_kernel<<<dim3((unsigned)wg_pairs(q), (unsigned)KS), kUmThreads, kWgSmem, W.st>>>(
-        (const float *)W.X, q, J, p, cpart, hpart, W.err, skip);
+    const CUtensorMap *xm = reinterpret_cast<const CUtensorMap *>(W.xmap);
+    gram_f16_wide_kernel<<<dim3((unsigned)wg_pairs(q), (unsigned)KS), kUmThreads, kTgSmem, W.st>>>(
+        *xm, q, W.x16_k, J, p, cpart, W.err, skip);
     ++W.nlaunch;
     return cudaGetLastError();
 }
 
-cudaError_t launch_gram_umma_sum(Work &W, int nb, const float *cpart, const float2 *hpart, double *G, double *h)
+cudaError_t launch_gram_umma_sum(Work &W, int nb, const float *cpart, int nbh, const float2 *hpart, double *G,
+                                 double *h)
 {
-    gram_sum_kernel<<<W.nsm, 256, 0, W.st>>>((int)W.q, nb, cpart, hpart, G, h);
+    gram_sum_kernel<<<W.nsm, 256, 0, W.st>>>((int)W.q, nb, cpart, nbh, hpart, G, h);
+    ++W.nlaunch;
+    return cudaGetLastError();
+}
+
+int colsum_blocks(const Work &W, long long p, int max_blocks)
+{
+    long long nb = (p + 63) / 64;   // about 64 rows per block
+    if (nb > 4 * W.nsm) nb = 4 * W.nsm;
+    if (nb > max_blocks) nb = max_blocks;
+    return nb < 1 ? 1 : (int)nb;
+}
+
+cudaError_t launch_colsum(Work &W, const int32_t *J, long long p, int nb, float2 *part, float2 *H)
+{
+    if (W.csr || !W.xf32 || W.q > 1024 || W.q % 4 != 0 || nb < 1) return cudaErrorInvalidValue;
+    colsum_kernel<<<nb, 256, 0, W.st>>>((const float *)W.X, (int)W.q, J, p, part, W.rm_counter + 1, H);
     ++W.nlaunch;
     return cudaGetLastError();
 }

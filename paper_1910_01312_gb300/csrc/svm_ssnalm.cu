@@ -178,6 +178,10 @@ static void free_work(Work &W)
                     W.jcsc_row, W.jcsc_val, W.jcnt, W.jtask_part, W.csr_vf, W.csr_df, W.csr_cf, W.csr_tnf};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    if (W.x16_own) {
+        cudaFree(W.x16);
+        cudaFree(W.x16_k);
+    }
     for (int b = 0; b < 2; ++b) {
         void *pp[] = {W.pb[b].u, W.pb[b].uf, W.pb[b].pi, W.pb[b].wpi, W.pb[b].J, W.pb[b].S};
         for (void *p : pp)
@@ -1342,6 +1346,20 @@ extern "C" svm_status svm_ssnalm_solve_batch(svm_ssnalm_t *h, int32_t B, const i
         }
         h->pd_cap = B;
     }
+    // the wide Newton steps' FP16 copy of X: made once here, borrowed by every sub-handle
+    if (W.mfw_st) {
+        if (x16_prepare(W) != cudaSuccess) {
+            h->err = "batch: the FP16 copy of X could not be made";
+            return SVM_ERR_OOM;
+        }
+        for (svm_ssnalm *sb : h->subs) {
+            if (sb->W.x16) continue;
+            sb->W.x16 = W.x16;
+            sb->W.x16_k = W.x16_k;
+            sb->W.x16_own = false;
+            memcpy(sb->W.xmap, W.xmap, sizeof(W.xmap));
+        }
+    }
     std::vector<svm_result> res((size_t)B);
     std::vector<Run> runs((size_t)B);
     std::vector<long long> launch0((size_t)B);
@@ -1573,12 +1591,25 @@ extern "C" svm_status svm_op_gram(svm_ssnalm_t *h, const int32_t *J, int64_t p, 
         }
         float2 *hpart = reinterpret_cast<float2 *>(cpart + (size_t)gram_umma_blocks(W) * q * q);
         CK(timed(h, TK_NEWTON, [&] { return launch_gram_umma(W, J, p, cpart, hpart); }));
-        CK(launch_gram_umma_sum(W, gram_umma_blocks(W), cpart, hpart, G, hsum));
+        CK(launch_gram_umma_sum(W, gram_umma_blocks(W), cpart, gram_umma_blocks(W), hpart, G, hsum));
     } else {
+        // the FP16 tensor-core Gram, then the exact column sums (scratch after the Gram partials)
         const int KS = gram_wide_splits(W, p);
-        float2 *hpart = reinterpret_cast<float2 *>(cpart + (size_t)KS * q * q);
-        CK(timed(h, TK_NEWTON, [&] { return launch_gram_umma_wide(W, J, p, KS, cpart, hpart); }));
-        CK(launch_gram_umma_sum(W, KS, cpart, hpart, G, hsum));
+        float2 *hs = reinterpret_cast<float2 *>(cpart + (size_t)KS * q * q);
+        float2 *cs_part = hs + q;
+        const long long room = ((long long)(2 * W.part_len) - (long long)KS * q * q - 2 * q) / (2 * q);
+        if (room < 1) {
+            h->err = "svm_op_gram: workspace too small";
+            return SVM_ERR_UNSUPPORTED;
+        }
+        const int nbc = colsum_blocks(W, p, (int)(room < (1 << 20) ? room : (1 << 20)));
+        CK(timed(h, TK_NEWTON, [&] { return launch_gram_umma_wide(W, J, p, KS, cpart); }));
+        if (p > 0) {
+            CK(launch_colsum(W, J, p, nbc, cs_part, hs));
+        } else {
+            CK(cudaMemsetAsync(hs, 0, q * sizeof(float2), W.st));
+        }
+        CK(launch_gram_umma_sum(W, KS, cpart, 1, hs, G, hsum));
     }
     return sync_read(h);
 }

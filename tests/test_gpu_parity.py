@@ -246,11 +246,12 @@ def test_newton_wide_consecutive_steps(q, swap):
                                          (500, 256, 0, "sorted"), (6000, 512, 5000, "random")])
 def test_gram_tensor_cores(n, q, p, order):
     """G = X_J' X_J as the preconditioner of the large-free-set Newton step
-    forms it on the tcgen05 tensor cores (TF32 products: inputs keep 10 of
-    their 23 mantissa bits, so each product is within 2^-9 of exact; FP32 sums
-    within a block of at most ~p/300 rows add < 1e-4 relative; blocks added in
-    FP64), against the FP64 product of the gathered rows, elementwise relative
-    to |X_J|'|X_J|.  h = X_J' 1 is double-float: 1e-10 of sum |x|.  Covers a
+    forms it on the tcgen05 tensor cores (q <= 128: TF32 products, inputs
+    keep 10 of their 23 mantissa bits; q > 128: FP16 products of X scaled per
+    feature by a power of two, 11-bit significands rounded to nearest; either
+    way each product is within 2^-9 of exact; FP32 sums within a block of at
+    most ~p/300 rows add < 1e-4 relative; blocks added in FP64), against the
+    FP64 product of the gathered rows, elementwise relative to |X_J|'|X_J|.  h = X_J' 1 is double-float: 1e-10 of sum |x|.  Covers a
     ragged last stage (p not a multiple of 64), blocks with no rows (p < number
     of blocks), p = 0, q < 128 (zero-padded MMA rows) and unsorted J; for q >
     128 also row tiles only partly inside q (q = 144, 400, 784), a last column
