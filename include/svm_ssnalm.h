@@ -241,8 +241,8 @@ svm_status svm_op_newton(svm_ssnalm_t *h, const int32_t *J, int64_t p, double si
  * blocks added in FP64; hsum is exact to double-float accuracy.  q <= 128:
  * TF32 products (10-bit mantissa), one 128 x q accumulator per block;
  * 128 < q <= 1024: FP16 products of an FP16 copy of X scaled per feature by
- * a power of two (11-bit significand; the copy, n x q x 2 bytes, is made on
- * the first call and kept with the handle), (128-feature x 256-feature)
+ * a power of two (11-bit significand; the copy, n x 64 ceil(q / 64) x 2
+ * bytes, is made on the first call and kept with the handle), (128-feature x 256-feature)
  * tiles of the lower triangle, G symmetrised from it.  Dense FP32 X with
  * q % 16 == 0 and q <= 1024 only (else SVM_ERR_UNSUPPORTED).  Synchronises
  * the stream. */

@@ -214,11 +214,11 @@ struct Work {
     MfwArgs mfw_c{};
     // the FP16 copy of a dense FP32 X for the wide Gram (made on first use,
     // or borrowed from the handle of a batched solve): X16_if = fl16(x_if
-    // 2^k_f), the per-feature exponents k_f, and its tensor map (a CUtensorMap)
+    // 2^k_f) in rows padded to a multiple of 64 entries, and the per-feature
+    // exponents k_f
     void *x16 = nullptr;
     int *x16_k = nullptr;
     bool x16_own = false;
-    alignas(64) unsigned char xmap[128] = {};
     double *M = nullptr;      // q*q Newton matrix / Cholesky factor
     float *Lf = nullptr;      // q*(q+1) FP32 factor when it does not fit in shared memory
     float2 *Mf = nullptr;     // q*q FP32 (hi, lo) split of M (double-float CG operator)
@@ -360,8 +360,8 @@ cudaError_t launch_gram_umma_wide(Work &W, const int32_t *J, long long p, int KS
 // the FP16 copy of X for launch_gram_umma_wide (a no-op once made or borrowed)
 cudaError_t x16_prepare(Work &W);
 // H = X_J' 1 exactly (double-float, column sums in row order within each of
-// nb blocks, the blocks' sums in block order); part: nb x q float2 scratch,
-// nb = colsum_blocks(W, p) at most max_blocks
+// nb blocks, the blocks' sums in block order, two launches); part: nb x q
+// float2 scratch, nb = colsum_blocks(W, p) at most max_blocks
 int colsum_blocks(const Work &W, long long p, int max_blocks);
 cudaError_t launch_colsum(Work &W, const int32_t *J, long long p, int nb, float2 *part, float2 *H);
 // M_pre = I + sigma (G - h h'/p) into W.Mf from G partials of tensor-core

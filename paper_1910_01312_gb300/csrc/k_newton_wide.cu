@@ -306,6 +306,27 @@ __global__ void mfw_mask_set_kernel(const int32_t *__restrict__ J, long long p, 
 // h = X_J'1 (double-float) when the Gram is skipped: each block a contiguous
 // share of J, a thread per 4 columns, rows in order (TwoSum); the last block
 // adds the block partials in block order.
+// M_pre = I + sigma (G - h h'/p), lower triangle (the factor reads no more),
+// one thread per entry: G_ab summed over the KS row-split partials in split
+// order (FP32), the rest in double-float from the exact h
+__global__ void __launch_bounds__(256) mfw_build_m_kernel(int q, int KS, const float *__restrict__ cpart,
+                                                          const float2 *__restrict__ H, float2 rp, float2 sig,
+                                                          float2 *__restrict__ Mf, const int *skip)
+{
+    if (__ldcg(skip)) return;
+    const long long qq = (long long)q * q;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < qq; t += (long long)gridDim.x * blockDim.x) {
+        const int a = (int)(t / q), b = (int)(t - (long long)a * q);
+        if (b > a) continue;
+        float gs = 0.f;
+        for (int k = 0; k < KS; ++k) gs += __ldcg(&cpart[(size_t)k * qq + t]);
+        const float2 ha = __ldcg(&H[a]), hb = __ldcg(&H[b]);
+        float2 m = dfx_mul(sig, dfx_sub(make_float2(gs, 0.f), dfx_mul(dfx_mul(ha, hb), rp)));
+        if (a == b) m = dfx_addf(m, 1.f);
+        Mf[t] = m;
+    }
+}
+
 // dynamic shared memory of newton_mfw_cg_kernel<NF4>
 constexpr size_t mfw_smem(int nf4)
 {
@@ -705,8 +726,15 @@ cudaError_t newton_mfw_prepare(Work &W, const int32_t *J, long long p, double si
     // scratch after the column sums are done)
     e = launch_colsum(W, J, p, colsum_blocks(W, p, Gc), cgp, H);
     if (e == cudaSuccess) e = launch_gram_umma_wide(W, J, p, KS, cpart, skip);
-    if (e == cudaSuccess) e = launch_build_m_tc(W, KS, cpart, 1, H, p, sigma, nullptr, skip);
     if (e != cudaSuccess) return e;
+    {
+        const long long nb = ((long long)q * q + 255) / 256;
+        mfw_build_m_kernel<<<(unsigned)(nb < 8 * W.nsm ? nb : 8 * W.nsm), 256, 0, W.st>>>(
+            q, KS, cpart, H, split2w(1.0 / (double)p), split2w(sigma), W.Mf, skip);
+        ++W.nlaunch;
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     MfwSetupArgs &s = W.mfw_s;
     s.q = q;
     s.Mf = W.Mf;

@@ -25,8 +25,6 @@
 // Every wait is bounded: a commit or copy that does not arrive within ~1 s
 // records DEV_TIMEOUT, the block waits for what it issued, frees its tensor
 // memory and returns.
-#include <cuda.h>
-#include <cudaTypedefs.h>
 #include <cuda_fp16.h>
 
 #include "internal.cuh"
@@ -247,21 +245,21 @@ __global__ void __launch_bounds__(kUmThreads) gram_umma_kernel(const float *__re
 // (split-K).
 //
 // The operands come from X16, an FP16 copy of X with a power-of-two scale
-// 2^k_f per feature (made once per X, x16_prepare): FP16's 11-bit significand
-// is TF32's, and the scale keeps every column inside FP16's range.  The rows
-// are gathered by the tensor memory accelerator -- one cp.async.bulk.tensor
-// tile::gather4 copies 128 bytes (64 features) of 4 arbitrary rows, 128-byte
-// swizzled -- straight into the MMA's operand layout: MN-major (features
-// contiguous, as in X), a 64-feature block of a stage is 32 rows x 128 bytes,
-// blocks 4 KB apart (the descriptor's leading offset), rows 8 at a time in
-// 1024-byte swizzle atoms (the stride offset).  A stage holds B's blocks and
-// A's when A's features lie outside B's (otherwise A's descriptor points into
-// B's panel).  Warp 0 issues the copies (four stages in flight), warp 1 the
-// MMAs (one elected lane, kind::f16, K = 16 rows each, FP32 accumulation in
-// tensor memory) after zeroing the rows past the end of the block's share in
-// its last stage; no thread touches the data otherwise.  The epilogue undoes
-// the scales (C_ab = D_ab 2^-(k_a + k_b)).  The exact column sums h come from
-// a separate pass over the FP32 rows.
+// 2^k_f per feature (made once per X, x16_prepare; rows padded to 128-byte
+// multiples): FP16's 11-bit significand is TF32's, and the scale keeps every
+// column inside FP16's range.  The gathered rows go straight into the MMA's
+// operand layout, 16-byte cp.async copies into 128-byte swizzled MN-major
+// panels (features contiguous, as in X): a 64-feature block of a stage is 32
+// rows x 128 bytes, blocks 4 KB apart (the descriptor's leading offset), rows
+// 8 at a time in 1024-byte swizzle atoms (the stride offset).  A stage holds
+// B's blocks and A's when A's features lie outside B's (otherwise A's
+// descriptor points into B's panel).  Seven warps copy (four stages, three in
+// flight), warp 1 issues the MMAs (one elected lane, kind::f16, K = 16 rows
+// each, FP32 accumulation in tensor memory).  The epilogue undoes the scales
+// (C_ab = D_ab 2^-(k_a + k_b)).  The exact column sums h come from a separate
+// pass over the FP32 rows.  (A TMA tile::gather4 producer -- one instruction
+// per 4 rows x 128 bytes -- measured 1.13x slower here: at about 10 cycles per
+// gathered 128-byte row per SM the copy engine set the pace.)
 constexpr int kTgK = 32;                                 // gathered rows per stage
 constexpr int kTgNS = 4;                                 // stages
 constexpr int kTgBN = 256;                               // B features (MMA N, max)
@@ -321,18 +319,6 @@ __device__ __forceinline__ void tc_mma_f16(unsigned dtmem, unsigned long long ad
         : "memory");
 }
 
-// 4 rows (y0..y3) x 128 bytes from x of the 2-D map into dst (128-byte
-// aligned, 512 bytes), completing on bar
-__device__ __forceinline__ void tma_gather4(unsigned dst, const void *tmap, int x, int y0, int y1, int y2, int y3,
-                                            unsigned bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y0), "r"(y1), "r"(y2), "r"(y3), "r"(bar)
-        : "memory");
-}
-
 // the lane-0 result of a bounded wait, in every lane of the warp
 __device__ __forceinline__ bool warp_wait(unsigned long long *bar, unsigned parity, int *err, int lane)
 {
@@ -341,7 +327,7 @@ __device__ __forceinline__ bool warp_wait(unsigned long long *bar, unsigned pari
     return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
-__global__ void __launch_bounds__(kUmThreads, 2) gram_f16_wide_kernel(const __grid_constant__ CUtensorMap xmap, int q,
+__global__ void __launch_bounds__(kUmThreads, 2) gram_f16_wide_kernel(const void *__restrict__ x16, int x16_ld, int q,
                                                                    const int *__restrict__ kf,
                                                                    const int32_t *__restrict__ J, long long p,
                                                                    float *__restrict__ cpart, int *err,
@@ -380,7 +366,7 @@ __global__ void __launch_bounds__(kUmThreads, 2) gram_f16_wide_kernel(const __gr
     }
     if (threadIdx.x == 32) {
         for (int s = 0; s < kTgNS; ++s) {
-            mbar_init(&full[s], 1);
+            mbar_init(&full[s], kUmThreads - 32);   // every producer thread
             mbar_init(&empty[s], 1);   // the MMAs' commit
         }
         mbar_init(&done, 1);
@@ -397,43 +383,53 @@ __global__ void __launch_bounds__(kUmThreads, 2) gram_f16_wide_kernel(const __gr
     tc_fence_after();
     const unsigned tmem = tmem_slot;
     const unsigned sbase = smem_u32(base);
-    int issued = 0;   // stages whose copies were issued (warp 0)
 
-    if (warp == 0) {
-        // ---- producer: the copies of stage it once its previous use is done ----
-        const int ncopy = (nbB + nbA) * (kTgK / 4);
-        const unsigned bytes = (unsigned)(nbB + nbA) * kTgBlk;
-        for (int it = 0; it < nst; ++it) {
-            const int s = it % kTgNS;
-            if (it >= kTgNS && !warp_wait(&empty[s], (unsigned)((it / kTgNS) - 1) & 1u, err, lane)) {
-                abort_flag = 1;
-                break;
-            }
-            if (*(volatile int *)&abort_flag) break;
-            const long long rb = r0 + (long long)it * kTgK;
-            // lane k holds the stage's row k (past the end: the share's last row, zeroed later)
-            const int myrow = __ldg(&J[rb + lane < r1 ? rb + lane : r1 - 1]);
-            if (lane == 0) mbar_arrive_expect_tx(&full[s], bytes);
-            __syncwarp();
-            const unsigned st = sbase + (unsigned)s * kTgStage;
-            for (int i0 = 0; i0 < ncopy; i0 += 32) {
-                const int i = i0 + lane;
-                const int quad = i % (kTgK / 4), blk = i / (kTgK / 4);
-                const int y0 = __shfl_sync(0xffffffffu, myrow, 4 * quad + 0);
-                const int y1 = __shfl_sync(0xffffffffu, myrow, 4 * quad + 1);
-                const int y2 = __shfl_sync(0xffffffffu, myrow, 4 * quad + 2);
-                const int y3 = __shfl_sync(0xffffffffu, myrow, 4 * quad + 3);
-                if (i < ncopy) {
+    if (warp != 1) {
+        // ---- producers (every warp but the MMA warp): 16-byte cp.async copies of
+        // stage it into the swizzled blocks once the MMAs of its previous use are
+        // done; rows past the share's end are written as zeros.  A thread's copies
+        // of stage it - kLag are complete once stage it is committed and at most
+        // kLag groups remain; it then makes them visible to the tensor core (proxy
+        // fence) and arrives on that stage's full barrier.
+        constexpr int kLag = kTgNS - 1;
+        const int pt = threadIdx.x < 32 ? threadIdx.x : threadIdx.x - 32;   // 0 .. kUmThreads - 33
+        constexpr int kProd = kUmThreads - 32;
+        const int nblk = nbB + nbA;
+        const int chunks = nblk * kTgK * 8;
+        const __half *X16 = reinterpret_cast<const __half *>(x16);
+        for (int it = 0; it < nst + kLag; ++it) {
+            if (it < nst) {
+                const int s = it % kTgNS;
+                if (it >= kTgNS && !warp_wait(&empty[s], (unsigned)((it / kTgNS) - 1) & 1u, err, lane)) {
+                    abort_flag = 1;
+                    break;
+                }
+                if (*(volatile int *)&abort_flag) break;
+                const long long rb = r0 + (long long)it * kTgK;
+                const int valid = (int)(r1 - rb < kTgK ? r1 - rb : kTgK);
+                const unsigned st = sbase + (unsigned)s * kTgStage;
+                for (int e = pt; e < chunks; e += kProd) {
+                    const int c = e & 7, blk = (e >> 3) % nblk, k = (e >> 3) / nblk;
                     const bool isb = blk < nbB;
-                    const int x = isb ? b0 + kTgF * blk : a0 + kTgF * (blk - nbB);
-                    const unsigned dst =
-                        st + (isb ? (unsigned)blk * kTgBlk : (unsigned)kTgBBytes + (unsigned)(blk - nbB) * kTgBlk) +
-                        (unsigned)quad * 512u;
-                    tma_gather4(dst, &xmap, x, y0, y1, y2, y3, smem_u32(&full[s]));
+                    const unsigned dst = st + (isb ? (unsigned)blk * kTgBlk : (unsigned)kTgBBytes + (unsigned)(blk - nbB) * kTgBlk) +
+                                         (unsigned)k * 128u + ((unsigned)(c ^ (k & 7)) << 4);
+                    if (k < valid) {
+                        const int x = (isb ? b0 + kTgF * blk : a0 + kTgF * (blk - nbB)) + 8 * c;
+                        const __half *src = X16 + (long long)__ldg(&J[rb + k]) * x16_ld + x;
+                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+                    } else {
+                        asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};" ::"r"(dst), "r"(0u) : "memory");
+                    }
                 }
             }
-            issued = it + 1;
+            asm volatile("cp.async.commit_group;" ::: "memory");
+            if (it >= kLag) {
+                asm volatile("cp.async.wait_group %0;" ::"n"(kLag) : "memory");
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive(&full[(it - kLag) % kTgNS]);
+            }
         }
+        asm volatile("cp.async.wait_all;" ::: "memory");
     } else if (warp == 1) {
         // ---- the MMAs of each stage (rows past the share's end zeroed first) ----
         const unsigned idesc = umma_idesc_f16_mn(kTgAM, nb);
@@ -446,18 +442,6 @@ __global__ void __launch_bounds__(kUmThreads, 2) gram_f16_wide_kernel(const __gr
             }
             const long long rb = r0 + (long long)it * kTgK;
             const int valid = (int)(r1 - rb < kTgK ? r1 - rb : kTgK);
-            unsigned char *stp = base + (size_t)s * kTgStage;
-            if (valid < kTgK) {
-                const int nz = kTgK - valid;
-                for (int e = lane; e < (nbB + nbA) * nz * 8; e += 32) {
-                    const int blk = e / (nz * 8), rem = e - blk * nz * 8;
-                    const int k = valid + rem / 8, c = rem % 8;
-                    unsigned char *bp = blk < nbB ? stp + blk * kTgBlk : stp + kTgBBytes + (blk - nbB) * kTgBlk;
-                    *reinterpret_cast<float4 *>(bp + k * 128 + c * 16) = make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                __syncwarp();
-            }
             if (lane == 0) {
                 tc_fence_after();
                 const unsigned sb = sbase + (unsigned)s * kTgStage;
@@ -481,11 +465,6 @@ __global__ void __launch_bounds__(kUmThreads, 2) gram_f16_wide_kernel(const __gr
     __syncthreads();
     if (threadIdx.x == 0) {
         if (mma_count > 0 && !mbar_wait_bounded(&done, 0u, err)) abort_flag = 1;
-        if (abort_flag) {
-            // a wait gave up: the copies already issued land before the block leaves
-            for (int it = issued - kTgNS < 0 ? 0 : issued - kTgNS; it < issued; ++it)
-                mbar_wait_bounded(&full[it % kTgNS], (unsigned)(it / kTgNS) & 1u, err);
-        }
     }
     tc_fence_before();
     __syncthreads();
@@ -549,27 +528,30 @@ __global__ void x16_scale_kernel(int q, const unsigned *__restrict__ cmax, int *
     }
 }
 
-__global__ void x16_convert_kernel(const float *__restrict__ X, long long n, int q, const int *__restrict__ kf,
-                                   __half *__restrict__ X16)
+// rows of ld >= q entries (a multiple of 64: every 128-byte box of a row
+// starts on a 128-byte line), zero past q
+__global__ void x16_convert_kernel(const float *__restrict__ X, long long n, int q, int ld,
+                                   const int *__restrict__ kf, __half *__restrict__ X16)
 {
-    const long long total = n * q;
+    const long long total = n * ld;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
-        const int f = (int)(e % q);
-        X16[e] = __float2half_rn(ldexpf(X[e], __ldg(&kf[f])));
+        const long long i = e / ld;
+        const int f = (int)(e - i * ld);
+        X16[e] = f < q ? __float2half_rn(ldexpf(X[i * q + f], __ldg(&kf[f]))) : __float2half_rn(0.f);
     }
 }
 
 int g_wg_attr = 0;
 
 // Exact column sums of the gathered rows: block b sums its contiguous share
-// of J in row order (TwoSum per feature, four features per thread), the last
-// block to finish adds the nb partials in block order (eight lanes per column,
-// a fixed shuffle order).
+// of J in row order (TwoSum per feature, four features per thread) into
+// part[b]; colsum_reduce_kernel then adds the nb partials of each column in
+// block order (eight lanes per column, a fixed shuffle order), 32 columns per
+// block.
 __global__ void __launch_bounds__(256) colsum_kernel(const float *__restrict__ X, int q,
                                                      const int32_t *__restrict__ J, long long p,
-                                                     float2 *__restrict__ part, unsigned *counter,
-                                                     float2 *__restrict__ H)
+                                                     float2 *__restrict__ part)
 {
     const int G = gridDim.x, c = threadIdx.x;
     const bool has = 4 * c < q;
@@ -605,47 +587,19 @@ __global__ void __launch_bounds__(256) colsum_kernel(const float *__restrict__ X
             part[(size_t)blockIdx.x * q + 4 * c + k] = make_float2(hi, lo);
         }
     }
-    __threadfence();
-    __syncthreads();
-    __shared__ int last;
-    if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == (unsigned)(G - 1);
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    const int lane = threadIdx.x & 31, sub = lane & 7;
-    for (int j0 = (threadIdx.x >> 3); j0 < ((q + 3) & ~3); j0 += blockDim.x >> 3) {
-        const int j = j0 < q ? j0 : q - 1;
-        float2 t = make_float2(0.f, 0.f);
-        for (int b = sub; b < G; b += 8) t = dfx_add(t, __ldcg(&part[(size_t)b * q + j]));
-#pragma unroll
-        for (int o = 1; o < 8; o <<= 1) t = dfx_add(t, shfl_xor_f2(t, o));
-        if (sub == 0 && j0 < q) H[j] = t;
-    }
-    if (threadIdx.x == 0) *counter = 0u;
 }
 
-// The tensor map of X16 (n x q FP16, row-major) for tile::gather4: 64-feature
-// (128-byte) boxes one row high, 128-byte swizzle.  The encoder is the
-// driver's, reached through the runtime (no link against libcuda).
-cudaError_t encode_xmap(Work &W)
+__global__ void __launch_bounds__(256) colsum_reduce_kernel(int q, int nb, const float2 *__restrict__ part,
+                                                            float2 *__restrict__ H)
 {
-    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-    if (!encode) {
-        void *fn = nullptr;
-        cudaDriverEntryPointQueryResult qr = cudaDriverEntryPointSymbolNotFound;
-        const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
-                                                               &qr);
-        if (e != cudaSuccess || qr != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
-        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-    }
-    const cuuint64_t dims[2] = {(cuuint64_t)W.q, (cuuint64_t)W.n};
-    const cuuint64_t strides[1] = {(cuuint64_t)W.q * sizeof(__half)};
-    const cuuint32_t box[2] = {kTgF, 1};
-    const cuuint32_t estr[2] = {1, 1};
-    const CUresult r = encode(reinterpret_cast<CUtensorMap *>(W.xmap), CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, W.x16, dims,
-                              strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+    const int lane = threadIdx.x & 31, sub = lane & 7;
+    const int j0 = blockIdx.x * 32 + (threadIdx.x >> 3);
+    const int j = j0 < q ? j0 : q - 1;
+    float2 t = make_float2(0.f, 0.f);
+    for (int b = sub; b < nb; b += 8) t = dfx_add(t, __ldcg(&part[(size_t)b * q + j]));
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) t = dfx_add(t, shfl_xor_f2(t, o));
+    if (sub == 0 && j0 < q) H[j] = t;
 }
 
 // G = sum_b C_b and h = sum_b h_b in FP64, in block order (the step-level
@@ -728,7 +682,8 @@ cudaError_t x16_prepare(Work &W)
     if (!W.xf32 || W.csr || q % 16 != 0 || W.n < 1 || W.n > 0x7fffffffLL) return cudaErrorInvalidValue;
     void *x16 = nullptr;
     int *kf = nullptr;
-    if (cudaMalloc(&x16, (size_t)W.n * q * sizeof(__half)) != cudaSuccess) return cudaErrorMemoryAllocation;
+    const int ld = (q + kTgF - 1) / kTgF * kTgF;
+    if (cudaMalloc(&x16, (size_t)W.n * ld * sizeof(__half)) != cudaSuccess) return cudaErrorMemoryAllocation;
     if (cudaMalloc((void **)&kf, 2 * (size_t)q * sizeof(int)) != cudaSuccess) {
         cudaFree(x16);
         return cudaErrorMemoryAllocation;
@@ -741,10 +696,10 @@ cudaError_t x16_prepare(Work &W)
     if (e != cudaSuccess) return e;
     x16_colmax_kernel<<<4 * W.nsm, 256, 0, W.st>>>((const float *)W.X, W.n, q, cmax);
     x16_scale_kernel<<<(q + 255) / 256, 256, 0, W.st>>>(q, cmax, kf);
-    x16_convert_kernel<<<8 * W.nsm, 256, 0, W.st>>>((const float *)W.X, W.n, q, kf, reinterpret_cast<__half *>(x16));
+    x16_convert_kernel<<<8 * W.nsm, 256, 0, W.st>>>((const float *)W.X, W.n, q, ld, kf,
+                                                    reinterpret_cast<__half *>(x16));
     W.nlaunch += 3;
-    e = cudaGetLastError();
-    return e == cudaSuccess ? encode_xmap(W) : e;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_gram_umma_wide(Work &W, const int32_t *J, long long p, int KS, float *cpart, const int *skip)
@@ -759,9 +714,9 @@ cudaError_t launch_gram_umma_wide(Work &W, const int32_t *J, long long p, int KS
         if (e != cudaSuccess) return e;
         g_wg_attr = 1;
     }
-    const CUtensorMap *xm = reinterpret_cast<const CUtensorMap *>(W.xmap);
+    const int ld = (q + kTgF - 1) / kTgF * kTgF;
     gram_f16_wide_kernel<<<dim3((unsigned)wg_pairs(q), (unsigned)KS), kUmThreads, kTgSmem, W.st>>>(
-        *xm, q, W.x16_k, J, p, cpart, W.err, skip);
+        W.x16, ld, q, W.x16_k, J, p, cpart, W.err, skip);
     ++W.nlaunch;
     return cudaGetLastError();
 }
@@ -785,8 +740,9 @@ int colsum_blocks(const Work &W, long long p, int max_blocks)
 cudaError_t launch_colsum(Work &W, const int32_t *J, long long p, int nb, float2 *part, float2 *H)
 {
     if (W.csr || !W.xf32 || W.q > 1024 || W.q % 4 != 0 || nb < 1) return cudaErrorInvalidValue;
-    colsum_kernel<<<nb, 256, 0, W.st>>>((const float *)W.X, (int)W.q, J, p, part, W.rm_counter + 1, H);
-    ++W.nlaunch;
+    colsum_kernel<<<nb, 256, 0, W.st>>>((const float *)W.X, (int)W.q, J, p, part);
+    colsum_reduce_kernel<<<(unsigned)((W.q + 31) / 32), 256, 0, W.st>>>((int)W.q, nb, part, H);
+    W.nlaunch += 2;
     return cudaGetLastError();
 }
 

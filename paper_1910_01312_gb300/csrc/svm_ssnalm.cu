@@ -1357,7 +1357,6 @@ extern "C" svm_status svm_ssnalm_solve_batch(svm_ssnalm_t *h, int32_t B, const i
             sb->W.x16 = W.x16;
             sb->W.x16_k = W.x16_k;
             sb->W.x16_own = false;
-            memcpy(sb->W.xmap, W.xmap, sizeof(W.xmap));
         }
     }
     std::vector<svm_result> res((size_t)B);
