@@ -275,6 +275,16 @@ __device__ __forceinline__ void mbar_fence_init()
 {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
+// The CG's residual target for M dv = -g (|g| = gn): Algorithm 3's bound
+// min(eta, |g|^{1+tau}), tightened to max(1e-10 |g|, floor) -- floor a
+// fraction of the level at which the subproblem stops (0 at the step-level
+// entry point: the step as exact as a direct solve) -- and never below
+// 1e-14 |g|.
+__device__ __forceinline__ float cg_tol(float gn, float eta, float tau, float floor)
+{
+    return fmaxf(fminf(fminf(eta, powf(gn, 1.f + tau)), fmaxf(1e-10f * gn, floor)), 1e-14f * gn);
+}
+
 __device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");

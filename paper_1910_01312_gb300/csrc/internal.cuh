@@ -130,7 +130,7 @@ struct MfwArgs {   // the CG
     const float *Pinv;     // q x q, row-major
     const double *g;
     double *dv;
-    float eta, tau;
+    float eta, tau, floor;
     int maxit;
     double *info;          // [0] CG steps, [1] |residual| ([2] the factor's shift, from the set-up)
     int *err;
@@ -223,6 +223,7 @@ struct Work {
     float *Lf = nullptr;      // q*(q+1) FP32 factor when it does not fit in shared memory
     float2 *Mf = nullptr;     // q*q FP32 (hi, lo) split of M (double-float CG operator)
     double eta = 0.1, tau = 0.5;   // inexact-Newton constants of Algorithm 3
+    double cg_floor = 0.0;         // CG residual floor of the next Newton step (cg_tol)
     int cg_maxit = 50;
     double *part = nullptr;   // partial sums (size part_len doubles)
     size_t part_len = 0;
@@ -329,7 +330,7 @@ struct NewtonTask {
     int ks, maxit;
     float2 *part, *hpart, *Mf;
     float2 pinv, sig;
-    float eta, tau;
+    float eta, tau, floor;
     const double *g;
     double *dv, *info, *rdots;
     int *err;

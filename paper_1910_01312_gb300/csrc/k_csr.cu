@@ -409,7 +409,7 @@ __device__ bool last_block_sums(double (&v)[K], double *sh, double *bpart, unsig
 __global__ void __launch_bounds__(256) cg_setup_kernel(int q, long long cap, const int64_t *__restrict__ ct,
                                                        const double *__restrict__ part, const double *__restrict__ g,
                                                        double sigma, long long pc, double eta, double tau,
-                                                       CsrCg *st, double *__restrict__ h, double *__restrict__ dinv,
+                                                       double floor, CsrCg *st, double *__restrict__ h, double *__restrict__ dinv,
                                                        double *__restrict__ x, double *__restrict__ r,
                                                        double *__restrict__ z, double *__restrict__ d,
                                                        float2 *__restrict__ dsplit, double *__restrict__ bpart,
@@ -444,8 +444,9 @@ __global__ void __launch_bounds__(256) cg_setup_kernel(int q, long long cap, con
     double tot[3];
     if (last_block_sums<3>(v, sh, bpart, counter, tot) && threadIdx.x == 0) {
         const double gn = sqrt(tot[2]);
+        // as cg_tol (common.cuh) in FP64
         double tol = fmin(eta, pow(gn, 1.0 + tau));
-        tol = fmin(tol, 1e-10 * gn);
+        tol = fmin(tol, fmax(1e-10 * gn, floor));
         st->rz = tot[0];
         st->hp = tot[1];
         st->tol2 = tol * tol;
@@ -790,7 +791,7 @@ cudaError_t newton_csr_t(Work &W, const int32_t *J, long long p, double sigma, c
     const bool mx = mixed_csr(W);
     float2 *dsp = mx ? W.csr_df : nullptr;
     if (mx && (e = cudaMemsetAsync(W.csr_tnf, 0, sizeof(float2) * W.n, W.st)) != cudaSuccess) return e;
-    cg_setup_kernel<<<G, 256, 0, W.st>>>(q, cs.cap, cs.ct, cs.part, g, sigma, p, W.eta, W.tau, st, W.h, dinv, x, r, z,
+    cg_setup_kernel<<<G, 256, 0, W.st>>>(q, cs.cap, cs.ct, cs.part, g, sigma, p, W.eta, W.tau, W.cg_floor, st, W.h, dinv, x, r, z,
                                          d, dsp, st->bpart, &st->counter);
     ++W.nlaunch;
     const int maxit = W.csr_cg_maxit;

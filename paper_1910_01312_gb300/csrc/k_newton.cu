@@ -460,9 +460,9 @@ __device__ bool cg_load_factor(CgSmem &S, int q, const float2 *__restrict__ Mf, 
 
 __device__ __forceinline__ void newton_cg_fast_body(int q, const float2 *__restrict__ Mf,
                                                     const double *__restrict__ g, double *__restrict__ dv,
-                                                    float eta, float tau, int maxit, double *__restrict__ info,
-                                                    int *err, const double *__restrict__ vdot,
-                                                    double *__restrict__ rdots)
+                                                    float eta, float tau, float floor, int maxit,
+                                                    double *__restrict__ info, int *err,
+                                                    const double *__restrict__ vdot, double *__restrict__ rdots)
 {
     extern __shared__ float4 cg_sm4[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
@@ -492,7 +492,7 @@ __device__ __forceinline__ void newton_cg_fast_body(int q, const float2 *__restr
     __syncthreads();
     float2 rr = cg_dot(S.R, S.R, qp, red);
     const float gn = sqrtf(fmaxf(rr.x, 0.f));
-    const float tol = fmaxf(fminf(fminf(eta, powf(gn, 1.f + tau)), 1e-10f * gn), 1e-14f * gn);
+    const float tol = cg_tol(gn, eta, tau, floor);
     const float tol2 = tol * tol;
     cg_precond(S, qp);
     if (tid < qp) { S.Z[tid] = make_float2(S.t[tid], 0.f); S.P[tid] = S.Z[tid]; }
@@ -592,18 +592,18 @@ __device__ __forceinline__ void newton_cg_fast_body(int q, const float2 *__restr
 __global__ void __launch_bounds__(kCgThreads) newton_cg_fast_kernel(int q, const float2 *__restrict__ Mf,
                                                                     const double *__restrict__ g,
                                                                     double *__restrict__ dv, float eta, float tau,
-                                                                    int maxit, double *__restrict__ info, int *err,
-                                                                    const double *__restrict__ vdot,
+                                                                    float floor, int maxit, double *__restrict__ info,
+                                                                    int *err, const double *__restrict__ vdot,
                                                                     double *__restrict__ rdots)
 {
-    newton_cg_fast_body(q, Mf, g, dv, eta, tau, maxit, info, err, vdot, rdots);
+    newton_cg_fast_body(q, Mf, g, dv, eta, tau, floor, maxit, info, err, vdot, rdots);
 }
 
 // One block per problem of a batch (blockIdx.x).
 __global__ void __launch_bounds__(kCgThreads) newton_cg_fast_batch_kernel(int q, const NewtonTask *__restrict__ T)
 {
     const NewtonTask &t = T[blockIdx.x];
-    newton_cg_fast_body(q, t.Mf, t.g, t.dv, t.eta, t.tau, t.maxit, t.info, t.err, t.vdot, t.rdots);
+    newton_cg_fast_body(q, t.Mf, t.g, t.dv, t.eta, t.tau, t.floor, t.maxit, t.info, t.err, t.vdot, t.rdots);
 }
 
 // ---------------------------------------------------------------------------
@@ -683,7 +683,7 @@ __device__ void bc_chol_solve(const float *__restrict__ Lg, const float *__restr
 
 __global__ void __launch_bounds__(kCgThreads, 1) newton_bchol_kernel(int q, const float2 *__restrict__ Mf,
                                                                   const double *__restrict__ g, double *__restrict__ dv,
-                                                                  float eta, float tau, int maxit,
+                                                                  float eta, float tau, float floor, int maxit,
                                                                   double *__restrict__ info, int *err,
                                                                   const double *__restrict__ vdot,
                                                                   double *__restrict__ rdots, float *__restrict__ Lg,
@@ -720,7 +720,7 @@ __global__ void __launch_bounds__(kCgThreads, 1) newton_bchol_kernel(int q, cons
     __syncthreads();
     float2 rr = bc_dot(R, R, q, red);
     const float gn = sqrtf(fmaxf(rr.x, 0.f));
-    const float tol = fmaxf(fminf(fminf(eta, powf(gn, 1.f + tau)), 1e-10f * gn), 1e-14f * gn);
+    const float tol = cg_tol(gn, eta, tau, floor);
     const float tol2 = tol * tol;
     auto precond = [&]() -> bool {
         if (b == 0) {
@@ -918,7 +918,7 @@ __device__ __forceinline__ void mf_finish(const float2 *X, int q, int qp, double
 __global__ void __launch_bounds__(kCgThreads) newton_mf_setup_kernel(int q, const float2 *__restrict__ Mf,
                                                                      const double *__restrict__ g,
                                                                      double *__restrict__ dv, float eta, float tau,
-                                                                     MfState *__restrict__ st,
+                                                                     float floor, MfState *__restrict__ st,
                                                                      float *__restrict__ Pinv, int *err,
                                                                      const double *__restrict__ vdot,
                                                                      double *__restrict__ rdots)
@@ -983,7 +983,7 @@ __global__ void __launch_bounds__(kCgThreads) newton_mf_setup_kernel(int q, cons
     const float2 rr = cg_dot(S.R, S.R, qp, red);
     const float2 rz = cg_dot(S.R, S.Z, qp, red);
     const float gn = sqrtf(fmaxf(rr.x, 0.f));
-    const float tol = fmaxf(fminf(fminf(eta, powf(gn, 1.f + tau)), 1e-10f * gn), 1e-14f * gn);
+    const float tol = cg_tol(gn, eta, tau, floor);
     const bool done = !(rr.x > tol * tol);
     if (tid < qp) {
         st->X[tid] = S.X[tid];
@@ -1344,7 +1344,8 @@ static cudaError_t launch_newton_mf(Work &W, const int32_t *J, long long p, doub
     }
     const double *vdot = dots ? W.v : nullptr;
     newton_mf_setup_kernel<<<1, kCgThreads, cg_fast_smem(q), W.st>>>(q, W.Mf, g, dv, (float)W.eta, (float)W.tau,
-                                                                     W.mf_st, W.mf_pinv, W.err, vdot, W.red);
+                                                                     (float)W.cg_floor, W.mf_st, W.mf_pinv, W.err,
+                                                                     vdot, W.red);
     const float2 sig = split2(sigma), rp = split2(1.0 / (double)p);
     float2 *pp = reinterpret_cast<float2 *>(W.part);
     const int G = W.nsm;
@@ -1395,6 +1396,7 @@ bool newton_task(const Work &W, const int32_t *J, long long p, double sigma, con
     t->pinv = split2(1.0 / (double)p);
     t->sig = split2(sigma);
     t->eta = (float)W.eta;
+    t->floor = (float)W.cg_floor;
     t->tau = (float)W.tau;
     t->g = g;
     t->dv = dv;
@@ -1475,7 +1477,8 @@ static cudaError_t launch_newton_bchol(Work &W, const double *g, double *dv, dou
     float *Dg = reinterpret_cast<float *>(xch + 2 * kBcMaxQ);
     int *fflag = reinterpret_cast<int *>(Dg + dg_floats);
     unsigned *bar = W.bar;
-    void *args[] = {&qq, &Mf, &g, &dv, &eta, &tau, &maxit, &info, &err, &vd, &rd, &Lg, &Dg, &xch, &fflag, &bar};
+    float floor = (float)W.cg_floor;
+    void *args[] = {&qq, &Mf, &g, &dv, &eta, &tau, &floor, &maxit, &info, &err, &vd, &rd, &Lg, &Dg, &xch, &fflag, &bar};
     return cudaLaunchCooperativeKernel((const void *)newton_bchol_kernel, dim3(G), dim3(kCgThreads), args, smem, W.st);
 }
 
@@ -1500,8 +1503,8 @@ cudaError_t launch_newton(Work &W, const int32_t *J, long long p_host, const lon
             gram_df_kernel<<<dim3(ntiles, (unsigned)t.ks), 256, 0, W.st>>>((const float *)W.X, q, J, p_host, t.ks,
                                                                             t.part, t.hpart, 1);
             build_m_df_kernel<<<W.nsm * 2, 256, 0, W.st>>>(q, t.ks, t.part, t.hpart, t.pinv, t.sig, t.Mf);
-            newton_cg_fast_kernel<<<1, kCgThreads, cg_fast_smem(q), W.st>>>(q, t.Mf, t.g, t.dv, t.eta, t.tau, t.maxit,
-                                                                            t.info, t.err, t.vdot, t.rdots);
+            newton_cg_fast_kernel<<<1, kCgThreads, cg_fast_smem(q), W.st>>>(q, t.Mf, t.g, t.dv, t.eta, t.tau, t.floor,
+                                                                            t.maxit, t.info, t.err, t.vdot, t.rdots);
             W.nlaunch += 3;
             return cudaGetLastError();
         }
@@ -1556,8 +1559,8 @@ cudaError_t launch_newton(Work &W, const int32_t *J, long long p_host, const lon
                 g_cgs_attr = 1;
             }
             newton_cg_fast_kernel<<<1, kCgThreads, smem_new, W.st>>>(q, W.Mf, g, dv, (float)W.eta, (float)W.tau,
-                                                                    W.cg_maxit, info, W.err, dots ? W.v : nullptr,
-                                                                    W.red);
+                                                                    (float)W.cg_floor, W.cg_maxit, info, W.err,
+                                                                    dots ? W.v : nullptr, W.red);
             return cudaGetLastError();
         }
         return launch_newton_bchol(W, g, dv, info, dots);

@@ -367,7 +367,7 @@ __device__ void mfw_cg_body(const MfwArgs &A, const int b, const int G)
     __syncthreads();
     float2 rr = bc_dot(Rv, Rv, q, red);
     const float gn = sqrtf(fmaxf(rr.x, 0.f));
-    const float tol = fmaxf(fminf(fminf(A.eta, powf(gn, 1.f + A.tau)), 1e-10f * gn), 1e-14f * gn);
+    const float tol = cg_tol(gn, A.eta, A.tau, A.floor);
     const float tol2 = tol * tol;
 
     // z = Pinv r, rows shared out over the grid's warps; Zv = (z, 0)
@@ -760,6 +760,7 @@ cudaError_t newton_mfw_prepare(Work &W, const int32_t *J, long long p, double si
     a.dv = dv;
     a.eta = (float)W.eta;
     a.tau = (float)W.tau;
+    a.floor = (float)W.cg_floor;
     a.maxit = W.cg_maxit;
     a.info = info;
     a.err = W.err;

@@ -603,12 +603,20 @@ struct Run {
     bool has_task = false;       // ... and this phase's step was left there
     NewtonTask task;
     bool has_wtask = false;      // a wide step was prepared and left to the batch launch
+    double t_in = 0.0;           // the level at which the current subproblem stops (|g| <= t_in)
     int cont = 0;                // batched: what follows a recorded projection (a RunCont)
 };
 
 // The kernels of a phase that follow its projection, when the projection was
 // recorded for a batched launch (run_post_cont issues them after it).
 enum RunCont { RC_NONE = 0, RC_READBACK = 1, RC_SUBSTART = 2, RC_TRIAL = 3 };
+
+// The CG of a Newton step stops once its residual is below kCgFloor times the
+// level at which the subproblem stops (and within Algorithm 3's bound): the
+// step's new gradient is then about that residual, so the subproblem's last
+// step still ends it, while earlier steps, whose gradients are far above the
+// level, are not solved to 1e-10 of |g|.
+constexpr double kCgFloor = 0.01;
 
 static void mv_add(Work &W, MvReq &m, const double *v, float2 *zf, double *z)
 {
@@ -785,6 +793,8 @@ static svm_status run_pre(Run &r)
         const long long p = W.h_pout[1 + r.cur].p;
         const double sigma = r.sigma;
         const int cur = r.cur;
+        // CG is run to kCgFloor x the subproblem's stopping level (within Algorithm 3's bound)
+        W.cg_floor = kCgFloor * r.t_in;
         r.has_task = r.defer_newton && newton_task(W, W.pb[cur].J, p, sigma, W.g, W.dv, true, &r.task);
         r.has_wtask = !r.has_task && r.defer_newton && newton_is_wide(W, p);
         if (r.has_task) {
@@ -943,6 +953,7 @@ static svm_status inner_check(Run &r)
     if (h->trace)
         fprintf(stderr, "[svm] k=%d j=%d sigma=%.3g p=%lld s=%lld |g|=%.3e tol=%.3e passes=%d lam=%.6g\n", r.k, r.j,
                 r.sigma, (long long)m.p, (long long)m.s, gn, fmax(tol_in, floor_g), m.passes, m.lam);
+    r.t_in = fmax(tol_in, floor_g);
     if (gn <= fmax(tol_in, floor_g) || r.j >= P.max_inner) {
         r.inner_total += r.j;
         r.ph = RP_OUTER_END;
@@ -1569,6 +1580,7 @@ extern "C" svm_status svm_op_newton(svm_ssnalm_t *h, const int32_t *J, int64_t p
 {
     if (!h || !g || !dv || p < 0 || (p > 0 && !J) || !(sigma > 0.0)) return SVM_ERR_INVALID_ARG;
     Work &W = h->W;
+    W.cg_floor = 0.0;   // the step as exact as a direct solve
     CK(timed(h, TK_NEWTON, [&] { return launch_newton(W, J, p, nullptr, sigma, g, dv); }));
     return sync_read(h);
 }
