@@ -394,12 +394,29 @@ __global__ void __launch_bounds__(kUmThreads, 2) gram_f16_wide_kernel(const void
         constexpr int kLag = kTgNS - 1;
         const int pt = threadIdx.x < 32 ? threadIdx.x : threadIdx.x - 32;   // 0 .. kUmThreads - 33
         constexpr int kProd = kUmThreads - 32;
+        static_assert(kProd % 8 == 0 && kProd / 8 == 28, "chunk stepping assumes 28 rows of 8 chunks per round");
         const int nblk = nbB + nbA;
         const int chunks = nblk * kTgK * 8;
         const __half *X16 = reinterpret_cast<const __half *>(x16);
+        // chunk e = pt + kProd u: 16-byte chunk c = e & 7 (fixed per thread) of
+        // block (e >> 3) % nblk of stage row (e >> 3) / nblk; (block, row)
+        // advance by 28 blocks a round, i.e. by (28 / nblk, 28 % nblk)
+        const int c = pt & 7;
+        const int blk0 = (pt >> 3) % nblk, k0 = (pt >> 3) / nblk;
+        const int dk = 28 / nblk, dblk = 28 % nblk;
+        const int rounds = (chunks + kProd - 1) / kProd;   // the same in every warp
+        // lane k holds the row index of stage row k, one stage ahead
+        auto stage_row = [&](int st2) -> int {
+            if (st2 >= nst) return 0;
+            const long long r = r0 + (long long)st2 * kTgK + lane;
+            return __ldg(&J[r < r1 ? r : r1 - 1]);
+        };
+        int jnext = stage_row(0);
         for (int it = 0; it < nst + kLag; ++it) {
             if (it < nst) {
                 const int s = it % kTgNS;
+                const int jrow = jnext;
+                jnext = stage_row(it + 1);
                 if (it >= kTgNS && !warp_wait(&empty[s], (unsigned)((it / kTgNS) - 1) & 1u, err, lane)) {
                     abort_flag = 1;
                     break;
@@ -408,17 +425,27 @@ __global__ void __launch_bounds__(kUmThreads, 2) gram_f16_wide_kernel(const void
                 const long long rb = r0 + (long long)it * kTgK;
                 const int valid = (int)(r1 - rb < kTgK ? r1 - rb : kTgK);
                 const unsigned st = sbase + (unsigned)s * kTgStage;
-                for (int e = pt; e < chunks; e += kProd) {
-                    const int c = e & 7, blk = (e >> 3) % nblk, k = (e >> 3) / nblk;
-                    const bool isb = blk < nbB;
-                    const unsigned dst = st + (isb ? (unsigned)blk * kTgBlk : (unsigned)kTgBBytes + (unsigned)(blk - nbB) * kTgBlk) +
-                                         (unsigned)k * 128u + ((unsigned)(c ^ (k & 7)) << 4);
-                    if (k < valid) {
-                        const int x = (isb ? b0 + kTgF * blk : a0 + kTgF * (blk - nbB)) + 8 * c;
-                        const __half *src = X16 + (long long)__ldg(&J[rb + k]) * x16_ld + x;
-                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
-                    } else {
-                        asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};" ::"r"(dst), "r"(0u) : "memory");
+                int blk = blk0, k = k0;
+                for (int u = 0; u < rounds; ++u) {
+                    const int row = __shfl_sync(0xffffffffu, jrow, k & 31);
+                    if (pt + kProd * u < chunks) {
+                        const bool isb = blk < nbB;
+                        const unsigned dst = st +
+                                             (isb ? (unsigned)blk * kTgBlk : (unsigned)kTgBBytes + (unsigned)(blk - nbB) * kTgBlk) +
+                                             (unsigned)k * 128u + ((unsigned)(c ^ (k & 7)) << 4);
+                        if (k < valid) {
+                            const int x = (isb ? b0 + kTgF * blk : a0 + kTgF * (blk - nbB)) + 8 * c;
+                            const __half *src = X16 + (long long)row * x16_ld + x;
+                            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+                        } else {
+                            asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};" ::"r"(dst), "r"(0u) : "memory");
+                        }
+                    }
+                    blk += dblk;
+                    k += dk;
+                    if (blk >= nblk) {
+                        blk -= nblk;
+                        ++k;
                     }
                 }
             }
