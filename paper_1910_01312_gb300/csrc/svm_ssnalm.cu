@@ -340,6 +340,13 @@ static svm_status create_impl(svm_ssnalm_t **out, const svm_problem *prob, const
     size_t part_gram = (size_t)(4 * W.nsm) * (q * q + q);
     const size_t gram_cap = ((size_t)32 << 20) / sizeof(double);
     if (part_gram > gram_cap) part_gram = gram_cap > (q * q + q) ? gram_cap : (q * q + q);
+    if (!csr && W.precision == SVM_PREC_MIXED && q > 128 && q <= 1024 && q % 16 == 0) {
+        // the wide Gram's row splits: enough (128 x 256)-tile blocks for two per SM
+        const size_t np = (size_t)gram_wide_pairs((int)q);
+        const size_t ks = (2 * (size_t)W.nsm + np - 1) / np;
+        const size_t need = (ks * (q * q + 2 * q) + 1) / 2;   // FP32 partials, counted in doubles
+        if (part_gram < need) part_gram = need;
+    }
     size_t part_rm = (size_t)2 * W.rm_grid * q;
     if (csr) part_gram = part_rm = 0;   // no dense Gram, no row-block partials
     const size_t qq = csr ? 1 : q * q;   // the dense q x q Newton matrices
