@@ -458,7 +458,7 @@ __global__ void __launch_bounds__(kUmThreads, 2) gram_f16_wide_kernel(const void
         }
         asm volatile("cp.async.wait_all;" ::: "memory");
     } else if (warp == 1) {
-        // ---- the MMAs of each stage (rows past the share's end zeroed first) ----
+        // ---- the MMAs of each stage: two per 32 rows, one for a last stage of <= 16 ----
         const unsigned idesc = umma_idesc_f16_mn(kTgAM, nb);
         int mmas = 0;
         for (int it = 0; it < nst; ++it) {
