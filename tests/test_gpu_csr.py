@@ -212,6 +212,7 @@ def test_csr_text_shaped_solve():
     grad = yf * (X @ wr) - 1.0
     pi, _ = oracle.project(alpha - grad, y, C)
     R = np.linalg.norm(alpha - pi) / (1.0 + np.linalg.norm(alpha))
-    assert R <= 2e-6, R
+    # the solver's own target; 1e-9 covers the rounding between two FP64 evaluations
+    assert R <= 1e-6 + 1e-9, (R, r["kkt"])
     assert r["objective"] == pytest.approx(0.5 * wr @ wr - alpha.sum(), rel=1e-9)
     s.close()
