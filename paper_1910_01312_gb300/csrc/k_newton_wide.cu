@@ -686,11 +686,15 @@ cudaError_t newton_mfw_reset(Work &W)
     return cudaMemsetAsync(W.mfw_st, 0, sizeof(MfwState), W.st);
 }
 
-// Large free set, 128 < q <= 1024 (dense FP32 X, q % 16 == 0): tensor-core
-// Gram -> preconditioner -> matrix-free CG.  Workspace: the Gram partials in
-// W.part (consumed by build_m_tc), then W.part holds the 8 x 8 diagonal
-// inverses, the inverse tiles, the CG's exchange vectors and the factor's flag;
-// Pinv and h sit in W.M (unused by the mixed form), the factor in W.Lf.
+// Large free set, 128 < q <= 1024 (dense FP32 X, q % 16 == 0): exact column
+// sums -> tensor-core Gram -> M_pre -> preconditioner -> matrix-free CG.
+// Workspace: the column sums' block partials in the region of the CG's chunk
+// partials, then the Gram partials from the start of W.part (consumed by
+// mfw_build_m_kernel), then W.part holds the 8 x 8 diagonal inverses, the
+// inverse tiles, the CG's exchange vectors and the factor's flag; Pinv and h
+// sit in W.M (unused by the mixed form), the factor in W.Lf.  prepare issues
+// the ordinary launches and fills W.mfw_s / W.mfw_c; run (or the batch's
+// grouped run) issues the two cooperative ones.
 cudaError_t newton_mfw_prepare(Work &W, const int32_t *J, long long p, double sigma, const double *g, double *dv,
                                bool dots)
 {
