@@ -179,8 +179,12 @@ svm_status svm_ssnalm_solve(svm_ssnalm_t *h, const double *alpha0, svm_result *r
  * synchronisation, problems that have converged drop out, and the forward
  * products A v of all problems in a phase share passes over X (1, 2, 4 or 8
  * vectors per pass, split by an autotuner that times the pass widths on this
- * X at the first call).  Each problem's iterates, and so its results, are
- * bit-identical to svm_ssnalm_solve of the same problem (cold start).
+ * X at the first call); the Newton steps of a phase also run together (for
+ * q <= 128 in three launches over all problems; for 128 < q <= 1024 the
+ * preconditioner set-ups in one cooperative launch and the CGs in another, a
+ * group of blocks per problem, all problems sharing one FP16 copy of X).
+ * Each problem's iterates, and so its results, are bit-identical to
+ * svm_ssnalm_solve of the same problem (cold start).
  * Memory kind as the handle's: Y (B*n int8), alpha (B*n FP64, row b = problem
  * b) and w (B*q FP64) are device pointers for SVM_MEM_DEVICE, host pointers
  * for SVM_MEM_HOST; C (B doubles) and results (B entries) are host memory.
